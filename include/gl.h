@@ -1,0 +1,169 @@
+/*
+ * gl.h -- C-ABI of the B300 oblate-planet transit library (libgl.so).
+ *
+ * The library evaluates relative-flux light curves of a planet shaped as an
+ * oblate spheroid at arbitrary orientation, for many parameter sets and many
+ * exposure times at once, on one NVIDIA B300 (sm_103a).
+ *
+ * Method (arxiv 2410.05408):
+ *   - sky-plane projection of the spheroid: Sec. 2, Eqs. dx, dy1, dy2, with the
+ *     oblate case b = c of Appendix A and the mean-radius parameter of Sec. 3;
+ *   - occulted stellar flux for quadratic limb darkening by Green's theorem:
+ *     the integrands f_flat, f_lin, f_quad of Sec. 2 summed over the part of
+ *     the projected boundary inside the stellar disk plus the part of the limb
+ *     inside the projection (Sec. 2 replaces the latter by "snapping"; here the
+ *     boundary is split exactly at the ellipse/limb crossings);
+ *   - orbit: Sec. 2 uses a circular orbit; here a Keplerian orbit with
+ *     eccentricity e and argument of periastron omega, t0 = time of conjunction
+ *     (true anomaly pi/2 - omega), reducing to Sec. 2 for e = 0, omega = pi/2.
+ *
+ * Conventions.  Lengths in stellar radii, times in days, angles in radians.
+ * Sky frame (Sec. 2): z along the line of sight from the observer to the star,
+ * y along the transit chord, x completing a right-handed frame.  A planet with
+ * z > 0 (behind the star) occults nothing.
+ *
+ * Memory.  Every array argument may live in host memory (pageable or pinned) or
+ * in device memory of the context's GPU; the library finds out with
+ * cudaPointerGetAttributes.  The caller owns every buffer; the library never
+ * frees or retains them after the call returns.  The context owns its own
+ * device workspace (grow-only, freed by gl_context_destroy).
+ *
+ * Errors.  Every function returns GL_OK (0) or a negative GL_E* code; the
+ * message of the last failure is kept per context (gl_last_error).  Invalid
+ * physical parameters of one set are not a call error: that set's outputs are
+ * NaN and GL_ENUMERIC is reported by the next gl_sync.
+ *
+ * Streams.  Calls are asynchronous on the given CUDA stream (NULL = the legacy
+ * default stream) when every buffer is in device memory.  When any input or the
+ * output is in host memory, the call returns only after the outputs are in
+ * place.  A context must not be used from two host threads at once.
+ */
+#ifndef GL_H
+#define GL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GL_OK 0
+#define GL_EINVAL (-1)    /* bad argument: NULL pointer, negative size, ... */
+#define GL_ENOMEM (-2)    /* device workspace could not be allocated */
+#define GL_ECUDA (-3)     /* a CUDA runtime call failed */
+#define GL_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define GL_ENUMERIC (-5)  /* a parameter set was physically invalid (output NaN) */
+
+typedef enum {
+  GL_FP64 = 0,  /* plain FP64 path: everything in double */
+  GL_FP32C = 1, /* FP32 quadrature with compensated sums; Kepler solve,
+                   intersection roots and the exposure sum in FP64 */
+} gl_precision;
+
+typedef struct gl_context gl_context;
+
+/* Parameter sets, structure of arrays, n_sets entries each (Sec. 3, Table priors):
+ *   t0      time of conjunction (days)          period  orbital period (days)
+ *   a_rs    semi-major axis / R*                b       impact parameter at conjunction,
+ *                                                       b = a_rs cos(i) (1-e^2)/(1+e sin w)
+ *   ecc     eccentricity, 0 <= e < 1            omega   argument of periastron (rad)
+ *   k       mean radius ratio r = (a b c)^(1/3)/R* (Sec. 3); the equatorial radius is
+ *           R_eq = k (1-f)^(-1/3) and the polar radius R_eq (1-f)
+ *   f       flattening (R_eq - R_pol)/R_eq, 0 <= f < 1 (Sec. 1)
+ *   eta     rotation about y' (tilt of the spin axis out of the sky plane), rad
+ *   xi      rotation about z' (position angle of the spin axis on the sky), rad;
+ *           the projected spin axis points along (cos xi, -sin xi) in (x, y)
+ *   u1, u2  quadratic limb darkening, I(mu) = 1 - u1 (1-mu) - u2 (1-mu)^2
+ */
+typedef struct {
+  int64_t n_sets;
+  const double *t0, *period, *a_rs, *b, *ecc, *omega;
+  const double *k, *f, *eta, *xi;
+  const double *u1, *u2;
+} gl_params;
+
+/* Exposure times.
+ *   t         mid-exposure times (days).
+ *   offsets   NULL: every set uses the same grid t[0 .. n_times) and the output is
+ *             n_sets x n_times, row-major.  Otherwise int64 offsets[n_sets + 1],
+ *             non-decreasing, offsets[0] = 0: set s owns t[offsets[s] ..
+ *             offsets[s+1]) and the output has the same layout (CSR).
+ *   n_times   shared-grid length (ignored when offsets != NULL).
+ *   n_total   number of exposures = length of out: n_sets * n_times for a shared
+ *             grid, offsets[n_sets] otherwise.  Must be < 2^31.
+ *   exptime   per-set exposure length (days, >= 0).
+ *   nsuper    per-set number of sub-exposures (int32, >= 1), or NULL to use
+ *             nsuper_all for every set.
+ * Sub-exposure q of an exposure at t sits at t + ((q + 1/2)/n - 1/2) exptime and
+ * the exposure's flux is the mean of its sub-exposure fluxes (the paper does not
+ * describe supersampling; this is the midpoint rule).
+ */
+typedef struct {
+  const double *t;
+  const int64_t *offsets;
+  int64_t n_times;
+  int64_t n_total;
+  const double *exptime;
+  const int32_t *nsuper;
+  int32_t nsuper_all;
+} gl_times;
+
+/* Create a context bound to CUDA device `device`; uploads the quadrature node
+ * tables to that device.  *ctx receives the handle.  GL_EINVAL if ctx is NULL or
+ * the device does not exist, GL_ECUDA on a runtime failure. */
+int gl_context_create(gl_context **ctx, int device);
+
+/* Wait for the context's outstanding work, free its workspace and the handle.
+ * Passing NULL is a no-op returning GL_OK. */
+int gl_context_destroy(gl_context *ctx);
+
+/* Message of the last failure on this context ("" if none).  The pointer stays
+ * valid until the next call on the context. */
+const char *gl_last_error(const gl_context *ctx);
+
+/* Light curves of a batch of parameter sets (Sec. 2 method, see header top).
+ *   out[j]  relative flux of exposure j (1 exactly when no sub-exposure occults
+ *           the star), FP64, n_total entries, layout as described for gl_times.
+ *   prec    GL_FP64 or GL_FP32C.
+ *   stream  cudaStream_t to run on, or NULL.
+ * Returns GL_OK, GL_EINVAL (NULL pointer, negative size, nsuper < 1, n_total
+ * inconsistent with a shared grid or >= 2^31, bad precision), GL_ENOMEM or
+ * GL_ECUDA.  Parameter sets that are physically invalid (period <= 0, a_rs <= 0,
+ * e outside [0,1), k <= 0, f outside [0,1), |cos i| > 1, non-finite values,
+ * exptime < 0, nsuper < 1, limb darkening with no flux) yield NaN outputs and a
+ * sticky GL_ENUMERIC reported by gl_sync. */
+int gl_lightcurve_batch(gl_context *ctx, const gl_params *p, const gl_times *t, double *out,
+                        gl_precision prec, void *stream);
+
+/* Relative flux for given sky positions, bypassing the orbit (geometry level
+ * of Sec. 2).  All arrays have n entries:
+ *   x0, y0, z       planet centre in the sky frame (stellar radii)
+ *   k, f, eta, xi   shape and orientation as in gl_params
+ *   u1, u2          limb darkening
+ *   out             relative flux, FP64
+ * Same memory, stream and error rules as gl_lightcurve_batch. */
+int gl_flux_sky(gl_context *ctx, int64_t n, const double *x0, const double *y0,
+                const double *z, const double *k, const double *f, const double *eta,
+                const double *xi, const double *u1, const double *u2, double *out,
+                gl_precision prec, void *stream);
+
+/* Kipping (2013) map from (q1, q2) in [0,1]^2 to quadratic coefficients,
+ * u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2) (cited in Sec. 3, Table priors,
+ * note f; the formula is not printed in the paper).  Host arrays of n entries;
+ * runs on the host, needs no context.  GL_EINVAL on NULL pointers or n < 0. */
+int gl_q_to_u(int64_t n, const double *q1, const double *q2, double *u1, double *u2);
+
+/* Wait for all work the context issued on `stream` and return the sticky status
+ * of the device-side checks since the last gl_sync (GL_OK, GL_ENUMERIC or
+ * GL_ETIMEOUT), clearing it. */
+int gl_sync(gl_context *ctx, void *stream);
+
+/* Number of kernel launches the context has issued since creation (for
+ * accounting in benchmarks). */
+int64_t gl_launch_count(const gl_context *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GL_H */
