@@ -1,0 +1,374 @@
+"""Benchmark: oblate-planet transit flux evaluations per second on one B300.
+
+Workload (default): the MCMC batch - 256 parameter sets x 2000 shared exposure
+times (29.4-min cadence) x 15 sub-exposures = 7.68e6 flux evaluations per step,
+parameters drawn uniformly over the MCMC box (seed 1).  A step is one call of
+gl_lightcurve_batch over the whole batch with inputs resident in HBM; the timed
+path is the FP32-compensated one (FP64 Kepler, roots and exposure sums), whose
+max |delta flux| against the plain FP64 GPU path is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload mcmc_batch|uneven_batch|single_transit]
+
+Under torchrun (N > 1) every rank evaluates its own batch (different seeds):
+the work units are independent, so the ranks share no data-path collective
+(weak scaling); the timed region is bracketed by barriers and the max over
+ranks is reported.  ``--impl reference`` times the FP64 CPU oracle on this
+host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2410_05408_b300 import inputs  # noqa: E402
+
+METRIC = "oblate flux evals/sec at |dflux|<=1e-7 (FP32) vs FP64 GPU path"
+UNIT = "evals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 / FP64 non-tensor peaks from unit counts x maximum SM clock (148 SMs,
+# 128 FP32 lanes and 2 FP64 lanes (measured: 1/62 of FP32) per SM, FMA = 2 flops)
+SM_COUNT = 148
+
+
+def alu_peaks(sm_mhz: float):
+    fp32 = SM_COUNT * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp64 = SM_COUNT * 2 * 2 * sm_mhz * 1e6 / 1e12
+    return fp32, fp64
+
+
+def workload(name: str, seed_offset: int = 0):
+    if name == "mcmc_batch":
+        return inputs.mcmc_batch(seed=1 + 1000 * seed_offset)
+    if name == "uneven_batch":
+        return inputs.uneven_batch(seed=2 + 1000 * seed_offset)
+    if name == "single_transit":
+        return inputs.single_transit()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def n_evals(wl) -> int:
+    n_sets = len(wl["params"]["t0"])
+    ns = wl["nsuper"]
+    if wl.get("offsets") is None:
+        per = np.full(n_sets, len(wl["t"]), dtype=np.int64)
+    else:
+        per = np.diff(wl["offsets"])
+    nsa = np.broadcast_to(np.asarray(ns, dtype=np.int64), (n_sets,))
+    return int(np.sum(per * nsa))
+
+
+def n_exposures(wl) -> int:
+    n_sets = len(wl["params"]["t0"])
+    return n_sets * len(wl["t"]) if wl.get("offsets") is None else int(wl["offsets"][-1])
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_sample(wl, max_sets: int):
+    """A bounded, seeded sample of the workload's parameter sets."""
+    n_sets = len(wl["params"]["t0"])
+    rng = np.random.default_rng(99)
+    idx = np.sort(rng.choice(n_sets, min(max_sets, n_sets), replace=False))
+    return idx
+
+
+def run_oracle(wl, idx, nthreads=0):
+    import oracle
+    p = {k: np.asarray(v, dtype=np.float64)[idx] for k, v in wl["params"].items()}
+    if "u1" not in p:
+        u = np.array([oracle.q_to_u(a, b) for a, b in zip(p.pop("q1"), p.pop("q2"))])
+        p["u1"], p["u2"] = u[:, 0].copy(), u[:, 1].copy()
+    exptime = np.broadcast_to(np.asarray(wl["exptime"], dtype=np.float64),
+                              (len(wl["params"]["t0"]),))[idx]
+    ns = wl["nsuper"]
+    ns_sub = ns if np.ndim(ns) == 0 else np.asarray(ns)[idx]
+    if wl.get("offsets") is None:
+        t_sub, off_sub = wl["t"], None
+        evals = len(idx) * len(wl["t"]) * int(ns)
+    else:
+        off = wl["offsets"]
+        lengths = np.diff(off)[idx]
+        off_sub = np.zeros(len(idx) + 1, dtype=np.int64)
+        off_sub[1:] = np.cumsum(lengths)
+        t_sub = np.concatenate([wl["t"][off[s]:off[s + 1]] for s in idx])
+        evals = int(np.sum(lengths * np.asarray(ns_sub)))
+    t0 = time.perf_counter()
+    oracle.lightcurve(p, t_sub, exptime, ns_sub, offsets=off_sub, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return evals, dt, oracle.max_threads()
+
+
+def cpu_baseline(wl, sample_sets: int):
+    idx = oracle_sample(wl, sample_sets)
+    evals, dt, cores = run_oracle(wl, idx)
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} of {len(wl['params']['t0'])} parameter sets, all their "
+                      f"exposures and sub-exposures ({evals} evals, {dt:.2f} s)"}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    sample = args.ref_sets
+    idx = oracle_sample(wl, sample)
+    for _ in range(args.warmup):
+        run_oracle(wl, idx[:1])
+    tot_evals, tot_t, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        e, dt, cores = run_oracle(wl, idx)
+        tot_evals += e
+        tot_t += dt
+    value = tot_evals / tot_t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "parallelism": "cpu-openmp"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(idx)} parameter sets per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mcmc_batch")
+    ap.add_argument("--ref-sets", type=int, default=32)
+    ap.add_argument("--cpu-sets", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2410_05408_b300 import binding, build
+
+    world, rank, local = dist_setup()
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(local)
+
+    wl = workload(args.workload, seed_offset=rank)
+    p = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in wl["params"].items()}
+    if "u1" not in p:
+        p["u1"], p["u2"] = binding.gl_q_to_u(p.pop("q1"), p.pop("q2"))
+    p = {k: p[k] for k in binding.PARAM_NAMES}
+    n_sets = len(p["t0"])
+    exptime = np.ascontiguousarray(np.broadcast_to(wl["exptime"], (n_sets,)), dtype=np.float64)
+    ns = np.ascontiguousarray(np.broadcast_to(np.asarray(wl["nsuper"], dtype=np.int32), (n_sets,)))
+    t = np.ascontiguousarray(wl["t"], dtype=np.float64)
+    offsets = wl.get("offsets")
+    offsets = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.int64)
+    n_tot = n_exposures(wl)
+    evals = n_evals(wl)
+
+    # device-resident inputs
+    dp = {k: torch.as_tensor(v, device=dev) for k, v in p.items()}
+    d_t = torch.as_tensor(t, device=dev)
+    d_exp = torch.as_tensor(exptime, device=dev)
+    d_ns = torch.as_tensor(ns, device=dev)
+    d_off = None if offsets is None else torch.as_tensor(offsets, device=dev)
+    out32 = torch.empty(n_tot, dtype=torch.float64, device=dev)
+    out64 = torch.empty(n_tot, dtype=torch.float64, device=dev)
+
+    def step(out, prec):
+        ctx.lightcurve(dp, d_t, out, d_exp, nsuper=d_ns, offsets=d_off, precision=prec,
+                       stream=stream)
+
+    # accuracy of the timed path against the FP64 GPU path
+    step(out64, binding.GL_FP64)
+    step(out32, binding.GL_FP32C)
+    torch.cuda.synchronize(dev)
+    status = ctx.sync(stream)
+    max_dflux = float((out32 - out64).abs().max().item())
+    in_transit = int((out64 < 1.0).sum().item())
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(prec, out, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        l0 = ctx.launches()
+        ctx.profile(True)
+        for i in range(k):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step(out, prec)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        kern_ms, kern_n = ctx.profile_read(binding.GL_KERNEL_CURVE)
+        ctx.profile(False)
+        return ms, ctx.launches() - l0, kern_ms / max(kern_n, 1)
+
+    for _ in range(args.warmup):
+        step(out32, binding.GL_FP32C)
+        step(out64, binding.GL_FP64)
+    torch.cuda.synchronize(dev)
+
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ms32, launches, kern32 = timed(binding.GL_FP32C, out32, args.steps)
+    barrier(world)
+    ms32 = allreduce_max(ms32, world)
+    k64 = max(3, min(args.steps, 20))
+    ms64, _, kern64 = timed(binding.GL_FP64, out64, k64)
+    ms64 = allreduce_max(ms64, world)
+    clocks = clk.summary()
+
+    value = world * evals * args.steps / (ms32 * 1e-3)
+    fp64_value = world * evals * k64 / (ms64 * 1e-3)
+
+    # end to end: pinned host inputs and output through the same public call
+    hp = {k: torch.as_tensor(v).pin_memory() for k, v in p.items()}
+    h_t = torch.as_tensor(t).pin_memory()
+    h_exp = torch.as_tensor(exptime).pin_memory()
+    h_ns = torch.as_tensor(ns).pin_memory()
+    h_off = None if offsets is None else torch.as_tensor(offsets).pin_memory()
+    h_out = torch.empty(n_tot, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        ctx.lightcurve(hp, h_t, h_out, h_exp, nsuper=h_ns, offsets=h_off,
+                       precision=binding.GL_FP32C, stream=stream)
+    barrier(world)
+    k_e2e = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.lightcurve(hp, h_t, h_out, h_exp, nsuper=h_ns, offsets=h_off,
+                       precision=binding.GL_FP32C, stream=stream)
+    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    h2d = sum(v.numel() * v.element_size() for v in hp.values()) + h_t.numel() * 8 + \
+        h_exp.numel() * 8 + h_ns.numel() * 4 + (0 if h_off is None else h_off.numel() * 8)
+    d2h = h_out.numel() * 8
+
+    if rank != 0:
+        return
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak, fp64_peak = alu_peaks(peaks.get("sm_max_mhz", 2032.0))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "evals_per_step": evals,
+                   "exposures_per_step": n_tot, "parameter_sets": n_sets,
+                   "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)"},
+        "max_dflux_vs_fp64_gpu": max_dflux, "in_transit_exposures": in_transit,
+        "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / k64},
+        "kernel_ms": {"curve_fp32c": kern32, "curve_fp64": kern64},
+        "gpu_launches": launches,
+        "status": status,
+        "clocks": clocks,
+        "e2e": {"value": world * evals * k_e2e / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "sm_mhz": peaks.get("sm_max_mhz", 2032.0)},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sets)
+    print(json.dumps(line))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,24 @@ int gl_sync(gl_context *ctx, void *stream);
  * accounting in benchmarks). */
 int64_t gl_launch_count(const gl_context *ctx);
 
+/* Kernel kinds for gl_profile_read. */
+#define GL_KERNEL_SETUP 0   /* per-set constants */
+#define GL_KERNEL_CURVE 1   /* light-curve kernel (FP64 or FP32C) */
+#define GL_KERNEL_SKY 2     /* geometry-level kernel */
+#define GL_KERNEL_KINDS 3
+
+/* Per-kernel device timing for benchmarks.  While enabled (on != 0), every
+ * kernel launch of the context is bracketed by CUDA events recorded on its
+ * launch stream (at most 65536 launches per kind are kept; later ones are not
+ * timed).  Enabling resets the accumulated times.  GL_EINVAL on a NULL context. */
+int gl_profile_enable(gl_context *ctx, int on);
+
+/* Total device time in milliseconds and number of timed launches of kernel kind
+ * `kind` since profiling was enabled.  Waits for the recorded events.
+ * GL_EINVAL on a NULL context or pointer or an unknown kind, GL_ECUDA on a
+ * runtime failure. */
+int gl_profile_read(gl_context *ctx, int kind, double *ms, int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

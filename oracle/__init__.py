@@ -19,6 +19,7 @@ through ctypes.  Functions and the passages of the paper they follow:
                           line integrals of Sec. 2 reach)
 * ``flux_sky``          - relative flux for a quadratic limb-darkening law
 * ``lightcurve``        - batch of light curves with exposure supersampling
+* ``flux_sky_batch``    - ``flux_sky`` over arrays (OpenMP)
 * ``q_to_u``            - Kipping (2013) map cited in Sec. 3 (not printed there)
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
@@ -85,7 +86,10 @@ def _load():
         lib.orc_lightcurve.restype = ctypes.c_int
         lib.orc_lightcurve.argtypes = ([ctypes.c_int64] + [pd] * 13
                                        + [ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
-                                          pd, ctypes.c_int, d, ctypes.c_int, pd])
+                                          pd, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, d,
+                                          ctypes.c_int, pd])
+        lib.orc_flux_sky_batch.restype = None
+        lib.orc_flux_sky_batch.argtypes = [ctypes.c_int64] + [pd] * 9 + [d, ctypes.c_int, pd]
         lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_max_threads.argtypes = []
         _lib = lib
@@ -154,14 +158,15 @@ PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi
                "u1", "u2")
 
 
-def lightcurve(params: dict, t, exptime, nsuper: int, offsets=None,
+def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
                tol: float = DEFAULT_TOL, nthreads: int = 0) -> np.ndarray:
     """Supersampled light curves for a batch of parameter sets.
 
     ``params`` maps each of PARAM_NAMES to an array of n_sets floats.  With
     ``offsets`` None, ``t`` is one grid shared by every set and the result has
     shape (n_sets, len(t)); otherwise set s owns t[offsets[s]:offsets[s+1]] and the
-    result is flat in the same layout.
+    result is flat in the same layout.  ``nsuper`` is an int or an array of
+    n_sets ints.
     """
     lib = _load()
     arrs = [np.ascontiguousarray(np.asarray(params[n], dtype=np.float64).reshape(-1))
@@ -179,12 +184,28 @@ def lightcurve(params: dict, t, exptime, nsuper: int, offsets=None,
         out = np.empty(int(offsets[-1]))
         offp = offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         n_times = 0
+    if np.ndim(nsuper) == 0:
+        ns_arr, ns_p, ns_all = None, None, int(nsuper)
+    else:
+        ns_arr = np.ascontiguousarray(np.asarray(nsuper, dtype=np.int32))
+        ns_p, ns_all = ns_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0
     st = lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], _p(t), offp, n_times,
-                            _p(exptime), int(nsuper), float(tol), int(nthreads), _p(out))
+                            _p(exptime), ns_p, ns_all, float(tol), int(nthreads), _p(out))
     if st != 0:
         raise ValueError("oracle rejected its inputs")
     if offsets is None:
         return out.reshape(n_sets, t.size)
+    return out
+
+
+def flux_sky_batch(x0, y0, z, k, f, eta, xi, u1, u2, tol: float = DEFAULT_TOL,
+                   nthreads: int = 0) -> np.ndarray:
+    """Relative flux for arrays of sky positions and shapes (k, f, eta, xi)."""
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+            for a in (x0, y0, z, k, f, eta, xi, u1, u2)]
+    n = arrs[0].size
+    out = np.empty(n)
+    _load().orc_flux_sky_batch(n, *[_p(a) for a in arrs], float(tol), int(nthreads), _p(out))
     return out
 
 
@@ -194,4 +215,5 @@ def max_threads() -> int:
 
 __all__ = ["build", "kepler_E", "cos_inclination", "sky_position", "projected_ellipse",
            "oblate_ellipse", "q_to_u", "occulted_moments", "flux_sky", "lightcurve",
+           "flux_sky_batch",
            "max_threads", "PARAM_NAMES", "DEFAULT_TOL", "math"]

@@ -404,6 +404,7 @@ double orc_flux_sky(double x0, double y0, double z, double dx, double dy1, doubl
 /* Parameter sets in structure-of-arrays form; all arrays have n_sets entries.
  * Times: if offsets == NULL, every set uses the same n_times grid t[0..n_times);
  * otherwise set s owns t[offsets[s] .. offsets[s+1]) and out has the same layout.
+ * nsuper_arr (per set) or, if NULL, nsuper_all sub-exposures per exposure.
  * Sub-exposure s of exposure j sits at t_j + ((s + 1/2)/n_s - 1/2) * exptime and
  * the exposure flux is their arithmetic mean (supersampling is not described in
  * the paper; this is the midpoint reading).  Returns 0, or -1 on bad input. */
@@ -412,9 +413,9 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
                    const double *omega, const double *k, const double *f,
                    const double *eta, const double *xi, const double *u1,
                    const double *u2, const double *t, const int64_t *offsets,
-                   int64_t n_times, const double *exptime, int nsuper, double tol,
-                   int nthreads, double *out) {
-    if (n_sets < 0 || nsuper <= 0) return -1;
+                   int64_t n_times, const double *exptime, const int32_t *nsuper_arr,
+                   int nsuper_all, double tol, int nthreads, double *out) {
+    if (n_sets < 0 || (!nsuper_arr && nsuper_all <= 0)) return -1;
     int64_t total = offsets ? offsets[n_sets] : n_sets * n_times;
     gl_init();
 #ifdef _OPENMP
@@ -440,6 +441,8 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
         double dx, dy1, dy2;
         orc_oblate_ellipse(k[s], f[s], eta[s], xi[s], &dx, &dy1, &dy2);
         double cosi = orc_cos_inclination(b[s], a_rs[s], ecc[s], omega[s]);
+        int nsuper = nsuper_arr ? nsuper_arr[s] : nsuper_all;
+        if (nsuper <= 0) { out[j] = NAN; continue; }
         double acc = 0.0;
         for (int q = 0; q < nsuper; ++q) {
             double tq = tj + ((q + 0.5) / nsuper - 0.5) * exptime[s];
@@ -451,6 +454,23 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
         out[j] = acc / nsuper;
     }
     return 0;
+}
+
+/* Relative flux for n given sky positions and shapes (OpenMP over items). */
+void orc_flux_sky_batch(int64_t n, const double *x0, const double *y0, const double *z,
+                        const double *k, const double *f, const double *eta, const double *xi,
+                        const double *u1, const double *u2, double tol, int nthreads,
+                        double *out) {
+    gl_init();
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double dx, dy1, dy2;
+        orc_oblate_ellipse(k[i], f[i], eta[i], xi[i], &dx, &dy1, &dy2);
+        out[i] = orc_flux_sky(x0[i], y0[i], z[i], dx, dy1, dy2, u1[i], u2[i], tol);
+    }
 }
 
 /* Number of OpenMP threads the oracle would use (for reporting). */

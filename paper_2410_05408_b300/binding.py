@@ -1,0 +1,250 @@
+"""Thin ctypes binding of ``libgl.so`` (C-ABI in include/gl.h).
+
+Argument marshalling only: every step of the light-curve path runs in the CUDA
+kernels of the library.  The functions keep the C names.  Arrays may be torch
+tensors (CUDA or CPU) or numpy arrays; they must already have the dtype the ABI
+names (float64, int64 offsets, int32 nsuper) and be contiguous - nothing is
+converted silently.  If the library has not been built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgl.so")
+
+GL_OK = 0
+GL_EINVAL = -1
+GL_ENOMEM = -2
+GL_ECUDA = -3
+GL_ETIMEOUT = -4
+GL_ENUMERIC = -5
+GL_FP64 = 0
+GL_FP32C = 1
+
+EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_lightcurve_batch",
+            "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
+            "gl_profile_read")
+
+GL_KERNEL_SETUP = 0
+GL_KERNEL_CURVE = 1
+GL_KERNEL_SKY = 2
+
+PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
+
+
+class GLError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gl error {code}: {msg}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n_sets", ctypes.c_int64)] + [(n, ctypes.c_void_p) for n in PARAM_NAMES]
+
+
+class _Times(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("n_times", ctypes.c_int64), ("n_total", ctypes.c_int64),
+                ("exptime", ctypes.c_void_p), ("nsuper", ctypes.c_void_p),
+                ("nsuper_all", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libgl.so; raises FileNotFoundError if it was not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise FileNotFoundError(f"{LIB_PATH} is missing: build it with "
+                                    "paper_2410_05408_b300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.gl_context_create.argtypes = [ctypes.POINTER(vp), i32]
+        lib.gl_context_create.restype = i32
+        lib.gl_context_destroy.argtypes = [vp]
+        lib.gl_context_destroy.restype = i32
+        lib.gl_last_error.argtypes = [vp]
+        lib.gl_last_error.restype = ctypes.c_char_p
+        lib.gl_lightcurve_batch.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times),
+                                            vp, i32, vp]
+        lib.gl_lightcurve_batch.restype = i32
+        lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
+        lib.gl_flux_sky.restype = i32
+        lib.gl_q_to_u.argtypes = [i64, vp, vp, vp, vp]
+        lib.gl_q_to_u.restype = i32
+        lib.gl_sync.argtypes = [vp, vp]
+        lib.gl_sync.restype = i32
+        lib.gl_launch_count.argtypes = [vp]
+        lib.gl_launch_count.restype = i64
+        lib.gl_profile_enable.argtypes = [vp, i32]
+        lib.gl_profile_enable.restype = i32
+        lib.gl_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]
+        lib.gl_profile_read.restype = i32
+        _lib = lib
+        return lib
+
+
+def _ptr(a, dtype: str):
+    """Raw pointer of a contiguous tensor/array of the given dtype (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected contiguous {dtype} numpy array, got {a.dtype}")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        want = {"float64": torch.float64, "int64": torch.int64, "int32": torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected contiguous {dtype} tensor, got {a.dtype}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, rc):
+    if rc != GL_OK:
+        msg = load().gl_last_error(ctx)
+        raise GLError(rc, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream   # torch.cuda.Stream
+
+
+def gl_context_create(device: int = 0):
+    lib = load()
+    h = ctypes.c_void_p()
+    rc = lib.gl_context_create(ctypes.byref(h), int(device))
+    if rc != GL_OK:
+        raise GLError(rc, f"gl_context_create(device={device}) failed")
+    return h
+
+
+def gl_context_destroy(ctx) -> int:
+    return load().gl_context_destroy(ctx)
+
+
+def gl_last_error(ctx) -> str:
+    s = load().gl_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def gl_lightcurve_batch(ctx, params: dict, t, out, precision: int = GL_FP32C, offsets=None,
+                        exptime=None, nsuper=None, nsuper_all: int = 1, stream=None,
+                        check: bool = True) -> int:
+    """Marshal arrays into gl_params / gl_times and call the library.
+
+    ``params`` maps PARAM_NAMES to float64 arrays of n_sets entries; ``exptime``
+    is a float64 array of n_sets; ``nsuper`` an int32 array or None (then
+    ``nsuper_all``); ``offsets`` int64 of n_sets + 1 or None for a shared grid.
+    """
+    lib = load()
+    n_sets = int(len(params["t0"]))
+    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    n_t = int(len(t))
+    n_total = int(len(out))
+    tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"), 0 if offsets is not None else n_t,
+                n_total, _ptr(exptime, "float64"), _ptr(nsuper, "int32"), int(nsuper_all))
+    rc = lib.gl_lightcurve_batch(ctx, ctypes.byref(p), ctypes.byref(tm), _ptr(out, "float64"),
+                                 int(precision), _stream_ptr(stream))
+    if check:
+        _check(ctx, rc)
+    return rc
+
+
+def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_FP32C,
+                stream=None, check: bool = True) -> int:
+    lib = load()
+    n = int(len(out))
+    rc = lib.gl_flux_sky(ctx, n, *[_ptr(a, "float64") for a in (x0, y0, z, k, f, eta, xi, u1, u2)],
+                         _ptr(out, "float64"), int(precision), _stream_ptr(stream))
+    if check:
+        _check(ctx, rc)
+    return rc
+
+
+def gl_q_to_u(q1, q2):
+    q1 = np.ascontiguousarray(q1, dtype=np.float64)
+    q2 = np.ascontiguousarray(q2, dtype=np.float64)
+    u1 = np.empty_like(q1)
+    u2 = np.empty_like(q1)
+    rc = load().gl_q_to_u(q1.size, q1.ctypes.data, q2.ctypes.data, u1.ctypes.data, u2.ctypes.data)
+    if rc != GL_OK:
+        raise GLError(rc, "gl_q_to_u")
+    return u1, u2
+
+
+def gl_sync(ctx, stream=None) -> int:
+    return load().gl_sync(ctx, _stream_ptr(stream))
+
+
+def gl_launch_count(ctx) -> int:
+    return load().gl_launch_count(ctx)
+
+
+def gl_profile_enable(ctx, on: bool = True) -> int:
+    return load().gl_profile_enable(ctx, int(bool(on)))
+
+
+def gl_profile_read(ctx, kind: int):
+    """(total device milliseconds, number of timed launches) of a kernel kind."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, load().gl_profile_read(ctx, int(kind), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+class Context:
+    """Owns one gl_context; convenience wrappers over the C functions."""
+
+    def __init__(self, device: int = 0):
+        self.handle = gl_context_create(device)
+        self.device = device
+
+    def close(self):
+        if self.handle is not None:
+            gl_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lightcurve(self, params, t, out, exptime, nsuper=None, nsuper_all=1, offsets=None,
+                   precision=GL_FP32C, stream=None):
+        return gl_lightcurve_batch(self.handle, params, t, out, precision, offsets, exptime,
+                                   nsuper, nsuper_all, stream)
+
+    def flux_sky(self, x0, y0, z, k, f, eta, xi, u1, u2, out, precision=GL_FP32C, stream=None):
+        return gl_flux_sky(self.handle, x0, y0, z, k, f, eta, xi, u1, u2, out, precision, stream)
+
+    def sync(self, stream=None) -> int:
+        return gl_sync(self.handle, stream)
+
+    def launches(self) -> int:
+        return gl_launch_count(self.handle)
+
+    def last_error(self) -> str:
+        return gl_last_error(self.handle)
+
+    def profile(self, on: bool = True):
+        gl_profile_enable(self.handle, on)
+
+    def profile_read(self, kind: int):
+        return gl_profile_read(self.handle, kind)

@@ -1,0 +1,547 @@
+// gl_api.cu -- kernels and the C-ABI (include/gl.h) of the oblate-transit library.
+//
+// One B300 (sm_103a), one process.  Kernels:
+//   gl_setup_kernel    one thread per parameter set: projected ellipse (Sec. 2,
+//                      Eqs. dx, dy1, dy2; Appendix A), LD basis, orbit constants,
+//                      transit window (FP64)
+//   gl_curve_kernel    one thread per exposure: window test, then per
+//                      sub-exposure Kepler solve (FP64), overlap class, Green's
+//                      theorem quadrature (R = double or float) and the FP64
+//                      exposure mean
+//   gl_sky_kernel      geometry-level flux for given sky positions
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "../../include/gl.h"
+#include "gl_math.cuh"
+
+using gl::NodeRule;
+using gl::SetConst;
+
+namespace {
+
+// status bits accumulated on the device
+enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4 };
+
+// quadrature orders: FP64 path and FP32C path
+constexpr int kNodes64 = 32;
+constexpr int kNodes32 = 20;
+
+__constant__ NodeRule<double> c_rule64;
+__constant__ NodeRule<float> c_rule32;
+
+template <typename R> __device__ __forceinline__ const NodeRule<R>& rule();
+template <> __device__ __forceinline__ const NodeRule<double>& rule<double>() { return c_rule64; }
+template <> __device__ __forceinline__ const NodeRule<float>& rule<float>() { return c_rule32; }
+
+// ------------------------------------------------------------------ kernels
+struct ParamPtrs {
+  const double *t0, *period, *a_rs, *b, *ecc, *omega, *k, *f, *eta, *xi, *u1, *u2;
+  const double* exptime;
+  const int32_t* nsuper;
+  int32_t nsuper_all;
+};
+
+__global__ void gl_setup_kernel(ParamPtrs p, int64_t n_sets, const int64_t* offsets,
+                                int64_t n_total, SetConst* sets, int* status) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sets) return;
+  int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
+  SetConst c;
+  bool ok = gl::set_setup(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], p.omega[s],
+                          p.k[s], p.f[s], p.eta[s], p.xi[s], p.u1[s], p.u2[s], p.exptime[s],
+                          ns, &c);
+  sets[s] = c;
+  if (!ok) atomicOr(status, kStatusInvalidSet);
+  if (offsets) {
+    bool bad = offsets[s] > offsets[s + 1] || (s == 0 && offsets[0] != 0) ||
+               (s == n_sets - 1 && offsets[n_sets] != n_total);
+    if (bad) atomicOr(status, kStatusBadOffsets);
+  }
+}
+
+// index of the set owning exposure j in a CSR layout (offsets non-decreasing)
+__device__ __forceinline__ int64_t owner_of(const int64_t* offsets, int64_t n_sets, int64_t j) {
+  int64_t lo = 0, hi = n_sets;   // offsets[lo] <= j < offsets[hi]
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (offsets[mid] <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) gl_curve_kernel(const SetConst* __restrict__ sets,
+                                                       const double* __restrict__ t,
+                                                       const int64_t* __restrict__ offsets,
+                                                       int64_t n_times, int64_t n_sets,
+                                                       int64_t n_total,
+                                                       double* __restrict__ out) {
+  const NodeRule<R>& rl = rule<R>();
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s;
+    double tj;
+    if (offsets) {
+      s = owner_of(offsets, n_sets, j);
+      tj = t[j];
+    } else {
+      s = j / n_times;
+      tj = t[j - s * n_times];
+    }
+    const SetConst& c = sets[s];
+    if (c.flags & gl::kSetInvalid) {
+      out[j] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    double tau = gl::wrap_tau(c, tj);
+    int ns = c.nsuper;
+    if (!gl::in_window(c, tau, 0.5 * c.exptime)) {
+      out[j] = 1.0;
+      continue;
+    }
+    double acc = 0.0;
+    for (int q = 0; q < ns; ++q) {
+      double tq = tau + gl::subexposure_offset(q, ns, c.exptime);
+      acc += gl::subexposure_flux<R>(c, tq, rl);
+    }
+    out[j] = acc / ns;
+  }
+}
+
+struct SkyPtrs {
+  const double *x0, *y0, *z, *k, *f, *eta, *xi, *u1, *u2;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) gl_sky_kernel(SkyPtrs p, int64_t n, double* out,
+                                                     int* status) {
+  const NodeRule<R>& rl = rule<R>();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    SetConst c;
+    // orbit fields are placeholders: only the shape and LD parts are used
+    bool ok = gl::set_setup(0.0, 1.0, 10.0, 0.0, 0.0, 0.0, p.k[i], p.f[i], p.eta[i], p.xi[i],
+                            p.u1[i], p.u2[i], 0.0, 1, &c);
+    double x0 = p.x0[i], y0 = p.y0[i], z = p.z[i];
+    if (!ok || !isfinite(x0) || !isfinite(y0) || !isfinite(z)) {
+      out[i] = __longlong_as_double(0x7ff8000000000000LL);
+      atomicOr(status, kStatusInvalidSet);
+      continue;
+    }
+    int cls = gl::classify(c, x0, y0, z);
+    if (cls == gl::kOut) {
+      out[i] = 1.0;
+      continue;
+    }
+    R I[3];
+    gl::occulted<R>(c, x0, y0, cls, rl, I);
+    R def = (R)c.c0 * I[0] + (R)c.c1 * I[1] + (R)c.c2 * I[2];
+    out[i] = 1.0 - (double)def * c.invF0;
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on the Legendre recurrence,
+// mapped through theta = m + h sin(pi s / 2).
+template <typename R>
+NodeRule<R> build_rule(int n) {
+  NodeRule<R> r;
+  memset(&r, 0, sizeof r);
+  r.n = n;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(gl::kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double w = 2.0 / ((1.0 - z * z) * dp * dp);
+    double sg = sin(0.5 * gl::kPi * z);
+    r.sig[i] = (R)sg;
+    r.wt[i] = (R)(w * 0.5 * gl::kPi * cos(0.5 * gl::kPi * z));
+    r.cph[i] = (R)cos(gl::kPi * sg);
+    r.sph[i] = (R)sin(gl::kPi * sg);
+  }
+  return r;
+}
+
+std::mutex g_dev_mutex;
+std::vector<int> g_dev_ready;   // per device: node tables uploaded
+
+cudaError_t ensure_device_tables(int device) {
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  if ((int)g_dev_ready.size() <= device) g_dev_ready.resize(device + 1, 0);
+  if (g_dev_ready[device]) return cudaSuccess;
+  NodeRule<double> r64 = build_rule<double>(kNodes64);
+  NodeRule<float> r32 = build_rule<float>(kNodes32);
+  cudaError_t e = cudaMemcpyToSymbol(c_rule64, &r64, sizeof r64);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32, &r32, sizeof r32);
+  if (e == cudaSuccess) g_dev_ready[device] = 1;
+  return e;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct gl_context {
+  int device = 0;
+  char err[512] = {0};
+  SetConst* d_sets = nullptr;
+  size_t sets_cap = 0;
+  char* d_stage = nullptr;     // staging of host inputs
+  size_t stage_cap = 0;
+  double* d_out = nullptr;     // staging of a host output
+  size_t out_cap = 0;
+  int* d_status = nullptr;
+  int64_t launches = 0;
+  // per-kernel event timing (gl_profile_enable)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev[GL_KERNEL_KINDS];   // pairs: start, stop
+  size_t ev_used[GL_KERNEL_KINDS] = {0, 0, 0};
+};
+
+namespace {
+
+int fail(gl_context* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define GL_CUDA(ctx, call)                                                             \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      return fail((ctx), GL_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    }                                                                                  \
+  } while (0)
+
+// true if p is device (or managed) memory usable on `device`
+bool is_device_ptr(const void* p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice) return a.device == device;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return false;
+}
+
+int grow(gl_context* ctx, void** buf, size_t* cap, size_t need) {
+  if (need <= *cap) return GL_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  size_t sz = need + need / 4 + 4096;
+  if (cudaMalloc(buf, sz) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, GL_ENOMEM, "cudaMalloc of %zu bytes failed", sz);
+  }
+  *cap = sz;
+  return GL_OK;
+}
+
+// Stage a list of input arrays: device arrays pass through, host arrays are
+// copied into ctx->d_stage.  `any_host` reports whether a copy was made.
+struct StageItem {
+  const void** ptr;
+  size_t bytes;
+};
+
+int stage_inputs(gl_context* ctx, StageItem* items, int n, cudaStream_t st, bool* any_host) {
+  size_t need = 0;
+  bool host[64];
+  for (int i = 0; i < n; ++i) {
+    host[i] = (*items[i].ptr != nullptr) && !is_device_ptr(*items[i].ptr, ctx->device);
+    if (host[i]) need += (items[i].bytes + 255) & ~(size_t)255;
+  }
+  *any_host = false;
+  if (need == 0) return GL_OK;
+  int rc = grow(ctx, (void**)&ctx->d_stage, &ctx->stage_cap, need);
+  if (rc) return rc;
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!host[i]) continue;
+    char* dst = ctx->d_stage + off;
+    if (items[i].bytes) {
+      GL_CUDA(ctx, cudaMemcpyAsync(dst, *items[i].ptr, items[i].bytes, cudaMemcpyHostToDevice, st));
+    }
+    *items[i].ptr = dst;
+    off += (items[i].bytes + 255) & ~(size_t)255;
+    *any_host = true;
+  }
+  return GL_OK;
+}
+
+constexpr size_t kMaxTimed = 65536;
+
+// Record the start event of a launch of `kind` (returns the pair index or -1).
+long prof_begin(gl_context* ctx, int kind, cudaStream_t st) {
+  if (!ctx->profiling) return -1;
+  size_t i = ctx->ev_used[kind];
+  if (i >= kMaxTimed) return -1;
+  auto& v = ctx->ev[kind];
+  if (v.size() < 2 * (i + 1)) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return -1;
+    }
+    v.push_back(a);
+    v.push_back(b);
+  }
+  cudaEventRecord(v[2 * i], st);
+  ctx->ev_used[kind] = i + 1;
+  return (long)i;
+}
+
+void prof_end(gl_context* ctx, int kind, long i, cudaStream_t st) {
+  if (i >= 0) cudaEventRecord(ctx->ev[kind][2 * i + 1], st);
+}
+
+int launch_grid(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = 148LL * 32;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gl_context_create(gl_context** out, int device) {
+  if (!out) return GL_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return GL_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return GL_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return GL_ECUDA;
+  if (ensure_device_tables(device) != cudaSuccess) return GL_ECUDA;
+  gl_context* ctx = new gl_context();
+  ctx->device = device;
+  if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    delete ctx;
+    return GL_ECUDA;
+  }
+  *out = ctx;
+  return GL_OK;
+}
+
+int gl_context_destroy(gl_context* ctx) {
+  if (!ctx) return GL_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->d_sets) cudaFree(ctx->d_sets);
+  if (ctx->d_stage) cudaFree(ctx->d_stage);
+  if (ctx->d_out) cudaFree(ctx->d_out);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  for (int k = 0; k < GL_KERNEL_KINDS; ++k)
+    for (cudaEvent_t e : ctx->ev[k]) cudaEventDestroy(e);
+  delete ctx;
+  return GL_OK;
+}
+
+const char* gl_last_error(const gl_context* ctx) { return ctx ? ctx->err : "no context"; }
+
+int64_t gl_launch_count(const gl_context* ctx) { return ctx ? ctx->launches : 0; }
+
+int gl_profile_enable(gl_context* ctx, int on) {
+  if (!ctx) return GL_EINVAL;
+  ctx->profiling = on != 0;
+  for (int k = 0; k < GL_KERNEL_KINDS; ++k) ctx->ev_used[k] = 0;
+  return GL_OK;
+}
+
+int gl_profile_read(gl_context* ctx, int kind, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches || kind < 0 || kind >= GL_KERNEL_KINDS) return GL_EINVAL;
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  double tot = 0.0;
+  for (size_t i = 0; i < ctx->ev_used[kind]; ++i) {
+    GL_CUDA(ctx, cudaEventSynchronize(ctx->ev[kind][2 * i + 1]));
+    float m = 0.f;
+    GL_CUDA(ctx, cudaEventElapsedTime(&m, ctx->ev[kind][2 * i], ctx->ev[kind][2 * i + 1]));
+    tot += m;
+  }
+  *ms = tot;
+  *launches = (int64_t)ctx->ev_used[kind];
+  return GL_OK;
+}
+
+int gl_q_to_u(int64_t n, const double* q1, const double* q2, double* u1, double* u2) {
+  if (n < 0 || (n > 0 && (!q1 || !q2 || !u1 || !u2))) return GL_EINVAL;
+  for (int64_t i = 0; i < n; ++i) {
+    double s = sqrt(q1[i]);
+    u1[i] = 2.0 * s * q2[i];
+    u2[i] = s * (1.0 - 2.0 * q2[i]);
+  }
+  return GL_OK;
+}
+
+int gl_sync(gl_context* ctx, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  GL_CUDA(ctx, cudaStreamSynchronize(st));
+  int h = 0;
+  GL_CUDA(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  GL_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  if (h & kStatusTimeout) return fail(ctx, GL_ETIMEOUT, "a bounded device wait gave up");
+  if (h & kStatusBadOffsets) return fail(ctx, GL_EINVAL, "offsets are not a valid CSR index");
+  if (h & kStatusInvalidSet) return fail(ctx, GL_ENUMERIC, "a parameter set is physically invalid");
+  return GL_OK;
+}
+
+int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
+                        gl_precision prec, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (!p || !tm) return fail(ctx, GL_EINVAL, "NULL params or times");
+  if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision %d", (int)prec);
+  int64_t n_sets = p->n_sets;
+  if (n_sets < 0) return fail(ctx, GL_EINVAL, "n_sets < 0");
+  if (tm->n_total < 0 || tm->n_total >= (1LL << 31)) return fail(ctx, GL_EINVAL, "n_total out of range");
+  if (!tm->offsets) {
+    if (tm->n_times < 0) return fail(ctx, GL_EINVAL, "n_times < 0");
+    if (tm->n_total != n_sets * tm->n_times)
+      return fail(ctx, GL_EINVAL, "n_total != n_sets * n_times for a shared grid");
+  }
+  if (!tm->nsuper && tm->nsuper_all < 1) return fail(ctx, GL_EINVAL, "nsuper_all < 1");
+  if (n_sets == 0 || tm->n_total == 0) return GL_OK;
+  const double* arr[12] = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega,
+                           p->k, p->f, p->eta, p->xi, p->u1, p->u2};
+  for (int i = 0; i < 12; ++i)
+    if (!arr[i]) return fail(ctx, GL_EINVAL, "NULL parameter array %d", i);
+  if (!tm->t || !tm->exptime || !out) return fail(ctx, GL_EINVAL, "NULL times, exptime or out");
+  if (tm->offsets && !is_device_ptr(tm->offsets, ctx->device) &&
+      (tm->offsets[0] != 0 || tm->offsets[n_sets] != tm->n_total))
+    return fail(ctx, GL_EINVAL, "offsets[0] != 0 or offsets[n_sets] != n_total");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+
+  ParamPtrs pp = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
+                  p->eta, p->xi, p->u1, p->u2, tm->exptime, tm->nsuper, tm->nsuper_all};
+  const double* t = tm->t;
+  const int64_t* offsets = tm->offsets;
+  int64_t n_t = offsets ? tm->n_total : tm->n_times;
+  size_t sb = (size_t)n_sets * sizeof(double);
+  StageItem items[] = {
+      {(const void**)&pp.t0, sb}, {(const void**)&pp.period, sb}, {(const void**)&pp.a_rs, sb},
+      {(const void**)&pp.b, sb}, {(const void**)&pp.ecc, sb}, {(const void**)&pp.omega, sb},
+      {(const void**)&pp.k, sb}, {(const void**)&pp.f, sb}, {(const void**)&pp.eta, sb},
+      {(const void**)&pp.xi, sb}, {(const void**)&pp.u1, sb}, {(const void**)&pp.u2, sb},
+      {(const void**)&pp.exptime, sb},
+      {(const void**)&pp.nsuper, (size_t)n_sets * sizeof(int32_t)},
+      {(const void**)&t, (size_t)n_t * sizeof(double)},
+      {(const void**)&offsets, (size_t)(n_sets + 1) * sizeof(int64_t)},
+  };
+  bool any_host = false;
+  int rc = stage_inputs(ctx, items, (int)(sizeof items / sizeof items[0]), st, &any_host);
+  if (rc) return rc;
+  rc = grow(ctx, (void**)&ctx->d_sets, &ctx->sets_cap, (size_t)n_sets * sizeof(SetConst));
+  if (rc) return rc;
+  bool out_host = !is_device_ptr(out, ctx->device);
+  double* d_out = out;
+  if (out_host) {
+    rc = grow(ctx, (void**)&ctx->d_out, &ctx->out_cap, (size_t)tm->n_total * sizeof(double));
+    if (rc) return rc;
+    d_out = ctx->d_out;
+  }
+  long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
+  gl_setup_kernel<<<(int)((n_sets + 127) / 128), 128, 0, st>>>(pp, n_sets, offsets, tm->n_total,
+                                                                ctx->d_sets, ctx->d_status);
+  prof_end(ctx, GL_KERNEL_SETUP, pe, st);
+  ctx->launches++;
+  int grid = launch_grid(tm->n_total, 256);
+  pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
+  if (prec == GL_FP64)
+    gl_curve_kernel<double><<<grid, 256, 0, st>>>(ctx->d_sets, t, offsets, tm->n_times, n_sets,
+                                                  tm->n_total, d_out);
+  else
+    gl_curve_kernel<float><<<grid, 256, 0, st>>>(ctx->d_sets, t, offsets, tm->n_times, n_sets,
+                                                 tm->n_total, d_out);
+  prof_end(ctx, GL_KERNEL_CURVE, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  if (out_host) {
+    GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, (size_t)tm->n_total * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  }
+  if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
+  return GL_OK;
+}
+
+int gl_flux_sky(gl_context* ctx, int64_t n, const double* x0, const double* y0, const double* z,
+                const double* k, const double* f, const double* eta, const double* xi,
+                const double* u1, const double* u2, double* out, gl_precision prec,
+                void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n < 0) return fail(ctx, GL_EINVAL, "n < 0");
+  if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision %d", (int)prec);
+  if (n == 0) return GL_OK;
+  if (!x0 || !y0 || !z || !k || !f || !eta || !xi || !u1 || !u2 || !out)
+    return fail(ctx, GL_EINVAL, "NULL array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  SkyPtrs sp = {x0, y0, z, k, f, eta, xi, u1, u2};
+  size_t b = (size_t)n * sizeof(double);
+  StageItem items[] = {{(const void**)&sp.x0, b}, {(const void**)&sp.y0, b},
+                       {(const void**)&sp.z, b},  {(const void**)&sp.k, b},
+                       {(const void**)&sp.f, b},  {(const void**)&sp.eta, b},
+                       {(const void**)&sp.xi, b}, {(const void**)&sp.u1, b},
+                       {(const void**)&sp.u2, b}};
+  bool any_host = false;
+  int rc = stage_inputs(ctx, items, 9, st, &any_host);
+  if (rc) return rc;
+  bool out_host = !is_device_ptr(out, ctx->device);
+  double* d_out = out;
+  if (out_host) {
+    rc = grow(ctx, (void**)&ctx->d_out, &ctx->out_cap, b);
+    if (rc) return rc;
+    d_out = ctx->d_out;
+  }
+  int grid = launch_grid(n, 256);
+  long pe = prof_begin(ctx, GL_KERNEL_SKY, st);
+  if (prec == GL_FP64)
+    gl_sky_kernel<double><<<grid, 256, 0, st>>>(sp, n, d_out, ctx->d_status);
+  else
+    gl_sky_kernel<float><<<grid, 256, 0, st>>>(sp, n, d_out, ctx->d_status);
+  prof_end(ctx, GL_KERNEL_SKY, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  if (out_host) GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, b, cudaMemcpyDeviceToHost, st));
+  if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
+  return GL_OK;
+}
+
+}  // extern "C"

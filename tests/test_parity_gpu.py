@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances (max |delta flux| over every compared exposure): FP64 path 1e-10,
+FP32-compensated path 1e-7.  Out-of-transit exposures must be exactly 1.0 on
+both paths.  The full-size workloads run on the GPU exactly as the benchmark
+launches them; the oracle checks a seeded sample of their parameter sets.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2410_05408_b300 import binding, inputs
+
+from _common import PARAM_NAMES, nsuper_array, oracle_params, product_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {binding.GL_FP64: 1e-10, binding.GL_FP32C: 1e-7}
+PRECS = [binding.GL_FP64, binding.GL_FP32C]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.array(a, copy=True)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _run(ctx, wl, prec, device=True):
+    p = product_params(wl)
+    n_sets = len(p["t0"])
+    exptime = np.ascontiguousarray(np.broadcast_to(wl["exptime"], (n_sets,)), dtype=np.float64)
+    ns = nsuper_array(wl, n_sets)
+    t = np.ascontiguousarray(wl["t"], dtype=np.float64)
+    offsets = wl.get("offsets")
+    n_total = n_sets * len(t) if offsets is None else int(offsets[-1])
+    if device:
+        dp = {k: _dev(v) for k, v in p.items()}
+        out = torch.empty(n_total, dtype=torch.float64, device="cuda")
+        ctx.lightcurve(dp, _dev(t), out, _dev(exptime), nsuper=_dev(ns, torch.int32),
+                       offsets=None if offsets is None else _dev(offsets, torch.int64),
+                       precision=prec)
+        torch.cuda.synchronize()
+        assert ctx.sync() == binding.GL_OK
+        return out.cpu().numpy()
+    out = np.empty(n_total)
+    ctx.lightcurve(p, t, out, exptime, nsuper=ns,
+                   offsets=None if offsets is None else np.ascontiguousarray(offsets, np.int64),
+                   precision=prec)
+    return out
+
+
+def _compare(got, ref, prec):
+    err = np.max(np.abs(got - ref)) if got.size else 0.0
+    assert err <= TOL[prec], f"max |dflux| {err:.3e} > {TOL[prec]:.0e}"
+    out = ref == 1.0
+    assert np.all(got[out] == 1.0), "out-of-transit exposures must be exactly 1"
+    return err
+
+
+# ---------------------------------------------------------------- single transit
+@pytest.fixture(scope="module")
+def single_ref():
+    import oracle
+    wl = inputs.single_transit()
+    return wl, oracle.lightcurve(oracle_params(wl), wl["t"], wl["exptime"], wl["nsuper"])[0]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_transit(ctx, single_ref, prec):
+    wl, ref = single_ref
+    got = _run(ctx, wl, prec)
+    assert np.mean(ref < 1.0) > 0.5     # most of the window is in transit
+    _compare(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_and_device_buffers_agree(ctx, prec):
+    wl = inputs.single_transit()
+    a = _run(ctx, wl, prec, device=True)
+    b = _run(ctx, wl, prec, device=False)
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- MCMC batch
+@pytest.fixture(scope="module")
+def mcmc():
+    import oracle
+    wl = inputs.mcmc_batch()
+    rng = np.random.default_rng(101)
+    idx = np.sort(rng.choice(256, 12, replace=False))
+    ref = oracle.lightcurve(oracle_params(wl, idx), wl["t"], wl["exptime"][idx], wl["nsuper"])
+    return wl, idx, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mcmc_batch_full_size_sampled(ctx, mcmc, prec):
+    wl, idx, ref = mcmc
+    got = _run(ctx, wl, prec).reshape(256, -1)
+    _compare(got[idx].ravel(), ref.ravel(), prec)
+    assert np.all(np.isfinite(got))
+
+
+# ---------------------------------------------------------------- uneven CSR batch
+@pytest.fixture(scope="module")
+def uneven():
+    import oracle
+    wl = inputs.uneven_batch()
+    off = wl["offsets"]
+    lengths = np.diff(off)
+    rng = np.random.default_rng(202)
+    short = np.flatnonzero(lengths < 3000)
+    longer = np.flatnonzero((lengths >= 3000) & (lengths < 20000))
+    idx = np.sort(np.concatenate([rng.choice(short, 16, replace=False),
+                                  rng.choice(longer, 4, replace=False)]))
+    sub_off = np.zeros(idx.size + 1, dtype=np.int64)
+    sub_off[1:] = np.cumsum(lengths[idx])
+    t_sub = np.concatenate([wl["t"][off[s]:off[s + 1]] for s in idx])
+    ref = oracle.lightcurve(oracle_params(wl, idx), t_sub, wl["exptime"][idx],
+                            wl["nsuper"][idx], offsets=sub_off)
+    return wl, idx, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_uneven_batch_full_size_sampled(ctx, uneven, prec):
+    wl, idx, ref = uneven
+    got = _run(ctx, wl, prec)
+    off = wl["offsets"]
+    got_sub = np.concatenate([got[off[s]:off[s + 1]] for s in idx])
+    _compare(got_sub, ref, prec)
+    assert np.all(np.isfinite(got))
+
+
+# ---------------------------------------------------------------- geometry level
+@pytest.fixture(scope="module")
+def geometry():
+    import oracle
+    g = inputs.geometry_sample(30000)
+    u = np.array([oracle.q_to_u(a, b) for a, b in zip(g["q1"], g["q2"])])
+    g["u1"], g["u2"] = u[:, 0].copy(), u[:, 1].copy()
+    ref = oracle.flux_sky_batch(g["x0"], g["y0"], g["z"], g["k"], g["f"], g["eta"], g["xi"],
+                                g["u1"], g["u2"])
+    return g, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_geometry_parity(ctx, geometry, prec):
+    g, ref = geometry
+    u1, u2 = binding.gl_q_to_u(g["q1"], g["q2"])
+    args = [_dev(g[n]) for n in ("x0", "y0", "z", "k", "f", "eta", "xi")] + [_dev(u1), _dev(u2)]
+    out = torch.empty(len(ref), dtype=torch.float64, device="cuda")
+    ctx.flux_sky(*args, out, precision=prec)
+    got = out.cpu().numpy()
+    assert np.mean((ref < 1) & (ref > 0)) > 0.5
+    _compare(got, ref, prec)
+
+
+# ---------------------------------------------------------------- worked example
+def test_degeneracy_example_on_gpu(ctx):
+    """Appendix A: f = 1/2, eta = 0 and f = 2/3, eta = arccos(11/16)/2 at equal R_eq."""
+    req = 0.1
+    eta2 = 0.5 * math.acos(11 / 16)
+    base = dict(t0=0.0, period=542.0, a_rs=230.0, b=0.2, ecc=0.0, omega=math.pi / 2, xi=0.4,
+                u1=0.4, u2=0.25)
+    p = {n: np.array([base[n]] * 2) for n in base}
+    p["k"] = np.array([req * 0.5 ** (1 / 3), req * (1 / 3) ** (1 / 3)])
+    p["f"] = np.array([0.5, 2 / 3])
+    p["eta"] = np.array([0.0, eta2])
+    p = {n: p[n] for n in PARAM_NAMES}
+    t = np.linspace(-0.5, 0.5, 401)
+    out = np.empty(2 * t.size)
+    ctx.lightcurve(p, t, out, np.full(2, 0.02), nsuper_all=5, precision=binding.GL_FP64)
+    a, b = out[:t.size], out[t.size:]
+    assert np.max(1 - a) > 1e-3
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_batches(ctx):
+    p = {n: np.zeros(0) for n in PARAM_NAMES}
+    ctx.lightcurve(p, np.zeros(0), np.zeros(0), np.zeros(0), nsuper_all=3)
+    wl = inputs.single_transit()
+    pp = product_params(wl)
+    ctx.lightcurve(pp, np.zeros(0), np.zeros(0), np.array([0.02]), nsuper_all=3)
+    assert ctx.sync() == binding.GL_OK
+
+
+def test_ragged_csr_with_empty_curves(ctx):
+    import oracle
+    wl = inputs.uneven_batch(n_curves=6, max_len=400)
+    lengths = np.diff(wl["offsets"])
+    lengths[[1, 4]] = 0
+    off = np.zeros(7, dtype=np.int64)
+    off[1:] = np.cumsum(lengths)
+    t = np.concatenate([wl["t"][wl["offsets"][s]:wl["offsets"][s] + lengths[s]] for s in range(6)])
+    wl2 = dict(wl, t=t, offsets=off)
+    ref = oracle.lightcurve(oracle_params(wl2), t, wl["exptime"], wl["nsuper"], offsets=off)
+    for prec in PRECS:
+        _compare(_run(ctx, wl2, prec), ref, prec)
+
+
+def test_invalid_set_gives_nan_and_status(ctx):
+    wl = inputs.mcmc_batch(n_sets=4, n_times=50)
+    p = product_params(wl)
+    p["ecc"] = p["ecc"].copy()
+    p["ecc"][2] = 1.5          # unbound orbit: invalid
+    out = np.empty(4 * 50)
+    ctx.lightcurve(p, wl["t"], out, wl["exptime"], nsuper_all=15)
+    out = out.reshape(4, 50)
+    assert np.all(np.isnan(out[2]))
+    assert np.all(np.isfinite(out[[0, 1, 3]]))
+    assert ctx.sync() == binding.GL_ENUMERIC
+    assert ctx.sync() == binding.GL_OK     # sticky until read
+
+
+def test_bad_arguments_are_rejected(ctx):
+    wl = inputs.single_transit()
+    p = product_params(wl)
+    out = np.empty(1000)
+    with pytest.raises(binding.GLError) as e:
+        ctx.lightcurve(p, wl["t"], out, np.array([0.02]), nsuper_all=0)
+    assert e.value.code == binding.GL_EINVAL
+    bad = dict(p)
+    bad["k"] = None
+    with pytest.raises((binding.GLError, TypeError)):
+        ctx.lightcurve(bad, wl["t"], out, np.array([0.02]), nsuper_all=3)
+    with pytest.raises(binding.GLError):
+        ctx.lightcurve(p, wl["t"], np.empty(999), np.array([0.02]), nsuper_all=3)
+
+
+def test_launches_are_counted(ctx):
+    n0 = ctx.launches()
+    _run(ctx, inputs.single_transit(n_times=10), binding.GL_FP32C)
+    assert ctx.launches() > n0
