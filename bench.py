@@ -231,8 +231,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mcmc_batch")
-    ap.add_argument("--ref-sets", type=int, default=32)
-    ap.add_argument("--cpu-sets", type=int, default=48)
+    ap.add_argument("--ref-sets", type=int, default=96)
+    ap.add_argument("--cpu-sets", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
