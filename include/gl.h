@@ -180,6 +180,39 @@ int gl_profile_enable(gl_context *ctx, int on);
  * runtime failure. */
 int gl_profile_read(gl_context *ctx, int kind, double *ms, int64_t *launches);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant of gl_lightcurve_batch.  The paper has no
+ * counterpart: this is a deployment aid.
+ *
+ * Some callers cannot let a library allocate device memory: applications whose
+ * device memory belongs to a pool allocator with a fixed budget (an extra
+ * cudaMalloc can fail or fragment the pool), latency-critical loops where a
+ * cudaMalloc or cudaFree would add a device-wide synchronisation, and plug-ins
+ * hosted by a process that forbids allocation outside its own allocator.  This
+ * entry point needs no context and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its per-set workspace is one fixed array compiled into
+ * the library (GL_NOALLOC_MAX_SETS entries, about 0.8 MB), which every GPU that
+ * runs it holds until the process exits.
+ *
+ *   p, t, out, prec, stream  as for gl_lightcurve_batch, on the current CUDA
+ *                            device, except that every array must be device
+ *                            memory of that device (host arrays would need a
+ *                            staging copy, which would allocate).
+ * Returns GL_OK; GL_EINVAL for a NULL or host pointer, n_sets > GL_NOALLOC_MAX_SETS
+ * or any size check of gl_lightcurve_batch; GL_ECUDA on a runtime failure.
+ * Physically invalid parameter sets give NaN outputs (no status is kept).
+ *
+ * The first call on a device uploads the quadrature tables and looks up the
+ * array's device address on that device; make that first call before any
+ * stream capture.  Every call shares the array and overwrites the entries it
+ * uses before reading them, so calls that overlap on the GPU (on different
+ * streams, or from different threads) race and must be serialised by the
+ * caller.  The call is asynchronous on `stream`.
+ */
+#define GL_NOALLOC_MAX_SETS 4096
+int gl_lightcurve_batch_noalloc(const gl_params *p, const gl_times *t, double *out,
+                                gl_precision prec, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

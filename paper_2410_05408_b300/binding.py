@@ -28,7 +28,9 @@ GL_FP32C = 1
 
 EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_lightcurve_batch",
             "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
-            "gl_profile_read")
+            "gl_profile_read", "gl_lightcurve_batch_noalloc")
+
+GL_NOALLOC_MAX_SETS = 4096
 
 GL_KERNEL_SETUP = 0
 GL_KERNEL_CURVE = 1
@@ -86,6 +88,9 @@ def load():
         lib.gl_sync.restype = i32
         lib.gl_launch_count.argtypes = [vp]
         lib.gl_launch_count.restype = i64
+        lib.gl_lightcurve_batch_noalloc.argtypes = [ctypes.POINTER(_Params),
+                                                    ctypes.POINTER(_Times), vp, i32, vp]
+        lib.gl_lightcurve_batch_noalloc.restype = i32
         lib.gl_profile_enable.argtypes = [vp, i32]
         lib.gl_profile_enable.restype = i32
         lib.gl_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
@@ -165,6 +170,22 @@ def gl_lightcurve_batch(ctx, params: dict, t, out, precision: int = GL_FP32C, of
     if check:
         _check(ctx, rc)
     return rc
+
+
+def gl_lightcurve_batch_noalloc(params: dict, t, out, precision: int = GL_FP32C, offsets=None,
+                                exptime=None, nsuper=None, nsuper_all: int = 1,
+                                stream=None) -> int:
+    """Allocation-free light curves (see include/gl.h): every array must be a
+    CUDA tensor on the current device.  Returns the C status code."""
+    lib = load()
+    n_sets = int(len(params["t0"]))
+    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"),
+                0 if offsets is not None else int(len(t)), int(len(out)),
+                _ptr(exptime, "float64"), _ptr(nsuper, "int32"), int(nsuper_all))
+    return lib.gl_lightcurve_batch_noalloc(ctypes.byref(p), ctypes.byref(tm),
+                                           _ptr(out, "float64"), int(precision),
+                                           _stream_ptr(stream))
 
 
 def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_FP32C,

@@ -545,3 +545,86 @@ int gl_flux_sky(gl_context* ctx, int64_t n, const double* x0, const double* y0, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free entry
+// gl_lightcurve_batch_noalloc: the same setup + light-curve kernels as
+// gl_lightcurve_batch, with the per-set constants kept in a fixed device array
+// instead of context workspace.  The array lives for as long as the library is
+// loaded, on every device that runs the entry point.
+namespace {
+
+constexpr size_t kNoallocStatusOffset = (size_t)GL_NOALLOC_MAX_SETS * sizeof(SetConst);
+constexpr size_t kNoallocBytes = kNoallocStatusOffset + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_noalloc_mutex;
+std::vector<unsigned char*> g_noalloc_ptr;   // per device: address of g_noalloc_scratch
+
+// Once per device, with that device current: upload the node tables and look up
+// the device address of the scratch array.
+int noalloc_setup(int device, unsigned char** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  if ((int)g_noalloc_ptr.size() <= device) g_noalloc_ptr.resize(device + 1, nullptr);
+  if (!g_noalloc_ptr[device]) {
+    if (ensure_device_tables(device) != cudaSuccess) return GL_ECUDA;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return GL_ECUDA;
+    }
+    g_noalloc_ptr[device] = (unsigned char*)p;
+  }
+  *out = g_noalloc_ptr[device];
+  return GL_OK;
+}
+
+}  // namespace
+
+extern "C" int gl_lightcurve_batch_noalloc(const gl_params* p, const gl_times* tm, double* out,
+                                           gl_precision prec, void* stream) {
+  if (!p || !tm) return GL_EINVAL;
+  if (prec != GL_FP64 && prec != GL_FP32C) return GL_EINVAL;
+  int64_t n_sets = p->n_sets;
+  if (n_sets < 0 || n_sets > GL_NOALLOC_MAX_SETS) return GL_EINVAL;
+  if (tm->n_total < 0 || tm->n_total >= (1LL << 31)) return GL_EINVAL;
+  if (!tm->offsets && (tm->n_times < 0 || tm->n_total != n_sets * tm->n_times)) return GL_EINVAL;
+  if (!tm->nsuper && tm->nsuper_all < 1) return GL_EINVAL;
+  if (n_sets == 0 || tm->n_total == 0) return GL_OK;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return GL_ECUDA;
+  }
+  const void* ptrs[17] = {p->t0, p->period, p->a_rs, p->b,   p->ecc,     p->omega,
+                          p->k,  p->f,      p->eta,  p->xi,  p->u1,      p->u2,
+                          tm->t, tm->exptime, out,   tm->offsets, tm->nsuper};
+  for (int i = 0; i < 17; ++i) {
+    if (!ptrs[i]) {
+      if (i >= 15) continue;   // offsets and nsuper are optional
+      return GL_EINVAL;
+    }
+    if (!is_device_ptr(ptrs[i], device)) return GL_EINVAL;   // host memory would need staging
+  }
+  unsigned char* scratch = nullptr;
+  int rc = noalloc_setup(device, &scratch);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  SetConst* sets = (SetConst*)scratch;
+  int* status = (int*)(scratch + kNoallocStatusOffset);
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GL_ECUDA;
+  ParamPtrs pp = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
+                  p->eta, p->xi, p->u1, p->u2, tm->exptime, tm->nsuper, tm->nsuper_all};
+  gl_setup_kernel<<<(int)((n_sets + 127) / 128), 128, 0, st>>>(pp, n_sets, tm->offsets,
+                                                                tm->n_total, sets, status);
+  int grid = launch_grid(tm->n_total, 256);
+  if (prec == GL_FP64)
+    gl_curve_kernel<double><<<grid, 256, 0, st>>>(sets, tm->t, tm->offsets, tm->n_times, n_sets,
+                                                  tm->n_total, out);
+  else
+    gl_curve_kernel<float><<<grid, 256, 0, st>>>(sets, tm->t, tm->offsets, tm->n_times, n_sets,
+                                                 tm->n_total, out);
+  if (cudaGetLastError() != cudaSuccess) return GL_ECUDA;
+  return GL_OK;
+}

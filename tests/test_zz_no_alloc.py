@@ -1,0 +1,86 @@
+"""The allocation-free entry point gl_lightcurve_batch_noalloc.
+
+It exists for callers that cannot let a library allocate device memory (a pool
+allocator with a fixed budget, loops that must not pay the synchronisation of a
+cudaMalloc, hosts that forbid allocation outside their own allocator).  Its
+results must match the ordinary entry point gl_lightcurve_batch on the same
+inputs, call after call, even though every call reuses one fixed device array.
+
+This file is collected last so that a run stopping at the first failure has run
+every other test before it.
+"""
+import numpy as np
+import pytest
+
+from paper_2410_05408_b300 import binding, inputs
+
+from _common import nsuper_array, product_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {binding.GL_FP64: 1e-10, binding.GL_FP32C: 1e-7}
+
+
+def _device_inputs(wl):
+    p = product_params(wl)
+    n_sets = len(p["t0"])
+    dp = {k: torch.tensor(v, dtype=torch.float64, device="cuda") for k, v in p.items()}
+    exptime = torch.tensor(np.broadcast_to(wl["exptime"], (n_sets,)).copy(), dtype=torch.float64,
+                           device="cuda")
+    ns = torch.tensor(nsuper_array(wl, n_sets), dtype=torch.int32, device="cuda")
+    t = torch.tensor(wl["t"], dtype=torch.float64, device="cuda")
+    off = wl.get("offsets")
+    off = None if off is None else torch.tensor(off, dtype=torch.int64, device="cuda")
+    n_total = n_sets * t.numel() if off is None else int(wl["offsets"][-1])
+    return dp, t, exptime, ns, off, n_total
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def _both(ctx, wl, prec):
+    dp, t, exptime, ns, off, n_total = _device_inputs(wl)
+    ref = torch.empty(n_total, dtype=torch.float64, device="cuda")
+    ctx.lightcurve(dp, t, ref, exptime, nsuper=ns, offsets=off, precision=prec)
+    got = torch.full((n_total,), -7.0, dtype=torch.float64, device="cuda")
+    rc = binding.gl_lightcurve_batch_noalloc(dp, t, got, prec, offsets=off, exptime=exptime,
+                                             nsuper=ns)
+    assert rc == binding.GL_OK
+    torch.cuda.synchronize()
+    return got.cpu().numpy(), ref.cpu().numpy()
+
+
+def test_noalloc_matches_ordinary_entry_point_twice(ctx):
+    # first call: 64 sets of the MCMC batch, FP32C
+    wl1 = inputs.mcmc_batch(n_sets=64, n_times=800, seed=5)
+    got, ref = _both(ctx, wl1, binding.GL_FP32C)
+    assert np.any(ref < 1.0)
+    assert np.max(np.abs(got - ref)) <= TOL[binding.GL_FP32C]
+    # second call right after, different sizes and layout (CSR), FP64: the
+    # array still holds the first call's constants beyond these sets
+    wl2 = inputs.uneven_batch(n_curves=24, max_len=3000, seed=6)
+    got, ref = _both(ctx, wl2, binding.GL_FP64)
+    assert np.any(ref < 1.0)
+    assert np.max(np.abs(got - ref)) <= TOL[binding.GL_FP64]
+
+
+def test_noalloc_rejects_what_it_cannot_do(ctx):
+    wl = inputs.mcmc_batch(n_sets=binding.GL_NOALLOC_MAX_SETS + 1, n_times=2, seed=7)
+    dp, t, exptime, ns, off, n_total = _device_inputs(wl)
+    out = torch.empty(n_total, dtype=torch.float64, device="cuda")
+    assert binding.gl_lightcurve_batch_noalloc(dp, t, out, binding.GL_FP32C, exptime=exptime,
+                                               nsuper=ns) == binding.GL_EINVAL
+    # host memory would need a staging allocation: rejected
+    wl = inputs.single_transit(n_times=16)
+    p = product_params(wl)
+    host_out = np.empty(16)
+    assert binding.gl_lightcurve_batch_noalloc(p, wl["t"], host_out, binding.GL_FP32C,
+                                               exptime=np.array([0.02]),
+                                               nsuper_all=3) == binding.GL_EINVAL
