@@ -117,6 +117,243 @@ __global__ void __launch_bounds__(256) gl_curve_kernel(const SetConst* __restric
   }
 }
 
+// ------------------------------------------------------------------ fused persistent kernel
+// One CTA processes tiles of TILE consecutive exposures, taken from an atomic
+// tile counter until none are left:
+//   phase 0  one thread per exposure: conservative FP32 window test; exposures
+//            outside get flux 1 at once, the rest are compacted in shared memory
+//   phase 1  one thread per kept exposure: exact FP64 window test and, for the
+//            FP32C path, the FP64 Kepler state at the exposure midpoint
+//   rounds   up to CAP sub-exposure items at a time:
+//            2: position (cubic Taylor step in FP32 from the midpoint state, or
+//               FP64 Kepler per item), classification, queueing
+//            3: whole-ellipse items (full-turn quadrature)
+//            4: crossing items (roots, arcs)
+//            5: FP64 accumulation of 1 - deficit per exposure, in item order
+//   phase 6  mean over the exposure's sub-exposures -> out
+struct LcArgs {
+  const SetConst* sets;
+  const double* t;
+  const int64_t* offsets;
+  int64_t n_times, n_sets, n_total;
+  double* out;
+  unsigned int* tile_counter;
+  int n_tiles, tile, cap;
+};
+
+template <typename R>
+struct LcSmem {
+  // byte offsets into dynamic shared memory
+  static __host__ __device__ size_t acc(int tile) { return 0; }
+  static __host__ __device__ size_t tau(int tile) { return acc(tile) + 8 * (size_t)tile; }
+  static __host__ __device__ size_t mid(int tile) { return tau(tile) + 8 * (size_t)tile; }
+  static __host__ __device__ size_t ej(int tile) { return mid(tile) + sizeof(gl::MidState) * (size_t)tile; }
+  static __host__ __device__ size_t es(int tile) { return ej(tile) + 4 * (size_t)tile; }
+  static __host__ __device__ size_t ens(int tile) { return es(tile) + 4 * (size_t)tile; }
+  static __host__ __device__ size_t ebase(int tile) { return ens(tile) + 4 * (size_t)tile; }
+  static __host__ __device__ size_t eflag(int tile) { return ebase(tile) + 4 * (size_t)(tile + 1); }
+  static __host__ __device__ size_t pos(int tile) { return (eflag(tile) + 4 * (size_t)tile + 15) & ~(size_t)15; }
+  static __host__ __device__ size_t def(int tile, int cap) { return pos(tile) + 3 * sizeof(R) * (size_t)cap; }
+  static __host__ __device__ size_t qf(int tile, int cap) { return def(tile, cap) + sizeof(R) * (size_t)cap; }
+  static __host__ __device__ size_t qp(int tile, int cap) { return qf(tile, cap) + 4 * (size_t)cap; }
+  static __host__ __device__ size_t total(int tile, int cap) { return qp(tile, cap) + 4 * (size_t)cap; }
+};
+
+enum : int { kExpDead = 1, kExpTaylor = 2 };
+
+// exclusive prefix sum over the block of one int per thread; returns the
+// prefix, writes the total to *total (all threads)
+template <int NT>
+__device__ __forceinline__ int block_scan(int v, int* warp_tot, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < NT / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < NT / 32) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  int before = (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+  *total = warp_tot[NT / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int warp_tot[32];
+  __shared__ int s_tile, s_nf, s_np;
+  __shared__ long long s_first;
+  const int tile_sz = a.tile, cap = a.cap;
+  double* e_acc = (double*)(smem + LcSmem<R>::acc(tile_sz));
+  double* e_tau = (double*)(smem + LcSmem<R>::tau(tile_sz));
+  gl::MidState* e_mid = (gl::MidState*)(smem + LcSmem<R>::mid(tile_sz));
+  int* e_j = (int*)(smem + LcSmem<R>::ej(tile_sz));
+  int* e_s = (int*)(smem + LcSmem<R>::es(tile_sz));
+  int* e_ns = (int*)(smem + LcSmem<R>::ens(tile_sz));
+  int* e_base = (int*)(smem + LcSmem<R>::ebase(tile_sz));
+  int* e_flag = (int*)(smem + LcSmem<R>::eflag(tile_sz));
+  R* it_pos = (R*)(smem + LcSmem<R>::pos(tile_sz));
+  R* it_def = (R*)(smem + LcSmem<R>::def(tile_sz, cap));
+  int* q_full = (int*)(smem + LcSmem<R>::qf(tile_sz, cap));
+  int* q_part = (int*)(smem + LcSmem<R>::qp(tile_sz, cap));
+  const NodeRule<R>& rl = rule<R>();
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    if (tid == 0) s_tile = (int)atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= a.n_tiles) break;
+    const int64_t j0 = (int64_t)tile * tile_sz;
+    if (a.offsets && tid == 0) s_first = owner_of(a.offsets, a.n_sets, j0);
+    __syncthreads();
+
+    // ---- phase 0: conservative window test, compaction
+    int keep = 0, my_s = 0, my_ns = 0;
+    double my_t = 0.0;
+    int64_t j = j0 + tid;
+    if (tid < tile_sz && j < a.n_total) {
+      int64_t ti;   // index into t: CSR shares the exposure index, a shared grid repeats
+      if (a.offsets) {
+        int64_t s = s_first;
+        while (s + 1 < a.n_sets && a.offsets[s + 1] <= j) ++s;
+        my_s = (int)s;
+        ti = j;
+      } else {
+        my_s = (int)((unsigned)j / (unsigned)a.n_times);
+        ti = j - (int64_t)my_s * a.n_times;
+      }
+      const SetConst& c = a.sets[my_s];
+      my_t = a.t[ti];
+      if (c.flags & gl::kSetInvalid) {
+        a.out[j] = __longlong_as_double(0x7ff8000000000000LL);
+      } else if (gl::window_maybe(c, my_t)) {
+        keep = 1;
+        my_ns = c.nsuper;
+      } else {
+        a.out[j] = 1.0;
+      }
+    }
+    int m;
+    int slot = block_scan<NT>(keep, warp_tot, &m);
+    if (keep) {
+      e_j[slot] = (int)j;
+      e_s[slot] = my_s;
+      e_ns[slot] = my_ns;
+      e_tau[slot] = my_t;   // the time; phase 1 turns it into tau
+    }
+    __syncthreads();
+    if (m == 0) continue;
+    int M;
+    int base = block_scan<NT>(tid < m ? e_ns[tid] : 0, warp_tot, &M);
+    if (tid < m) e_base[tid] = base;
+    if (tid == 0) e_base[m] = M;
+
+    // ---- phase 1: exact window test and midpoint state
+    for (int i = tid; i < m; i += NT) {
+      const SetConst& c = a.sets[e_s[i]];
+      double tau = gl::wrap_tau(c, e_tau[i]);
+      int fl = 0;
+      if (!gl::in_window(c, tau, 0.5 * c.exptime)) {
+        fl = kExpDead;
+      } else if (sizeof(R) == 4 && (c.flags & gl::kSetTaylor)) {
+        gl::SkyState st;
+        gl::sky_state(c, tau, &st);
+        e_mid[i] = gl::mid_state(st);
+        fl = kExpTaylor;
+      }
+      e_tau[i] = tau;
+      e_flag[i] = fl;
+      e_acc[i] = 0.0;
+    }
+    __syncthreads();
+
+    for (int r0 = 0; r0 < M; r0 += cap) {
+      const int nr = min(cap, M - r0);
+      if (tid == 0) {
+        s_nf = 0;
+        s_np = 0;
+      }
+      __syncthreads();
+      // ---- phase 2: positions and classes
+      for (int k = tid; k < nr; k += NT) {
+        int it = r0 + k;
+        int lo = 0, hi = m;   // e_base[lo] <= it < e_base[hi]
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (e_base[mid] <= it) lo = mid; else hi = mid;
+        }
+        const int i = lo, q = it - e_base[i];
+        it_def[k] = R(0);
+        if (e_flag[i] & kExpDead) continue;
+        const SetConst& c = a.sets[e_s[i]];
+        const double dt = gl::subexposure_offset(q, e_ns[i], c.exptime);
+        R x, y, o;
+        int cls;
+        if (e_flag[i] & kExpTaylor) {
+          float xf, yf, zf, of;
+          gl::taylor_position(e_mid[i], (float)dt, &xf, &yf, &zf, &of);
+          cls = gl::classify_t<float>((float)c.req, xf, yf, zf, 1e-6f);
+          x = (R)xf;
+          y = (R)yf;
+          o = (R)of;
+        } else {
+          double xd, yd, zd;
+          gl::sky_position(c, e_tau[i] + dt, &xd, &yd, &zd);
+          cls = gl::classify(c, xd, yd, zd);
+          x = (R)xd;
+          y = (R)yd;
+          o = (R)((1.0 - xd) * (1.0 + xd) - yd * yd);
+        }
+        if (cls == gl::kOut) continue;
+        it_pos[3 * k] = x;
+        it_pos[3 * k + 1] = y;
+        it_pos[3 * k + 2] = o;
+        int packed = k | (i << 16);
+        if (cls == gl::kFull) q_full[atomicAdd(&s_nf, 1)] = packed;
+        else q_part[atomicAdd(&s_np, 1)] = packed;
+      }
+      __syncthreads();
+      // ---- phases 3 and 4: quadrature, whole-ellipse items first
+      const int nf = s_nf, np = s_np;
+      for (int u = tid; u < nf + np; u += NT) {
+        int packed = u < nf ? q_full[u] : q_part[u - nf];
+        int k = packed & 0xffff, i = packed >> 16;
+        const SetConst& c = a.sets[e_s[i]];
+        R I[3];
+        gl::occulted_r<R>(c, it_pos[3 * k], it_pos[3 * k + 1], it_pos[3 * k + 2],
+                          u < nf ? gl::kFull : gl::kPartial, rl, I);
+        it_def[k] = ((R)c.c0 * I[0] + (R)c.c1 * I[1] + (R)c.c2 * I[2]) * (R)c.invF0;
+      }
+      __syncthreads();
+      // ---- phase 5: FP64 accumulation in item order
+      for (int i = tid; i < m; i += NT) {
+        int b0 = max(e_base[i], r0), b1 = min(e_base[i + 1], r0 + nr);
+        double acc = e_acc[i];
+        for (int it = b0; it < b1; ++it) acc += 1.0 - (double)it_def[it - r0];
+        e_acc[i] = acc;
+      }
+      __syncthreads();
+    }
+    // ---- phase 6: exposure means
+    for (int i = tid; i < m; i += NT) a.out[e_j[i]] = e_acc[i] / e_ns[i];
+    __syncthreads();
+  }
+}
+
 struct SkyPtrs {
   const double *x0, *y0, *z, *k, *f, *eta, *xi, *u1, *u2;
 };
@@ -209,6 +446,9 @@ struct gl_context {
   double* d_out = nullptr;     // staging of a host output
   size_t out_cap = 0;
   int* d_status = nullptr;
+  unsigned int* d_counter = nullptr;   // tile counter of the persistent kernel
+  int sms = 0;
+  int occ[2] = {0, 0};                 // resident CTAs per SM: FP64, FP32C kernel
   int64_t launches = 0;
   // per-kernel event timing (gl_profile_enable)
   bool profiling = false;
@@ -331,6 +571,38 @@ int launch_grid(int64_t n, int threads) {
   return (int)b;
 }
 
+constexpr int kLcThreads = 256;
+constexpr int kLcTile = 256;
+constexpr int kLcCap = 1024;
+
+template <typename R>
+int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
+  LcArgs args = args0;
+  args.tile = kLcTile;
+  args.cap = kLcCap;
+  args.n_tiles = (int)((args.n_total + kLcTile - 1) / kLcTile);
+  args.tile_counter = ctx->d_counter;
+  size_t smem = LcSmem<R>::total(kLcTile, kLcCap);
+  int& occ = ctx->occ[sizeof(R) == 4 ? 1 : 0];
+  if (occ == 0) {
+    GL_CUDA(ctx, cudaFuncSetAttribute(gl_lc_kernel<R, kLcThreads>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gl_lc_kernel<R, kLcThreads>,
+                                                               kLcThreads, smem));
+    if (occ < 1) return fail(ctx, GL_ECUDA, "light-curve kernel does not fit on an SM");
+  }
+  int grid = ctx->sms * occ;
+  if (grid > args.n_tiles) grid = args.n_tiles;
+  if (grid < 1) grid = 1;
+  GL_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), st));
+  long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
+  gl_lc_kernel<R, kLcThreads><<<grid, kLcThreads, smem, st>>>(args);
+  prof_end(ctx, GL_KERNEL_CURVE, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -349,7 +621,10 @@ int gl_context_create(gl_context** out, int device) {
   gl_context* ctx = new gl_context();
   ctx->device = device;
   if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
-      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_counter, sizeof(unsigned int)) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
     return GL_ECUDA;
   }
@@ -365,6 +640,7 @@ int gl_context_destroy(gl_context* ctx) {
   if (ctx->d_stage) cudaFree(ctx->d_stage);
   if (ctx->d_out) cudaFree(ctx->d_out);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_counter) cudaFree(ctx->d_counter);
   for (int k = 0; k < GL_KERNEL_KINDS; ++k)
     for (cudaEvent_t e : ctx->ev[k]) cudaEventDestroy(e);
   delete ctx;
@@ -481,17 +757,17 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
                                                                 ctx->d_sets, ctx->d_status);
   prof_end(ctx, GL_KERNEL_SETUP, pe, st);
   ctx->launches++;
-  int grid = launch_grid(tm->n_total, 256);
-  pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
-  if (prec == GL_FP64)
-    gl_curve_kernel<double><<<grid, 256, 0, st>>>(ctx->d_sets, t, offsets, tm->n_times, n_sets,
-                                                  tm->n_total, d_out);
-  else
-    gl_curve_kernel<float><<<grid, 256, 0, st>>>(ctx->d_sets, t, offsets, tm->n_times, n_sets,
-                                                 tm->n_total, d_out);
-  prof_end(ctx, GL_KERNEL_CURVE, pe, st);
-  ctx->launches++;
-  GL_CUDA(ctx, cudaGetLastError());
+  LcArgs la;
+  memset(&la, 0, sizeof la);
+  la.sets = ctx->d_sets;
+  la.t = t;
+  la.offsets = offsets;
+  la.n_times = tm->n_times;
+  la.n_sets = n_sets;
+  la.n_total = tm->n_total;
+  la.out = d_out;
+  rc = (prec == GL_FP64) ? launch_lc<double>(ctx, la, st) : launch_lc<float>(ctx, la, st);
+  if (rc) return rc;
   if (out_host) {
     GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, (size_t)tm->n_total * sizeof(double),
                                  cudaMemcpyDeviceToHost, st));

@@ -31,7 +31,7 @@ namespace gl {
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr int kMaxNodes = 48;
 
-enum : int { kSetInvalid = 1, kSetWholeOrbit = 2 };
+enum : int { kSetInvalid = 1, kSetWholeOrbit = 2, kSetTaylor = 4 };
 
 // Per-parameter-set constants, computed once per set in FP64.
 struct SetConst {
@@ -47,6 +47,9 @@ struct SetConst {
   // limb darkening I = c0 + c1 mu + c2 r^2, F0 = pi (1 - u1/3 - u2/6)
   double c0, c1, c2, invF0;
   double exptime;
+  double invP;                     // 1 / P
+  // conservative FP32 window for the per-exposure test (see window_maybe)
+  float t0f, Pf, invPf, wlo_f, whi_f, slack_f;
   int nsuper;
   int flags;
 };
@@ -231,13 +234,45 @@ GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc
     c->tau_lo = fmin(taus[0], 0.0) - margin;
     c->tau_hi = fmax(taus[1], 0.0) + margin;
   }
+  c->invP = 1.0 / period;
+  // FP32 copy of the window for the per-exposure test, widened for rounding:
+  // every FP32 operation of window_maybe errs by at most 2^-24 of its operands.
+  c->t0f = (float)t0;
+  c->Pf = (float)period;
+  c->invPf = (float)c->invP;
+  c->slack_f = (float)(ldexp(fabs(t0) + period, -20) + 1e-6);
+  c->wlo_f = (float)(c->tau_lo - 0.5 * exptime);
+  c->whi_f = (float)(c->tau_hi + 0.5 * exptime);
+  // Sub-exposure positions may come from a cubic Taylor expansion about the
+  // exposure midpoint.  For a Kepler orbit |d^4 r/dt^4| <= C n^4 a (2+e)/(1-e)^5
+  // (from r'' = -mu r/|r|^3, mu = n^2 a^3, r >= a(1-e)); with C = 60 the
+  // truncation over half an exposure must stay below 1e-10 stellar radii.
+  {
+    double n4 = c->nmean * c->nmean * c->nmean * c->nmean;
+    double h = 0.5 * exptime;
+    double om = 1.0 - ecc;
+    double bound = 60.0 * n4 * a_rs * (2.0 + ecc) / (om * om * om * om * om) * (h * h * h * h) / 24.0;
+    if (bound <= 1e-10) c->flags |= kSetTaylor;
+  }
   return true;
 }
 
 // (t - t0) wrapped to one period around the conjunction.
 GL_HD double wrap_tau(const SetConst& c, double t) {
   double tau = t - c.t0;
-  return tau - c.period * rint(tau / c.period);
+  return tau - c.period * rint(tau * c.invP);
+}
+
+// Conservative FP32 window test of an exposure at time t (true whenever any
+// sub-exposure may overlap the star; false positives are resolved in FP64).
+GL_HD bool window_maybe(const SetConst& c, double t) {
+  if (c.flags & kSetWholeOrbit) return true;
+  float tf = (float)t;
+  float tau = tf - c.t0f;
+  float ep = rintf(tau * c.invPf);
+  float tw = fmaf(-ep, c.Pf, tau);
+  float m = (fabsf(tf) + fabsf(c.t0f)) * 4.76837158203125e-07f + c.slack_f;   // 2^-21
+  return tw >= c.wlo_f - m && tw <= c.whi_f + m;
 }
 
 GL_HD bool in_window(const SetConst& c, double tau, double halfwidth) {
@@ -246,13 +281,11 @@ GL_HD bool in_window(const SetConst& c, double tau, double halfwidth) {
 }
 
 // ------------------------------------------------------------------ orbit
-// Sky position at time offset tau from conjunction.  Kepler's equation is
-// solved for the eccentric anomaly E = E_c + d about the conjunction:
-//   d - e [cos E_c sin d + sin E_c (cos d - 1)] = n tau,
-// by Newton's method (bisection safeguard on the bracket |E - M| <= e).  The sky
-// coordinates are formed from differences to the conjunction point, where
-// r cos(w + nu) = 0 and r sin(w + nu) = r_c, so no large terms cancel.
-GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, double* z) {
+// Kepler's equation for the eccentric anomaly E = E_c + d about the
+// conjunction:  d - e [cos E_c sin d + sin E_c (cos d - 1)] = n tau,
+// by Newton's method (bisection safeguard on the bracket |E - M| <= e).
+// Returns sin d and cos d - 1.
+GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* cm1_out) {
   double nt = c.nmean * tau;
   double e = c.ecc;
   double ec = e * c.cosEc, es = e * c.sinEc;
@@ -271,7 +304,6 @@ GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, d
     }
   }
   if (!conv) {
-    // bisection on E in [M - e, M + e], expressed in d = E - E_c
     double M = c.Mc + nt;
     double Ec = atan2(c.sinEc, c.cosEc);
     double lo = M - e - Ec, hi = M + e - Ec;
@@ -283,7 +315,15 @@ GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, d
     }
     d = 0.5 * (lo + hi);
   }
-  sin_cosm1(d, &sd, &cm1);
+  sin_cosm1(d, sd_out, cm1_out);
+}
+
+// Sky position at time offset tau from conjunction.  The sky coordinates are
+// formed from differences to the conjunction point, where r cos(w + nu) = 0 and
+// r sin(w + nu) = r_c, so no large terms cancel.
+GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, double* z) {
+  double sd, cm1;
+  kepler_offset(c, tau, &sd, &cm1);
   double dcosE = c.cosEc * cm1 - c.sinEc * sd;    // cos E - cos E_c
   double dsinE = c.sinEc * cm1 + c.cosEc * sd;    // sin E - sin E_c
   double dX = c.a_rs * dcosE, dY = c.b_orb * dsinE;
@@ -294,17 +334,84 @@ GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, d
   *z = -p2 * c.sini;
 }
 
+// Position and its first three time derivatives (velocity, acceleration,
+// jerk) in the sky frame; acceleration and jerk from r'' = -mu r/|r|^3 with
+// mu = n^2 a^3 (exact for a Kepler orbit).
+struct SkyState {
+  double x, y, z;
+  double d1[3], d2[3], d3[3];
+};
+
+GL_HD void sky_state(const SetConst& c, double tau, SkyState* s) {
+  double sd, cm1;
+  kepler_offset(c, tau, &sd, &cm1);
+  double dcosE = c.cosEc * cm1 - c.sinEc * sd;
+  double dsinE = c.sinEc * cm1 + c.cosEc * sd;
+  double dX = c.a_rs * dcosE, dY = c.b_orb * dsinE;
+  double p1 = dX * c.cosw - dY * c.sinw;
+  double p2 = c.rc + (dX * c.sinw + dY * c.cosw);
+  s->y = -p1;
+  s->x = p2 * c.cosi;
+  s->z = -p2 * c.sini;
+  double cosE = c.cosEc + dcosE, sinE = c.sinEc + dsinE;
+  double X = c.a_rs * (cosE - c.ecc), Y = c.b_orb * sinE;
+  double r = c.a_rs * (1.0 - c.ecc * cosE);
+  double Ed = c.nmean * c.a_rs / r;                 // dE/dt
+  double Xd = -c.a_rs * sinE * Ed, Yd = c.b_orb * cosE * Ed;
+  double mu = c.nmean * c.nmean * c.a_rs * c.a_rs * c.a_rs;
+  double ir2 = 1.0 / (r * r), ir3 = ir2 / r;
+  double rv = X * Xd + Y * Yd;
+  double Xa = -mu * X * ir3, Ya = -mu * Y * ir3;
+  double Xj = -mu * (Xd * ir3 - 3.0 * X * rv * ir3 * ir2);
+  double Yj = -mu * (Yd * ir3 - 3.0 * Y * rv * ir3 * ir2);
+  double in[3][2] = {{Xd, Yd}, {Xa, Ya}, {Xj, Yj}};
+  double* out[3] = {s->d1, s->d2, s->d3};
+  for (int k = 0; k < 3; ++k) {
+    double q1 = in[k][0] * c.cosw - in[k][1] * c.sinw;
+    double q2 = in[k][0] * c.sinw + in[k][1] * c.cosw;
+    out[k][0] = q2 * c.cosi;
+    out[k][1] = -q1;
+    out[k][2] = -q2 * c.sini;
+  }
+}
+
+// ------------------------------------------------------------------ precision helpers
+GL_HD double m_sqrt(double x) { return sqrt(x); }
+GL_HD float m_sqrt(float x) { return sqrtf(x); }
+GL_HD double m_cbrt(double x) { return cbrt(x); }
+GL_HD float m_cbrt(float x) { return cbrtf(x); }
+GL_HD double m_acos(double x) { return acos(x); }
+GL_HD float m_acos(float x) { return acosf(x); }
+GL_HD double m_cos(double x) { return cos(x); }
+GL_HD float m_cos(float x) { return cosf(x); }
+GL_HD double m_atan2(double y, double x) { return atan2(y, x); }
+GL_HD float m_atan2(float y, float x) { return atan2f(y, x); }
+GL_HD double m_abs(double x) { return fabs(x); }
+GL_HD float m_abs(float x) { return fabsf(x); }
+GL_HD double m_copysign(double a, double b) { return copysign(a, b); }
+GL_HD float m_copysign(float a, float b) { return copysignf(a, b); }
+GL_HD bool m_finite(double x) { return isfinite(x); }
+GL_HD bool m_finite(float x) { return isfinite(x); }
+template <typename T> GL_HD T m_eps();
+template <> GL_HD double m_eps<double>() { return 2.220446049250313e-16; }
+template <> GL_HD float m_eps<float>() { return 1.1920929e-07f; }
+
 // ------------------------------------------------------------------ sky geometry
 enum : int { kOut = 0, kFull = 1, kPartial = 2 };
 
 // Quick classification from the centre distance alone (R_eq is the largest
 // semi-axis of the projection).  kPartial means "decide with the roots".
-GL_HD int classify(const SetConst& c, double x0, double y0, double z) {
-  if (z > 0.0) return kOut;
-  double rho = sqrt(x0 * x0 + y0 * y0);
-  if (rho >= 1.0 + c.req) return kOut;
-  if (rho + c.req <= 1.0) return kFull;
+// `slack` widens the undecided band to cover rounding of the centre.
+template <typename T>
+GL_HD int classify_t(T req, T x0, T y0, T z, T slack) {
+  if (z > T(0)) return kOut;
+  T rho = m_sqrt(x0 * x0 + y0 * y0);
+  if (rho >= T(1) + req + slack) return kOut;
+  if (rho + req <= T(1) - slack) return kFull;
   return kPartial;
+}
+GL_HD int classify(const SetConst& c, double x0, double y0, double z) {
+  return classify_t<double>(c.req, x0, y0, z, 0.0);
 }
 
 // Geometry of one evaluation in the quadrature precision R.
@@ -315,18 +422,19 @@ struct Geo {
   R W0, Wc, Ws;        // x y' - y x' = W0 + Wc cos th + Ws sin th
 };
 
+// omr2 = 1 - x0^2 - y0^2, supplied by the caller in the best precision it has.
 template <typename R>
-GL_HD Geo<R> make_geo(const SetConst& c, double x0, double y0) {
+GL_HD Geo<R> make_geo(const SetConst& c, R x0, R y0, R omr2) {
   Geo<R> g;
-  g.x0 = (R)x0;
-  g.y0 = (R)y0;
-  g.omr2 = (R)((1.0 - x0) * (1.0 + x0) - y0 * y0);
+  g.x0 = x0;
+  g.y0 = y0;
+  g.omr2 = omr2;
   g.dx = (R)c.dx;
   g.dy1 = (R)c.dy1;
   g.dy2 = (R)c.dy2;
   g.W0 = (R)(c.dx * c.dy2);
-  g.Wc = (R)(x0 * c.dy2);
-  g.Ws = (R)(y0 * c.dx - x0 * c.dy1);
+  g.Wc = x0 * g.dy2;
+  g.Ws = y0 * g.dx - x0 * g.dy1;
   return g;
 }
 
@@ -371,7 +479,6 @@ template <typename R>
 GL_HD R lin_full(const Geo<R>& g, R cs, R ss, const NodeRule<R>& rule) {
   CSum<R> acc;
   for (int j = 0; j < rule.n; ++j) {
-    // theta = th* + pi + pi sig_j
     R ct = -(cs * rule.cph[j] - ss * rule.sph[j]);
     R st = -(ss * rule.cph[j] + cs * rule.sph[j]);
     acc.add(rule.wt[j] * lin_point<R>(g, ct, st));
@@ -380,33 +487,38 @@ GL_HD R lin_full(const Geo<R>& g, R cs, R ss, const NodeRule<R>& rule) {
 }
 
 // g(th) = |p(th)|^2 - 1 = A + B cos th + C sin th + D cos 2th + E sin 2th.
+template <typename T>
 struct Trig2 {
-  double A, B, C, D, E;
+  T A, B, C, D, E;
 };
-GL_HD Trig2 limb_poly(const SetConst& c, double x0, double y0) {
-  Trig2 t;
-  t.A = (1.0 - x0) * (1.0 + x0) - y0 * y0;
-  t.A = -t.A + 0.5 * (c.dx * c.dx + c.dy1 * c.dy1 + c.dy2 * c.dy2);
-  t.B = 2.0 * (x0 * c.dx + y0 * c.dy1);
-  t.C = 2.0 * y0 * c.dy2;
-  t.D = 0.5 * (c.dx * c.dx + c.dy1 * c.dy1 - c.dy2 * c.dy2);
-  t.E = c.dy1 * c.dy2;
+// omr2 = 1 - x0^2 - y0^2.
+template <typename T>
+GL_HD Trig2<T> limb_poly(const SetConst& c, T x0, T y0, T omr2) {
+  T dx = (T)c.dx, dy1 = (T)c.dy1, dy2 = (T)c.dy2;
+  Trig2<T> t;
+  t.A = -omr2 + T(0.5) * (dx * dx + dy1 * dy1 + dy2 * dy2);
+  t.B = T(2) * (x0 * dx + y0 * dy1);
+  t.C = T(2) * y0 * dy2;
+  t.D = T(0.5) * (dx * dx + dy1 * dy1 - dy2 * dy2);
+  t.E = dy1 * dy2;
   return t;
+}
+template <typename T>
+GL_HD T trig2_eval(const Trig2<T>& t, T ct, T st) {
+  return t.A + t.B * ct + t.C * st + t.D * (ct * ct - st * st) + t.E * (T(2) * st * ct);
 }
 
 // Angle of the boundary point nearest the limb (maximum of g): start at the
 // point whose outward normal is along the centre direction, then Newton on g'.
 template <typename R>
-GL_HD void nearest_limb_angle(const SetConst& c, double x0, double y0, R* cs, R* ss) {
-  R bx = (R)(c.dx * x0 + c.dy1 * y0), by = (R)(c.dy2 * y0);
-  R nrm = sqrt(bx * bx + by * by);
+GL_HD void nearest_limb_angle(const Geo<R>& g, const Trig2<R>& t, R* cs, R* ss) {
+  R bx = g.dx * g.x0 + g.dy1 * g.y0, by = g.dy2 * g.y0;
+  R nrm = m_sqrt(bx * bx + by * by);
   R ct = nrm > R(0) ? bx / nrm : R(1), st = nrm > R(0) ? by / nrm : R(0);
-  Trig2 t = limb_poly(c, x0, y0);
-  R B = (R)t.B, C = (R)t.C, D = (R)t.D, E = (R)t.E;
   for (int it = 0; it < 3; ++it) {
     R c2 = ct * ct - st * st, s2 = R(2) * st * ct;
-    R g1 = -B * st + C * ct - R(2) * D * s2 + R(2) * E * c2;
-    R g2 = -B * ct - C * st - R(4) * D * c2 - R(4) * E * s2;
+    R g1 = -t.B * st + t.C * ct - R(2) * t.D * s2 + R(2) * t.E * c2;
+    R g2 = -t.B * ct - t.C * st - R(4) * t.D * c2 - R(4) * t.E * s2;
     if (!(g2 < R(0))) break;
     R step = g1 / g2;
     if (step > R(0.5)) step = R(0.5);
@@ -421,83 +533,297 @@ GL_HD void nearest_limb_angle(const SetConst& c, double x0, double y0, R* cs, R*
   *ss = st;
 }
 
-// ------------------------------------------------------------------ quartic (FP64)
+// ------------------------------------------------------------------ quartics
 // Largest real root of z^3 + a z^2 + b z + c, refined by Newton.
-GL_HD double cubic_largest_root(double a, double b, double c) {
-  double Q = (a * a - 3.0 * b) / 9.0;
-  double Rr = (2.0 * a * a * a - 9.0 * a * b + 27.0 * c) / 54.0;
-  double z;
-  if (Q > 0.0 && Rr * Rr < Q * Q * Q) {
-    double th = acos(fmax(-1.0, fmin(1.0, Rr / sqrt(Q * Q * Q))));
-    z = -2.0 * sqrt(Q) * cos((th + 2.0 * kPi) / 3.0) - a / 3.0;
+template <typename T>
+GL_HD T cubic_largest_root(T a, T b, T c) {
+  T Q = (a * a - T(3) * b) / T(9);
+  T Rr = (T(2) * a * a * a - T(9) * a * b + T(27) * c) / T(54);
+  T z;
+  if (Q > T(0) && Rr * Rr < Q * Q * Q) {
+    T arg = Rr / m_sqrt(Q * Q * Q);
+    arg = arg < T(-1) ? T(-1) : (arg > T(1) ? T(1) : arg);
+    T th = m_acos(arg);
+    z = -T(2) * m_sqrt(Q) * m_cos((th + T(2 * kPi)) / T(3)) - a / T(3);
   } else {
-    double A = -copysign(cbrt(fabs(Rr) + sqrt(fmax(0.0, Rr * Rr - Q * Q * Q))), Rr);
-    double B = (A != 0.0) ? Q / A : 0.0;
-    z = A + B - a / 3.0;
+    T disc = Rr * Rr - Q * Q * Q;
+    T A = -m_copysign(m_cbrt(m_abs(Rr) + m_sqrt(disc > T(0) ? disc : T(0))), Rr);
+    T B = (A != T(0)) ? Q / A : T(0);
+    z = A + B - a / T(3);
   }
   for (int it = 0; it < 3; ++it) {
-    double f = ((z + a) * z + b) * z + c;
-    double fp = (3.0 * z + 2.0 * a) * z + b;
-    if (fp == 0.0) break;
-    double step = f / fp;
+    T f = ((z + a) * z + b) * z + c;
+    T fp = (T(3) * z + T(2) * a) * z + b;
+    if (fp == T(0)) break;
+    T step = f / fp;
     z -= step;
-    if (fabs(step) <= 1e-16 * fabs(z)) break;
+    if (m_abs(step) <= m_eps<T>() * m_abs(z)) break;
   }
   return z;
 }
 
 // Real roots of the monic quadratic y^2 + p y + q; returns how many (0 or 2).
-GL_HD int quad_roots(double p, double q, double* r) {
-  double disc = p * p - 4.0 * q;
-  if (disc < 0.0) return 0;
-  double s = sqrt(disc);
-  double y1 = -0.5 * (p + copysign(s, p));
+template <typename T>
+GL_HD int quad_roots(T p, T q, T* r) {
+  T disc = p * p - T(4) * q;
+  if (disc < T(0)) return 0;
+  T s = m_sqrt(disc);
+  T y1 = -T(0.5) * (p + m_copysign(s, p));
   r[0] = y1;
-  r[1] = (y1 != 0.0) ? q / y1 : 0.0;
+  r[1] = (y1 != T(0)) ? q / y1 : T(0);
   return 2;
 }
 
 // Real roots of x^4 + a x^3 + b x^2 + c x + d by Ferrari's resolvent, each
 // polished by Newton on the quartic.  Returns the count (0..4).
-GL_HD int quartic_real_roots(double a, double b, double c, double d, double* x) {
-  double a2 = a * a;
-  double p = b - 0.375 * a2;
-  double q = c - 0.5 * a * b + 0.125 * a2 * a;
-  double r = d - 0.25 * a * c + 0.0625 * a2 * b - 0.01171875 * a2 * a2;
-  double y[4];
+template <typename T>
+GL_HD int quartic_real_roots(T a, T b, T c, T d, T* x) {
+  T a2 = a * a;
+  T p = b - T(0.375) * a2;
+  T q = c - T(0.5) * a * b + T(0.125) * a2 * a;
+  T r = d - T(0.25) * a * c + T(0.0625) * a2 * b - T(0.01171875) * a2 * a2;
+  T y[4];
   int n = 0;
   // resolvent: z^3 + 2p z^2 + (p^2 - 4r) z - q^2 = 0, z = s^2 >= 0
-  double z = cubic_largest_root(2.0 * p, p * p - 4.0 * r, -q * q);
-  if (z > 1e-14 * (fabs(p) + sqrt(fabs(r)) + 1e-300)) {
-    double s = sqrt(z);
-    double al = 0.5 * (p + z - q / s), be = 0.5 * (p + z + q / s);
-    n += quad_roots(s, al, y + n);
-    n += quad_roots(-s, be, y + n);
+  T z = cubic_largest_root<T>(T(2) * p, p * p - T(4) * r, -q * q);
+  if (z > T(64) * m_eps<T>() * (m_abs(p) + m_sqrt(m_abs(r)) + T(1e-30))) {
+    T s = m_sqrt(z);
+    T al = T(0.5) * (p + z - q / s), be = T(0.5) * (p + z + q / s);
+    n += quad_roots<T>(s, al, y + n);
+    n += quad_roots<T>(-s, be, y + n);
   } else {
     // biquadratic: y^2 = w, w^2 + p w + r = 0
-    double w[2];
-    int nw = quad_roots(p, r, w);
+    T w[2];
+    int nw = quad_roots<T>(p, r, w);
     for (int i = 0; i < nw; ++i) {
-      if (w[i] >= 0.0) {
-        double sw = sqrt(w[i]);
+      if (w[i] >= T(0)) {
+        T sw = m_sqrt(w[i]);
         y[n++] = sw;
         y[n++] = -sw;
       }
     }
   }
   for (int i = 0; i < n; ++i) {
-    double t = y[i] - 0.25 * a;
+    T t = y[i] - T(0.25) * a;
     for (int it = 0; it < 3; ++it) {
-      double f = (((t + a) * t + b) * t + c) * t + d;
-      double fp = ((4.0 * t + 3.0 * a) * t + 2.0 * b) * t + c;
-      if (fp == 0.0) break;
-      double step = f / fp;
+      T f = (((t + a) * t + b) * t + c) * t + d;
+      T fp = ((T(4) * t + T(3) * a) * t + T(2) * b) * t + c;
+      if (fp == T(0)) break;
+      T step = f / fp;
       t -= step;
-      if (fabs(step) <= 1e-16 * (1.0 + fabs(t))) break;
+      if (m_abs(step) <= m_eps<T>() * (T(1) + m_abs(t))) break;
     }
     x[i] = t;
   }
   return n;
+}
+
+GL_HD void sort_small(double* v, int n) {
+  for (int i = 1; i < n; ++i) {
+    double x = v[i];
+    int j = i - 1;
+    while (j >= 0 && v[j] > x) {
+      v[j + 1] = v[j];
+      --j;
+    }
+    v[j + 1] = x;
+  }
+}
+GL_HD void sort_small(float* v, int n) {
+  for (int i = 1; i < n; ++i) {
+    float x = v[i];
+    int j = i - 1;
+    while (j >= 0 && v[j] > x) {
+      v[j + 1] = v[j];
+      --j;
+    }
+    v[j + 1] = x;
+  }
+}
+
+// g in the frame th = delta + phi, t = tan(phi/2): g (1 + t^2)^2 = sum q_k t^k.
+// delta is chosen so that t -> infinity falls on the one of eight sampled
+// angles where |g| is largest, which keeps q4 away from zero.
+template <typename T>
+struct Frame {
+  T cd, sd;      // cos, sin of delta
+  T q[5];        // q0..q4
+};
+
+template <typename T>
+GL_HD Frame<T> make_frame(const Trig2<T>& t) {
+  const T r2 = T(0.70710678118654752440);
+  const T cs8[8] = {T(1), r2, T(0), -r2, T(-1), -r2, T(0), r2};
+  const T sn8[8] = {T(0), r2, T(1), r2, T(0), -r2, T(-1), -r2};
+  int kbest = 0;
+  T gbest = T(-1);
+  for (int kk = 0; kk < 8; ++kk) {
+    T c1 = cs8[kk], s1 = sn8[kk];
+    T c2 = c1 * c1 - s1 * s1, s2 = T(2) * s1 * c1;
+    T gv = m_abs(t.A + t.B * c1 + t.C * s1 + t.D * c2 + t.E * s2);
+    if (gv > gbest) {
+      gbest = gv;
+      kbest = kk;
+    }
+  }
+  Frame<T> f;
+  f.cd = -cs8[kbest];
+  f.sd = -sn8[kbest];
+  T c2d = f.cd * f.cd - f.sd * f.sd, s2d = T(2) * f.sd * f.cd;
+  T Bp = t.B * f.cd + t.C * f.sd, Cp = t.C * f.cd - t.B * f.sd;
+  T Dp = t.D * c2d + t.E * s2d, Ep = t.E * c2d - t.D * s2d;
+  f.q[4] = t.A - Bp + Dp;
+  f.q[3] = T(2) * Cp - T(4) * Ep;
+  f.q[2] = T(2) * t.A - T(6) * Dp;
+  f.q[1] = T(2) * Cp + T(4) * Ep;
+  f.q[0] = t.A + Bp + Dp;
+  return f;
+}
+
+template <typename T>
+GL_HD T frame_poly(const Frame<T>& f, T t) {
+  return (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
+}
+
+// Drop coincident neighbours of a sorted list (tangency: no crossing).
+template <typename T>
+GL_HD int drop_pairs(T* tr, int nr, T tol) {
+  T tt[4];
+  int m = 0;
+  for (int i = 0; i < nr; ++i) {
+    if (i + 1 < nr && m_abs(tr[i + 1] - tr[i]) <= tol * (T(1) + m_abs(tr[i]))) {
+      ++i;
+      continue;
+    }
+    tt[m++] = tr[i];
+  }
+  for (int i = 0; i < m; ++i) tr[i] = tt[i];
+  return m;
+}
+
+// Real roots of the frame's quartic in t, sorted ascending (= counter-clockwise
+// order in theta), in the frame's own precision.
+template <typename T>
+GL_HD int frame_roots(const Frame<T>& f, T* tr) {
+  if (!(m_abs(f.q[4]) > T(0))) return 0;
+  T inv = T(1) / f.q[4];
+  int nr = quartic_real_roots<T>(f.q[3] * inv, f.q[2] * inv, f.q[1] * inv, f.q[0] * inv, tr);
+  sort_small(tr, nr);
+  return drop_pairs<T>(tr, nr, T(1024) * m_eps<T>());
+}
+
+// Crossings of the boundary with the limb, in FP64.  R = double: FP64 Ferrari.
+// R = float: FP32 Ferrari estimates polished by FP64 Newton on the FP64
+// quartic; if the polish does not converge, two roots merge or the count is
+// odd, the FP64 Ferrari result is used instead.
+template <typename R>
+GL_HD int crossing_roots(const Frame<double>& f, double* tr);
+
+template <>
+GL_HD int crossing_roots<double>(const Frame<double>& f, double* tr) {
+  return frame_roots<double>(f, tr);
+}
+
+template <>
+GL_HD int crossing_roots<float>(const Frame<double>& f, double* tr) {
+  if (!(fabs(f.q[4]) > 0.0)) return 0;
+  double inv = 1.0 / f.q[4];
+  double a = f.q[3] * inv, b = f.q[2] * inv, c = f.q[1] * inv, d = f.q[0] * inv;
+  float xs[4];
+  int nr = quartic_real_roots<float>((float)a, (float)b, (float)c, (float)d, xs);
+  bool ok = (nr % 2) == 0;
+  for (int i = 0; i < nr && ok; ++i) {
+    double t = (double)xs[i];
+    bool conv = false;
+    for (int it = 0; it < 6; ++it) {
+      double fv = (((t + a) * t + b) * t + c) * t + d;
+      double fp = ((4.0 * t + 3.0 * a) * t + 2.0 * b) * t + c;
+      if (fp == 0.0) break;
+      double step = fv / fp;
+      t -= step;
+      if (fabs(step) <= 1e-15 * (1.0 + fabs(t))) {
+        conv = true;
+        break;
+      }
+    }
+    ok = conv;
+    tr[i] = t;
+  }
+  if (ok) {
+    sort_small(tr, nr);
+    for (int i = 0; i + 1 < nr; ++i)
+      if (tr[i + 1] - tr[i] <= 1e-9 * (1.0 + fabs(tr[i]))) ok = false;
+  }
+  if (!ok) return frame_roots<double>(f, tr);
+  return nr;
+}
+
+// (cos th, sin th) of the point t of frame f.
+template <typename T>
+GL_HD void frame_angle(const Frame<T>& f, T t, T* ct, T* st) {
+  T den = T(1) / (T(1) + t * t);
+  T cph = (T(1) - t * t) * den, sph = T(2) * t * den;
+  *ct = f.cd * cph - f.sd * sph;
+  *st = f.sd * cph + f.cd * sph;
+}
+
+// t of frame f for the angle (cos th, sin th); +inf at phi = pi.
+template <typename T>
+GL_HD T frame_t(const Frame<T>& f, T ct, T st) {
+  T cph = ct * f.cd + st * f.sd, sph = st * f.cd - ct * f.sd;
+  T den = T(1) + cph;
+  if (!(den > T(1e-30))) return T(INFINITY);
+  return sph / den;
+}
+
+// Arc of the ellipse from t_a to t_b (counter-clockwise; wrap = passes t = inf):
+// half-width h and (cos, sin) of its mid-direction, in precision R.
+template <typename R>
+GL_HD void frame_arc(R N, R D, bool wrap, R cta, R sta, R* h, R* cm, R* sm) {
+  R hyp = m_sqrt(N * N + D * D);
+  R ch, sh;
+  if (!wrap) {
+    *h = m_atan2(N, D);
+    ch = D / hyp;
+    sh = N / hyp;
+  } else {
+    *h = R(kPi) + m_atan2(N, D);
+    ch = -D / hyp;
+    sh = -N / hyp;
+  }
+  *cm = cta * ch - sta * sh;
+  *sm = sta * ch + cta * sh;
+}
+
+// Local maxima of g that lie inside the disk (g < 0): the points where the
+// boundary comes nearest the limb without reaching it.  The quadrature is split
+// there so that the near-singular (1 - r^2)^(3/2) sits at an arc end, where the
+// mapped rule clusters its nodes.  Returns (cos, sin) of up to 2 maxima.
+template <typename T>
+GL_HD int inner_maxima(const Trig2<T>& t, T* cm, T* sm) {
+  Trig2<T> d;   // g'(th)
+  d.A = T(0);
+  d.B = t.C;
+  d.C = -t.B;
+  d.D = T(2) * t.E;
+  d.E = T(-2) * t.D;
+  if (!(m_abs(d.B) + m_abs(d.C) + m_abs(d.D) + m_abs(d.E) > T(1e-30))) return 0;
+  Frame<T> f = make_frame<T>(d);
+  T tr[4];
+  int nr = frame_roots<T>(f, tr);
+  int m = 0;
+  for (int i = 0; i < nr; ++i) {
+    T ct, st;
+    frame_angle<T>(f, tr[i], &ct, &st);
+    T c2 = ct * ct - st * st, s2 = T(2) * st * ct;
+    T g2 = -t.B * ct - t.C * st - T(4) * t.D * c2 - T(4) * t.E * s2;
+    if (g2 < T(0) && trig2_eval<T>(t, ct, st) < T(0) && m < 2) {
+      cm[m] = ct;
+      sm[m] = st;
+      ++m;
+    }
+  }
+  return m;
 }
 
 // Closed-form antiderivative of f_quad along the ellipse boundary (a trig
@@ -546,167 +872,32 @@ GL_HD R quad_poly_trig(const QuadPoly<R>& q, R ct, R st) {
   return acc;
 }
 
-// ------------------------------------------------------------------ trig quartics
-// g(th) in the frame th = delta + phi, t = tan(phi/2): g (1 + t^2)^2 = sum q_k t^k.
-// delta is chosen so that t -> infinity falls on the one of eight sampled
-// angles where |g| is largest, which keeps q4 away from zero.
-struct Frame {
-  double cd, sd;      // cos, sin of delta
-  double q[5];        // q0..q4
-};
-
-GL_HD Frame make_frame(const Trig2& t) {
-  const double r2 = 0.70710678118654752440;
-  const double cs8[8] = {1.0, r2, 0.0, -r2, -1.0, -r2, 0.0, r2};
-  const double sn8[8] = {0.0, r2, 1.0, r2, 0.0, -r2, -1.0, -r2};
-  int kbest = 0;
-  double gbest = -1.0;
-  for (int kk = 0; kk < 8; ++kk) {
-    double c1 = cs8[kk], s1 = sn8[kk];
-    double c2 = c1 * c1 - s1 * s1, s2 = 2.0 * s1 * c1;
-    double gv = fabs(t.A + t.B * c1 + t.C * s1 + t.D * c2 + t.E * s2);
-    if (gv > gbest) {
-      gbest = gv;
-      kbest = kk;
-    }
-  }
-  Frame f;
-  f.cd = -cs8[kbest];
-  f.sd = -sn8[kbest];
-  double c2d = f.cd * f.cd - f.sd * f.sd, s2d = 2.0 * f.sd * f.cd;
-  double Bp = t.B * f.cd + t.C * f.sd, Cp = t.C * f.cd - t.B * f.sd;
-  double Dp = t.D * c2d + t.E * s2d, Ep = t.E * c2d - t.D * s2d;
-  f.q[4] = t.A - Bp + Dp;
-  f.q[3] = 2.0 * Cp - 4.0 * Ep;
-  f.q[2] = 2.0 * t.A - 6.0 * Dp;
-  f.q[1] = 2.0 * Cp + 4.0 * Ep;
-  f.q[0] = t.A + Bp + Dp;
-  return f;
-}
-
-GL_HD double frame_poly(const Frame& f, double t) {
-  return (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
-}
-
-// Real roots in t, sorted ascending (= counter-clockwise order in theta), with
-// coincident pairs (tangency, no crossing) removed.
-GL_HD int frame_roots(const Frame& f, double* tr) {
-  if (!(fabs(f.q[4]) > 0.0)) return 0;
-  double inv = 1.0 / f.q[4];
-  int nr = quartic_real_roots(f.q[3] * inv, f.q[2] * inv, f.q[1] * inv, f.q[0] * inv, tr);
-  for (int i = 1; i < nr; ++i) {
-    double v = tr[i];
-    int j = i - 1;
-    while (j >= 0 && tr[j] > v) {
-      tr[j + 1] = tr[j];
-      --j;
-    }
-    tr[j + 1] = v;
-  }
-  double tt[4];
-  int m = 0;
-  for (int i = 0; i < nr; ++i) {
-    if (i + 1 < nr && fabs(tr[i + 1] - tr[i]) <= 1e-13 * (1.0 + fabs(tr[i]))) {
-      ++i;
-      continue;
-    }
-    tt[m++] = tr[i];
-  }
-  for (int i = 0; i < m; ++i) tr[i] = tt[i];
-  return m;
-}
-
-// (cos th, sin th) of the point t of frame f.
-GL_HD void frame_angle(const Frame& f, double t, double* ct, double* st) {
-  double den = 1.0 / (1.0 + t * t);
-  double cph = (1.0 - t * t) * den, sph = 2.0 * t * den;
-  *ct = f.cd * cph - f.sd * sph;
-  *st = f.sd * cph + f.cd * sph;
-}
-
-GL_HD double trig2_eval(const Trig2& t, double ct, double st) {
-  return t.A + t.B * ct + t.C * st + t.D * (ct * ct - st * st) + t.E * (2.0 * st * ct);
-}
-
-// Local maxima of g that lie inside the disk (g < 0): the points where the
-// boundary comes nearest the limb without reaching it.  The quadrature is split
-// there so that the near-singular (1 - r^2)^(3/2) sits at an arc end, where the
-// mapped rule clusters its nodes.  Returns (cos, sin) of up to 2 maxima.
-GL_HD int inner_maxima(const Trig2& t, double* cm, double* sm) {
-  Trig2 d;   // g'(th)
-  d.A = 0.0;
-  d.B = t.C;
-  d.C = -t.B;
-  d.D = 2.0 * t.E;
-  d.E = -2.0 * t.D;
-  if (!(fabs(d.B) + fabs(d.C) + fabs(d.D) + fabs(d.E) > 1e-300)) return 0;
-  Frame f = make_frame(d);
-  double tr[4];
-  int nr = frame_roots(f, tr);
-  int m = 0;
-  for (int i = 0; i < nr; ++i) {
-    double ct, st;
-    frame_angle(f, tr[i], &ct, &st);
-    double c2 = ct * ct - st * st, s2 = 2.0 * st * ct;
-    double g2 = -t.B * ct - t.C * st - 4.0 * t.D * c2 - 4.0 * t.E * s2;
-    if (g2 < 0.0 && trig2_eval(t, ct, st) < 0.0 && m < 2) {
-      cm[m] = ct;
-      sm[m] = st;
-      ++m;
-    }
-  }
-  return m;
-}
-
-// t of frame f for the angle (cos th, sin th); +inf at phi = pi.
-GL_HD double frame_t(const Frame& f, double ct, double st) {
-  double cph = ct * f.cd + st * f.sd, sph = st * f.cd - ct * f.sd;
-  double den = 1.0 + cph;
-  if (!(den > 1e-300)) return INFINITY;
-  return sph / den;
-}
-
-// Arc of the ellipse from t_a to t_b (counter-clockwise; wrap = passes t = inf):
-// half-width h and (cos, sin) of its mid-direction in theta.
-GL_HD void frame_arc(const Frame& f, double ta, double tb, bool wrap, double cta, double sta,
-                     double* h, double* cm, double* sm) {
-  double N = tb - ta, D = 1.0 + ta * tb;
-  double hyp = sqrt(N * N + D * D);
-  double ch, sh;
-  if (!wrap) {
-    *h = atan2(N, D);
-    ch = D / hyp;
-    sh = N / hyp;
-  } else {
-    *h = kPi + atan2(N, D);
-    ch = -D / hyp;
-    sh = -N / hyp;
-  }
-  *cm = cta * ch - sta * sh;
-  *sm = sta * ch + cta * sh;
-}
-
 // ------------------------------------------------------------------ occulted moments
-// I[0] = area, I[1] = Integral mu dA, I[2] = Integral r^2 dA of the region where
-// the projected ellipse covers the stellar disk.  `cls` comes from classify().
+// Moments of the region where the projected ellipse covers the stellar disk:
+// I[0] = area, I[1] = Integral mu dA, I[2] = Integral r^2 dA.
+// (x0, y0, omr2 = 1 - x0^2 - y0^2) in the quadrature precision R; the
+// crossings are found in FP64 from the same (x0, y0) widened to double.
+// `cls` comes from the classification (kFull skips the crossings).
 template <typename R>
-GL_HD void occulted(const SetConst& c, double x0, double y0, int cls, const NodeRule<R>& rule,
-                    R I[3]) {
+GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const NodeRule<R>& rule,
+                      R I[3]) {
   I[0] = I[1] = I[2] = R(0);
   if (cls == kOut) return;
-  Geo<R> g = make_geo<R>(c, x0, y0);
-  Trig2 tg = limb_poly(c, x0, y0);
+  Geo<R> g = make_geo<R>(c, x0, y0, omr2);
+  Trig2<R> tg = limb_poly<R>(c, x0, y0, omr2);
   R area = R(kPi) * g.dx * g.dy2;
-  double cmx[2], smx[2];
-  int nmax = inner_maxima(tg, cmx, smx);
+  R cmx[2], smx[2];
+  int nmax = inner_maxima<R>(tg, cmx, smx);
   if (cls == kPartial) {
-    Frame fr = make_frame(tg);
+    double xd = (double)x0, yd = (double)y0;
+    Trig2<double> tgd = limb_poly<double>(c, xd, yd, (1.0 - xd) * (1.0 + xd) - yd * yd);
+    Frame<double> fr = make_frame<double>(tgd);
     double tb[8];
-    int nr = frame_roots(fr, tb);
+    int nr = crossing_roots<R>(fr, tb);
     if (nr == 0) {
       if (!(fr.q[4] < 0.0)) {
         // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
-        double v1 = -x0 / c.dx, v2 = (-y0 - c.dy1 * v1) / c.dy2;
+        double v1 = -xd / c.dx, v2 = (-yd - c.dy1 * v1) / c.dy2;
         if (v1 * v1 + v2 * v2 < 1.0) {
           I[0] = R(kPi);
           I[1] = R(2.0 * kPi / 3.0);
@@ -721,7 +912,7 @@ GL_HD void occulted(const SetConst& c, double x0, double y0, int cls, const Node
       for (int i = 0; i < nr; ++i) kind[i] = 1;
       int nb = nr;
       for (int i = 0; i < nmax; ++i) {
-        double tv = frame_t(fr, cmx[i], smx[i]);
+        double tv = frame_t<double>(fr, (double)cmx[i], (double)smx[i]);
         if (!isfinite(tv)) continue;
         int j = nb - 1;
         while (j >= 0 && tb[j] > tv) {
@@ -733,45 +924,49 @@ GL_HD void occulted(const SetConst& c, double x0, double y0, int cls, const Node
         kind[j + 1] = 0;
         ++nb;
       }
-      double cth[8], sth[8], px[8], py[8];
+      R cth[8], sth[8], px[8], py[8];
       for (int i = 0; i < nb; ++i) {
-        frame_angle(fr, tb[i], &cth[i], &sth[i]);
-        px[i] = x0 + c.dx * cth[i];
-        py[i] = y0 + c.dy1 * cth[i] + c.dy2 * sth[i];
-        double nrm = 1.0 / sqrt(px[i] * px[i] + py[i] * py[i]);
-        px[i] *= nrm;
-        py[i] *= nrm;
+        double ctd, std_;
+        frame_angle<double>(fr, tb[i], &ctd, &std_);
+        cth[i] = (R)ctd;
+        sth[i] = (R)std_;
+        R qx = g.x0 + g.dx * cth[i];
+        R qy = g.y0 + g.dy1 * cth[i] + g.dy2 * sth[i];
+        R nrm = rsqrt_<R>(qx * qx + qy * qy);
+        px[i] = qx * nrm;
+        py[i] = qy * nrm;
       }
       QuadPoly<R> qp = quad_poly<R>(g.x0, g.y0, g.dx, g.dy1, g.dy2);
       CSum<R> sflat, slin, squad;
       for (int i = 0; i < nb; ++i) {
         int ip = (i + 1 == nb) ? 0 : i + 1;
         bool wrap = (i + 1 == nb);
-        double h, cm, sm;
-        frame_arc(fr, tb[i], tb[ip], wrap, cth[i], sth[i], &h, &cm, &sm);
+        R h, cm, sm;
+        frame_arc<R>((R)(tb[ip] - tb[i]), (R)(1.0 + tb[i] * tb[ip]), wrap, cth[i], sth[i], &h,
+                     &cm, &sm);
         if (nb == 1) {   // a lone breakpoint: the arc is the full turn
-          h = kPi;
+          h = R(kPi);
           cm = -cth[i];
           sm = -sth[i];
         }
-        bool inside = wrap ? (fr.q[4] < 0.0) : (frame_poly(fr, 0.5 * (tb[i] + tb[ip])) < 0.0);
+        bool inside =
+            wrap ? (fr.q[4] < 0.0) : (frame_poly<double>(fr, 0.5 * (tb[i] + tb[ip])) < 0.0);
         if (inside) {
-          slin.add(lin_arc<R>(g, (R)cm, (R)sm, (R)h, rule));
-          R ca = (R)cth[i], sa = (R)sth[i], cb = (R)cth[ip], sb = (R)sth[ip];
-          R dth = (R)(2.0 * h);
+          slin.add(lin_arc<R>(g, cm, sm, h, rule));
+          R ca = cth[i], sa = sth[i], cb = cth[ip], sb = sth[ip];
+          R dth = R(2) * h;
           sflat.add(R(0.5) * (g.W0 * dth + g.Wc * (sb - sa) - g.Ws * (cb - ca)));
           squad.add(qp.K * dth + (quad_poly_trig<R>(qp, cb, sb) - quad_poly_trig<R>(qp, ca, sa)));
         } else if (kind[i] && kind[ip]) {
           // the limb arc between the same two crossings lies inside the ellipse
-          double cr = px[i] * py[ip] - py[i] * px[ip], dt = px[i] * px[ip] + py[i] * py[ip];
-          double dl = atan2(cr, dt);
-          if (dl < 0.0) dl += 2.0 * kPi;
-          double s4a = 4.0 * px[i] * py[i] * (px[i] * px[i] - py[i] * py[i]);
-          double s4b = 4.0 * px[ip] * py[ip] * (px[ip] * px[ip] - py[ip] * py[ip]);
-          R dlr = (R)dl;
-          sflat.add(R(0.5) * dlr);
-          slin.add(dlr / R(3));
-          squad.add(R(0.25) * dlr - (R)((s4b - s4a) / 48.0));
+          R cr = px[i] * py[ip] - py[i] * px[ip], dt = px[i] * px[ip] + py[i] * py[ip];
+          R dl = m_atan2(cr, dt);
+          if (dl < R(0)) dl += R(2 * kPi);
+          R s4a = R(4) * px[i] * py[i] * (px[i] * px[i] - py[i] * py[i]);
+          R s4b = R(4) * px[ip] * py[ip] * (px[ip] * px[ip] - py[ip] * py[ip]);
+          sflat.add(R(0.5) * dl);
+          slin.add(dl / R(3));
+          squad.add(R(0.25) * dl - (s4b - s4a) / R(48));
         }
       }
       I[0] = sflat.value();
@@ -782,35 +977,41 @@ GL_HD void occulted(const SetConst& c, double x0, double y0, int cls, const Node
   }
   // whole ellipse inside the disk: split the turn at the inner maxima
   I[0] = area;
-  I[2] = area * ((R)(x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4));
+  I[2] = area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4));
   if (nmax <= 1) {
     R cs, ss;
     if (nmax == 1) {
-      cs = (R)cmx[0];
-      ss = (R)smx[0];
+      cs = cmx[0];
+      ss = smx[0];
     } else {
-      nearest_limb_angle<R>(c, x0, y0, &cs, &ss);
+      nearest_limb_angle<R>(g, tg, &cs, &ss);
     }
     I[1] = lin_full<R>(g, cs, ss, rule);
   } else {
-    Frame fr = make_frame(tg);
-    double ta = frame_t(fr, cmx[0], smx[0]), tb2 = frame_t(fr, cmx[1], smx[1]);
-    double ca = cmx[0], sa = smx[0], cb = cmx[1], sb = smx[1];
-    if (!isfinite(ta) || !isfinite(tb2)) {
-      R cs = (R)cmx[0], ss = (R)smx[0];
-      I[1] = lin_full<R>(g, cs, ss, rule);
+    Frame<R> fr = make_frame<R>(tg);
+    R ta = frame_t<R>(fr, cmx[0], smx[0]), tb2 = frame_t<R>(fr, cmx[1], smx[1]);
+    R ca = cmx[0], sa = smx[0], cb = cmx[1], sb = smx[1];
+    if (!m_finite(ta) || !m_finite(tb2)) {
+      I[1] = lin_full<R>(g, cmx[0], smx[0], rule);
       return;
     }
     if (ta > tb2) {
-      double tmp = ta; ta = tb2; tb2 = tmp;
+      R tmp = ta; ta = tb2; tb2 = tmp;
       tmp = ca; ca = cb; cb = tmp;
       tmp = sa; sa = sb; sb = tmp;
     }
-    double h1, cm1, sm1, h2, cm2, sm2;
-    frame_arc(fr, ta, tb2, false, ca, sa, &h1, &cm1, &sm1);
-    frame_arc(fr, tb2, ta, true, cb, sb, &h2, &cm2, &sm2);
-    I[1] = lin_arc<R>(g, (R)cm1, (R)sm1, (R)h1, rule) + lin_arc<R>(g, (R)cm2, (R)sm2, (R)h2, rule);
+    R h1, cm1, sm1, h2, cm2, sm2;
+    frame_arc<R>(tb2 - ta, R(1) + ta * tb2, false, ca, sa, &h1, &cm1, &sm1);
+    frame_arc<R>(ta - tb2, R(1) + ta * tb2, true, cb, sb, &h2, &cm2, &sm2);
+    I[1] = lin_arc<R>(g, cm1, sm1, h1, rule) + lin_arc<R>(g, cm2, sm2, h2, rule);
   }
+}
+
+// Same, from an FP64 centre (omr2 formed in FP64 before rounding to R).
+template <typename R>
+GL_HD void occulted(const SetConst& c, double x0, double y0, int cls, const NodeRule<R>& rule,
+                    R I[3]) {
+  occulted_r<R>(c, (R)x0, (R)y0, (R)((1.0 - x0) * (1.0 + x0) - y0 * y0), cls, rule, I);
 }
 
 // Relative flux of one sub-exposure.  The subtraction from 1 is in FP64.
@@ -825,6 +1026,50 @@ GL_HD double subexposure_flux(const SetConst& c, double tau, const NodeRule<R>& 
   occulted<R>(c, x0, y0, cls, rule, I);
   R def = (R)c.c0 * I[0] + (R)c.c1 * I[1] + (R)c.c2 * I[2];
   return 1.0 - (double)def * c.invF0;
+}
+
+// Exposure midpoint state rounded for FP32 sub-exposure steps: position,
+// 1 - x^2 - y^2 (formed in FP64) and the first three derivatives.
+struct MidState {
+  float x, y, z, omr2;
+  float d1[3], d2[3], d3[3];
+};
+
+GL_HD MidState mid_state(const SkyState& s) {
+  MidState m;
+  m.x = (float)s.x;
+  m.y = (float)s.y;
+  m.z = (float)s.z;
+  m.omr2 = (float)((1.0 - s.x) * (1.0 + s.x) - s.y * s.y);
+  for (int k = 0; k < 3; ++k) {
+    m.d1[k] = (float)s.d1[k];
+    m.d2[k] = (float)(0.5 * s.d2[k]);
+    m.d3[k] = (float)(s.d3[k] / 6.0);
+  }
+  return m;
+}
+
+// Position dt after the midpoint by the cubic Taylor step, in FP32.  The step
+// is small (|v dt| < 0.1 stellar radii), so its rounding error is far below
+// the FP32 quadrature's.
+GL_HD void taylor_position(const MidState& m, float dt, float* x, float* y, float* z,
+                           float* omr2) {
+  float dd[3];
+  for (int k = 0; k < 3; ++k) dd[k] = ((m.d3[k] * dt + m.d2[k]) * dt + m.d1[k]) * dt;
+  *x = m.x + dd[0];
+  *y = m.y + dd[1];
+  *z = m.z + dd[2];
+  *omr2 = m.omr2 - 2.0f * (m.x * dd[0] + m.y * dd[1]) - (dd[0] * dd[0] + dd[1] * dd[1]);
+}
+
+// Deficit (1 - flux) of one sub-exposure at the given FP32 geometry.
+GL_HD float deficit_f32(const SetConst& c, float x, float y, float z, float omr2,
+                        const NodeRule<float>& rule) {
+  int cls = classify_t<float>((float)c.req, x, y, z, 1e-6f);
+  if (cls == kOut) return 0.0f;
+  float I[3];
+  occulted_r<float>(c, x, y, omr2, cls, rule, I);
+  return ((float)c.c0 * I[0] + (float)c.c1 * I[1] + (float)c.c2 * I[2]) * (float)c.invF0;
 }
 
 // Sub-exposure time offset: ((q + 1/2)/n - 1/2) * exptime.
