@@ -48,6 +48,41 @@ def alu_peaks(sm_mhz: float):
     return fp32, fp64
 
 
+# Algorithmic work per unit of the FP32C light-curve kernel (flops, FMA = 2),
+# counted from the source (see the kernel section of the design doc):
+#   FP32: per exposure window test 12; per sub-exposure position and class 40;
+#         whole-ellipse item 1175 (inner maxima 310, geometry 30, 20 nodes x 41,
+#         closed forms 15); crossing item 2300 (maxima 310, FP32 Ferrari 290,
+#         breakpoints 50, 1.5 arcs x (20 nodes x 49 + 80), limb arcs 25, geometry 30)
+#   FP64: per in-window exposure 10 (exact window); midpoint Kepler state 250;
+#         per sub-exposure FP64 Kepler (no expansion) 250; crossing item 200
+#         (limb polynomial, frame, Newton polish, sign tests); exposure sum 2 per item
+F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 1175, 2300
+F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 250, 200, 2
+
+
+def roofline(c: dict, kernel_ms: float, fp32_peak: float, fp64_peak: float) -> dict:
+    """ALU roofline of the FP32C light-curve kernel: algorithmic FP32 and FP64
+    flops of one launch over its CUDA-event duration, against the pipe that
+    bounds it (the larger of flops/peak)."""
+    f32 = (c["exposures"] * F32_EXPOSURE + c["items"] * F32_ITEM + c["full"] * F32_FULL +
+           c["partial"] * F32_PARTIAL)
+    f64 = (c["in_window"] * F64_WINDOW + (c["kepler"] + c["item_kepler"]) * F64_KEPLER +
+           c["partial"] * F64_PARTIAL + c["items"] * F64_SUM)
+    t = kernel_ms * 1e-3
+    a32, a64 = f32 / t / 1e12, f64 / t / 1e12
+    pipe = "fp64" if f64 / fp64_peak >= f32 / fp32_peak else "fp32"
+    ach, peak = (a64, fp64_peak) if pipe == "fp64" else (a32, fp32_peak)
+    return {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None,
+            "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x max SM clock",
+            "fp32": {"achieved": a32, "peak": fp32_peak, "frac": a32 / fp32_peak,
+                     "flops_per_launch": f32},
+            "fp64": {"achieved": a64, "peak": fp64_peak, "frac": a64 / fp64_peak,
+                     "flops_per_launch": f64},
+            "kernel_ms": kernel_ms}
+
+
 def workload(name: str, seed_offset: int = 0):
     if name == "mcmc_batch":
         return inputs.mcmc_batch(seed=1 + 1000 * seed_offset)
@@ -286,11 +321,14 @@ def main():
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def timed(prec, out, k):
+    def timed(prec, out, k, profile):
+        """k steps, L2 flushed before each, CUDA events on the launch stream around
+        each step (the flush is outside them).  With profile=True the library also
+        times each kernel with events (graph replay is off then)."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(k)]
         l0 = ctx.launches()
-        ctx.profile(True)
+        ctx.profile(profile)
         for i in range(k):
             flush.zero_()
             evs[i][0].record(stream)
@@ -298,9 +336,19 @@ def main():
             evs[i][1].record(stream)
         torch.cuda.synchronize(dev)
         ms = sum(a.elapsed_time(b) for a, b in evs)
-        kern_ms, kern_n = ctx.profile_read(binding.GL_KERNEL_CURVE)
-        ctx.profile(False)
-        return ms, ctx.launches() - l0, kern_ms / max(kern_n, 1)
+        kern = {}
+        if profile:
+            for name, kind in (("curve", binding.GL_KERNEL_CURVE), ("setup", binding.GL_KERNEL_SETUP)):
+                t_ms, n = ctx.profile_read(kind)
+                kern[name] = t_ms / max(n, 1)
+            ctx.profile(False)
+        return ms, ctx.launches() - l0, kern
+
+    # workload counts of one FP32C step (instrumented kernel instance, untimed)
+    ctx.counts(True)
+    step(out32, binding.GL_FP32C)
+    counts = ctx.counts_read()
+    ctx.counts(False)
 
     for _ in range(args.warmup):
         step(out32, binding.GL_FP32C)
@@ -310,17 +358,19 @@ def main():
     barrier(world)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        ms32, launches, kern32 = timed(binding.GL_FP32C, out32, args.steps)
+        ms32, launches, _ = timed(binding.GL_FP32C, out32, args.steps, profile=False)
     barrier(world)
     ms32 = allreduce_max(ms32, world)
-    k64 = max(3, min(args.steps, 20))
-    ms64, _, kern64 = timed(binding.GL_FP64, out64, k64)
-    ms64 = allreduce_max(ms64, world)
     clocks = clk.summary()
+    k_prof = max(3, min(args.steps, 20))
+    _, _, kern32 = timed(binding.GL_FP32C, out32, k_prof, profile=True)
+    k64 = max(3, min(args.steps, 20))
+    ms64, _, _ = timed(binding.GL_FP64, out64, k64, profile=False)
+    ms64 = allreduce_max(ms64, world)
+    _, _, kern64 = timed(binding.GL_FP64, out64, 3, profile=True)
 
     value = world * evals * args.steps / (ms32 * 1e-3)
     fp64_value = world * evals * k64 / (ms64 * 1e-3)
-
     # end to end: pinned host inputs and output through the same public call
     hp = {k: torch.as_tensor(v).pin_memory() for k, v in p.items()}
     h_t = torch.as_tensor(t).pin_memory()
@@ -345,7 +395,6 @@ def main():
     if rank != 0:
         return
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
     fp32_peak, fp64_peak = alu_peaks(peaks.get("sm_max_mhz", 2032.0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -353,16 +402,19 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "evals_per_step": evals,
                    "exposures_per_step": n_tot, "parameter_sets": n_sets,
-                   "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)"},
+                   "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
+                   "graphs": "step replayed as a CUDA graph"},
         "max_dflux_vs_fp64_gpu": max_dflux, "in_transit_exposures": in_transit,
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / k64},
-        "kernel_ms": {"curve_fp32c": kern32, "curve_fp64": kern64},
+        "kernel_ms": {"curve_fp32c": kern32.get("curve"), "setup": kern32.get("setup"),
+                      "curve_fp64": kern64.get("curve")},
+        "workload_counts": counts,
+        "roofline": roofline(counts, kern32["curve"], fp32_peak, fp64_peak),
         "gpu_launches": launches,
         "status": status,
         "clocks": clocks,
         "e2e": {"value": world * evals * k_e2e / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "sm_mhz": peaks.get("sm_max_mhz", 2032.0)},
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sets)

@@ -162,6 +162,39 @@ int gl_sync(gl_context *ctx, void *stream);
  * accounting in benchmarks). */
 int64_t gl_launch_count(const gl_context *ctx);
 
+/* Workload counters of the light-curve kernel (gl_counts_read slots). */
+#define GL_COUNT_EXPOSURES 0    /* exposures tested */
+#define GL_COUNT_KEPT 1         /* exposures passing the FP32 window test */
+#define GL_COUNT_IN_WINDOW 2    /* exposures inside the exact FP64 window */
+#define GL_COUNT_KEPLER 3       /* exposures whose sub-exposures use the midpoint expansion */
+#define GL_COUNT_ITEMS 4        /* sub-exposures of in-window exposures */
+#define GL_COUNT_ITEM_KEPLER 5  /* sub-exposures with their own FP64 Kepler solve */
+#define GL_COUNT_FULL 6         /* sub-exposures with the whole ellipse on the disk */
+#define GL_COUNT_PARTIAL 7      /* sub-exposures needing the crossings */
+#define GL_COUNT_SLOTS 8
+
+/* Workload counting for benchmarks and tests.  While enabled, gl_lightcurve_batch
+ * runs an instrumented instance of its kernel that adds to the GL_COUNT_* slots
+ * (enabling resets them; no graph replay while counting).  GL_EINVAL on a NULL
+ * context, GL_ECUDA on a runtime failure. */
+int gl_counts_enable(gl_context *ctx, int on);
+
+/* Copy the first n counters (int64) to `counts` after waiting for the device;
+ * slots beyond GL_COUNT_SLOTS read 0.  GL_EINVAL on NULL pointers or n < 0. */
+int gl_counts_read(gl_context *ctx, int64_t *counts, int n);
+
+/* CUDA-graph replay of gl_lightcurve_batch (on by default).  When every buffer is
+ * device memory and neither profiling nor counting is on, the step (per-set
+ * constants + light-curve kernel) is captured once per distinct argument set
+ * (pointers, sizes, precision; up to 16 kept, least recently used dropped) and
+ * replayed with cudaGraphLaunch on the caller's stream.  Arguments are read when
+ * the graph runs, so updating the parameter arrays in place between calls is
+ * correct.  Turning it off drops the cached graphs.  GL_EINVAL on NULL. */
+int gl_graphs_enable(gl_context *ctx, int on);
+
+/* Number of graph replays the context has issued. */
+int64_t gl_graph_launches(const gl_context *ctx);
+
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */
 #define GL_KERNEL_CURVE 1   /* light-curve kernel (FP64 or FP32C) */

@@ -28,7 +28,11 @@ GL_FP32C = 1
 
 EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_lightcurve_batch",
             "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
-            "gl_profile_read", "gl_lightcurve_batch_noalloc")
+            "gl_profile_read", "gl_lightcurve_batch_noalloc", "gl_counts_enable",
+            "gl_counts_read", "gl_graphs_enable", "gl_graph_launches")
+
+COUNT_NAMES = ("exposures", "kept", "in_window", "kepler", "items", "item_kepler", "full",
+               "partial")
 
 GL_NOALLOC_MAX_SETS = 4096
 
@@ -88,6 +92,14 @@ def load():
         lib.gl_sync.restype = i32
         lib.gl_launch_count.argtypes = [vp]
         lib.gl_launch_count.restype = i64
+        lib.gl_counts_enable.argtypes = [vp, i32]
+        lib.gl_counts_enable.restype = i32
+        lib.gl_counts_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
+        lib.gl_counts_read.restype = i32
+        lib.gl_graphs_enable.argtypes = [vp, i32]
+        lib.gl_graphs_enable.restype = i32
+        lib.gl_graph_launches.argtypes = [vp]
+        lib.gl_graph_launches.restype = i64
         lib.gl_lightcurve_batch_noalloc.argtypes = [ctypes.POINTER(_Params),
                                                     ctypes.POINTER(_Times), vp, i32, vp]
         lib.gl_lightcurve_batch_noalloc.restype = i32
@@ -218,6 +230,24 @@ def gl_launch_count(ctx) -> int:
     return load().gl_launch_count(ctx)
 
 
+def gl_counts_enable(ctx, on: bool = True) -> int:
+    return load().gl_counts_enable(ctx, int(bool(on)))
+
+
+def gl_counts_read(ctx) -> dict:
+    buf = (ctypes.c_int64 * len(COUNT_NAMES))()
+    _check(ctx, load().gl_counts_read(ctx, buf, len(COUNT_NAMES)))
+    return dict(zip(COUNT_NAMES, list(buf)))
+
+
+def gl_graphs_enable(ctx, on: bool = True) -> int:
+    return load().gl_graphs_enable(ctx, int(bool(on)))
+
+
+def gl_graph_launches(ctx) -> int:
+    return load().gl_graph_launches(ctx)
+
+
 def gl_profile_enable(ctx, on: bool = True) -> int:
     return load().gl_profile_enable(ctx, int(bool(on)))
 
@@ -263,6 +293,18 @@ class Context:
 
     def last_error(self) -> str:
         return gl_last_error(self.handle)
+
+    def counts(self, on: bool = True):
+        gl_counts_enable(self.handle, on)
+
+    def counts_read(self) -> dict:
+        return gl_counts_read(self.handle)
+
+    def graphs(self, on: bool = True):
+        gl_graphs_enable(self.handle, on)
+
+    def graph_launches(self) -> int:
+        return gl_graph_launches(self.handle)
 
     def profile(self, on: bool = True):
         gl_profile_enable(self.handle, on)

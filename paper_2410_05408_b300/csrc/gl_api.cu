@@ -50,15 +50,41 @@ struct ParamPtrs {
   int32_t nsuper_all;
 };
 
+// Four lanes per set: each computes one FP64 transcendental of the set (sincos w,
+// cbrt(1 - f), cos eta, sincos xi) in parallel, the first lane assembles the
+// constants.  Launched with 32-thread blocks, 8 sets per block.
 __global__ void gl_setup_kernel(ParamPtrs p, int64_t n_sets, const int64_t* offsets,
                                 int64_t n_total, SetConst* sets, int* status) {
-  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_sets) return;
+  const int lane = threadIdx.x & 31, role = lane & 3;
+  const int64_t s = (int64_t)blockIdx.x * 8 + (lane >> 2);
+  const bool live = s < n_sets;
+  double v0 = 0.0, v1 = 1.0;
+  if (live) {
+    if (role == 0) {
+      double w = p.omega[s];
+      if (isfinite(w)) sincos(w, &v0, &v1);
+    } else if (role == 1) {
+      double f = p.f[s];
+      v0 = (isfinite(f) && f < 1.0) ? cbrt(1.0 - f) : 1.0;
+    } else if (role == 2) {
+      double eta = p.eta[s];
+      v0 = isfinite(eta) ? cos(eta) : 1.0;
+    } else {
+      double xi = p.xi[s];
+      if (isfinite(xi)) sincos(xi, &v0, &v1);
+    }
+  }
+  const int base = lane & ~3;
+  double sw = __shfl_sync(0xffffffffu, v0, base), cw = __shfl_sync(0xffffffffu, v1, base);
+  double cb = __shfl_sync(0xffffffffu, v0, base + 1);
+  double ce = __shfl_sync(0xffffffffu, v0, base + 2);
+  double sx = __shfl_sync(0xffffffffu, v0, base + 3), cx = __shfl_sync(0xffffffffu, v1, base + 3);
+  if (!live || role != 0) return;
   int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
   SetConst c;
-  bool ok = gl::set_setup(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], p.omega[s],
-                          p.k[s], p.f[s], p.eta[s], p.xi[s], p.u1[s], p.u2[s], p.exptime[s],
-                          ns, &c);
+  bool ok = gl::set_setup_trig(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], p.omega[s],
+                               p.k[s], p.f[s], p.eta[s], p.xi[s], p.u1[s], p.u2[s],
+                               p.exptime[s], ns, sw, cw, cb, ce, sx, cx, &c);
   sets[s] = c;
   if (!ok) atomicOr(status, kStatusInvalidSet);
   if (offsets) {
@@ -138,6 +164,7 @@ struct LcArgs {
   int64_t n_times, n_sets, n_total;
   double* out;
   unsigned int* tile_counter;
+  unsigned long long* counts;   // instrumented instances: GL_COUNT_* slots
   int n_tiles, tile, cap;
 };
 
@@ -190,7 +217,13 @@ __device__ __forceinline__ int block_scan(int v, int* warp_tot, int* total) {
   return before;
 }
 
-template <typename R, int NT>
+// Warp-aggregated add to a device counter (instrumented instances only).
+__device__ __forceinline__ void count_add(unsigned long long* c, bool pred) {
+  unsigned m = __ballot_sync(__activemask(), pred);
+  if (m && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicAdd(c, (unsigned long long)__popc(m));
+}
+
+template <typename R, int NT, bool COUNT>
 __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int warp_tot[32];
@@ -247,6 +280,10 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
         a.out[j] = 1.0;
       }
     }
+    if (COUNT) {
+      count_add(&a.counts[GL_COUNT_EXPOSURES], tid < tile_sz && j < a.n_total);
+      count_add(&a.counts[GL_COUNT_KEPT], keep != 0);
+    }
     int m;
     int slot = block_scan<NT>(keep, warp_tot, &m);
     if (keep) {
@@ -278,6 +315,10 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
       e_tau[i] = tau;
       e_flag[i] = fl;
       e_acc[i] = 0.0;
+      if (COUNT) {
+        atomicAdd(&a.counts[GL_COUNT_IN_WINDOW], (unsigned long long)!(fl & kExpDead));
+        atomicAdd(&a.counts[GL_COUNT_KEPLER], (unsigned long long)((fl & kExpTaylor) ? 1 : 0));
+      }
     }
     __syncthreads();
 
@@ -300,23 +341,29 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
         it_def[k] = R(0);
         if (e_flag[i] & kExpDead) continue;
         const SetConst& c = a.sets[e_s[i]];
-        const double dt = gl::subexposure_offset(q, e_ns[i], c.exptime);
+        const int twice = 2 * q + 1 - e_ns[i];   // dt = (q + 1/2 - n/2) exptime / n
         R x, y, o;
         int cls;
         if (e_flag[i] & kExpTaylor) {
           float xf, yf, zf, of;
-          gl::taylor_position(e_mid[i], (float)dt, &xf, &yf, &zf, &of);
-          cls = gl::classify_t<float>((float)c.req, xf, yf, zf, 1e-6f);
+          gl::taylor_position(e_mid[i], 0.5f * (float)twice * c.fsub_step, &xf, &yf, &zf, &of);
+          cls = gl::classify_t<float>(c.freq, xf, yf, zf, 1e-6f);
           x = (R)xf;
           y = (R)yf;
           o = (R)of;
         } else {
           double xd, yd, zd;
-          gl::sky_position(c, e_tau[i] + dt, &xd, &yd, &zd);
+          gl::sky_position(c, e_tau[i] + 0.5 * (double)twice * c.sub_step, &xd, &yd, &zd);
           cls = gl::classify(c, xd, yd, zd);
           x = (R)xd;
           y = (R)yd;
           o = (R)((1.0 - xd) * (1.0 + xd) - yd * yd);
+        }
+        if (COUNT) {
+          atomicAdd(&a.counts[GL_COUNT_ITEMS], 1ull);
+          if (!(e_flag[i] & kExpTaylor)) atomicAdd(&a.counts[GL_COUNT_ITEM_KEPLER], 1ull);
+          if (cls == gl::kFull) atomicAdd(&a.counts[GL_COUNT_FULL], 1ull);
+          if (cls == gl::kPartial) atomicAdd(&a.counts[GL_COUNT_PARTIAL], 1ull);
         }
         if (cls == gl::kOut) continue;
         it_pos[3 * k] = x;
@@ -336,7 +383,8 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
         R I[3];
         gl::occulted_r<R>(c, it_pos[3 * k], it_pos[3 * k + 1], it_pos[3 * k + 2],
                           u < nf ? gl::kFull : gl::kPartial, rl, I);
-        it_def[k] = ((R)c.c0 * I[0] + (R)c.c1 * I[1] + (R)c.c2 * I[2]) * (R)c.invF0;
+        it_def[k] = (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
+                     gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
       }
       __syncthreads();
       // ---- phase 5: FP64 accumulation in item order
@@ -448,7 +496,21 @@ struct gl_context {
   int* d_status = nullptr;
   unsigned int* d_counter = nullptr;   // tile counter of the persistent kernel
   int sms = 0;
-  int occ[2] = {0, 0};                 // resident CTAs per SM: FP64, FP32C kernel
+  int occ[4] = {0, 0, 0, 0};           // resident CTAs per SM: FP64, FP32C, counting variants
+  unsigned long long* d_counts = nullptr;   // GL_COUNT_* slots
+  bool counting = false;
+  // graph cache: one captured step per distinct argument set
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  struct GraphEntry {
+    unsigned char key[256];
+    size_t key_len;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+  };
+  std::vector<GraphEntry> graph_cache;
+  uint64_t graph_clock = 0;
+  int64_t graph_launches = 0;
   int64_t launches = 0;
   // per-kernel event timing (gl_profile_enable)
   bool profiling = false;
@@ -490,8 +552,14 @@ bool is_device_ptr(const void* p, int device) {
   return false;
 }
 
+void drop_graphs(gl_context* ctx) {
+  for (auto& g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+  ctx->graph_cache.clear();
+}
+
 int grow(gl_context* ctx, void** buf, size_t* cap, size_t need) {
   if (need <= *cap) return GL_OK;
+  drop_graphs(ctx);   // captured steps hold the old addresses
   if (*buf) cudaFree(*buf);
   *buf = nullptr;
   *cap = 0;
@@ -575,20 +643,21 @@ constexpr int kLcThreads = 256;
 constexpr int kLcTile = 256;
 constexpr int kLcCap = 1024;
 
-template <typename R>
+template <typename R, bool COUNT>
 int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
   LcArgs args = args0;
   args.tile = kLcTile;
   args.cap = kLcCap;
   args.n_tiles = (int)((args.n_total + kLcTile - 1) / kLcTile);
   args.tile_counter = ctx->d_counter;
+  args.counts = ctx->d_counts;
   size_t smem = LcSmem<R>::total(kLcTile, kLcCap);
-  int& occ = ctx->occ[sizeof(R) == 4 ? 1 : 0];
+  int& occ = ctx->occ[(sizeof(R) == 4 ? 1 : 0) + (COUNT ? 2 : 0)];
   if (occ == 0) {
-    GL_CUDA(ctx, cudaFuncSetAttribute(gl_lc_kernel<R, kLcThreads>,
+    GL_CUDA(ctx, cudaFuncSetAttribute(gl_lc_kernel<R, kLcThreads, COUNT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gl_lc_kernel<R, kLcThreads>,
-                                                               kLcThreads, smem));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &occ, gl_lc_kernel<R, kLcThreads, COUNT>, kLcThreads, smem));
     if (occ < 1) return fail(ctx, GL_ECUDA, "light-curve kernel does not fit on an SM");
   }
   int grid = ctx->sms * occ;
@@ -596,10 +665,94 @@ int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
   if (grid < 1) grid = 1;
   GL_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), st));
   long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
-  gl_lc_kernel<R, kLcThreads><<<grid, kLcThreads, smem, st>>>(args);
+  gl_lc_kernel<R, kLcThreads, COUNT><<<grid, kLcThreads, smem, st>>>(args);
   prof_end(ctx, GL_KERNEL_CURVE, pe, st);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+// One light-curve step: per-set constants, then the fused kernel.
+struct StepArgs {
+  ParamPtrs pp;
+  int64_t n_sets;
+  const int64_t* offsets;
+  const double* t;
+  int64_t n_times, n_total;
+  double* out;
+  int prec;
+  SetConst* sets;
+};
+
+int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
+  long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
+  gl_setup_kernel<<<(int)((sa.n_sets + 7) / 8), 32, 0, st>>>(sa.pp, sa.n_sets, sa.offsets,
+                                                              sa.n_total, sa.sets, ctx->d_status);
+  prof_end(ctx, GL_KERNEL_SETUP, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  LcArgs la;
+  memset(&la, 0, sizeof la);
+  la.sets = sa.sets;
+  la.t = sa.t;
+  la.offsets = sa.offsets;
+  la.n_times = sa.n_times;
+  la.n_sets = sa.n_sets;
+  la.n_total = sa.n_total;
+  la.out = sa.out;
+  if (sa.prec == GL_FP64)
+    return ctx->counting ? launch_lc<double, true>(ctx, la, st) : launch_lc<double, false>(ctx, la, st);
+  return ctx->counting ? launch_lc<float, true>(ctx, la, st) : launch_lc<float, false>(ctx, la, st);
+}
+
+// Replay a captured step for these exact arguments, capturing it on first use.
+// Capture happens on the context's private stream; the graph is launched on `st`.
+int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
+  unsigned char key[sizeof(StepArgs)];
+  memcpy(key, &sa, sizeof sa);
+  gl_context::GraphEntry* hit = nullptr;
+  for (auto& g : ctx->graph_cache)
+    if (g.key_len == sizeof key && memcmp(g.key, key, sizeof key) == 0) hit = &g;
+  if (!hit) {
+    // the occupancy query and attribute setting must not happen inside a capture
+    int rc0 = GL_OK;
+    if (sa.prec == GL_FP64 && ctx->occ[0] == 0) rc0 = -1;
+    if (sa.prec != GL_FP64 && ctx->occ[1] == 0) rc0 = -1;
+    if (rc0) return enqueue_step(ctx, sa, st);   // first call: run eagerly, capture next time
+    GL_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int64_t l0 = ctx->launches;
+    int rc = enqueue_step(ctx, sa, ctx->cap_stream);
+    ctx->launches = l0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(ctx, GL_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, GL_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    if (ctx->graph_cache.size() >= 16) {
+      size_t lru = 0;
+      for (size_t i = 1; i < ctx->graph_cache.size(); ++i)
+        if (ctx->graph_cache[i].last_use < ctx->graph_cache[lru].last_use) lru = i;
+      cudaGraphExecDestroy(ctx->graph_cache[lru].exec);
+      ctx->graph_cache.erase(ctx->graph_cache.begin() + lru);
+    }
+    gl_context::GraphEntry ge;
+    memcpy(ge.key, key, sizeof key);
+    ge.key_len = sizeof key;
+    ge.exec = exec;
+    ge.last_use = 0;
+    ctx->graph_cache.push_back(ge);
+    hit = &ctx->graph_cache.back();
+  }
+  hit->last_use = ++ctx->graph_clock;
+  GL_CUDA(ctx, cudaGraphLaunch(hit->exec, st));
+  ctx->launches += 2;
+  ctx->graph_launches++;
   return GL_OK;
 }
 
@@ -623,6 +776,9 @@ int gl_context_create(gl_context** out, int device) {
   if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_counter, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_counts, GL_COUNT_SLOTS * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->d_counts, 0, GL_COUNT_SLOTS * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
@@ -641,6 +797,9 @@ int gl_context_destroy(gl_context* ctx) {
   if (ctx->d_out) cudaFree(ctx->d_out);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
+  if (ctx->d_counts) cudaFree(ctx->d_counts);
+  for (auto& g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (int k = 0; k < GL_KERNEL_KINDS; ++k)
     for (cudaEvent_t e : ctx->ev[k]) cudaEventDestroy(e);
   delete ctx;
@@ -650,6 +809,34 @@ int gl_context_destroy(gl_context* ctx) {
 const char* gl_last_error(const gl_context* ctx) { return ctx ? ctx->err : "no context"; }
 
 int64_t gl_launch_count(const gl_context* ctx) { return ctx ? ctx->launches : 0; }
+
+int gl_counts_enable(gl_context* ctx, int on) {
+  if (!ctx) return GL_EINVAL;
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  GL_CUDA(ctx, cudaMemset(ctx->d_counts, 0, GL_COUNT_SLOTS * sizeof(unsigned long long)));
+  ctx->counting = on != 0;
+  return GL_OK;
+}
+
+int gl_counts_read(gl_context* ctx, int64_t* counts, int n) {
+  if (!ctx || !counts || n < 0) return GL_EINVAL;
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  GL_CUDA(ctx, cudaDeviceSynchronize());
+  unsigned long long h[GL_COUNT_SLOTS];
+  GL_CUDA(ctx, cudaMemcpy(h, ctx->d_counts, sizeof h, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n && i < GL_COUNT_SLOTS; ++i) counts[i] = (int64_t)h[i];
+  for (int i = GL_COUNT_SLOTS; i < n; ++i) counts[i] = 0;
+  return GL_OK;
+}
+
+int gl_graphs_enable(gl_context* ctx, int on) {
+  if (!ctx) return GL_EINVAL;
+  ctx->graphs = on != 0;
+  if (!ctx->graphs) drop_graphs(ctx);
+  return GL_OK;
+}
+
+int64_t gl_graph_launches(const gl_context* ctx) { return ctx ? ctx->graph_launches : 0; }
 
 int gl_profile_enable(gl_context* ctx, int on) {
   if (!ctx) return GL_EINVAL;
@@ -724,8 +911,23 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
   GL_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
 
-  ParamPtrs pp = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
-                  p->eta, p->xi, p->u1, p->u2, tm->exptime, tm->nsuper, tm->nsuper_all};
+  ParamPtrs pp;
+  memset(&pp, 0, sizeof pp);   // the struct's bytes key the graph cache
+  pp.t0 = p->t0;
+  pp.period = p->period;
+  pp.a_rs = p->a_rs;
+  pp.b = p->b;
+  pp.ecc = p->ecc;
+  pp.omega = p->omega;
+  pp.k = p->k;
+  pp.f = p->f;
+  pp.eta = p->eta;
+  pp.xi = p->xi;
+  pp.u1 = p->u1;
+  pp.u2 = p->u2;
+  pp.exptime = tm->exptime;
+  pp.nsuper = tm->nsuper;
+  pp.nsuper_all = tm->nsuper_all;
   const double* t = tm->t;
   const int64_t* offsets = tm->offsets;
   int64_t n_t = offsets ? tm->n_total : tm->n_times;
@@ -752,21 +954,23 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
     if (rc) return rc;
     d_out = ctx->d_out;
   }
-  long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
-  gl_setup_kernel<<<(int)((n_sets + 127) / 128), 128, 0, st>>>(pp, n_sets, offsets, tm->n_total,
-                                                                ctx->d_sets, ctx->d_status);
-  prof_end(ctx, GL_KERNEL_SETUP, pe, st);
-  ctx->launches++;
-  LcArgs la;
-  memset(&la, 0, sizeof la);
-  la.sets = ctx->d_sets;
-  la.t = t;
-  la.offsets = offsets;
-  la.n_times = tm->n_times;
-  la.n_sets = n_sets;
-  la.n_total = tm->n_total;
-  la.out = d_out;
-  rc = (prec == GL_FP64) ? launch_lc<double>(ctx, la, st) : launch_lc<float>(ctx, la, st);
+  StepArgs sa;
+  memset(&sa, 0, sizeof sa);
+  sa.pp = pp;
+  sa.n_sets = n_sets;
+  sa.offsets = offsets;
+  sa.t = t;
+  sa.n_times = tm->n_times;
+  sa.n_total = tm->n_total;
+  sa.out = d_out;
+  sa.prec = (int)prec;
+  sa.sets = ctx->d_sets;
+  bool use_graph = ctx->graphs && !any_host && !out_host && !ctx->profiling && !ctx->counting;
+  if (use_graph) {
+    rc = launch_step_graph(ctx, sa, st);
+  } else {
+    rc = enqueue_step(ctx, sa, st);
+  }
   if (rc) return rc;
   if (out_host) {
     GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, (size_t)tm->n_total * sizeof(double),
@@ -892,8 +1096,8 @@ extern "C" int gl_lightcurve_batch_noalloc(const gl_params* p, const gl_times* t
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GL_ECUDA;
   ParamPtrs pp = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
                   p->eta, p->xi, p->u1, p->u2, tm->exptime, tm->nsuper, tm->nsuper_all};
-  gl_setup_kernel<<<(int)((n_sets + 127) / 128), 128, 0, st>>>(pp, n_sets, tm->offsets,
-                                                                tm->n_total, sets, status);
+  gl_setup_kernel<<<(int)((n_sets + 7) / 8), 32, 0, st>>>(pp, n_sets, tm->offsets,
+                                                          tm->n_total, sets, status);
   int grid = launch_grid(tm->n_total, 256);
   if (prec == GL_FP64)
     gl_curve_kernel<double><<<grid, 256, 0, st>>>(sets, tm->t, tm->offsets, tm->n_times, n_sets,

@@ -39,7 +39,7 @@ struct SetConst {
   double t0, period, nmean;        // days, days, 2 pi / P
   double a_rs, ecc, b_orb;         // a, e, a sqrt(1 - e^2)
   double cosw, sinw, cosi, sini;
-  double cosEc, sinEc, Mc, rc;     // eccentric anomaly, mean anomaly, radius at conjunction
+  double cosEc, sinEc, rc;         // eccentric anomaly and radius at conjunction
   double tau_lo, tau_hi;           // window of (t - t0) wrapped to [-P/2, P/2) outside
                                    // of which the planet cannot overlap the star
   // projected ellipse x = x0 + dx cos th, y = y0 + dy1 cos th + dy2 sin th
@@ -48,6 +48,10 @@ struct SetConst {
   double c0, c1, c2, invF0;
   double exptime;
   double invP;                     // 1 / P
+  double W0;                       // dx dy2
+  double sub_step;                 // exptime / nsuper
+  // FP32 copies of the shape and LD constants for the FP32C quadrature
+  float fdx, fdy1, fdy2, freq, fW0, fc0, fc1, fc2, finvF0, fsub_step;
   // conservative FP32 window for the per-exposure test (see window_maybe)
   float t0f, Pf, invPf, wlo_f, whi_f, slack_f;
   int nsuper;
@@ -95,7 +99,7 @@ template <> GL_HD void sincos_<double>(double x, double* s, double* c) {
 }
 template <> GL_HD void sincos_<float>(float x, float* s, float* c) {
 #if defined(__CUDA_ARCH__)
-  __sincosf(x, s, c);   // |x| <= pi here
+  sincosf(x, s, c);   // |x| <= pi here: the accurate version stays on its fast path
 #else
   *s = ::sinf(x);
   *c = ::cosf(x);
@@ -114,10 +118,41 @@ struct CSum {
   GL_HD R value() const { return s + c; }
 };
 
+// The double or the float copy of a constant, by quadrature precision.
+template <typename R> GL_HD R pick(double d, float f);
+template <> GL_HD double pick<double>(double d, float) { return d; }
+template <> GL_HD float pick<float>(double, float f) { return f; }
+
+// Reciprocal: hardware approximation refined by Newton steps (full precision
+// after two; used where a divide would cost a long FP64 sequence).
+GL_HD double rcp64(double x) {
+#if defined(__CUDA_ARCH__)
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return r;
+#else
+  return 1.0 / x;
+#endif
+}
+
 // sin(d) and cos(d) - 1 for the Kepler update.  Small |d|: Taylor series in d^2
 // (coefficients 1/n!, truncation below 1e-21 for |d| < 1/4); otherwise sincos.
 GL_HD void sin_cosm1(double d, double* sd, double* cm1) {
-  if (fabs(d) < 0.25) {
+  if (fabs(d) < 0.02) {
+    // truncation below 1e-26 for |d| < 0.02
+    double d2 = d * d;
+    double s = -1.0 / 5040.0;
+    s = s * d2 + 1.0 / 120.0;
+    s = s * d2 - 1.0 / 6.0;
+    *sd = d + d * d2 * s;
+    double c = 1.0 / 40320.0;
+    c = c * d2 - 1.0 / 720.0;
+    c = c * d2 + 1.0 / 24.0;
+    c = c * d2 - 0.5;
+    *cm1 = d2 * c;
+  } else if (fabs(d) < 0.25) {
     double d2 = d * d;
     double s = 1.0 / 6227020800.0;
     s = s * d2 - 1.0 / 39916800.0;
@@ -148,11 +183,14 @@ GL_HD double ecc_anomaly_from_true(double nu, double e) {
   return 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * nu), sqrt(1.0 + e) * cos(0.5 * nu));
 }
 
-// Parameters of one set -> constants.  Returns false (and sets kSetInvalid) when
-// the set is physically invalid.
-GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc,
-                     double omega, double k, double f, double eta, double xi, double u1,
-                     double u2, double exptime, int nsuper, SetConst* c) {
+// Parameters of one set -> constants, given the four transcendentals of the
+// set (so that a caller can compute them in parallel): sin w, cos w,
+// cbrt(1 - f), cos eta, sin xi, cos xi.  Returns false (and sets kSetInvalid)
+// when the set is physically invalid.
+GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, double ecc,
+                          double omega, double k, double f, double eta, double xi, double u1,
+                          double u2, double exptime, int nsuper, double sinw, double cosw,
+                          double cbrt1mf, double ce, double sx, double cx, SetConst* c) {
   c->flags = 0;
   c->t0 = t0;
   c->period = period;
@@ -163,14 +201,9 @@ GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc
             isfinite(eta) && isfinite(xi) && isfinite(u1) && isfinite(u2) &&
             isfinite(exptime) && period > 0.0 && a_rs > 0.0 && ecc >= 0.0 && ecc < 1.0 &&
             k > 0.0 && f >= 0.0 && f < 1.0 && exptime >= 0.0 && nsuper >= 1;
-  double F0 = kPi * (1.0 - u1 / 3.0 - u2 / 6.0);
+  double F0 = kPi * (1.0 - u1 * (1.0 / 3.0) - u2 * (1.0 / 6.0));
   ok = ok && F0 > 0.0;
-  double sinw = 0.0, cosw = 1.0;
-  if (ok) {
-    sinw = sin(omega);
-    cosw = cos(omega);
-  }
-  double cosi = ok ? b * (1.0 + ecc * sinw) / (a_rs * (1.0 - ecc * ecc)) : 0.0;
+  double cosi = ok ? b * (1.0 + ecc * sinw) * rcp64(a_rs * (1.0 - ecc) * (1.0 + ecc)) : 0.0;
   ok = ok && fabs(cosi) <= 1.0;
   if (!ok) {
     c->flags = kSetInvalid;
@@ -181,60 +214,88 @@ GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc
   //    -cos eta sin xi, sin eta)).  The sky covariance S = R^T diag(a^2,b^2,c^2) R
   //    restricted to (x, y) is R_eq^2 I - (R_eq^2 - R_pol^2) n_xy n_xy^T, and
   //    (dx, dy1, dy2) of Eqs. dx, dy1, dy2 are its Cholesky factor.
-  double req = k / cbrt(1.0 - f);
-  double ce = cos(eta), cx = cos(xi), sx = sin(xi);
+  double req = k * rcp64(cbrt1mf);
   double delta = req * req * f * (2.0 - f) * ce * ce;   // R_eq^2 - R_pol^2 times cos^2 eta
   double sxx = req * req - delta * cx * cx;
   double sxy = delta * cx * sx;
   double dx = sqrt(sxx);
+  double idx = rcp64(dx);
   c->dx = dx;
-  c->dy1 = sxy / dx;
-  c->dy2 = req * sqrt(req * req - delta) / dx;
+  c->dy1 = sxy * idx;
+  c->dy2 = req * sqrt(req * req - delta) * idx;
   c->req = req;
   // -- limb darkening in the basis (1, mu, r^2)
   c->c0 = 1.0 - u1 - 2.0 * u2;
   c->c1 = u1 + 2.0 * u2;
   c->c2 = u2;
-  c->invF0 = 1.0 / F0;
-  // -- orbit
-  c->nmean = 2.0 * kPi / period;
+  c->invF0 = rcp64(F0);
+  // -- orbit.  At conjunction nu_c = pi/2 - w: cos nu_c = sin w, sin nu_c = cos w,
+  //    and cos E = (e + cos nu)/(1 + e cos nu), sin E = sqrt(1-e^2) sin nu/(1 + e cos nu),
+  //    r = a (1 - e^2)/(1 + e cos nu).
+  c->invP = rcp64(period);
+  c->nmean = 2.0 * kPi * c->invP;
   c->a_rs = a_rs;
   c->ecc = ecc;
-  c->b_orb = a_rs * sqrt(1.0 - ecc * ecc);
+  double se = sqrt((1.0 - ecc) * (1.0 + ecc));
+  c->b_orb = a_rs * se;
   c->cosw = cosw;
   c->sinw = sinw;
   c->cosi = cosi;
-  c->sini = sqrt(fmax(0.0, 1.0 - cosi * cosi));
+  c->sini = sqrt(fmax(0.0, (1.0 - cosi) * (1.0 + cosi)));
+  double iden = rcp64(1.0 + ecc * sinw);
+  c->cosEc = (ecc + sinw) * iden;
+  c->sinEc = se * cosw * iden;
+  c->rc = a_rs * (1.0 - ecc) * (1.0 + ecc) * iden;
   double nuc = 0.5 * kPi - omega;
-  double Ec = ecc_anomaly_from_true(nuc, ecc);
-  c->cosEc = cos(Ec);
-  c->sinEc = sin(Ec);
-  c->Mc = Ec - ecc * c->sinEc;
-  c->rc = a_rs * (1.0 - ecc * c->cosEc);
   // -- window: the sky separation is at least r |sin phi| >= a (1-e) |sin phi|,
   //    phi = angle from conjunction along the orbit; behind the star (|phi| > pi/2)
-  //    nothing is occulted.  Outside |phi| <= phi_w the flux is exactly 1.
+  //    nothing is occulted.  Outside |phi| <= phi_w the flux is exactly 1.  The
+  //    window only has to contain every overlapping time, so it is computed in
+  //    FP32 and widened by a relative 1e-4 plus an absolute 1e-4 days, far more
+  //    than the FP32 rounding of these few operations.
   double smax = 1.0 + req * (1.0 + 1e-9) + 1e-9;
   double rmin = a_rs * (1.0 - ecc);
-  if (smax >= rmin * (1.0 - 1e-12)) {
+  if (smax >= rmin * (1.0 - 1e-4)) {
     c->flags |= kSetWholeOrbit;
     c->tau_lo = -period;
     c->tau_hi = period;
   } else {
-    double phw = asin(smax / rmin);
-    double taus[2];
+    // The mean anomaly is a continuous increasing function of the unwrapped true
+    // anomaly; across the window it may change by more than pi (eccentric orbits
+    // with conjunction near apoapsis), so no wrapping is applied.
+    float phw = asinf((float)(smax / rmin)) * 1.0001f;
+    float ef = (float)ecc;
+    float nucf = (float)remainder(nuc, 2.0 * kPi);
+    float sq1 = sqrtf(1.0f - ef), sq2 = sqrtf(1.0f + ef);
+    auto mean_anomaly = [&](float nu) {
+      float turns = rintf(nu * 0.15915494309189535f);
+      float nu0 = nu - 6.283185307179586f * turns;
+      float E = 2.0f * atan2f(sq1 * sinf(0.5f * nu0), sq2 * cosf(0.5f * nu0)) +
+                6.283185307179586f * turns;
+      return E - ef * sinf(E);
+    };
+    float Mcf = mean_anomaly(nucf);
+    float taus[2];
     for (int sgn = 0; sgn < 2; ++sgn) {
-      double nu = nuc + (sgn ? phw : -phw);
-      double E = ecc_anomaly_from_true(nu, ecc);
-      double M = E - ecc * sin(E);
-      double dM = remainder(M - c->Mc, 2.0 * kPi);
-      taus[sgn] = dM / c->nmean;
+      float dM = mean_anomaly(nucf + (sgn ? phw : -phw)) - Mcf;
+      taus[sgn] = dM / (float)c->nmean;
     }
-    double margin = 1e-9 * period + 1e-12;
-    c->tau_lo = fmin(taus[0], 0.0) - margin;
-    c->tau_hi = fmax(taus[1], 0.0) + margin;
+    double margin = 1e-4 * (fabs((double)taus[0]) + fabs((double)taus[1])) + 1e-4;
+    c->tau_lo = fmin((double)taus[0], 0.0) - margin;
+    c->tau_hi = fmax((double)taus[1], 0.0) + margin;
   }
-  c->invP = 1.0 / period;
+  c->W0 = c->dx * c->dy2;
+  c->sub_step = exptime / nsuper;
+  c->fdx = (float)c->dx;
+  c->fdy1 = (float)c->dy1;
+  c->fdy2 = (float)c->dy2;
+  c->freq = (float)req;
+  c->fW0 = (float)c->W0;
+  c->fc0 = (float)c->c0;
+  c->fc1 = (float)c->c1;
+  c->fc2 = (float)c->c2;
+  c->finvF0 = (float)c->invF0;
+  c->fsub_step = (float)c->sub_step;
   // FP32 copy of the window for the per-exposure test, widened for rounding:
   // every FP32 operation of window_maybe errs by at most 2^-24 of its operands.
   c->t0f = (float)t0;
@@ -255,6 +316,18 @@ GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc
     if (bound <= 1e-10) c->flags |= kSetTaylor;
   }
   return true;
+}
+
+GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc,
+                     double omega, double k, double f, double eta, double xi, double u1,
+                     double u2, double exptime, int nsuper, SetConst* c) {
+  double sw = 0.0, cw = 1.0, sx = 0.0, cx = 1.0, ce = 1.0, cb = 1.0;
+  if (isfinite(omega)) sincos_<double>(omega, &sw, &cw);
+  if (isfinite(xi)) sincos_<double>(xi, &sx, &cx);
+  if (isfinite(eta)) ce = cos(eta);
+  if (isfinite(f) && f < 1.0) cb = cbrt(1.0 - f);
+  return set_setup_trig(t0, period, a_rs, b, ecc, omega, k, f, eta, xi, u1, u2, exptime, nsuper,
+                        sw, cw, cb, ce, sx, cx, c);
 }
 
 // (t - t0) wrapped to one period around the conjunction.
@@ -289,14 +362,16 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
   double nt = c.nmean * tau;
   double e = c.ecc;
   double ec = e * c.cosEc, es = e * c.sinEc;
-  double d = nt / (1.0 - ec);
+  double ir1 = rcp64(1.0 - ec);
+  double d = nt * ir1;
+  d -= 0.5 * es * d * d * ir1;   // second-order start: F ~ d (1 - ec) + es d^2 / 2 - n tau
   double sd, cm1;
   bool conv = false;
   for (int it = 0; it < 12; ++it) {
     sin_cosm1(d, &sd, &cm1);
     double F = d - ec * sd - es * cm1 - nt;
     double Fp = 1.0 - ec * (1.0 + cm1) + es * sd;
-    double step = F / Fp;
+    double step = F * rcp64(Fp);
     d -= step;
     if (fabs(step) <= 1e-16 * (1.0 + fabs(d))) {
       conv = true;
@@ -304,8 +379,8 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
     }
   }
   if (!conv) {
-    double M = c.Mc + nt;
     double Ec = atan2(c.sinEc, c.cosEc);
+    double M = Ec - e * c.sinEc + nt;
     double lo = M - e - Ec, hi = M + e - Ec;
     for (int it = 0; it < 200 && hi - lo > 1e-16 * (1.0 + fabs(lo)); ++it) {
       double mid = 0.5 * (lo + hi);
@@ -356,10 +431,11 @@ GL_HD void sky_state(const SetConst& c, double tau, SkyState* s) {
   double cosE = c.cosEc + dcosE, sinE = c.sinEc + dsinE;
   double X = c.a_rs * (cosE - c.ecc), Y = c.b_orb * sinE;
   double r = c.a_rs * (1.0 - c.ecc * cosE);
-  double Ed = c.nmean * c.a_rs / r;                 // dE/dt
+  double ir = rcp64(r);
+  double Ed = c.nmean * c.a_rs * ir;                // dE/dt
   double Xd = -c.a_rs * sinE * Ed, Yd = c.b_orb * cosE * Ed;
   double mu = c.nmean * c.nmean * c.a_rs * c.a_rs * c.a_rs;
-  double ir2 = 1.0 / (r * r), ir3 = ir2 / r;
+  double ir2 = ir * ir, ir3 = ir2 * ir;
   double rv = X * Xd + Y * Yd;
   double Xa = -mu * X * ir3, Ya = -mu * Y * ir3;
   double Xj = -mu * (Xd * ir3 - 3.0 * X * rv * ir3 * ir2);
@@ -429,10 +505,10 @@ GL_HD Geo<R> make_geo(const SetConst& c, R x0, R y0, R omr2) {
   g.x0 = x0;
   g.y0 = y0;
   g.omr2 = omr2;
-  g.dx = (R)c.dx;
-  g.dy1 = (R)c.dy1;
-  g.dy2 = (R)c.dy2;
-  g.W0 = (R)(c.dx * c.dy2);
+  g.dx = pick<R>(c.dx, c.fdx);
+  g.dy1 = pick<R>(c.dy1, c.fdy1);
+  g.dy2 = pick<R>(c.dy2, c.fdy2);
+  g.W0 = pick<R>(c.W0, c.fW0);
   g.Wc = x0 * g.dy2;
   g.Ws = y0 * g.dx - x0 * g.dy1;
   return g;
@@ -442,8 +518,7 @@ GL_HD Geo<R> make_geo(const SetConst& c, R x0, R y0, R omr2) {
 // (1 + mu + mu^2) / (3 (1 + mu)), mu = sqrt(1 - r^2).
 template <typename R>
 GL_HD R lin_kernel(R omr2) {
-  R q = omr2 > (R)1e-30 ? omr2 : (R)1e-30;
-  R mu = q * rsqrt_<R>(q);
+  R mu = m_sqrt(omr2 > R(0) ? omr2 : R(0));
   return (R(1) + mu + mu * mu) * rcp_<R>(R(3) + R(3) * mu);
 }
 
@@ -494,7 +569,7 @@ struct Trig2 {
 // omr2 = 1 - x0^2 - y0^2.
 template <typename T>
 GL_HD Trig2<T> limb_poly(const SetConst& c, T x0, T y0, T omr2) {
-  T dx = (T)c.dx, dy1 = (T)c.dy1, dy2 = (T)c.dy2;
+  T dx = pick<T>(c.dx, c.fdx), dy1 = pick<T>(c.dy1, c.fdy1), dy2 = pick<T>(c.dy2, c.fdy2);
   Trig2<T> t;
   t.A = -omr2 + T(0.5) * (dx * dx + dy1 * dy1 + dy2 * dy2);
   t.B = T(2) * (x0 * dx + y0 * dy1);
@@ -650,8 +725,9 @@ struct Frame {
   T q[5];        // q0..q4
 };
 
+// Index k of the sampled angle k pi/4 where |g| is largest.
 template <typename T>
-GL_HD Frame<T> make_frame(const Trig2<T>& t) {
+GL_HD int frame_choice(const Trig2<T>& t) {
   const T r2 = T(0.70710678118654752440);
   const T cs8[8] = {T(1), r2, T(0), -r2, T(-1), -r2, T(0), r2};
   const T sn8[8] = {T(0), r2, T(1), r2, T(0), -r2, T(-1), -r2};
@@ -666,6 +742,15 @@ GL_HD Frame<T> make_frame(const Trig2<T>& t) {
       kbest = kk;
     }
   }
+  return kbest;
+}
+
+// The frame whose t = infinity falls on the sampled angle k pi/4.
+template <typename T>
+GL_HD Frame<T> make_frame_k(const Trig2<T>& t, int kbest) {
+  const T r2 = T(0.70710678118654752440);
+  const T cs8[8] = {T(1), r2, T(0), -r2, T(-1), -r2, T(0), r2};
+  const T sn8[8] = {T(0), r2, T(1), r2, T(0), -r2, T(-1), -r2};
   Frame<T> f;
   f.cd = -cs8[kbest];
   f.sd = -sn8[kbest];
@@ -678,6 +763,11 @@ GL_HD Frame<T> make_frame(const Trig2<T>& t) {
   f.q[1] = T(2) * Cp + T(4) * Ep;
   f.q[0] = t.A + Bp + Dp;
   return f;
+}
+
+template <typename T>
+GL_HD Frame<T> make_frame(const Trig2<T>& t) {
+  return make_frame_k<T>(t, frame_choice<T>(t));
 }
 
 template <typename T>
@@ -712,36 +802,40 @@ GL_HD int frame_roots(const Frame<T>& f, T* tr) {
   return drop_pairs<T>(tr, nr, T(1024) * m_eps<T>());
 }
 
-// Crossings of the boundary with the limb, in FP64.  R = double: FP64 Ferrari.
-// R = float: FP32 Ferrari estimates polished by FP64 Newton on the FP64
-// quartic; if the polish does not converge, two roots merge or the count is
-// odd, the FP64 Ferrari result is used instead.
+// Crossings of the boundary with the limb, in FP64 (frame f; fr is the same
+// frame in precision R).  R = double: FP64 Ferrari.  R = float: FP32 Ferrari
+// estimates, each polished by FP64 Newton steps on the FP64 quartic; if a
+// polish does not converge, two roots merge or the count is odd, the FP64
+// Ferrari result is used instead.
 template <typename R>
-GL_HD int crossing_roots(const Frame<double>& f, double* tr);
+GL_HD int crossing_roots(const Frame<double>& f, const Frame<R>& fr, double* tr);
 
 template <>
-GL_HD int crossing_roots<double>(const Frame<double>& f, double* tr) {
+GL_HD int crossing_roots<double>(const Frame<double>& f, const Frame<double>&, double* tr) {
   return frame_roots<double>(f, tr);
 }
 
 template <>
-GL_HD int crossing_roots<float>(const Frame<double>& f, double* tr) {
-  if (!(fabs(f.q[4]) > 0.0)) return 0;
-  double inv = 1.0 / f.q[4];
-  double a = f.q[3] * inv, b = f.q[2] * inv, c = f.q[1] * inv, d = f.q[0] * inv;
+GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, double* tr) {
+  if (!(fabsf(fr.q[4]) > 0.0f)) return frame_roots<double>(f, tr);
+  float inv = 1.0f / fr.q[4];
   float xs[4];
-  int nr = quartic_real_roots<float>((float)a, (float)b, (float)c, (float)d, xs);
+  int nr = quartic_real_roots<float>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv, fr.q[0] * inv,
+                                     xs);
   bool ok = (nr % 2) == 0;
   for (int i = 0; i < nr && ok; ++i) {
+    // Newton steps with the derivative frozen at the FP32 estimate: each step
+    // shrinks the error by ~|1 - P'(t*)/P'(t0)|, i.e. to FP32 rounding squared
     double t = (double)xs[i];
+    double fp = ((4.0 * f.q[4] * t + 3.0 * f.q[3]) * t + 2.0 * f.q[2]) * t + f.q[1];
+    double r = rcp64(fp);
     bool conv = false;
-    for (int it = 0; it < 6; ++it) {
-      double fv = (((t + a) * t + b) * t + c) * t + d;
-      double fp = ((4.0 * t + 3.0 * a) * t + 2.0 * b) * t + c;
-      if (fp == 0.0) break;
-      double step = fv / fp;
+    for (int it = 0; it < 4; ++it) {
+      double fv = (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
+      double step = fv * r;
+      if (!isfinite(step)) break;
       t -= step;
-      if (fabs(step) <= 1e-15 * (1.0 + fabs(t))) {
+      if (fabs(step) <= 1e-9 * (1.0 + fabs(t))) {
         conv = true;
         break;
       }
@@ -891,9 +985,11 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
   if (cls == kPartial) {
     double xd = (double)x0, yd = (double)y0;
     Trig2<double> tgd = limb_poly<double>(c, xd, yd, (1.0 - xd) * (1.0 + xd) - yd * yd);
-    Frame<double> fr = make_frame<double>(tgd);
+    int kb = frame_choice<R>(tg);
+    Frame<double> fr = make_frame_k<double>(tgd, kb);
+    Frame<R> frr = make_frame_k<R>(tg, kb);
     double tb[8];
-    int nr = crossing_roots<R>(fr, tb);
+    int nr = crossing_roots<R>(fr, frr, tb);
     if (nr == 0) {
       if (!(fr.q[4] < 0.0)) {
         // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
@@ -912,8 +1008,9 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
       for (int i = 0; i < nr; ++i) kind[i] = 1;
       int nb = nr;
       for (int i = 0; i < nmax; ++i) {
-        double tv = frame_t<double>(fr, (double)cmx[i], (double)smx[i]);
-        if (!isfinite(tv)) continue;
+        R tvr = frame_t<R>(frr, cmx[i], smx[i]);
+        if (!m_finite(tvr)) continue;
+        double tv = (double)tvr;
         int j = nb - 1;
         while (j >= 0 && tb[j] > tv) {
           tb[j + 1] = tb[j];
@@ -925,11 +1022,10 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
         ++nb;
       }
       R cth[8], sth[8], px[8], py[8];
+      R tr_[8];
       for (int i = 0; i < nb; ++i) {
-        double ctd, std_;
-        frame_angle<double>(fr, tb[i], &ctd, &std_);
-        cth[i] = (R)ctd;
-        sth[i] = (R)std_;
+        tr_[i] = (R)tb[i];
+        frame_angle<R>(frr, tr_[i], &cth[i], &sth[i]);
         R qx = g.x0 + g.dx * cth[i];
         R qy = g.y0 + g.dy1 * cth[i] + g.dy2 * sth[i];
         R nrm = rsqrt_<R>(qx * qx + qy * qy);
@@ -942,8 +1038,8 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
         int ip = (i + 1 == nb) ? 0 : i + 1;
         bool wrap = (i + 1 == nb);
         R h, cm, sm;
-        frame_arc<R>((R)(tb[ip] - tb[i]), (R)(1.0 + tb[i] * tb[ip]), wrap, cth[i], sth[i], &h,
-                     &cm, &sm);
+        frame_arc<R>(tr_[ip] - tr_[i], R(1) + tr_[i] * tr_[ip], wrap, cth[i], sth[i], &h, &cm,
+                     &sm);
         if (nb == 1) {   // a lone breakpoint: the arc is the full turn
           h = R(kPi);
           cm = -cth[i];
@@ -1065,11 +1161,11 @@ GL_HD void taylor_position(const MidState& m, float dt, float* x, float* y, floa
 // Deficit (1 - flux) of one sub-exposure at the given FP32 geometry.
 GL_HD float deficit_f32(const SetConst& c, float x, float y, float z, float omr2,
                         const NodeRule<float>& rule) {
-  int cls = classify_t<float>((float)c.req, x, y, z, 1e-6f);
+  int cls = classify_t<float>(c.freq, x, y, z, 1e-6f);
   if (cls == kOut) return 0.0f;
   float I[3];
   occulted_r<float>(c, x, y, omr2, cls, rule, I);
-  return ((float)c.c0 * I[0] + (float)c.c1 * I[1] + (float)c.c2 * I[2]) * (float)c.invF0;
+  return (c.fc0 * I[0] + c.fc1 * I[1] + c.fc2 * I[2]) * c.finvF0;
 }
 
 // Sub-exposure time offset: ((q + 1/2)/n - 1/2) * exptime.

@@ -165,3 +165,22 @@ def geometry_sample(n: int, seed: int = 10, k_range=(0.01, 0.2), f_max: float = 
                 k=k, f=f, eta=rng.uniform(0.0, 90.0 * DEG, n),
                 xi=rng.uniform(0.0, 180.0 * DEG, n), q1=rng.uniform(0, 1, n),
                 q2=rng.uniform(0, 1, n))
+
+
+def extreme_orbits(n_sets: int = 48, n_times: int = 3000, seed: int = 11) -> dict:
+    """Short-period, eccentric, close-in orbits with long exposures: P U[0.5, 3.5] d,
+    a/R* U[2.5, 10.5], e U[0, 0.8], b U[0, 0.45], k U[0.02, 0.22], exposure
+    U[0.01, 0.11] d x 7; 3000 shared times every 0.0021 d around t0.  They exercise
+    transit windows that cover the whole orbit, several transits per curve and
+    exposures too long for a low-order time expansion of the orbit."""
+    rng = _rng(seed)
+    p = dict(
+        t0=rng.uniform(-0.2, 0.2, n_sets), period=rng.uniform(0.5, 3.5, n_sets),
+        a_rs=rng.uniform(2.5, 10.5, n_sets), b=rng.uniform(0.0, 0.45, n_sets),
+        ecc=rng.uniform(0.0, 0.8, n_sets), omega=rng.uniform(0.0, 2.0 * np.pi, n_sets),
+        k=rng.uniform(0.02, 0.22, n_sets), f=rng.uniform(0.0, 0.9, n_sets),
+        eta=rng.uniform(0.0, 90.0 * DEG, n_sets), xi=rng.uniform(0.0, 180.0 * DEG, n_sets),
+        q1=rng.uniform(0.0, 1.0, n_sets), q2=rng.uniform(0.0, 1.0, n_sets))
+    t = (np.arange(n_times) - 0.5 * (n_times - 1)) * 0.0021
+    return dict(params=p, t=t, offsets=None, exptime=rng.uniform(0.01, 0.11, n_sets),
+                nsuper=7)

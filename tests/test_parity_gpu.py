@@ -138,6 +138,23 @@ def test_uneven_batch_full_size_sampled(ctx, uneven, prec):
     assert np.all(np.isfinite(got))
 
 
+# ---------------------------------------------------------------- extreme orbits
+@pytest.fixture(scope="module")
+def extreme():
+    import oracle
+    wl = inputs.extreme_orbits()
+    ref = oracle.lightcurve(oracle_params(wl), wl["t"], wl["exptime"], wl["nsuper"])
+    return wl, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_extreme_orbits(ctx, extreme, prec):
+    wl, ref = extreme
+    got = _run(ctx, wl, prec).reshape(ref.shape)
+    assert np.mean(ref < 1.0) > 0.05      # several transits per curve
+    _compare(got.ravel(), ref.ravel(), prec)
+
+
 # ---------------------------------------------------------------- geometry level
 @pytest.fixture(scope="module")
 def geometry():
@@ -233,6 +250,42 @@ def test_bad_arguments_are_rejected(ctx):
         ctx.lightcurve(bad, wl["t"], out, np.array([0.02]), nsuper_all=3)
     with pytest.raises(binding.GLError):
         ctx.lightcurve(p, wl["t"], np.empty(999), np.array([0.02]), nsuper_all=3)
+
+
+def test_graph_replay_matches_eager_and_follows_in_place_updates(ctx):
+    wl = inputs.mcmc_batch(n_sets=32, n_times=400, seed=21)
+    p = product_params(wl)
+    dp = {k: _dev(v) for k, v in p.items()}
+    t, exp = _dev(wl["t"]), _dev(wl["exptime"][:32])
+    outs = [torch.empty(32 * 400, dtype=torch.float64, device="cuda") for _ in range(4)]
+    g0 = ctx.graph_launches()
+    for o in outs[:3]:                      # first eager, then captured and replayed
+        ctx.lightcurve(dp, t, o, exp, nsuper_all=15, precision=binding.GL_FP32C)
+    torch.cuda.synchronize()
+    assert ctx.graph_launches() > g0
+    assert torch.equal(outs[0], outs[2])
+    dp["k"].mul_(1.1)                       # update a parameter in place
+    ctx.lightcurve(dp, t, outs[3], exp, nsuper_all=15, precision=binding.GL_FP32C)
+    ctx.graphs(False)
+    eager = torch.empty_like(outs[3])
+    ctx.lightcurve(dp, t, eager, exp, nsuper_all=15, precision=binding.GL_FP32C)
+    ctx.graphs(True)
+    torch.cuda.synchronize()
+    assert not torch.equal(outs[3], outs[0])
+    assert torch.equal(outs[3], eager)
+
+
+def test_workload_counts(ctx):
+    wl = inputs.single_transit()
+    ctx.counts(True)
+    _run(ctx, wl, binding.GL_FP32C)
+    c = ctx.counts_read()
+    ctx.counts(False)
+    assert c["exposures"] == 1000
+    assert c["kept"] >= c["in_window"] > 0
+    assert c["items"] == 15 * c["kept"]
+    assert c["full"] + c["partial"] <= c["items"]
+    assert c["partial"] > 0 and c["full"] > c["partial"]
 
 
 def test_launches_are_counted(ctx):
