@@ -344,6 +344,13 @@ def main():
             ctx.profile(False)
         return ms, ctx.launches() - l0, kern
 
+    # autotuner: kernel shape and FP32 quadrature order for this batch (untimed)
+    tune = ctx.autotune(dp, d_t, out32, d_exp, nsuper=d_ns, offsets=d_off,
+                        precision=binding.GL_FP32C, stream=stream)
+    step(out32, binding.GL_FP32C)
+    torch.cuda.synchronize(dev)
+    max_dflux = float((out32 - out64).abs().max().item())
+
     # workload counts of one FP32C step (instrumented kernel instance, untimed)
     ctx.counts(True)
     step(out32, binding.GL_FP32C)
@@ -409,6 +416,7 @@ def main():
         "kernel_ms": {"curve_fp32c": kern32.get("curve"), "setup": kern32.get("setup"),
                       "curve_fp64": kern64.get("curve")},
         "workload_counts": counts,
+        "autotune": tune,
         "roofline": roofline(counts, kern32["curve"], fp32_peak, fp64_peak),
         "gpu_launches": launches,
         "status": status,

@@ -195,6 +195,32 @@ int gl_graphs_enable(gl_context *ctx, int on);
 /* Number of graph replays the context has issued. */
 int64_t gl_graph_launches(const gl_context *ctx);
 
+/* Result of gl_autotune. */
+typedef struct {
+  int threads;         /* threads per CTA of the light-curve kernel */
+  int tile;            /* exposures per tile */
+  int nodes;           /* Gauss-Legendre nodes per arc */
+  double ms;           /* best step time (ms, CUDA events, warm) */
+  double default_ms;   /* step time of the default configuration, 0 if inadmissible */
+  double max_abs_err;  /* max |flux - FP64 path| of the chosen configuration */
+  int candidates;      /* configurations tried */
+  int admissible;      /* configurations within 0.9 x tolerance of the FP64 path */
+} gl_tune_report;
+
+/* Autotuner of the light-curve kernel for the batch (p, t) at precision prec.
+ * Candidates: 128 or 256 threads per CTA (tile = threads, 4 x threads items per
+ * round) and, for GL_FP32C, 16, 20, 24 or 28 Gauss-Legendre nodes per arc.  Each
+ * candidate runs on the batch; only those whose max |flux - FP64 path| stays
+ * within 0.9 x the precision's tolerance (1e-7 FP32C, 1e-10 FP64) are timed (CUDA
+ * events, best of 3) and the fastest is kept by the context for later calls at
+ * that precision.  `out` (device memory, n_total doubles) receives the chosen
+ * configuration's last result; the context holds one FP64 reference of n_total
+ * doubles.  Synchronises `stream`; must not be called during stream capture.
+ * `rep` may be NULL.  GL_EINVAL for host buffers or an empty batch, GL_ENUMERIC
+ * if no candidate meets the tolerance (the previous configuration stays). */
+int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *out,
+                gl_precision prec, void *stream, gl_tune_report *rep);
+
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */
 #define GL_KERNEL_CURVE 1   /* light-curve kernel (FP64 or FP32C) */

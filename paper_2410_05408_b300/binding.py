@@ -29,7 +29,7 @@ GL_FP32C = 1
 EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_lightcurve_batch",
             "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
             "gl_profile_read", "gl_lightcurve_batch_noalloc", "gl_counts_enable",
-            "gl_counts_read", "gl_graphs_enable", "gl_graph_launches")
+            "gl_counts_read", "gl_graphs_enable", "gl_graph_launches", "gl_autotune")
 
 COUNT_NAMES = ("exposures", "kept", "in_window", "kepler", "items", "item_kepler", "full",
                "partial")
@@ -51,6 +51,13 @@ class GLError(RuntimeError):
 
 class _Params(ctypes.Structure):
     _fields_ = [("n_sets", ctypes.c_int64)] + [(n, ctypes.c_void_p) for n in PARAM_NAMES]
+
+
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("tile", ctypes.c_int), ("nodes", ctypes.c_int),
+                ("ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("max_abs_err", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("admissible", ctypes.c_int)]
 
 
 class _Times(ctypes.Structure):
@@ -92,6 +99,9 @@ def load():
         lib.gl_sync.restype = i32
         lib.gl_launch_count.argtypes = [vp]
         lib.gl_launch_count.restype = i64
+        lib.gl_autotune.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times), vp, i32,
+                                    vp, ctypes.POINTER(_TuneReport)]
+        lib.gl_autotune.restype = i32
         lib.gl_counts_enable.argtypes = [vp, i32]
         lib.gl_counts_enable.restype = i32
         lib.gl_counts_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
@@ -200,6 +210,21 @@ def gl_lightcurve_batch_noalloc(params: dict, t, out, precision: int = GL_FP32C,
                                            _stream_ptr(stream))
 
 
+def gl_autotune(ctx, params: dict, t, out, precision: int = GL_FP32C, offsets=None,
+                exptime=None, nsuper=None, nsuper_all: int = 1, stream=None) -> dict:
+    """Run the library's autotuner on this batch; returns its report as a dict."""
+    lib = load()
+    n_sets = int(len(params["t0"]))
+    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"),
+                0 if offsets is not None else int(len(t)), int(len(out)),
+                _ptr(exptime, "float64"), _ptr(nsuper, "int32"), int(nsuper_all))
+    rep = _TuneReport()
+    _check(ctx, lib.gl_autotune(ctx, ctypes.byref(p), ctypes.byref(tm), _ptr(out, "float64"),
+                                int(precision), _stream_ptr(stream), ctypes.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in rep._fields_}
+
+
 def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_FP32C,
                 stream=None, check: bool = True) -> int:
     lib = load()
@@ -293,6 +318,11 @@ class Context:
 
     def last_error(self) -> str:
         return gl_last_error(self.handle)
+
+    def autotune(self, params, t, out, exptime, nsuper=None, nsuper_all=1, offsets=None,
+                 precision=GL_FP32C, stream=None) -> dict:
+        return gl_autotune(self.handle, params, t, out, precision, offsets, exptime, nsuper,
+                           nsuper_all, stream)
 
     def counts(self, on: bool = True):
         gl_counts_enable(self.handle, on)

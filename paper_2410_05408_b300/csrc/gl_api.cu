@@ -36,7 +36,10 @@ constexpr int kNodes64 = 32;
 constexpr int kNodes32 = 20;
 
 __constant__ NodeRule<double> c_rule64;
-__constant__ NodeRule<float> c_rule32;
+__constant__ NodeRule<float> c_rule32;                 // default order (kNodes32)
+// orders the autotuner may choose for the FP32C light-curve kernel
+constexpr int kTuneNodes[4] = {16, 20, 24, 28};
+__constant__ NodeRule<float> c_rule32_tuned[4];
 
 template <typename R> __device__ __forceinline__ const NodeRule<R>& rule();
 template <> __device__ __forceinline__ const NodeRule<double>& rule<double>() { return c_rule64; }
@@ -143,6 +146,20 @@ __global__ void __launch_bounds__(256) gl_curve_kernel(const SetConst* __restric
   }
 }
 
+// max |a - b| over n doubles (NaN counts as infinite), into *err (non-negative
+// doubles order like their bit patterns)
+__global__ void gl_maxdiff_kernel(const double* a, const double* b, int64_t n,
+                                  unsigned long long* err) {
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double d = fabs(a[i] - b[i]);
+    if (!(d <= m)) m = isnan(d) ? INFINITY : d;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(err, (unsigned long long)__double_as_longlong(m));
+}
+
 // ------------------------------------------------------------------ fused persistent kernel
 // One CTA processes tiles of TILE consecutive exposures, taken from an atomic
 // tile counter until none are left:
@@ -166,7 +183,14 @@ struct LcArgs {
   unsigned int* tile_counter;
   unsigned long long* counts;   // instrumented instances: GL_COUNT_* slots
   int n_tiles, tile, cap;
+  int rule_idx;                 // FP32 quadrature order: index into c_rule32_tuned, -1 = default
 };
+
+template <typename R> __device__ __forceinline__ const NodeRule<R>& lc_rule(int idx);
+template <> __device__ __forceinline__ const NodeRule<double>& lc_rule<double>(int) { return c_rule64; }
+template <> __device__ __forceinline__ const NodeRule<float>& lc_rule<float>(int idx) {
+  return idx < 0 ? c_rule32 : c_rule32_tuned[idx];
+}
 
 template <typename R>
 struct LcSmem {
@@ -242,7 +266,7 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
   R* it_def = (R*)(smem + LcSmem<R>::def(tile_sz, cap));
   int* q_full = (int*)(smem + LcSmem<R>::qf(tile_sz, cap));
   int* q_part = (int*)(smem + LcSmem<R>::qp(tile_sz, cap));
-  const NodeRule<R>& rl = rule<R>();
+  const NodeRule<R>& rl = lc_rule<R>(a.rule_idx);
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -475,8 +499,11 @@ cudaError_t ensure_device_tables(int device) {
   if (g_dev_ready[device]) return cudaSuccess;
   NodeRule<double> r64 = build_rule<double>(kNodes64);
   NodeRule<float> r32 = build_rule<float>(kNodes32);
+  NodeRule<float> rt[4];
+  for (int i = 0; i < 4; ++i) rt[i] = build_rule<float>(kTuneNodes[i]);
   cudaError_t e = cudaMemcpyToSymbol(c_rule64, &r64, sizeof r64);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32, &r32, sizeof r32);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32_tuned, rt, sizeof rt);
   if (e == cudaSuccess) g_dev_ready[device] = 1;
   return e;
 }
@@ -496,7 +523,17 @@ struct gl_context {
   int* d_status = nullptr;
   unsigned int* d_counter = nullptr;   // tile counter of the persistent kernel
   int sms = 0;
-  int occ[4] = {0, 0, 0, 0};           // resident CTAs per SM: FP64, FP32C, counting variants
+  int occ[16] = {0};                   // resident CTAs per SM by (precision, counting, threads)
+  struct LcCfg {
+    int threads, tile, cap, rule_idx;
+  } cfg[2] = {{256, 256, 1024, -1}, {256, 256, 1024, -1}};   // FP64, FP32C
+  struct TuneInfo {
+    int tuned = 0, candidates = 0, admissible = 0;
+    double best_ms = 0, default_ms = 0, max_err = 0;
+  } tune[2];
+  double* d_ref = nullptr;             // autotuner: FP64 reference output
+  size_t ref_cap = 0;
+  double* d_err = nullptr;             // autotuner: max |difference| slot
   unsigned long long* d_counts = nullptr;   // GL_COUNT_* slots
   bool counting = false;
   // graph cache: one captured step per distinct argument set
@@ -639,25 +676,15 @@ int launch_grid(int64_t n, int threads) {
   return (int)b;
 }
 
-constexpr int kLcThreads = 256;
-constexpr int kLcTile = 256;
-constexpr int kLcCap = 1024;
-
-template <typename R, bool COUNT>
-int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
-  LcArgs args = args0;
-  args.tile = kLcTile;
-  args.cap = kLcCap;
-  args.n_tiles = (int)((args.n_total + kLcTile - 1) / kLcTile);
-  args.tile_counter = ctx->d_counter;
-  args.counts = ctx->d_counts;
-  size_t smem = LcSmem<R>::total(kLcTile, kLcCap);
-  int& occ = ctx->occ[(sizeof(R) == 4 ? 1 : 0) + (COUNT ? 2 : 0)];
+template <typename R, int NT, bool COUNT>
+int launch_lc_nt(gl_context* ctx, LcArgs args, int occ_slot, cudaStream_t st) {
+  size_t smem = LcSmem<R>::total(args.tile, args.cap);
+  int& occ = ctx->occ[occ_slot];
   if (occ == 0) {
-    GL_CUDA(ctx, cudaFuncSetAttribute(gl_lc_kernel<R, kLcThreads, COUNT>,
+    GL_CUDA(ctx, cudaFuncSetAttribute(gl_lc_kernel<R, NT, COUNT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                     &occ, gl_lc_kernel<R, kLcThreads, COUNT>, kLcThreads, smem));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gl_lc_kernel<R, NT, COUNT>,
+                                                               NT, smem));
     if (occ < 1) return fail(ctx, GL_ECUDA, "light-curve kernel does not fit on an SM");
   }
   int grid = ctx->sms * occ;
@@ -665,11 +692,33 @@ int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
   if (grid < 1) grid = 1;
   GL_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), st));
   long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
-  gl_lc_kernel<R, kLcThreads, COUNT><<<grid, kLcThreads, smem, st>>>(args);
+  gl_lc_kernel<R, NT, COUNT><<<grid, NT, smem, st>>>(args);
   prof_end(ctx, GL_KERNEL_CURVE, pe, st);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
   return GL_OK;
+}
+
+// occupancy is cached per (precision, counting, threads) instance
+bool lc_ready(const gl_context* ctx, int prec) {
+  const gl_context::LcCfg& cf = ctx->cfg[prec == GL_FP64 ? 0 : 1];
+  int slot = (prec == GL_FP64 ? 0 : 1) + (ctx->counting ? 2 : 0) + (cf.threads == 128 ? 4 : 0);
+  return ctx->occ[slot] != 0;
+}
+
+template <typename R, bool COUNT>
+int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
+  const gl_context::LcCfg& cf = ctx->cfg[sizeof(R) == 4 ? 1 : 0];
+  LcArgs args = args0;
+  args.tile = cf.tile;
+  args.cap = cf.cap;
+  args.rule_idx = cf.rule_idx;
+  args.n_tiles = (int)((args.n_total + cf.tile - 1) / cf.tile);
+  args.tile_counter = ctx->d_counter;
+  args.counts = ctx->d_counts;
+  int slot = (sizeof(R) == 4 ? 1 : 0) + (COUNT ? 2 : 0) + (cf.threads == 128 ? 4 : 0);
+  if (cf.threads == 128) return launch_lc_nt<R, 128, COUNT>(ctx, args, slot, st);
+  return launch_lc_nt<R, 256, COUNT>(ctx, args, slot, st);
 }
 
 // One light-curve step: per-set constants, then the fused kernel.
@@ -715,10 +764,7 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     if (g.key_len == sizeof key && memcmp(g.key, key, sizeof key) == 0) hit = &g;
   if (!hit) {
     // the occupancy query and attribute setting must not happen inside a capture
-    int rc0 = GL_OK;
-    if (sa.prec == GL_FP64 && ctx->occ[0] == 0) rc0 = -1;
-    if (sa.prec != GL_FP64 && ctx->occ[1] == 0) rc0 = -1;
-    if (rc0) return enqueue_step(ctx, sa, st);   // first call: run eagerly, capture next time
+    if (!lc_ready(ctx, sa.prec)) return enqueue_step(ctx, sa, st);   // first call: eager
     GL_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int64_t l0 = ctx->launches;
     int rc = enqueue_step(ctx, sa, ctx->cap_stream);
@@ -798,6 +844,8 @@ int gl_context_destroy(gl_context* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
   if (ctx->d_counts) cudaFree(ctx->d_counts);
+  if (ctx->d_ref) cudaFree(ctx->d_ref);
+  if (ctx->d_err) cudaFree(ctx->d_err);
   for (auto& g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (int k = 0; k < GL_KERNEL_KINDS; ++k)
@@ -837,6 +885,116 @@ int gl_graphs_enable(gl_context* ctx, int on) {
 }
 
 int64_t gl_graph_launches(const gl_context* ctx) { return ctx ? ctx->graph_launches : 0; }
+
+int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
+                gl_precision prec, void* stream, gl_tune_report* rep) {
+  if (!ctx || !p || !tm || !out) return GL_EINVAL;
+  if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision");
+  if (!is_device_ptr(out, ctx->device) || !is_device_ptr(tm->t, ctx->device))
+    return fail(ctx, GL_EINVAL, "autotuning needs device buffers");
+  if (tm->n_total <= 0 || p->n_sets <= 0) return fail(ctx, GL_EINVAL, "empty batch");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  bool was_prof = ctx->profiling, was_count = ctx->counting, was_graph = ctx->graphs;
+  ctx->profiling = false;
+  ctx->counting = false;
+  ctx->graphs = false;
+  drop_graphs(ctx);
+  int rc = grow(ctx, (void**)&ctx->d_ref, &ctx->ref_cap, (size_t)tm->n_total * sizeof(double));
+  if (rc) return rc;
+  if (!ctx->d_err) GL_CUDA(ctx, cudaMalloc(&ctx->d_err, sizeof(unsigned long long)));
+  // reference: the FP64 path with its default configuration
+  gl_context::LcCfg saved[2] = {ctx->cfg[0], ctx->cfg[1]};
+  ctx->cfg[0] = {256, 256, 1024, -1};
+  rc = gl_lightcurve_batch(ctx, p, tm, ctx->d_ref, GL_FP64, stream);
+  if (rc) return rc;
+  const int pi = prec == GL_FP64 ? 0 : 1;
+  const double tol = prec == GL_FP64 ? 1e-10 : 1e-7;
+  struct Cand { int threads, nodes_idx; };
+  Cand cands[8];
+  int nc = 0;
+  for (int th : {128, 256}) {
+    if (prec == GL_FP64) {
+      cands[nc++] = {th, -1};
+    } else {
+      for (int ni = 0; ni < 4; ++ni) cands[nc++] = {th, ni};
+    }
+  }
+  cudaEvent_t e0, e1;
+  GL_CUDA(ctx, cudaEventCreate(&e0));
+  GL_CUDA(ctx, cudaEventCreate(&e1));
+  double best_ms = 1e30, default_ms = 0.0, best_err = 0.0;
+  int best = -1, admissible = 0;
+  for (int ci = 0; ci < nc && rc == GL_OK; ++ci) {
+    ctx->cfg[pi] = {cands[ci].threads, cands[ci].threads, 4 * cands[ci].threads,
+                    cands[ci].nodes_idx};
+    rc = gl_lightcurve_batch(ctx, p, tm, out, prec, stream);
+    if (rc) break;
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned long long), st);
+    gl_maxdiff_kernel<<<ctx->sms * 4, 256, 0, st>>>(out, ctx->d_ref, tm->n_total,
+                                                     (unsigned long long*)ctx->d_err);
+    unsigned long long eb = 0;
+    cudaMemcpyAsync(&eb, ctx->d_err, sizeof eb, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = fail(ctx, GL_ECUDA, "autotune synchronisation failed");
+      break;
+    }
+    double err;
+    memcpy(&err, &eb, sizeof err);
+    bool ok = err <= 0.9 * tol;
+    float ms = 1e30f;
+    if (ok) {
+      ++admissible;
+      for (int rep_i = 0; rep_i < 3; ++rep_i) {
+        cudaEventRecord(e0, st);
+        rc = gl_lightcurve_batch(ctx, p, tm, out, prec, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float m = 0.f;
+        cudaEventElapsedTime(&m, e0, e1);
+        if (m < ms) ms = m;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ci;
+        best_err = err;
+      }
+    }
+    if (cands[ci].threads == 256 && (cands[ci].nodes_idx == 1 || cands[ci].nodes_idx == -1))
+      default_ms = ok ? ms : 0.0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->cfg[0] = saved[0];
+  ctx->cfg[1] = saved[1];
+  if (best >= 0)
+    ctx->cfg[pi] = {cands[best].threads, cands[best].threads, 4 * cands[best].threads,
+                    cands[best].nodes_idx};
+  ctx->profiling = was_prof;
+  ctx->counting = was_count;
+  ctx->graphs = was_graph;
+  drop_graphs(ctx);
+  if (rc) return rc;
+  if (best < 0) return fail(ctx, GL_ENUMERIC, "no candidate met the tolerance");
+  gl_context::TuneInfo& ti = ctx->tune[pi];
+  ti.tuned = 1;
+  ti.candidates = nc;
+  ti.admissible = admissible;
+  ti.best_ms = best_ms;
+  ti.default_ms = default_ms;
+  ti.max_err = best_err;
+  if (rep) {
+    rep->threads = cands[best].threads;
+    rep->tile = cands[best].threads;
+    rep->nodes = prec == GL_FP64 ? kNodes64 : kTuneNodes[cands[best].nodes_idx];
+    rep->ms = best_ms;
+    rep->default_ms = default_ms;
+    rep->max_abs_err = best_err;
+    rep->candidates = nc;
+    rep->admissible = admissible;
+  }
+  return GL_OK;
+}
 
 int gl_profile_enable(gl_context* ctx, int on) {
   if (!ctx) return GL_EINVAL;

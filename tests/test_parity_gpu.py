@@ -288,6 +288,23 @@ def test_workload_counts(ctx):
     assert c["partial"] > 0 and c["full"] > c["partial"]
 
 
+def test_autotuner_keeps_only_tolerance_passing_configurations(ctx, mcmc):
+    import oracle  # noqa: F401  (reference values come from the mcmc fixture)
+    wl, idx, ref = mcmc
+    p = {k: _dev(v) for k, v in product_params(wl).items()}
+    t, exp = _dev(wl["t"]), _dev(wl["exptime"])
+    out = torch.empty(256 * len(wl["t"]), dtype=torch.float64, device="cuda")
+    rep = ctx.autotune(p, t, out, exp, nsuper_all=15, precision=binding.GL_FP32C)
+    assert rep["candidates"] == 8 and rep["admissible"] >= 1
+    assert rep["max_abs_err"] <= 0.9e-7 and rep["threads"] in (128, 256)
+    assert rep["nodes"] in (16, 20, 24, 28)
+    # later calls use the chosen configuration and stay within tolerance of the oracle
+    out2 = torch.empty_like(out)
+    ctx.lightcurve(p, t, out2, exp, nsuper_all=15, precision=binding.GL_FP32C)
+    got = out2.cpu().numpy().reshape(256, -1)
+    _compare(got[idx].ravel(), ref.ravel(), binding.GL_FP32C)
+
+
 def test_launches_are_counted(ctx):
     n0 = ctx.launches()
     _run(ctx, inputs.single_transit(n_times=10), binding.GL_FP32C)
