@@ -147,6 +147,18 @@ int gl_flux_sky(gl_context *ctx, int64_t n, const double *x0, const double *y0,
                 const double *xi, const double *u1, const double *u2, double *out,
                 gl_precision prec, void *stream);
 
+/* Relative flux of a spherical planet of radius p (stellar radii) centred at
+ * (x0, y0, z), quadratic limb darkening (u1, u2); n entries each, FP64.  The
+ * circle case of the same Green's-theorem formulation (Sec. 2 integrands):
+ * crossings, f_flat and f_quad in closed form, f_lin by the mapped Gauss-Legendre
+ * rule on the symmetric half-arc (the FP32C order for GL_FP32C, the FP64 order for
+ * GL_FP64).  It is the base term of the oblate-minus-spherical surrogate.  Same
+ * memory, stream and error rules as gl_flux_sky; invalid inputs (p <= 0,
+ * non-finite values, LD with no flux) give NaN and GL_ENUMERIC at gl_sync. */
+int gl_flux_sphere(gl_context *ctx, int64_t n, const double *x0, const double *y0,
+                   const double *z, const double *p, const double *u1, const double *u2,
+                   double *out, gl_precision prec, void *stream);
+
 /* Kipping (2013) map from (q1, q2) in [0,1]^2 to quadratic coefficients,
  * u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2) (cited in Sec. 3, Table priors,
  * note f; the formula is not printed in the paper).  Host arrays of n entries;
@@ -225,7 +237,8 @@ int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *
 #define GL_KERNEL_SETUP 0   /* per-set constants */
 #define GL_KERNEL_CURVE 1   /* light-curve kernel (FP64 or FP32C) */
 #define GL_KERNEL_SKY 2     /* geometry-level kernel */
-#define GL_KERNEL_KINDS 3
+#define GL_KERNEL_SPHERE 3  /* spherical-planet kernel */
+#define GL_KERNEL_KINDS 8
 
 /* Per-kernel device timing for benchmarks.  While enabled (on != 0), every
  * kernel launch of the context is bracketed by CUDA events recorded on its

@@ -286,7 +286,7 @@ int orc_occulted_moments(double x0, double y0, double dx, double dy1, double dy2
 
     /* Breakpoints in phi: crossings of the boundary with the limb, near-tangent
      * extrema of g, and the abscissae x = +-1. */
-    double bp[64];
+    double bp[72];
     int nbp = 0;
     bp[nbp++] = 0.0;
     bp[nbp++] = M_PI;
@@ -317,9 +317,25 @@ int orc_occulted_moments(double x0, double y0, double dx, double dy1, double dy2
                 if ((dm < 0) == (dlo < 0)) { lo = m; dlo = dm; } else hi = m;
             }
             double r = 0.5 * (lo + hi);
-            if (fabs(gfun(&g, r)) < 1e-6) {
+            double gr = gfun(&g, r);
+            if (fabs(gr) < 1e-6) {
                 double phi = r <= M_PI ? r : 2.0 * M_PI - r;
                 if (nbp < 60) bp[nbp++] = phi;
+            }
+            /* two crossings inside one sampling step: the samples on both sides
+             * of the extremum share a sign that the extremum does not */
+            if ((prev_g < 0) == (gv < 0) && (gr < 0) != (gv < 0)) {
+                double ends[2][2] = {{prev_th, r}, {r, th}};
+                for (int side = 0; side < 2; ++side) {
+                    double a = ends[side][0], b = ends[side][1], ga = gfun(&g, a);
+                    for (int it = 0; it < 200 && b - a > 1e-17; ++it) {
+                        double m = 0.5 * (a + b), gm = gfun(&g, m);
+                        if ((gm < 0) == (ga < 0)) { a = m; ga = gm; } else b = m;
+                    }
+                    double rr = 0.5 * (a + b);
+                    double phi = rr <= M_PI ? rr : 2.0 * M_PI - rr;
+                    if (nbp < 60) bp[nbp++] = phi;
+                }
             }
         }
         prev_th = th;

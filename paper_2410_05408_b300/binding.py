@@ -29,7 +29,8 @@ GL_FP32C = 1
 EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_lightcurve_batch",
             "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
             "gl_profile_read", "gl_lightcurve_batch_noalloc", "gl_counts_enable",
-            "gl_counts_read", "gl_graphs_enable", "gl_graph_launches", "gl_autotune")
+            "gl_counts_read", "gl_graphs_enable", "gl_graph_launches", "gl_autotune",
+            "gl_flux_sphere")
 
 COUNT_NAMES = ("exposures", "kept", "in_window", "kepler", "items", "item_kepler", "full",
                "partial")
@@ -39,6 +40,7 @@ GL_NOALLOC_MAX_SETS = 4096
 GL_KERNEL_SETUP = 0
 GL_KERNEL_CURVE = 1
 GL_KERNEL_SKY = 2
+GL_KERNEL_SPHERE = 3
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 
@@ -93,6 +95,8 @@ def load():
         lib.gl_lightcurve_batch.restype = i32
         lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
         lib.gl_flux_sky.restype = i32
+        lib.gl_flux_sphere.argtypes = [vp, i64] + [vp] * 7 + [i32, vp]
+        lib.gl_flux_sphere.restype = i32
         lib.gl_q_to_u.argtypes = [i64, vp, vp, vp, vp]
         lib.gl_q_to_u.restype = i32
         lib.gl_sync.argtypes = [vp, vp]
@@ -236,6 +240,17 @@ def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_
     return rc
 
 
+def gl_flux_sphere(ctx, x0, y0, z, p, u1, u2, out, precision: int = GL_FP32C, stream=None,
+                   check: bool = True) -> int:
+    lib = load()
+    n = int(len(out))
+    rc = lib.gl_flux_sphere(ctx, n, *[_ptr(a, "float64") for a in (x0, y0, z, p, u1, u2)],
+                            _ptr(out, "float64"), int(precision), _stream_ptr(stream))
+    if check:
+        _check(ctx, rc)
+    return rc
+
+
 def gl_q_to_u(q1, q2):
     q1 = np.ascontiguousarray(q1, dtype=np.float64)
     q2 = np.ascontiguousarray(q2, dtype=np.float64)
@@ -309,6 +324,9 @@ class Context:
 
     def flux_sky(self, x0, y0, z, k, f, eta, xi, u1, u2, out, precision=GL_FP32C, stream=None):
         return gl_flux_sky(self.handle, x0, y0, z, k, f, eta, xi, u1, u2, out, precision, stream)
+
+    def flux_sphere(self, x0, y0, z, p, u1, u2, out, precision=GL_FP32C, stream=None):
+        return gl_flux_sphere(self.handle, x0, y0, z, p, u1, u2, out, precision, stream)
 
     def sync(self, stream=None) -> int:
         return gl_sync(self.handle, stream)

@@ -426,6 +426,38 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
   }
 }
 
+// Spherical planet: one item per thread.
+struct SpherePtrs {
+  const double *x0, *y0, *z, *p, *u1, *u2;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) gl_sphere_kernel(SpherePtrs a, int64_t n, double* out,
+                                                        int* status) {
+  const NodeRule<R>& rl = rule<R>();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x0 = a.x0[i], y0 = a.y0[i], zz = a.z[i], p = a.p[i], u1 = a.u1[i], u2 = a.u2[i];
+    double F0 = gl::kPi * (1.0 - u1 * (1.0 / 3.0) - u2 * (1.0 / 6.0));
+    if (!(isfinite(x0) && isfinite(y0) && isfinite(zz) && isfinite(p) && p > 0.0 &&
+          isfinite(u1) && isfinite(u2) && F0 > 0.0)) {
+      out[i] = __longlong_as_double(0x7ff8000000000000LL);
+      atomicOr(status, kStatusInvalidSet);
+      continue;
+    }
+    double rho = sqrt(x0 * x0 + y0 * y0);
+    if (zz > 0.0 || rho >= 1.0 + p) {
+      out[i] = 1.0;
+      continue;
+    }
+    R I[3];
+    gl::sphere_moments<R>((R)rho, (R)p, (R)((1.0 - x0) * (1.0 + x0) - y0 * y0), rl, I);
+    double def = (1.0 - u1 - 2.0 * u2) * (double)I[0] + (u1 + 2.0 * u2) * (double)I[1] +
+                 u2 * (double)I[2];
+    out[i] = 1.0 - def / F0;
+  }
+}
+
 struct SkyPtrs {
   const double *x0, *y0, *z, *k, *f, *eta, *xi, *u1, *u2;
 };
@@ -552,7 +584,7 @@ struct gl_context {
   // per-kernel event timing (gl_profile_enable)
   bool profiling = false;
   std::vector<cudaEvent_t> ev[GL_KERNEL_KINDS];   // pairs: start, stop
-  size_t ev_used[GL_KERNEL_KINDS] = {0, 0, 0};
+  size_t ev_used[GL_KERNEL_KINDS] = {0};
 };
 
 namespace {
@@ -1134,6 +1166,46 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
     GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, (size_t)tm->n_total * sizeof(double),
                                  cudaMemcpyDeviceToHost, st));
   }
+  if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
+  return GL_OK;
+}
+
+int gl_flux_sphere(gl_context* ctx, int64_t n, const double* x0, const double* y0,
+                   const double* z, const double* p, const double* u1, const double* u2,
+                   double* out, gl_precision prec, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n < 0) return fail(ctx, GL_EINVAL, "n < 0");
+  if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision %d", (int)prec);
+  if (n == 0) return GL_OK;
+  if (!x0 || !y0 || !z || !p || !u1 || !u2 || !out) return fail(ctx, GL_EINVAL, "NULL array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  SpherePtrs sp = {x0, y0, z, p, u1, u2};
+  size_t b = (size_t)n * sizeof(double);
+  StageItem items[] = {{(const void**)&sp.x0, b}, {(const void**)&sp.y0, b},
+                       {(const void**)&sp.z, b},  {(const void**)&sp.p, b},
+                       {(const void**)&sp.u1, b}, {(const void**)&sp.u2, b}};
+  bool any_host = false;
+  int rc = stage_inputs(ctx, items, 6, st, &any_host);
+  if (rc) return rc;
+  bool out_host = !is_device_ptr(out, ctx->device);
+  double* d_out = out;
+  if (out_host) {
+    rc = grow(ctx, (void**)&ctx->d_out, &ctx->out_cap, b);
+    if (rc) return rc;
+    d_out = ctx->d_out;
+  }
+  int grid = launch_grid(n, 256);
+  long pe = prof_begin(ctx, GL_KERNEL_SPHERE, st);
+  if (prec == GL_FP64)
+    gl_sphere_kernel<double><<<grid, 256, 0, st>>>(sp, n, d_out, ctx->d_status);
+  else
+    gl_sphere_kernel<float><<<grid, 256, 0, st>>>(sp, n, d_out, ctx->d_status);
+  prof_end(ctx, GL_KERNEL_SPHERE, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  if (out_host) GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, b, cudaMemcpyDeviceToHost, st));
   if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
   return GL_OK;
 }

@@ -1124,6 +1124,85 @@ GL_HD double subexposure_flux(const SetConst& c, double tau, const NodeRule<R>& 
   return 1.0 - (double)def * c.invF0;
 }
 
+// ------------------------------------------------------------------ spherical planet
+// Moments of the region a circle of radius p at distance z from the star's
+// centre covers (the planet boundary x = z + p cos phi, y = p sin phi):
+// crossings at cos phi_c = (1 - z^2 - p^2)/(2 z p) in closed form; f_flat and
+// f_quad (Sec. 2) in closed form on the planet arc and the limb arc; f_lin on the
+// planet arc by the mapped Gauss-Legendre rule over the half-arc [phi_c, pi]
+// (the arc is symmetric about phi = pi), whose end phi_c carries the
+// (1 - r^2)^(3/2) behaviour.  omz2 = 1 - z^2 from the caller's best precision.
+template <typename R>
+GL_HD void sphere_moments(R z, R p, R omz2, const NodeRule<R>& rule, R I[3]) {
+  I[0] = I[1] = I[2] = R(0);
+  if (!(p > R(0)) || z >= R(1) + p) return;
+  if (z <= p - R(1)) {            // the planet covers the whole star
+    I[0] = R(kPi);
+    I[1] = R(2.0 * kPi / 3.0);
+    I[2] = R(0.5 * kPi);
+    return;
+  }
+  const R p2 = p * p;
+  R phc, sphc, cphc;               // planet-arc crossing angle
+  R lam = R(0), s4lam = R(0);      // limb-arc half-angle and sin(4 lambda_c)
+  bool full = (z + p <= R(1));
+  if (full) {
+    phc = R(0);
+    sphc = R(0);
+    cphc = R(1);
+  } else {
+    // triangle (star centre, planet centre, crossing) with sides 1, z, p: twice
+    // its area by Heron's formula, with 1 - z taken from 1 - z^2 (no cancellation
+    // near tangency); then the angles at the planet centre and the star centre
+    R omz = omz2 / (R(1) + z);
+    R h2 = (R(1) + z + p) * (R(1) + z - p) * (p + omz) * (p - omz);
+    R twoK = R(0.5) * m_sqrt(h2 > R(0) ? h2 : R(0));             // = z p sin(phi_c)
+    R cnum = R(0.5) * (omz2 - p2);                                // = z p cos(phi_c)
+    phc = m_atan2(twoK, cnum);
+    R zp = z * p;
+    sphc = twoK / zp;
+    cphc = cnum / zp;
+    R lnum = R(0.5) * (R(1) + z * z - p2);                         // = z cos(lambda_c)
+    lam = m_atan2(twoK, lnum);                                      // z sin(lambda_c) = 2K
+    R nrm = rsqrt_<R>(lnum * lnum + twoK * twoK);
+    R cl = lnum * nrm, sl = twoK * nrm;
+    s4lam = R(4) * sl * cl * (cl * cl - sl * sl);
+  }
+  // f_flat: planet arc [phi_c, 2 pi - phi_c] + limb arc [-lambda_c, lambda_c]
+  I[0] = p2 * (R(kPi) - phc) - z * p * sphc + lam;   // the lens area when partial
+  // f_quad: antiderivative along the planet circle (a = b2 = p, b1 = 0, y0 = 0),
+  // symmetric arc: F(2 pi - phi_c) - F(phi_c) = K (2 pi - 2 phi_c) - 2 sum_n S_n sin(n phi_c)
+  {
+    QuadPoly<R> q = quad_poly<R>(z, R(0), p, R(0), p);
+    R cn = cphc, sn = sphc, cp = R(1), sp = R(0), sines = R(0);
+    for (int n = 0; n < 4; ++n) {
+      sines += q.S[n] * sn;
+      R cnext = R(2) * cphc * cn - cp, snext = R(2) * cphc * sn - sp;
+      cp = cn;
+      sp = sn;
+      cn = cnext;
+      sn = snext;
+    }
+    I[2] = q.K * (R(2 * kPi) - R(2) * phc) - R(2) * sines + (R(0.5) * lam - s4lam / R(24));
+  }
+  // f_lin: 2 x half-arc quadrature + limb arc (1/3)(2 lambda_c)
+  {
+    R a = phc, b = R(kPi);
+    R m = R(0.5) * (a + b), h = R(0.5) * (b - a);
+    R sm, cm;
+    sincos_<R>(m, &sm, &cm);
+    CSum<R> acc;
+    for (int j = 0; j < rule.n; ++j) {
+      R sa, ca;
+      sincos_<R>(h * rule.sig[j], &sa, &ca);
+      R cph = cm * ca - sm * sa;
+      R omr2 = omz2 - p2 - R(2) * z * p * cph;
+      acc.add(rule.wt[j] * lin_kernel<R>(omr2) * (z * p * cph + p2));
+    }
+    I[1] = R(2) * h * acc.value() + R(2) * lam / R(3);
+  }
+}
+
 // Exposure midpoint state rounded for FP32 sub-exposure steps: position,
 // 1 - x^2 - y^2 (formed in FP64) and the first three derivatives.
 struct MidState {

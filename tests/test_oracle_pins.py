@@ -262,6 +262,22 @@ def test_circle_area_is_lens_area(p):
         assert abs(m[0] - _lens_area(p, rho)) < 2e-14
 
 
+def test_near_tangent_crossing_pair_in_any_orientation():
+    """A circle overlapping the limb by a sliver of depth ~5e-8: its two crossings
+    are closer than the oracle's sampling step, in every orientation."""
+    mp.mp.dps = 40
+    for p, depth in [(0.41376514184929669, 4.8e-8), (0.2, 1e-9), (0.05, 3e-7)]:
+        z = 1.0 - p + depth
+        Z, P = mp.mpf(z), mp.mpf(p)
+        k0 = mp.acos((P * P + Z * Z - 1) / (2 * P * Z))
+        k1 = mp.acos((1 - P * P + Z * Z) / (2 * Z))
+        exact = float(P * P * k0 + k1 - mp.sqrt(4 * Z * Z - (1 + Z * Z - P * P) ** 2) / 2)
+        for ang in np.linspace(0.1, 6.2, 7):
+            m = oracle.occulted_moments(z * math.cos(ang), z * math.sin(ang), p, 0.0, p)
+            assert abs(m[0] - exact) < 1e-14
+    mp.mp.dps = 30
+
+
 def test_full_inside_closed_forms():
     rng = np.random.default_rng(3)
     for _ in range(30):

@@ -179,6 +179,36 @@ def test_geometry_parity(ctx, geometry, prec):
     _compare(got, ref, prec)
 
 
+# ---------------------------------------------------------------- spherical planet
+SPHERE_TOL = {binding.GL_FP64: 1e-10, binding.GL_FP32C: 2e-7}
+
+
+@pytest.fixture(scope="module")
+def sphere_geometry():
+    import oracle
+    g = inputs.geometry_sample(20000, seed=12, k_range=(0.005, 0.45), f_max=0.0)
+    u = np.array([oracle.q_to_u(a, b) for a, b in zip(g["q1"], g["q2"])])
+    g["u1"], g["u2"] = u[:, 0].copy(), u[:, 1].copy()
+    zeros = np.zeros_like(g["k"])
+    ref = oracle.flux_sky_batch(g["x0"], g["y0"], g["z"], g["k"], zeros, zeros, zeros,
+                                g["u1"], g["u2"])
+    return g, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sphere_parity(ctx, sphere_geometry, prec):
+    g, ref = sphere_geometry
+    u1, u2 = binding.gl_q_to_u(g["q1"], g["q2"])
+    out = torch.empty(len(ref), dtype=torch.float64, device="cuda")
+    ctx.flux_sphere(*[_dev(g[n]) for n in ("x0", "y0", "z", "k")], _dev(u1), _dev(u2), out,
+                    precision=prec)
+    got = out.cpu().numpy()
+    assert np.mean((ref < 1) & (ref > 0)) > 0.5
+    err = np.max(np.abs(got - ref))
+    assert err <= SPHERE_TOL[prec], f"{err:.3e}"
+    assert np.all(got[ref == 1.0] == 1.0)
+
+
 # ---------------------------------------------------------------- worked example
 def test_degeneracy_example_on_gpu(ctx):
     """Appendix A: f = 1/2, eta = 0 and f = 2/3, eta = arccos(11/16)/2 at equal R_eq."""
