@@ -253,6 +253,38 @@ int gl_profile_enable(gl_context *ctx, int on);
 int gl_profile_read(gl_context *ctx, int kind, double *ms, int64_t *launches);
 
 /* ------------------------------------------------------------------------
+ * Surrogate network (not in the paper): a fully connected network
+ * 7 -> 256 -> 256 -> 256 -> 256 -> 1 with SiLU activations and a linear output,
+ * predicting the oblate-minus-spherical flux residual from seven features.
+ * FP32 master parameters; the three 256 x 256 layers run on the tensor cores
+ * (tcgen05, BF16 operands, FP32 accumulation); loss = mean squared error.
+ * Parameter vector (FP32, gl_mlp_param_count() = 199681 entries): W1[7][256],
+ * b1[256], W2[256][256], b2, W3, b3, W4, b4 (row-major, z = x W + b), w5[256], b5.
+ * All functions return GL_OK or a negative GL_E* code. */
+typedef struct gl_mlp gl_mlp;
+
+int64_t gl_mlp_param_count(void);
+/* Create a network on `device` with all parameters zero. */
+int gl_mlp_create(gl_mlp **m, int device);
+int gl_mlp_destroy(gl_mlp *m);
+/* Copy n = gl_mlp_param_count() FP32 parameters in (host or device memory);
+ * resets the Adam state.  GL_EINVAL on NULL or a wrong n. */
+int gl_mlp_set_params(gl_mlp *m, const float *p, int64_t n);
+int gl_mlp_get_params(gl_mlp *m, float *p, int64_t n);
+/* Gradients of the last gl_mlp_loss_grad, same layout. */
+int gl_mlp_get_grads(gl_mlp *m, float *g, int64_t n);
+/* y[i] = network(x[i][0..7)) for i < n; x (n x 7) and y (n) FP32 device memory. */
+int gl_mlp_forward(gl_mlp *m, int64_t n, const float *x, float *y, void *stream);
+/* Mean squared error of the network on (x, t) and its gradient (kept by the
+ * network); *loss (host, may be NULL) is written after synchronising `stream`. */
+int gl_mlp_loss_grad(gl_mlp *m, int64_t n, const float *x, const float *t, double *loss,
+                     void *stream);
+/* One Adam step (bias-corrected) with the last gradient. */
+int gl_mlp_adam(gl_mlp *m, float lr, float beta1, float beta2, float eps, void *stream);
+/* GL_ETIMEOUT if a tensor-core wait gave up since the last call, else GL_OK. */
+int gl_mlp_status(gl_mlp *m);
+
+/* ------------------------------------------------------------------------
  * Allocation-free variant of gl_lightcurve_batch.  The paper has no
  * counterpart: this is a deployment aid.
  *

@@ -30,7 +30,9 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
             "gl_profile_read", "gl_lightcurve_batch_noalloc", "gl_counts_enable",
             "gl_counts_read", "gl_graphs_enable", "gl_graph_launches", "gl_autotune",
-            "gl_flux_sphere")
+            "gl_flux_sphere", "gl_mlp_param_count", "gl_mlp_create", "gl_mlp_destroy",
+            "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
+            "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status")
 
 COUNT_NAMES = ("exposures", "kept", "in_window", "kepler", "items", "item_kepler", "full",
                "partial")
@@ -95,6 +97,24 @@ def load():
         lib.gl_lightcurve_batch.restype = i32
         lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
         lib.gl_flux_sky.restype = i32
+        lib.gl_mlp_param_count.argtypes = []
+        lib.gl_mlp_param_count.restype = i64
+        lib.gl_mlp_create.argtypes = [ctypes.POINTER(vp), i32]
+        lib.gl_mlp_create.restype = i32
+        lib.gl_mlp_destroy.argtypes = [vp]
+        lib.gl_mlp_destroy.restype = i32
+        for fn in ("gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads"):
+            getattr(lib, fn).argtypes = [vp, vp, i64]
+            getattr(lib, fn).restype = i32
+        lib.gl_mlp_forward.argtypes = [vp, i64, vp, vp, vp]
+        lib.gl_mlp_forward.restype = i32
+        lib.gl_mlp_loss_grad.argtypes = [vp, i64, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+        lib.gl_mlp_loss_grad.restype = i32
+        lib.gl_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, vp]
+        lib.gl_mlp_adam.restype = i32
+        lib.gl_mlp_status.argtypes = [vp]
+        lib.gl_mlp_status.restype = i32
         lib.gl_flux_sphere.argtypes = [vp, i64] + [vp] * 7 + [i32, vp]
         lib.gl_flux_sphere.restype = i32
         lib.gl_q_to_u.argtypes = [i64, vp, vp, vp, vp]
@@ -136,7 +156,8 @@ def _ptr(a, dtype: str):
         return a.ctypes.data
     import torch
     if isinstance(a, torch.Tensor):
-        want = {"float64": torch.float64, "int64": torch.int64, "int32": torch.int32}[dtype]
+        want = {"float64": torch.float64, "int64": torch.int64, "int32": torch.int32,
+                "float32": torch.float32}[dtype]
         if a.dtype != want or not a.is_contiguous():
             raise TypeError(f"expected contiguous {dtype} tensor, got {a.dtype}")
         return a.data_ptr()
@@ -297,6 +318,68 @@ def gl_profile_read(ctx, kind: int):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(ctx, load().gl_profile_read(ctx, int(kind), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+class Mlp:
+    """Owns one gl_mlp (surrogate network); arrays are float32 tensors/arrays."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        rc = lib.gl_mlp_create(ctypes.byref(h), int(device))
+        if rc != GL_OK:
+            raise GLError(rc, "gl_mlp_create failed")
+        self.handle = h
+        self.n_params = int(lib.gl_mlp_param_count())
+
+    def close(self):
+        if self.handle is not None:
+            load().gl_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rc(self, rc, what):
+        if rc != GL_OK:
+            raise GLError(rc, what)
+
+    def set_params(self, p):
+        self._rc(load().gl_mlp_set_params(self.handle, _ptr(p, "float32"), self.n_params),
+                 "gl_mlp_set_params")
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._rc(load().gl_mlp_get_params(self.handle, out.ctypes.data, self.n_params),
+                 "gl_mlp_get_params")
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._rc(load().gl_mlp_get_grads(self.handle, out.ctypes.data, self.n_params),
+                 "gl_mlp_get_grads")
+        return out
+
+    def forward(self, x, y, stream=None):
+        self._rc(load().gl_mlp_forward(self.handle, int(len(y)), _ptr(x, "float32"),
+                                       _ptr(y, "float32"), _stream_ptr(stream)), "gl_mlp_forward")
+
+    def loss_grad(self, x, t, stream=None) -> float:
+        loss = ctypes.c_double()
+        self._rc(load().gl_mlp_loss_grad(self.handle, int(len(t)), _ptr(x, "float32"),
+                                         _ptr(t, "float32"), ctypes.byref(loss),
+                                         _stream_ptr(stream)), "gl_mlp_loss_grad")
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._rc(load().gl_mlp_adam(self.handle, lr, beta1, beta2, eps, _stream_ptr(stream)),
+                 "gl_mlp_adam")
+
+    def status(self) -> int:
+        return load().gl_mlp_status(self.handle)
 
 
 class Context:

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgl.so")
-SOURCES = [os.path.join(HERE, "csrc", "gl_api.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "gl_api.cu"), os.path.join(HERE, "csrc", "gl_mlp.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
                   if f.endswith((".cuh", ".h"))] + [os.path.join(ROOT, "include", "gl.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

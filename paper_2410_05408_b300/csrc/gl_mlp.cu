@@ -1,0 +1,730 @@
+// gl_mlp.cu -- surrogate network kernels (tcgen05 on sm_103a) and their C-ABI.
+//
+// Network: 7 -> 256 -> 256 -> 256 -> 256 -> 1, SiLU between layers, linear
+// output, mean-squared-error loss, Adam.  The surrogate is not part of the paper;
+// it predicts the oblate-minus-spherical flux residual of the light-curve path.
+//
+// Precision: FP32 master parameters, BF16 copies of the three 256x256 weight
+// matrices and BF16 activations for the tensor-core layers, FP32 accumulation
+// in tensor memory.  The 7-wide input layer, the 1-wide output layer, the
+// biases, the loss and Adam run on CUDA cores in FP32.
+//
+// Tensor-core kernels (one CTA per SM, 128 threads, operands staged in shared
+// memory in the K-major no-swizzle core-matrix layout, accumulators in TMEM):
+//   gl_mlp_gemm_kernel   D[128 x 256] = A[128 x 256] B[256 x 256] per row tile,
+//                        weights resident in shared memory, epilogue:
+//                        forward (z = D + b, h = SiLU(z)) or backward
+//                        (dz_prev = D * SiLU'(z_prev))
+//   gl_mlp_wgrad_kernel  dW[256 x 256] += A^T dZ over row tiles (two M = 128
+//                        accumulators, 512 TMEM columns), then added to the
+//                        FP32 gradient
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/gl.h"
+
+namespace {
+
+constexpr int W = 256;          // hidden width
+constexpr int NIN = 7;          // input features
+constexpr int TILE_M = 128;     // rows (samples) per tensor-core tile
+constexpr int NTHREADS = 128;
+
+// parameter layout (FP32): W1[7][256], b1, W2[256][256], b2, W3, b3, W4, b4, w5[256], b5
+constexpr int64_t OFF_W1 = 0;
+constexpr int64_t OFF_B1 = OFF_W1 + NIN * W;
+constexpr int64_t OFF_W2 = OFF_B1 + W;
+constexpr int64_t LAYER_STRIDE = (int64_t)W * W + W;
+__host__ __device__ constexpr int64_t off_w(int l) { return OFF_W2 + (l - 2) * LAYER_STRIDE; }   // l = 2, 3, 4
+__host__ __device__ constexpr int64_t off_b(int l) { return off_w(l) + (int64_t)W * W; }
+constexpr int64_t OFF_W5 = OFF_W2 + 3 * LAYER_STRIDE;
+constexpr int64_t OFF_B5 = OFF_W5 + W;
+constexpr int64_t NPARAM = OFF_B5 + 1;   // 199,681
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, no swizzle.  LBO = byte
+// step between core matrices along K, SBO = byte step between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version
+  return d;
+}
+// instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+// byte offset of element (r, k) in a K-major no-swizzle tile with kgroups
+// core matrices along K
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int kgroups) {
+  return (uint32_t)((((r >> 3) * kgroups + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(mbar)));
+}
+// bounded wait on an mbarrier phase; returns 1 if the phase completed
+__device__ __forceinline__ uint32_t mbar_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < (1L << 22) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity));
+  }
+  return done;
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+enum : int { EPI_FWD_TRAIN = 0, EPI_FWD_INFER = 1, EPI_BWD = 2 };
+
+struct GemmArgs {
+  const __nv_bfloat16* a;     // [n][256] row-major (activations or dZ)
+  const __nv_bfloat16* b;     // [256 (N)][256 (K)] row-major: the K-major B operand
+  const float* bias;          // forward: [256]
+  const float* zprev;         // backward: pre-activations of the previous layer [n][256]
+  float* zout;                // forward-train: pre-activations [n][256]
+  __nv_bfloat16* hout;        // forward: SiLU(z); backward: dz_prev  [n][256]
+  int64_t n;
+  int* status;
+};
+
+// Persistent tensor-core layer: B resident in shared memory, one 128-row tile
+// of A at a time, D in TMEM (256 columns).
+template <int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_gemm_kernel(GemmArgs g) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t* sB = sm;                    // 256 x 256 bf16 = 128 KB
+  uint8_t* sA = sm + 131072;           // 128 x 256 bf16 = 64 KB
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (g.n + TILE_M - 1) / TILE_M;
+  if ((int64_t)blockIdx.x >= ntiles) return;
+  for (int v = tid; v < W * 32; v += NTHREADS) {
+    int r = v >> 5, kg = v & 31;
+    uint4 val = *(const uint4*)(g.b + (int64_t)r * W + kg * 8);
+    *(uint4*)(sB + kmaj_off(r, kg * 8, 32)) = val;
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = idesc_bf16(TILE_M, W);
+  uint32_t phase = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * TILE_M;
+    for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
+      int r = v >> 5, kg = v & 31;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (row0 + r < g.n) val = *(const uint4*)(g.a + (row0 + r) * W + kg * 8);
+      *(uint4*)(sA + kmaj_off(r, kg * 8, 32)) = val;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      for (int ks = 0; ks < W / 16; ++ks) {
+        uint64_t ad = umma_desc(smem_u32(sA) + ks * 256, 128, 32 * 128);
+        uint64_t bd = umma_desc(smem_u32(sB) + ks * 256, 128, 32 * 128);
+        mma_bf16(tmem, ad, bd, idesc, ks > 0);
+      }
+      mma_commit(&mbar);
+    }
+    uint32_t done = mbar_wait(&mbar, phase);
+    done = __shfl_sync(0xffffffffu, done, 0);
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!done) {
+      if (lane == 0) {
+        atomicOr(g.status, 1);
+        s_abort = 1;
+      }
+    } else {
+      const int r = warp * 32 + lane;
+      const int64_t row = row0 + r;
+      for (int c = 0; c < W; c += 32) {
+        uint32_t acc[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, acc);
+        if (row < g.n) {
+          if (EPI == EPI_BWD) {
+            const float* zp = g.zprev + row * W + c;
+            __align__(16) __nv_bfloat16 hv[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) hv[j] = __float2bfloat16(__uint_as_float(acc[j]) * silu_grad(zp[j]));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *(uint4*)(g.hout + row * W + c + 8 * q) = *(uint4*)(hv + 8 * q);
+          } else {
+            __align__(16) __nv_bfloat16 hv[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float z = __uint_as_float(acc[j]) + g.bias[c + j];
+              if (EPI == EPI_FWD_TRAIN) g.zout[row * W + c + j] = z;
+              hv[j] = __float2bfloat16(silu(z));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *(uint4*)(g.hout + row * W + c + 8 * q) = *(uint4*)(hv + 8 * q);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (s_abort) break;
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
+struct WgradArgs {
+  const __nv_bfloat16* a;    // layer input activations [n][256]
+  const __nv_bfloat16* dz;   // layer output gradient [n][256]
+  float* dw;                 // FP32 gradient [256 (in)][256 (out)] (added to)
+  int64_t n;
+  int* status;
+};
+
+// dW = A^T dZ: M = input features (two halves of 128), N = outputs, K = samples
+// (128 per tile); the two accumulators use all 512 TMEM columns.
+__global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t* sA = sm;             // 256 (features) x 128 (samples) bf16 = 64 KB
+  uint8_t* sB = sm + 65536;     // 256 (outputs)  x 128 (samples) bf16 = 64 KB
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (g.n + TILE_M - 1) / TILE_M;
+  if ((int64_t)blockIdx.x >= ntiles) return;
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = idesc_bf16(128, W);
+  uint32_t phase = 0;
+  bool first = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * TILE_M;
+    // transpose on the way in: element (sample s, feature f) -> (f, s) of a K-major
+    // tile with K = samples (16 core matrices along K)
+    for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
+      int s = v >> 5, fg = v & 31;
+      uint4 av = make_uint4(0, 0, 0, 0), dv = make_uint4(0, 0, 0, 0);
+      if (row0 + s < g.n) {
+        av = *(const uint4*)(g.a + (row0 + s) * W + fg * 8);
+        dv = *(const uint4*)(g.dz + (row0 + s) * W + fg * 8);
+      }
+      const __nv_bfloat16* ae = (const __nv_bfloat16*)&av;
+      const __nv_bfloat16* de = (const __nv_bfloat16*)&dv;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        *(__nv_bfloat16*)(sA + kmaj_off(fg * 8 + j, s, 16)) = ae[j];
+        *(__nv_bfloat16*)(sB + kmaj_off(fg * 8 + j, s, 16)) = de[j];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      for (int h = 0; h < 2; ++h) {
+        for (int ks = 0; ks < TILE_M / 16; ++ks) {
+          uint64_t ad = umma_desc(smem_u32(sA) + h * 16 * 16 * 128 + ks * 256, 128, 16 * 128);
+          uint64_t bd = umma_desc(smem_u32(sB) + ks * 256, 128, 16 * 128);
+          mma_bf16(tmem + (uint32_t)(h * W), ad, bd, idesc, (first && ks == 0) ? 0u : 1u);
+        }
+      }
+      mma_commit(&mbar);
+    }
+    first = false;
+    uint32_t done = mbar_wait(&mbar, phase);
+    done = __shfl_sync(0xffffffffu, done, 0);
+    phase ^= 1;
+    if (!done && lane == 0) {
+      atomicOr(g.status, 1);
+      s_abort = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (s_abort) break;
+  }
+  if (!s_abort) {
+    for (int h = 0; h < 2; ++h) {
+      const int f = h * 128 + warp * 32 + lane;
+      for (int c = 0; c < W; c += 32) {
+        uint32_t acc[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * W + c), acc);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) atomicAdd(&g.dw[(int64_t)f * W + c + j], __uint_as_float(acc[j]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// ---- CUDA-core kernels
+// layer 1: z1 = x W1 + b1, h1 = SiLU(z1); one thread per (sample, output)
+__global__ void gl_mlp_in_kernel(const float* __restrict__ x, const float* __restrict__ p,
+                                 float* __restrict__ z1, __nv_bfloat16* __restrict__ h1,
+                                 int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * W) return;
+  int64_t s = i / W;
+  int o = (int)(i % W);
+  float z = p[OFF_B1 + o];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) z = fmaf(x[s * NIN + k], p[OFF_W1 + k * W + o], z);
+  if (z1) z1[i] = z;
+  h1[i] = __float2bfloat16(silu(z));
+}
+
+// output layer y = h4 . w5 + b5; one warp per sample
+__global__ void gl_mlp_out_kernel(const __nv_bfloat16* __restrict__ h4, const float* __restrict__ p,
+                                  float* __restrict__ y, int64_t n) {
+  int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (s >= n) return;
+  float acc = 0.f;
+  for (int k = lane; k < W; k += 32) acc = fmaf(__bfloat162float(h4[s * W + k]), p[OFF_W5 + k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[s] = acc + p[OFF_B5];
+}
+
+// output-layer backward, per sample: r = y - t, dy = 2 r / n, rr = r^2 / n,
+// dz4 = dy w5 SiLU'(z4).  One warp per sample.
+__global__ void gl_mlp_outgrad_kernel(const float* __restrict__ z4, const float* __restrict__ y,
+                                      const float* __restrict__ t, const float* __restrict__ p,
+                                      float* __restrict__ dy, float* __restrict__ rr,
+                                      __nv_bfloat16* __restrict__ dz4, int64_t n) {
+  int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (s >= n) return;
+  float r = y[s] - t[s];
+  float d = 2.0f * r / (float)n;
+  if (lane == 0) {
+    dy[s] = d;
+    rr[s] = r * r / (float)n;
+  }
+  for (int k = lane; k < W; k += 32)
+    dz4[s * W + k] = __float2bfloat16(d * p[OFF_W5 + k] * silu_grad(z4[s * W + k]));
+}
+
+// output-layer reductions: dw5[k] += sum_s h4[s][k] dy[s]; thread 0 also sums
+// dy (db5) and rr (loss).  Thread per k, samples strided over blocks.
+__global__ void gl_mlp_outred_kernel(const __nv_bfloat16* __restrict__ h4,
+                                     const float* __restrict__ dy, const float* __restrict__ rr,
+                                     float* __restrict__ grad, double* __restrict__ loss,
+                                     int64_t n) {
+  int k = threadIdx.x;
+  float acc = 0.f, sdy = 0.f;
+  double sl = 0.0;
+  for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+    float d = dy[s];
+    acc = fmaf(__bfloat162float(h4[s * W + k]), d, acc);
+    if (k == 0) {
+      sdy += d;
+      sl += (double)rr[s];
+    }
+  }
+  atomicAdd(&grad[OFF_W5 + k], acc);
+  if (k == 0) {
+    atomicAdd(&grad[OFF_B5], sdy);
+    atomicAdd(loss, sl);
+  }
+}
+
+// bias gradient: db[o] += sum_s dz[s][o]; one thread per output column, samples
+// strided over blocks
+__global__ void gl_mlp_bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* __restrict__ db,
+                                    int64_t n) {
+  int o = threadIdx.x;
+  float acc = 0.f;
+  for (int64_t s = blockIdx.x; s < n; s += gridDim.x) acc += __bfloat162float(dz[s * W + o]);
+  atomicAdd(&db[o], acc);
+}
+
+// input-layer weight gradient: dW1[k][o] += sum_s x[s][k] dz1[s][o]
+__global__ void gl_mlp_w1grad_kernel(const float* __restrict__ x, const __nv_bfloat16* __restrict__ dz1,
+                                     float* __restrict__ grad, int64_t n) {
+  int o = threadIdx.x;
+  float acc[NIN] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+    float d = __bfloat162float(dz1[s * W + o]);
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) acc[k] = fmaf(x[s * NIN + k], d, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) atomicAdd(&grad[OFF_W1 + k * W + o], acc[k]);
+}
+
+// Adam on the FP32 master parameters (bias-corrected), then refresh the BF16
+// operand copies: wt_l[o][i] = W_l[i][o] (forward), wk_l[i][o] = W_l[i][o] (backward).
+__global__ void gl_mlp_adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                                   float* __restrict__ m, float* __restrict__ v, float lr,
+                                   float b1, float b2, float eps, float c1, float c2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NPARAM) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.0f - b1) * gi;
+  float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void gl_mlp_cast_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ wt,
+                                   __nv_bfloat16* __restrict__ wk) {
+  // grid: 3 layers x 256 rows; thread o
+  int l = blockIdx.x / W, i = blockIdx.x % W, o = threadIdx.x;
+  float w = p[off_w(l + 2) + (int64_t)i * W + o];
+  __nv_bfloat16 b = __float2bfloat16(w);
+  wt[(int64_t)l * W * W + (int64_t)o * W + i] = b;
+  wk[(int64_t)l * W * W + (int64_t)i * W + o] = b;
+}
+
+constexpr size_t GEMM_SMEM = 131072 + 65536;
+constexpr size_t WGRAD_SMEM = 65536 + 65536;
+
+}  // namespace
+
+struct gl_mlp {
+  int device = 0;
+  int sms = 0;
+  float* p = nullptr;          // master parameters
+  float* g = nullptr;          // gradients
+  float* m = nullptr;          // Adam first moment
+  float* v = nullptr;          // Adam second moment
+  __nv_bfloat16* wt = nullptr; // [3][256][256] forward operands
+  __nv_bfloat16* wk = nullptr; // [3][256][256] backward operands
+  int64_t step = 0;
+  // activation workspace (grow-only)
+  int64_t cap = 0;
+  float* z = nullptr;          // [4][cap][256]
+  __nv_bfloat16* h = nullptr;  // [4][cap][256]
+  __nv_bfloat16* dz = nullptr; // [2][cap][256]
+  float* y = nullptr;          // [cap]
+  float* dy = nullptr;         // [cap]
+  float* rr = nullptr;         // [cap]
+  double* d_loss = nullptr;
+  int* d_status = nullptr;
+  bool attr_set = false;
+};
+
+namespace {
+
+int mlp_grow(gl_mlp* m, int64_t n) {
+  if (n <= m->cap) return GL_OK;
+  cudaFree(m->z);
+  cudaFree(m->h);
+  cudaFree(m->dz);
+  cudaFree(m->y);
+  cudaFree(m->dy);
+  cudaFree(m->rr);
+  m->z = nullptr;
+  m->h = nullptr;
+  m->dz = nullptr;
+  m->y = nullptr;
+  m->dy = nullptr;
+  m->rr = nullptr;
+  m->cap = 0;
+  int64_t c = n + n / 4 + TILE_M;
+  if (cudaMalloc(&m->z, (size_t)4 * c * W * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->h, (size_t)4 * c * W * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc(&m->dz, (size_t)2 * c * W * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc(&m->y, (size_t)c * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->dy, (size_t)c * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->rr, (size_t)c * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return GL_ENOMEM;
+  }
+  m->cap = c;
+  return GL_OK;
+}
+
+int mlp_attrs(gl_mlp* m) {
+  if (m->attr_set) return GL_OK;
+  if (cudaFuncSetAttribute(gl_mlp_gemm_kernel<EPI_FWD_TRAIN>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(gl_mlp_gemm_kernel<EPI_FWD_INFER>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(gl_mlp_gemm_kernel<EPI_BWD>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(gl_mlp_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)WGRAD_SMEM) != cudaSuccess)
+    return GL_ECUDA;
+  m->attr_set = true;
+  return GL_OK;
+}
+
+int grid_for(const gl_mlp* m, int64_t n) {
+  int64_t tiles = (n + TILE_M - 1) / TILE_M;
+  return (int)(tiles < m->sms ? tiles : m->sms);
+}
+
+bool dev_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice && a.device == device) || a.type == cudaMemoryTypeManaged;
+}
+
+// forward through all layers; train = keep pre-activations for backward
+int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cudaStream_t st) {
+  int rc = mlp_grow(m, n);
+  if (rc) return rc;
+  if ((rc = mlp_attrs(m))) return rc;
+  const int64_t cs = m->cap * W;
+  int64_t nth = n * W;
+  gl_mlp_in_kernel<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(x, m->p, train ? m->z : nullptr,
+                                                                  m->h, n);
+  for (int l = 2; l <= 4; ++l) {
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.a = m->h + (l - 2) * cs;
+    g.b = m->wt + (int64_t)(l - 2) * W * W;
+    g.bias = m->p + off_b(l);
+    g.zout = m->z + (l - 1) * cs;
+    g.hout = m->h + (l - 1) * cs;
+    g.n = n;
+    g.status = m->d_status;
+    if (train)
+      gl_mlp_gemm_kernel<EPI_FWD_TRAIN><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
+    else
+      gl_mlp_gemm_kernel<EPI_FWD_INFER><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
+  }
+  gl_mlp_out_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(m->h + 3 * cs, m->p, y, n);
+  return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gl_mlp_param_count(void) { return NPARAM; }
+
+int gl_mlp_create(gl_mlp** out, int device) {
+  if (!out) return GL_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return GL_EINVAL;
+  gl_mlp* m = new gl_mlp();
+  m->device = device;
+  size_t pb = (size_t)NPARAM * sizeof(float);
+  if (cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&m->p, pb) != cudaSuccess || cudaMalloc(&m->g, pb) != cudaSuccess ||
+      cudaMalloc(&m->m, pb) != cudaSuccess || cudaMalloc(&m->v, pb) != cudaSuccess ||
+      cudaMalloc(&m->wt, (size_t)3 * W * W * 2) != cudaSuccess ||
+      cudaMalloc(&m->wk, (size_t)3 * W * W * 2) != cudaSuccess ||
+      cudaMalloc(&m->d_loss, sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return GL_ENOMEM;
+  }
+  cudaMemset(m->p, 0, pb);
+  cudaMemset(m->g, 0, pb);
+  cudaMemset(m->m, 0, pb);
+  cudaMemset(m->v, 0, pb);
+  cudaMemset(m->d_status, 0, sizeof(int));
+  *out = m;
+  return GL_OK;
+}
+
+int gl_mlp_destroy(gl_mlp* m) {
+  if (!m) return GL_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  cudaFree(m->p);
+  cudaFree(m->g);
+  cudaFree(m->m);
+  cudaFree(m->v);
+  cudaFree(m->wt);
+  cudaFree(m->wk);
+  cudaFree(m->z);
+  cudaFree(m->h);
+  cudaFree(m->dz);
+  cudaFree(m->y);
+  cudaFree(m->dy);
+  cudaFree(m->rr);
+  cudaFree(m->d_loss);
+  cudaFree(m->d_status);
+  delete m;
+  return GL_OK;
+}
+
+int gl_mlp_set_params(gl_mlp* m, const float* p, int64_t n) {
+  if (!m || !p || n != NPARAM) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  if (cudaMemcpy(m->p, p, (size_t)NPARAM * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+    return GL_ECUDA;
+  gl_mlp_cast_kernel<<<3 * W, W>>>(m->p, m->wt, m->wk);
+  size_t pb = (size_t)NPARAM * sizeof(float);
+  cudaMemset(m->m, 0, pb);
+  cudaMemset(m->v, 0, pb);
+  m->step = 0;
+  return cudaDeviceSynchronize() == cudaSuccess ? GL_OK : GL_ECUDA;
+}
+
+int gl_mlp_get_params(gl_mlp* m, float* p, int64_t n) {
+  if (!m || !p || n != NPARAM) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  return cudaMemcpy(p, m->p, (size_t)NPARAM * sizeof(float), cudaMemcpyDefault) == cudaSuccess
+             ? GL_OK : GL_ECUDA;
+}
+
+int gl_mlp_get_grads(gl_mlp* m, float* g, int64_t n) {
+  if (!m || !g || n != NPARAM) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  return cudaMemcpy(g, m->g, (size_t)NPARAM * sizeof(float), cudaMemcpyDefault) == cudaSuccess
+             ? GL_OK : GL_ECUDA;
+}
+
+int gl_mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, void* stream) {
+  if (!m || n < 0 || (n > 0 && (!x || !y))) return GL_EINVAL;
+  if (n == 0) return GL_OK;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  if (!dev_ptr(x, m->device) || !dev_ptr(y, m->device)) return GL_EINVAL;
+  return mlp_forward(m, n, x, y, false, (cudaStream_t)stream);
+}
+
+int gl_mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, double* loss,
+                     void* stream) {
+  if (!m || n <= 0 || !x || !t) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  if (!dev_ptr(x, m->device) || !dev_ptr(t, m->device)) return GL_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = mlp_grow(m, n);
+  if (rc) return rc;
+  rc = mlp_forward(m, n, x, m->y, true, st);
+  if (rc) return rc;
+  const int64_t cs = m->cap * W;
+  cudaMemsetAsync(m->g, 0, (size_t)NPARAM * sizeof(float), st);
+  cudaMemsetAsync(m->d_loss, 0, sizeof(double), st);
+  __nv_bfloat16* dzA = m->dz;
+  __nv_bfloat16* dzB = m->dz + cs;
+  int bgrid = (int)(n < 1024 ? n : 1024);
+  gl_mlp_outgrad_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
+      m->z + 3 * cs, m->y, t, m->p, m->dy, m->rr, dzA, n);
+  gl_mlp_outred_kernel<<<bgrid, W, 0, st>>>(m->h + 3 * cs, m->dy, m->rr, m->g, m->d_loss, n);
+  for (int l = 4; l >= 2; --l) {
+    // bias and weight gradients of layer l from dz_l (in dzA)
+    gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->g + off_b(l), n);
+    WgradArgs wg;
+    wg.a = m->h + (l - 2) * cs;
+    wg.dz = dzA;
+    wg.dw = m->g + off_w(l);
+    wg.n = n;
+    wg.status = m->d_status;
+    gl_mlp_wgrad_kernel<<<grid_for(m, n), NTHREADS, WGRAD_SMEM, st>>>(wg);
+    // dz_{l-1} = (dz_l W_l^T) * SiLU'(z_{l-1})
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.a = dzA;
+    g.b = m->wk + (int64_t)(l - 2) * W * W;
+    g.zprev = m->z + (l - 2) * cs;
+    g.hout = dzB;
+    g.n = n;
+    g.status = m->d_status;
+    gl_mlp_gemm_kernel<EPI_BWD><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
+    __nv_bfloat16* tmp = dzA;
+    dzA = dzB;
+    dzB = tmp;
+  }
+  // layer 1 from dz_1 (in dzA)
+  gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->g + OFF_B1, n);
+  gl_mlp_w1grad_kernel<<<bgrid, W, 0, st>>>(x, dzA, m->g, n);
+  if (cudaGetLastError() != cudaSuccess) return GL_ECUDA;
+  if (loss) {
+    if (cudaMemcpyAsync(loss, m->d_loss, sizeof(double), cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return GL_ECUDA;
+  }
+  return GL_OK;
+}
+
+int gl_mlp_adam(gl_mlp* m, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!m || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps > 0.f))
+    return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  m->step++;
+  float c1 = 1.0f - powf(beta1, (float)m->step), c2 = 1.0f - powf(beta2, (float)m->step);
+  gl_mlp_adam_kernel<<<(unsigned)((NPARAM + 255) / 256), 256, 0, st>>>(m->p, m->g, m->m, m->v, lr,
+                                                                       beta1, beta2, eps, c1, c2);
+  gl_mlp_cast_kernel<<<3 * W, W, 0, st>>>(m->p, m->wt, m->wk);
+  return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
+}
+
+int gl_mlp_status(gl_mlp* m) {
+  if (!m) return GL_EINVAL;
+  int h = 0;
+  if (cudaMemcpy(&h, m->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GL_ECUDA;
+  cudaMemset(m->d_status, 0, sizeof(int));
+  return h ? GL_ETIMEOUT : GL_OK;
+}
+
+}  // extern "C"
