@@ -285,6 +285,51 @@ int gl_mlp_adam(gl_mlp *m, float lr, float beta1, float beta2, float eps, void *
 int gl_mlp_status(gl_mlp *m);
 
 /* ------------------------------------------------------------------------
+ * Surrogate light curves (not in the paper).  For every sub-exposure whose
+ * planet overlaps the star, the deficit is the spherical planet's of equal
+ * projected area (radius sqrt(dx dy2), gl_flux_sphere arithmetic, FP32) minus
+ * the network's predicted oblate-minus-spherical residual times R_eq^2.  Seven
+ * features feed the network: the centre distance rho, the angle between the
+ * projected spin axis and the radial direction folded into [0, pi/2], k, f,
+ * cos(eta) and Kipping's q1 = (u1+u2)^2, q2 = u1/(2 (u1+u2)), each scaled to
+ * about [-1, 1].  A sub-exposure whose error bound, bound_table[bin] x R_eq^2,
+ * exceeds bound_limit is recomputed by the exact FP32C path.  Bins (16): 8
+ * equal bins of k over [0.01, 0.2] (clamped), for sub-exposures with the whole
+ * ellipse on the disk (bins 0-7) and with crossings (8-15).  bound_table is 16
+ * floats, host or device.  Geometry and orbit as in gl_lightcurve_batch (FP64
+ * Kepler, FP64 exposure sum).
+ * Device buffers only; nsuper must be uniform (tm->nsuper NULL).  Synchronises
+ * `stream` (to size the network pass).  The context keeps a workspace of about
+ * 60 bytes per sub-exposure of the batch.  stats may be NULL. */
+typedef struct {
+  int64_t items;      /* sub-exposures of in-window exposures */
+  int64_t exposures;  /* in-window exposures */
+  int64_t fallback;   /* sub-exposures recomputed exactly */
+} gl_surrogate_stats;
+
+int gl_lightcurve_surrogate(gl_context *ctx, gl_mlp *mlp, const gl_params *p,
+                            const gl_times *t, double *out, const float *bound_table,
+                            double bound_limit, void *stream, gl_surrogate_stats *stats);
+
+/* Training data of the surrogate (device arrays, n entries): the seven features
+ * (feat, n x 7 FP32), scale = R_eq^2 (FP32), the equal-area radius (FP64) and
+ * the error-table bin (int32; -1 when the planet does not overlap the star) for
+ * sky positions (x0, y0) and shapes (k, f, eta, xi, u1, u2). */
+int gl_surrogate_features(gl_context *ctx, int64_t n, const double *x0, const double *y0,
+                          const double *k, const double *f, const double *eta, const double *xi,
+                          const double *u1, const double *u2, float *feat, float *scale,
+                          double *r_area, int32_t *bin, void *stream);
+/* t = (f_oblate - f_sphere) / scale (0 where scale is 0). */
+int gl_surrogate_targets(gl_context *ctx, int64_t n, const double *f_oblate,
+                         const double *f_sphere, const float *scale, float *t, void *stream);
+
+/* Gaussian log-likelihood of n_sets light curves against one data set:
+ * loglike[s] = -1/2 sum_j ((flux[s][j] - data[j]) / sigma[j])^2 (constant terms
+ * dropped).  flux n_sets x n_times, data and sigma n_times, all device memory. */
+int gl_loglike(gl_context *ctx, int64_t n_sets, int64_t n_times, const double *flux,
+               const double *data, const double *sigma, double *loglike, void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free variant of gl_lightcurve_batch.  The paper has no
  * counterpart: this is a deployment aid.
  *

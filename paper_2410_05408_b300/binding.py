@@ -32,7 +32,10 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_counts_read", "gl_graphs_enable", "gl_graph_launches", "gl_autotune",
             "gl_flux_sphere", "gl_mlp_param_count", "gl_mlp_create", "gl_mlp_destroy",
             "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
-            "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status")
+            "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
+            "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike")
+
+SUR_BINS = 16
 
 COUNT_NAMES = ("exposures", "kept", "in_window", "kepler", "items", "item_kepler", "full",
                "partial")
@@ -62,6 +65,11 @@ class _TuneReport(ctypes.Structure):
                 ("ms", ctypes.c_double), ("default_ms", ctypes.c_double),
                 ("max_abs_err", ctypes.c_double), ("candidates", ctypes.c_int),
                 ("admissible", ctypes.c_int)]
+
+
+class _SurStats(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int64), ("exposures", ctypes.c_int64),
+                ("fallback", ctypes.c_int64)]
 
 
 class _Times(ctypes.Structure):
@@ -97,6 +105,16 @@ def load():
         lib.gl_lightcurve_batch.restype = i32
         lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
         lib.gl_flux_sky.restype = i32
+        lib.gl_lightcurve_surrogate.argtypes = [vp, vp, ctypes.POINTER(_Params),
+                                                ctypes.POINTER(_Times), vp, vp, ctypes.c_double,
+                                                vp, ctypes.POINTER(_SurStats)]
+        lib.gl_lightcurve_surrogate.restype = i32
+        lib.gl_surrogate_features.argtypes = [vp, i64] + [vp] * 12 + [vp]
+        lib.gl_surrogate_features.restype = i32
+        lib.gl_surrogate_targets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        lib.gl_surrogate_targets.restype = i32
+        lib.gl_loglike.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+        lib.gl_loglike.restype = i32
         lib.gl_mlp_param_count.argtypes = []
         lib.gl_mlp_param_count.restype = i64
         lib.gl_mlp_create.argtypes = [ctypes.POINTER(vp), i32]
@@ -270,6 +288,47 @@ def gl_flux_sphere(ctx, x0, y0, z, p, u1, u2, out, precision: int = GL_FP32C, st
     if check:
         _check(ctx, rc)
     return rc
+
+
+def gl_lightcurve_surrogate(ctx, mlp, params: dict, t, out, bound_table, bound_limit: float,
+                            exptime=None, nsuper_all: int = 1, offsets=None, stream=None) -> dict:
+    """Surrogate light curves (device buffers, uniform nsuper); returns the stats."""
+    lib = load()
+    n_sets = int(len(params["t0"]))
+    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"),
+                0 if offsets is not None else int(len(t)), int(len(out)),
+                _ptr(exptime, "float64"), None, int(nsuper_all))
+    st = _SurStats()
+    _check(ctx, lib.gl_lightcurve_surrogate(ctx, mlp.handle, ctypes.byref(p), ctypes.byref(tm),
+                                            _ptr(out, "float64"), _ptr(bound_table, "float32"),
+                                            float(bound_limit), _stream_ptr(stream),
+                                            ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def gl_surrogate_features(ctx, x0, y0, k, f, eta, xi, u1, u2, feat, scale, r_area, bins,
+                          stream=None):
+    lib = load()
+    _check(ctx, lib.gl_surrogate_features(
+        ctx, int(len(x0)), *[_ptr(a, "float64") for a in (x0, y0, k, f, eta, xi, u1, u2)],
+        _ptr(feat, "float32"), _ptr(scale, "float32"), _ptr(r_area, "float64"),
+        _ptr(bins, "int32"), _stream_ptr(stream)))
+
+
+def gl_surrogate_targets(ctx, f_oblate, f_sphere, scale, t, stream=None):
+    lib = load()
+    _check(ctx, lib.gl_surrogate_targets(ctx, int(len(t)), _ptr(f_oblate, "float64"),
+                                         _ptr(f_sphere, "float64"), _ptr(scale, "float32"),
+                                         _ptr(t, "float32"), _stream_ptr(stream)))
+
+
+def gl_loglike(ctx, flux, data, sigma, loglike, stream=None):
+    lib = load()
+    n_sets, n_times = int(len(loglike)), int(len(data))
+    _check(ctx, lib.gl_loglike(ctx, n_sets, n_times, _ptr(flux, "float64"),
+                               _ptr(data, "float64"), _ptr(sigma, "float64"),
+                               _ptr(loglike, "float64"), _stream_ptr(stream)))
 
 
 def gl_q_to_u(q1, q2):

@@ -29,7 +29,7 @@ using gl::SetConst;
 namespace {
 
 // status bits accumulated on the device
-enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4 };
+enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4, kStatusOverflow = 8 };
 
 // quadrature orders: FP64 path and FP32C path
 constexpr int kNodes64 = 32;
@@ -458,6 +458,332 @@ __global__ void __launch_bounds__(256) gl_sphere_kernel(SpherePtrs a, int64_t n,
   }
 }
 
+// ------------------------------------------------------------------ surrogate path
+// Collect kernel: the exposure window, exact window and sub-exposure geometry of
+// the FP32C light-curve kernel, but instead of integrating it writes every
+// sub-exposure of an in-window exposure to global item arrays (position, 1 - r^2,
+// set, class) and one record per exposure (output index, nsuper, first item).
+// Items of an exposure are contiguous.  Exposures outside the window get flux 1
+// at once.  One CTA per tile of exposures (atomic tile counter).
+struct CollectArgs {
+  const SetConst* sets;
+  const double* t;
+  const int64_t* offsets;
+  int64_t n_times, n_sets, n_total;
+  double* out;
+  unsigned int* tile_counter;
+  int n_tiles, tile;
+  float *ix, *iy, *io;      // item geometry
+  int *iset, *icls;         // item set and class (gl::kOut / kFull / kPartial)
+  int64_t item_cap;
+  unsigned long long* n_items;
+  int *rj, *rns, *rfirst;   // exposure records
+  int64_t rec_cap;
+  unsigned long long* n_recs;
+  int* status;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) gl_collect_kernel(CollectArgs a) {
+  __shared__ int warp_tot[32];
+  __shared__ int s_tile;
+  __shared__ long long s_first, s_item_base, s_rec_base;
+  __shared__ int e_j[NT], e_s[NT], e_ns[NT], e_base[NT + 1], e_flag[NT];
+  __shared__ double e_tau[NT];
+  __shared__ gl::MidState e_mid[NT];
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_tile = (int)atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= a.n_tiles) break;
+    const int64_t j0 = (int64_t)tile * a.tile;
+    if (a.offsets && tid == 0) s_first = owner_of(a.offsets, a.n_sets, j0);
+    __syncthreads();
+    int keep = 0, my_s = 0, my_ns = 0;
+    double my_t = 0.0;
+    int64_t j = j0 + tid;
+    if (tid < a.tile && j < a.n_total) {
+      int64_t ti;
+      if (a.offsets) {
+        int64_t s = s_first;
+        while (s + 1 < a.n_sets && a.offsets[s + 1] <= j) ++s;
+        my_s = (int)s;
+        ti = j;
+      } else {
+        my_s = (int)((unsigned)j / (unsigned)a.n_times);
+        ti = j - (int64_t)my_s * a.n_times;
+      }
+      const SetConst& c = a.sets[my_s];
+      my_t = a.t[ti];
+      if (c.flags & gl::kSetInvalid) {
+        a.out[j] = __longlong_as_double(0x7ff8000000000000LL);
+      } else if (gl::window_maybe(c, my_t)) {
+        double tau = gl::wrap_tau(c, my_t);
+        if (gl::in_window(c, tau, 0.5 * c.exptime)) {
+          keep = 1;
+          my_ns = c.nsuper;
+          my_t = tau;
+        } else {
+          a.out[j] = 1.0;
+        }
+      } else {
+        a.out[j] = 1.0;
+      }
+    }
+    int m;
+    int slot = block_scan<NT>(keep, warp_tot, &m);
+    if (keep) {
+      e_j[slot] = (int)j;
+      e_s[slot] = my_s;
+      e_ns[slot] = my_ns;
+      e_tau[slot] = my_t;
+    }
+    __syncthreads();
+    if (m == 0) continue;
+    int M;
+    int base = block_scan<NT>(tid < m ? e_ns[tid] : 0, warp_tot, &M);
+    if (tid < m) e_base[tid] = base;
+    if (tid == 0) {
+      e_base[m] = M;
+      s_item_base = (long long)atomicAdd(a.n_items, (unsigned long long)M);
+      s_rec_base = (long long)atomicAdd(a.n_recs, (unsigned long long)m);
+    }
+    for (int i = tid; i < m; i += NT) {
+      const SetConst& c = a.sets[e_s[i]];
+      int fl = 0;
+      if (c.flags & gl::kSetTaylor) {
+        gl::SkyState st;
+        gl::sky_state(c, e_tau[i], &st);
+        e_mid[i] = gl::mid_state(st);
+        fl = kExpTaylor;
+      }
+      e_flag[i] = fl;
+    }
+    __syncthreads();
+    const long long ib = s_item_base, rb = s_rec_base;
+    if (ib + M > a.item_cap || rb + m > a.rec_cap) {
+      if (tid == 0) atomicOr(a.status, kStatusOverflow);
+      for (int i = tid; i < m; i += NT) a.out[e_j[i]] = __longlong_as_double(0x7ff8000000000000LL);
+      __syncthreads();
+      continue;
+    }
+    for (int it = tid; it < M; it += NT) {
+      int lo = 0, hi = m;
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (e_base[mid] <= it) lo = mid; else hi = mid;
+      }
+      const int i = lo, q = it - e_base[i];
+      const SetConst& c = a.sets[e_s[i]];
+      const int twice = 2 * q + 1 - e_ns[i];
+      float x, y, o;
+      int cls;
+      if (e_flag[i] & kExpTaylor) {
+        float zf;
+        gl::taylor_position(e_mid[i], 0.5f * (float)twice * c.fsub_step, &x, &y, &zf, &o);
+        cls = gl::classify_t<float>(c.freq, x, y, zf, 1e-6f);
+      } else {
+        double xd, yd, zd;
+        gl::sky_position(c, e_tau[i] + 0.5 * (double)twice * c.sub_step, &xd, &yd, &zd);
+        cls = gl::classify(c, xd, yd, zd);
+        x = (float)xd;
+        y = (float)yd;
+        o = (float)((1.0 - xd) * (1.0 + xd) - yd * yd);
+      }
+      a.ix[ib + it] = x;
+      a.iy[ib + it] = y;
+      a.io[ib + it] = o;
+      a.iset[ib + it] = e_s[i];
+      a.icls[ib + it] = cls;
+    }
+    for (int i = tid; i < m; i += NT) {
+      a.rj[rb + i] = e_j[i];
+      a.rns[rb + i] = e_ns[i];
+      a.rfirst[rb + i] = (int)(ib + e_base[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// Surrogate inputs of one item: seven features scaled to about [-1, 1]
+//   rho = |centre|, psi = angle between the projected spin axis and the radial
+//   direction folded into [0, pi/2] (the flux is unchanged by a half turn of the
+//   ellipse and by reflection about the radial line), k, f, cos(eta), and the
+//   Kipping coordinates q1 = (u1 + u2)^2, q2 = u1 / (2 (u1 + u2));
+// and the equal-area sphere radius R_area = sqrt(dx dy2), scale = R_eq^2.
+struct SurFeat {
+  float f[7];
+  float r_area, scale;
+};
+__device__ __forceinline__ SurFeat sur_features(double x0, double y0, double k, double f,
+                                                double ce, double xi, double u1, double u2,
+                                                double dx, double dy2, double req) {
+  SurFeat o;
+  double rho = sqrt(x0 * x0 + y0 * y0);
+  double ang = -xi - atan2(y0, x0);
+  double psi = ang - gl::kPi * floor(ang / gl::kPi);      // [0, pi)
+  if (psi > 0.5 * gl::kPi) psi = gl::kPi - psi;           // [0, pi/2]
+  double s = u1 + u2;
+  double q1 = s * s, q2 = s > 0.0 ? u1 / (2.0 * s) : 0.0;
+  o.f[0] = (float)(rho / 0.85 - 1.0);
+  o.f[1] = (float)(psi * (4.0 / gl::kPi) - 1.0);
+  o.f[2] = (float)((k - 0.105) / 0.095);
+  o.f[3] = (float)((f - 0.45) / 0.45);
+  o.f[4] = (float)(2.0 * ce - 1.0);
+  o.f[5] = (float)(2.0 * q1 - 1.0);
+  o.f[6] = (float)(2.0 * q2 - 1.0);
+  o.r_area = (float)sqrt(dx * dy2);
+  o.scale = (float)(req * req);
+  return o;
+}
+
+constexpr int kSurBins = 16;
+__device__ __forceinline__ int sur_bin(int cls, double k) {
+  int kb = (int)floor((k - 0.01) / (0.19 / 8.0));
+  kb = kb < 0 ? 0 : (kb > 7 ? 7 : kb);
+  return (cls == gl::kPartial ? 8 : 0) + kb;
+}
+
+// features, scale and the FP32 sphere deficit of every collected item
+__global__ void gl_sur_features_kernel(const SetConst* __restrict__ sets, const ParamPtrs pp,
+                                       const float* __restrict__ ix, const float* __restrict__ iy,
+                                       const float* __restrict__ io, const int* __restrict__ iset,
+                                       const int* __restrict__ icls,
+                                       const unsigned long long* __restrict__ n_items,
+                                       float* __restrict__ feat, float* __restrict__ scale,
+                                       float* __restrict__ dsph) {
+  const int64_t n = (int64_t)*n_items;
+  const NodeRule<float>& rl = rule<float>();
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    if (icls[it] == gl::kOut) {
+      for (int q = 0; q < 7; ++q) feat[it * 7 + q] = 0.f;
+      scale[it] = 0.f;
+      dsph[it] = 0.f;
+      continue;
+    }
+    const int s = iset[it];
+    const SetConst& c = sets[s];
+    double x = ix[it], y = iy[it];
+    SurFeat sf = sur_features(x, y, pp.k[s], pp.f[s], cos(pp.eta[s]), pp.xi[s], pp.u1[s], pp.u2[s],
+                              c.dx, c.dy2, c.req);
+    for (int q = 0; q < 7; ++q) feat[it * 7 + q] = sf.f[q];
+    scale[it] = sf.scale;
+    float I[3];
+    float rho = sqrtf(ix[it] * ix[it] + iy[it] * iy[it]);
+    gl::sphere_moments<float>(rho, sf.r_area, io[it], rl, I);   // io = 1 - rho^2
+    dsph[it] = (c.fc0 * I[0] + c.fc1 * I[1] + c.fc2 * I[2]) * c.finvF0;
+  }
+}
+
+// deficit = sphere deficit - predicted residual * scale; the items whose error
+// bound (table[bin] * scale) exceeds the limit are queued for the exact path
+__global__ void gl_sur_combine_kernel(const SetConst* __restrict__ sets,
+                                      const double* __restrict__ kk, const int* __restrict__ iset,
+                                      const int* __restrict__ icls,
+                                      const unsigned long long* __restrict__ n_items,
+                                      const float* __restrict__ that, const float* __restrict__ scale,
+                                      const float* __restrict__ dsph, const float* __restrict__ table,
+                                      float limit, float* __restrict__ def, int* __restrict__ fb,
+                                      unsigned long long* __restrict__ n_fb) {
+  const int64_t n = (int64_t)*n_items;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    int cls = icls[it];
+    if (cls == gl::kOut) {
+      def[it] = 0.f;
+      continue;
+    }
+    float sc = scale[it];
+    def[it] = dsph[it] - that[it] * sc;
+    float bound = table[sur_bin(cls, kk[iset[it]])] * sc;
+    if (!(bound <= limit)) fb[atomicAdd(n_fb, 1ull)] = (int)it;
+  }
+}
+
+// exact FP32C deficit for the queued items
+__global__ void gl_sur_fallback_kernel(const SetConst* __restrict__ sets, const float* __restrict__ ix,
+                                       const float* __restrict__ iy, const float* __restrict__ io,
+                                       const int* __restrict__ iset, const int* __restrict__ icls,
+                                       const int* __restrict__ fb,
+                                       const unsigned long long* __restrict__ n_fb,
+                                       float* __restrict__ def) {
+  const int64_t n = (int64_t)*n_fb;
+  const NodeRule<float>& rl = rule<float>();
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int it = fb[u];
+    const SetConst& c = sets[iset[it]];
+    float I[3];
+    gl::occulted_r<float>(c, ix[it], iy[it], io[it], icls[it], rl, I);
+    def[it] = (c.fc0 * I[0] + c.fc1 * I[1] + c.fc2 * I[2]) * c.finvF0;
+  }
+}
+
+// exposure flux = mean over its sub-exposures of 1 - deficit (FP64, item order)
+__global__ void gl_sur_reduce_kernel(const int* __restrict__ rj, const int* __restrict__ rns,
+                                     const int* __restrict__ rfirst,
+                                     const unsigned long long* __restrict__ n_recs,
+                                     const float* __restrict__ def, double* __restrict__ out) {
+  const int64_t n = (int64_t)*n_recs;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int f0 = rfirst[r], ns = rns[r];
+    double acc = 0.0;
+    for (int q = 0; q < ns; ++q) acc += 1.0 - (double)def[f0 + q];
+    out[rj[r]] = acc / ns;
+  }
+}
+
+// training data: features from sky positions and shapes
+__global__ void gl_sur_geom_features_kernel(int64_t n, const double* x0, const double* y0,
+                                            const double* k, const double* f, const double* eta,
+                                            const double* xi, const double* u1, const double* u2,
+                                            float* feat, float* scale, double* r_area, int* bin) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    SetConst c;
+    gl::set_setup(0.0, 1.0, 10.0, 0.0, 0.0, 0.0, k[i], f[i], eta[i], xi[i], u1[i], u2[i], 0.0, 1, &c);
+    SurFeat sf = sur_features(x0[i], y0[i], k[i], f[i], cos(eta[i]), xi[i], u1[i], u2[i], c.dx,
+                              c.dy2, c.req);
+    for (int q = 0; q < 7; ++q) feat[i * 7 + q] = sf.f[q];
+    scale[i] = sf.scale;
+    r_area[i] = sqrt(c.dx * c.dy2);
+    int cls = gl::classify(c, x0[i], y0[i], -1.0);
+    bin[i] = cls == gl::kOut ? -1 : sur_bin(cls, k[i]);
+  }
+}
+
+// training targets: (F_oblate - F_sphere) / scale
+__global__ void gl_sur_targets_kernel(int64_t n, const double* fo, const double* fs,
+                                      const float* scale, float* t) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    t[i] = scale[i] > 0.f ? (float)((fo[i] - fs[i]) / (double)scale[i]) : 0.f;
+}
+
+// log-likelihood per set: -chi^2 / 2 with chi^2 = sum_j ((flux_j - data_j) / sigma_j)^2
+__global__ void gl_loglike_kernel(int64_t n_sets, int64_t n_times, const double* __restrict__ flux,
+                                  const double* __restrict__ data, const double* __restrict__ sigma,
+                                  double* __restrict__ ll) {
+  int64_t s = blockIdx.x;
+  if (s >= n_sets) return;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < n_times; j += blockDim.x) {
+    double r = (flux[s * n_times + j] - data[j]) / sigma[j];
+    acc += r * r;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ll[s] = -0.5 * red[0];
+}
+
 struct SkyPtrs {
   const double *x0, *y0, *z, *k, *f, *eta, *xi, *u1, *u2;
 };
@@ -563,6 +889,13 @@ struct gl_context {
     int tuned = 0, candidates = 0, admissible = 0;
     double best_ms = 0, default_ms = 0, max_err = 0;
   } tune[2];
+  // surrogate path workspace (grow-only)
+  int64_t sur_cap = 0, sur_rec_cap = 0;
+  float *sx = nullptr, *sy = nullptr, *so = nullptr, *sfeat = nullptr, *sscale = nullptr;
+  float *sdsph = nullptr, *sthat = nullptr, *sdef = nullptr, *stable = nullptr;
+  int *sset = nullptr, *scls = nullptr, *sfb = nullptr, *srj = nullptr, *srns = nullptr,
+      *srfirst = nullptr;
+  unsigned long long* scount = nullptr;   // items, records, fallback
   double* d_ref = nullptr;             // autotuner: FP64 reference output
   size_t ref_cap = 0;
   double* d_err = nullptr;             // autotuner: max |difference| slot
@@ -877,6 +1210,11 @@ int gl_context_destroy(gl_context* ctx) {
   if (ctx->d_counter) cudaFree(ctx->d_counter);
   if (ctx->d_counts) cudaFree(ctx->d_counts);
   if (ctx->d_ref) cudaFree(ctx->d_ref);
+  for (void* q : {(void*)ctx->sx, (void*)ctx->sy, (void*)ctx->so, (void*)ctx->sfeat,
+                  (void*)ctx->sscale, (void*)ctx->sdsph, (void*)ctx->sthat, (void*)ctx->sdef,
+                  (void*)ctx->stable, (void*)ctx->sset, (void*)ctx->scls, (void*)ctx->sfb,
+                  (void*)ctx->srj, (void*)ctx->srns, (void*)ctx->srfirst, (void*)ctx->scount})
+    if (q) cudaFree(q);
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (auto& g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1207,6 +1545,195 @@ int gl_flux_sphere(gl_context* ctx, int64_t n, const double* x0, const double* y
   GL_CUDA(ctx, cudaGetLastError());
   if (out_host) GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, b, cudaMemcpyDeviceToHost, st));
   if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
+  return GL_OK;
+}
+
+int gl_surrogate_features(gl_context* ctx, int64_t n, const double* x0, const double* y0,
+                          const double* k, const double* f, const double* eta, const double* xi,
+                          const double* u1, const double* u2, float* feat, float* scale,
+                          double* r_area, int32_t* bin, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n < 0) return fail(ctx, GL_EINVAL, "n < 0");
+  if (n == 0) return GL_OK;
+  const void* ptrs[12] = {x0, y0, k, f, eta, xi, u1, u2, feat, scale, r_area, bin};
+  for (const void* q : ptrs)
+    if (!q || !is_device_ptr(q, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  gl_sur_geom_features_kernel<<<launch_grid(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      n, x0, y0, k, f, eta, xi, u1, u2, feat, scale, r_area, bin);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+int gl_surrogate_targets(gl_context* ctx, int64_t n, const double* f_oblate,
+                         const double* f_sphere, const float* scale, float* t, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n < 0) return fail(ctx, GL_EINVAL, "n < 0");
+  if (n == 0) return GL_OK;
+  const void* ptrs[4] = {f_oblate, f_sphere, scale, t};
+  for (const void* q : ptrs)
+    if (!q || !is_device_ptr(q, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  gl_sur_targets_kernel<<<launch_grid(n, 256), 256, 0, (cudaStream_t)stream>>>(n, f_oblate, f_sphere,
+                                                                                scale, t);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+int gl_loglike(gl_context* ctx, int64_t n_sets, int64_t n_times, const double* flux,
+               const double* data, const double* sigma, double* loglike, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n_sets < 0 || n_times < 0) return fail(ctx, GL_EINVAL, "negative size");
+  if (n_sets == 0) return GL_OK;
+  const void* ptrs[4] = {flux, data, sigma, loglike};
+  for (const void* q : ptrs)
+    if (!q || !is_device_ptr(q, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (n_sets > 2147483647LL) return fail(ctx, GL_EINVAL, "too many sets");
+  gl_loglike_kernel<<<(unsigned)n_sets, 256, 0, (cudaStream_t)stream>>>(n_sets, n_times, flux, data,
+                                                                        sigma, loglike);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+int gl_lightcurve_surrogate(gl_context* ctx, gl_mlp* mlp, const gl_params* p, const gl_times* tm,
+                            double* out, const float* bound_table, double bound_limit,
+                            void* stream, gl_surrogate_stats* stats) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (!mlp || !p || !tm || !out || !bound_table) return fail(ctx, GL_EINVAL, "NULL argument");
+  int64_t n_sets = p->n_sets, n_total = tm->n_total;
+  if (n_sets < 0 || n_total < 0 || n_total >= (1LL << 31)) return fail(ctx, GL_EINVAL, "bad sizes");
+  if (tm->nsuper || tm->nsuper_all < 1) return fail(ctx, GL_EINVAL, "needs a uniform nsuper_all");
+  if (!tm->offsets && n_total != n_sets * tm->n_times) return fail(ctx, GL_EINVAL, "n_total");
+  if (stats) memset(stats, 0, sizeof *stats);
+  if (n_sets == 0 || n_total == 0) return GL_OK;
+  const double* arr[15] = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
+                           p->eta, p->xi, p->u1, p->u2, tm->t, tm->exptime, out};
+  for (const double* q : arr)
+    if (!q || !is_device_ptr(q, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host array");
+  if (tm->offsets && !is_device_ptr(tm->offsets, ctx->device))
+    return fail(ctx, GL_EINVAL, "host offsets");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = grow(ctx, (void**)&ctx->d_sets, &ctx->sets_cap, (size_t)n_sets * sizeof(SetConst));
+  if (rc) return rc;
+  const int64_t items = n_total * (int64_t)tm->nsuper_all;
+  if (items > ctx->sur_cap || n_total > ctx->sur_rec_cap) {
+    for (void* q : {(void*)ctx->sx, (void*)ctx->sy, (void*)ctx->so, (void*)ctx->sfeat,
+                    (void*)ctx->sscale, (void*)ctx->sdsph, (void*)ctx->sthat, (void*)ctx->sdef,
+                    (void*)ctx->sset, (void*)ctx->scls, (void*)ctx->sfb, (void*)ctx->srj,
+                    (void*)ctx->srns, (void*)ctx->srfirst})
+      if (q) cudaFree(q);
+    ctx->sur_cap = ctx->sur_rec_cap = 0;
+    size_t fi = (size_t)items * sizeof(float), ii = (size_t)items * sizeof(int);
+    size_t ri = (size_t)n_total * sizeof(int);
+    bool ok = cudaMalloc(&ctx->sx, fi) == cudaSuccess && cudaMalloc(&ctx->sy, fi) == cudaSuccess &&
+              cudaMalloc(&ctx->so, fi) == cudaSuccess &&
+              cudaMalloc(&ctx->sfeat, 7 * fi) == cudaSuccess &&
+              cudaMalloc(&ctx->sscale, fi) == cudaSuccess &&
+              cudaMalloc(&ctx->sdsph, fi) == cudaSuccess &&
+              cudaMalloc(&ctx->sthat, fi) == cudaSuccess &&
+              cudaMalloc(&ctx->sdef, fi) == cudaSuccess && cudaMalloc(&ctx->sset, ii) == cudaSuccess &&
+              cudaMalloc(&ctx->scls, ii) == cudaSuccess && cudaMalloc(&ctx->sfb, ii) == cudaSuccess &&
+              cudaMalloc(&ctx->srj, ri) == cudaSuccess && cudaMalloc(&ctx->srns, ri) == cudaSuccess &&
+              cudaMalloc(&ctx->srfirst, ri) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return fail(ctx, GL_ENOMEM, "surrogate workspace of %lld items", (long long)items);
+    }
+    ctx->sur_cap = items;
+    ctx->sur_rec_cap = n_total;
+  }
+  if (!ctx->scount) GL_CUDA(ctx, cudaMalloc(&ctx->scount, 3 * sizeof(unsigned long long)));
+  if (!ctx->stable) GL_CUDA(ctx, cudaMalloc(&ctx->stable, kSurBins * sizeof(float)));
+  GL_CUDA(ctx, cudaMemcpyAsync(ctx->stable, bound_table, kSurBins * sizeof(float), cudaMemcpyDefault, st));
+  GL_CUDA(ctx, cudaMemsetAsync(ctx->scount, 0, 3 * sizeof(unsigned long long), st));
+  GL_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), st));
+  ParamPtrs pp;
+  memset(&pp, 0, sizeof pp);
+  pp.t0 = p->t0;
+  pp.period = p->period;
+  pp.a_rs = p->a_rs;
+  pp.b = p->b;
+  pp.ecc = p->ecc;
+  pp.omega = p->omega;
+  pp.k = p->k;
+  pp.f = p->f;
+  pp.eta = p->eta;
+  pp.xi = p->xi;
+  pp.u1 = p->u1;
+  pp.u2 = p->u2;
+  pp.exptime = tm->exptime;
+  pp.nsuper_all = tm->nsuper_all;
+  gl_setup_kernel<<<(int)((n_sets + 7) / 8), 32, 0, st>>>(pp, n_sets, tm->offsets, n_total,
+                                                          ctx->d_sets, ctx->d_status);
+  CollectArgs ca;
+  memset(&ca, 0, sizeof ca);
+  ca.sets = ctx->d_sets;
+  ca.t = tm->t;
+  ca.offsets = tm->offsets;
+  ca.n_times = tm->n_times;
+  ca.n_sets = n_sets;
+  ca.n_total = n_total;
+  ca.out = out;
+  ca.tile_counter = ctx->d_counter;
+  ca.tile = 256;
+  ca.n_tiles = (int)((n_total + 255) / 256);
+  ca.ix = ctx->sx;
+  ca.iy = ctx->sy;
+  ca.io = ctx->so;
+  ca.iset = ctx->sset;
+  ca.icls = ctx->scls;
+  ca.item_cap = ctx->sur_cap;
+  ca.n_items = ctx->scount;
+  ca.rj = ctx->srj;
+  ca.rns = ctx->srns;
+  ca.rfirst = ctx->srfirst;
+  ca.rec_cap = ctx->sur_rec_cap;
+  ca.n_recs = ctx->scount + 1;
+  ca.status = ctx->d_status;
+  int grid = ctx->sms * 4;
+  if (grid > ca.n_tiles) grid = ca.n_tiles;
+  gl_collect_kernel<256><<<grid, 256, 0, st>>>(ca);
+  ctx->launches += 2;
+  GL_CUDA(ctx, cudaGetLastError());
+  unsigned long long cnt[3] = {0, 0, 0};
+  GL_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->scount, sizeof cnt, cudaMemcpyDeviceToHost, st));
+  GL_CUDA(ctx, cudaStreamSynchronize(st));
+  const int64_t n_items = (int64_t)cnt[0];
+  if (n_items > 0) {
+    int g2 = launch_grid(n_items, 256);
+    gl_sur_features_kernel<<<g2, 256, 0, st>>>(ctx->d_sets, pp, ctx->sx, ctx->sy, ctx->so, ctx->sset,
+                                               ctx->scls, ctx->scount, ctx->sfeat, ctx->sscale,
+                                               ctx->sdsph);
+    GL_CUDA(ctx, cudaGetLastError());
+    rc = gl_mlp_forward(mlp, n_items, ctx->sfeat, ctx->sthat, stream);
+    if (rc) return fail(ctx, rc, "surrogate network forward failed");
+    gl_sur_combine_kernel<<<g2, 256, 0, st>>>(ctx->d_sets, p->k, ctx->sset, ctx->scls, ctx->scount,
+                                              ctx->sthat, ctx->sscale, ctx->sdsph, ctx->stable,
+                                              (float)bound_limit, ctx->sdef, ctx->sfb,
+                                              ctx->scount + 2);
+    gl_sur_fallback_kernel<<<g2, 256, 0, st>>>(ctx->d_sets, ctx->sx, ctx->sy, ctx->so, ctx->sset,
+                                               ctx->scls, ctx->sfb, ctx->scount + 2, ctx->sdef);
+    gl_sur_reduce_kernel<<<launch_grid((int64_t)cnt[1], 256), 256, 0, st>>>(
+        ctx->srj, ctx->srns, ctx->srfirst, ctx->scount + 1, ctx->sdef, out);
+    ctx->launches += 4;
+    GL_CUDA(ctx, cudaGetLastError());
+  }
+  if (stats) {
+    GL_CUDA(ctx, cudaMemcpyAsync(cnt, ctx->scount, sizeof cnt, cudaMemcpyDeviceToHost, st));
+    GL_CUDA(ctx, cudaStreamSynchronize(st));
+    stats->items = (int64_t)cnt[0];
+    stats->exposures = (int64_t)cnt[1];
+    stats->fallback = (int64_t)cnt[2];
+  }
   return GL_OK;
 }
 
