@@ -258,6 +258,175 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ surrogate workloads
+MLP_TRAIN_FLOPS = 3 * 2 * (7 * 256 + 3 * 256 * 256 + 256)   # forward + 2x backward, per sample
+MLP_TC_TRAIN_FLOPS = 3 * 2 * 3 * 256 * 256                # the tensor-core part of it
+
+
+def stretch_move(logp, walkers: np.ndarray, rng, a: float = 2.0):
+    """One sweep of the affine-invariant stretch move (Goodman and Weare 2010):
+    each half of the ensemble proposes moves along lines through members of the
+    other half; `logp` evaluates all proposals at once on the GPU."""
+    n, d = walkers.shape
+    lp = logp(walkers)
+    acc = 0
+    for half in (0, 1):
+        act = np.arange(half, n, 2)
+        oth = np.arange(1 - half, n, 2)
+        zz = ((a - 1.0) * rng.uniform(size=act.size) + 1.0) ** 2 / a
+        partner = walkers[rng.choice(oth, act.size)]
+        prop = partner + zz[:, None] * (walkers[act] - partner)
+        full = walkers.copy()
+        full[act] = prop
+        lp_new = logp(full)[act]
+        logr = (d - 1) * np.log(zz) + lp_new - lp[act]
+        ok = np.log(rng.uniform(size=act.size)) < logr
+        walkers[act[ok]] = prop[ok]
+        lp[act[ok]] = lp_new[ok]
+        acc += int(ok.sum())
+    return walkers, acc / n
+
+
+def surrogate_train_arm(args):
+    import torch
+    from paper_2410_05408_b300 import binding, build, surrogate
+    build.build()
+    ctx = binding.Context(0)
+    mlp = binding.Mlp(0)
+    from oracle import mlp as omlp   # initial weights only (He-uniform draws)
+    rng = np.random.default_rng(0)
+    mlp.set_params(np.concatenate([np.concatenate([W.ravel(), b])
+                                   for W, b in omlp.init_params(rng)]).astype(np.float32))
+    t0 = time.perf_counter()
+    train = surrogate.make_dataset(ctx, args.sur_train, seed=3)
+    held = surrogate.make_dataset(ctx, args.sur_held, seed=1003)
+    gen_s = time.perf_counter() - t0
+    # timed training: CUDA events around every step (forward + backward + Adam)
+    batch = args.sur_batch
+    n = train["t"].numel()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    hist = surrogate.train(mlp, train, epochs=args.sur_epochs, batch=batch, lr=args.sur_lr)
+    ev1.record()
+    torch.cuda.synchronize()
+    train_s = ev0.elapsed_time(ev1) * 1e-3
+    samples = args.sur_epochs * n
+    table = surrogate.error_table(mlp, held)
+    q = surrogate.flux_error_quantiles(mlp, held)
+    if args.sur_save:
+        surrogate.save(args.sur_save, mlp, table, dict(train=n, epochs=args.sur_epochs,
+                                                        batch=batch, history=hist))
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    tc = samples * MLP_TC_TRAIN_FLOPS / train_s / 1e12
+    line = {"metric": "surrogate training samples/sec (forward + backward + Adam)",
+            "value": samples / train_s, "unit": "samples/s", "n_gpus": 1,
+            "steps": args.sur_epochs * ((n + batch - 1) // batch), "warmup": 0,
+            "higher_is_better": True, "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": "surrogate_train", "train_samples": n,
+                       "heldout_samples": held["t"].numel(), "epochs": args.sur_epochs,
+                       "batch": batch, "network": "7-256-256-256-256-1 SiLU"},
+            "data_generation_s": gen_s, "train_s": train_s, "loss_history": hist,
+            "tensor_core": {"achieved_tflops": tc,
+                            "peak": peaks.get("bf16_tflops_sustained", 1407.5),
+                            "frac": tc / peaks.get("bf16_tflops_sustained", 1407.5),
+                            "note": "3 hidden 256x256 layers, forward + 2 backward GEMMs, "
+                                    "whole training step time (incl. CUDA-core layers, Adam)"},
+            "heldout_flux_error_quantiles": q,
+            "error_table_normalised": [float(x) for x in table]}
+    print(json.dumps(line))
+
+
+def surrogate_mcmc_arm(args):
+    import torch
+    from paper_2410_05408_b300 import binding, build, surrogate
+    build.build()
+    ctx = binding.Context(0)
+    mlp = binding.Mlp(0)
+    table, meta = surrogate.load(args.sur_load, mlp)
+    wl = inputs.injected_curve(n_walkers=args.walkers)
+    names = binding.PARAM_NAMES
+    nt = len(wl["t"])
+    t = torch.tensor(wl["t"], device="cuda")
+    exp = torch.full((args.walkers,), wl["exptime"], dtype=torch.float64, device="cuda")
+    p = {k: torch.tensor(np.ascontiguousarray(wl["walkers"][k]), dtype=torch.float64,
+                         device="cuda") for k in names}
+    out_s = torch.empty(args.walkers * nt, dtype=torch.float64, device="cuda")
+    out_e = torch.empty_like(out_s)
+    evals = args.walkers * nt * wl["nsuper"]
+
+    def run_s():
+        return binding.gl_lightcurve_surrogate(ctx.handle, mlp, p, t, out_s, table,
+                                               args.sur_limit, exptime=exp,
+                                               nsuper_all=wl["nsuper"])
+
+    def run_e():
+        ctx.lightcurve(p, t, out_e, exp, nsuper_all=wl["nsuper"], precision=binding.GL_FP32C)
+
+    for _ in range(args.warmup):
+        stats = run_s()
+        run_e()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        stats = run_s()
+    torch.cuda.synchronize()
+    ts = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run_e()
+    torch.cuda.synchronize()
+    te = (time.perf_counter() - t0) / args.steps
+    # accuracy against the oracle on a few walkers
+    import oracle
+    idx = np.arange(0, args.walkers, max(1, args.walkers // 4))[:4]
+    ref = oracle.lightcurve({k: wl["walkers"][k][idx] for k in names}, wl["t"], wl["exptime"],
+                            wl["nsuper"])
+    got = out_s.view(args.walkers, nt).cpu().numpy()[idx]
+    max_err = float(np.max(np.abs(got - ref)))
+    # a few sweeps of an ensemble sampler on the injected data, likelihood on the GPU
+    truth = {k: float(wl["truth"][k][0]) for k in names}
+    flux_true = torch.empty(nt, dtype=torch.float64, device="cuda")
+    ctx.lightcurve({k: torch.tensor([truth[k]], dtype=torch.float64, device="cuda")
+                    for k in names}, t, flux_true, exp[:1], nsuper_all=wl["nsuper"],
+                   precision=binding.GL_FP64)
+    data = flux_true + torch.tensor(wl["noise"], device="cuda")
+    sigma = torch.full((nt,), 1e-4, dtype=torch.float64, device="cuda")
+    free = ["t0", "b", "k", "f", "eta", "xi"]
+    ll = torch.empty(args.walkers, dtype=torch.float64, device="cuda")
+
+    def logp(wk):
+        for i, name in enumerate(free):
+            p[name].copy_(torch.tensor(wk[:, i]))
+        bad = (wk[:, 3] < 0) | (wk[:, 3] > 0.9) | (wk[:, 1] < 0) | (wk[:, 2] <= 0)
+        run_s()
+        binding.gl_loglike(ctx.handle, out_s, data, sigma, ll)
+        v = ll.cpu().numpy().copy()
+        v[bad] = -np.inf
+        return v
+
+    walkers = np.stack([wl["walkers"][n_] for n_ in free], axis=1)
+    rng = np.random.default_rng(7)
+    t0 = time.perf_counter()
+    accs = []
+    for _ in range(args.sweeps):
+        walkers, a = stretch_move(logp, walkers, rng)
+        accs.append(a)
+    sweep_s = (time.perf_counter() - t0) / max(args.sweeps, 1)
+    line = {"metric": "surrogate-in-the-loop likelihood evals/sec", "value": evals / ts,
+            "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ts * 1e3, "higher_is_better": True, "dtype": "bf16+f32+f64",
+            "data": "synthetic", "config": {"workload": "surrogate_mcmc",
+                                            "walkers": args.walkers, "exposures": nt,
+                                            "nsuper": wl["nsuper"],
+                                            "bound_limit": args.sur_limit},
+            "exact_fp32c": {"value": evals / te, "ms_per_step": te * 1e3},
+            "gain_vs_exact": te / ts, "fallback": stats,
+            "max_dflux_vs_oracle": max_err,
+            "sampler": {"sweeps": args.sweeps, "acceptance": accs, "s_per_sweep": sweep_s}}
+    print(json.dumps(line))
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -269,10 +438,24 @@ def main():
     ap.add_argument("--ref-sets", type=int, default=96)
     ap.add_argument("--cpu-sets", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sur-train", type=int, default=10_000_000)
+    ap.add_argument("--sur-held", type=int, default=1_000_000)
+    ap.add_argument("--sur-epochs", type=int, default=6)
+    ap.add_argument("--sur-batch", type=int, default=16384)
+    ap.add_argument("--sur-lr", type=float, default=2e-3)
+    ap.add_argument("--sur-save", default="")
+    ap.add_argument("--sur-load", default="")
+    ap.add_argument("--sur-limit", type=float, default=1e-6)
+    ap.add_argument("--walkers", type=int, default=1024)
+    ap.add_argument("--sweeps", type=int, default=5)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "surrogate_train":
+        return surrogate_train_arm(args)
+    if args.workload == "surrogate_mcmc":
+        return surrogate_mcmc_arm(args)
 
     import torch
     from paper_2410_05408_b300 import binding, build
