@@ -161,13 +161,16 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def dist_setup():
+def dist_setup(backend: str = None):
+    """Rank layout from the torchrun environment; NCCL on GPUs, gloo otherwise."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(backend or ("nccl" if torch.cuda.is_available() else "gloo"))
     return world, rank, local
 
 
@@ -178,13 +181,20 @@ def barrier(world):
 
 
 def allreduce_max(x: float, world: int) -> float:
+    """Max over ranks (timing only: the work units share no data)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(world: int, evals_per_rank_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank evaluates its own batch of the same size."""
+    return world * evals_per_rank_step * steps / (max_ms * 1e-3)
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
@@ -559,8 +569,8 @@ def main():
     ms64 = allreduce_max(ms64, world)
     _, _, kern64 = timed(binding.GL_FP64, out64, 3, profile=True)
 
-    value = world * evals * args.steps / (ms32 * 1e-3)
-    fp64_value = world * evals * k64 / (ms64 * 1e-3)
+    value = aggregate_value(world, evals, args.steps, ms32)
+    fp64_value = aggregate_value(world, evals, k64, ms64)
     # end to end: pinned host inputs and output through the same public call
     hp = {k: torch.as_tensor(v).pin_memory() for k, v in p.items()}
     h_t = torch.as_tensor(t).pin_memory()
