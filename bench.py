@@ -48,39 +48,66 @@ def alu_peaks(sm_mhz: float):
     return fp32, fp64
 
 
-# Algorithmic work per unit of the FP32C light-curve kernel (flops, FMA = 2),
-# counted from the source (see the kernel section of the design doc):
-#   FP32: per exposure window test 12; per sub-exposure position and class 40;
-#         whole-ellipse item 1175 (inner maxima 310, geometry 30, 20 nodes x 41,
-#         closed forms 15); crossing item 2300 (maxima 310, FP32 Ferrari 290,
-#         breakpoints 50, 1.5 arcs x (20 nodes x 49 + 80), limb arcs 25, geometry 30)
-#   FP64: per in-window exposure 10 (exact window); midpoint Kepler state 250;
-#         per sub-exposure FP64 Kepler (no expansion) 250; crossing item 200
-#         (limb polynomial, frame, Newton polish, sign tests); exposure sum 2 per item
+# Algorithmic work per unit of the FP32C light-curve step (flops, FMA = 2),
+# counted from the source (see the kernel section of the design doc), by kernel:
+#   tiles (gl_lc_kernel): FP32 per exposure window test 12, per sub-exposure
+#         position and class 40; FP64 per in-window exposure 10 (exact window),
+#         midpoint Kepler state 250, per sub-exposure FP64 Kepler (no expansion) 250
+#   quadrature (gl_items_quad_kernel): FP32 whole-ellipse item 1175 (inner maxima
+#         310, geometry 30, 20 nodes x 41, closed forms 15), crossing item 2300
+#         (maxima 310, FP32 Ferrari 290, breakpoints 50, 1.5 arcs x (20 nodes x 49
+#         + 80), limb arcs 25, geometry 30); FP64 crossing item 200 (limb
+#         polynomial, frame, Newton polish, sign tests)
+#   exposure sums (gl_items_sum_kernel): FP64 2 per sub-exposure
 F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 1175, 2300
 F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 250, 200, 2
 
 
-def roofline(c: dict, kernel_ms: float, fp32_peak: float, fp64_peak: float) -> dict:
-    """ALU roofline of the FP32C light-curve kernel: algorithmic FP32 and FP64
-    flops of one launch over its CUDA-event duration, against the pipe that
-    bounds it (the larger of flops/peak)."""
-    f32 = (c["exposures"] * F32_EXPOSURE + c["items"] * F32_ITEM + c["full"] * F32_FULL +
-           c["partial"] * F32_PARTIAL)
-    f64 = (c["in_window"] * F64_WINDOW + (c["kepler"] + c["item_kepler"]) * F64_KEPLER +
-           c["partial"] * F64_PARTIAL + c["items"] * F64_SUM)
-    t = kernel_ms * 1e-3
+def kernel_flops(c: dict) -> dict:
+    """(FP32, FP64) algorithmic flops of one step, per kernel of the step."""
+    return {
+        "tiles": (c["exposures"] * F32_EXPOSURE + c["items"] * F32_ITEM,
+                  c["in_window"] * F64_WINDOW + (c["kepler"] + c["item_kepler"]) * F64_KEPLER),
+        "quadrature": (c["full"] * F32_FULL + c["partial"] * F32_PARTIAL,
+                       c["partial"] * F64_PARTIAL),
+        "sums": (0, c["items"] * F64_SUM),
+    }
+
+
+def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak: float) -> dict:
+    """Algorithmic FP32 and FP64 flops over a CUDA-event duration, against the
+    pipe that bounds them (the larger of flops/peak)."""
+    t = ms * 1e-3
     a32, a64 = f32 / t / 1e12, f64 / t / 1e12
     pipe = "fp64" if f64 / fp64_peak >= f32 / fp32_peak else "fp32"
     ach, peak = (a64, fp64_peak) if pipe == "fp64" else (a32, fp32_peak)
     return {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None,
-            "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x max SM clock",
+            "frac": ach / peak,
             "fp32": {"achieved": a32, "peak": fp32_peak, "frac": a32 / fp32_peak,
                      "flops_per_launch": f32},
             "fp64": {"achieved": a64, "peak": fp64_peak, "frac": a64 / fp64_peak,
                      "flops_per_launch": f64},
-            "kernel_ms": kernel_ms}
+            "kernel_ms": ms}
+
+
+KERNEL_NAMES = {"tiles": "gl_lc_kernel", "quadrature": "gl_items_quad_kernel",
+                "sums": "gl_items_sum_kernel"}
+
+
+def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float) -> dict:
+    """ALU roofline of the dominant kernel of the FP32C step (the one with the
+    largest measured time), with every kernel's own figures beside it."""
+    flops = kernel_flops(c)
+    per = {k: alu_roofline(*flops[k], kern[k], fp32_peak, fp64_peak)
+           for k in flops if kern.get(k)}
+    top = max(per, key=lambda k: per[k]["kernel_ms"])
+    line = dict(per[top])
+    line.update({"kernel": KERNEL_NAMES[top], "traffic": None,
+                 "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x "
+                                "max SM clock",
+                 "kernels": {KERNEL_NAMES[k]: {"ms": v["kernel_ms"], "pipe": v["pipe"],
+                                               "frac": v["frac"]} for k, v in per.items()}})
+    return line
 
 
 def workload(name: str, seed_offset: int = 0):
@@ -531,9 +558,11 @@ def main():
         ms = sum(a.elapsed_time(b) for a, b in evs)
         kern = {}
         if profile:
-            for name, kind in (("curve", binding.GL_KERNEL_CURVE), ("setup", binding.GL_KERNEL_SETUP)):
+            for name, kind in (("tiles", binding.GL_KERNEL_CURVE),
+                               ("quadrature", binding.GL_KERNEL_QUAD),
+                               ("sums", binding.GL_KERNEL_SUM), ("setup", binding.GL_KERNEL_SETUP)):
                 t_ms, n = ctx.profile_read(kind)
-                kern[name] = t_ms / max(n, 1)
+                kern[name] = t_ms / n if n else None
             ctx.profile(False)
         return ms, ctx.launches() - l0, kern
 
@@ -606,11 +635,10 @@ def main():
                    "graphs": "step replayed as a CUDA graph"},
         "max_dflux_vs_fp64_gpu": max_dflux, "in_transit_exposures": in_transit,
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / k64},
-        "kernel_ms": {"curve_fp32c": kern32.get("curve"), "setup": kern32.get("setup"),
-                      "curve_fp64": kern64.get("curve")},
+        "kernel_ms": {"fp32c": kern32, "fp64": kern64},
         "workload_counts": counts,
         "autotune": tune,
-        "roofline": roofline(counts, kern32["curve"], fp32_peak, fp64_peak),
+        "roofline": roofline(counts, kern32, fp32_peak, fp64_peak),
         "gpu_launches": launches,
         "status": status,
         "clocks": clocks,

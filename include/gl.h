@@ -207,6 +207,25 @@ int gl_graphs_enable(gl_context *ctx, int on);
 /* Number of graph replays the context has issued. */
 int64_t gl_graph_launches(const gl_context *ctx);
 
+/* Item pipeline of gl_lightcurve_batch (on by default).  With it on, the step
+ * after the per-set constants is four flat kernels: window tests over every
+ * exposure (flux 1 outside the transit window), one thread per kept exposure
+ * (Kepler midpoint state, position and overlap class of each sub-exposure,
+ * Sec. 2 geometry), the quadrature of every sub-exposure that meets the disk with
+ * warps spread over the whole GPU, and each exposure's FP64 mean in sub-exposure
+ * order.  With it off, a tile kernel takes consecutive exposures and does all of
+ * this per tile.  The pipeline balances batches whose transits fall in few
+ * places; its workspace (64 bytes per sub-exposure, context-owned, grown on
+ * demand and kept) holds n_total x nsuper_all sub-exposures (16 per exposure
+ * with per-set nsuper), at most `max_items` (0 = default 2^23); an exposure that
+ * does not fit is finished by the thread holding it.  Every sub-exposure is
+ * evaluated by the same compiled functions and every exposure summed in the same
+ * order either way, so results are bit-identical with the pipeline on or off
+ * and for any workspace size.  While counting (gl_counts_enable) the tile
+ * kernel runs.  Drops the cached graphs.  GL_EINVAL on NULL or max_items
+ * outside [0, 2^31). */
+int gl_item_pipeline(gl_context *ctx, int on, int64_t max_items);
+
 /* Result of gl_autotune. */
 typedef struct {
   int threads;         /* threads per CTA of the light-curve kernel */
@@ -235,9 +254,12 @@ int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *
 
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */
-#define GL_KERNEL_CURVE 1   /* light-curve kernel (FP64 or FP32C) */
+#define GL_KERNEL_CURVE 1   /* light-curve tile kernel, or the item pipeline's window and
+                               kept-exposure kernels (FP64 or FP32C) */
 #define GL_KERNEL_SKY 2     /* geometry-level kernel */
 #define GL_KERNEL_SPHERE 3  /* spherical-planet kernel */
+#define GL_KERNEL_QUAD 4    /* item pipeline: quadrature of queued sub-exposures */
+#define GL_KERNEL_SUM 5     /* item pipeline: exposure means */
 #define GL_KERNEL_KINDS 8
 
 /* Per-kernel device timing for benchmarks.  While enabled (on != 0), every

@@ -33,7 +33,7 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_flux_sphere", "gl_mlp_param_count", "gl_mlp_create", "gl_mlp_destroy",
             "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
             "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
-            "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike")
+            "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike", "gl_item_pipeline")
 
 SUR_BINS = 16
 
@@ -46,6 +46,8 @@ GL_KERNEL_SETUP = 0
 GL_KERNEL_CURVE = 1
 GL_KERNEL_SKY = 2
 GL_KERNEL_SPHERE = 3
+GL_KERNEL_QUAD = 4
+GL_KERNEL_SUM = 5
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 
@@ -152,6 +154,8 @@ def load():
         lib.gl_graphs_enable.restype = i32
         lib.gl_graph_launches.argtypes = [vp]
         lib.gl_graph_launches.restype = i64
+        lib.gl_item_pipeline.argtypes = [vp, i32, i64]
+        lib.gl_item_pipeline.restype = i32
         lib.gl_lightcurve_batch_noalloc.argtypes = [ctypes.POINTER(_Params),
                                                     ctypes.POINTER(_Times), vp, i32, vp]
         lib.gl_lightcurve_batch_noalloc.restype = i32
@@ -368,6 +372,10 @@ def gl_graph_launches(ctx) -> int:
     return load().gl_graph_launches(ctx)
 
 
+def gl_item_pipeline(ctx, on: bool = True, max_items: int = 0) -> None:
+    _check(ctx, load().gl_item_pipeline(ctx, int(bool(on)), int(max_items)))
+
+
 def gl_profile_enable(ctx, on: bool = True) -> int:
     return load().gl_profile_enable(ctx, int(bool(on)))
 
@@ -495,6 +503,9 @@ class Context:
 
     def graph_launches(self) -> int:
         return gl_graph_launches(self.handle)
+
+    def item_pipeline(self, on: bool = True, max_items: int = 0):
+        gl_item_pipeline(self.handle, on, max_items)
 
     def profile(self, on: bool = True):
         gl_profile_enable(self.handle, on)

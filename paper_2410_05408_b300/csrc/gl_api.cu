@@ -35,6 +35,13 @@ enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4, k
 constexpr int kNodes64 = 32;
 constexpr int kNodes32 = 20;
 
+// item pipeline workspace: at most this many sub-exposure items per call by
+// default; per item 3 positions + deficit (FP64 sizing) + set + class + queue
+// slot + record (output index, first item, count); plus one int per exposure
+// for the kept-exposure list
+constexpr int64_t kItemMaxDefault = 1LL << 23;
+constexpr size_t kItemBytes = 4 * sizeof(double) + 6 * sizeof(int);
+
 __constant__ NodeRule<double> c_rule64;
 __constant__ NodeRule<float> c_rule32;                 // default order (kNodes32)
 // orders the autotuner may choose for the FP32C light-curve kernel
@@ -160,13 +167,29 @@ __global__ void gl_maxdiff_kernel(const double* a, const double* b, int64_t n,
   if ((threadIdx.x & 31) == 0) atomicMax(err, (unsigned long long)__double_as_longlong(m));
 }
 
-// ------------------------------------------------------------------ fused persistent kernel
-// One CTA processes tiles of TILE consecutive exposures, taken from an atomic
-// tile counter until none are left:
+// ------------------------------------------------------------------ light-curve kernels
+// Two ways to the same numbers (chosen by gl_item_pipeline):
+//
+// Item pipeline (default), four flat kernels after the per-set constants:
+//   gl_win_kernel    one thread per exposure: conservative FP32 window test and
+//                    the exact FP64 one; exposures outside get flux 1, the rest
+//                    are appended to a kept-exposure list
+//   gl_exp_kernel    one thread per kept exposure: midpoint state (FP64 Kepler),
+//                    the position and overlap class of each sub-exposure; items
+//                    that meet the disk go to a global queue (crossing items
+//                    from the back, whole-ellipse items from the front)
+//   gl_items_quad_kernel   the quadrature of every queued item, warps spread over
+//                    the whole GPU, crossing (heavier) items first
+//   gl_items_sum_kernel    FP64 mean of each exposure, in sub-exposure order
+// When the workspace is full, an exposure is finished by the thread that holds it.
+//
+// Tiles (gl_lc_kernel): one CTA takes tiles of TILE consecutive exposures from an
+// atomic tile counter and finishes them itself:
 //   phase 0  one thread per exposure: conservative FP32 window test; exposures
 //            outside get flux 1 at once, the rest are compacted in shared memory
-//   phase 1  one thread per kept exposure: exact FP64 window test and, for the
-//            FP32C path, the FP64 Kepler state at the exposure midpoint
+//   phase 1  one thread per kept exposure: exact FP64 window test (exposures that
+//            fail it get flux 1 and no sub-exposure items) and, for the FP32C
+//            path, the FP64 Kepler state at the exposure midpoint
 //   rounds   up to CAP sub-exposure items at a time:
 //            2: position (cubic Taylor step in FP32 from the midpoint state, or
 //               FP64 Kepler per item), classification, queueing
@@ -174,6 +197,11 @@ __global__ void gl_maxdiff_kernel(const double* a, const double* b, int64_t n,
 //            4: crossing items (roots, arcs)
 //            5: FP64 accumulation of 1 - deficit per exposure, in item order
 //   phase 6  mean over the exposure's sub-exposures -> out
+//
+// Every exposure's midpoint state, every item's geometry and deficit come from
+// the same compiled functions (exposure_prep, item_geometry, item_deficit) and
+// every exposure is summed in sub-exposure order, so the two ways, and any
+// workspace size, give bit-identical results.
 struct LcArgs {
   const SetConst* sets;
   const double* t;
@@ -184,6 +212,20 @@ struct LcArgs {
   unsigned long long* counts;   // instrumented instances: GL_COUNT_* slots
   int n_tiles, tile, cap;
   int rule_idx;                 // FP32 quadrature order: index into c_rule32_tuned, -1 = default
+  // item pipeline workspace
+  void* ipos;                   // R[3 * item_cap]: x0, y0, 1 - x0^2 - y0^2 of each item
+  void* idef;                   // R[item_cap]: deficit (c0 I0 + c1 I1 + c2 I2) / F0 of each item
+  int* iset;                    // parameter set of each item
+  int* iq;                      // whole-ellipse items from the front, crossing items from the back
+  int *rj, *rfirst, *rns;       // exposure records: output index, first item, sub-exposures
+  int* klist;                   // kept exposures (output index); n_total entries
+  unsigned long long* ictr;     // kIc* counters
+  int64_t item_cap;
+  int* icls;                    // overlap class of each item
+};
+
+enum : int {
+  kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcSlots = 6
 };
 
 template <typename R> __device__ __forceinline__ const NodeRule<R>& lc_rule(int idx);
@@ -245,6 +287,100 @@ __device__ __forceinline__ int block_scan(int v, int* warp_tot, int* total) {
 __device__ __forceinline__ void count_add(unsigned long long* c, bool pred) {
   unsigned m = __ballot_sync(__activemask(), pred);
   if (m && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicAdd(c, (unsigned long long)__popc(m));
+}
+
+// Warp-aggregated append: the lanes (of those active) with pred get consecutive
+// slots from one atomic add on *ctr; returns the slot, or -1 without pred.
+__device__ __forceinline__ long long warp_append(unsigned long long* ctr, bool pred) {
+  const unsigned mask = __activemask();
+  const unsigned bal = __ballot_sync(mask, pred);
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader && bal) base = atomicAdd(ctr, (unsigned long long)__popc(bal));
+  base = __shfl_sync(mask, base, leader);
+  return pred ? (long long)base + __popc(bal & ((1u << lane) - 1u)) : -1;
+}
+
+// Exclusive prefix sum over a converged warp; *total gets the warp's sum.
+__device__ __forceinline__ int warp_scan(int v, int* total) {
+  const int lane = threadIdx.x & 31;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// Exposure at time t: tau (t - t0 wrapped about the conjunction), the exact FP64
+// window test (kExpDead outside) and, for the FP32C path of a set that allows
+// it, the FP64 Kepler state at the midpoint for the cubic Taylor steps.
+// exposure_prep, item_geometry and item_deficit are compiled once (not inlined),
+// so every call site runs the same instructions: inlined copies may contract
+// multiply-adds differently.
+template <typename R>
+__device__ __noinline__ int exposure_prep(const SetConst& c, double t, double* tau_out,
+                                          gl::MidState* mid) {
+  const double tau = gl::wrap_tau(c, t);
+  *tau_out = tau;
+  if (!gl::in_window(c, tau, 0.5 * c.exptime)) return kExpDead;
+  if (sizeof(R) == 4 && (c.flags & gl::kSetTaylor)) {
+    gl::SkyState st;
+    gl::sky_state(c, tau, &st);
+    *mid = gl::mid_state(st);
+    return kExpTaylor;
+  }
+  return 0;
+}
+
+// Sky position (x0, y0, 1 - x0^2 - y0^2 in precision R) and overlap class of the
+// sub-exposure at offset (twice / 2) * sub_step from the exposure midpoint tau:
+// a cubic Taylor step in FP32 from the midpoint state when the set allows it,
+// otherwise the FP64 Kepler solve.
+template <typename R>
+__device__ __noinline__ int item_geometry(const SetConst& c, int flag, const gl::MidState& mid,
+                                          double tau, int twice, R* x, R* y, R* o) {
+  if (flag & kExpTaylor) {
+    float xf, yf, zf, of;
+    gl::taylor_position(mid, 0.5f * (float)twice * c.fsub_step, &xf, &yf, &zf, &of);
+    *x = (R)xf;
+    *y = (R)yf;
+    *o = (R)of;
+    return gl::classify_t<float>(c.freq, xf, yf, zf, 1e-6f);
+  }
+  double xd, yd, zd;
+  gl::sky_position(c, tau + 0.5 * (double)twice * c.sub_step, &xd, &yd, &zd);
+  *x = (R)xd;
+  *y = (R)yd;
+  *o = (R)((1.0 - xd) * (1.0 + xd) - yd * yd);
+  return gl::classify(c, xd, yd, zd);
+}
+
+// Deficit of one item: limb-darkened occulted flux over F0, in precision R.
+template <typename R>
+__device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls,
+                                       const NodeRule<R>& rl) {
+  R I[3];
+  gl::occulted_r<R>(c, x, y, o, cls, rl, I);
+  return (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
+          gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
+}
+
+// Flux of one live exposure computed by the calling thread alone (the item
+// pipeline's fallback when its workspace is full).
+template <typename R>
+__device__ double exposure_local(const SetConst& c, int flag, const gl::MidState& mid, double tau,
+                                 int ns, const NodeRule<R>& rl) {
+  double acc = 0.0;
+  for (int q = 0; q < ns; ++q) {
+    R x, y, o;
+    const int cls = item_geometry<R>(c, flag, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
+    const R d = cls == gl::kOut ? R(0) : item_deficit<R>(c, x, y, o, cls, rl);
+    acc += 1.0 - (double)d;
+  }
+  return acc / ns;
 }
 
 template <typename R, int NT, bool COUNT>
@@ -318,23 +454,15 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
     }
     __syncthreads();
     if (m == 0) continue;
-    int M;
-    int base = block_scan<NT>(tid < m ? e_ns[tid] : 0, warp_tot, &M);
-    if (tid < m) e_base[tid] = base;
-    if (tid == 0) e_base[m] = M;
 
     // ---- phase 1: exact window test and midpoint state
     for (int i = tid; i < m; i += NT) {
       const SetConst& c = a.sets[e_s[i]];
-      double tau = gl::wrap_tau(c, e_tau[i]);
-      int fl = 0;
-      if (!gl::in_window(c, tau, 0.5 * c.exptime)) {
-        fl = kExpDead;
-      } else if (sizeof(R) == 4 && (c.flags & gl::kSetTaylor)) {
-        gl::SkyState st;
-        gl::sky_state(c, tau, &st);
-        e_mid[i] = gl::mid_state(st);
-        fl = kExpTaylor;
+      double tau;
+      const int fl = exposure_prep<R>(c, e_tau[i], &tau, &e_mid[i]);
+      if (fl & kExpDead) {
+        a.out[e_j[i]] = 1.0;
+        e_ns[i] = 0;   // no sub-exposure items
       }
       e_tau[i] = tau;
       e_flag[i] = fl;
@@ -344,6 +472,11 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
         atomicAdd(&a.counts[GL_COUNT_KEPLER], (unsigned long long)((fl & kExpTaylor) ? 1 : 0));
       }
     }
+    __syncthreads();
+    int M;
+    int base = block_scan<NT>(tid < m ? e_ns[tid] : 0, warp_tot, &M);
+    if (tid < m) e_base[tid] = base;
+    if (tid == 0) e_base[m] = M;
     __syncthreads();
 
     for (int r0 = 0; r0 < M; r0 += cap) {
@@ -356,33 +489,17 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
       // ---- phase 2: positions and classes
       for (int k = tid; k < nr; k += NT) {
         int it = r0 + k;
-        int lo = 0, hi = m;   // e_base[lo] <= it < e_base[hi]
+        int lo = 0, hi = m;   // e_base[lo] <= it < e_base[hi]: skips empty ranges
         while (hi - lo > 1) {
           int mid = (lo + hi) >> 1;
           if (e_base[mid] <= it) lo = mid; else hi = mid;
         }
         const int i = lo, q = it - e_base[i];
         it_def[k] = R(0);
-        if (e_flag[i] & kExpDead) continue;
         const SetConst& c = a.sets[e_s[i]];
-        const int twice = 2 * q + 1 - e_ns[i];   // dt = (q + 1/2 - n/2) exptime / n
         R x, y, o;
-        int cls;
-        if (e_flag[i] & kExpTaylor) {
-          float xf, yf, zf, of;
-          gl::taylor_position(e_mid[i], 0.5f * (float)twice * c.fsub_step, &xf, &yf, &zf, &of);
-          cls = gl::classify_t<float>(c.freq, xf, yf, zf, 1e-6f);
-          x = (R)xf;
-          y = (R)yf;
-          o = (R)of;
-        } else {
-          double xd, yd, zd;
-          gl::sky_position(c, e_tau[i] + 0.5 * (double)twice * c.sub_step, &xd, &yd, &zd);
-          cls = gl::classify(c, xd, yd, zd);
-          x = (R)xd;
-          y = (R)yd;
-          o = (R)((1.0 - xd) * (1.0 + xd) - yd * yd);
-        }
+        const int cls = item_geometry<R>(c, e_flag[i], e_mid[i], e_tau[i], 2 * q + 1 - e_ns[i],
+                                         &x, &y, &o);
         if (COUNT) {
           atomicAdd(&a.counts[GL_COUNT_ITEMS], 1ull);
           if (!(e_flag[i] & kExpTaylor)) atomicAdd(&a.counts[GL_COUNT_ITEM_KEPLER], 1ull);
@@ -404,11 +521,8 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
         int packed = u < nf ? q_full[u] : q_part[u - nf];
         int k = packed & 0xffff, i = packed >> 16;
         const SetConst& c = a.sets[e_s[i]];
-        R I[3];
-        gl::occulted_r<R>(c, it_pos[3 * k], it_pos[3 * k + 1], it_pos[3 * k + 2],
-                          u < nf ? gl::kFull : gl::kPartial, rl, I);
-        it_def[k] = (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
-                     gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
+        it_def[k] = item_deficit<R>(c, it_pos[3 * k], it_pos[3 * k + 1], it_pos[3 * k + 2],
+                                    u < nf ? gl::kFull : gl::kPartial, rl);
       }
       __syncthreads();
       // ---- phase 5: FP64 accumulation in item order
@@ -420,9 +534,190 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
       }
       __syncthreads();
     }
-    // ---- phase 6: exposure means
-    for (int i = tid; i < m; i += NT) a.out[e_j[i]] = e_acc[i] / e_ns[i];
+    // ---- phase 6: exposure means (exposures that failed the exact test are done)
+    for (int i = tid; i < m; i += NT)
+      if (e_ns[i] > 0) a.out[e_j[i]] = e_acc[i] / e_ns[i];
     __syncthreads();
+  }
+}
+
+// Item pipeline, stage 1: window tests over all exposures.  Each block takes a
+// contiguous range of exposures, 256 at a time, and follows the owning set of a
+// CSR batch forward from the range's start.
+__global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
+  __shared__ long long s_set;
+  const int64_t per = (a.n_total + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * per;
+  const int64_t hi = min(a.n_total, lo + per);
+  if (lo >= hi) return;
+  if (a.offsets && threadIdx.x == 0) s_set = owner_of(a.offsets, a.n_sets, lo);
+  __syncthreads();
+  for (int64_t j0 = lo; j0 < hi; j0 += 256) {
+    const int64_t j = j0 + threadIdx.x;
+    int64_t first = a.offsets ? s_set : 0;
+    bool keep = false;
+    int s = 0;
+    if (j < hi) {
+      int64_t ti;
+      if (a.offsets) {
+        int64_t ss = first;
+        while (ss + 1 < a.n_sets && a.offsets[ss + 1] <= j) ++ss;
+        s = (int)ss;
+        ti = j;
+      } else {
+        s = (int)((unsigned)j / (unsigned)a.n_times);
+        ti = j - (int64_t)s * a.n_times;
+      }
+      const SetConst& c = a.sets[s];
+      const double tj = a.t[ti];
+      if (c.flags & gl::kSetInvalid)
+        a.out[j] = __longlong_as_double(0x7ff8000000000000LL);
+      else if (gl::window_maybe(c, tj) && gl::in_window(c, gl::wrap_tau(c, tj), 0.5 * c.exptime))
+        keep = true;
+      else
+        a.out[j] = 1.0;
+    }
+    const long long slot = warp_append(&a.ictr[kIcKept], keep);
+    if (keep) a.klist[slot] = (int)j;   // at most n_total entries
+    if (a.offsets) {
+      __syncthreads();
+      if (j < hi && (threadIdx.x == 255 || j == hi - 1)) s_set = s;   // owner of the pass's last exposure
+      __syncthreads();
+    }
+  }
+}
+
+// Item pipeline, stage 2: one lane per kept exposure, 32 kept exposures per warp
+// and pass.  Sub-exposure slots and exposure records are taken with one atomic
+// add per warp, then the queue positions of the items that meet the disk with
+// two more.  A warp whose items do not fit the workspace finishes its exposures
+// itself.
+template <typename R>
+__global__ void __launch_bounds__(128) gl_exp_kernel(LcArgs a) {
+  const NodeRule<R>& rl = lc_rule<R>(a.rule_idx);
+  const long long nk = (long long)a.ictr[kIcKept];
+  R* ipos = (R*)a.ipos;
+  R* idef = (R*)a.idef;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k0 = warp * 32; k0 < nk; k0 += nwarp * 32) {
+    const long long k = k0 + lane;
+    int j = 0, s = 0, fl = kExpDead, ns = 0;
+    double tau = 0.0;
+    gl::MidState mid;
+    if (k < nk) {
+      j = a.klist[k];
+      if (a.offsets) {
+        s = (int)owner_of(a.offsets, a.n_sets, j);
+      } else {
+        s = (int)((unsigned)j / (unsigned)a.n_times);
+      }
+      const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)s * a.n_times;
+      fl = exposure_prep<R>(a.sets[s], a.t[ti], &tau, &mid);
+      if (fl & kExpDead) a.out[j] = 1.0;
+      else ns = a.sets[s].nsuper;
+    }
+    __syncwarp();
+    int tot_items, n_live;
+    const int off = warp_scan(ns, &tot_items);
+    const int roff = warp_scan(ns > 0 ? 1 : 0, &n_live);
+    unsigned long long b0 = 0, r0 = 0;
+    if (lane == 0 && tot_items > 0) {
+      b0 = atomicAdd(&a.ictr[kIcItems], (unsigned long long)tot_items);
+      if ((long long)b0 + tot_items <= a.item_cap)
+        r0 = atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_live);   // records <= items
+    }
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    if (tot_items == 0) continue;
+    if ((long long)b0 + tot_items > a.item_cap) {   // workspace full
+      if (ns > 0) a.out[j] = exposure_local<R>(a.sets[s], fl, mid, tau, ns, rl);
+      continue;
+    }
+    const long long b = (long long)b0 + off;
+    int nf = 0, np = 0;
+    if (ns > 0) {
+      const SetConst& c = a.sets[s];
+      a.rj[r0 + roff] = j;
+      a.rfirst[r0 + roff] = (int)b;
+      a.rns[r0 + roff] = ns;
+      for (int q = 0; q < ns; ++q) {
+        R x, y, o;
+        const int cls = item_geometry<R>(c, fl, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
+        const long long g = b + q;
+        a.icls[g] = cls;
+        if (cls == gl::kOut) {
+          idef[g] = R(0);
+          continue;
+        }
+        ipos[3 * g] = x;
+        ipos[3 * g + 1] = y;
+        ipos[3 * g + 2] = o;
+        a.iset[g] = s;
+        if (cls == gl::kFull) ++nf; else ++np;
+      }
+    }
+    __syncwarp();
+    int tf, tp;
+    const int of = warp_scan(nf, &tf), op = warp_scan(np, &tp);
+    unsigned long long qf0 = 0, qp0 = 0;
+    if (lane == 0) {
+      if (tf) qf0 = atomicAdd(&a.ictr[kIcFull], (unsigned long long)tf);
+      if (tp) qp0 = atomicAdd(&a.ictr[kIcPart], (unsigned long long)tp);
+    }
+    qf0 = __shfl_sync(0xffffffffu, qf0, 0);
+    qp0 = __shfl_sync(0xffffffffu, qp0, 0);
+    long long fpos = (long long)qf0 + of, ppos = (long long)qp0 + op;
+    for (int q = 0; q < ns; ++q) {
+      const long long g = b + q;
+      const int cls = a.icls[g];
+      if (cls == gl::kFull) a.iq[fpos++] = (int)g;
+      else if (cls == gl::kPartial) a.iq[a.item_cap - 1 - (ppos++)] = (int)g;
+    }
+  }
+}
+
+// Item pipeline, stage 3: the quadrature of every queued item, spread over the
+// whole GPU.  Each warp takes 32 consecutive queue positions at a time: crossing
+// items (the heavier ones) first, then whole-ellipse items, so a warp's lanes
+// mostly follow the same path and the last warps to finish have light work.
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) gl_items_quad_kernel(LcArgs a) {
+  const NodeRule<R>& rl = lc_rule<R>(a.rule_idx);
+  const long long np = (long long)a.ictr[kIcPart], nf = (long long)a.ictr[kIcFull];
+  const long long total = np + nf;
+  const R* ipos = (const R*)a.ipos;
+  R* idef = (R*)a.idef;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(&a.ictr[kIcFetch], 32ull);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if ((long long)b >= total) break;
+    const long long u = (long long)b + lane;
+    if (u < total) {
+      const bool part = u < np;
+      const long long g = part ? a.iq[a.item_cap - 1 - u] : a.iq[u - np];
+      const SetConst& c = a.sets[a.iset[g]];
+      idef[g] = item_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2],
+                                part ? gl::kPartial : gl::kFull, rl);
+    }
+  }
+}
+
+// Item pipeline, stage 4: the FP64 exposure means, each in item order.
+template <typename R>
+__global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
+  const long long nrec = (long long)a.ictr[kIcRecs];
+  const R* idef = (const R*)a.idef;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrec;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int ns = a.rns[r];
+    const long long f = a.rfirst[r];
+    double acc = 0.0;
+    for (int q = 0; q < ns; ++q) acc += 1.0 - (double)idef[f + q];
+    a.out[a.rj[r]] = acc / ns;
   }
 }
 
@@ -901,6 +1196,14 @@ struct gl_context {
   double* d_err = nullptr;             // autotuner: max |difference| slot
   unsigned long long* d_counts = nullptr;   // GL_COUNT_* slots
   bool counting = false;
+  // item pipeline of the light-curve kernel (grow-only workspace, sized for FP64 items)
+  bool item_pipeline = true;
+  int64_t item_max = kItemMaxDefault;   // most items one call may queue
+  void* d_items = nullptr;
+  size_t items_bytes = 0;
+  unsigned long long* d_ictr = nullptr;    // kIcSlots counters, zeroed by every step
+  int qocc[2] = {0, 0};                    // resident quadrature CTAs per SM (FP64, FP32C)
+  int eocc[2] = {0, 0};                    // resident kept-exposure CTAs per SM
   // graph cache: one captured step per distinct argument set
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
@@ -909,6 +1212,7 @@ struct gl_context {
     size_t key_len;
     cudaGraphExec_t exec;
     uint64_t last_use;
+    int64_t kernels;   // kernel launches in the captured step
   };
   std::vector<GraphEntry> graph_cache;
   uint64_t graph_clock = 0;
@@ -1041,6 +1345,64 @@ int launch_grid(int64_t n, int threads) {
   return (int)b;
 }
 
+// Carve the item workspace (kItemBytes per item) into the kernels' arrays.
+void item_arrays(void* base, int64_t cap, size_t rsize, LcArgs* a) {
+  char* p = (char*)base;
+  auto take = [&](size_t bytes) {
+    char* q = p;
+    p += (bytes + 255) & ~(size_t)255;
+    return q;
+  };
+  a->ipos = take(3 * rsize * (size_t)cap);
+  a->idef = take(rsize * (size_t)cap);
+  a->iset = (int*)take(sizeof(int) * (size_t)cap);
+  a->iq = (int*)take(sizeof(int) * (size_t)cap);
+  a->rj = (int*)take(sizeof(int) * (size_t)cap);
+  a->rfirst = (int*)take(sizeof(int) * (size_t)cap);
+  a->rns = (int*)take(sizeof(int) * (size_t)cap);
+  a->icls = (int*)take(sizeof(int) * (size_t)cap);
+  a->item_cap = cap;
+  a->klist = (int*)p;   // n_total entries
+}
+
+size_t item_workspace_bytes(int64_t cap, int64_t n_total) {
+  return (size_t)cap * kItemBytes + (size_t)n_total * sizeof(int) + 9 * 256;
+}
+
+// The item pipeline: window tests, kept exposures, quadrature, exposure sums.
+template <typename R>
+int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
+  int& qocc = ctx->qocc[sizeof(R) == 4 ? 1 : 0];
+  int& eocc = ctx->eocc[sizeof(R) == 4 ? 1 : 0];
+  if (qocc == 0) {
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qocc, gl_items_quad_kernel<R, 128>,
+                                                               128, 0));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&eocc, gl_exp_kernel<R>, 128, 0));
+    if (qocc < 1 || eocc < 1) return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
+  }
+  GL_CUDA(ctx, cudaMemsetAsync(ctx->d_ictr, 0, kIcSlots * sizeof(unsigned long long), st));
+  int64_t wb = (args.n_total + 1023) / 1024;   // at least 4 passes of 256 per block
+  if (wb > (int64_t)ctx->sms * 8) wb = (int64_t)ctx->sms * 8;
+  if (wb < 1) wb = 1;
+  long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
+  gl_win_kernel<<<(int)wb, 256, 0, st>>>(args);
+  gl_exp_kernel<R><<<ctx->sms * eocc, 128, 0, st>>>(args);
+  prof_end(ctx, GL_KERNEL_CURVE, pe, st);
+  ctx->launches += 2;
+  GL_CUDA(ctx, cudaGetLastError());
+  pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
+  gl_items_quad_kernel<R, 128><<<ctx->sms * qocc, 128, 0, st>>>(args);
+  prof_end(ctx, GL_KERNEL_QUAD, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  pe = prof_begin(ctx, GL_KERNEL_SUM, st);
+  gl_items_sum_kernel<R><<<ctx->sms * 2, 256, 0, st>>>(args);
+  prof_end(ctx, GL_KERNEL_SUM, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
 template <typename R, int NT, bool COUNT>
 int launch_lc_nt(gl_context* ctx, LcArgs args, int occ_slot, cudaStream_t st) {
   size_t smem = LcSmem<R>::total(args.tile, args.cap);
@@ -1065,7 +1427,8 @@ int launch_lc_nt(gl_context* ctx, LcArgs args, int occ_slot, cudaStream_t st) {
 }
 
 // occupancy is cached per (precision, counting, threads) instance
-bool lc_ready(const gl_context* ctx, int prec) {
+bool lc_ready(const gl_context* ctx, int prec, bool items) {
+  if (items) return ctx->qocc[prec == GL_FP64 ? 0 : 1] != 0;
   const gl_context::LcCfg& cf = ctx->cfg[prec == GL_FP64 ? 0 : 1];
   int slot = (prec == GL_FP64 ? 0 : 1) + (ctx->counting ? 2 : 0) + (cf.threads == 128 ? 4 : 0);
   return ctx->occ[slot] != 0;
@@ -1081,12 +1444,14 @@ int launch_lc(gl_context* ctx, const LcArgs& args0, cudaStream_t st) {
   args.n_tiles = (int)((args.n_total + cf.tile - 1) / cf.tile);
   args.tile_counter = ctx->d_counter;
   args.counts = ctx->d_counts;
+  if (args.ipos && !COUNT) return launch_items<R>(ctx, args, st);
   int slot = (sizeof(R) == 4 ? 1 : 0) + (COUNT ? 2 : 0) + (cf.threads == 128 ? 4 : 0);
   if (cf.threads == 128) return launch_lc_nt<R, 128, COUNT>(ctx, args, slot, st);
   return launch_lc_nt<R, 256, COUNT>(ctx, args, slot, st);
 }
 
-// One light-curve step: per-set constants, then the fused kernel.
+// One light-curve step: per-set constants, then the fused kernel (and, with the
+// item pipeline, its quadrature and exposure-sum stages).
 struct StepArgs {
   ParamPtrs pp;
   int64_t n_sets;
@@ -1096,6 +1461,8 @@ struct StepArgs {
   double* out;
   int prec;
   SetConst* sets;
+  void* items;        // item workspace, or null: every tile integrates locally
+  int64_t item_cap;
 };
 
 int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
@@ -1114,6 +1481,10 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
   la.n_sets = sa.n_sets;
   la.n_total = sa.n_total;
   la.out = sa.out;
+  if (sa.items) {
+    item_arrays(sa.items, sa.item_cap, sa.prec == GL_FP64 ? sizeof(double) : sizeof(float), &la);
+    la.ictr = ctx->d_ictr;
+  }
   if (sa.prec == GL_FP64)
     return ctx->counting ? launch_lc<double, true>(ctx, la, st) : launch_lc<double, false>(ctx, la, st);
   return ctx->counting ? launch_lc<float, true>(ctx, la, st) : launch_lc<float, false>(ctx, la, st);
@@ -1129,10 +1500,11 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     if (g.key_len == sizeof key && memcmp(g.key, key, sizeof key) == 0) hit = &g;
   if (!hit) {
     // the occupancy query and attribute setting must not happen inside a capture
-    if (!lc_ready(ctx, sa.prec)) return enqueue_step(ctx, sa, st);   // first call: eager
+    if (!lc_ready(ctx, sa.prec, sa.items != nullptr)) return enqueue_step(ctx, sa, st);   // first call: eager
     GL_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int64_t l0 = ctx->launches;
     int rc = enqueue_step(ctx, sa, ctx->cap_stream);
+    const int64_t kernels = ctx->launches - l0;
     ctx->launches = l0;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
@@ -1157,12 +1529,13 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     ge.key_len = sizeof key;
     ge.exec = exec;
     ge.last_use = 0;
+    ge.kernels = kernels;
     ctx->graph_cache.push_back(ge);
     hit = &ctx->graph_cache.back();
   }
   hit->last_use = ++ctx->graph_clock;
   GL_CUDA(ctx, cudaGraphLaunch(hit->exec, st));
-  ctx->launches += 2;
+  ctx->launches += hit->kernels;
   ctx->graph_launches++;
   return GL_OK;
 }
@@ -1210,6 +1583,8 @@ int gl_context_destroy(gl_context* ctx) {
   if (ctx->d_counter) cudaFree(ctx->d_counter);
   if (ctx->d_counts) cudaFree(ctx->d_counts);
   if (ctx->d_ref) cudaFree(ctx->d_ref);
+  if (ctx->d_items) cudaFree(ctx->d_items);
+  if (ctx->d_ictr) cudaFree(ctx->d_ictr);
   for (void* q : {(void*)ctx->sx, (void*)ctx->sy, (void*)ctx->so, (void*)ctx->sfeat,
                   (void*)ctx->sscale, (void*)ctx->sdsph, (void*)ctx->sthat, (void*)ctx->sdef,
                   (void*)ctx->stable, (void*)ctx->sset, (void*)ctx->scls, (void*)ctx->sfb,
@@ -1255,6 +1630,16 @@ int gl_graphs_enable(gl_context* ctx, int on) {
 }
 
 int64_t gl_graph_launches(const gl_context* ctx) { return ctx ? ctx->graph_launches : 0; }
+
+int gl_item_pipeline(gl_context* ctx, int on, int64_t max_items) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (max_items < 0 || max_items >= (1LL << 31)) return fail(ctx, GL_EINVAL, "max_items out of range");
+  ctx->item_pipeline = on != 0;
+  ctx->item_max = max_items > 0 ? max_items : kItemMaxDefault;
+  drop_graphs(ctx);
+  return GL_OK;
+}
 
 int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
                 gl_precision prec, void* stream, gl_tune_report* rep) {
@@ -1482,8 +1867,23 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
     if (rc) return rc;
     d_out = ctx->d_out;
   }
+  void* iws = nullptr;
+  int64_t item_cap = 0;
+  if (ctx->item_pipeline) {
+    // sized for every sub-exposure of the batch (per-set nsuper: 16 per exposure),
+    // capped at item_max; tiles whose items do not fit integrate locally
+    int64_t per = tm->nsuper ? 16 : tm->nsuper_all;
+    item_cap = tm->n_total > ctx->item_max / per ? ctx->item_max : tm->n_total * per;
+    rc = grow(ctx, &ctx->d_items, &ctx->items_bytes, item_workspace_bytes(item_cap, tm->n_total));
+    if (rc) return rc;
+    if (!ctx->d_ictr)
+      GL_CUDA(ctx, cudaMalloc(&ctx->d_ictr, kIcSlots * sizeof(unsigned long long)));
+    iws = ctx->d_items;
+  }
   StepArgs sa;
   memset(&sa, 0, sizeof sa);
+  sa.items = iws;
+  sa.item_cap = item_cap;
   sa.pp = pp;
   sa.n_sets = n_sets;
   sa.offsets = offsets;

@@ -1,0 +1,110 @@
+"""GPU: the item pipeline of the light-curve kernel gives bit-identical output.
+
+With the pipeline on, tiles of exposures hand their in-window sub-exposures to a
+global queue that a second kernel integrates and a third sums per exposure; with
+it off each tile integrates its own; with a small workspace some tiles do one and
+some the other.  Every item is evaluated with the same arithmetic and every
+exposure is summed in sub-exposure order, so all three must agree bit for bit, on
+both precisions, for a shared time grid, a ragged CSR batch and eccentric orbits.
+"""
+import numpy as np
+import pytest
+
+from paper_2410_05408_b300 import binding, inputs
+
+from _common import nsuper_array, product_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = [binding.GL_FP64, binding.GL_FP32C]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.array(a, copy=True)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _prepare(wl):
+    p = product_params(wl)
+    n_sets = len(p["t0"])
+    exptime = np.ascontiguousarray(np.broadcast_to(wl["exptime"], (n_sets,)), dtype=np.float64)
+    offsets = wl.get("offsets")
+    n_total = n_sets * len(wl["t"]) if offsets is None else int(offsets[-1])
+    return dict(p={k: _dev(v) for k, v in p.items()}, t=_dev(wl["t"]), exptime=_dev(exptime),
+                ns=_dev(nsuper_array(wl, n_sets), torch.int32),
+                offsets=None if offsets is None else _dev(offsets, torch.int64), n_total=n_total)
+
+
+def _run(ctx, d, prec):
+    out = torch.empty(d["n_total"], dtype=torch.float64, device="cuda")
+    for _ in range(2):   # eager first call, then the captured graph
+        ctx.lightcurve(d["p"], d["t"], out, d["exptime"], nsuper=d["ns"], offsets=d["offsets"],
+                       precision=prec)
+    torch.cuda.synchronize()
+    assert ctx.sync() == binding.GL_OK
+    return out.cpu().numpy()
+
+
+def _items(ctx, d, prec):
+    ctx.counts(True)
+    _run(ctx, d, prec)
+    n = ctx.counts_read()["items"]
+    ctx.counts(False)
+    return n
+
+
+WORKLOADS = {
+    "mcmc_batch": lambda: inputs.mcmc_batch(seed=11),
+    "uneven_batch": lambda: inputs.uneven_batch(seed=12),
+    "extreme_orbits": lambda: inputs.extreme_orbits(seed=13),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+@pytest.mark.parametrize("prec", PRECS)
+def test_pipeline_local_and_mixed_are_bit_identical(ctx, name, prec):
+    d = _prepare(WORKLOADS[name]())
+    try:
+        ctx.item_pipeline(True)
+        on = _run(ctx, d, prec)
+        items = _items(ctx, d, prec)
+        ctx.item_pipeline(False)
+        off = _run(ctx, d, prec)
+        # a workspace smaller than the batch's items but larger than one tile's
+        # (256 exposures x 15): the first tiles queue, later ones integrate locally
+        cap = max(4000, items // 3)
+        ctx.item_pipeline(True, cap)
+        mixed = _run(ctx, d, prec)
+    finally:
+        ctx.item_pipeline(True)
+    assert items > 0
+    for other in (off, mixed):
+        same = (on == other) | (np.isnan(on) & np.isnan(other))
+        assert same.all(), (int((~same).sum()), float(np.nanmax(np.abs(on - other))))
+    assert (on < 1.0).sum() > 0
+
+
+def test_pipeline_setting_is_validated(ctx):
+    with pytest.raises(binding.GLError):
+        ctx.item_pipeline(True, -1)
+    with pytest.raises(binding.GLError):
+        ctx.item_pipeline(True, 1 << 31)
+    ctx.item_pipeline(True)
+
+
+def test_pipeline_kernels_are_profiled(ctx):
+    d = _prepare(inputs.mcmc_batch(seed=14))
+    ctx.profile(True)
+    _run(ctx, d, binding.GL_FP32C)
+    got = {k: ctx.profile_read(k)[1] for k in (binding.GL_KERNEL_SETUP, binding.GL_KERNEL_CURVE,
+                                                binding.GL_KERNEL_QUAD, binding.GL_KERNEL_SUM)}
+    ctx.profile(False)
+    assert all(n == 2 for n in got.values()), got
