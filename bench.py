@@ -50,15 +50,16 @@ def alu_peaks(sm_mhz: float):
 
 # Algorithmic work per unit of the FP32C light-curve step (flops, FMA = 2),
 # counted from the source (see the kernel section of the design doc), by kernel:
-#   tiles (gl_lc_kernel): FP32 per exposure window test 12, per sub-exposure
-#         position and class 40; FP64 per in-window exposure 10 (exact window),
-#         midpoint Kepler state 250, per sub-exposure FP64 Kepler (no expansion) 250
-#   quadrature (gl_items_quad_kernel): FP32 whole-ellipse item 1175 (inner maxima
+#   exposures (gl_win_kernel + gl_exp_kernel): FP32 per exposure window test 12,
+#         per sub-exposure position and class 40; FP64 per in-window exposure 10
+#         (exact window), midpoint Kepler state 250, per sub-exposure FP64 Kepler
+#         (no expansion) 250
+#   quadrature (gl_items_quad_kernel, then gl_items_sum_kernel): FP32 whole-ellipse item 1175 (inner maxima
 #         310, geometry 30, 20 nodes x 41, closed forms 15), crossing item 2300
 #         (maxima 310, FP32 Ferrari 290, breakpoints 50, 1.5 arcs x (20 nodes x 49
 #         + 80), limb arcs 25, geometry 30); FP64 crossing item 200 (limb
-#         polynomial, frame, Newton polish, sign tests)
-#   exposure sums (gl_items_sum_kernel): FP64 2 per sub-exposure
+#         polynomial, frame, Newton polish, sign tests), exposure sums 2 per
+#         sub-exposure
 F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 1175, 2300
 F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 250, 200, 2
 
@@ -69,8 +70,7 @@ def kernel_flops(c: dict) -> dict:
         "tiles": (c["exposures"] * F32_EXPOSURE + c["items"] * F32_ITEM,
                   c["in_window"] * F64_WINDOW + (c["kepler"] + c["item_kepler"]) * F64_KEPLER),
         "quadrature": (c["full"] * F32_FULL + c["partial"] * F32_PARTIAL,
-                       c["partial"] * F64_PARTIAL),
-        "sums": (0, c["items"] * F64_SUM),
+                       c["partial"] * F64_PARTIAL + c["items"] * F64_SUM),
     }
 
 
@@ -90,8 +90,8 @@ def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak:
             "kernel_ms": ms}
 
 
-KERNEL_NAMES = {"tiles": "gl_lc_kernel", "quadrature": "gl_items_quad_kernel",
-                "sums": "gl_items_sum_kernel"}
+KERNEL_NAMES = {"tiles": "gl_win_kernel+gl_exp_kernel",
+                "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
 
 
 def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float) -> dict:
@@ -560,7 +560,7 @@ def main():
         if profile:
             for name, kind in (("tiles", binding.GL_KERNEL_CURVE),
                                ("quadrature", binding.GL_KERNEL_QUAD),
-                               ("sums", binding.GL_KERNEL_SUM), ("setup", binding.GL_KERNEL_SETUP)):
+                               ("setup", binding.GL_KERNEL_SETUP)):
                 t_ms, n = ctx.profile_read(kind)
                 kern[name] = t_ms / n if n else None
             ctx.profile(False)

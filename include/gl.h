@@ -212,11 +212,11 @@ int64_t gl_graph_launches(const gl_context *ctx);
  * exposure (flux 1 outside the transit window), one thread per kept exposure
  * (Kepler midpoint state, position and overlap class of each sub-exposure,
  * Sec. 2 geometry), the quadrature of every sub-exposure that meets the disk with
- * warps spread over the whole GPU, and each exposure's FP64 mean in sub-exposure
- * order.  With it off, a tile kernel takes consecutive exposures and does all of
+ * warps spread over the whole GPU, and each exposure's FP64 mean in
+ * sub-exposure order.  With it off, a tile kernel takes consecutive exposures and does all of
  * this per tile.  The pipeline balances batches whose transits fall in few
- * places; its workspace (64 bytes per sub-exposure, context-owned, grown on
- * demand and kept) holds n_total x nsuper_all sub-exposures (16 per exposure
+ * places; its workspace (56 bytes per sub-exposure and 8 per exposure,
+ * context-owned, grown on demand and kept) holds n_total x nsuper_all sub-exposures (16 per exposure
  * with per-set nsuper), at most `max_items` (0 = default 2^23); an exposure that
  * does not fit is finished by the thread holding it.  Every sub-exposure is
  * evaluated by the same compiled functions and every exposure summed in the same
@@ -258,8 +258,8 @@ int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *
                                kept-exposure kernels (FP64 or FP32C) */
 #define GL_KERNEL_SKY 2     /* geometry-level kernel */
 #define GL_KERNEL_SPHERE 3  /* spherical-planet kernel */
-#define GL_KERNEL_QUAD 4    /* item pipeline: quadrature of queued sub-exposures */
-#define GL_KERNEL_SUM 5     /* item pipeline: exposure means */
+#define GL_KERNEL_QUAD 4    /* item pipeline: quadrature of queued sub-exposures and the
+                               exposure means (two kernels) */
 #define GL_KERNEL_KINDS 8
 
 /* Per-kernel device timing for benchmarks.  While enabled (on != 0), every

@@ -47,7 +47,6 @@ GL_KERNEL_CURVE = 1
 GL_KERNEL_SKY = 2
 GL_KERNEL_SPHERE = 3
 GL_KERNEL_QUAD = 4
-GL_KERNEL_SUM = 5
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 

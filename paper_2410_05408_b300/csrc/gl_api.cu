@@ -33,24 +33,43 @@ enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4, k
 
 // quadrature orders: FP64 path and FP32C path
 constexpr int kNodes64 = 32;
+constexpr int kNodes64Wide = 48;   // FP64 order for large, strongly flattened shapes
 constexpr int kNodes32 = 20;
 
 // item pipeline workspace: at most this many sub-exposure items per call by
 // default; per item 3 positions + deficit (FP64 sizing) + set + class + queue
-// slot + record (output index, first item, count); plus one int per exposure
+// slot + record (output index, first item, count); plus two ints per exposure
 // for the kept-exposure list
 constexpr int64_t kItemMaxDefault = 1LL << 23;
 constexpr size_t kItemBytes = 4 * sizeof(double) + 6 * sizeof(int);
 
 __constant__ NodeRule<double> c_rule64;
+__constant__ NodeRule<double> c_rule64_wide;
 __constant__ NodeRule<float> c_rule32;                 // default order (kNodes32)
 // orders the autotuner may choose for the FP32C light-curve kernel
 constexpr int kTuneNodes[4] = {16, 20, 24, 28};
+constexpr int kRuleDefault = 1;   // 20 nodes
 __constant__ NodeRule<float> c_rule32_tuned[4];
 
 template <typename R> __device__ __forceinline__ const NodeRule<R>& rule();
 template <> __device__ __forceinline__ const NodeRule<double>& rule<double>() { return c_rule64; }
 template <> __device__ __forceinline__ const NodeRule<float>& rule<float>() { return c_rule32; }
+
+// Quadrature rule of parameter set c: FP64 (32 nodes, 48 for shapes with a
+// raised FP32 order), or the FP32 order `base` (index into c_rule32_tuned)
+// raised to the set's least order for its shape.
+template <typename R>
+__device__ __forceinline__ const NodeRule<R>& set_rule(const SetConst& c, int base);
+template <>
+__device__ __forceinline__ const NodeRule<double>& set_rule<double>(const SetConst& c, int) {
+  // shapes that need more FP32 nodes also need more FP64 ones: 32 nodes leave
+  // errors up to 3e-10 near tangency there, 48 keep them below 1e-12
+  return c.rule_min > 0 ? c_rule64_wide : c_rule64;
+}
+template <>
+__device__ __forceinline__ const NodeRule<float>& set_rule<float>(const SetConst& c, int base) {
+  return c_rule32_tuned[base > c.rule_min ? base : c.rule_min];
+}
 
 // ------------------------------------------------------------------ kernels
 struct ParamPtrs {
@@ -121,7 +140,6 @@ __global__ void __launch_bounds__(256) gl_curve_kernel(const SetConst* __restric
                                                        int64_t n_times, int64_t n_sets,
                                                        int64_t n_total,
                                                        double* __restrict__ out) {
-  const NodeRule<R>& rl = rule<R>();
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_total;
        j += (int64_t)gridDim.x * blockDim.x) {
     int64_t s;
@@ -147,7 +165,7 @@ __global__ void __launch_bounds__(256) gl_curve_kernel(const SetConst* __restric
     double acc = 0.0;
     for (int q = 0; q < ns; ++q) {
       double tq = tau + gl::subexposure_offset(q, ns, c.exptime);
-      acc += gl::subexposure_flux<R>(c, tq, rl);
+      acc += gl::subexposure_flux<R>(c, tq, set_rule<R>(c, kRuleDefault));
     }
     out[j] = acc / ns;
   }
@@ -219,20 +237,18 @@ struct LcArgs {
   int* iq;                      // whole-ellipse items from the front, crossing items from the back
   int *rj, *rfirst, *rns;       // exposure records: output index, first item, sub-exposures
   int* klist;                   // kept exposures (output index); n_total entries
+  int* kset;                    // their parameter sets; n_total entries
   unsigned long long* ictr;     // kIc* counters
   int64_t item_cap;
-  int* icls;                    // overlap class of each item
+  int* icls;                    // overlap class of each item (exposures of more than 32 items)
 };
 
 enum : int {
   kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcSlots = 6
 };
 
-template <typename R> __device__ __forceinline__ const NodeRule<R>& lc_rule(int idx);
-template <> __device__ __forceinline__ const NodeRule<double>& lc_rule<double>(int) { return c_rule64; }
-template <> __device__ __forceinline__ const NodeRule<float>& lc_rule<float>(int idx) {
-  return idx < 0 ? c_rule32 : c_rule32_tuned[idx];
-}
+// Index of the batch's FP32 quadrature order in c_rule32_tuned (-1 = default).
+__device__ __forceinline__ int rule_base(int idx) { return idx < 0 ? kRuleDefault : idx; }
 
 template <typename R>
 struct LcSmem {
@@ -327,9 +343,18 @@ __device__ __noinline__ int exposure_prep(const SetConst& c, double t, double* t
   *tau_out = tau;
   if (!gl::in_window(c, tau, 0.5 * c.exptime)) return kExpDead;
   if (sizeof(R) == 4 && (c.flags & gl::kSetTaylor)) {
-    gl::SkyState st;
-    gl::sky_state(c, tau, &st);
-    *mid = gl::mid_state(st);
+    if (c.nsuper == 1) {
+      // the one sub-exposure sits at the midpoint: no derivatives needed (the
+      // Taylor step with dt = 0 returns the midpoint values unchanged)
+      gl::SkyState st;
+      gl::sky_position(c, tau, &st.x, &st.y, &st.z);
+      for (int k = 0; k < 3; ++k) st.d1[k] = st.d2[k] = st.d3[k] = 0.0;
+      *mid = gl::mid_state(st);
+    } else {
+      gl::SkyState st;
+      gl::sky_state(c, tau, &st);
+      *mid = gl::mid_state(st);
+    }
     return kExpTaylor;
   }
   return 0;
@@ -360,10 +385,9 @@ __device__ __noinline__ int item_geometry(const SetConst& c, int flag, const gl:
 
 // Deficit of one item: limb-darkened occulted flux over F0, in precision R.
 template <typename R>
-__device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls,
-                                       const NodeRule<R>& rl) {
+__device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls, int base) {
   R I[3];
-  gl::occulted_r<R>(c, x, y, o, cls, rl, I);
+  gl::occulted_r<R>(c, x, y, o, cls, set_rule<R>(c, base), I);
   return (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
           gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
 }
@@ -372,12 +396,12 @@ __device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls
 // pipeline's fallback when its workspace is full).
 template <typename R>
 __device__ double exposure_local(const SetConst& c, int flag, const gl::MidState& mid, double tau,
-                                 int ns, const NodeRule<R>& rl) {
+                                 int ns, int base) {
   double acc = 0.0;
   for (int q = 0; q < ns; ++q) {
     R x, y, o;
     const int cls = item_geometry<R>(c, flag, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
-    const R d = cls == gl::kOut ? R(0) : item_deficit<R>(c, x, y, o, cls, rl);
+    const R d = cls == gl::kOut ? R(0) : item_deficit<R>(c, x, y, o, cls, base);
     acc += 1.0 - (double)d;
   }
   return acc / ns;
@@ -402,7 +426,7 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
   R* it_def = (R*)(smem + LcSmem<R>::def(tile_sz, cap));
   int* q_full = (int*)(smem + LcSmem<R>::qf(tile_sz, cap));
   int* q_part = (int*)(smem + LcSmem<R>::qp(tile_sz, cap));
-  const NodeRule<R>& rl = lc_rule<R>(a.rule_idx);
+  const int rb = rule_base(a.rule_idx);
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -522,7 +546,7 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
         int k = packed & 0xffff, i = packed >> 16;
         const SetConst& c = a.sets[e_s[i]];
         it_def[k] = item_deficit<R>(c, it_pos[3 * k], it_pos[3 * k + 1], it_pos[3 * k + 2],
-                                    u < nf ? gl::kFull : gl::kPartial, rl);
+                                    u < nf ? gl::kFull : gl::kPartial, rb);
       }
       __syncthreads();
       // ---- phase 5: FP64 accumulation in item order
@@ -578,7 +602,10 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
         a.out[j] = 1.0;
     }
     const long long slot = warp_append(&a.ictr[kIcKept], keep);
-    if (keep) a.klist[slot] = (int)j;   // at most n_total entries
+    if (keep) {   // at most n_total entries
+      a.klist[slot] = (int)j;
+      a.kset[slot] = s;
+    }
     if (a.offsets) {
       __syncthreads();
       if (j < hi && (threadIdx.x == 255 || j == hi - 1)) s_set = s;   // owner of the pass's last exposure
@@ -590,11 +617,11 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
 // Item pipeline, stage 2: one lane per kept exposure, 32 kept exposures per warp
 // and pass.  Sub-exposure slots and exposure records are taken with one atomic
 // add per warp, then the queue positions of the items that meet the disk with
-// two more.  A warp whose items do not fit the workspace finishes its exposures
-// itself.
+// two more.  An exposure none of whose items meets the disk gets flux 1 at once.
+// A warp whose items do not fit the workspace finishes its exposures itself.
 template <typename R>
 __global__ void __launch_bounds__(128) gl_exp_kernel(LcArgs a) {
-  const NodeRule<R>& rl = lc_rule<R>(a.rule_idx);
+  const int rb = rule_base(a.rule_idx);
   const long long nk = (long long)a.ictr[kIcKept];
   R* ipos = (R*)a.ipos;
   R* idef = (R*)a.idef;
@@ -608,45 +635,34 @@ __global__ void __launch_bounds__(128) gl_exp_kernel(LcArgs a) {
     gl::MidState mid;
     if (k < nk) {
       j = a.klist[k];
-      if (a.offsets) {
-        s = (int)owner_of(a.offsets, a.n_sets, j);
-      } else {
-        s = (int)((unsigned)j / (unsigned)a.n_times);
-      }
+      s = a.kset[k];
       const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)s * a.n_times;
       fl = exposure_prep<R>(a.sets[s], a.t[ti], &tau, &mid);
       if (fl & kExpDead) a.out[j] = 1.0;
       else ns = a.sets[s].nsuper;
     }
     __syncwarp();
-    int tot_items, n_live;
+    int tot_items;
     const int off = warp_scan(ns, &tot_items);
-    const int roff = warp_scan(ns > 0 ? 1 : 0, &n_live);
-    unsigned long long b0 = 0, r0 = 0;
-    if (lane == 0 && tot_items > 0) {
-      b0 = atomicAdd(&a.ictr[kIcItems], (unsigned long long)tot_items);
-      if ((long long)b0 + tot_items <= a.item_cap)
-        r0 = atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_live);   // records <= items
-    }
+    unsigned long long b0 = 0;
+    if (lane == 0 && tot_items > 0) b0 = atomicAdd(&a.ictr[kIcItems], (unsigned long long)tot_items);
     b0 = __shfl_sync(0xffffffffu, b0, 0);
-    r0 = __shfl_sync(0xffffffffu, r0, 0);
     if (tot_items == 0) continue;
     if ((long long)b0 + tot_items > a.item_cap) {   // workspace full
-      if (ns > 0) a.out[j] = exposure_local<R>(a.sets[s], fl, mid, tau, ns, rl);
+      if (ns > 0) a.out[j] = exposure_local<R>(a.sets[s], fl, mid, tau, ns, rb);
       continue;
     }
     const long long b = (long long)b0 + off;
     int nf = 0, np = 0;
+    unsigned long long cmask = 0;   // 2 bits per item, items 0..31
     if (ns > 0) {
       const SetConst& c = a.sets[s];
-      a.rj[r0 + roff] = j;
-      a.rfirst[r0 + roff] = (int)b;
-      a.rns[r0 + roff] = ns;
       for (int q = 0; q < ns; ++q) {
         R x, y, o;
         const int cls = item_geometry<R>(c, fl, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
         const long long g = b + q;
-        a.icls[g] = cls;
+        if (q < 32) cmask |= (unsigned long long)cls << (2 * q);
+        else a.icls[g] = cls;
         if (cls == gl::kOut) {
           idef[g] = R(0);
           continue;
@@ -657,23 +673,35 @@ __global__ void __launch_bounds__(128) gl_exp_kernel(LcArgs a) {
         a.iset[g] = s;
         if (cls == gl::kFull) ++nf; else ++np;
       }
+      if (nf + np == 0) a.out[j] = 1.0;   // = (sum of ns ones) / ns, exactly
     }
+    // records for exposures with work in the quadrature kernel (records <= items)
+    const bool rec_needed = nf + np > 0;
     __syncwarp();
-    int tf, tp;
+    int n_rec, tf, tp;
+    const int roff = warp_scan(rec_needed ? 1 : 0, &n_rec);
     const int of = warp_scan(nf, &tf), op = warp_scan(np, &tp);
-    unsigned long long qf0 = 0, qp0 = 0;
+    unsigned long long r0 = 0, qf0 = 0, qp0 = 0;
     if (lane == 0) {
+      if (n_rec) r0 = atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_rec);
       if (tf) qf0 = atomicAdd(&a.ictr[kIcFull], (unsigned long long)tf);
       if (tp) qp0 = atomicAdd(&a.ictr[kIcPart], (unsigned long long)tp);
     }
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
     qf0 = __shfl_sync(0xffffffffu, qf0, 0);
     qp0 = __shfl_sync(0xffffffffu, qp0, 0);
+    if (!rec_needed) continue;
+    const long long r = (long long)r0 + roff;
+    a.rj[r] = j;
+    a.rfirst[r] = (int)b;
+    a.rns[r] = ns;
     long long fpos = (long long)qf0 + of, ppos = (long long)qp0 + op;
     for (int q = 0; q < ns; ++q) {
       const long long g = b + q;
-      const int cls = a.icls[g];
+      const int cls = q < 32 ? (int)((cmask >> (2 * q)) & 3u) : a.icls[g];
+      if (cls == gl::kOut) continue;
       if (cls == gl::kFull) a.iq[fpos++] = (int)g;
-      else if (cls == gl::kPartial) a.iq[a.item_cap - 1 - (ppos++)] = (int)g;
+      else a.iq[a.item_cap - 1 - (ppos++)] = (int)g;
     }
   }
 }
@@ -684,7 +712,7 @@ __global__ void __launch_bounds__(128) gl_exp_kernel(LcArgs a) {
 // mostly follow the same path and the last warps to finish have light work.
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) gl_items_quad_kernel(LcArgs a) {
-  const NodeRule<R>& rl = lc_rule<R>(a.rule_idx);
+  const int rb = rule_base(a.rule_idx);
   const long long np = (long long)a.ictr[kIcPart], nf = (long long)a.ictr[kIcFull];
   const long long total = np + nf;
   const R* ipos = (const R*)a.ipos;
@@ -701,12 +729,13 @@ __global__ void __launch_bounds__(NT) gl_items_quad_kernel(LcArgs a) {
       const long long g = part ? a.iq[a.item_cap - 1 - u] : a.iq[u - np];
       const SetConst& c = a.sets[a.iset[g]];
       idef[g] = item_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2],
-                                part ? gl::kPartial : gl::kFull, rl);
+                                part ? gl::kPartial : gl::kFull, rb);
     }
   }
 }
 
-// Item pipeline, stage 4: the FP64 exposure means, each in item order.
+// Item pipeline, stage 4: the FP64 mean of each exposure with items on the disk,
+// summed in sub-exposure order.
 template <typename R>
 __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
   const long long nrec = (long long)a.ictr[kIcRecs];
@@ -1005,13 +1034,12 @@ __global__ void gl_sur_fallback_kernel(const SetConst* __restrict__ sets, const 
                                        const unsigned long long* __restrict__ n_fb,
                                        float* __restrict__ def) {
   const int64_t n = (int64_t)*n_fb;
-  const NodeRule<float>& rl = rule<float>();
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     int it = fb[u];
     const SetConst& c = sets[iset[it]];
     float I[3];
-    gl::occulted_r<float>(c, ix[it], iy[it], io[it], icls[it], rl, I);
+    gl::occulted_r<float>(c, ix[it], iy[it], io[it], icls[it], set_rule<float>(c, kRuleDefault), I);
     def[it] = (c.fc0 * I[0] + c.fc1 * I[1] + c.fc2 * I[2]) * c.finvF0;
   }
 }
@@ -1086,7 +1114,6 @@ struct SkyPtrs {
 template <typename R>
 __global__ void __launch_bounds__(256) gl_sky_kernel(SkyPtrs p, int64_t n, double* out,
                                                      int* status) {
-  const NodeRule<R>& rl = rule<R>();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     SetConst c;
@@ -1105,7 +1132,7 @@ __global__ void __launch_bounds__(256) gl_sky_kernel(SkyPtrs p, int64_t n, doubl
       continue;
     }
     R I[3];
-    gl::occulted<R>(c, x0, y0, cls, rl, I);
+    gl::occulted<R>(c, x0, y0, cls, set_rule<R>(c, kRuleDefault), I);
     R def = (R)c.c0 * I[0] + (R)c.c1 * I[1] + (R)c.c2 * I[2];
     out[i] = 1.0 - (double)def * c.invF0;
   }
@@ -1151,10 +1178,12 @@ cudaError_t ensure_device_tables(int device) {
   if ((int)g_dev_ready.size() <= device) g_dev_ready.resize(device + 1, 0);
   if (g_dev_ready[device]) return cudaSuccess;
   NodeRule<double> r64 = build_rule<double>(kNodes64);
+  NodeRule<double> r64w = build_rule<double>(kNodes64Wide);
   NodeRule<float> r32 = build_rule<float>(kNodes32);
   NodeRule<float> rt[4];
   for (int i = 0; i < 4; ++i) rt[i] = build_rule<float>(kTuneNodes[i]);
   cudaError_t e = cudaMemcpyToSymbol(c_rule64, &r64, sizeof r64);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule64_wide, &r64w, sizeof r64w);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32, &r32, sizeof r32);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32_tuned, rt, sizeof rt);
   if (e == cudaSuccess) g_dev_ready[device] = 1;
@@ -1346,7 +1375,7 @@ int launch_grid(int64_t n, int threads) {
 }
 
 // Carve the item workspace (kItemBytes per item) into the kernels' arrays.
-void item_arrays(void* base, int64_t cap, size_t rsize, LcArgs* a) {
+void item_arrays(void* base, int64_t cap, int64_t n_total, size_t rsize, LcArgs* a) {
   char* p = (char*)base;
   auto take = [&](size_t bytes) {
     char* q = p;
@@ -1362,11 +1391,12 @@ void item_arrays(void* base, int64_t cap, size_t rsize, LcArgs* a) {
   a->rns = (int*)take(sizeof(int) * (size_t)cap);
   a->icls = (int*)take(sizeof(int) * (size_t)cap);
   a->item_cap = cap;
-  a->klist = (int*)p;   // n_total entries
+  a->klist = (int*)take(sizeof(int) * (size_t)n_total);
+  a->kset = (int*)take(sizeof(int) * (size_t)n_total);
 }
 
 size_t item_workspace_bytes(int64_t cap, int64_t n_total) {
-  return (size_t)cap * kItemBytes + (size_t)n_total * sizeof(int) + 9 * 256;
+  return (size_t)cap * kItemBytes + (size_t)n_total * 2 * sizeof(int) + 12 * 256;
 }
 
 // The item pipeline: window tests, kept exposures, quadrature, exposure sums.
@@ -1392,13 +1422,9 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   GL_CUDA(ctx, cudaGetLastError());
   pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
   gl_items_quad_kernel<R, 128><<<ctx->sms * qocc, 128, 0, st>>>(args);
-  prof_end(ctx, GL_KERNEL_QUAD, pe, st);
-  ctx->launches++;
-  GL_CUDA(ctx, cudaGetLastError());
-  pe = prof_begin(ctx, GL_KERNEL_SUM, st);
   gl_items_sum_kernel<R><<<ctx->sms * 2, 256, 0, st>>>(args);
-  prof_end(ctx, GL_KERNEL_SUM, pe, st);
-  ctx->launches++;
+  prof_end(ctx, GL_KERNEL_QUAD, pe, st);
+  ctx->launches += 2;
   GL_CUDA(ctx, cudaGetLastError());
   return GL_OK;
 }
@@ -1482,7 +1508,8 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
   la.n_total = sa.n_total;
   la.out = sa.out;
   if (sa.items) {
-    item_arrays(sa.items, sa.item_cap, sa.prec == GL_FP64 ? sizeof(double) : sizeof(float), &la);
+    item_arrays(sa.items, sa.item_cap, sa.n_total, sa.prec == GL_FP64 ? sizeof(double) : sizeof(float),
+                &la);
     la.ictr = ctx->d_ictr;
   }
   if (sa.prec == GL_FP64)

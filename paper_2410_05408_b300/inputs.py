@@ -167,6 +167,18 @@ def geometry_sample(n: int, seed: int = 10, k_range=(0.01, 0.2), f_max: float = 
                 q2=rng.uniform(0, 1, n))
 
 
+def tangency_sample(n: int, seed: int = 21, k_range=(0.01, 0.25), f_max: float = 0.9) -> dict:
+    """Shapes and LD as in geometry_sample, a direction angle, a side (inner:
+    the planet's outline reaches just past the limb from inside; outer: from
+    outside) and a log-uniform offset delta in [1e-8, 1e-3] stellar radii."""
+    rng = _rng(seed)
+    return dict(k=rng.uniform(k_range[0], k_range[1], n), f=rng.uniform(0.0, f_max, n),
+                eta=rng.uniform(0.0, 90.0 * DEG, n), xi=rng.uniform(0.0, 180.0 * DEG, n),
+                q1=rng.uniform(0, 1, n), q2=rng.uniform(0, 1, n),
+                ang=rng.uniform(0.0, 2.0 * np.pi, n), inner=rng.uniform(0, 1, n) < 0.5,
+                delta=10.0 ** rng.uniform(-8.0, -3.0, n))
+
+
 def extreme_orbits(n_sets: int = 48, n_times: int = 3000, seed: int = 11) -> dict:
     """Short-period, eccentric, close-in orbits with long exposures: P U[0.5, 3.5] d,
     a/R* U[2.5, 10.5], e U[0, 0.8], b U[0, 0.45], k U[0.02, 0.22], exposure

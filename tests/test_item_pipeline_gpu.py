@@ -105,6 +105,6 @@ def test_pipeline_kernels_are_profiled(ctx):
     ctx.profile(True)
     _run(ctx, d, binding.GL_FP32C)
     got = {k: ctx.profile_read(k)[1] for k in (binding.GL_KERNEL_SETUP, binding.GL_KERNEL_CURVE,
-                                                binding.GL_KERNEL_QUAD, binding.GL_KERNEL_SUM)}
+                                                binding.GL_KERNEL_QUAD)}
     ctx.profile(False)
     assert all(n == 2 for n in got.values()), got

@@ -179,6 +179,98 @@ def test_geometry_parity(ctx, geometry, prec):
     _compare(got, ref, prec)
 
 
+def _extreme_distance(x0, y0, dx, dy1, dy2, largest):
+    """Largest (or smallest) distance from the disk centre over the outline
+    x0 + dx cos th, y0 + dy1 cos th + dy2 sin th: a 2048-angle grid, then golden-
+    section refinement around the best grid angle (vectorised over cases)."""
+    th = np.linspace(0.0, 2.0 * np.pi, 2048, endpoint=False)[None, :]
+    def dist(t):
+        return np.hypot(x0[:, None] + dx[:, None] * np.cos(t),
+                        y0[:, None] + dy1[:, None] * np.cos(t) + dy2[:, None] * np.sin(t))
+    d = dist(th)
+    i = np.argmax(d, axis=1) if largest else np.argmin(d, axis=1)
+    lo = (th[0, i] - 2.0 * np.pi / 2048)[:, None]
+    hi = (th[0, i] + 2.0 * np.pi / 2048)[:, None]
+    r = (np.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(45):
+        a = hi - r * (hi - lo)
+        b = lo + r * (hi - lo)
+        fa, fb = dist(a), dist(b)
+        better_a = fa > fb if largest else fa < fb
+        hi = np.where(better_a, b, hi)
+        lo = np.where(better_a, lo, a)
+    return dist(0.5 * (lo + hi))[:, 0]
+
+
+@pytest.fixture(scope="module")
+def tangency():
+    """Centres where the outline reaches delta past the limb: from inside
+    (largest distance 1 + delta) or from outside (smallest distance 1 - delta),
+    found by bisection on the centre distance along the sampled direction.  Two
+    close crossings bound a thin sliver there; rounding decides the details."""
+    import oracle
+    g = inputs.tangency_sample(3000)
+    n = len(g["k"])
+    ell = np.array([oracle.oblate_ellipse(*a) for a in zip(g["k"], g["f"], g["eta"], g["xi"])])
+    dx, dy1, dy2 = ell[:, 0], ell[:, 1], ell[:, 2]
+    c, s_ = np.cos(g["ang"]), np.sin(g["ang"])
+    target = np.where(g["inner"], 1.0 + g["delta"], 1.0 - g["delta"])
+    req = np.maximum(np.abs(dx), np.hypot(dy1, dy2)) * 1.5
+    lo = np.where(g["inner"], 1.0 - 2.0 * req, 1.0 - 0.5 * req)
+    hi = np.where(g["inner"], 1.0 + 0.5 * req, 1.0 + 2.0 * req)
+    inner = g["inner"]
+    for _ in range(52):
+        mid = 0.5 * (lo + hi)
+        val = np.empty(n)
+        val[inner] = _extreme_distance(mid[inner] * c[inner], mid[inner] * s_[inner], dx[inner],
+                                       dy1[inner], dy2[inner], largest=True)
+        val[~inner] = _extreme_distance(mid[~inner] * c[~inner], mid[~inner] * s_[~inner],
+                                        dx[~inner], dy1[~inner], dy2[~inner], largest=False)
+        up = val < target   # the extreme distance grows with the centre distance
+        lo = np.where(up, mid, lo)
+        hi = np.where(up, hi, mid)
+    rho = 0.5 * (lo + hi)
+    u = np.array([oracle.q_to_u(a, b) for a, b in zip(g["q1"], g["q2"])])
+    geo = dict(x0=rho * c, y0=rho * s_, z=-np.ones(n), k=g["k"], f=g["f"], eta=g["eta"],
+               xi=g["xi"], u1=u[:, 0].copy(), u2=u[:, 1].copy())
+    ref = oracle.flux_sky_batch(*[geo[q] for q in ("x0", "y0", "z", "k", "f", "eta", "xi",
+                                                    "u1", "u2")])
+    return geo, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_near_tangency_parity(ctx, tangency, prec):
+    g, ref = tangency
+    args = [_dev(g[n]) for n in ("x0", "y0", "z", "k", "f", "eta", "xi", "u1", "u2")]
+    out = torch.empty(len(ref), dtype=torch.float64, device="cuda")
+    ctx.flux_sky(*args, out, precision=prec)
+    got = out.cpu().numpy()
+    assert np.mean((ref < 1) & (ref > 0)) > 0.95
+    _compare(got, ref, prec)
+
+
+@pytest.fixture(scope="module")
+def large_flat():
+    """Large, strongly flattened planets (R_eq up to ~0.5), the shapes that need
+    more FP32 quadrature nodes."""
+    import oracle
+    g = inputs.geometry_sample(20000, seed=23, k_range=(0.15, 0.25), f_max=0.9)
+    u = np.array([oracle.q_to_u(a, b) for a, b in zip(g["q1"], g["q2"])])
+    g["u1"], g["u2"] = u[:, 0].copy(), u[:, 1].copy()
+    ref = oracle.flux_sky_batch(g["x0"], g["y0"], g["z"], g["k"], g["f"], g["eta"], g["xi"],
+                                g["u1"], g["u2"])
+    return g, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_large_flattened_planets_parity(ctx, large_flat, prec):
+    g, ref = large_flat
+    args = [_dev(g[n]) for n in ("x0", "y0", "z", "k", "f", "eta", "xi", "u1", "u2")]
+    out = torch.empty(len(ref), dtype=torch.float64, device="cuda")
+    ctx.flux_sky(*args, out, precision=prec)
+    _compare(out.cpu().numpy(), ref, prec)
+
+
 # ---------------------------------------------------------------- spherical planet
 SPHERE_TOL = {binding.GL_FP64: 1e-10, binding.GL_FP32C: 2e-7}
 
