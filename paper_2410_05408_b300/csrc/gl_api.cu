@@ -37,11 +37,12 @@ constexpr int kNodes64Wide = 48;   // FP64 order for large, strongly flattened s
 constexpr int kNodes32 = 20;
 
 // item pipeline workspace: at most this many sub-exposure items per call by
-// default; per item 3 positions + deficit (FP64 sizing) + set + class + queue
-// slot + record (output index, first item, count); plus two ints per exposure
-// for the kept-exposure list
+// default; per item 3 positions + deficit (FP64 sizing) + set + queue slot +
+// record index, and a record (at most one per item: output index, first item,
+// count, set, flags, tau, midpoint state); plus three ints per exposure for
+// the kept-exposure list and the overflow list
 constexpr int64_t kItemMaxDefault = 1LL << 23;
-constexpr size_t kItemBytes = 4 * sizeof(double) + 6 * sizeof(int);
+constexpr size_t kItemBytes = 5 * sizeof(double) + 8 * sizeof(int) + sizeof(gl::MidState);
 
 __constant__ NodeRule<double> c_rule64;
 __constant__ NodeRule<double> c_rule64_wide;
@@ -79,42 +80,58 @@ struct ParamPtrs {
   int32_t nsuper_all;
 };
 
-// Four lanes per set: each computes one FP64 transcendental of the set (sincos w,
-// cbrt(1 - f), cos eta, sincos xi) in parallel, the first lane assembles the
-// constants.  Launched with 32-thread blocks, 8 sets per block.
-__global__ void gl_setup_kernel(ParamPtrs p, int64_t n_sets, const int64_t* offsets,
-                                int64_t n_total, SetConst* sets, int* status) {
-  const int lane = threadIdx.x & 31, role = lane & 3;
-  const int64_t s = (int64_t)blockIdx.x * 8 + (lane >> 2);
+// 32 sets per 128-thread block, one role per warp, so that the four FP64
+// instruction streams run on four SM sub-partitions at once (an FP64 warp
+// instruction costs the same whether one lane or 32 are active).
+//   stage 1: warps 0-2 compute sin and cos of omega, xi and eta, warp 3 the cube
+//            root of 1 - f, one set per lane
+//   stage 2: warp 0 the orbit and validity, warp 1 the projected ellipse, warp 2
+//            the transit window, warp 3 the limb darkening, each writing its own
+//            fields of the set's constants; warp 0 then sets the flags
+__global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_sets,
+                                                       const int64_t* offsets, int64_t n_total,
+                                                       SetConst* sets, int* status) {
+  __shared__ double sh_s[3][32], sh_c[3][32], sh_cb[32];
+  __shared__ int sh_win[32];
+  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+  const int64_t s = (int64_t)blockIdx.x * 32 + lane;
   const bool live = s < n_sets;
-  double v0 = 0.0, v1 = 1.0;
+  if (role < 3) {
+    double v0 = 0.0, v1 = 1.0;
+    const double ang = live ? (role == 0 ? p.omega[s] : role == 1 ? p.xi[s] : p.eta[s]) : 0.0;
+    if (isfinite(ang)) gl::sincos_setup(ang, &v0, &v1);
+    sh_s[role][lane] = v0;
+    sh_c[role][lane] = v1;
+  } else {
+    const double f = live ? p.f[s] : 0.0;
+    sh_cb[lane] = (isfinite(f) && f < 1.0) ? gl::cbrt_setup(1.0 - f) : 1.0;
+  }
+  __syncthreads();
+  const double cb = sh_cb[lane];
+  int orbit_ok = 0;
   if (live) {
+    SetConst* c = sets + s;
     if (role == 0) {
-      double w = p.omega[s];
-      if (isfinite(w)) sincos(w, &v0, &v1);
+      orbit_ok = gl::set_orbit(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], sh_s[0][lane],
+                               sh_c[0][lane], c);
     } else if (role == 1) {
-      double f = p.f[s];
-      v0 = (isfinite(f) && f < 1.0) ? cbrt(1.0 - f) : 1.0;
+      gl::set_shape(p.k[s], p.f[s], cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
     } else if (role == 2) {
-      double eta = p.eta[s];
-      v0 = isfinite(eta) ? cos(eta) : 1.0;
+      const double period = p.period[s], invP = gl::rcp64(period);
+      sh_win[lane] = gl::set_window(p.t0[s], period, p.a_rs[s], p.ecc[s], p.omega[s],
+                                    gl::set_req(p.k[s], cb), 2.0 * gl::kPi * invP, invP,
+                                    p.exptime[s], p.nsuper ? p.nsuper[s] : p.nsuper_all, c);
     } else {
-      double xi = p.xi[s];
-      if (isfinite(xi)) sincos(xi, &v0, &v1);
+      gl::set_ld(p.u1[s], p.u2[s], c);
     }
   }
-  const int base = lane & ~3;
-  double sw = __shfl_sync(0xffffffffu, v0, base), cw = __shfl_sync(0xffffffffu, v1, base);
-  double cb = __shfl_sync(0xffffffffu, v0, base + 1);
-  double ce = __shfl_sync(0xffffffffu, v0, base + 2);
-  double sx = __shfl_sync(0xffffffffu, v0, base + 3), cx = __shfl_sync(0xffffffffu, v1, base + 3);
+  __syncthreads();
   if (!live || role != 0) return;
-  int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
-  SetConst c;
-  bool ok = gl::set_setup_trig(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], p.omega[s],
-                               p.k[s], p.f[s], p.eta[s], p.xi[s], p.u1[s], p.u2[s],
-                               p.exptime[s], ns, sw, cw, cb, ce, sx, cx, &c);
-  sets[s] = c;
+  const int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
+  const bool ok = orbit_ok && gl::set_valid(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s],
+                                            p.omega[s], p.k[s], p.f[s], p.eta[s], p.xi[s],
+                                            p.u1[s], p.u2[s], p.exptime[s], ns);
+  sets[s].flags = ok ? sh_win[lane] : gl::kSetInvalid;
   if (!ok) atomicOr(status, kStatusInvalidSet);
   if (offsets) {
     bool bad = offsets[s] > offsets[s + 1] || (s == 0 && offsets[0] != 0) ||
@@ -240,11 +257,16 @@ struct LcArgs {
   int* kset;                    // their parameter sets; n_total entries
   unsigned long long* ictr;     // kIc* counters
   int64_t item_cap;
-  int* icls;                    // overlap class of each item (exposures of more than 32 items)
+  int* ovlist;                  // kept-list indices of exposures left to the sum kernel
+  // per record: set, flags, tau, midpoint state; per item: record
+  int *rset, *rflag, *irec;
+  double* rtau;
+  gl::MidState* rmid;
 };
 
 enum : int {
-  kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcSlots = 6
+  kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcOver = 6,
+  kIcValid = 7, kIcSlots = 8
 };
 
 // Index of the batch's FP32 quadrature order in c_rule32_tuned (-1 = default).
@@ -614,95 +636,121 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
   }
 }
 
-// Item pipeline, stage 2: one lane per kept exposure, 32 kept exposures per warp
-// and pass.  Sub-exposure slots and exposure records are taken with one atomic
-// add per warp, then the queue positions of the items that meet the disk with
-// two more.  An exposure none of whose items meets the disk gets flux 1 at once.
-// A warp whose items do not fit the workspace finishes its exposures itself.
+// Item pipeline, stage 2a: one thread per kept exposure: exact window and
+// midpoint state, stored in an exposure record with the exposure's range of
+// sub-exposure slots (one atomic add per block reserves the block's slots and
+// records).  If the workspace is full, the exposure goes to the overflow list,
+// finished by the sum kernel.
+// 64-thread blocks spread the FP64 work (the midpoint state) over every SM
+// even when few exposures are kept.
+constexpr int kExpThreads = 64;
+constexpr int kGeoThreads = 256;
+
 template <typename R>
-__global__ void __launch_bounds__(128) gl_exp_kernel(LcArgs a) {
-  const int rb = rule_base(a.rule_idx);
+__global__ void __launch_bounds__(kExpThreads) gl_exp_kernel(LcArgs a) {
+  __shared__ int warp_tot[32];
+  __shared__ long long s_base, s_rec;
+  __shared__ int s_fits;
+  const int tid = threadIdx.x;
   const long long nk = (long long)a.ictr[kIcKept];
-  R* ipos = (R*)a.ipos;
-  R* idef = (R*)a.idef;
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long k0 = warp * 32; k0 < nk; k0 += nwarp * 32) {
-    const long long k = k0 + lane;
-    int j = 0, s = 0, fl = kExpDead, ns = 0;
+  for (long long k0 = (long long)blockIdx.x * kExpThreads; k0 < nk;
+       k0 += (long long)gridDim.x * kExpThreads) {
+    const long long k = k0 + tid;
+    int j = 0, st = 0, fl = kExpDead, ns = 0;
     double tau = 0.0;
     gl::MidState mid;
     if (k < nk) {
       j = a.klist[k];
-      s = a.kset[k];
-      const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)s * a.n_times;
-      fl = exposure_prep<R>(a.sets[s], a.t[ti], &tau, &mid);
+      st = a.kset[k];
+      const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)st * a.n_times;
+      fl = exposure_prep<R>(a.sets[st], a.t[ti], &tau, &mid);
       if (fl & kExpDead) a.out[j] = 1.0;
-      else ns = a.sets[s].nsuper;
+      else ns = a.sets[st].nsuper;
     }
-    __syncwarp();
-    int tot_items;
-    const int off = warp_scan(ns, &tot_items);
-    unsigned long long b0 = 0;
-    if (lane == 0 && tot_items > 0) b0 = atomicAdd(&a.ictr[kIcItems], (unsigned long long)tot_items);
-    b0 = __shfl_sync(0xffffffffu, b0, 0);
-    if (tot_items == 0) continue;
-    if ((long long)b0 + tot_items > a.item_cap) {   // workspace full
-      if (ns > 0) a.out[j] = exposure_local<R>(a.sets[s], fl, mid, tau, ns, rb);
-      continue;
-    }
-    const long long b = (long long)b0 + off;
-    int nf = 0, np = 0;
-    unsigned long long cmask = 0;   // 2 bits per item, items 0..31
-    if (ns > 0) {
-      const SetConst& c = a.sets[s];
-      for (int q = 0; q < ns; ++q) {
-        R x, y, o;
-        const int cls = item_geometry<R>(c, fl, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
-        const long long g = b + q;
-        if (q < 32) cmask |= (unsigned long long)cls << (2 * q);
-        else a.icls[g] = cls;
-        if (cls == gl::kOut) {
-          idef[g] = R(0);
-          continue;
+    int total, n_live;
+    const int off = block_scan<kExpThreads>(ns, warp_tot, &total);
+    const int roff = block_scan<kExpThreads>(ns > 0 ? 1 : 0, warp_tot, &n_live);
+    if (tid == 0) {
+      long long b = 0, r = 0;
+      int fits = 0;
+      if (total > 0) {
+        b = (long long)atomicAdd(&a.ictr[kIcItems], (unsigned long long)total);
+        fits = b + total <= a.item_cap;
+        // records <= items <= item_cap; reservations are contiguous from slot 0,
+        // so the largest end of a fitting one bounds the filled slots
+        if (fits) {
+          r = (long long)atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_live);
+          atomicMax(&a.ictr[kIcValid], (unsigned long long)(b + total));
         }
+      }
+      s_base = b;
+      s_rec = r;
+      s_fits = fits;
+    }
+    __syncthreads();
+    if (ns > 0) {
+      if (s_fits) {
+        const long long r = s_rec + roff, first = s_base + off;
+        a.rj[r] = j;
+        a.rfirst[r] = (int)first;
+        a.rns[r] = ns;
+        a.rset[r] = st;
+        a.rflag[r] = fl;
+        a.rtau[r] = tau;
+        a.rmid[r] = mid;
+        for (int q = 0; q < ns; ++q) a.irec[first + q] = (int)r;
+      } else {
+        a.ovlist[atomicAdd(&a.ictr[kIcOver], 1ull)] = (int)k;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Item pipeline, stage 2b: one thread per sub-exposure slot: position and
+// overlap class; items that meet the disk are appended to the queue (one atomic
+// add per block and class), the others get a zero deficit.
+template <typename R>
+__global__ void __launch_bounds__(kGeoThreads) gl_geo_kernel(LcArgs a) {
+  __shared__ int s_nf, s_np;
+  __shared__ long long s_qf, s_qp;
+  const int tid = threadIdx.x;
+  const long long n = (long long)a.ictr[kIcValid];
+  R* ipos = (R*)a.ipos;
+  R* idef = (R*)a.idef;
+  for (long long g0 = (long long)blockIdx.x * kGeoThreads; g0 < n;
+       g0 += (long long)gridDim.x * kGeoThreads) {
+    const long long g = g0 + tid;
+    if (tid == 0) {
+      s_nf = 0;
+      s_np = 0;
+    }
+    __syncthreads();
+    int cls = gl::kOut, slot = 0;
+    if (g < n) {
+      const int r = a.irec[g];
+      const int st = a.rset[r], ns = a.rns[r], q = (int)(g - a.rfirst[r]);
+      R x, y, o;
+      cls = item_geometry<R>(a.sets[st], a.rflag[r], a.rmid[r], a.rtau[r], 2 * q + 1 - ns, &x, &y,
+                             &o);
+      if (cls == gl::kOut) {
+        idef[g] = R(0);
+      } else {
         ipos[3 * g] = x;
         ipos[3 * g + 1] = y;
         ipos[3 * g + 2] = o;
-        a.iset[g] = s;
-        if (cls == gl::kFull) ++nf; else ++np;
+        a.iset[g] = st;
+        slot = atomicAdd(cls == gl::kFull ? &s_nf : &s_np, 1);
       }
-      if (nf + np == 0) a.out[j] = 1.0;   // = (sum of ns ones) / ns, exactly
     }
-    // records for exposures with work in the quadrature kernel (records <= items)
-    const bool rec_needed = nf + np > 0;
-    __syncwarp();
-    int n_rec, tf, tp;
-    const int roff = warp_scan(rec_needed ? 1 : 0, &n_rec);
-    const int of = warp_scan(nf, &tf), op = warp_scan(np, &tp);
-    unsigned long long r0 = 0, qf0 = 0, qp0 = 0;
-    if (lane == 0) {
-      if (n_rec) r0 = atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_rec);
-      if (tf) qf0 = atomicAdd(&a.ictr[kIcFull], (unsigned long long)tf);
-      if (tp) qp0 = atomicAdd(&a.ictr[kIcPart], (unsigned long long)tp);
+    __syncthreads();
+    if (tid == 0) {
+      s_qf = s_nf ? (long long)atomicAdd(&a.ictr[kIcFull], (unsigned long long)s_nf) : 0;
+      s_qp = s_np ? (long long)atomicAdd(&a.ictr[kIcPart], (unsigned long long)s_np) : 0;
     }
-    r0 = __shfl_sync(0xffffffffu, r0, 0);
-    qf0 = __shfl_sync(0xffffffffu, qf0, 0);
-    qp0 = __shfl_sync(0xffffffffu, qp0, 0);
-    if (!rec_needed) continue;
-    const long long r = (long long)r0 + roff;
-    a.rj[r] = j;
-    a.rfirst[r] = (int)b;
-    a.rns[r] = ns;
-    long long fpos = (long long)qf0 + of, ppos = (long long)qp0 + op;
-    for (int q = 0; q < ns; ++q) {
-      const long long g = b + q;
-      const int cls = q < 32 ? (int)((cmask >> (2 * q)) & 3u) : a.icls[g];
-      if (cls == gl::kOut) continue;
-      if (cls == gl::kFull) a.iq[fpos++] = (int)g;
-      else a.iq[a.item_cap - 1 - (ppos++)] = (int)g;
-    }
+    __syncthreads();
+    if (cls == gl::kFull) a.iq[s_qf + slot] = (int)g;
+    else if (cls == gl::kPartial) a.iq[a.item_cap - 1 - (s_qp + slot)] = (int)g;
   }
 }
 
@@ -736,17 +784,32 @@ __global__ void __launch_bounds__(NT) gl_items_quad_kernel(LcArgs a) {
 
 // Item pipeline, stage 4: the FP64 mean of each exposure with items on the disk,
 // summed in sub-exposure order.
+// Exposures that did not fit the workspace are finished here, each by one
+// thread (exact window, midpoint state, every sub-exposure in order).
 template <typename R>
 __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
   const long long nrec = (long long)a.ictr[kIcRecs];
+  const long long nover = (long long)a.ictr[kIcOver];
   const R* idef = (const R*)a.idef;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrec;
+  const int rb = rule_base(a.rule_idx);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrec + nover;
        r += (long long)gridDim.x * blockDim.x) {
-    const int ns = a.rns[r];
-    const long long f = a.rfirst[r];
-    double acc = 0.0;
-    for (int q = 0; q < ns; ++q) acc += 1.0 - (double)idef[f + q];
-    a.out[a.rj[r]] = acc / ns;
+    if (r < nrec) {
+      const int ns = a.rns[r];
+      const long long f = a.rfirst[r];
+      double acc = 0.0;
+      for (int q = 0; q < ns; ++q) acc += 1.0 - (double)idef[f + q];
+      a.out[a.rj[r]] = acc / ns;
+    } else {
+      const int k = a.ovlist[r - nrec];
+      const int j = a.klist[k], st = a.kset[k];
+      const SetConst& c = a.sets[st];
+      const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)st * a.n_times;
+      double tau;
+      gl::MidState mid;
+      const int fl = exposure_prep<R>(c, a.t[ti], &tau, &mid);
+      a.out[j] = (fl & kExpDead) ? 1.0 : exposure_local<R>(c, fl, mid, tau, c.nsuper, rb);
+    }
   }
 }
 
@@ -1389,14 +1452,19 @@ void item_arrays(void* base, int64_t cap, int64_t n_total, size_t rsize, LcArgs*
   a->rj = (int*)take(sizeof(int) * (size_t)cap);
   a->rfirst = (int*)take(sizeof(int) * (size_t)cap);
   a->rns = (int*)take(sizeof(int) * (size_t)cap);
-  a->icls = (int*)take(sizeof(int) * (size_t)cap);
   a->item_cap = cap;
+  a->rset = (int*)take(sizeof(int) * (size_t)cap);
+  a->rflag = (int*)take(sizeof(int) * (size_t)cap);
+  a->irec = (int*)take(sizeof(int) * (size_t)cap);
+  a->rtau = (double*)take(sizeof(double) * (size_t)cap);
+  a->rmid = (gl::MidState*)take(sizeof(gl::MidState) * (size_t)cap);
   a->klist = (int*)take(sizeof(int) * (size_t)n_total);
   a->kset = (int*)take(sizeof(int) * (size_t)n_total);
+  a->ovlist = (int*)take(sizeof(int) * (size_t)n_total);
 }
 
 size_t item_workspace_bytes(int64_t cap, int64_t n_total) {
-  return (size_t)cap * kItemBytes + (size_t)n_total * 2 * sizeof(int) + 12 * 256;
+  return (size_t)cap * kItemBytes + (size_t)n_total * 3 * sizeof(int) + 18 * 256;
 }
 
 // The item pipeline: window tests, kept exposures, quadrature, exposure sums.
@@ -1407,7 +1475,8 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   if (qocc == 0) {
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qocc, gl_items_quad_kernel<R, 128>,
                                                                128, 0));
-    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&eocc, gl_exp_kernel<R>, 128, 0));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&eocc, gl_exp_kernel<R>,
+                                                               kExpThreads, 0));
     if (qocc < 1 || eocc < 1) return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
   }
   GL_CUDA(ctx, cudaMemsetAsync(ctx->d_ictr, 0, kIcSlots * sizeof(unsigned long long), st));
@@ -1416,9 +1485,10 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   if (wb < 1) wb = 1;
   long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
   gl_win_kernel<<<(int)wb, 256, 0, st>>>(args);
-  gl_exp_kernel<R><<<ctx->sms * eocc, 128, 0, st>>>(args);
+  gl_exp_kernel<R><<<ctx->sms * eocc, kExpThreads, 0, st>>>(args);
+  gl_geo_kernel<R><<<ctx->sms * 8, kGeoThreads, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_CURVE, pe, st);
-  ctx->launches += 2;
+  ctx->launches += 3;
   GL_CUDA(ctx, cudaGetLastError());
   pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
   gl_items_quad_kernel<R, 128><<<ctx->sms * qocc, 128, 0, st>>>(args);
@@ -1493,7 +1563,7 @@ struct StepArgs {
 
 int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
   long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
-  gl_setup_kernel<<<(int)((sa.n_sets + 7) / 8), 32, 0, st>>>(sa.pp, sa.n_sets, sa.offsets,
+  gl_setup_kernel<<<(int)((sa.n_sets + 31) / 32), 128, 0, st>>>(sa.pp, sa.n_sets, sa.offsets,
                                                               sa.n_total, sa.sets, ctx->d_status);
   prof_end(ctx, GL_KERNEL_SETUP, pe, st);
   ctx->launches++;
@@ -2099,7 +2169,7 @@ int gl_lightcurve_surrogate(gl_context* ctx, gl_mlp* mlp, const gl_params* p, co
   pp.u2 = p->u2;
   pp.exptime = tm->exptime;
   pp.nsuper_all = tm->nsuper_all;
-  gl_setup_kernel<<<(int)((n_sets + 7) / 8), 32, 0, st>>>(pp, n_sets, tm->offsets, n_total,
+  gl_setup_kernel<<<(int)((n_sets + 31) / 32), 128, 0, st>>>(pp, n_sets, tm->offsets, n_total,
                                                           ctx->d_sets, ctx->d_status);
   CollectArgs ca;
   memset(&ca, 0, sizeof ca);
@@ -2280,7 +2350,7 @@ extern "C" int gl_lightcurve_batch_noalloc(const gl_params* p, const gl_times* t
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GL_ECUDA;
   ParamPtrs pp = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
                   p->eta, p->xi, p->u1, p->u2, tm->exptime, tm->nsuper, tm->nsuper_all};
-  gl_setup_kernel<<<(int)((n_sets + 7) / 8), 32, 0, st>>>(pp, n_sets, tm->offsets,
+  gl_setup_kernel<<<(int)((n_sets + 31) / 32), 128, 0, st>>>(pp, n_sets, tm->offsets,
                                                           tm->n_total, sets, status);
   int grid = launch_grid(tm->n_total, 256);
   if (prec == GL_FP64)

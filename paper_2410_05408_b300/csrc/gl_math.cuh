@@ -184,39 +184,86 @@ GL_HD double ecc_anomaly_from_true(double nu, double e) {
   return 2.0 * atan2(sqrt(1.0 - e) * sin(0.5 * nu), sqrt(1.0 + e) * cos(0.5 * nu));
 }
 
-// Parameters of one set -> constants, given the four transcendentals of the
-// set (so that a caller can compute them in parallel): sin w, cos w,
-// cbrt(1 - f), cos eta, sin xi, cos xi.  Returns false (and sets kSetInvalid)
-// when the set is physically invalid.
-GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, double ecc,
-                          double omega, double k, double f, double eta, double xi, double u1,
-                          double u2, double exptime, int nsuper, double sinw, double cosw,
-                          double cbrt1mf, double ce, double sx, double cx, SetConst* c) {
-  c->flags = 0;
-  c->rule_min = 0;
-  c->t0 = t0;
-  c->period = period;
-  c->exptime = exptime;
-  c->nsuper = nsuper;
+// sin x and cos x in FP64 for the per-set constants, with a short dependent
+// chain: Cody-Waite reduction by pi/2 (x = k pi/2 + r, pi/2 split in a 33-bit
+// head, so that k * head is exact for |k| < 2^20, and a tail), then the Taylor
+// series of sin r and cos r on |r| <= pi/4 (terms through r^19 and r^18: the
+// first omitted term is below 1e-19) and the quadrant of k.  Beyond |x| = 1e5
+// the library sincos is used.
+GL_HD void sincos_setup(double x, double* s, double* c) {
+  if (!(fabs(x) <= 1e5)) {
+    sincos_<double>(x, s, c);
+    return;
+  }
+  const double two_over_pi = 0.63661977236758134308;
+  const double half_pi_hi = 1.5707963267341256142;     // pi/2 to 33 bits
+  const double half_pi_lo = 6.0771005065061922e-11;    // pi/2 - half_pi_hi
+  const double kq = rint(x * two_over_pi);
+  const double r = (x - kq * half_pi_hi) - kq * half_pi_lo;
+  const double r2 = r * r;
+  // sin r = r (1 - r^2/3! + r^4/5! - ...), cos r = 1 - r^2/2! + r^4/4! - ...
+  double ps = -1.0 / 121645100408832000.0;   // -1/19!
+  ps = ps * r2 + 1.0 / 355687428096000.0;    // 1/17!
+  ps = ps * r2 - 1.0 / 1307674368000.0;      // 1/15!
+  ps = ps * r2 + 1.0 / 6227020800.0;         // 1/13!
+  ps = ps * r2 - 1.0 / 39916800.0;           // 1/11!
+  ps = ps * r2 + 1.0 / 362880.0;             // 1/9!
+  ps = ps * r2 - 1.0 / 5040.0;               // 1/7!
+  ps = ps * r2 + 1.0 / 120.0;                // 1/5!
+  ps = ps * r2 - 1.0 / 6.0;                  // 1/3!
+  const double sr = r + r * r2 * ps;
+  double pc = 1.0 / 6402373705728000.0;      // 1/18!
+  pc = pc * r2 - 1.0 / 20922789888000.0;     // 1/16!
+  pc = pc * r2 + 1.0 / 87178291200.0;        // 1/14!
+  pc = pc * r2 - 1.0 / 479001600.0;          // 1/12!
+  pc = pc * r2 + 1.0 / 3628800.0;            // 1/10!
+  pc = pc * r2 - 1.0 / 40320.0;              // 1/8!
+  pc = pc * r2 + 1.0 / 720.0;                // 1/6!
+  pc = pc * r2 - 1.0 / 24.0;                 // 1/4!
+  pc = pc * r2 + 0.5;                        // 1/2!
+  const double cr = 1.0 - r2 * pc;
+  const int q = (int)((long long)kq & 3);
+  *s = q == 0 ? sr : q == 1 ? cr : q == 2 ? -sr : -cr;
+  *c = q == 0 ? cr : q == 1 ? -sr : q == 2 ? -cr : sr;
+}
+
+// Cube root of a > 0 in FP64: FP32 estimate and one Halley step
+// y <- y (y^3 + 2a) / (2 y^3 + a), which triples the number of correct digits.
+GL_HD double cbrt_setup(double a) {
+  if (!(a > 1e-30 && a < 1e30)) return cbrt(a);
+  const double y = (double)cbrtf((float)a);
+  const double y3 = y * y * y;
+  return y * (y3 + 2.0 * a) * rcp64(2.0 * y3 + a);
+}
+
+// The per-set constants in four parts with no dependence on one another
+// beyond the transcendentals (sin w, cos w, cbrt(1 - f), cos eta, sin xi,
+// cos xi), so that a caller may compute the parts in parallel.  Each part
+// writes its own fields of c; set_setup_trig runs all four.
+
+// Physical validity of a set (the orbit part also checks |cos i| <= 1).
+GL_HD bool set_valid(double t0, double period, double a_rs, double b, double ecc, double omega,
+                     double k, double f, double eta, double xi, double u1, double u2,
+                     double exptime, int nsuper) {
   bool ok = isfinite(t0) && isfinite(period) && isfinite(a_rs) && isfinite(b) &&
             isfinite(ecc) && isfinite(omega) && isfinite(k) && isfinite(f) &&
             isfinite(eta) && isfinite(xi) && isfinite(u1) && isfinite(u2) &&
             isfinite(exptime) && period > 0.0 && a_rs > 0.0 && ecc >= 0.0 && ecc < 1.0 &&
             k > 0.0 && f >= 0.0 && f < 1.0 && exptime >= 0.0 && nsuper >= 1;
-  double F0 = kPi * (1.0 - u1 * (1.0 / 3.0) - u2 * (1.0 / 6.0));
-  ok = ok && F0 > 0.0;
-  double cosi = ok ? b * (1.0 + ecc * sinw) * rcp64(a_rs * (1.0 - ecc) * (1.0 + ecc)) : 0.0;
-  ok = ok && fabs(cosi) <= 1.0;
-  if (!ok) {
-    c->flags = kSetInvalid;
-    return false;
-  }
-  // -- projected ellipse of the oblate spheroid (b = c = R_eq, a = R_pol along
-  //    the spin axis n = first row of R(zeta, eta, xi) = (cos eta cos xi,
-  //    -cos eta sin xi, sin eta)).  The sky covariance S = R^T diag(a^2,b^2,c^2) R
-  //    restricted to (x, y) is R_eq^2 I - (R_eq^2 - R_pol^2) n_xy n_xy^T, and
-  //    (dx, dy1, dy2) of Eqs. dx, dy1, dy2 are its Cholesky factor.
-  double req = k * rcp64(cbrt1mf);
+  return ok && kPi * (1.0 - u1 * (1.0 / 3.0) - u2 * (1.0 / 6.0)) > 0.0;
+}
+
+// Equatorial radius R_eq = k (1 - f)^(-1/3) (k the mean radius, Appendix A).
+GL_HD double set_req(double k, double cbrt1mf) { return k * rcp64(cbrt1mf); }
+
+// Projected ellipse of the oblate spheroid (b = c = R_eq, a = R_pol along the
+// spin axis n = first row of R(zeta, eta, xi) = (cos eta cos xi, -cos eta sin xi,
+// sin eta)).  The sky covariance S = R^T diag(a^2,b^2,c^2) R restricted to (x, y)
+// is R_eq^2 I - (R_eq^2 - R_pol^2) n_xy n_xy^T, and (dx, dy1, dy2) of Eqs. dx,
+// dy1, dy2 are its Cholesky factor.  Also the least FP32 quadrature order.
+GL_HD void set_shape(double k, double f, double cbrt1mf, double ce, double sx, double cx,
+                     SetConst* c) {
+  double req = set_req(k, cbrt1mf);
   // Least FP32 quadrature order for this shape.  Measured per-evaluation errors
   // of the FP32 path against the FP64 one (random positions on and around the
   // disk, random orientations, f < 0.9) stay below 1e-7 with 16 nodes for
@@ -234,14 +281,35 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
   c->dy1 = sxy * idx;
   c->dy2 = req * sqrt(req * req - delta) * idx;
   c->req = req;
-  // -- limb darkening in the basis (1, mu, r^2)
+  c->W0 = c->dx * c->dy2;
+  c->fdx = (float)c->dx;
+  c->fdy1 = (float)c->dy1;
+  c->fdy2 = (float)c->dy2;
+  c->freq = (float)req;
+  c->fW0 = (float)c->W0;
+}
+
+// Limb darkening in the basis (1, mu, r^2): I = c0 + c1 mu + c2 r^2 with
+// F0 = pi (1 - u1/3 - u2/6).
+GL_HD void set_ld(double u1, double u2, SetConst* c) {
   c->c0 = 1.0 - u1 - 2.0 * u2;
   c->c1 = u1 + 2.0 * u2;
   c->c2 = u2;
-  c->invF0 = rcp64(F0);
-  // -- orbit.  At conjunction nu_c = pi/2 - w: cos nu_c = sin w, sin nu_c = cos w,
-  //    and cos E = (e + cos nu)/(1 + e cos nu), sin E = sqrt(1-e^2) sin nu/(1 + e cos nu),
-  //    r = a (1 - e^2)/(1 + e cos nu).
+  c->invF0 = rcp64(kPi * (1.0 - u1 * (1.0 / 3.0) - u2 * (1.0 / 6.0)));
+  c->fc0 = (float)c->c0;
+  c->fc1 = (float)c->c1;
+  c->fc2 = (float)c->c2;
+  c->finvF0 = (float)c->invF0;
+}
+
+// Orbit.  At conjunction nu_c = pi/2 - w: cos nu_c = sin w, sin nu_c = cos w,
+// and cos E = (e + cos nu)/(1 + e cos nu), sin E = sqrt(1-e^2) sin nu/(1 + e cos nu),
+// r = a (1 - e^2)/(1 + e cos nu).  Returns false when |cos i| > 1.
+GL_HD bool set_orbit(double t0, double period, double a_rs, double b, double ecc, double sinw,
+                     double cosw, SetConst* c) {
+  c->t0 = t0;
+  c->period = period;
+  double cosi = b * (1.0 + ecc * sinw) * rcp64(a_rs * (1.0 - ecc) * (1.0 + ecc));
   c->invP = rcp64(period);
   c->nmean = 2.0 * kPi * c->invP;
   c->a_rs = a_rs;
@@ -256,17 +324,27 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
   c->cosEc = (ecc + sinw) * iden;
   c->sinEc = se * cosw * iden;
   c->rc = a_rs * (1.0 - ecc) * (1.0 + ecc) * iden;
-  double nuc = 0.5 * kPi - omega;
-  // -- window: the sky separation is at least r |sin phi| >= a (1-e) |sin phi|,
-  //    phi = angle from conjunction along the orbit; behind the star (|phi| > pi/2)
-  //    nothing is occulted.  Outside |phi| <= phi_w the flux is exactly 1.  The
-  //    window only has to contain every overlapping time, so it is computed in
-  //    FP32 and widened by a relative 1e-4 plus an absolute 1e-4 days, far more
-  //    than the FP32 rounding of these few operations.
+  return fabs(cosi) <= 1.0;
+}
+
+// Transit window, exposure fields and the sub-exposure expansion flag; returns
+// the flags kSetWholeOrbit and kSetTaylor.
+//  The sky separation is at least r |sin phi| >= a (1-e) |sin phi|, phi = angle
+//  from conjunction along the orbit; behind the star (|phi| > pi/2) nothing is
+//  occulted.  Outside |phi| <= phi_w the flux is exactly 1.  The window only has
+//  to contain every overlapping time, so it is computed in FP32 and widened by a
+//  relative 1e-4 plus an absolute 1e-4 days, far more than the FP32 rounding of
+//  these few operations.
+GL_HD int set_window(double t0, double period, double a_rs, double ecc, double omega,
+                     double req, double nmean, double invP, double exptime, int nsuper,
+                     SetConst* c) {
+  int flags = 0;
+  c->exptime = exptime;
+  c->nsuper = nsuper;
   double smax = 1.0 + req * (1.0 + 1e-9) + 1e-9;
   double rmin = a_rs * (1.0 - ecc);
   if (smax >= rmin * (1.0 - 1e-4)) {
-    c->flags |= kSetWholeOrbit;
+    flags |= kSetWholeOrbit;
     c->tau_lo = -period;
     c->tau_hi = period;
   } else {
@@ -275,7 +353,8 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
     // with conjunction near apoapsis), so no wrapping is applied.
     float phw = asinf((float)(smax / rmin)) * 1.0001f;
     float ef = (float)ecc;
-    float nucf = (float)remainder(nuc, 2.0 * kPi);
+    double nuc = 0.5 * kPi - omega;   // true anomaly at conjunction, reduced to [-pi, pi]
+    float nucf = (float)(nuc - 2.0 * kPi * rint(nuc * (0.5 / kPi)));
     float sq1 = sqrtf(1.0f - ef), sq2 = sqrtf(1.0f + ef);
     auto mean_anomaly = [&](float nu) {
       float turns = rintf(nu * 0.15915494309189535f);
@@ -288,29 +367,19 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
     float taus[2];
     for (int sgn = 0; sgn < 2; ++sgn) {
       float dM = mean_anomaly(nucf + (sgn ? phw : -phw)) - Mcf;
-      taus[sgn] = dM / (float)c->nmean;
+      taus[sgn] = dM / (float)nmean;
     }
     double margin = 1e-4 * (fabs((double)taus[0]) + fabs((double)taus[1])) + 1e-4;
     c->tau_lo = fmin((double)taus[0], 0.0) - margin;
     c->tau_hi = fmax((double)taus[1], 0.0) + margin;
   }
-  c->W0 = c->dx * c->dy2;
   c->sub_step = exptime / nsuper;
-  c->fdx = (float)c->dx;
-  c->fdy1 = (float)c->dy1;
-  c->fdy2 = (float)c->dy2;
-  c->freq = (float)req;
-  c->fW0 = (float)c->W0;
-  c->fc0 = (float)c->c0;
-  c->fc1 = (float)c->c1;
-  c->fc2 = (float)c->c2;
-  c->finvF0 = (float)c->invF0;
   c->fsub_step = (float)c->sub_step;
   // FP32 copy of the window for the per-exposure test, widened for rounding:
   // every FP32 operation of window_maybe errs by at most 2^-24 of its operands.
   c->t0f = (float)t0;
   c->Pf = (float)period;
-  c->invPf = (float)c->invP;
+  c->invPf = (float)invP;
   c->slack_f = (float)(ldexp(fabs(t0) + period, -20) + 1e-6);
   c->wlo_f = (float)(c->tau_lo - 0.5 * exptime);
   c->whi_f = (float)(c->tau_hi + 0.5 * exptime);
@@ -319,23 +388,49 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
   // (from r'' = -mu r/|r|^3, mu = n^2 a^3, r >= a(1-e)); with C = 60 the
   // truncation over half an exposure must stay below 1e-10 stellar radii.
   {
-    double n4 = c->nmean * c->nmean * c->nmean * c->nmean;
+    double n4 = nmean * nmean * nmean * nmean;
     double h = 0.5 * exptime;
     double om = 1.0 - ecc;
     double bound = 60.0 * n4 * a_rs * (2.0 + ecc) / (om * om * om * om * om) * (h * h * h * h) / 24.0;
-    if (bound <= 1e-10) c->flags |= kSetTaylor;
+    if (bound <= 1e-10) flags |= kSetTaylor;
   }
+  return flags;
+}
+
+// Parameters of one set -> constants, given the transcendentals of the set
+// (so that a caller can compute them in parallel): sin w, cos w, cbrt(1 - f),
+// cos eta, sin xi, cos xi.  Returns false (and sets kSetInvalid) when the set
+// is physically invalid.
+GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, double ecc,
+                          double omega, double k, double f, double eta, double xi, double u1,
+                          double u2, double exptime, int nsuper, double sinw, double cosw,
+                          double cbrt1mf, double ce, double sx, double cx, SetConst* c) {
+  c->flags = 0;
+  c->rule_min = 0;
+  c->t0 = t0;
+  c->period = period;
+  c->exptime = exptime;
+  c->nsuper = nsuper;
+  if (!set_valid(t0, period, a_rs, b, ecc, omega, k, f, eta, xi, u1, u2, exptime, nsuper) ||
+      !set_orbit(t0, period, a_rs, b, ecc, sinw, cosw, c)) {
+    c->flags = kSetInvalid;
+    return false;
+  }
+  set_shape(k, f, cbrt1mf, ce, sx, cx, c);
+  set_ld(u1, u2, c);
+  c->flags = set_window(t0, period, a_rs, ecc, omega, c->req, c->nmean, c->invP, exptime, nsuper,
+                        c);
   return true;
 }
 
 GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc,
                      double omega, double k, double f, double eta, double xi, double u1,
                      double u2, double exptime, int nsuper, SetConst* c) {
-  double sw = 0.0, cw = 1.0, sx = 0.0, cx = 1.0, ce = 1.0, cb = 1.0;
-  if (isfinite(omega)) sincos_<double>(omega, &sw, &cw);
-  if (isfinite(xi)) sincos_<double>(xi, &sx, &cx);
-  if (isfinite(eta)) ce = cos(eta);
-  if (isfinite(f) && f < 1.0) cb = cbrt(1.0 - f);
+  double sw = 0.0, cw = 1.0, sx = 0.0, cx = 1.0, ce = 1.0, cb = 1.0, se = 0.0;
+  if (isfinite(omega)) sincos_setup(omega, &sw, &cw);
+  if (isfinite(xi)) sincos_setup(xi, &sx, &cx);
+  if (isfinite(eta)) sincos_setup(eta, &se, &ce);
+  if (isfinite(f) && f < 1.0) cb = cbrt_setup(1.0 - f);
   return set_setup_trig(t0, period, a_rs, b, ecc, omega, k, f, eta, xi, u1, u2, exptime, nsuper,
                         sw, cw, cb, ce, sx, cx, c);
 }
@@ -364,27 +459,60 @@ GL_HD bool in_window(const SetConst& c, double tau, double halfwidth) {
 }
 
 // ------------------------------------------------------------------ orbit
+// sin(d) and cos(d) - 1 in FP32 (Taylor series below |d| = 1/4: truncation
+// below 1e-11; sincosf beyond).
+GL_HD void sin_cosm1_f(float d, float* sd, float* cm1) {
+  if (fabsf(d) < 0.25f) {
+    float d2 = d * d;
+    *sd = d + d * d2 * (-1.0f / 6.0f + d2 * (1.0f / 120.0f + d2 * (-1.0f / 5040.0f)));
+    *cm1 = d2 * (-0.5f + d2 * (1.0f / 24.0f + d2 * (-1.0f / 720.0f + d2 * (1.0f / 40320.0f))));
+  } else {
+    float s, c;
+    sincos_<float>(d, &s, &c);
+    *sd = s;
+    *cm1 = c - 1.0f;
+  }
+}
+
 // Kepler's equation for the eccentric anomaly E = E_c + d about the
-// conjunction:  d - e [cos E_c sin d + sin E_c (cos d - 1)] = n tau,
-// by Newton's method (bisection safeguard on the bracket |E - M| <= e).
-// Returns sin d and cos d - 1.
+// conjunction:  d - e [cos E_c sin d + sin E_c (cos d - 1)] = n tau.
+// Newton's method in FP32 first (cheap), then Halley's method in FP64 from the
+// FP32 iterate: with F' >= 1 - e and |F''|, |F'''| <= e, a Halley step s leaves
+// an error below C |s|^3, C = e / (1 - e) (1 + e / (1 - e)), so the FP64
+// iteration stops once C |s|^3 <= 1e-17 -- one step from a converged FP32
+// iterate (|s| ~ 1e-7 |d|).  A bisection on the bracket |E - M| <= e backs up an
+// iteration that does not settle.  Returns sin d and cos d - 1.
 GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* cm1_out) {
   double nt = c.nmean * tau;
   double e = c.ecc;
   double ec = e * c.cosEc, es = e * c.sinEc;
-  double ir1 = rcp64(1.0 - ec);
-  double d = nt * ir1;
-  d -= 0.5 * es * d * d * ir1;   // second-order start: F ~ d (1 - ec) + es d^2 / 2 - n tau
+  const float ntf = (float)nt, ecf = (float)ec, esf = (float)es;
+  const float ir1f = 1.0f / (1.0f - ecf);
+  float df = ntf * ir1f;
+  df -= 0.5f * esf * df * df * ir1f;   // second-order start: F ~ d (1 - ec) + es d^2 / 2 - n tau
+  for (int it = 0; it < 4; ++it) {
+    float sdf, cmf;
+    sin_cosm1_f(df, &sdf, &cmf);
+    const float F = df - ecf * sdf - esf * cmf - ntf;
+    const float Fp = 1.0f - ecf * (1.0f + cmf) + esf * sdf;
+    df -= F / Fp;
+  }
+  const double q1e = e * rcp64(1.0 - e);
+  const double C = q1e * (1.0 + q1e);
+  double d = isfinite(df) ? (double)df : nt;
   double sd, cm1;
   bool conv = false;
   for (int it = 0; it < 12; ++it) {
     sin_cosm1(d, &sd, &cm1);
-    double F = d - ec * sd - es * cm1 - nt;
-    double Fp = 1.0 - ec * (1.0 + cm1) + es * sd;
-    double step = F * rcp64(Fp);
+    const double F = d - ec * sd - es * cm1 - nt;
+    const double Fp = 1.0 - ec * (1.0 + cm1) + es * sd;
+    const double Fpp = ec * sd + es * (1.0 + cm1);
+    // Halley step: 2 F F1 / (2 F1^2 - F F2) with F1, F2 the first two derivatives
+    const double step = 2.0 * F * Fp * rcp64(2.0 * Fp * Fp - F * Fpp);
     d -= step;
-    if (fabs(step) <= 1e-16 * (1.0 + fabs(d))) {
-      conv = true;
+    const double as = fabs(step);
+    if (C * as * as * as <= 1e-17 || as <= 1e-16 * (1.0 + fabs(d))) {
+      conv = isfinite(d);
       break;
     }
   }
@@ -438,26 +566,30 @@ GL_HD void sky_state(const SetConst& c, double tau, SkyState* s) {
   s->y = -p1;
   s->x = p2 * c.cosi;
   s->z = -p2 * c.sini;
-  double cosE = c.cosEc + dcosE, sinE = c.sinEc + dsinE;
-  double X = c.a_rs * (cosE - c.ecc), Y = c.b_orb * sinE;
-  double r = c.a_rs * (1.0 - c.ecc * cosE);
-  double ir = rcp64(r);
-  double Ed = c.nmean * c.a_rs * ir;                // dE/dt
-  double Xd = -c.a_rs * sinE * Ed, Yd = c.b_orb * cosE * Ed;
-  double mu = c.nmean * c.nmean * c.a_rs * c.a_rs * c.a_rs;
-  double ir2 = ir * ir, ir3 = ir2 * ir;
-  double rv = X * Xd + Y * Yd;
-  double Xa = -mu * X * ir3, Ya = -mu * Y * ir3;
-  double Xj = -mu * (Xd * ir3 - 3.0 * X * rv * ir3 * ir2);
-  double Yj = -mu * (Yd * ir3 - 3.0 * Y * rv * ir3 * ir2);
-  double in[3][2] = {{Xd, Yd}, {Xa, Ya}, {Xj, Yj}};
+  // The derivatives only scale time offsets within an exposure (|v dt| < 0.1
+  // stellar radii), so FP32 (relative error ~1e-7) is ample for them.
+  const float a = (float)c.a_rs, bo = (float)c.b_orb, ef = (float)c.ecc, nm = (float)c.nmean;
+  const float cosE = (float)(c.cosEc + dcosE), sinE = (float)(c.sinEc + dsinE);
+  const float X = a * (cosE - ef), Y = bo * sinE;
+  const float r = a * (1.0f - ef * cosE);
+  const float ir = 1.0f / r;
+  const float Ed = nm * a * ir;                 // dE/dt
+  const float Xd = -a * sinE * Ed, Yd = bo * cosE * Ed;
+  const float mu = nm * nm * a * a * a;
+  const float ir2 = ir * ir, ir3 = ir2 * ir;
+  const float rv = X * Xd + Y * Yd;
+  const float Xa = -mu * X * ir3, Ya = -mu * Y * ir3;
+  const float Xj = -mu * (Xd * ir3 - 3.0f * X * rv * ir3 * ir2);
+  const float Yj = -mu * (Yd * ir3 - 3.0f * Y * rv * ir3 * ir2);
+  const float in[3][2] = {{Xd, Yd}, {Xa, Ya}, {Xj, Yj}};
   double* out[3] = {s->d1, s->d2, s->d3};
+  const float cw = (float)c.cosw, sw = (float)c.sinw, ci = (float)c.cosi, si = (float)c.sini;
   for (int k = 0; k < 3; ++k) {
-    double q1 = in[k][0] * c.cosw - in[k][1] * c.sinw;
-    double q2 = in[k][0] * c.sinw + in[k][1] * c.cosw;
-    out[k][0] = q2 * c.cosi;
+    const float q1 = in[k][0] * cw - in[k][1] * sw;
+    const float q2 = in[k][0] * sw + in[k][1] * cw;
+    out[k][0] = q2 * ci;
     out[k][1] = -q1;
-    out[k][2] = -q2 * c.sini;
+    out[k][2] = -q2 * si;
   }
 }
 
@@ -1233,8 +1365,8 @@ GL_HD MidState mid_state(const SkyState& s) {
   m.omr2 = (float)((1.0 - s.x) * (1.0 + s.x) - s.y * s.y);
   for (int k = 0; k < 3; ++k) {
     m.d1[k] = (float)s.d1[k];
-    m.d2[k] = (float)(0.5 * s.d2[k]);
-    m.d3[k] = (float)(s.d3[k] / 6.0);
+    m.d2[k] = 0.5f * (float)s.d2[k];
+    m.d3[k] = (float)s.d3[k] * (1.0f / 6.0f);
   }
   return m;
 }
