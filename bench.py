@@ -472,6 +472,60 @@ def surrogate_mcmc_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def simpson_arm(args):
+    """Geometry-level comparison of the split Gauss-Legendre path (gl_flux_sky)
+    with the paper's snapped Simpson scheme (gl_flux_sky_simpson) at several N:
+    evaluations/s over a large geometry sample (device-resident, CUDA events) and
+    max |dflux| against the FP64 oracle on a seeded subset."""
+    import torch
+    import oracle
+    from paper_2410_05408_b300 import binding, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    n, n_ref = 200_000, 2000
+    g = inputs.geometry_sample(n, seed=41)
+    g["u1"], g["u2"] = binding.gl_q_to_u(g["q1"], g["q2"])
+    ref = oracle.flux_sky_batch(*[g[q][:n_ref] for q in ("x0", "y0", "z", "k", "f", "eta", "xi",
+                                                         "u1", "u2")])
+    d = [torch.as_tensor(np.ascontiguousarray(g[q]), device=dev)
+         for q in ("x0", "y0", "z", "k", "f", "eta", "xi", "u1", "u2")]
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def measure(call):
+        for _ in range(args.warmup):
+            call()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            call()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / args.steps
+        err = float(np.max(np.abs(out[:n_ref].cpu().numpy() - ref)))
+        return {"evals_per_s": n / (ms * 1e-3), "ms": ms, "max_dflux_vs_oracle": err}
+
+    rows = {}
+    for name, prec in (("fp32", binding.GL_FP32C), ("fp64", binding.GL_FP64)):
+        rows[f"split_gauss_legendre_{name}"] = measure(
+            lambda: ctx.flux_sky(*d, out, precision=prec, stream=stream))
+        for n_int in (64, 256, 1024, 4096, 16384):
+            rows[f"simpson_{name}_N{n_int}"] = measure(
+                lambda: ctx.flux_sky_simpson(*d, out, n_int, precision=prec, stream=stream))
+    best = rows["split_gauss_legendre_fp32"]
+    line = {"metric": "geometry-level flux evals/s, split Gauss-Legendre vs the paper's snapped "
+                      "Simpson scheme", "value": best["evals_per_s"], "unit": "evals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": best["ms"], "higher_is_better": True, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "simpson_variant", "geometries": n,
+                       "oracle_checked": n_ref, "sample": "geometry_sample(seed=41)"},
+            "paths": rows}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,6 +554,8 @@ def main():
         return surrogate_train_arm(args)
     if args.workload == "surrogate_mcmc":
         return surrogate_mcmc_arm(args)
+    if args.workload == "simpson_variant":
+        return simpson_arm(args)
 
     import torch
     from paper_2410_05408_b300 import binding, build

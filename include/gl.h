@@ -159,6 +159,21 @@ int gl_flux_sphere(gl_context *ctx, int64_t n, const double *x0, const double *y
                    const double *z, const double *p, const double *u1, const double *u2,
                    double *out, gl_precision prec, void *stream);
 
+/* Relative flux at sky positions by the paper's own integration scheme (Sec. 2),
+ * for comparison with gl_flux_sky: composite Simpson's rule over `n_intervals`
+ * uniform intervals (even, 2..2^24) of the ellipse angle, the boundary "snapped"
+ * along its ray onto the limb wherever it lies outside the disk, and no
+ * crossings.  The integrand has a kink where the boundary meets the limb, so the
+ * error falls as n_intervals^-2 on partial overlaps.  GL_FP32C evaluates the
+ * integrands in FP32 with compensated sums (the paper's single precision);
+ * GL_FP64 in FP64.  Positions behind the star or with rho >= 1 + R_eq give 1.
+ * Same arguments, memory, stream and error rules as gl_flux_sky; GL_EINVAL for an
+ * odd or out-of-range n_intervals. */
+int gl_flux_sky_simpson(gl_context *ctx, int64_t n, const double *x0, const double *y0,
+                        const double *z, const double *k, const double *f, const double *eta,
+                        const double *xi, const double *u1, const double *u2, double *out,
+                        int n_intervals, gl_precision prec, void *stream);
+
 /* Kipping (2013) map from (q1, q2) in [0,1]^2 to quadratic coefficients,
  * u1 = 2 sqrt(q1) q2, u2 = sqrt(q1) (1 - 2 q2) (cited in Sec. 3, Table priors,
  * note f; the formula is not printed in the paper).  Host arrays of n entries;
@@ -258,6 +273,7 @@ int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *
                                kept-exposure kernels (FP64 or FP32C) */
 #define GL_KERNEL_SKY 2     /* geometry-level kernel */
 #define GL_KERNEL_SPHERE 3  /* spherical-planet kernel */
+#define GL_KERNEL_SIMPSON 5 /* the paper's snapped Simpson scheme (gl_flux_sky_simpson) */
 #define GL_KERNEL_QUAD 4    /* item pipeline: quadrature of queued sub-exposures and the
                                exposure means (two kernels) */
 #define GL_KERNEL_KINDS 8

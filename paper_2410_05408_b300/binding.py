@@ -33,7 +33,8 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_flux_sphere", "gl_mlp_param_count", "gl_mlp_create", "gl_mlp_destroy",
             "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
             "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
-            "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike", "gl_item_pipeline")
+            "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike", "gl_item_pipeline",
+            "gl_flux_sky_simpson")
 
 SUR_BINS = 16
 
@@ -47,6 +48,7 @@ GL_KERNEL_CURVE = 1
 GL_KERNEL_SKY = 2
 GL_KERNEL_SPHERE = 3
 GL_KERNEL_QUAD = 4
+GL_KERNEL_SIMPSON = 5
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 
@@ -106,6 +108,8 @@ def load():
         lib.gl_lightcurve_batch.restype = i32
         lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
         lib.gl_flux_sky.restype = i32
+        lib.gl_flux_sky_simpson.argtypes = [vp, i64] + [vp] * 10 + [i32, i32, vp]
+        lib.gl_flux_sky_simpson.restype = i32
         lib.gl_lightcurve_surrogate.argtypes = [vp, vp, ctypes.POINTER(_Params),
                                                 ctypes.POINTER(_Times), vp, vp, ctypes.c_double,
                                                 vp, ctypes.POINTER(_SurStats)]
@@ -277,6 +281,19 @@ def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_
     n = int(len(out))
     rc = lib.gl_flux_sky(ctx, n, *[_ptr(a, "float64") for a in (x0, y0, z, k, f, eta, xi, u1, u2)],
                          _ptr(out, "float64"), int(precision), _stream_ptr(stream))
+    if check:
+        _check(ctx, rc)
+    return rc
+
+
+def gl_flux_sky_simpson(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, n_intervals: int,
+                        precision: int = GL_FP32C, stream=None, check: bool = True) -> int:
+    lib = load()
+    n = int(len(out))
+    rc = lib.gl_flux_sky_simpson(ctx, n, *[_ptr(a, "float64") for a in
+                                           (x0, y0, z, k, f, eta, xi, u1, u2)],
+                                 _ptr(out, "float64"), int(n_intervals), int(precision),
+                                 _stream_ptr(stream))
     if check:
         _check(ctx, rc)
     return rc
@@ -473,6 +490,11 @@ class Context:
 
     def flux_sky(self, x0, y0, z, k, f, eta, xi, u1, u2, out, precision=GL_FP32C, stream=None):
         return gl_flux_sky(self.handle, x0, y0, z, k, f, eta, xi, u1, u2, out, precision, stream)
+
+    def flux_sky_simpson(self, x0, y0, z, k, f, eta, xi, u1, u2, out, n_intervals,
+                         precision=GL_FP32C, stream=None):
+        return gl_flux_sky_simpson(self.handle, x0, y0, z, k, f, eta, xi, u1, u2, out,
+                                   n_intervals, precision, stream)
 
     def flux_sphere(self, x0, y0, z, p, u1, u2, out, precision=GL_FP32C, stream=None):
         return gl_flux_sphere(self.handle, x0, y0, z, p, u1, u2, out, precision, stream)

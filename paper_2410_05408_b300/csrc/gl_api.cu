@@ -1201,6 +1201,59 @@ __global__ void __launch_bounds__(256) gl_sky_kernel(SkyPtrs p, int64_t n, doubl
   }
 }
 
+// ------------------------------------------------------------------ the paper's scheme
+// Geometry-level flux by the paper's own integration (Sec. 2): composite Simpson's
+// rule over n_int uniform intervals of the ellipse angle th in [0, 2 pi) (periodic,
+// so the end node weighs 2 like every even node), the boundary snapped to the
+// limb where it lies outside the disk, no crossings.  One warp per evaluation:
+// lanes take nodes j = lane, lane + 32, ..., each keeping a compensated sum in
+// precision R; the lanes' sums are combined in FP64.  Positions with the planet
+// behind the star or beyond rho >= 1 + R_eq give flux exactly 1.
+template <typename R>
+__global__ void __launch_bounds__(256) gl_simpson_kernel(SkyPtrs p, int64_t n, int n_int,
+                                                         double* out, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarp) {
+    SetConst c;
+    const bool ok = gl::set_setup(0.0, 1.0, 10.0, 0.0, 0.0, 0.0, p.k[i], p.f[i], p.eta[i],
+                                  p.xi[i], p.u1[i], p.u2[i], 0.0, 1, &c);
+    const double x0 = p.x0[i], y0 = p.y0[i], z = p.z[i];
+    if (!ok || !isfinite(x0) || !isfinite(y0) || !isfinite(z)) {
+      if (lane == 0) {
+        out[i] = __longlong_as_double(0x7ff8000000000000LL);
+        atomicOr(status, kStatusInvalidSet);
+      }
+      continue;
+    }
+    if (gl::classify(c, x0, y0, z) == gl::kOut) {
+      if (lane == 0) out[i] = 1.0;
+      continue;
+    }
+    const R rx = (R)x0, ry = (R)y0, dx = gl::pick<R>(c.dx, c.fdx), dy1 = gl::pick<R>(c.dy1, c.fdy1),
+            dy2 = gl::pick<R>(c.dy2, c.fdy2);
+    gl::CSum<R> s0, s1, s2;
+    for (int j = lane; j < n_int; j += 32) {
+      R sn, cs;
+      gl::sincospi_<R>(R(2) * (R)j / (R)n_int, &sn, &cs);
+      R ff, fl, fq;
+      gl::snapped_integrands<R>(rx, ry, dx, dy1, dy2, cs, sn, &ff, &fl, &fq);
+      const R w = (j & 1) ? R(4) : R(2);
+      s0.add(w * ff);
+      s1.add(w * fl);
+      s2.add(w * fq);
+    }
+    double I[3] = {(double)s0.value(), (double)s1.value(), (double)s2.value()};
+    for (int o = 16; o > 0; o >>= 1)
+      for (int m = 0; m < 3; ++m) I[m] += __shfl_xor_sync(0xffffffffu, I[m], o);
+    const double h3 = 2.0 * gl::kPi / n_int / 3.0;
+    if (lane == 0)
+      out[i] = 1.0 - (c.c0 * I[0] + c.c1 * I[1] + c.c2 * I[2]) * h3 * c.invF0;
+  }
+}
+
+
 // ------------------------------------------------------------------ host helpers
 // Gauss-Legendre nodes on [-1, 1] by Newton's method on the Legendre recurrence,
 // mapped through theta = m + h sin(pi s / 2).
@@ -2271,6 +2324,53 @@ int gl_flux_sky(gl_context* ctx, int64_t n, const double* x0, const double* y0, 
   else
     gl_sky_kernel<float><<<grid, 256, 0, st>>>(sp, n, d_out, ctx->d_status);
   prof_end(ctx, GL_KERNEL_SKY, pe, st);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  if (out_host) GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, b, cudaMemcpyDeviceToHost, st));
+  if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
+  return GL_OK;
+}
+
+int gl_flux_sky_simpson(gl_context* ctx, int64_t n, const double* x0, const double* y0,
+                        const double* z, const double* k, const double* f, const double* eta,
+                        const double* xi, const double* u1, const double* u2, double* out,
+                        int n_intervals, gl_precision prec, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n < 0) return fail(ctx, GL_EINVAL, "n < 0");
+  if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision %d", (int)prec);
+  if (n_intervals < 2 || (n_intervals & 1) || n_intervals > (1 << 24))
+    return fail(ctx, GL_EINVAL, "n_intervals must be even, in [2, 2^24]");
+  if (n == 0) return GL_OK;
+  if (!x0 || !y0 || !z || !k || !f || !eta || !xi || !u1 || !u2 || !out)
+    return fail(ctx, GL_EINVAL, "NULL array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  SkyPtrs sp = {x0, y0, z, k, f, eta, xi, u1, u2};
+  size_t b = (size_t)n * sizeof(double);
+  StageItem items[] = {{(const void**)&sp.x0, b}, {(const void**)&sp.y0, b},
+                       {(const void**)&sp.z, b},  {(const void**)&sp.k, b},
+                       {(const void**)&sp.f, b},  {(const void**)&sp.eta, b},
+                       {(const void**)&sp.xi, b}, {(const void**)&sp.u1, b},
+                       {(const void**)&sp.u2, b}};
+  bool any_host = false;
+  int rc = stage_inputs(ctx, items, 9, st, &any_host);
+  if (rc) return rc;
+  bool out_host = !is_device_ptr(out, ctx->device);
+  double* d_out = out;
+  if (out_host) {
+    rc = grow(ctx, (void**)&ctx->d_out, &ctx->out_cap, b);
+    if (rc) return rc;
+    d_out = ctx->d_out;
+  }
+  int64_t blocks = (n + 7) / 8;   // 8 warps per block, one evaluation per warp
+  if (blocks > (int64_t)ctx->sms * 64) blocks = (int64_t)ctx->sms * 64;
+  long pe = prof_begin(ctx, GL_KERNEL_SIMPSON, st);
+  if (prec == GL_FP64)
+    gl_simpson_kernel<double><<<(int)blocks, 256, 0, st>>>(sp, n, n_intervals, d_out, ctx->d_status);
+  else
+    gl_simpson_kernel<float><<<(int)blocks, 256, 0, st>>>(sp, n, n_intervals, d_out, ctx->d_status);
+  prof_end(ctx, GL_KERNEL_SIMPSON, pe, st);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
   if (out_host) GL_CUDA(ctx, cudaMemcpyAsync(out, d_out, b, cudaMemcpyDeviceToHost, st));

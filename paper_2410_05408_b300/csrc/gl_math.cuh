@@ -107,6 +107,25 @@ template <> GL_HD void sincos_<float>(float x, float* s, float* c) {
 #endif
 }
 
+// sin(pi x) and cos(pi x).
+template <typename R> GL_HD void sincospi_(R x, R* s, R* c);
+template <> GL_HD void sincospi_<double>(double x, double* s, double* c) {
+#if defined(__CUDA_ARCH__)
+  sincospi(x, s, c);
+#else
+  *s = ::sin(kPi * x);
+  *c = ::cos(kPi * x);
+#endif
+}
+template <> GL_HD void sincospi_<float>(float x, float* s, float* c) {
+#if defined(__CUDA_ARCH__)
+  sincospif(x, s, c);
+#else
+  *s = ::sinf(3.14159265358979f * x);
+  *c = ::cosf(3.14159265358979f * x);
+#endif
+}
+
 // Neumaier-compensated accumulation.
 template <typename R>
 struct CSum {
@@ -1106,6 +1125,37 @@ GL_HD R quad_poly_trig(const QuadPoly<R>& q, R ct, R st) {
     sn = snext;
   }
   return acc;
+}
+
+// ------------------------------------------------------------------ the paper's scheme
+// Integrands of the paper's snapped-boundary scheme (Sec. 2) at angle th of the
+// projected ellipse.  The boundary point p = (x0 + dx cos th, y0 + dy1 cos th +
+// dy2 sin th) and its derivative p' = (-dx sin th, -dy1 sin th + dy2 cos th); a
+// point outside the disk is moved along its ray to the limb, (x_d, y_d) =
+// p / |p| = (cos lambda, sin lambda), with d lambda / d th = (x y' - y x') / |p|^2
+// and the derivative of the moved point lambda' (-y_d, x_d).  On the moved curve
+// the three integrands reduce to lambda'/2, lambda'/3 and
+// lambda' ((x_d^4 + y_d^4)/3 + 2 x_d^2 y_d^2) / 2.  Their integrals over th in
+// [0, 2 pi) are the area, Integral mu dA and Integral r^2 dA of the overlap (the
+// paper's f_flat, f_lin, f_quad; f_lin written without the small-r cancellation).
+template <typename T>
+GL_HD void snapped_integrands(T x0, T y0, T dx, T dy1, T dy2, T ct, T st, T* ff, T* fl, T* fq) {
+  const T xe = x0 + dx * ct, ye = y0 + dy1 * ct + dy2 * st;
+  const T xp = -dx * st, yp = -dy1 * st + dy2 * ct;
+  const T r2 = xe * xe + ye * ye;
+  const T cross = xe * yp - ye * xp;
+  if (r2 > T(1)) {
+    const T lp = cross / r2;
+    const T x2 = xe * xe / r2, y2 = ye * ye / r2;
+    *ff = T(0.5) * lp;
+    *fl = lp / T(3);
+    *fq = T(0.5) * lp * ((x2 * x2 + y2 * y2) / T(3) + T(2) * x2 * y2);
+  } else {
+    const T mu = m_sqrt(T(1) - r2);
+    *ff = T(0.5) * cross;
+    *fl = (T(2) / T(3)) * (T(1) + mu + mu * mu) / (T(1) + mu) * (*ff);
+    *fq = T(0.5) * (xe * (xe * xe / T(3) + ye * ye) * yp - ye * (xe * xe + ye * ye / T(3)) * xp);
+  }
 }
 
 // ------------------------------------------------------------------ occulted moments
