@@ -74,12 +74,18 @@ typedef struct gl_context gl_context;
  *   xi      rotation about z' (position angle of the spin axis on the sky), rad;
  *           the projected spin axis points along (cos xi, -sin xi) in (x, y)
  *   u1, u2  quadratic limb darkening, I(mu) = 1 - u1 (1-mu) - u2 (1-mu)^2
+ * Optional (NULL: the oblate spheroid b = c of the fits, Appendix A):
+ *   g       equatorial flattening of a general triaxial ellipsoid (Sec. 2):
+ *           semi-axes c (largest, along z'), b = c (1-g) (y'), a = c (1-f) (x'),
+ *           k = (a b c)^(1/3), so c = k ((1-f)(1-g))^(-1/3); 0 <= g < 1
+ *   zeta    rotation about x', rad (no effect when g = 0)
  */
 typedef struct {
   int64_t n_sets;
   const double *t0, *period, *a_rs, *b, *ecc, *omega;
   const double *k, *f, *eta, *xi;
   const double *u1, *u2;
+  const double *g, *zeta;   /* optional, may be NULL */
 } gl_params;
 
 /* Exposure times.

@@ -84,12 +84,14 @@ def _load():
         lib.orc_flux_sky.restype = d
         lib.orc_flux_sky.argtypes = [d, d, d, d, d, d, d, d, d]
         lib.orc_lightcurve.restype = ctypes.c_int
-        lib.orc_lightcurve.argtypes = ([ctypes.c_int64] + [pd] * 13
+        lib.orc_lightcurve.argtypes = ([ctypes.c_int64] + [pd] * 15
                                        + [ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                           pd, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, d,
                                           ctypes.c_int, pd])
         lib.orc_flux_sky_batch.restype = None
-        lib.orc_flux_sky_batch.argtypes = [ctypes.c_int64] + [pd] * 9 + [d, ctypes.c_int, pd]
+        lib.orc_flux_sky_batch.argtypes = [ctypes.c_int64] + [pd] * 11 + [d, ctypes.c_int, pd]
+        lib.orc_triaxial_ellipse.restype = None
+        lib.orc_triaxial_ellipse.argtypes = [d, d, d, d, d, d, pd, pd, pd]
         lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_max_threads.argtypes = []
         _lib = lib
@@ -133,6 +135,22 @@ def oblate_ellipse(k, f, eta, xi):
     return tuple(v.value for v in o)
 
 
+def triaxial_ellipse(k, f, g, zeta, eta, xi):
+    """(dx, dy1, dy2) of a triaxial ellipsoid: c the largest semi-axis,
+    b = c (1 - g), a = c (1 - f), geometric mean k."""
+    o = [ctypes.c_double() for _ in range(3)]
+    _load().orc_triaxial_ellipse(float(k), float(f), float(g), float(zeta), float(eta),
+                                 float(xi), *[ctypes.byref(v) for v in o])
+    return tuple(v.value for v in o)
+
+
+def _optional(arr, n):
+    if arr is None:
+        return None, None
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(arr, dtype=np.float64), (n,)).copy())
+    return a, _p(a)
+
+
 def q_to_u(q1, q2):
     u1, u2 = ctypes.c_double(), ctypes.c_double()
     _load().orc_q_to_u(float(q1), float(q2), ctypes.byref(u1), ctypes.byref(u2))
@@ -162,7 +180,9 @@ def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
                tol: float = DEFAULT_TOL, nthreads: int = 0) -> np.ndarray:
     """Supersampled light curves for a batch of parameter sets.
 
-    ``params`` maps each of PARAM_NAMES to an array of n_sets floats.  With
+    ``params`` maps each of PARAM_NAMES to an array of n_sets floats, and may add
+    "g" and "zeta" (triaxial shape: c the largest semi-axis, b = c (1 - g),
+    a = c (1 - f); rotation zeta about x').  With
     ``offsets`` None, ``t`` is one grid shared by every set and the result has
     shape (n_sets, len(t)); otherwise set s owns t[offsets[s]:offsets[s+1]] and the
     result is flat in the same layout.  ``nsuper`` is an int or an array of
@@ -189,7 +209,9 @@ def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
     else:
         ns_arr = np.ascontiguousarray(np.asarray(nsuper, dtype=np.int32))
         ns_p, ns_all = ns_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0
-    st = lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], _p(t), offp, n_times,
+    g_arr, g_p = _optional(params.get("g"), n_sets)
+    z_arr, z_p = _optional(params.get("zeta"), n_sets)
+    st = lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], g_p, z_p, _p(t), offp, n_times,
                             _p(exptime), ns_p, ns_all, float(tol), int(nthreads), _p(out))
     if st != 0:
         raise ValueError("oracle rejected its inputs")
@@ -199,13 +221,17 @@ def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
 
 
 def flux_sky_batch(x0, y0, z, k, f, eta, xi, u1, u2, tol: float = DEFAULT_TOL,
-                   nthreads: int = 0) -> np.ndarray:
-    """Relative flux for arrays of sky positions and shapes (k, f, eta, xi)."""
+                   nthreads: int = 0, g=None, zeta=None) -> np.ndarray:
+    """Relative flux for arrays of sky positions and shapes (k, f, eta, xi; with
+    g and zeta, the triaxial shape of triaxial_ellipse)."""
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
             for a in (x0, y0, z, k, f, eta, xi, u1, u2)]
     n = arrs[0].size
+    g_arr, g_p = _optional(g, n)
+    z_arr, z_p = _optional(zeta, n)
     out = np.empty(n)
-    _load().orc_flux_sky_batch(n, *[_p(a) for a in arrs], float(tol), int(nthreads), _p(out))
+    _load().orc_flux_sky_batch(n, *[_p(a) for a in arrs], g_p, z_p, float(tol), int(nthreads),
+                               _p(out))
     return out
 
 

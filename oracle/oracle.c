@@ -194,6 +194,17 @@ void orc_oblate_ellipse(double k, double f, double eta, double xi, double *dx,
     orc_projected_ellipse(rpol, req, req, 0.0, eta, xi, dx, dy1, dy2);
 }
 
+/* General triaxial ellipsoid (Sec. 2: semi-axes a, b, c along x', y', z', all
+ * three rotation angles active).  Parameterised like the oblate case: c is the
+ * largest semi-axis, b = c (1 - g), a = c (1 - f), and k is the geometric mean of
+ * the three (Sec. 3), so c = k ((1 - f)(1 - g))^(-1/3).  g = 0 is the oblate
+ * spheroid, for which zeta has no effect. */
+void orc_triaxial_ellipse(double k, double f, double g, double zeta, double eta, double xi,
+                          double *dx, double *dy1, double *dy2) {
+    double c = k / cbrt((1.0 - f) * (1.0 - g));
+    orc_projected_ellipse(c * (1.0 - f), c * (1.0 - g), c, zeta, eta, xi, dx, dy1, dy2);
+}
+
 /* Kipping (2013) map from (q1, q2) to quadratic coefficients (cited in Sec. 3,
  * Table priors, note f; the formula itself is not printed in the paper). */
 void orc_q_to_u(double q1, double q2, double *u1, double *u2) {
@@ -428,7 +439,8 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
                    const double *a_rs, const double *b, const double *ecc,
                    const double *omega, const double *k, const double *f,
                    const double *eta, const double *xi, const double *u1,
-                   const double *u2, const double *t, const int64_t *offsets,
+                   const double *u2, const double *g, const double *zeta,
+                   const double *t, const int64_t *offsets,
                    int64_t n_times, const double *exptime, const int32_t *nsuper_arr,
                    int nsuper_all, double tol, int nthreads, double *out) {
     if (n_sets < 0 || (!nsuper_arr && nsuper_all <= 0)) return -1;
@@ -455,7 +467,11 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
             tj = t[j % n_times];
         }
         double dx, dy1, dy2;
-        orc_oblate_ellipse(k[s], f[s], eta[s], xi[s], &dx, &dy1, &dy2);
+        if (g || zeta)
+            orc_triaxial_ellipse(k[s], f[s], g ? g[s] : 0.0, zeta ? zeta[s] : 0.0, eta[s],
+                                 xi[s], &dx, &dy1, &dy2);
+        else
+            orc_oblate_ellipse(k[s], f[s], eta[s], xi[s], &dx, &dy1, &dy2);
         double cosi = orc_cos_inclination(b[s], a_rs[s], ecc[s], omega[s]);
         int nsuper = nsuper_arr ? nsuper_arr[s] : nsuper_all;
         if (nsuper <= 0) { out[j] = NAN; continue; }
@@ -475,8 +491,8 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
 /* Relative flux for n given sky positions and shapes (OpenMP over items). */
 void orc_flux_sky_batch(int64_t n, const double *x0, const double *y0, const double *z,
                         const double *k, const double *f, const double *eta, const double *xi,
-                        const double *u1, const double *u2, double tol, int nthreads,
-                        double *out) {
+                        const double *u1, const double *u2, const double *g,
+                        const double *zeta, double tol, int nthreads, double *out) {
     gl_init();
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -484,7 +500,11 @@ void orc_flux_sky_batch(int64_t n, const double *x0, const double *y0, const dou
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i) {
         double dx, dy1, dy2;
-        orc_oblate_ellipse(k[i], f[i], eta[i], xi[i], &dx, &dy1, &dy2);
+        if (g || zeta)
+            orc_triaxial_ellipse(k[i], f[i], g ? g[i] : 0.0, zeta ? zeta[i] : 0.0, eta[i],
+                                 xi[i], &dx, &dy1, &dy2);
+        else
+            orc_oblate_ellipse(k[i], f[i], eta[i], xi[i], &dx, &dy1, &dy2);
         out[i] = orc_flux_sky(x0[i], y0[i], z[i], dx, dy1, dy2, u1[i], u2[i], tol);
     }
 }

@@ -60,7 +60,16 @@ class GLError(RuntimeError):
 
 
 class _Params(ctypes.Structure):
-    _fields_ = [("n_sets", ctypes.c_int64)] + [(n, ctypes.c_void_p) for n in PARAM_NAMES]
+    _fields_ = ([("n_sets", ctypes.c_int64)] + [(n, ctypes.c_void_p) for n in PARAM_NAMES] +
+                [("g", ctypes.c_void_p), ("zeta", ctypes.c_void_p)])
+
+
+def _params(params: dict) -> "_Params":
+    """Marshal a parameter dict (PARAM_NAMES, plus optional "g" and "zeta" for a
+    triaxial shape) into the C struct."""
+    n_sets = int(len(params["t0"]))
+    return _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES],
+                   _ptr(params.get("g"), "float64"), _ptr(params.get("zeta"), "float64"))
 
 
 class _TuneReport(ctypes.Structure):
@@ -232,7 +241,7 @@ def gl_lightcurve_batch(ctx, params: dict, t, out, precision: int = GL_FP32C, of
     """
     lib = load()
     n_sets = int(len(params["t0"]))
-    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    p = _params(params)
     n_t = int(len(t))
     n_total = int(len(out))
     tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"), 0 if offsets is not None else n_t,
@@ -251,7 +260,7 @@ def gl_lightcurve_batch_noalloc(params: dict, t, out, precision: int = GL_FP32C,
     CUDA tensor on the current device.  Returns the C status code."""
     lib = load()
     n_sets = int(len(params["t0"]))
-    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    p = _params(params)
     tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"),
                 0 if offsets is not None else int(len(t)), int(len(out)),
                 _ptr(exptime, "float64"), _ptr(nsuper, "int32"), int(nsuper_all))
@@ -265,7 +274,7 @@ def gl_autotune(ctx, params: dict, t, out, precision: int = GL_FP32C, offsets=No
     """Run the library's autotuner on this batch; returns its report as a dict."""
     lib = load()
     n_sets = int(len(params["t0"]))
-    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    p = _params(params)
     tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"),
                 0 if offsets is not None else int(len(t)), int(len(out)),
                 _ptr(exptime, "float64"), _ptr(nsuper, "int32"), int(nsuper_all))
@@ -315,7 +324,7 @@ def gl_lightcurve_surrogate(ctx, mlp, params: dict, t, out, bound_table, bound_l
     """Surrogate light curves (device buffers, uniform nsuper); returns the stats."""
     lib = load()
     n_sets = int(len(params["t0"]))
-    p = _Params(n_sets, *[_ptr(params[n], "float64") for n in PARAM_NAMES])
+    p = _params(params)
     tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"),
                 0 if offsets is not None else int(len(t)), int(len(out)),
                 _ptr(exptime, "float64"), None, int(nsuper_all))

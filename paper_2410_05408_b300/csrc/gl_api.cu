@@ -75,6 +75,7 @@ __device__ __forceinline__ const NodeRule<float>& set_rule<float>(const SetConst
 // ------------------------------------------------------------------ kernels
 struct ParamPtrs {
   const double *t0, *period, *a_rs, *b, *ecc, *omega, *k, *f, *eta, *xi, *u1, *u2;
+  const double *g, *zeta;   // optional triaxial shape (NULL: oblate)
   const double* exptime;
   const int32_t* nsuper;
   int32_t nsuper_all;
@@ -91,7 +92,7 @@ struct ParamPtrs {
 __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_sets,
                                                        const int64_t* offsets, int64_t n_total,
                                                        SetConst* sets, int* status) {
-  __shared__ double sh_s[3][32], sh_c[3][32], sh_cb[32];
+  __shared__ double sh_s[4][32], sh_c[4][32], sh_cb[32];
   __shared__ int sh_win[32];
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
   const int64_t s = (int64_t)blockIdx.x * 32 + lane;
@@ -103,8 +104,16 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
     sh_s[role][lane] = v0;
     sh_c[role][lane] = v1;
   } else {
+    // cube root of (1 - f)(1 - g) and, for a triaxial shape, sin and cos of zeta
     const double f = live ? p.f[s] : 0.0;
-    sh_cb[lane] = (isfinite(f) && f < 1.0) ? gl::cbrt_setup(1.0 - f) : 1.0;
+    const double g = (live && p.g) ? p.g[s] : 0.0;
+    const double q = (1.0 - f) * (1.0 - g);
+    sh_cb[lane] = (isfinite(q) && q > 0.0) ? gl::cbrt_setup(q) : 1.0;
+    double v0 = 0.0, v1 = 1.0;
+    const double zeta = (live && p.zeta) ? p.zeta[s] : 0.0;
+    if (p.g && isfinite(zeta)) gl::sincos_setup(zeta, &v0, &v1);
+    sh_s[3][lane] = v0;
+    sh_c[3][lane] = v1;
   }
   __syncthreads();
   const double cb = sh_cb[lane];
@@ -115,7 +124,12 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
       orbit_ok = gl::set_orbit(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], sh_s[0][lane],
                                sh_c[0][lane], c);
     } else if (role == 1) {
-      gl::set_shape(p.k[s], p.f[s], cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
+      const double g = p.g ? p.g[s] : 0.0;
+      if (g != 0.0)
+        gl::set_shape_triaxial(p.k[s], p.f[s], g, cb, sh_s[3][lane], sh_c[3][lane],
+                               sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
+      else
+        gl::set_shape(p.k[s], p.f[s], cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
     } else if (role == 2) {
       const double period = p.period[s], invP = gl::rcp64(period);
       sh_win[lane] = gl::set_window(p.t0[s], period, p.a_rs[s], p.ecc[s], p.omega[s],
@@ -128,9 +142,11 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
   __syncthreads();
   if (!live || role != 0) return;
   const int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
-  const bool ok = orbit_ok && gl::set_valid(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s],
-                                            p.omega[s], p.k[s], p.f[s], p.eta[s], p.xi[s],
-                                            p.u1[s], p.u2[s], p.exptime[s], ns);
+  const double g = p.g ? p.g[s] : 0.0, zeta = p.zeta ? p.zeta[s] : 0.0;
+  const bool ok = orbit_ok && isfinite(g) && g >= 0.0 && g < 1.0 && isfinite(zeta) &&
+                  gl::set_valid(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s],
+                                p.omega[s], p.k[s], p.f[s], p.eta[s], p.xi[s],
+                                p.u1[s], p.u2[s], p.exptime[s], ns);
   sets[s].flags = ok ? sh_win[lane] : gl::kSetInvalid;
   if (!ok) atomicOr(status, kStatusInvalidSet);
   if (offsets) {
@@ -337,19 +353,6 @@ __device__ __forceinline__ long long warp_append(unsigned long long* ctr, bool p
   if (lane == leader && bal) base = atomicAdd(ctr, (unsigned long long)__popc(bal));
   base = __shfl_sync(mask, base, leader);
   return pred ? (long long)base + __popc(bal & ((1u << lane) - 1u)) : -1;
-}
-
-// Exclusive prefix sum over a converged warp; *total gets the warp's sum.
-__device__ __forceinline__ int warp_scan(int v, int* total) {
-  const int lane = threadIdx.x & 31;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  *total = __shfl_sync(0xffffffffu, x, 31);
-  return x - v;
 }
 
 // Exposure at time t: tau (t - t0 wrapped about the conjunction), the exact FP64
@@ -1988,6 +1991,8 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
   pp.xi = p->xi;
   pp.u1 = p->u1;
   pp.u2 = p->u2;
+  pp.g = p->g;
+  pp.zeta = p->zeta;
   pp.exptime = tm->exptime;
   pp.nsuper = tm->nsuper;
   pp.nsuper_all = tm->nsuper_all;
@@ -2004,6 +2009,7 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
       {(const void**)&pp.nsuper, (size_t)n_sets * sizeof(int32_t)},
       {(const void**)&t, (size_t)n_t * sizeof(double)},
       {(const void**)&offsets, (size_t)(n_sets + 1) * sizeof(int64_t)},
+      {(const void**)&pp.g, sb}, {(const void**)&pp.zeta, sb},
   };
   bool any_host = false;
   int rc = stage_inputs(ctx, items, (int)(sizeof items / sizeof items[0]), st, &any_host);
@@ -2220,6 +2226,8 @@ int gl_lightcurve_surrogate(gl_context* ctx, gl_mlp* mlp, const gl_params* p, co
   pp.xi = p->xi;
   pp.u1 = p->u1;
   pp.u2 = p->u2;
+  pp.g = p->g;
+  pp.zeta = p->zeta;
   pp.exptime = tm->exptime;
   pp.nsuper_all = tm->nsuper_all;
   gl_setup_kernel<<<(int)((n_sets + 31) / 32), 128, 0, st>>>(pp, n_sets, tm->offsets, n_total,
@@ -2431,12 +2439,12 @@ extern "C" int gl_lightcurve_batch_noalloc(const gl_params* p, const gl_times* t
     cudaGetLastError();
     return GL_ECUDA;
   }
-  const void* ptrs[17] = {p->t0, p->period, p->a_rs, p->b,   p->ecc,     p->omega,
+  const void* ptrs[19] = {p->t0, p->period, p->a_rs, p->b,   p->ecc,     p->omega,
                           p->k,  p->f,      p->eta,  p->xi,  p->u1,      p->u2,
-                          tm->t, tm->exptime, out,   tm->offsets, tm->nsuper};
-  for (int i = 0; i < 17; ++i) {
+                          tm->t, tm->exptime, out,   tm->offsets, tm->nsuper, p->g, p->zeta};
+  for (int i = 0; i < 19; ++i) {
     if (!ptrs[i]) {
-      if (i >= 15) continue;   // offsets and nsuper are optional
+      if (i >= 15) continue;   // offsets, nsuper, g and zeta are optional
       return GL_EINVAL;
     }
     if (!is_device_ptr(ptrs[i], device)) return GL_EINVAL;   // host memory would need staging
@@ -2449,7 +2457,8 @@ extern "C" int gl_lightcurve_batch_noalloc(const gl_params* p, const gl_times* t
   int* status = (int*)(scratch + kNoallocStatusOffset);
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GL_ECUDA;
   ParamPtrs pp = {p->t0, p->period, p->a_rs, p->b, p->ecc, p->omega, p->k, p->f,
-                  p->eta, p->xi, p->u1, p->u2, tm->exptime, tm->nsuper, tm->nsuper_all};
+                  p->eta, p->xi, p->u1, p->u2, p->g, p->zeta, tm->exptime, tm->nsuper,
+                  tm->nsuper_all};
   gl_setup_kernel<<<(int)((n_sets + 31) / 32), 128, 0, st>>>(pp, n_sets, tm->offsets,
                                                           tm->n_total, sets, status);
   int grid = launch_grid(tm->n_total, 256);

@@ -308,6 +308,37 @@ GL_HD void set_shape(double k, double f, double cbrt1mf, double ce, double sx, d
   c->fW0 = (float)c->W0;
 }
 
+// Projected ellipse of a general triaxial ellipsoid (Sec. 2, Eqs. dx, dy1, dy2
+// with R = Rx(zeta) Ry(eta) Rz(xi), all three angles active): semi-axes c (the
+// largest), b = c (1 - g), a = c (1 - f), with c = k ((1 - f)(1 - g))^(-1/3) given
+// as c = k / cbrt_fg.  R_eq (the classification radius) is c; the least
+// quadrature order uses the larger of f and g.
+GL_HD void set_shape_triaxial(double k, double f, double g, double cbrt_fg, double sz,
+                              double cz, double se, double ce, double sx, double cx,
+                              SetConst* c) {
+  const double cax = k * rcp64(cbrt_fg);
+  const double a = cax * (1.0 - f), b = cax * (1.0 - g);
+  // rows of Rx(zeta) Ry(eta) Rz(xi)
+  const double r1 = ce * cx, r2 = -ce * sx, r3 = se;
+  const double r4 = cz * sx + sz * se * cx, r5 = cz * cx - sz * se * sx, r6 = -sz * ce;
+  const double r7 = sz * sx - cz * se * cx, r8 = sz * cx + cz * se * sx, r9 = cz * ce;
+  const double a2 = a * a, b2 = b * b, c2 = cax * cax;
+  const double dx = sqrt(a2 * r1 * r1 + b2 * r4 * r4 + c2 * r7 * r7);
+  const double idx = rcp64(dx);
+  c->dx = dx;
+  c->dy1 = (a2 * r1 * r2 + b2 * r4 * r5 + c2 * r7 * r8) * idx;
+  c->dy2 = sqrt(a2 * b2 * r9 * r9 + a2 * c2 * r6 * r6 + b2 * c2 * r3 * r3) * idx;
+  c->req = cax;
+  const double fe = f > g ? f : g;
+  c->rule_min = cax >= 0.45 ? 3 : (cax < 0.2 || fe < 0.5) ? 0 : (fe < 0.7 ? 1 : 3);
+  c->W0 = c->dx * c->dy2;
+  c->fdx = (float)c->dx;
+  c->fdy1 = (float)c->dy1;
+  c->fdy2 = (float)c->dy2;
+  c->freq = (float)cax;
+  c->fW0 = (float)c->W0;
+}
+
 // Limb darkening in the basis (1, mu, r^2): I = c0 + c1 mu + c2 r^2 with
 // F0 = pi (1 - u1/3 - u2/6).
 GL_HD void set_ld(double u1, double u2, SetConst* c) {

@@ -91,6 +91,19 @@ def mcmc_batch(n_sets: int = 256, n_times: int = 2000, seed: int = 1) -> dict:
                 exptime=np.full(n_sets, LONG_CADENCE), nsuper=15)
 
 
+def triaxial_batch(n_sets: int = 12, n_times: int = 400, seed: int = 51) -> dict:
+    """The MCMC box with a general triaxial shape: equatorial flattening g
+    U[0, 0.6] and rotation zeta U[0, pi) added to each set; k U[0.05, 0.15];
+    times every 5 min over +-17 h around the conjunction (the transit), x 7."""
+    rng = _rng(seed)
+    params = _draw_sets(rng, n_sets, k_range=(0.05, 0.15))
+    params["g"] = rng.uniform(0.0, 0.6, n_sets)
+    params["zeta"] = rng.uniform(0.0, np.pi, n_sets)
+    t = (np.arange(n_times) - 0.5 * (n_times - 1)) * (5.0 / 1440.0)
+    return dict(params=params, t=t, offsets=None, exptime=np.full(n_sets, 5.0 / 1440.0),
+                nsuper=7)
+
+
 def uneven_batch(n_curves: int = 4096, seed: int = 2, min_len: int = 100,
                  max_len: int = 50000) -> dict:
     """Curves of log-uniform length; even curves 60-s cadence (nsuper 1), odd

@@ -142,6 +142,28 @@ def test_oblate_projection_axes_and_zeta_invariance():
         np.testing.assert_allclose(ev, [minor2, req * req], rtol=1e-12)
 
 
+def test_triaxial_ellipse_closed_forms():
+    """Triaxial shape (c largest, b = c (1-g), a = c (1-f), abc = k^3): with every
+    angle zero the sky axes are a along x and b along y; with eta = 90 deg the x'
+    axis points along the line of sight and the projected area is pi b c for any
+    zeta, xi; g = 0 is the oblate spheroid whatever zeta."""
+    rng = np.random.default_rng(5)
+    for _ in range(40):
+        k, f, g = rng.uniform(0.02, 0.3), rng.uniform(0, 0.9), rng.uniform(0, 0.9)
+        c = k / ((1 - f) * (1 - g)) ** (1.0 / 3.0)
+        a, b = c * (1 - f), c * (1 - g)
+        np.testing.assert_allclose(a * b * c, k ** 3, rtol=1e-13)
+        dx, dy1, dy2 = oracle.triaxial_ellipse(k, f, g, 0.0, 0.0, 0.0)
+        np.testing.assert_allclose([dx, dy1, dy2], [a, 0.0, b], rtol=1e-13, atol=1e-17)
+        zeta, xi = rng.uniform(-3, 3, 2)
+        dx, dy1, dy2 = oracle.triaxial_ellipse(k, f, g, zeta, 0.5 * math.pi, xi)
+        np.testing.assert_allclose(dx * dy2, b * c, rtol=1e-12)
+        eta = rng.uniform(-3, 3)
+        base = oracle.oblate_ellipse(k, f, eta, xi)
+        np.testing.assert_allclose(oracle.triaxial_ellipse(k, f, 0.0, zeta, eta, xi), base,
+                                   rtol=1e-12, atol=1e-16)
+
+
 def test_oblate_ellipse_uses_mean_radius():
     k, f = 0.066, 0.5
     dx, dy1, dy2 = oracle.oblate_ellipse(k, f, 0.0, 0.0)   # spin axis along x
