@@ -526,6 +526,59 @@ def simpson_arm(args):
     ctx.close()
 
 
+def locked_arm(args):
+    """Tidally locked light curves (gl_lightcurve_locked, projection per
+    sub-exposure) against the unlocked item pipeline on the same close-in,
+    triaxial planets: evals/s of each, L2 flushed before every step."""
+    import torch
+    from paper_2410_05408_b300 import binding, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    wl = inputs.locked_batch(n_sets=256, n_times=2000, seed=61)
+    p = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in wl["params"].items()}
+    p["u1"], p["u2"] = binding.gl_q_to_u(p.pop("q1"), p.pop("q2"))
+    n_sets, n_t = len(p["t0"]), len(wl["t"])
+    dp = {k: torch.as_tensor(v, device=dev) for k, v in p.items()}
+    d_t = torch.as_tensor(np.ascontiguousarray(wl["t"]), device=dev)
+    d_exp = torch.as_tensor(np.ascontiguousarray(wl["exptime"]), device=dev)
+    out = torch.empty(n_sets * n_t, dtype=torch.float64, device=dev)
+    evals = n_sets * n_t * int(wl["nsuper"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+    for name, prec, locked in (("locked_fp32c", binding.GL_FP32C, True),
+                               ("locked_fp64", binding.GL_FP64, True),
+                               ("unlocked_fp32c", binding.GL_FP32C, False),
+                               ("unlocked_fp64", binding.GL_FP64, False)):
+        def step():
+            ctx.lightcurve(dp, d_t, out, d_exp, nsuper_all=int(wl["nsuper"]), precision=prec,
+                           stream=stream, locked=locked)
+        for _ in range(args.warmup):
+            step()
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += a.elapsed_time(b)
+        rows[name] = {"evals_per_s": evals / (ms / args.steps * 1e-3), "ms": ms / args.steps}
+    line = {"metric": "tidally locked light-curve evals/s (projection per sub-exposure)",
+            "value": rows["locked_fp32c"]["evals_per_s"], "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": rows["locked_fp32c"]["ms"], "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "locked_batch", "parameter_sets": n_sets, "exposures": n_t,
+                       "nsuper": int(wl["nsuper"]), "evals_per_step": evals,
+                       "l2": "flushed between steps (256 MB write)"},
+            "paths": rows}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -556,6 +609,8 @@ def main():
         return surrogate_mcmc_arm(args)
     if args.workload == "simpson_variant":
         return simpson_arm(args)
+    if args.workload == "locked_batch":
+        return locked_arm(args)
 
     import torch
     from paper_2410_05408_b300 import binding, build

@@ -141,6 +141,18 @@ const char *gl_last_error(const gl_context *ctx);
 int gl_lightcurve_batch(gl_context *ctx, const gl_params *p, const gl_times *t, double *out,
                         gl_precision prec, void *stream);
 
+/* Light curves of tidally locked bodies (Appendix B): the body frame turns with
+ * the orbit, so the projected ellipse is recomputed for every sub-exposure from
+ * the orbital angle alpha from conjunction (alpha = w + nu - pi/2 for the
+ * Keplerian orbit; r cos alpha = x0 cos i - z sin i, r sin alpha = y0) and
+ * beta = pi/2 - i, by the paper's Eqs. dx-locked, dy1-locked, dy2-locked; shapes
+ * as in gl_params (oblate, or triaxial with g and zeta).  One thread per
+ * exposure, FP64 Kepler per sub-exposure, the same quadrature as
+ * gl_lightcurve_batch.  Same arguments, memory, stream and error rules as
+ * gl_lightcurve_batch. */
+int gl_lightcurve_locked(gl_context *ctx, const gl_params *p, const gl_times *t, double *out,
+                         gl_precision prec, void *stream);
+
 /* Relative flux for given sky positions, bypassing the orbit (geometry level
  * of Sec. 2).  All arrays have n entries:
  *   x0, y0, z       planet centre in the sky frame (stellar radii)

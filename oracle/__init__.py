@@ -84,12 +84,14 @@ def _load():
         lib.orc_flux_sky.restype = d
         lib.orc_flux_sky.argtypes = [d, d, d, d, d, d, d, d, d]
         lib.orc_lightcurve.restype = ctypes.c_int
-        lib.orc_lightcurve.argtypes = ([ctypes.c_int64] + [pd] * 15
+        lib.orc_lightcurve.argtypes = ([ctypes.c_int64] + [pd] * 14 + [ctypes.c_int, pd]
                                        + [ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                           pd, ctypes.POINTER(ctypes.c_int32), ctypes.c_int, d,
                                           ctypes.c_int, pd])
         lib.orc_flux_sky_batch.restype = None
         lib.orc_flux_sky_batch.argtypes = [ctypes.c_int64] + [pd] * 11 + [d, ctypes.c_int, pd]
+        lib.orc_locked_ellipse.restype = None
+        lib.orc_locked_ellipse.argtypes = [d, d, d, d, d, d, d, d, pd, pd, pd]
         lib.orc_triaxial_ellipse.restype = None
         lib.orc_triaxial_ellipse.argtypes = [d, d, d, d, d, d, pd, pd, pd]
         lib.orc_max_threads.restype = ctypes.c_int
@@ -144,6 +146,15 @@ def triaxial_ellipse(k, f, g, zeta, eta, xi):
     return tuple(v.value for v in o)
 
 
+def locked_ellipse(a, b, c, zeta, eta, xi, alpha, beta):
+    """(dx, dy1, dy2) of a tidally locked body (Appendix B) at orbital angle
+    alpha and elevation beta."""
+    o = [ctypes.c_double() for _ in range(3)]
+    _load().orc_locked_ellipse(*[float(v) for v in (a, b, c, zeta, eta, xi, alpha, beta)],
+                               *[ctypes.byref(v) for v in o])
+    return tuple(v.value for v in o)
+
+
 def _optional(arr, n):
     if arr is None:
         return None, None
@@ -177,12 +188,13 @@ PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi
 
 
 def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
-               tol: float = DEFAULT_TOL, nthreads: int = 0) -> np.ndarray:
+               tol: float = DEFAULT_TOL, nthreads: int = 0, locked: bool = False) -> np.ndarray:
     """Supersampled light curves for a batch of parameter sets.
 
     ``params`` maps each of PARAM_NAMES to an array of n_sets floats, and may add
     "g" and "zeta" (triaxial shape: c the largest semi-axis, b = c (1 - g),
-    a = c (1 - f); rotation zeta about x').  With
+    a = c (1 - f); rotation zeta about x').  ``locked`` makes the body
+    tidally locked (Appendix B): its projection follows the orbital angle.  With
     ``offsets`` None, ``t`` is one grid shared by every set and the result has
     shape (n_sets, len(t)); otherwise set s owns t[offsets[s]:offsets[s+1]] and the
     result is flat in the same layout.  ``nsuper`` is an int or an array of
@@ -211,7 +223,8 @@ def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
         ns_p, ns_all = ns_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0
     g_arr, g_p = _optional(params.get("g"), n_sets)
     z_arr, z_p = _optional(params.get("zeta"), n_sets)
-    st = lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], g_p, z_p, _p(t), offp, n_times,
+    st = lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], g_p, z_p, int(bool(locked)), _p(t),
+                            offp, n_times,
                             _p(exptime), ns_p, ns_all, float(tol), int(nthreads), _p(out))
     if st != 0:
         raise ValueError("oracle rejected its inputs")

@@ -205,6 +205,34 @@ void orc_triaxial_ellipse(double k, double f, double g, double zeta, double eta,
     orc_projected_ellipse(c * (1.0 - f), c * (1.0 - g), c, zeta, eta, xi, dx, dy1, dy2);
 }
 
+/* Tidally locked body (Appendix B): the projection at orbital angle alpha and
+ * elevation beta by the printed Eqs. dx-locked, dy1-locked, dy2-locked, with
+ * r1..r9 the components of R(zeta, eta, xi) as in Sec. 2. */
+void orc_locked_ellipse(double a, double b, double c, double zeta, double eta, double xi,
+                        double alpha, double beta, double *dx, double *dy1, double *dy2) {
+    double Rx[9], Ry[9], Rz[9], T[9], R[9];
+    rot_x(zeta, Rx);
+    rot_y(eta, Ry);
+    rot_z(xi, Rz);
+    matmul3(Rx, Ry, T);
+    matmul3(T, Rz, R);
+    double r1 = R[0], r2 = R[1], r3 = R[2], r4 = R[3], r5 = R[4], r6 = R[5];
+    double r7 = R[6], r8 = R[7], r9 = R[8];
+    double sa = sin(alpha), ca = cos(alpha), sb = sin(beta), cb = cos(beta);
+    double a2 = a * a, b2 = b * b, c2 = c * c;
+    double u1 = sb * (r3 * ca + r2 * sa) - r1 * cb;
+    double u2 = sb * (r6 * ca + r5 * sa) - r4 * cb;
+    double u3 = sb * (r9 * ca + r8 * sa) - r7 * cb;
+    double ddx = sqrt(a2 * u1 * u1 + b2 * u2 * u2 + c2 * u3 * u3);
+    *dx = ddx;
+    *dy1 = (a2 * u1 * (r3 * sa - r2 * ca) + b2 * u2 * (r6 * sa - r5 * ca) +
+            c2 * u3 * (r9 * sa - r8 * ca)) / ddx;
+    double w1 = r7 * sb + cb * (r9 * ca + r8 * sa);
+    double w2 = r4 * sb + cb * (r6 * ca + r5 * sa);
+    double w3 = r1 * sb + cb * (r3 * ca + r2 * sa);
+    *dy2 = sqrt(a2 * b2 * w1 * w1 + a2 * c2 * w2 * w2 + b2 * c2 * w3 * w3) / ddx;
+}
+
 /* Kipping (2013) map from (q1, q2) to quadratic coefficients (cited in Sec. 3,
  * Table priors, note f; the formula itself is not printed in the paper). */
 void orc_q_to_u(double q1, double q2, double *u1, double *u2) {
@@ -439,7 +467,7 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
                    const double *a_rs, const double *b, const double *ecc,
                    const double *omega, const double *k, const double *f,
                    const double *eta, const double *xi, const double *u1,
-                   const double *u2, const double *g, const double *zeta,
+                   const double *u2, const double *g, const double *zeta, int locked,
                    const double *t, const int64_t *offsets,
                    int64_t n_times, const double *exptime, const int32_t *nsuper_arr,
                    int nsuper_all, double tol, int nthreads, double *out) {
@@ -481,6 +509,18 @@ int orc_lightcurve(int64_t n_sets, const double *t0, const double *period,
             double x0, y0, z;
             orc_sky_position(tq, t0[s], period[s], a_rs[s], cosi, ecc[s], omega[s], &x0,
                              &y0, &z);
+            if (locked) {
+                /* Appendix B with the Keplerian orbit: beta = pi/2 - i and alpha the
+                 * orbital angle from conjunction, alpha = w + nu - pi/2, from
+                 * r cos(alpha) = r sin(w + nu) = x0 cos i - z sin i, r sin(alpha) = y0 */
+                double gg = g ? g[s] : 0.0, zz = zeta ? zeta[s] : 0.0;
+                double cax = k[s] / cbrt((1.0 - f[s]) * (1.0 - gg));
+                double sini = sqrt(1.0 - cosi * cosi);
+                double alpha = atan2(y0, x0 * cosi - z * sini);
+                double beta = 0.5 * M_PI - acos(cosi);
+                orc_locked_ellipse(cax * (1.0 - f[s]), cax * (1.0 - gg), cax, zz, eta[s], xi[s],
+                                   alpha, beta, &dx, &dy1, &dy2);
+            }
             acc += orc_flux_sky(x0, y0, z, dx, dy1, dy2, u1[s], u2[s], tol);
         }
         out[j] = acc / nsuper;

@@ -34,7 +34,7 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
             "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
             "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike", "gl_item_pipeline",
-            "gl_flux_sky_simpson")
+            "gl_flux_sky_simpson", "gl_lightcurve_locked")
 
 SUR_BINS = 16
 
@@ -115,6 +115,9 @@ def load():
         lib.gl_lightcurve_batch.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times),
                                             vp, i32, vp]
         lib.gl_lightcurve_batch.restype = i32
+        lib.gl_lightcurve_locked.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times),
+                                             vp, i32, vp]
+        lib.gl_lightcurve_locked.restype = i32
         lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
         lib.gl_flux_sky.restype = i32
         lib.gl_flux_sky_simpson.argtypes = [vp, i64] + [vp] * 10 + [i32, i32, vp]
@@ -232,12 +235,13 @@ def gl_last_error(ctx) -> str:
 
 def gl_lightcurve_batch(ctx, params: dict, t, out, precision: int = GL_FP32C, offsets=None,
                         exptime=None, nsuper=None, nsuper_all: int = 1, stream=None,
-                        check: bool = True) -> int:
+                        check: bool = True, locked: bool = False) -> int:
     """Marshal arrays into gl_params / gl_times and call the library.
 
-    ``params`` maps PARAM_NAMES to float64 arrays of n_sets entries; ``exptime``
-    is a float64 array of n_sets; ``nsuper`` an int32 array or None (then
-    ``nsuper_all``); ``offsets`` int64 of n_sets + 1 or None for a shared grid.
+    ``params`` maps PARAM_NAMES to float64 arrays of n_sets entries (plus optional
+    "g", "zeta"); ``exptime`` is a float64 array of n_sets; ``nsuper`` an int32
+    array or None (then ``nsuper_all``); ``offsets`` int64 of n_sets + 1 or None for
+    a shared grid.  ``locked`` calls gl_lightcurve_locked (tidally locked bodies).
     """
     lib = load()
     n_sets = int(len(params["t0"]))
@@ -246,8 +250,9 @@ def gl_lightcurve_batch(ctx, params: dict, t, out, precision: int = GL_FP32C, of
     n_total = int(len(out))
     tm = _Times(_ptr(t, "float64"), _ptr(offsets, "int64"), 0 if offsets is not None else n_t,
                 n_total, _ptr(exptime, "float64"), _ptr(nsuper, "int32"), int(nsuper_all))
-    rc = lib.gl_lightcurve_batch(ctx, ctypes.byref(p), ctypes.byref(tm), _ptr(out, "float64"),
-                                 int(precision), _stream_ptr(stream))
+    fn = lib.gl_lightcurve_locked if locked else lib.gl_lightcurve_batch
+    rc = fn(ctx, ctypes.byref(p), ctypes.byref(tm), _ptr(out, "float64"), int(precision),
+            _stream_ptr(stream))
     if check:
         _check(ctx, rc)
     return rc
@@ -493,9 +498,9 @@ class Context:
             pass
 
     def lightcurve(self, params, t, out, exptime, nsuper=None, nsuper_all=1, offsets=None,
-                   precision=GL_FP32C, stream=None):
+                   precision=GL_FP32C, stream=None, locked=False):
         return gl_lightcurve_batch(self.handle, params, t, out, precision, offsets, exptime,
-                                   nsuper, nsuper_all, stream)
+                                   nsuper, nsuper_all, stream, locked=locked)
 
     def flux_sky(self, x0, y0, z, k, f, eta, xi, u1, u2, out, precision=GL_FP32C, stream=None):
         return gl_flux_sky(self.handle, x0, y0, z, k, f, eta, xi, u1, u2, out, precision, stream)

@@ -124,12 +124,15 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
       orbit_ok = gl::set_orbit(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], sh_s[0][lane],
                                sh_c[0][lane], c);
     } else if (role == 1) {
-      const double g = p.g ? p.g[s] : 0.0;
+      const double g = p.g ? p.g[s] : 0.0, f = p.f[s];
       if (g != 0.0)
-        gl::set_shape_triaxial(p.k[s], p.f[s], g, cb, sh_s[3][lane], sh_c[3][lane],
+        gl::set_shape_triaxial(p.k[s], f, g, cb, sh_s[3][lane], sh_c[3][lane],
                                sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
       else
-        gl::set_shape(p.k[s], p.f[s], cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
+        gl::set_shape(p.k[s], f, cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
+      const double cax = p.k[s] * gl::rcp64(cb);   // c = k ((1 - f)(1 - g))^(-1/3)
+      gl::set_body(cax * (1.0 - f), cax * (1.0 - g), cax, sh_s[3][lane], sh_c[3][lane],
+                   sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
     } else if (role == 2) {
       const double period = p.period[s], invP = gl::rcp64(period);
       sh_win[lane] = gl::set_window(p.t0[s], period, p.a_rs[s], p.ecc[s], p.omega[s],
@@ -813,6 +816,63 @@ __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
       const int fl = exposure_prep<R>(c, a.t[ti], &tau, &mid);
       a.out[j] = (fl & kExpDead) ? 1.0 : exposure_local<R>(c, fl, mid, tau, c.nsuper, rb);
     }
+  }
+}
+
+// Tidally locked bodies (Appendix B): the projection follows the orbital angle,
+// so every sub-exposure has its own ellipse.  One thread per exposure: window
+// test, then per sub-exposure the FP64 Kepler position, the orbital angle alpha
+// from conjunction (r cos alpha = x0 cos i - z sin i, r sin alpha = y0, the
+// Keplerian reading of the paper's alpha), the locked projection and the same
+// quadrature as the other paths; FP64 exposure mean in sub-exposure order.
+template <typename R>
+__global__ void __launch_bounds__(128) gl_locked_kernel(const SetConst* __restrict__ sets,
+                                                        const double* __restrict__ t,
+                                                        const int64_t* __restrict__ offsets,
+                                                        int64_t n_times, int64_t n_sets,
+                                                        int64_t n_total, int rule_idx,
+                                                        double* __restrict__ out) {
+  const int rb = rule_base(rule_idx);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s;
+    double tj;
+    if (offsets) {
+      s = owner_of(offsets, n_sets, j);
+      tj = t[j];
+    } else {
+      s = j / n_times;
+      tj = t[j - s * n_times];
+    }
+    const SetConst& c = sets[s];
+    if (c.flags & gl::kSetInvalid) {
+      out[j] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    const double tau = gl::wrap_tau(c, tj);
+    const int ns = c.nsuper;
+    if (!gl::in_window(c, tau, 0.5 * c.exptime)) {
+      out[j] = 1.0;
+      continue;
+    }
+    double acc = 0.0;
+    for (int q = 0; q < ns; ++q) {
+      double x0, y0, z;
+      gl::sky_position(c, tau + gl::subexposure_offset(q, ns, c.exptime), &x0, &y0, &z);
+      const int cls = gl::classify(c, x0, y0, z);   // R_eq bounds every projection
+      if (cls == gl::kOut) {
+        acc += 1.0;
+        continue;
+      }
+      double ca = x0 * c.cosi - z * c.sini, sa = y0;
+      const double ir = gl::rcp64(sqrt(ca * ca + sa * sa));
+      SetConst cl;
+      gl::locked_shape(c, ca * ir, sa * ir, &cl);
+      const R d = item_deficit<R>(cl, (R)x0, (R)y0, (R)((1.0 - x0) * (1.0 + x0) - y0 * y0),
+                                  cls, rb);
+      acc += 1.0 - (double)d;
+    }
+    out[j] = acc / ns;
   }
 }
 
@@ -1615,6 +1675,7 @@ struct StepArgs {
   SetConst* sets;
   void* items;        // item workspace, or null: every tile integrates locally
   int64_t item_cap;
+  int locked;         // tidally locked bodies: gl_locked_kernel
 };
 
 int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
@@ -1633,6 +1694,21 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
   la.n_sets = sa.n_sets;
   la.n_total = sa.n_total;
   la.out = sa.out;
+  if (sa.locked) {
+    const int rule_idx = ctx->cfg[sa.prec == GL_FP64 ? 0 : 1].rule_idx;
+    pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
+    const int grid = launch_grid(sa.n_total, 128);
+    if (sa.prec == GL_FP64)
+      gl_locked_kernel<double><<<grid, 128, 0, st>>>(sa.sets, sa.t, sa.offsets, sa.n_times,
+                                                     sa.n_sets, sa.n_total, rule_idx, sa.out);
+    else
+      gl_locked_kernel<float><<<grid, 128, 0, st>>>(sa.sets, sa.t, sa.offsets, sa.n_times,
+                                                    sa.n_sets, sa.n_total, rule_idx, sa.out);
+    prof_end(ctx, GL_KERNEL_CURVE, pe, st);
+    ctx->launches++;
+    GL_CUDA(ctx, cudaGetLastError());
+    return GL_OK;
+  }
   if (sa.items) {
     item_arrays(sa.items, sa.item_cap, sa.n_total, sa.prec == GL_FP64 ? sizeof(double) : sizeof(float),
                 &la);
@@ -1653,7 +1729,8 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     if (g.key_len == sizeof key && memcmp(g.key, key, sizeof key) == 0) hit = &g;
   if (!hit) {
     // the occupancy query and attribute setting must not happen inside a capture
-    if (!lc_ready(ctx, sa.prec, sa.items != nullptr)) return enqueue_step(ctx, sa, st);   // first call: eager
+    if (!sa.locked && !lc_ready(ctx, sa.prec, sa.items != nullptr))
+      return enqueue_step(ctx, sa, st);   // first call: eager
     GL_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int64_t l0 = ctx->launches;
     int rc = enqueue_step(ctx, sa, ctx->cap_stream);
@@ -1950,8 +2027,12 @@ int gl_sync(gl_context* ctx, void* stream) {
   return GL_OK;
 }
 
-int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
-                        gl_precision prec, void* stream) {
+}  // extern "C"
+
+namespace {
+
+int lightcurve_impl(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
+                    gl_precision prec, void* stream, bool locked) {
   if (!ctx) return GL_EINVAL;
   ctx->err[0] = 0;
   if (!p || !tm) return fail(ctx, GL_EINVAL, "NULL params or times");
@@ -2025,7 +2106,7 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
   }
   void* iws = nullptr;
   int64_t item_cap = 0;
-  if (ctx->item_pipeline) {
+  if (ctx->item_pipeline && !locked) {
     // sized for every sub-exposure of the batch (per-set nsuper: 16 per exposure),
     // capped at item_max; tiles whose items do not fit integrate locally
     int64_t per = tm->nsuper ? 16 : tm->nsuper_all;
@@ -2038,6 +2119,11 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
   }
   StepArgs sa;
   memset(&sa, 0, sizeof sa);
+  sa.locked = locked ? 1 : 0;
+  if (locked) {
+    iws = nullptr;
+    item_cap = 0;
+  }
   sa.items = iws;
   sa.item_cap = item_cap;
   sa.pp = pp;
@@ -2062,6 +2148,20 @@ int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm,
   }
   if (out_host || any_host) GL_CUDA(ctx, cudaStreamSynchronize(st));
   return GL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gl_lightcurve_batch(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
+                        gl_precision prec, void* stream) {
+  return lightcurve_impl(ctx, p, tm, out, prec, stream, false);
+}
+
+int gl_lightcurve_locked(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
+                         gl_precision prec, void* stream) {
+  return lightcurve_impl(ctx, p, tm, out, prec, stream, true);
 }
 
 int gl_flux_sphere(gl_context* ctx, int64_t n, const double* x0, const double* y0,

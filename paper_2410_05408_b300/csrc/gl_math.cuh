@@ -57,6 +57,9 @@ struct SetConst {
   int nsuper;
   int flags;
   int rule_min;    // least FP32 quadrature order for this shape (index: 16, 20, 24, 28 nodes)
+  // body: semi-axes (a along x', b along y', c along z') and the rows of
+  // R(zeta, eta, xi), for projections that change along the orbit (tidal locking)
+  double ax[3], rot[9];
 };
 
 // Mapped Gauss-Legendre rule on s in [-1, 1] with theta = m + h sin(pi s / 2):
@@ -339,6 +342,53 @@ GL_HD void set_shape_triaxial(double k, double f, double g, double cbrt_fg, doub
   c->fW0 = (float)c->W0;
 }
 
+// Body semi-axes and the rows of R(zeta, eta, xi) = Rx(zeta) Ry(eta) Rz(xi).
+GL_HD void set_body(double a, double b, double cax, double sz, double cz, double se, double ce,
+                    double sx, double cx, SetConst* c) {
+  c->ax[0] = a;
+  c->ax[1] = b;
+  c->ax[2] = cax;
+  c->rot[0] = ce * cx;
+  c->rot[1] = -ce * sx;
+  c->rot[2] = se;
+  c->rot[3] = cz * sx + sz * se * cx;
+  c->rot[4] = cz * cx - sz * se * sx;
+  c->rot[5] = -sz * ce;
+  c->rot[6] = sz * sx - cz * se * cx;
+  c->rot[7] = sz * cx + cz * se * sx;
+  c->rot[8] = cz * ce;
+}
+
+// Projected ellipse of a tidally locked body (Appendix B) at the orbital angle
+// alpha from conjunction (cos, sin given) with beta = pi/2 - i: the body frame is
+// x' = R (Rx(-alpha) Ry(beta) x + (0, 0, d)), so with M = R Rx(-alpha) Ry(beta)
+// and D = diag(a^2, b^2, c^2) the sky covariance is M^T D M restricted to (x, y):
+// dx = sqrt(sum_k D_k M_k1^2), dy1 = sum_k D_k M_k1 M_k2 / dx and
+// dy2 = sqrt(D_a D_b M_33^2 + D_a D_c M_23^2 + D_b D_c M_13^2) / dx (a rotation's
+// cofactors are its elements) -- the paper's Eqs. dx-locked, dy1-locked,
+// dy2-locked in matrix form.  `out` gets a copy of c with the new shape.
+GL_HD void locked_shape(const SetConst& c, double ca, double sa, SetConst* out) {
+  *out = c;
+  const double sb = c.cosi, cb = c.sini;   // beta = pi/2 - i
+  // Q = Rx(-alpha) Ry(beta)
+  const double q[9] = {cb, 0.0, sb, -sa * sb, ca, sa * cb, -ca * sb, -sa, ca * cb};
+  double M[9];
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j)
+      M[3 * k + j] = c.rot[3 * k] * q[j] + c.rot[3 * k + 1] * q[3 + j] + c.rot[3 * k + 2] * q[6 + j];
+  const double D0 = c.ax[0] * c.ax[0], D1 = c.ax[1] * c.ax[1], D2 = c.ax[2] * c.ax[2];
+  const double dx = sqrt(D0 * M[0] * M[0] + D1 * M[3] * M[3] + D2 * M[6] * M[6]);
+  const double idx = rcp64(dx);
+  out->dx = dx;
+  out->dy1 = (D0 * M[0] * M[1] + D1 * M[3] * M[4] + D2 * M[6] * M[7]) * idx;
+  out->dy2 = sqrt(D0 * D1 * M[8] * M[8] + D0 * D2 * M[5] * M[5] + D1 * D2 * M[2] * M[2]) * idx;
+  out->W0 = out->dx * out->dy2;
+  out->fdx = (float)out->dx;
+  out->fdy1 = (float)out->dy1;
+  out->fdy2 = (float)out->dy2;
+  out->fW0 = (float)out->W0;
+}
+
 // Limb darkening in the basis (1, mu, r^2): I = c0 + c1 mu + c2 r^2 with
 // F0 = pi (1 - u1/3 - u2/6).
 GL_HD void set_ld(double u1, double u2, SetConst* c) {
@@ -481,8 +531,10 @@ GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc
   if (isfinite(xi)) sincos_setup(xi, &sx, &cx);
   if (isfinite(eta)) sincos_setup(eta, &se, &ce);
   if (isfinite(f) && f < 1.0) cb = cbrt_setup(1.0 - f);
-  return set_setup_trig(t0, period, a_rs, b, ecc, omega, k, f, eta, xi, u1, u2, exptime, nsuper,
-                        sw, cw, cb, ce, sx, cx, c);
+  const bool ok = set_setup_trig(t0, period, a_rs, b, ecc, omega, k, f, eta, xi, u1, u2, exptime,
+                                 nsuper, sw, cw, cb, ce, sx, cx, c);
+  if (ok) set_body(c->req * (1.0 - f), c->req, c->req, 0.0, 1.0, se, ce, sx, cx, c);
+  return ok;
 }
 
 // (t - t0) wrapped to one period around the conjunction.

@@ -104,6 +104,22 @@ def triaxial_batch(n_sets: int = 12, n_times: int = 400, seed: int = 51) -> dict
                 nsuper=7)
 
 
+def locked_batch(n_sets: int = 12, n_times: int = 300, seed: int = 61) -> dict:
+    """Close-in planets for the tidally locked mapping: P U[1, 4] d, a/R* U[3, 8],
+    e U[0, 0.1], b U[0, 0.6], k U[0.08, 0.2], f U[0, 0.5], g U[0, 0.4], all three
+    orientation angles uniform; 300 times every 2 min around the conjunction, x 5."""
+    rng = _rng(seed)
+    p = dict(t0=np.zeros(n_sets), period=rng.uniform(1.0, 4.0, n_sets),
+             a_rs=rng.uniform(3.0, 8.0, n_sets), b=rng.uniform(0.0, 0.6, n_sets),
+             ecc=rng.uniform(0.0, 0.1, n_sets), omega=rng.uniform(0.0, 2.0 * np.pi, n_sets),
+             k=rng.uniform(0.08, 0.2, n_sets), f=rng.uniform(0.0, 0.5, n_sets),
+             eta=rng.uniform(0.0, np.pi, n_sets), xi=rng.uniform(0.0, np.pi, n_sets),
+             q1=rng.uniform(0.0, 1.0, n_sets), q2=rng.uniform(0.0, 1.0, n_sets),
+             g=rng.uniform(0.0, 0.4, n_sets), zeta=rng.uniform(0.0, np.pi, n_sets))
+    t = (np.arange(n_times) - 0.5 * (n_times - 1)) * (2.0 / 1440.0)
+    return dict(params=p, t=t, offsets=None, exptime=np.full(n_sets, 2.0 / 1440.0), nsuper=5)
+
+
 def uneven_batch(n_curves: int = 4096, seed: int = 2, min_len: int = 100,
                  max_len: int = 50000) -> dict:
     """Curves of log-uniform length; even curves 60-s cadence (nsuper 1), odd

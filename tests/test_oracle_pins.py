@@ -126,6 +126,47 @@ def test_projection_support_function(abc, angles):
         assert abs(ell - brute) < 2e-4 * max(abc)
 
 
+def _locked_support(a, b, c, zeta, eta, xi, alpha, beta, u, n=400):
+    """Support function for the tidally locked mapping of Appendix B, brute force:
+    body coordinates x' = R(zeta, eta, xi) (Rx(-alpha) Ry(beta) x + (0, 0, d)), so a
+    surface point x' sits at x = (R Rx(-alpha) Ry(beta))^T x' from the centre."""
+    M = (_rotmat("x", zeta) @ _rotmat("y", eta) @ _rotmat("z", xi)
+         @ _rotmat("x", -alpha) @ _rotmat("y", beta))
+    th, ph = np.meshgrid(np.linspace(0, np.pi, n), np.linspace(0, 2 * np.pi, 2 * n))
+    pts = np.stack([a * np.sin(th) * np.cos(ph), b * np.sin(th) * np.sin(ph),
+                    c * np.cos(th)], -1).reshape(-1, 3)
+    sky = pts @ M
+    return np.max(sky[:, :2] @ u)
+
+
+@pytest.mark.parametrize("abc,angles,orbit", [((0.05, 0.08, 0.11), (0.3, 1.1, -0.7), (0.4, 0.1)),
+                                              ((0.12, 0.09, 0.06), (1.2, 0.4, 2.0), (-0.9, 0.3)),
+                                              ((0.07, 0.07, 0.03), (0.0, 0.9, 0.3), (2.5, -0.2))])
+def test_locked_projection_support_function(abc, angles, orbit):
+    """The printed Eqs. dx-locked, dy1-locked, dy2-locked against a brute-force
+    support function of the body in the locked orientation (Appendix B)."""
+    dx, dy1, dy2 = oracle.locked_ellipse(*abc, *angles, *orbit)
+    thg = np.linspace(0, 2 * np.pi, 20001)
+    for phi in np.linspace(0, np.pi, 13):
+        u = np.array([math.cos(phi), math.sin(phi)])
+        ell = np.max(u[0] * dx * np.cos(thg) + u[1] * (dy1 * np.cos(thg) + dy2 * np.sin(thg)))
+        assert abs(ell - _locked_support(*abc, *angles, *orbit, u)) < 2e-4 * max(abc)
+
+
+def test_locked_projection_special_cases():
+    """alpha = beta = 0 is the unlocked projection; a sphere projects to a circle
+    of its radius at every orbital angle."""
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        abc = rng.uniform(0.02, 0.2, 3)
+        ang = rng.uniform(-3, 3, 3)
+        np.testing.assert_allclose(oracle.locked_ellipse(*abc, *ang, 0.0, 0.0),
+                                   oracle.projected_ellipse(*abc, *ang), rtol=1e-12, atol=1e-16)
+        r = abc[0]
+        dx, dy1, dy2 = oracle.locked_ellipse(r, r, r, *ang, *rng.uniform(-3, 3, 2))
+        np.testing.assert_allclose([dx, dy1, dy2], [r, 0.0, r], rtol=1e-12, atol=1e-15)
+
+
 def test_oblate_projection_axes_and_zeta_invariance():
     rng = np.random.default_rng(0)
     for _ in range(40):
