@@ -579,6 +579,81 @@ def locked_arm(args):
     ctx.close()
 
 
+def ensemble_arm(args):
+    """The device-resident stretch-move ensemble (gl_ensemble_sweep) on the
+    injected single-transit curve: 1024 walkers in the (mu, nu) parameterisation
+    of Appendix A, 3000 exposures x 15; sweeps/s and light-curve evaluations/s
+    (two half-ensembles of proposals per sweep), CUDA events around the sweeps."""
+    import torch
+    from paper_2410_05408_b300 import binding, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    inj = inputs.injected_curve(n_walkers=args.walkers)
+    tr = {k: float(v[0]) for k, v in inj["truth"].items()}
+    u1, u2 = tr["u1"], tr["u2"]
+    q1 = (u1 + u2) ** 2
+    q2 = u1 / (2.0 * (u1 + u2))
+    # (mu, nu) of the truth, through the library's own kernel
+    f_d = torch.tensor([tr["f"]], dtype=torch.float64, device=dev)
+    e_d = torch.tensor([tr["eta"]], dtype=torch.float64, device=dev)
+    mu_d, nu_d = torch.empty_like(f_d), torch.empty_like(f_d)
+    binding.gl_munu(ctx.handle, "to_munu", f_d, e_d, mu_d, nu_d)
+    truth = np.array([tr["t0"], tr["period"], tr["a_rs"], tr["b"], tr["k"], float(mu_d.item()),
+                      float(nu_d.item()), tr["xi"], q1, q2])
+    lo = np.array([-0.2, 540.0, 150.0, 0.0, 0.03, -1.0, 0.0, 0.0, 0.0, 0.0])
+    hi = np.array([0.2, 544.0, 300.0, 0.9, 0.12, 1.0, 1.0, np.pi, 1.0, 1.0])
+    rng = np.random.default_rng(8)
+    n = args.walkers
+    scale = np.array([1e-3, 1e-3, 0.5, 0.01, 1e-4, 0.01, 0.01, 0.01, 0.01, 0.01])
+    X = np.clip(truth + scale * rng.standard_normal((n, 10)), lo + 1e-9, hi - 1e-9)
+    # data: the model at the truth (library FP64 path) plus the seeded noise
+    t = np.ascontiguousarray(inj["t"])
+    d_t = torch.as_tensor(t, device=dev)
+    p_true = {k: torch.tensor([float(v[0])], dtype=torch.float64, device=dev)
+              for k, v in inj["truth"].items()}
+    model = torch.empty(t.size, dtype=torch.float64, device=dev)
+    ctx.lightcurve(p_true, d_t, model, torch.full((1,), inj["exptime"], dtype=torch.float64,
+                                                  device=dev),
+                   nsuper_all=inj["nsuper"], precision=binding.GL_FP64)
+    data = model + torch.as_tensor(inj["noise"], device=dev)
+    sigma = torch.full_like(data, 1e-4)
+    walkers = torch.as_tensor(X, device=dev).contiguous()
+    ens = binding.Ensemble(ctx, walkers, torch.as_tensor(lo, device=dev),
+                           torch.as_tensor(hi, device=dev), d_t, data, sigma, inj["exptime"],
+                           inj["nsuper"], precision=binding.GL_FP32C)
+    ens.init()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9)
+    acc = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        ens.sweep(torch.rand(3 * n, dtype=torch.float64, device=dev, generator=gen), acc)
+    rnd = [torch.rand(3 * n, dtype=torch.float64, device=dev, generator=gen)
+           for _ in range(args.sweeps)]
+    acc.zero_()
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for r in rnd:
+        ens.sweep(r, acc, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / args.sweeps
+    evals = n * t.size * inj["nsuper"]
+    status = ctx.sync()
+    line = {"metric": "device-resident stretch-move sweeps: light-curve evals/s", "value":
+            evals / (ms * 1e-3), "unit": "evals/s", "n_gpus": 1, "steps": args.sweeps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "ensemble", "walkers": n, "exposures": int(t.size),
+                       "nsuper": int(inj["nsuper"]), "parameterisation": "(mu, nu) Appendix A"},
+            "sweeps_per_s": 1e3 / ms, "acceptance": int(acc.item()) / (n * args.sweeps),
+            "status": status}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -611,6 +686,8 @@ def main():
         return simpson_arm(args)
     if args.workload == "locked_batch":
         return locked_arm(args)
+    if args.workload == "ensemble":
+        return ensemble_arm(args)
 
     import torch
     from paper_2410_05408_b300 import binding, build

@@ -386,6 +386,58 @@ int gl_loglike(gl_context *ctx, int64_t n_sets, int64_t n_times, const double *f
                const double *data, const double *sigma, double *loglike, void *stream);
 
 /* ------------------------------------------------------------------------
+ * The (mu, nu) reparameterisation of Appendix A and a device-resident ensemble
+ * sampler.
+ *
+ * For an oblate spheroid the flux depends on (f, eta) only through
+ * mu = (f - 1)^2 + f (f - 2) cos(2 eta); nu in [0, 1] places f between
+ * f_min = 1 - sqrt((mu + 1)/2) and 1 (f = f_min + (1 - f_min) nu).  The joint
+ * density p(mu, nu) of Appendix A makes the prior on (f, eta) uniform in f and
+ * proportional to cos(eta); it is drawn from two uniforms (u, w) by the printed
+ * inverse transforms.  Element-wise on n entries, FP64, device memory;
+ * GL_EINVAL on NULL or host arrays. */
+int gl_munu_to_feta(gl_context *ctx, int64_t n, const double *mu, const double *nu,
+                    double *f, double *eta, void *stream);
+int gl_feta_to_munu(gl_context *ctx, int64_t n, const double *f, const double *eta,
+                    double *mu, double *nu, void *stream);
+int gl_munu_prior(gl_context *ctx, int64_t n, const double *u, const double *w,
+                  double *mu, double *nu, void *stream);
+
+/* Fit vector of a walker: t0, period, a_rs, b, k, mu, nu, xi, q1, q2 (circular
+ * orbit; f and eta from (mu, nu); u1, u2 from (q1, q2) by Kipping's map). */
+#define GL_FIT_DIM 10
+
+typedef struct {
+  int64_t n_walkers;       /* even, 4 .. 2^26 */
+  double *walkers;         /* n_walkers x GL_FIT_DIM, row-major, device; updated in place */
+  double *logpost;         /* n_walkers, device; written by init, updated by sweeps */
+  const double *lo, *hi;   /* GL_FIT_DIM box bounds of the uniform prior, device */
+  const double *t;         /* n_times exposure midpoints (days), device */
+  int64_t n_times;
+  const double *data, *sigma;   /* n_times observed relative flux and its error, device */
+  double exptime;          /* exposure time (days) */
+  int nsuper;              /* sub-exposures per exposure */
+  double a;                /* stretch scale (> 1; 2 is usual) */
+  gl_precision prec;       /* light-curve path */
+} gl_ensemble;
+
+/* log posterior of every walker: log prior (uniform in the box, -inf outside,
+ * times p(mu, nu)) + Gaussian log likelihood of its light curve (as gl_loglike).
+ * The context keeps a workspace of (12 + 2 + n_times) doubles per walker. */
+int gl_ensemble_init(gl_context *ctx, const gl_ensemble *e, void *stream);
+
+/* One sweep of the affine-invariant stretch move (Goodman and Weare 2010), all on
+ * the device: for each half h = 0, 1 of the ensemble (walkers k = 2 i + h,
+ * i < n/2), proposals Y = X_j + z (X_k - X_j) with partner
+ * j = 2 floor(r_j n/2) + 1 - h and z = ((a - 1) r_z + 1)^2 / a, their light curves
+ * and log posteriors, and acceptance when log(r_u) < (D - 1) log z + lp(Y) - lp(X).
+ * rnd: 3 n_walkers uniforms in [0, 1) on the device, laid out per half as
+ * (r_z, r_j, r_u), n/2 each.  accepted: optional device counter, incremented per
+ * accepted move.  Stream-ordered: no host synchronisation. */
+int gl_ensemble_sweep(gl_context *ctx, const gl_ensemble *e, const double *rnd,
+                      unsigned long long *accepted, void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free variant of gl_lightcurve_batch.  The paper has no
  * counterpart: this is a deployment aid.
  *

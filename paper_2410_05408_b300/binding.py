@@ -34,7 +34,8 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
             "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
             "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike", "gl_item_pipeline",
-            "gl_flux_sky_simpson", "gl_lightcurve_locked")
+            "gl_flux_sky_simpson", "gl_lightcurve_locked", "gl_munu_to_feta",
+            "gl_feta_to_munu", "gl_munu_prior", "gl_ensemble_init", "gl_ensemble_sweep")
 
 SUR_BINS = 16
 
@@ -79,6 +80,18 @@ class _TuneReport(ctypes.Structure):
                 ("admissible", ctypes.c_int)]
 
 
+GL_FIT_DIM = 10
+FIT_NAMES = ("t0", "period", "a_rs", "b", "k", "mu", "nu", "xi", "q1", "q2")
+
+
+class _Ensemble(ctypes.Structure):
+    _fields_ = [("n_walkers", ctypes.c_int64), ("walkers", ctypes.c_void_p),
+                ("logpost", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("n_times", ctypes.c_int64), ("data", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("exptime", ctypes.c_double),
+                ("nsuper", ctypes.c_int), ("a", ctypes.c_double), ("prec", ctypes.c_int)]
+
+
 class _SurStats(ctypes.Structure):
     _fields_ = [("items", ctypes.c_int64), ("exposures", ctypes.c_int64),
                 ("fallback", ctypes.c_int64)]
@@ -118,6 +131,13 @@ def load():
         lib.gl_lightcurve_locked.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times),
                                              vp, i32, vp]
         lib.gl_lightcurve_locked.restype = i32
+        for name in ("gl_munu_to_feta", "gl_feta_to_munu", "gl_munu_prior"):
+            getattr(lib, name).argtypes = [vp, i64, vp, vp, vp, vp, vp]
+            getattr(lib, name).restype = i32
+        lib.gl_ensemble_init.argtypes = [vp, ctypes.POINTER(_Ensemble), vp]
+        lib.gl_ensemble_init.restype = i32
+        lib.gl_ensemble_sweep.argtypes = [vp, ctypes.POINTER(_Ensemble), vp, vp, vp]
+        lib.gl_ensemble_sweep.restype = i32
         lib.gl_flux_sky.argtypes = [vp, i64] + [vp] * 10 + [i32, vp]
         lib.gl_flux_sky.restype = i32
         lib.gl_flux_sky_simpson.argtypes = [vp, i64] + [vp] * 10 + [i32, i32, vp]
@@ -311,6 +331,43 @@ def gl_flux_sky_simpson(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, n_intervals:
     if check:
         _check(ctx, rc)
     return rc
+
+
+def gl_munu(ctx, op: str, a, b, c, d, stream=None) -> None:
+    """op: "to_feta" ((mu, nu) -> (f, eta)), "to_munu" ((f, eta) -> (mu, nu)) or
+    "prior" ((u, w) -> (mu, nu)); four device float64 arrays of equal length."""
+    fn = {"to_feta": "gl_munu_to_feta", "to_munu": "gl_feta_to_munu",
+          "prior": "gl_munu_prior"}[op]
+    _check(ctx, getattr(load(), fn)(ctx, int(len(a)), *[_ptr(x, "float64") for x in (a, b, c, d)],
+                                    _stream_ptr(stream)))
+
+
+class Ensemble:
+    """Device-resident stretch-move ensemble (gl_ensemble_init / gl_ensemble_sweep):
+    walkers (n x GL_FIT_DIM), logpost, box bounds and data are torch CUDA tensors
+    kept by the caller; sweep() takes the 3 n uniforms of one sweep."""
+
+    def __init__(self, ctx, walkers, lo, hi, t, data, sigma, exptime: float, nsuper: int,
+                 precision: int = GL_FP32C, a: float = 2.0):
+        import torch
+        self.ctx = ctx
+        self.walkers = walkers
+        self.logpost = torch.empty(walkers.shape[0], dtype=torch.float64, device=walkers.device)
+        self._keep = (lo, hi, t, data, sigma)
+        self.e = _Ensemble(int(walkers.shape[0]), _ptr(walkers, "float64"),
+                           _ptr(self.logpost, "float64"), _ptr(lo, "float64"),
+                           _ptr(hi, "float64"), _ptr(t, "float64"), int(len(t)),
+                           _ptr(data, "float64"), _ptr(sigma, "float64"), float(exptime),
+                           int(nsuper), float(a), int(precision))
+
+    def init(self, stream=None):
+        _check(self.ctx.handle, load().gl_ensemble_init(self.ctx.handle, ctypes.byref(self.e),
+                                                        _stream_ptr(stream)))
+
+    def sweep(self, rnd, accepted=None, stream=None):
+        _check(self.ctx.handle, load().gl_ensemble_sweep(
+            self.ctx.handle, ctypes.byref(self.e), _ptr(rnd, "float64"),
+            None if accepted is None else accepted.data_ptr(), _stream_ptr(stream)))
 
 
 def gl_flux_sphere(ctx, x0, y0, z, p, u1, u2, out, precision: int = GL_FP32C, stream=None,

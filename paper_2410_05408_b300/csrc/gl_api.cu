@@ -1233,6 +1233,163 @@ __global__ void gl_loglike_kernel(int64_t n_sets, int64_t n_times, const double*
   if (threadIdx.x == 0) ll[s] = -0.5 * red[0];
 }
 
+// ------------------------------------------------------------------ (mu, nu) and the ensemble
+// Appendix A: mu = (f - 1)^2 + f (f - 2) cos(2 eta); f = f_min + (1 - f_min) nu with
+// f_min = 1 - sqrt((mu + 1)/2); eta in [0, pi/2] from cos(2 eta) = (mu - (f-1)^2) /
+// (f (f - 2)).  The printed nu(f, eta), joint density p(mu, nu) and the inverse
+// transforms nu(u) = u^2 / (u^2 - 2u + 2), mu(w | nu).
+__device__ __forceinline__ void munu_to_feta(double mu, double nu, double* f, double* eta) {
+  const double fm = 1.0 - sqrt(0.5 * (mu + 1.0));
+  const double ff = fm + (1.0 - fm) * nu;
+  const double q = ff * (ff - 2.0);
+  double c2 = q != 0.0 ? (mu - (ff - 1.0) * (ff - 1.0)) / q : 1.0;
+  c2 = fmin(1.0, fmax(-1.0, c2));
+  *f = ff;
+  *eta = 0.5 * acos(c2);
+}
+
+__device__ __forceinline__ void feta_to_munu(double f, double eta, double* mu, double* nu) {
+  const double c2 = cos(2.0 * eta), ce = cos(eta), q = f * (f - 2.0);
+  *mu = (f - 1.0) * (f - 1.0) + q * c2;
+  *nu = (2.0 + 2.0 * q * ce * ce + (f - 1.0) * sqrt(4.0 + 2.0 * q * (1.0 + c2))) /
+        (2.0 + q * (1.0 + c2));
+}
+
+__device__ __forceinline__ void munu_prior_draw(double u, double w, double* mu, double* nu) {
+  const double v = u * u / (u * u - 2.0 * u + 2.0);
+  const double s = sqrt(v * (2.0 - v)), d = (v - 1.0) * (v - 1.0);
+  *nu = v;
+  *mu = (4.0 * w + 4.0 * (w * w - w) * s + 2.0 * (v * (v - 2.0) - 1.0) * w * w - d) / d;
+}
+
+__device__ __forceinline__ double log_p_munu(double mu, double nu) {
+  const double x = nu * (nu - 2.0) * (mu * (nu - 1.0) * (nu - 1.0) + nu * (nu - 2.0) - 1.0);
+  return x > 0.0 ? -1.5 * 0.69314718055994530942 - 0.5 * log(x) : -INFINITY;
+}
+
+enum : int { kMunuToFeta = 0, kFetaToMunu = 1, kMunuPrior = 2 };
+
+__global__ void gl_munu_kernel(int op, int64_t n, const double* __restrict__ a,
+                               const double* __restrict__ b, double* __restrict__ c,
+                               double* __restrict__ d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x, y;
+    if (op == kMunuToFeta) munu_to_feta(a[i], b[i], &x, &y);
+    else if (op == kFetaToMunu) feta_to_munu(a[i], b[i], &x, &y);
+    else munu_prior_draw(a[i], b[i], &x, &y);
+    c[i] = x;
+    d[i] = y;
+  }
+}
+
+// Fit vector -> parameter sets (structure of arrays, 12 x m) and log prior:
+// uniform inside [lo, hi] (also 0 <= q1, q2 <= 1, -1 <= mu <= 1, 0 <= nu <= 1),
+// times p(mu, nu), which makes the prior on (f, eta) uniform in f and ~ cos(eta)
+// (Appendix A); circular orbit (e = 0, w = pi/2); Kipping's map for (q1, q2).
+// Rows outside the box get log prior -inf and a harmless valid parameter set.
+__global__ void gl_ens_params_kernel(const double* __restrict__ x, int64_t m,
+                                     const double* __restrict__ lo, const double* __restrict__ hi,
+                                     double* __restrict__ soa, double* __restrict__ logprior) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[GL_FIT_DIM];
+    bool in = true;
+    for (int d = 0; d < GL_FIT_DIM; ++d) {
+      v[d] = x[i * GL_FIT_DIM + d];
+      in = in && v[d] >= lo[d] && v[d] <= hi[d];
+    }
+    const double mu = v[5], nu = v[6], q1 = v[8], q2 = v[9];
+    // (mu = -1 or nu = 1 would give f = 1; b >= a_rs no inclination)
+    in = in && mu > -1.0 && mu <= 1.0 && nu >= 0.0 && nu < 1.0 && q1 >= 0.0 && q1 <= 1.0 &&
+         q2 >= 0.0 && q2 <= 1.0 && v[1] > 0.0 && v[2] > 1.0 && v[4] > 0.0 && v[3] >= 0.0 &&
+         v[3] < v[2];
+    double lp = in ? log_p_munu(mu, nu) : -INFINITY;
+    if (!in) {   // any valid set: its light curve is not used
+      for (int d = 0; d < GL_FIT_DIM; ++d) v[d] = 0.5 * (lo[d] + hi[d]);
+      v[1] = fmax(v[1], 1.0);
+      v[2] = fmax(v[2], 2.0);
+      v[3] = 0.0;
+      v[4] = 0.05;
+      v[5] = 0.0;
+      v[6] = 0.5;
+      v[8] = 0.5;
+      v[9] = 0.5;
+    }
+    double f, eta;
+    munu_to_feta(v[5], v[6], &f, &eta);
+    const double sq = sqrt(v[8]);
+    double* o = soa;
+    o[0 * m + i] = v[0];        // t0
+    o[1 * m + i] = v[1];        // period
+    o[2 * m + i] = v[2];        // a_rs
+    o[3 * m + i] = v[3];        // b
+    o[4 * m + i] = 0.0;         // ecc
+    o[5 * m + i] = 0.5 * gl::kPi;   // omega
+    o[6 * m + i] = v[4];        // k
+    o[7 * m + i] = f;
+    o[8 * m + i] = eta;
+    o[9 * m + i] = v[7];        // xi
+    o[10 * m + i] = 2.0 * sq * v[9];
+    o[11 * m + i] = sq * (1.0 - 2.0 * v[9]);
+    logprior[i] = lp;
+  }
+}
+
+// Stretch-move proposals of one half (walkers k = 2 i + h) along lines through
+// members of the other half: partner = 2 floor(r_j m) + (1 - h), z = ((a - 1) r_z + 1)^2 / a.
+__global__ void gl_ens_propose_kernel(const double* __restrict__ walkers, int64_t m, int h,
+                                      const double* __restrict__ rz, const double* __restrict__ rj,
+                                      double a, double* __restrict__ prop, double* __restrict__ z) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = 2 * i + h;
+    int64_t pj = (int64_t)(rj[i] * (double)m);
+    if (pj >= m) pj = m - 1;
+    if (pj < 0) pj = 0;
+    const int64_t j = 2 * pj + (1 - h);
+    const double zz = ((a - 1.0) * rz[i] + 1.0) * ((a - 1.0) * rz[i] + 1.0) / a;
+    z[i] = zz;
+    for (int d = 0; d < GL_FIT_DIM; ++d) {
+      const double xj = walkers[j * GL_FIT_DIM + d];
+      prop[i * GL_FIT_DIM + d] = xj + zz * (walkers[k * GL_FIT_DIM + d] - xj);
+    }
+  }
+}
+
+__global__ void gl_fill_kernel(double* __restrict__ x, int64_t n, double v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+// log posterior = log prior + log likelihood (-inf outside the prior).
+__global__ void gl_ens_post_kernel(int64_t m, const double* __restrict__ logprior,
+                                   const double* __restrict__ ll, double* __restrict__ logpost) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    logpost[i] = isfinite(logprior[i]) ? logprior[i] + ll[i] : -INFINITY;
+}
+
+// Accept or reject the half's proposals: log(r_u) < (D - 1) log z + lp(Y) - lp(X).
+__global__ void gl_ens_accept_kernel(double* __restrict__ walkers, double* __restrict__ logpost,
+                                     int64_t m, int h, const double* __restrict__ prop,
+                                     const double* __restrict__ z,
+                                     const double* __restrict__ lp_new,
+                                     const double* __restrict__ ru,
+                                     unsigned long long* __restrict__ accepted) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = 2 * i + h;
+    const double log_r = (GL_FIT_DIM - 1) * log(z[i]) + lp_new[i] - logpost[k];
+    if (log(ru[i]) < log_r) {
+      for (int d = 0; d < GL_FIT_DIM; ++d) walkers[k * GL_FIT_DIM + d] = prop[i * GL_FIT_DIM + d];
+      logpost[k] = lp_new[i];
+      if (accepted) atomicAdd(accepted, 1ull);
+    }
+  }
+}
+
 struct SkyPtrs {
   const double *x0, *y0, *z, *k, *f, *eta, *xi, *u1, *u2;
 };
@@ -1410,6 +1567,11 @@ struct gl_context {
   void* d_items = nullptr;
   size_t items_bytes = 0;
   unsigned long long* d_ictr = nullptr;    // kIcSlots counters, zeroed by every step
+  // ensemble workspace: parameter sets (12 x n), log prior, log likelihood, light
+  // curves (n x n_times), proposals (n/2 x GL_FIT_DIM), z, proposal log posterior,
+  // exposure times
+  double* d_ens = nullptr;
+  size_t ens_cap = 0;
   int qocc[2] = {0, 0};                    // resident quadrature CTAs per SM (FP64, FP32C)
   int eocc[2] = {0, 0};                    // resident kept-exposure CTAs per SM
   // graph cache: one captured step per distinct argument set
@@ -1814,6 +1976,7 @@ int gl_context_destroy(gl_context* ctx) {
   if (ctx->d_counts) cudaFree(ctx->d_counts);
   if (ctx->d_ref) cudaFree(ctx->d_ref);
   if (ctx->d_items) cudaFree(ctx->d_items);
+  if (ctx->d_ens) cudaFree(ctx->d_ens);
   if (ctx->d_ictr) cudaFree(ctx->d_ictr);
   for (void* q : {(void*)ctx->sx, (void*)ctx->sy, (void*)ctx->so, (void*)ctx->sfeat,
                   (void*)ctx->sscale, (void*)ctx->sdsph, (void*)ctx->sthat, (void*)ctx->sdef,
@@ -2255,6 +2418,134 @@ int gl_loglike(gl_context* ctx, int64_t n_sets, int64_t n_times, const double* f
                                                                         sigma, loglike);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+static int munu_op(gl_context* ctx, int op, int64_t n, const double* a, const double* b, double* c,
+                   double* d, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (n < 0) return fail(ctx, GL_EINVAL, "n < 0");
+  if (n == 0) return GL_OK;
+  const void* ptrs[4] = {a, b, c, d};
+  for (const void* q : ptrs)
+    if (!q || !is_device_ptr(q, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host array");
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  gl_munu_kernel<<<launch_grid(n, 256), 256, 0, (cudaStream_t)stream>>>(op, n, a, b, c, d);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+int gl_munu_to_feta(gl_context* ctx, int64_t n, const double* mu, const double* nu, double* f,
+                    double* eta, void* stream) {
+  return munu_op(ctx, kMunuToFeta, n, mu, nu, f, eta, stream);
+}
+
+int gl_feta_to_munu(gl_context* ctx, int64_t n, const double* f, const double* eta, double* mu,
+                    double* nu, void* stream) {
+  return munu_op(ctx, kFetaToMunu, n, f, eta, mu, nu, stream);
+}
+
+int gl_munu_prior(gl_context* ctx, int64_t n, const double* u, const double* w, double* mu,
+                  double* nu, void* stream) {
+  return munu_op(ctx, kMunuPrior, n, u, w, mu, nu, stream);
+}
+
+// Log posteriors of m fit vectors into lp (workspace layout of ensure_ensemble).
+static int ens_logpost(gl_context* ctx, const gl_ensemble* e, const double* x, int64_t m,
+                       double* lp, cudaStream_t st) {
+  double* soa = ctx->d_ens;
+  double* prior = soa + 12 * e->n_walkers;
+  double* ll = prior + e->n_walkers;
+  double* flux = ll + e->n_walkers;
+  double* exptime = flux + e->n_walkers * e->n_times + (e->n_walkers / 2) * (GL_FIT_DIM + 2);
+  const int g = launch_grid(m, 256);
+  gl_ens_params_kernel<<<g, 256, 0, st>>>(x, m, e->lo, e->hi, soa, prior);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  gl_params p;
+  memset(&p, 0, sizeof p);
+  p.n_sets = m;
+  const double** f[12] = {&p.t0, &p.period, &p.a_rs, &p.b, &p.ecc, &p.omega,
+                          &p.k,  &p.f,      &p.eta,  &p.xi, &p.u1, &p.u2};
+  for (int q = 0; q < 12; ++q) *f[q] = soa + q * m;
+  gl_times tm;
+  memset(&tm, 0, sizeof tm);
+  tm.t = e->t;
+  tm.n_times = e->n_times;
+  tm.n_total = m * e->n_times;
+  tm.exptime = exptime;
+  tm.nsuper_all = e->nsuper;
+  int rc = gl_lightcurve_batch(ctx, &p, &tm, flux, e->prec, st);
+  if (rc) return rc;
+  gl_loglike_kernel<<<(unsigned)m, 256, 0, st>>>(m, e->n_times, flux, e->data, e->sigma, ll);
+  gl_ens_post_kernel<<<g, 256, 0, st>>>(m, prior, ll, lp);
+  ctx->launches += 2;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+static int ensure_ensemble(gl_context* ctx, const gl_ensemble* e, cudaStream_t st) {
+  if (!e || e->n_walkers < 4 || (e->n_walkers & 1) || e->n_walkers > (1LL << 26))
+    return fail(ctx, GL_EINVAL, "n_walkers must be even, in [4, 2^26]");
+  if (e->n_times < 1 || e->nsuper < 1 || !(e->exptime >= 0.0) || !(e->a > 1.0))
+    return fail(ctx, GL_EINVAL, "bad n_times, nsuper, exptime or stretch scale");
+  if (e->prec != GL_FP64 && e->prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision");
+  const void* ptrs[7] = {e->walkers, e->logpost, e->lo, e->hi, e->t, e->data, e->sigma};
+  for (const void* q : ptrs)
+    if (!q || !is_device_ptr(q, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host array");
+  const int64_t n = e->n_walkers, h = n / 2;
+  const size_t need = ((size_t)12 * n + 2 * n + (size_t)n * e->n_times +
+                       (size_t)h * (GL_FIT_DIM + 2) + n) * sizeof(double);
+  int rc = grow(ctx, (void**)&ctx->d_ens, &ctx->ens_cap, need);
+  if (rc) return rc;
+  // exposure times (one value for every walker), stream-ordered
+  double* exptime = ctx->d_ens + 12 * n + 2 * n + n * e->n_times + h * (GL_FIT_DIM + 2);
+  gl_fill_kernel<<<launch_grid(n, 256), 256, 0, st>>>(exptime, n, e->exptime);
+  ctx->launches++;
+  GL_CUDA(ctx, cudaGetLastError());
+  return GL_OK;
+}
+
+int gl_ensemble_init(gl_context* ctx, const gl_ensemble* e, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_ensemble(ctx, e, st);
+  if (rc) return rc;
+  return ens_logpost(ctx, e, e->walkers, e->n_walkers, e->logpost, st);
+}
+
+int gl_ensemble_sweep(gl_context* ctx, const gl_ensemble* e, const double* rnd,
+                      unsigned long long* accepted, void* stream) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  GL_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = ensure_ensemble(ctx, e, st);
+  if (rc) return rc;
+  if (!rnd || !is_device_ptr(rnd, ctx->device)) return fail(ctx, GL_EINVAL, "NULL or host rnd");
+  if (accepted && !is_device_ptr(accepted, ctx->device))
+    return fail(ctx, GL_EINVAL, "host accepted counter");
+  const int64_t n = e->n_walkers, m = n / 2;
+  double* prop = ctx->d_ens + 12 * n + 2 * n + n * e->n_times;
+  double* z = prop + m * GL_FIT_DIM;
+  double* lp_new = z + m;
+  const int g = launch_grid(m, 256);
+  for (int h = 0; h < 2; ++h) {
+    const double* r = rnd + (size_t)h * 3 * m;   // per half: r_z, r_j, r_u (m each)
+    gl_ens_propose_kernel<<<g, 256, 0, st>>>(e->walkers, m, h, r, r + m, e->a, prop, z);
+    ctx->launches++;
+    GL_CUDA(ctx, cudaGetLastError());
+    rc = ens_logpost(ctx, e, prop, m, lp_new, st);
+    if (rc) return rc;
+    gl_ens_accept_kernel<<<g, 256, 0, st>>>(e->walkers, e->logpost, m, h, prop, z, lp_new,
+                                            r + 2 * m, accepted);
+    ctx->launches++;
+    GL_CUDA(ctx, cudaGetLastError());
+  }
   return GL_OK;
 }
 
