@@ -91,10 +91,12 @@ struct ParamPtrs {
 //            fields of the set's constants; warp 0 then sets the flags
 __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_sets,
                                                        const int64_t* offsets, int64_t n_total,
-                                                       SetConst* sets, int* status) {
+                                                       SetConst* sets, int* status,
+                                                       unsigned long long* zero, int n_zero) {
   __shared__ double sh_s[4][32], sh_c[4][32], sh_cb[32];
   __shared__ int sh_win[32];
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+  if (zero && blockIdx.x == 0 && (int)threadIdx.x < n_zero) zero[threadIdx.x] = 0ull;
   const int64_t s = (int64_t)blockIdx.x * 32 + lane;
   const bool live = s < n_sets;
   if (role < 3) {
@@ -1757,7 +1759,7 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
                                                                kExpThreads, 0));
     if (qocc < 1 || eocc < 1) return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
   }
-  GL_CUDA(ctx, cudaMemsetAsync(ctx->d_ictr, 0, kIcSlots * sizeof(unsigned long long), st));
+  // (the counters were zeroed by the setup kernel of this step)
   int64_t wb = (args.n_total + 1023) / 1024;   // at least 4 passes of 256 per block
   if (wb > (int64_t)ctx->sms * 8) wb = (int64_t)ctx->sms * 8;
   if (wb < 1) wb = 1;
@@ -1842,8 +1844,12 @@ struct StepArgs {
 
 int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
   long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
-  gl_setup_kernel<<<(int)((sa.n_sets + 31) / 32), 128, 0, st>>>(sa.pp, sa.n_sets, sa.offsets,
-                                                              sa.n_total, sa.sets, ctx->d_status);
+  // the item pipeline's counters are zeroed here (one graph node less than a
+  // separate memset)
+  const bool pipeline = sa.items && !sa.locked && !ctx->counting;
+  gl_setup_kernel<<<(int)((sa.n_sets + 31) / 32), 128, 0, st>>>(
+      sa.pp, sa.n_sets, sa.offsets, sa.n_total, sa.sets, ctx->d_status,
+      pipeline ? ctx->d_ictr : nullptr, pipeline ? (int)kIcSlots : 0);
   prof_end(ctx, GL_KERNEL_SETUP, pe, st);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
@@ -2622,7 +2628,7 @@ int gl_lightcurve_surrogate(gl_context* ctx, gl_mlp* mlp, const gl_params* p, co
   pp.exptime = tm->exptime;
   pp.nsuper_all = tm->nsuper_all;
   gl_setup_kernel<<<(int)((n_sets + 31) / 32), 128, 0, st>>>(pp, n_sets, tm->offsets, n_total,
-                                                          ctx->d_sets, ctx->d_status);
+                                                          ctx->d_sets, ctx->d_status, nullptr, 0);
   CollectArgs ca;
   memset(&ca, 0, sizeof ca);
   ca.sets = ctx->d_sets;
@@ -2851,7 +2857,7 @@ extern "C" int gl_lightcurve_batch_noalloc(const gl_params* p, const gl_times* t
                   p->eta, p->xi, p->u1, p->u2, p->g, p->zeta, tm->exptime, tm->nsuper,
                   tm->nsuper_all};
   gl_setup_kernel<<<(int)((n_sets + 31) / 32), 128, 0, st>>>(pp, n_sets, tm->offsets,
-                                                          tm->n_total, sets, status);
+                                                          tm->n_total, sets, status, nullptr, 0);
   int grid = launch_grid(tm->n_total, 256);
   if (prec == GL_FP64)
     gl_curve_kernel<double><<<grid, 256, 0, st>>>(sets, tm->t, tm->offsets, tm->n_times, n_sets,
