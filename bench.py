@@ -770,6 +770,8 @@ def main():
     # autotuner: kernel shape and FP32 quadrature order for this batch (untimed)
     tune = ctx.autotune(dp, d_t, out32, d_exp, nsuper=d_ns, offsets=d_off,
                         precision=binding.GL_FP32C, stream=stream)
+    tune64 = ctx.autotune(dp, d_t, out64, d_exp, nsuper=d_ns, offsets=d_off,
+                          precision=binding.GL_FP64, stream=stream)
     step(out32, binding.GL_FP32C)
     torch.cuda.synchronize(dev)
     max_dflux = float((out32 - out64).abs().max().item())
@@ -839,6 +841,7 @@ def main():
         "kernel_ms": {"fp32c": kern32, "fp64": kern64},
         "workload_counts": counts,
         "autotune": tune,
+        "autotune_fp64": tune64,
         "roofline": roofline(counts, kern32, fp32_peak, fp64_peak),
         "gpu_launches": launches,
         "status": status,

@@ -269,17 +269,23 @@ typedef struct {
   double max_abs_err;  /* max |flux - FP64 path| of the chosen configuration */
   int candidates;      /* configurations tried */
   int admissible;      /* configurations within 0.9 x tolerance of the FP64 path */
+  int quad_ctas_per_sm; /* item pipeline: resident CTAs per SM of the chosen quadrature
+                           kernel (4: all registers, 8: 64 registers), else 0 */
 } gl_tune_report;
 
 /* Autotuner of the light-curve kernel for the batch (p, t) at precision prec.
- * Candidates: 128 or 256 threads per CTA (tile = threads, 4 x threads items per
- * round) and, for GL_FP32C, 16, 20, 24 or 28 Gauss-Legendre nodes per arc.  Each
+ * Candidates: 128 or 256 threads per CTA of the tile kernel (tile = threads,
+ * 4 x threads items per round) -- or, with the item pipeline on, the two
+ * quadrature kernels (all registers, 4 CTAs per SM; or 64 registers, 8 CTAs per
+ * SM) -- and, for GL_FP32C, 16, 20, 24 or 28 Gauss-Legendre nodes per arc.  Each
  * candidate runs on the batch; only those whose max |flux - FP64 path| stays
  * within 0.9 x the precision's tolerance (1e-7 FP32C, 1e-10 FP64) are timed (CUDA
- * events, best of 3) and the fastest is kept by the context for later calls at
+ * events, best of 5, each from a cold L2; as CUDA-graph replays when graphs are on,
+ * the way later calls run) and the fastest is kept by the context for later calls at
  * that precision.  `out` (device memory, n_total doubles) receives the chosen
  * configuration's last result; the context holds one FP64 reference of n_total
- * doubles.  Synchronises `stream`; must not be called during stream capture.
+ * doubles, and tuning briefly allocates a buffer of twice the L2 size.
+ * Synchronises `stream`; must not be called during stream capture.
  * `rep` may be NULL.  GL_EINVAL for host buffers or an empty batch, GL_ENUMERIC
  * if no candidate meets the tolerance (the previous configuration stays). */
 int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *out,

@@ -77,7 +77,7 @@ class _TuneReport(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("tile", ctypes.c_int), ("nodes", ctypes.c_int),
                 ("ms", ctypes.c_double), ("default_ms", ctypes.c_double),
                 ("max_abs_err", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("admissible", ctypes.c_int)]
+                ("admissible", ctypes.c_int), ("quad_ctas_per_sm", ctypes.c_int)]
 
 
 GL_FIT_DIM = 10

@@ -42,7 +42,7 @@ constexpr int kNodes32 = 20;
 // count, set, flags, tau, midpoint state); plus three ints per exposure for
 // the kept-exposure list and the overflow list
 constexpr int64_t kItemMaxDefault = 1LL << 23;
-constexpr size_t kItemBytes = 5 * sizeof(double) + 8 * sizeof(int) + sizeof(gl::MidState);
+constexpr size_t kItemBytes = 5 * sizeof(double) + 9 * sizeof(int) + sizeof(gl::MidState);
 
 __constant__ NodeRule<double> c_rule64;
 __constant__ NodeRule<double> c_rule64_wide;
@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
   __shared__ double sh_s[4][32], sh_c[4][32], sh_cb[32];
   __shared__ int sh_win[32];
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
-  if (zero && blockIdx.x == 0 && (int)threadIdx.x < n_zero) zero[threadIdx.x] = 0ull;
+  if (zero)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_zero; i += gridDim.x * blockDim.x)
+      zero[i] = 0ull;
   const int64_t s = (int64_t)blockIdx.x * 32 + lane;
   const bool live = s < n_sets;
   if (role < 3) {
@@ -273,10 +275,12 @@ struct LcArgs {
   void* idef;                   // R[item_cap]: deficit (c0 I0 + c1 I1 + c2 I2) / F0 of each item
   int* iset;                    // parameter set of each item
   int* iq;                      // whole-ellipse items from the front, crossing items from the back
+  int* ihq;                     // whole-ellipse items whose boundary may have two inner maxima
   int *rj, *rfirst, *rns;       // exposure records: output index, first item, sub-exposures
   int* klist;                   // kept exposures (output index); n_total entries
   int* kset;                    // their parameter sets; n_total entries
-  unsigned long long* ictr;     // kIc* counters
+  unsigned long long* ictr;     // kIc* counters, then kSmspSlots 32-bit crossing-batch counters
+  int n_smsp;                   // SM sub-partitions of the device (4 per SM)
   int64_t item_cap;
   int* ovlist;                  // kept-list indices of exposures left to the sum kernel
   // per record: set, flags, tau, midpoint state; per item: record
@@ -287,7 +291,10 @@ struct LcArgs {
 
 enum : int {
   kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcOver = 6,
-  kIcValid = 7, kIcSlots = 8
+  kIcValid = 7, kIcFetchP = 8, kIcHeavy = 9, kIcFetchH = 10, kIcSlots = 11,
+  // per-sub-partition counters of crossing batches (32-bit, after the kIc slots)
+  kSmspSlots = 1024,
+  kIcWords = kIcSlots + kSmspSlots / 2   // 64-bit words zeroed by every step
 };
 
 // Index of the batch's FP32 quadrature order in c_rule32_tuned (-1 = default).
@@ -720,8 +727,8 @@ __global__ void __launch_bounds__(kExpThreads) gl_exp_kernel(LcArgs a) {
 // add per block and class), the others get a zero deficit.
 template <typename R>
 __global__ void __launch_bounds__(kGeoThreads) gl_geo_kernel(LcArgs a) {
-  __shared__ int s_nf, s_np;
-  __shared__ long long s_qf, s_qp;
+  __shared__ int s_nf, s_np, s_nh;
+  __shared__ long long s_qf, s_qp, s_qh;
   const int tid = threadIdx.x;
   const long long n = (long long)a.ictr[kIcValid];
   R* ipos = (R*)a.ipos;
@@ -732,9 +739,11 @@ __global__ void __launch_bounds__(kGeoThreads) gl_geo_kernel(LcArgs a) {
     if (tid == 0) {
       s_nf = 0;
       s_np = 0;
+      s_nh = 0;
     }
     __syncthreads();
     int cls = gl::kOut, slot = 0;
+    bool heavy = false;
     if (g < n) {
       const int r = a.irec[g];
       const int st = a.rset[r], ns = a.rns[r], q = (int)(g - a.rfirst[r]);
@@ -748,16 +757,19 @@ __global__ void __launch_bounds__(kGeoThreads) gl_geo_kernel(LcArgs a) {
         ipos[3 * g + 1] = y;
         ipos[3 * g + 2] = o;
         a.iset[g] = st;
-        slot = atomicAdd(cls == gl::kFull ? &s_nf : &s_np, 1);
+        heavy = cls == gl::kFull && gl::maybe_two_maxima(a.sets[st], (float)x, (float)y);
+        slot = atomicAdd(heavy ? &s_nh : cls == gl::kFull ? &s_nf : &s_np, 1);
       }
     }
     __syncthreads();
     if (tid == 0) {
       s_qf = s_nf ? (long long)atomicAdd(&a.ictr[kIcFull], (unsigned long long)s_nf) : 0;
       s_qp = s_np ? (long long)atomicAdd(&a.ictr[kIcPart], (unsigned long long)s_np) : 0;
+      s_qh = s_nh ? (long long)atomicAdd(&a.ictr[kIcHeavy], (unsigned long long)s_nh) : 0;
     }
     __syncthreads();
-    if (cls == gl::kFull) a.iq[s_qf + slot] = (int)g;
+    if (heavy) a.ihq[s_qh + slot] = (int)g;
+    else if (cls == gl::kFull) a.iq[s_qf + slot] = (int)g;
     else if (cls == gl::kPartial) a.iq[a.item_cap - 1 - (s_qp + slot)] = (int)g;
   }
 }
@@ -766,27 +778,79 @@ __global__ void __launch_bounds__(kGeoThreads) gl_geo_kernel(LcArgs a) {
 // whole GPU.  Each warp takes 32 consecutive queue positions at a time: crossing
 // items (the heavier ones) first, then whole-ellipse items, so a warp's lanes
 // mostly follow the same path and the last warps to finish have light work.
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) gl_items_quad_kernel(LcArgs a) {
+// SM index and warp slot of the calling warp (scheduling hints only: both may
+// change under preemption, and nothing depends on them for correctness).
+__device__ __forceinline__ unsigned smid_() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+  return v;
+}
+__device__ __forceinline__ unsigned warpid_() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%warpid;" : "=r"(v));
+  return v;
+}
+
+// MINB = 1 leaves the compiler its registers (4 resident CTAs per SM: the
+// shortest warps, for batches with few items per sub-partition); MINB = 8 caps
+// them at 64 (8 CTAs per SM: more warps to hide latency, for large batches).
+// The autotuner chooses between the two.
+template <typename R, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
   const int rb = rule_base(a.rule_idx);
   const long long np = (long long)a.ictr[kIcPart], nf = (long long)a.ictr[kIcFull];
-  const long long total = np + nf;
+  const long long nh = (long long)a.ictr[kIcHeavy];
   const R* ipos = (const R*)a.ipos;
   R* idef = (R*)a.idef;
   const int lane = threadIdx.x & 31;
+  auto run_item = [&](long long g, int cls) {
+    const SetConst& c = a.sets[a.iset[g]];
+    idef[g] = item_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2], cls, rb);
+  };
+  auto run = [&](long long u, bool part) {
+    run_item(part ? a.iq[a.item_cap - 1 - u] : a.iq[u], part ? gl::kPartial : gl::kFull);
+  };
+  // Pass 1, crossing items: a warp of them issues ~200 FP64 instructions and each
+  // holds its sub-partition's FP64 unit ~64 cycles whatever the active lanes, so
+  // their batches are spread evenly: at most `cap` per sub-partition, counted
+  // per (SM, warp slot mod 4).  The counters only steer the spread; every batch
+  // is still taken exactly once through the kIcFetchP counter.
+  const long long pb = (np + 31) / 32;
+  const unsigned cap = (unsigned)((pb + a.n_smsp - 1) / a.n_smsp);
+  unsigned* smsp_ctr = (unsigned*)(a.ictr + kIcSlots);
+  const unsigned key = (smid_() * 4u + (warpid_() & 3u)) & (kSmspSlots - 1);
+  for (;;) {
+    unsigned long long b = (unsigned long long)np;
+    if (lane == 0 && atomicAdd(&smsp_ctr[key], 1u) < cap) b = atomicAdd(&a.ictr[kIcFetchP], 32ull);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if ((long long)b >= np) break;
+    if ((long long)b + lane < np) run((long long)b + lane, true);
+  }
+  // Pass 2, whole-ellipse items that may have two inner maxima (their f_lin
+  // takes two mapped arcs instead of one table rule: ~3x the work), then the
+  // others, taken as they come, so that no heavy batch starts late.
+  for (;;) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(&a.ictr[kIcFetchH], 32ull);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if ((long long)b >= nh) break;
+    if ((long long)b + lane < nh) run_item(a.ihq[b + lane], gl::kFull);
+  }
   for (;;) {
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(&a.ictr[kIcFetch], 32ull);
     b = __shfl_sync(0xffffffffu, b, 0);
-    if ((long long)b >= total) break;
-    const long long u = (long long)b + lane;
-    if (u < total) {
-      const bool part = u < np;
-      const long long g = part ? a.iq[a.item_cap - 1 - u] : a.iq[u - np];
-      const SetConst& c = a.sets[a.iset[g]];
-      idef[g] = item_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2],
-                                part ? gl::kPartial : gl::kFull, rb);
-    }
+    if ((long long)b >= nf) break;
+    if ((long long)b + lane < nf) run((long long)b + lane, false);
+  }
+  // Pass 3, crossing batches that pass 1 left (none unless warps met fewer
+  // sub-partitions than the device has).
+  for (;;) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(&a.ictr[kIcFetchP], 32ull);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if ((long long)b >= np) break;
+    if ((long long)b + lane < np) run((long long)b + lane, true);
   }
 }
 
@@ -1546,7 +1610,8 @@ struct gl_context {
   int occ[16] = {0};                   // resident CTAs per SM by (precision, counting, threads)
   struct LcCfg {
     int threads, tile, cap, rule_idx;
-  } cfg[2] = {{256, 256, 1024, -1}, {256, 256, 1024, -1}};   // FP64, FP32C
+    int qvar;   // item pipeline: quadrature kernel variant (0: MINB = 1, 1: MINB = 8)
+  } cfg[2] = {{256, 256, 1024, -1, 0}, {256, 256, 1024, -1, 0}};   // FP64, FP32C
   struct TuneInfo {
     int tuned = 0, candidates = 0, admissible = 0;
     double best_ms = 0, default_ms = 0, max_err = 0;
@@ -1568,13 +1633,13 @@ struct gl_context {
   int64_t item_max = kItemMaxDefault;   // most items one call may queue
   void* d_items = nullptr;
   size_t items_bytes = 0;
-  unsigned long long* d_ictr = nullptr;    // kIcSlots counters, zeroed by every step
+  unsigned long long* d_ictr = nullptr;    // kIcWords counter words, zeroed by every step
   // ensemble workspace: parameter sets (12 x n), log prior, log likelihood, light
   // curves (n x n_times), proposals (n/2 x GL_FIT_DIM), z, proposal log posterior,
   // exposure times
   double* d_ens = nullptr;
   size_t ens_cap = 0;
-  int qocc[2] = {0, 0};                    // resident quadrature CTAs per SM (FP64, FP32C)
+  int qocc[2][2] = {{0, 0}, {0, 0}};       // resident quadrature CTAs per SM (FP64, FP32C) x variant
   int eocc[2] = {0, 0};                    // resident kept-exposure CTAs per SM
   // graph cache: one captured step per distinct argument set
   bool graphs = true;
@@ -1729,6 +1794,7 @@ void item_arrays(void* base, int64_t cap, int64_t n_total, size_t rsize, LcArgs*
   a->idef = take(rsize * (size_t)cap);
   a->iset = (int*)take(sizeof(int) * (size_t)cap);
   a->iq = (int*)take(sizeof(int) * (size_t)cap);
+  a->ihq = (int*)take(sizeof(int) * (size_t)cap);
   a->rj = (int*)take(sizeof(int) * (size_t)cap);
   a->rfirst = (int*)take(sizeof(int) * (size_t)cap);
   a->rns = (int*)take(sizeof(int) * (size_t)cap);
@@ -1744,17 +1810,19 @@ void item_arrays(void* base, int64_t cap, int64_t n_total, size_t rsize, LcArgs*
 }
 
 size_t item_workspace_bytes(int64_t cap, int64_t n_total) {
-  return (size_t)cap * kItemBytes + (size_t)n_total * 3 * sizeof(int) + 18 * 256;
+  return (size_t)cap * kItemBytes + (size_t)n_total * 3 * sizeof(int) + 20 * 256;
 }
 
 // The item pipeline: window tests, kept exposures, quadrature, exposure sums.
 template <typename R>
 int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
-  int& qocc = ctx->qocc[sizeof(R) == 4 ? 1 : 0];
+  const int qvar = ctx->cfg[sizeof(R) == 4 ? 1 : 0].qvar;
+  int& qocc = ctx->qocc[sizeof(R) == 4 ? 1 : 0][qvar];
   int& eocc = ctx->eocc[sizeof(R) == 4 ? 1 : 0];
   if (qocc == 0) {
-    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qocc, gl_items_quad_kernel<R, 128>,
-                                                               128, 0));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &qocc, qvar ? gl_items_quad_kernel<R, 128, 8> : gl_items_quad_kernel<R, 128, 1>,
+                     128, 0));
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&eocc, gl_exp_kernel<R>,
                                                                kExpThreads, 0));
     if (qocc < 1 || eocc < 1) return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
@@ -1771,7 +1839,10 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   ctx->launches += 3;
   GL_CUDA(ctx, cudaGetLastError());
   pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
-  gl_items_quad_kernel<R, 128><<<ctx->sms * qocc, 128, 0, st>>>(args);
+  if (qvar)
+    gl_items_quad_kernel<R, 128, 8><<<ctx->sms * qocc, 128, 0, st>>>(args);
+  else
+    gl_items_quad_kernel<R, 128, 1><<<ctx->sms * qocc, 128, 0, st>>>(args);
   gl_items_sum_kernel<R><<<ctx->sms * 2, 256, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_QUAD, pe, st);
   ctx->launches += 2;
@@ -1804,7 +1875,10 @@ int launch_lc_nt(gl_context* ctx, LcArgs args, int occ_slot, cudaStream_t st) {
 
 // occupancy is cached per (precision, counting, threads) instance
 bool lc_ready(const gl_context* ctx, int prec, bool items) {
-  if (items) return ctx->qocc[prec == GL_FP64 ? 0 : 1] != 0;
+  if (items) {
+    const int pi = prec == GL_FP64 ? 0 : 1;
+    return ctx->qocc[pi][ctx->cfg[pi].qvar] != 0;
+  }
   const gl_context::LcCfg& cf = ctx->cfg[prec == GL_FP64 ? 0 : 1];
   int slot = (prec == GL_FP64 ? 0 : 1) + (ctx->counting ? 2 : 0) + (cf.threads == 128 ? 4 : 0);
   return ctx->occ[slot] != 0;
@@ -1849,7 +1923,7 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
   const bool pipeline = sa.items && !sa.locked && !ctx->counting;
   gl_setup_kernel<<<(int)((sa.n_sets + 31) / 32), 128, 0, st>>>(
       sa.pp, sa.n_sets, sa.offsets, sa.n_total, sa.sets, ctx->d_status,
-      pipeline ? ctx->d_ictr : nullptr, pipeline ? (int)kIcSlots : 0);
+      pipeline ? ctx->d_ictr : nullptr, pipeline ? (int)kIcWords : 0);
   prof_end(ctx, GL_KERNEL_SETUP, pe, st);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
@@ -1881,6 +1955,7 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     item_arrays(sa.items, sa.item_cap, sa.n_total, sa.prec == GL_FP64 ? sizeof(double) : sizeof(float),
                 &la);
     la.ictr = ctx->d_ictr;
+    la.n_smsp = 4 * ctx->sms;
   }
   if (sa.prec == GL_FP64)
     return ctx->counting ? launch_lc<double, true>(ctx, la, st) : launch_lc<double, false>(ctx, la, st);
@@ -2052,6 +2127,8 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
   bool was_prof = ctx->profiling, was_count = ctx->counting, was_graph = ctx->graphs;
   ctx->profiling = false;
   ctx->counting = false;
+  // candidates are timed the way later calls run: as CUDA-graph replays when
+  // graphs are on (each candidate captures its own graph)
   ctx->graphs = false;
   drop_graphs(ctx);
   int rc = grow(ctx, (void**)&ctx->d_ref, &ctx->ref_cap, (size_t)tm->n_total * sizeof(double));
@@ -2059,29 +2136,46 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
   if (!ctx->d_err) GL_CUDA(ctx, cudaMalloc(&ctx->d_err, sizeof(unsigned long long)));
   // reference: the FP64 path with its default configuration
   gl_context::LcCfg saved[2] = {ctx->cfg[0], ctx->cfg[1]};
-  ctx->cfg[0] = {256, 256, 1024, -1};
+  ctx->cfg[0] = {256, 256, 1024, -1, 0};
   rc = gl_lightcurve_batch(ctx, p, tm, ctx->d_ref, GL_FP64, stream);
   if (rc) return rc;
   const int pi = prec == GL_FP64 ? 0 : 1;
   const double tol = prec == GL_FP64 ? 1e-10 : 1e-7;
-  struct Cand { int threads, nodes_idx; };
+  // The second axis is the tile kernel's CTA size, or with the item pipeline
+  // (whose launch shapes are fixed) the quadrature kernel's variant.
+  struct Cand { int threads, nodes_idx, qvar; };
   Cand cands[8];
   int nc = 0;
-  for (int th : {128, 256}) {
+  for (int ax = 0; ax < 2; ++ax) {
+    const int th = ctx->item_pipeline ? 256 : (ax ? 256 : 128);
+    const int qv = ctx->item_pipeline ? ax : 0;
     if (prec == GL_FP64) {
-      cands[nc++] = {th, -1};
+      cands[nc++] = {th, -1, qv};
     } else {
-      for (int ni = 0; ni < 4; ++ni) cands[nc++] = {th, ni};
+      for (int ni = 0; ni < 4; ++ni) cands[nc++] = {th, ni, qv};
     }
   }
   cudaEvent_t e0, e1;
   GL_CUDA(ctx, cudaEventCreate(&e0));
   GL_CUDA(ctx, cudaEventCreate(&e1));
+  // Each timed run starts from a cold L2 (a buffer twice its size is written
+  // first, outside the events): the conservative case, and the way benchmarks
+  // time a step.  Without room for the buffer the runs are timed warm.
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device);
+  const size_t flush_bytes = 2 * (size_t)(l2 > 0 ? l2 : 0);
+  void* flush = nullptr;
+  if (flush_bytes && cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
   double best_ms = 1e30, default_ms = 0.0, best_err = 0.0;
   int best = -1, admissible = 0;
   for (int ci = 0; ci < nc && rc == GL_OK; ++ci) {
     ctx->cfg[pi] = {cands[ci].threads, cands[ci].threads, 4 * cands[ci].threads,
-                    cands[ci].nodes_idx};
+                    cands[ci].nodes_idx, cands[ci].qvar};
+    drop_graphs(ctx);
+    ctx->graphs = was_graph;
     rc = gl_lightcurve_batch(ctx, p, tm, out, prec, stream);
     if (rc) break;
     cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned long long), st);
@@ -2099,7 +2193,8 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
     float ms = 1e30f;
     if (ok) {
       ++admissible;
-      for (int rep_i = 0; rep_i < 3; ++rep_i) {
+      for (int rep_i = 0; rep_i < 5; ++rep_i) {
+        if (flush) cudaMemsetAsync(flush, rep_i & 0xff, flush_bytes, st);
         cudaEventRecord(e0, st);
         rc = gl_lightcurve_batch(ctx, p, tm, out, prec, stream);
         cudaEventRecord(e1, st);
@@ -2114,16 +2209,23 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
         best_err = err;
       }
     }
-    if (cands[ci].threads == 256 && (cands[ci].nodes_idx == 1 || cands[ci].nodes_idx == -1))
+    if (cands[ci].threads == 256 && cands[ci].qvar == 0 &&
+        (cands[ci].nodes_idx == 1 || cands[ci].nodes_idx == -1))
       default_ms = ok ? ms : 0.0;
+    ctx->graphs = false;
+    drop_graphs(ctx);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (flush) {
+    cudaStreamSynchronize(st);
+    cudaFree(flush);
+  }
   ctx->cfg[0] = saved[0];
   ctx->cfg[1] = saved[1];
   if (best >= 0)
     ctx->cfg[pi] = {cands[best].threads, cands[best].threads, 4 * cands[best].threads,
-                    cands[best].nodes_idx};
+                    cands[best].nodes_idx, cands[best].qvar};
   ctx->profiling = was_prof;
   ctx->counting = was_count;
   ctx->graphs = was_graph;
@@ -2146,6 +2248,8 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
     rep->max_abs_err = best_err;
     rep->candidates = nc;
     rep->admissible = admissible;
+    rep->quad_ctas_per_sm =
+        ctx->item_pipeline ? ctx->qocc[pi][cands[best].qvar] : 0;
   }
   return GL_OK;
 }
@@ -2283,7 +2387,7 @@ int lightcurve_impl(gl_context* ctx, const gl_params* p, const gl_times* tm, dou
     rc = grow(ctx, &ctx->d_items, &ctx->items_bytes, item_workspace_bytes(item_cap, tm->n_total));
     if (rc) return rc;
     if (!ctx->d_ictr)
-      GL_CUDA(ctx, cudaMalloc(&ctx->d_ictr, kIcSlots * sizeof(unsigned long long)));
+      GL_CUDA(ctx, cudaMalloc(&ctx->d_ictr, kIcWords * sizeof(unsigned long long)));
     iws = ctx->d_items;
   }
   StepArgs sa;

@@ -1241,6 +1241,54 @@ GL_HD void snapped_integrands(T x0, T y0, T dx, T dy1, T dy2, T ct, T st, T* ff,
   }
 }
 
+// The arcs (mid-direction cos/sin, half-width) into which the whole turn of a
+// boundary lying inside the disk is split for the f_lin quadrature: at the two
+// inner maxima when there are two, otherwise one arc whose two ends meet at the
+// single maximum or at the point nearest the limb.
+template <typename R>
+GL_HD void whole_arcs(const Geo<R>& g, const Trig2<R>& tg, int nmax, const R* cmx, const R* smx,
+                      R* acm, R* asn, R* ah, int* na) {
+  if (nmax == 2) {
+    Frame<R> fr = make_frame<R>(tg);
+    R ta = frame_t<R>(fr, cmx[0], smx[0]), tb2 = frame_t<R>(fr, cmx[1], smx[1]);
+    if (m_finite(ta) && m_finite(tb2)) {
+      R ca = cmx[0], sa = smx[0], cb = cmx[1], sb = smx[1];
+      if (ta > tb2) {
+        R tmp = ta; ta = tb2; tb2 = tmp;
+        tmp = ca; ca = cb; cb = tmp;
+        tmp = sa; sa = sb; sb = tmp;
+      }
+      frame_arc<R>(tb2 - ta, R(1) + ta * tb2, false, ca, sa, &ah[0], &acm[0], &asn[0]);
+      frame_arc<R>(ta - tb2, R(1) + ta * tb2, true, cb, sb, &ah[1], &acm[1], &asn[1]);
+      *na = 2;
+      return;
+    }
+  }
+  R cs, ss;
+  if (nmax >= 1) {
+    cs = cmx[0];
+    ss = smx[0];
+  } else {
+    nearest_limb_angle<R>(g, tg, &cs, &ss);
+  }
+  acm[0] = -cs;
+  asn[0] = -ss;
+  ah[0] = R(kPi);
+  *na = 1;
+}
+
+// Whether the boundary of an ellipse centred at (x0, y0) may have two local
+// maxima of g (a scheduling hint).  g' is a first harmonic of amplitude
+// R1 = |(B, C)| plus a second of amplitude 2 R2, R2 = |(D, E)|; with
+// eps = 2 R2 / R1 < 0.447, g' keeps one sign wherever |sin| of the first
+// harmonic's phase exceeds eps and is monotone elsewhere, so it has exactly two
+// zeros (one maximum).  R1 > 5 R2 leaves margin; below that two maxima may exist.
+GL_HD bool maybe_two_maxima(const SetConst& c, float x0, float y0) {
+  const float B = 2.0f * (x0 * c.fdx + y0 * c.fdy1), C = 2.0f * y0 * c.fdy2;
+  const float D = 0.5f * (c.fdx * c.fdx + c.fdy1 * c.fdy1 - c.fdy2 * c.fdy2), E = c.fdy1 * c.fdy2;
+  return B * B + C * C <= 25.0f * (D * D + E * E);
+}
+
 // ------------------------------------------------------------------ occulted moments
 // Moments of the region where the projected ellipse covers the stellar disk:
 // I[0] = area, I[1] = Integral mu dA, I[2] = Integral r^2 dA.
@@ -1265,24 +1313,40 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
     Frame<R> frr = make_frame_k<R>(tg, kb);
     double tb[8];
     int nr = crossing_roots<R>(fr, frr, tb);
+    // The arcs of the boundary inside the disk are gathered first and integrated
+    // by one loop afterwards, so that a warp runs the quadrature once per arc
+    // count rather than once per breakpoint index.
+    R acm[4], asn[4], ah[4];
+    int na = 0;
+    CSum<R> sflat, slin, squad;
     if (nr == 0) {
       if (!(fr.q[4] < 0.0)) {
         // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
-        double v1 = -xd / c.dx, v2 = (-yd - c.dy1 * v1) / c.dy2;
-        if (v1 * v1 + v2 * v2 < 1.0) {
+        R v1 = -g.x0 / g.dx, v2 = (-g.y0 - g.dy1 * v1) / g.dy2;
+        if (v1 * v1 + v2 * v2 < R(1)) {
           I[0] = R(kPi);
           I[1] = R(2.0 * kPi / 3.0);
           I[2] = R(0.5 * kPi);
         }
         return;
       }
-      cls = kFull;   // boundary entirely inside the disk
+      // boundary entirely inside the disk: the whole turn, split at the inner
+      // maxima as in the whole-ellipse case below
+      sflat.add(area);
+      squad.add(area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4)));
+      whole_arcs<R>(g, tg, nmax, cmx, smx, acm, asn, ah, &na);
     } else {
-      // breakpoints: the crossings (kind 1) and the inner maxima (kind 0).  A
-      // maximum is kept only where the FP64 frame puts it strictly inside the
-      // disk: one that rounding placed inside while it lies on an outside arc
-      // between two close crossings would split that arc, and the limb arc
-      // joining the two crossings would be lost.
+      // g at the frame's t = infinity (q4, the largest |g| of eight samples, so
+      // its sign is safe) says whether the arc through it lies inside the disk;
+      // g changes sign at each crossing, so the others alternate from there.  An
+      // odd count (possible only from the FP64 fallback in degenerate cases)
+      // falls back to FP64 tests of g at the arc midpoints.
+      const bool wrap_in = fr.q[4] < 0.0;
+      const bool parity = (nr & 1) == 0;
+      // breakpoints: the crossings (kind 1) and the inner maxima (kind 0) that
+      // lie on an inside arc.  A maximum that rounding placed on an outside arc
+      // (between two close crossings) would split that arc and lose the limb arc
+      // joining the two crossings, so it is dropped.
       int kind[8];
       for (int i = 0; i < nr; ++i) kind[i] = 1;
       int nb = nr;
@@ -1290,7 +1354,11 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
         R tvr = frame_t<R>(frr, cmx[i], smx[i]);
         if (!m_finite(tvr)) continue;
         double tv = (double)tvr;
-        if (!(frame_poly<double>(fr, tv) < 0.0)) continue;
+        int below = 0;
+        for (int k = 0; k < nb; ++k) below += (kind[k] && tb[k] < tv) ? 1 : 0;
+        const bool on_inside = parity ? (wrap_in != ((below & 1) != 0))
+                                      : (frame_poly<double>(fr, tv) < 0.0);
+        if (!on_inside) continue;
         int j = nb - 1;
         while (j >= 0 && tb[j] > tv) {
           tb[j + 1] = tb[j];
@@ -1313,10 +1381,11 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
         py[i] = qy * nrm;
       }
       QuadPoly<R> qp = quad_poly<R>(g.x0, g.y0, g.dx, g.dy1, g.dy2);
-      CSum<R> sflat, slin, squad;
+      int ncross = 0;
       for (int i = 0; i < nb; ++i) {
         int ip = (i + 1 == nb) ? 0 : i + 1;
         bool wrap = (i + 1 == nb);
+        ncross += kind[i];
         R h, cm, sm;
         frame_arc<R>(tr_[ip] - tr_[i], R(1) + tr_[i] * tr_[ip], wrap, cth[i], sth[i], &h, &cm,
                      &sm);
@@ -1325,10 +1394,17 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
           cm = -cth[i];
           sm = -sth[i];
         }
-        bool inside =
-            wrap ? (fr.q[4] < 0.0) : (frame_poly<double>(fr, 0.5 * (tb[i] + tb[ip])) < 0.0);
+        bool inside;
+        if (wrap) inside = wrap_in;
+        else if (parity) inside = wrap_in != ((ncross & 1) != 0);
+        else inside = frame_poly<double>(fr, 0.5 * (tb[i] + tb[ip])) < 0.0;
         if (inside) {
-          slin.add(lin_arc<R>(g, cm, sm, h, rule));
+          if (na < 4) {
+            acm[na] = cm;
+            asn[na] = sm;
+            ah[na] = h;
+            ++na;
+          }
           R ca = cth[i], sa = sth[i], cb = cth[ip], sb = sth[ip];
           R dth = R(2) * h;
           sflat.add(R(0.5) * (g.W0 * dth + g.Wc * (sb - sa) - g.Ws * (cb - ca)));
@@ -1345,11 +1421,12 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
           squad.add(R(0.25) * dl - (s4b - s4a) / R(48));
         }
       }
-      I[0] = sflat.value();
-      I[1] = slin.value();
-      I[2] = squad.value();
-      return;
     }
+    for (int k = 0; k < na; ++k) slin.add(lin_arc<R>(g, acm[k], asn[k], ah[k], rule));
+    I[0] = sflat.value();
+    I[1] = slin.value();
+    I[2] = squad.value();
+    return;
   }
   // whole ellipse inside the disk: split the turn at the inner maxima
   I[0] = area;
