@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
     }
   }
   __syncthreads();
-  if (!live || role != 0) return;
+  if (!live) return;
+  if (role == 3) gl::set_kepler(sets + s);   // reads the orbit role 0 wrote
+  if (role != 0) return;
   const int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
   const double g = p.g ? p.g[s] : 0.0, zeta = p.zeta ? p.zeta[s] : 0.0;
   const bool ok = orbit_ok && isfinite(g) && g >= 0.0 && g < 1.0 && isfinite(zeta) &&
@@ -380,18 +382,9 @@ __device__ __noinline__ int exposure_prep(const SetConst& c, double t, double* t
   *tau_out = tau;
   if (!gl::in_window(c, tau, 0.5 * c.exptime)) return kExpDead;
   if (sizeof(R) == 4 && (c.flags & gl::kSetTaylor)) {
-    if (c.nsuper == 1) {
-      // the one sub-exposure sits at the midpoint: no derivatives needed (the
-      // Taylor step with dt = 0 returns the midpoint values unchanged)
-      gl::SkyState st;
-      gl::sky_position(c, tau, &st.x, &st.y, &st.z);
-      for (int k = 0; k < 3; ++k) st.d1[k] = st.d2[k] = st.d3[k] = 0.0;
-      *mid = gl::mid_state(st);
-    } else {
-      gl::SkyState st;
-      gl::sky_state(c, tau, &st);
-      *mid = gl::mid_state(st);
-    }
+    // with one sub-exposure it sits at the midpoint: no derivatives needed (the
+    // Taylor step with dt = 0 returns the midpoint values unchanged)
+    *mid = gl::mid_state_at(c, tau, c.nsuper != 1);
     return kExpTaylor;
   }
   return 0;
@@ -1069,9 +1062,7 @@ __global__ void __launch_bounds__(NT) gl_collect_kernel(CollectArgs a) {
       const SetConst& c = a.sets[e_s[i]];
       int fl = 0;
       if (c.flags & gl::kSetTaylor) {
-        gl::SkyState st;
-        gl::sky_state(c, e_tau[i], &st);
-        e_mid[i] = gl::mid_state(st);
+        e_mid[i] = gl::mid_state_at(c, e_tau[i], true);
         fl = kExpTaylor;
       }
       e_flag[i] = fl;

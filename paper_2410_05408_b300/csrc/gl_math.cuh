@@ -60,6 +60,12 @@ struct SetConst {
   // body: semi-axes (a along x', b along y', c along z') and the rows of
   // R(zeta, eta, xi), for projections that change along the orbit (tidal locking)
   double ax[3], rot[9];
+  // Kepler solve about the conjunction (set_kepler): e cos E_c, e sin E_c and the
+  // Halley error constant; FP32 copies of the orbit for the FP32 stages
+  double kep_ec, kep_es, kep_C;
+  float kf_ec, kf_es, kf_ir1;          // e cos E_c, e sin E_c, 1 / (1 - e cos E_c)
+  float kf_a, kf_bo, kf_e, kf_nm;      // a, a sqrt(1 - e^2), e, n
+  float kf_cEc, kf_sEc, kf_cw, kf_sw, kf_ci, kf_si;
 };
 
 // Mapped Gauss-Legendre rule on s in [-1, 1] with theta = m + h sin(pi s / 2):
@@ -427,6 +433,31 @@ GL_HD bool set_orbit(double t0, double period, double a_rs, double b, double ecc
   return fabs(cosi) <= 1.0;
 }
 
+// Constants of the Kepler solve about the conjunction (from set_orbit's fields).
+// With F' >= 1 - e and the second and third derivatives of F at most e in size,
+// a Halley step s leaves an error below C |s|^3, C = q (1 + q), q = e / (1 - e).
+// (An invalid orbit gives meaningless values here; such sets are never used.)
+GL_HD void set_kepler(SetConst* c) {
+  const double e = c->ecc;
+  c->kep_ec = e * c->cosEc;
+  c->kep_es = e * c->sinEc;
+  const double q = e * rcp64(1.0 - e);
+  c->kep_C = q * (1.0 + q);
+  c->kf_ec = (float)c->kep_ec;
+  c->kf_es = (float)c->kep_es;
+  c->kf_ir1 = 1.0f / (1.0f - c->kf_ec);
+  c->kf_a = (float)c->a_rs;
+  c->kf_bo = (float)c->b_orb;
+  c->kf_e = (float)e;
+  c->kf_nm = (float)c->nmean;
+  c->kf_cEc = (float)c->cosEc;
+  c->kf_sEc = (float)c->sinEc;
+  c->kf_cw = (float)c->cosw;
+  c->kf_sw = (float)c->sinw;
+  c->kf_ci = (float)c->cosi;
+  c->kf_si = (float)c->sini;
+}
+
 // Transit window, exposure fields and the sub-exposure expansion flag; returns
 // the flags kSetWholeOrbit and kSetTaylor.
 //  The sky separation is at least r |sin phi| >= a (1-e) |sin phi|, phi = angle
@@ -516,6 +547,7 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
     c->flags = kSetInvalid;
     return false;
   }
+  set_kepler(c);
   set_shape(k, f, cbrt1mf, ce, sx, cx, c);
   set_ld(u1, u2, c);
   c->flags = set_window(t0, period, a_rs, ecc, omega, c->req, c->nmean, c->invP, exptime, nsuper,
@@ -579,17 +611,18 @@ GL_HD void sin_cosm1_f(float d, float* sd, float* cm1) {
 // Kepler's equation for the eccentric anomaly E = E_c + d about the
 // conjunction:  d - e [cos E_c sin d + sin E_c (cos d - 1)] = n tau.
 // Newton's method in FP32 first (cheap), then Halley's method in FP64 from the
-// FP32 iterate: with F' >= 1 - e and |F''|, |F'''| <= e, a Halley step s leaves
-// an error below C |s|^3, C = e / (1 - e) (1 + e / (1 - e)), so the FP64
-// iteration stops once C |s|^3 <= 1e-17 -- one step from a converged FP32
-// iterate (|s| ~ 1e-7 |d|).  A bisection on the bracket |E - M| <= e backs up an
-// iteration that does not settle.  Returns sin d and cos d - 1.
+// FP32 iterate; the error after a step s is below C |s|^3 (set_kepler), so the
+// FP64 iteration stops once C |s|^3 <= 1e-17 -- one step from a converged FP32
+// iterate (|s| ~ 1e-7 |d|).  sin d and cos d - 1 of the final iterate follow
+// from those of the last evaluated one by the angle-difference formulas to
+// second order in s (the dropped terms are below |s|^3 / 6 < 1e-20).  A
+// bisection on the bracket |E - M| <= e backs up an iteration that does not
+// settle.  Returns sin d and cos d - 1.
 GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* cm1_out) {
-  double nt = c.nmean * tau;
-  double e = c.ecc;
-  double ec = e * c.cosEc, es = e * c.sinEc;
-  const float ntf = (float)nt, ecf = (float)ec, esf = (float)es;
-  const float ir1f = 1.0f / (1.0f - ecf);
+  const double nt = c.nmean * tau;
+  const double ec = c.kep_ec, es = c.kep_es;
+  const float ntf = (float)nt, ecf = c.kf_ec, esf = c.kf_es;
+  const float ir1f = c.kf_ir1;
   float df = ntf * ir1f;
   df -= 0.5f * esf * df * df * ir1f;   // second-order start: F ~ d (1 - ec) + es d^2 / 2 - n tau
   for (int it = 0; it < 4; ++it) {
@@ -599,8 +632,7 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
     const float Fp = 1.0f - ecf * (1.0f + cmf) + esf * sdf;
     df -= F / Fp;
   }
-  const double q1e = e * rcp64(1.0 - e);
-  const double C = q1e * (1.0 + q1e);
+  const double C = c.kep_C;
   double d = isfinite(df) ? (double)df : nt;
   double sd, cm1;
   bool conv = false;
@@ -615,13 +647,22 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
     const double as = fabs(step);
     if (C * as * as * as <= 1e-17 || as <= 1e-16 * (1.0 + fabs(d))) {
       conv = isfinite(d);
+      if (conv) {
+        // sin(d - s), cos(d - s) - 1 from sin d, cos d - 1 of the previous iterate
+        const double hs2 = 0.5 * step * step;
+        const double sd1 = sd - step * (1.0 + cm1) - hs2 * sd;
+        const double cm11 = cm1 + step * sd - hs2 * (1.0 + cm1);
+        *sd_out = sd1;
+        *cm1_out = cm11;
+        return;
+      }
       break;
     }
   }
-  if (!conv) {
+  {
     double Ec = atan2(c.sinEc, c.cosEc);
-    double M = Ec - e * c.sinEc + nt;
-    double lo = M - e - Ec, hi = M + e - Ec;
+    double M = Ec - c.ecc * c.sinEc + nt;
+    double lo = M - c.ecc - Ec, hi = M + c.ecc - Ec;
     for (int it = 0; it < 200 && hi - lo > 1e-16 * (1.0 + fabs(lo)); ++it) {
       double mid = 0.5 * (lo + hi);
       sin_cosm1(mid, &sd, &cm1);
@@ -649,51 +690,6 @@ GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, d
   *z = -p2 * c.sini;
 }
 
-// Position and its first three time derivatives (velocity, acceleration,
-// jerk) in the sky frame; acceleration and jerk from r'' = -mu r/|r|^3 with
-// mu = n^2 a^3 (exact for a Kepler orbit).
-struct SkyState {
-  double x, y, z;
-  double d1[3], d2[3], d3[3];
-};
-
-GL_HD void sky_state(const SetConst& c, double tau, SkyState* s) {
-  double sd, cm1;
-  kepler_offset(c, tau, &sd, &cm1);
-  double dcosE = c.cosEc * cm1 - c.sinEc * sd;
-  double dsinE = c.sinEc * cm1 + c.cosEc * sd;
-  double dX = c.a_rs * dcosE, dY = c.b_orb * dsinE;
-  double p1 = dX * c.cosw - dY * c.sinw;
-  double p2 = c.rc + (dX * c.sinw + dY * c.cosw);
-  s->y = -p1;
-  s->x = p2 * c.cosi;
-  s->z = -p2 * c.sini;
-  // The derivatives only scale time offsets within an exposure (|v dt| < 0.1
-  // stellar radii), so FP32 (relative error ~1e-7) is ample for them.
-  const float a = (float)c.a_rs, bo = (float)c.b_orb, ef = (float)c.ecc, nm = (float)c.nmean;
-  const float cosE = (float)(c.cosEc + dcosE), sinE = (float)(c.sinEc + dsinE);
-  const float X = a * (cosE - ef), Y = bo * sinE;
-  const float r = a * (1.0f - ef * cosE);
-  const float ir = 1.0f / r;
-  const float Ed = nm * a * ir;                 // dE/dt
-  const float Xd = -a * sinE * Ed, Yd = bo * cosE * Ed;
-  const float mu = nm * nm * a * a * a;
-  const float ir2 = ir * ir, ir3 = ir2 * ir;
-  const float rv = X * Xd + Y * Yd;
-  const float Xa = -mu * X * ir3, Ya = -mu * Y * ir3;
-  const float Xj = -mu * (Xd * ir3 - 3.0f * X * rv * ir3 * ir2);
-  const float Yj = -mu * (Yd * ir3 - 3.0f * Y * rv * ir3 * ir2);
-  const float in[3][2] = {{Xd, Yd}, {Xa, Ya}, {Xj, Yj}};
-  double* out[3] = {s->d1, s->d2, s->d3};
-  const float cw = (float)c.cosw, sw = (float)c.sinw, ci = (float)c.cosi, si = (float)c.sini;
-  for (int k = 0; k < 3; ++k) {
-    const float q1 = in[k][0] * cw - in[k][1] * sw;
-    const float q2 = in[k][0] * sw + in[k][1] * cw;
-    out[k][0] = q2 * ci;
-    out[k][1] = -q1;
-    out[k][2] = -q2 * si;
-  }
-}
 
 // ------------------------------------------------------------------ precision helpers
 GL_HD double m_sqrt(double x) { return sqrt(x); }
@@ -1561,22 +1557,59 @@ GL_HD void sphere_moments(R z, R p, R omz2, const NodeRule<R>& rule, R I[3]) {
 }
 
 // Exposure midpoint state rounded for FP32 sub-exposure steps: position,
-// 1 - x^2 - y^2 (formed in FP64) and the first three derivatives.
+// 1 - x^2 - y^2 (formed in FP64) and the Taylor coefficients of the first three
+// derivatives (v, a / 2, j / 6).
 struct MidState {
   float x, y, z, omr2;
   float d1[3], d2[3], d3[3];
 };
 
-GL_HD MidState mid_state(const SkyState& s) {
+// The midpoint state at time offset tau from conjunction: the FP64 Kepler
+// position, and (with derivs) velocity, acceleration and jerk from
+// r'' = -mu r / |r|^3, mu = n^2 a^3 (exact for a Kepler orbit).  The
+// derivatives only scale time offsets within an exposure (|v dt| < 0.1 stellar
+// radii), so FP32 (relative error ~1e-7) is ample for them.
+GL_HD MidState mid_state_at(const SetConst& c, double tau, bool derivs) {
+  double sd, cm1;
+  kepler_offset(c, tau, &sd, &cm1);
+  const double dcosE = c.cosEc * cm1 - c.sinEc * sd;   // cos E - cos E_c
+  const double dsinE = c.sinEc * cm1 + c.cosEc * sd;   // sin E - sin E_c
+  const double dX = c.a_rs * dcosE, dY = c.b_orb * dsinE;
+  const double p1 = dX * c.cosw - dY * c.sinw;
+  const double p2 = c.rc + (dX * c.sinw + dY * c.cosw);
+  const double x = p2 * c.cosi, y = -p1;
   MidState m;
-  m.x = (float)s.x;
-  m.y = (float)s.y;
-  m.z = (float)s.z;
-  m.omr2 = (float)((1.0 - s.x) * (1.0 + s.x) - s.y * s.y);
+  m.x = (float)x;
+  m.y = (float)y;
+  m.z = (float)(-p2 * c.sini);
+  m.omr2 = (float)((1.0 - x) * (1.0 + x) - y * y);
+  if (!derivs) {
+    for (int k = 0; k < 3; ++k) m.d1[k] = m.d2[k] = m.d3[k] = 0.0f;
+    return m;
+  }
+  const float a = c.kf_a, bo = c.kf_bo, ef = c.kf_e, nm = c.kf_nm;
+  const float cosE = c.kf_cEc + (float)dcosE, sinE = c.kf_sEc + (float)dsinE;
+  const float X = a * (cosE - ef), Y = bo * sinE;
+  const float r = a * (1.0f - ef * cosE);
+  const float ir = 1.0f / r;
+  const float Ed = nm * a * ir;                 // dE/dt
+  const float Xd = -a * sinE * Ed, Yd = bo * cosE * Ed;
+  const float mu = nm * nm * a * a * a;
+  const float ir2 = ir * ir, ir3 = ir2 * ir;
+  const float rv = X * Xd + Y * Yd;
+  const float Xa = -mu * X * ir3, Ya = -mu * Y * ir3;
+  const float Xj = -mu * (Xd * ir3 - 3.0f * X * rv * ir3 * ir2);
+  const float Yj = -mu * (Yd * ir3 - 3.0f * Y * rv * ir3 * ir2);
+  const float in[3][2] = {{Xd, Yd}, {Xa, Ya}, {Xj, Yj}};
+  const float scale[3] = {1.0f, 0.5f, 1.0f / 6.0f};
+  float* out[3] = {m.d1, m.d2, m.d3};
+  const float cw = c.kf_cw, sw = c.kf_sw, ci = c.kf_ci, si = c.kf_si;
   for (int k = 0; k < 3; ++k) {
-    m.d1[k] = (float)s.d1[k];
-    m.d2[k] = 0.5f * (float)s.d2[k];
-    m.d3[k] = (float)s.d3[k] * (1.0f / 6.0f);
+    const float q1 = in[k][0] * cw - in[k][1] * sw;
+    const float q2 = in[k][0] * sw + in[k][1] * cw;
+    out[k][0] = q2 * ci * scale[k];
+    out[k][1] = -q1 * scale[k];
+    out[k][2] = -q2 * si * scale[k];
   }
   return m;
 }
