@@ -784,10 +784,10 @@ __device__ __forceinline__ unsigned warpid_() {
   return v;
 }
 
-// MINB = 1 leaves the compiler its registers (4 resident CTAs per SM: the
-// shortest warps, for batches with few items per sub-partition); MINB = 8 caps
-// them at 64 (8 CTAs per SM: more warps to hide latency, for large batches).
-// The autotuner chooses between the two.
+// MINB = 4 allows 128 registers (4 resident CTAs per SM: the shortest warps,
+// for batches with few items per sub-partition); MINB = 8 caps them at 64
+// (8 CTAs per SM: more warps to hide latency, for large batches).  The
+// autotuner chooses between the two.
 template <typename R, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
   const int rb = rule_base(a.rule_idx);
@@ -1601,7 +1601,7 @@ struct gl_context {
   int occ[16] = {0};                   // resident CTAs per SM by (precision, counting, threads)
   struct LcCfg {
     int threads, tile, cap, rule_idx;
-    int qvar;   // item pipeline: quadrature kernel variant (0: MINB = 1, 1: MINB = 8)
+    int qvar;   // item pipeline: quadrature kernel variant (0: MINB = 4, 1: MINB = 8)
   } cfg[2] = {{256, 256, 1024, -1, 0}, {256, 256, 1024, -1, 0}};   // FP64, FP32C
   struct TuneInfo {
     int tuned = 0, candidates = 0, admissible = 0;
@@ -1812,7 +1812,7 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   int& eocc = ctx->eocc[sizeof(R) == 4 ? 1 : 0];
   if (qocc == 0) {
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                     &qocc, qvar ? gl_items_quad_kernel<R, 128, 8> : gl_items_quad_kernel<R, 128, 1>,
+                     &qocc, qvar ? gl_items_quad_kernel<R, 128, 8> : gl_items_quad_kernel<R, 128, 4>,
                      128, 0));
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&eocc, gl_exp_kernel<R>,
                                                                kExpThreads, 0));
@@ -1833,7 +1833,7 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   if (qvar)
     gl_items_quad_kernel<R, 128, 8><<<ctx->sms * qocc, 128, 0, st>>>(args);
   else
-    gl_items_quad_kernel<R, 128, 1><<<ctx->sms * qocc, 128, 0, st>>>(args);
+    gl_items_quad_kernel<R, 128, 4><<<ctx->sms * qocc, 128, 0, st>>>(args);
   gl_items_sum_kernel<R><<<ctx->sms * 2, 256, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_QUAD, pe, st);
   ctx->launches += 2;

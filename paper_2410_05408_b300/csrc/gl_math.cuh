@@ -1300,7 +1300,15 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
   Trig2<R> tg = limb_poly<R>(c, x0, y0, omr2);
   R area = R(kPi) * g.dx * g.dy2;
   R cmx[2], smx[2];
-  int nmax = inner_maxima<R>(tg, cmx, smx);
+  int nmax;
+  if (cls == kFull && !maybe_two_maxima(c, (float)x0, (float)y0)) {
+    // a whole ellipse whose g has a single maximum (maybe_two_maxima): find it
+    // by Newton's method rather than through the quartic of g'
+    nearest_limb_angle<R>(g, tg, &cmx[0], &smx[0]);
+    nmax = 1;
+  } else {
+    nmax = inner_maxima<R>(tg, cmx, smx);
+  }
   if (cls == kPartial) {
     double xd = (double)x0, yd = (double)y0;
     Trig2<double> tgd = limb_poly<double>(c, xd, yd, (1.0 - xd) * (1.0 + xd) - yd * yd);
