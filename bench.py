@@ -19,6 +19,7 @@ host's cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -158,7 +159,7 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(1.0)   # nvidia-smi's start-up stays out of the timed region
         return self
 
     def __exit__(self, *a):
@@ -664,6 +665,9 @@ def main():
     ap.add_argument("--ref-sets", type=int, default=96)
     ap.add_argument("--cpu-sets", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="",
+                    help="pin the FP32C configuration instead of autotuning it, as "
+                         "'nodes=N,quad=C' (a previous run's autotune report)")
     ap.add_argument("--sur-train", type=int, default=10_000_000)
     ap.add_argument("--sur-held", type=int, default=1_000_000)
     ap.add_argument("--sur-epochs", type=int, default=6)
@@ -736,6 +740,8 @@ def main():
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    step_stats = {}
+
     def timed(prec, out, k, profile):
         """k steps, L2 flushed before each, CUDA events on the launch stream around
         each step (the flush is outside them).  With profile=True the library also
@@ -750,13 +756,21 @@ def main():
             # the kernels rather than the launches
             for _ in range(4):
                 flush.zero_()
-        for i in range(k):
-            flush.zero_()
-            evs[i][0].record(stream)
-            step(out, prec)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize(dev)
-        ms = sum(a.elapsed_time(b) for a, b in evs)
+        gc_was = gc.isenabled()
+        gc.disable()   # no collector pause between a step's events
+        try:
+            for i in range(k):
+                flush.zero_()
+                evs[i][0].record(stream)
+                step(out, prec)
+                evs[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+        finally:
+            if gc_was:
+                gc.enable()
+        per_step = [a.elapsed_time(b) for a, b in evs]
+        step_stats[prec if not profile else -1] = per_step
+        ms = sum(per_step)
         kern = {}
         if profile:
             for name, kind in (("tiles", binding.GL_KERNEL_CURVE),
@@ -768,10 +782,17 @@ def main():
         return ms, ctx.launches() - l0, kern
 
     # autotuner: kernel shape and FP32 quadrature order for this batch (untimed)
-    tune = ctx.autotune(dp, d_t, out32, d_exp, nsuper=d_ns, offsets=d_off,
-                        precision=binding.GL_FP32C, stream=stream)
-    tune64 = ctx.autotune(dp, d_t, out64, d_exp, nsuper=d_ns, offsets=d_off,
-                          precision=binding.GL_FP64, stream=stream)
+    if args.config:
+        kv = dict(item.split("=") for item in args.config.split(","))
+        ctx.configure(binding.GL_FP32C, nodes=int(kv.get("nodes", 0)),
+                      quad_ctas=int(kv.get("quad", 0)))
+        ctx.configure(binding.GL_FP64, quad_ctas=int(kv.get("quad64", 0)))
+        tune = tune64 = {"pinned": args.config}
+    else:
+        tune = ctx.autotune(dp, d_t, out32, d_exp, nsuper=d_ns, offsets=d_off,
+                            precision=binding.GL_FP32C, stream=stream)
+        tune64 = ctx.autotune(dp, d_t, out64, d_exp, nsuper=d_ns, offsets=d_off,
+                              precision=binding.GL_FP64, stream=stream)
     step(out32, binding.GL_FP32C)
     torch.cuda.synchronize(dev)
     max_dflux = float((out32 - out64).abs().max().item())
@@ -782,14 +803,16 @@ def main():
     counts = ctx.counts_read()
     ctx.counts(False)
 
-    for _ in range(args.warmup):
-        step(out32, binding.GL_FP32C)
-        step(out64, binding.GL_FP64)
-    torch.cuda.synchronize(dev)
-
-    barrier(world)
-    torch.cuda.synchronize(dev)
+    # The clock sampler starts (and settles) before the warm-up steps, so that the
+    # GPU runs the warm-up right before the timed steps instead of idling while
+    # the sampler starts (an idle GPU lowers its clocks).
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step(out32, binding.GL_FP32C)
+            step(out64, binding.GL_FP64)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        torch.cuda.synchronize(dev)
         ms32, launches, _ = timed(binding.GL_FP32C, out32, args.steps, profile=False)
     barrier(world)
     ms32 = allreduce_max(ms32, world)
@@ -830,7 +853,9 @@ def main():
     fp32_peak, fp64_peak = alu_peaks(peaks.get("sm_max_mhz", 2032.0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
+        "ms_per_step_median": statistics.median(step_stats[binding.GL_FP32C]),
+        "ms_per_step_max": max(step_stats[binding.GL_FP32C]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "evals_per_step": evals,
                    "exposures_per_step": n_tot, "parameter_sets": n_sets,

@@ -291,6 +291,15 @@ typedef struct {
 int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *out,
                 gl_precision prec, void *stream, gl_tune_report *rep);
 
+/* Sets the light-curve configuration for precision prec directly (for example
+ * one an earlier gl_autotune chose): threads per CTA of the tile kernel (128 or
+ * 256), Gauss-Legendre nodes per arc of the FP32C quadrature (16, 20, 24, 28;
+ * the FP64 order is fixed) and resident CTAs per SM of the item pipeline's
+ * quadrature kernel (4 or 8).  0 selects the default of each (256 threads, the
+ * shape-dependent default order, 4 CTAs).  Drops the cached graphs.  GL_EINVAL
+ * for other values. */
+int gl_configure(gl_context *ctx, gl_precision prec, int threads, int nodes, int quad_ctas);
+
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */
 #define GL_KERNEL_CURVE 1   /* light-curve tile kernel, or the item pipeline's window and

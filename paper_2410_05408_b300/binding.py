@@ -30,6 +30,7 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_flux_sky", "gl_q_to_u", "gl_sync", "gl_launch_count", "gl_profile_enable",
             "gl_profile_read", "gl_lightcurve_batch_noalloc", "gl_counts_enable",
             "gl_counts_read", "gl_graphs_enable", "gl_graph_launches", "gl_autotune",
+            "gl_configure",
             "gl_flux_sphere", "gl_mlp_param_count", "gl_mlp_create", "gl_mlp_destroy",
             "gl_mlp_set_params", "gl_mlp_get_params", "gl_mlp_get_grads", "gl_mlp_forward",
             "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
@@ -181,6 +182,8 @@ def load():
         lib.gl_autotune.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times), vp, i32,
                                     vp, ctypes.POINTER(_TuneReport)]
         lib.gl_autotune.restype = i32
+        lib.gl_configure.argtypes = [vp, i32, i32, i32, i32]
+        lib.gl_configure.restype = i32
         lib.gl_counts_enable.argtypes = [vp, i32]
         lib.gl_counts_enable.restype = i32
         lib.gl_counts_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
@@ -307,6 +310,13 @@ def gl_autotune(ctx, params: dict, t, out, precision: int = GL_FP32C, offsets=No
     _check(ctx, lib.gl_autotune(ctx, ctypes.byref(p), ctypes.byref(tm), _ptr(out, "float64"),
                                 int(precision), _stream_ptr(stream), ctypes.byref(rep)))
     return {f: getattr(rep, f) for f, _ in rep._fields_}
+
+
+def gl_configure(ctx, precision: int, threads: int = 0, nodes: int = 0,
+                 quad_ctas: int = 0) -> None:
+    """Set the light-curve configuration of a precision directly (0 = default)."""
+    _check(ctx, load().gl_configure(ctx, int(precision), int(threads), int(nodes),
+                                    int(quad_ctas)))
 
 
 def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_FP32C,
@@ -578,6 +588,9 @@ class Context:
 
     def last_error(self) -> str:
         return gl_last_error(self.handle)
+
+    def configure(self, precision, threads=0, nodes=0, quad_ctas=0):
+        gl_configure(self.handle, precision, threads, nodes, quad_ctas)
 
     def autotune(self, params, t, out, exptime, nsuper=None, nsuper_all=1, offsets=None,
                  precision=GL_FP32C, stream=None) -> dict:

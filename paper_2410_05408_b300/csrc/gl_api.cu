@@ -2106,6 +2106,27 @@ int gl_item_pipeline(gl_context* ctx, int on, int64_t max_items) {
   return GL_OK;
 }
 
+int gl_configure(gl_context* ctx, gl_precision prec, int threads, int nodes, int quad_ctas) {
+  if (!ctx) return GL_EINVAL;
+  ctx->err[0] = 0;
+  if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision");
+  if (threads != 0 && threads != 128 && threads != 256)
+    return fail(ctx, GL_EINVAL, "threads must be 0, 128 or 256");
+  if (quad_ctas != 0 && quad_ctas != 4 && quad_ctas != 8)
+    return fail(ctx, GL_EINVAL, "quad_ctas must be 0, 4 or 8");
+  int ni = -1;
+  if (nodes != 0) {
+    if (prec == GL_FP64) return fail(ctx, GL_EINVAL, "the FP64 path has a fixed order");
+    for (int i = 0; i < 4; ++i)
+      if (kTuneNodes[i] == nodes) ni = i;
+    if (ni < 0) return fail(ctx, GL_EINVAL, "nodes must be 0, 16, 20, 24 or 28");
+  }
+  const int th = threads ? threads : 256;
+  ctx->cfg[prec == GL_FP64 ? 0 : 1] = {th, th, 4 * th, ni, quad_ctas == 8 ? 1 : 0};
+  drop_graphs(ctx);
+  return GL_OK;
+}
+
 int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
                 gl_precision prec, void* stream, gl_tune_report* rep) {
   if (!ctx || !p || !tm || !out) return GL_EINVAL;

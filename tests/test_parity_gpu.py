@@ -429,6 +429,26 @@ def test_autotuner_keeps_only_tolerance_passing_configurations(ctx, mcmc):
     _compare(got[idx].ravel(), ref.ravel(), binding.GL_FP32C)
 
 
+def test_configure_pins_a_configuration(ctx, mcmc):
+    """gl_configure sets what gl_autotune would choose; every pinned FP32C
+    configuration stays within tolerance of the oracle, and bad values are refused."""
+    wl, idx, ref = mcmc
+    p = {k: _dev(v) for k, v in product_params(wl).items()}
+    t, exp = _dev(wl["t"]), _dev(wl["exptime"])
+    out = torch.empty(256 * len(wl["t"]), dtype=torch.float64, device="cuda")
+    for nodes, quad in ((16, 4), (16, 8), (28, 8)):
+        ctx.configure(binding.GL_FP32C, nodes=nodes, quad_ctas=quad)
+        ctx.lightcurve(p, t, out, exp, nsuper_all=15, precision=binding.GL_FP32C)
+        got = out.cpu().numpy().reshape(256, -1)
+        _compare(got[idx].ravel(), ref.ravel(), binding.GL_FP32C)
+    for bad in (dict(nodes=17), dict(quad_ctas=5), dict(threads=64)):
+        with pytest.raises(binding.GLError):
+            ctx.configure(binding.GL_FP32C, **bad)
+    with pytest.raises(binding.GLError):
+        ctx.configure(binding.GL_FP64, nodes=16)
+    ctx.configure(binding.GL_FP32C)   # back to the defaults
+
+
 def test_launches_are_counted(ctx):
     n0 = ctx.launches()
     _run(ctx, inputs.single_transit(n_times=10), binding.GL_FP32C)
