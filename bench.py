@@ -50,19 +50,21 @@ def alu_peaks(sm_mhz: float):
 
 
 # Algorithmic work per unit of the FP32C light-curve step (flops, FMA = 2),
-# counted from the source (see the kernel section of the design doc), by kernel:
-#   exposures (gl_win_kernel + gl_exp_kernel): FP32 per exposure window test 12,
-#         per sub-exposure position and class 40; FP64 per in-window exposure 10
-#         (exact window), midpoint Kepler state 250, per sub-exposure FP64 Kepler
-#         (no expansion) 250
-#   quadrature (gl_items_quad_kernel, then gl_items_sum_kernel): FP32 whole-ellipse item 1175 (inner maxima
-#         310, geometry 30, 20 nodes x 41, closed forms 15), crossing item 2300
-#         (maxima 310, FP32 Ferrari 290, breakpoints 50, 1.5 arcs x (20 nodes x 49
-#         + 80), limb arcs 25, geometry 30); FP64 crossing item 200 (limb
-#         polynomial, frame, Newton polish, sign tests), exposure sums 2 per
-#         sub-exposure
-F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 1175, 2300
-F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 250, 200, 2
+# counted from the source, by kernel:
+#   exposures (gl_win_kernel + gl_exp_kernel + gl_geo_kernel): FP32 per exposure
+#         window test 12, per sub-exposure position and class 40; FP64 per
+#         in-window exposure 10 (exact window), midpoint Kepler state 90 (one
+#         Halley step with its series, second-order update, sky position), per
+#         sub-exposure FP64 Kepler (sets without the expansion) 90
+#   quadrature (gl_items_quad_kernel, then gl_items_sum_kernel): FP32 whole-ellipse
+#         item 840 (geometry and limb polynomial 35, Newton for the maximum 150,
+#         16 nodes x 40, closed forms 15), crossing item 1850 (inner maxima 310,
+#         frame 90, FP32 Ferrari 290, breakpoints 40, closed forms 160, arcs 110,
+#         one inside arc of 16 nodes x 56); FP64 crossing item 105 (limb
+#         polynomial 15, frame 25, Newton polish of two roots 58, ordering 7),
+#         exposure sums 2 per sub-exposure
+F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 840, 1850
+F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 90, 105, 2
 
 
 def kernel_flops(c: dict) -> dict:
