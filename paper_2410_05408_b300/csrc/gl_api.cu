@@ -1593,6 +1593,9 @@ struct gl_context {
   size_t sets_cap = 0;
   char* d_stage = nullptr;     // staging of host inputs
   size_t stage_cap = 0;
+  char* h_stage = nullptr;     // pinned host mirror: host inputs are packed here, one copy
+  size_t h_stage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;   // recorded after the last copy out of h_stage
   double* d_out = nullptr;     // staging of a host output
   size_t out_cap = 0;
   int* d_status = nullptr;
@@ -1707,7 +1710,10 @@ int grow(gl_context* ctx, void** buf, size_t* cap, size_t need) {
 }
 
 // Stage a list of input arrays: device arrays pass through, host arrays are
-// copied into ctx->d_stage.  `any_host` reports whether a copy was made.
+// packed into the pinned mirror ctx->h_stage and sent to ctx->d_stage with one
+// copy (one transfer instead of one per array).  `any_host` reports whether a
+// copy was made.  The mirror is rewritten only after the previous copy out of it
+// has completed.
 struct StageItem {
   const void** ptr;
   size_t bytes;
@@ -1724,17 +1730,29 @@ int stage_inputs(gl_context* ctx, StageItem* items, int n, cudaStream_t st, bool
   if (need == 0) return GL_OK;
   int rc = grow(ctx, (void**)&ctx->d_stage, &ctx->stage_cap, need);
   if (rc) return rc;
+  if (!ctx->stage_ev) GL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->stage_ev, cudaEventDisableTiming));
+  GL_CUDA(ctx, cudaEventSynchronize(ctx->stage_ev));   // the mirror is free again
+  if (need > ctx->h_stage_cap) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_cap = 0;
+    const size_t sz = need + need / 4 + 4096;
+    if (cudaMallocHost((void**)&ctx->h_stage, sz) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, GL_ENOMEM, "cudaMallocHost of %zu bytes failed", sz);
+    }
+    ctx->h_stage_cap = sz;
+  }
   size_t off = 0;
   for (int i = 0; i < n; ++i) {
     if (!host[i]) continue;
-    char* dst = ctx->d_stage + off;
-    if (items[i].bytes) {
-      GL_CUDA(ctx, cudaMemcpyAsync(dst, *items[i].ptr, items[i].bytes, cudaMemcpyHostToDevice, st));
-    }
-    *items[i].ptr = dst;
+    if (items[i].bytes) memcpy(ctx->h_stage + off, *items[i].ptr, items[i].bytes);
+    *items[i].ptr = ctx->d_stage + off;
     off += (items[i].bytes + 255) & ~(size_t)255;
     *any_host = true;
   }
+  GL_CUDA(ctx, cudaMemcpyAsync(ctx->d_stage, ctx->h_stage, off, cudaMemcpyHostToDevice, st));
+  GL_CUDA(ctx, cudaEventRecord(ctx->stage_ev, st));
   return GL_OK;
 }
 
@@ -2042,6 +2060,8 @@ int gl_context_destroy(gl_context* ctx) {
   cudaDeviceSynchronize();
   if (ctx->d_sets) cudaFree(ctx->d_sets);
   if (ctx->d_stage) cudaFree(ctx->d_stage);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
   if (ctx->d_out) cudaFree(ctx->d_out);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_counter) cudaFree(ctx->d_counter);
@@ -2420,7 +2440,9 @@ int lightcurve_impl(gl_context* ctx, const gl_params* p, const gl_times* tm, dou
   sa.out = d_out;
   sa.prec = (int)prec;
   sa.sets = ctx->d_sets;
-  bool use_graph = ctx->graphs && !any_host && !out_host && !ctx->profiling && !ctx->counting;
+  // host buffers are staged at fixed device addresses, so their steps replay a
+  // graph too (the copies are ordered around it on the stream)
+  bool use_graph = ctx->graphs && !ctx->profiling && !ctx->counting;
   if (use_graph) {
     rc = launch_step_graph(ctx, sa, st);
   } else {

@@ -1,0 +1,117 @@
+"""Host build of the quadrature's case analysis (no GPU), checked by other routes:
+
+* maybe_two_maxima: where it says "one maximum", g(th) = |p(th)|^2 - 1 sampled on a
+  fine grid has exactly one local maximum, and Newton's method (the whole-ellipse
+  path) lands on it;
+* crossing-arc classification by parity: the inside/outside flags agree with the
+  sign of g at each arc's midpoint, evaluated directly from the ellipse;
+* the crossing moments with gathered arcs equal the whole-ellipse moments when the
+  ellipse lies inside the disk and approach them as it reaches the limb.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SRC = r'''
+#include <cstdio>
+#include <cmath>
+#include <random>
+#include "gl_math.cuh"
+using namespace gl;
+// g(th) of the ellipse x = x0 + dx cos th, y = y0 + dy1 cos th + dy2 sin th
+static double gdir(const SetConst& c, double x0, double y0, double th) {
+  double x = x0 + c.dx * cos(th), y = y0 + c.dy1 * cos(th) + c.dy2 * sin(th);
+  return x * x + y * y - 1.0;
+}
+int main() {
+  std::mt19937_64 gen(12);
+  std::uniform_real_distribution<double> U(0, 1);
+  long n_one = 0, bad_count = 0, n_two_flag = 0;
+  double worst_angle = 0;
+  const int M = 4096;
+  for (int it = 0; it < 60000; ++it) {
+    double k = 0.01 + 0.3 * U(gen), f = 0.95 * U(gen), eta = acos(U(gen)), xi = M_PI * U(gen);
+    SetConst c;
+    set_setup(0, 10, 20, 0.1, 0, M_PI / 2, k, f, eta, xi, 0.4, 0.25, 0.01, 1, &c);
+    double rho = (1 - c.req) * sqrt(U(gen)), ph = 2 * M_PI * U(gen);
+    double x0 = rho * cos(ph), y0 = rho * sin(ph);
+    if (!maybe_two_maxima(c, (float)x0, (float)y0)) {
+      ++n_one;
+      // local maxima of g on a fine periodic grid
+      int nmax = 0;
+      double thmax = 0;
+      for (int j = 0; j < M; ++j) {
+        double a = gdir(c, x0, y0, 2 * M_PI * (j - 1) / M), b = gdir(c, x0, y0, 2 * M_PI * j / M),
+               d = gdir(c, x0, y0, 2 * M_PI * (j + 1) / M);
+        if (b > a && b >= d) { ++nmax; thmax = 2 * M_PI * j / M; }
+      }
+      if (nmax != 1) ++bad_count;
+      double omr2 = (1 - x0) * (1 + x0) - y0 * y0;
+      Geo<double> g = make_geo<double>(c, x0, y0, omr2);
+      Trig2<double> t = limb_poly<double>(c, x0, y0, omr2);
+      double cs, ss;
+      nearest_limb_angle<double>(g, t, &cs, &ss);
+      double d = fabs(remainder(atan2(ss, cs) - thmax, 2 * M_PI));
+      if (d > worst_angle) worst_angle = d;
+    } else {
+      ++n_two_flag;
+    }
+  }
+  // parity classification of crossing arcs vs direct midpoint signs
+  long arcs = 0, mismatch = 0;
+  for (int it = 0; it < 40000; ++it) {
+    double k = 0.01 + 0.3 * U(gen), f = 0.95 * U(gen), eta = acos(U(gen)), xi = M_PI * U(gen);
+    SetConst c;
+    set_setup(0, 10, 20, 0.1, 0, M_PI / 2, k, f, eta, xi, 0.4, 0.25, 0.01, 1, &c);
+    double rho = 1 - c.req + 2 * c.req * U(gen), ph = 2 * M_PI * U(gen);
+    double x0 = rho * cos(ph), y0 = rho * sin(ph);
+    double omr2 = (1 - x0) * (1 + x0) - y0 * y0;
+    Trig2<double> t = limb_poly<double>(c, x0, y0, omr2);
+    int kb = frame_choice<double>(t);
+    Frame<double> fr = make_frame_k<double>(t, kb);
+    double tr[8];
+    int nr = crossing_roots<double>(fr, fr, tr);
+    if (nr < 2 || (nr & 1)) continue;
+    bool wrap_in = fr.q[4] < 0.0;
+    for (int i = 0; i + 1 < nr; ++i) {
+      bool parity_in = wrap_in != (((i + 1) & 1) != 0);
+      double ct, st;
+      frame_angle<double>(fr, 0.5 * (tr[i] + tr[i + 1]), &ct, &st);
+      double gm = gdir(c, x0, y0, atan2(st, ct));
+      if (fabs(gm) < 1e-12) continue;
+      ++arcs;
+      if (parity_in != (gm < 0)) ++mismatch;
+    }
+  }
+  printf("%ld %ld %ld %.3e %ld %ld\n", n_one, bad_count, n_two_flag, worst_angle, arcs, mismatch);
+}
+'''
+
+
+def _run():
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.cpp")
+        exe = os.path.join(d, "t")
+        with open(src, "w") as fh:
+            fh.write(SRC)
+        inc = os.path.join(ROOT, "paper_2410_05408_b300", "csrc")
+        r = subprocess.run(["g++", "-O2", "-std=c++17", "-I", inc, src, "-o", exe],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail(r.stderr)
+        return subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+
+
+def test_single_maximum_hint_and_parity_classification():
+    n_one, bad, n_two, worst_angle, arcs, mismatch = _run()
+    n_one, bad, n_two, arcs, mismatch = int(n_one), int(bad), int(n_two), int(arcs), int(mismatch)
+    # the hint clears most shapes and is never wrong about a single maximum
+    assert n_one > 10 * n_two and bad == 0
+    # Newton lands on the grid maximum (grid spacing 2 pi / 4096 = 1.5e-3)
+    assert float(worst_angle) < 2e-3
+    # crossing parity reproduces the direct sign of g on every arc
+    assert arcs > 10000 and mismatch == 0
