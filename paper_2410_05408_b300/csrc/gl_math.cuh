@@ -1301,11 +1301,17 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
   R area = R(kPi) * g.dx * g.dy2;
   R cmx[2], smx[2];
   int nmax;
-  if (cls == kFull && !maybe_two_maxima(c, (float)x0, (float)y0)) {
+  const bool one_max = !maybe_two_maxima(c, (float)x0, (float)y0);
+  if (cls == kFull && one_max) {
     // a whole ellipse whose g has a single maximum (maybe_two_maxima): find it
     // by Newton's method rather than through the quartic of g'
     nearest_limb_angle<R>(g, tg, &cmx[0], &smx[0]);
     nmax = 1;
+  } else if (cls == kPartial && one_max) {
+    // a single maximum of g: if the boundary crosses the limb, g > 0 there, so
+    // there is no maximum inside the disk; if it does not cross, the whole-turn
+    // split below finds the maximum by Newton's method (whole_arcs, nmax = 0)
+    nmax = 0;
   } else {
     nmax = inner_maxima<R>(tg, cmx, smx);
   }
