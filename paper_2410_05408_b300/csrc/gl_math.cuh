@@ -52,6 +52,10 @@ struct SetConst {
   double sub_step;                 // exptime / nsuper
   // FP32 copies of the shape and LD constants for the FP32C quadrature
   float fdx, fdy1, fdy2, freq, fW0, fc0, fc1, fc2, finvF0, fsub_step;
+  // shape terms of g(th) = |p(th)|^2 - 1 (limb_poly): A = A0 - (1 - x0^2 - y0^2),
+  // D, E; and their FP32 copies
+  double lpA0, lpD, lpE;
+  float flpA0, flpD, flpE;
   // conservative FP32 window for the per-exposure test (see window_maybe)
   float t0f, Pf, invPf, wlo_f, whi_f, slack_f;
   int nsuper;
@@ -284,6 +288,22 @@ GL_HD bool set_valid(double t0, double period, double a_rs, double b, double ecc
 // Equatorial radius R_eq = k (1 - f)^(-1/3) (k the mean radius, Appendix A).
 GL_HD double set_req(double k, double cbrt1mf) { return k * rcp64(cbrt1mf); }
 
+// Quantities that follow from (dx, dy1, dy2): W0 = dx dy2, the shape terms of
+// g(th) and the FP32 copies.
+GL_HD void finish_shape(SetConst* c) {
+  c->W0 = c->dx * c->dy2;
+  c->lpA0 = 0.5 * (c->dx * c->dx + c->dy1 * c->dy1 + c->dy2 * c->dy2);
+  c->lpD = 0.5 * (c->dx * c->dx + c->dy1 * c->dy1 - c->dy2 * c->dy2);
+  c->lpE = c->dy1 * c->dy2;
+  c->fdx = (float)c->dx;
+  c->fdy1 = (float)c->dy1;
+  c->fdy2 = (float)c->dy2;
+  c->fW0 = (float)c->W0;
+  c->flpA0 = (float)c->lpA0;
+  c->flpD = (float)c->lpD;
+  c->flpE = (float)c->lpE;
+}
+
 // Projected ellipse of the oblate spheroid (b = c = R_eq, a = R_pol along the
 // spin axis n = first row of R(zeta, eta, xi) = (cos eta cos xi, -cos eta sin xi,
 // sin eta)).  The sky covariance S = R^T diag(a^2,b^2,c^2) R restricted to (x, y)
@@ -309,12 +329,8 @@ GL_HD void set_shape(double k, double f, double cbrt1mf, double ce, double sx, d
   c->dy1 = sxy * idx;
   c->dy2 = req * sqrt(req * req - delta) * idx;
   c->req = req;
-  c->W0 = c->dx * c->dy2;
-  c->fdx = (float)c->dx;
-  c->fdy1 = (float)c->dy1;
-  c->fdy2 = (float)c->dy2;
   c->freq = (float)req;
-  c->fW0 = (float)c->W0;
+  finish_shape(c);
 }
 
 // Projected ellipse of a general triaxial ellipsoid (Sec. 2, Eqs. dx, dy1, dy2
@@ -340,12 +356,8 @@ GL_HD void set_shape_triaxial(double k, double f, double g, double cbrt_fg, doub
   c->req = cax;
   const double fe = f > g ? f : g;
   c->rule_min = cax >= 0.45 ? 3 : (cax < 0.2 || fe < 0.5) ? 0 : (fe < 0.7 ? 1 : 3);
-  c->W0 = c->dx * c->dy2;
-  c->fdx = (float)c->dx;
-  c->fdy1 = (float)c->dy1;
-  c->fdy2 = (float)c->dy2;
   c->freq = (float)cax;
-  c->fW0 = (float)c->W0;
+  finish_shape(c);
 }
 
 // Body semi-axes and the rows of R(zeta, eta, xi) = Rx(zeta) Ry(eta) Rz(xi).
@@ -388,11 +400,7 @@ GL_HD void locked_shape(const SetConst& c, double ca, double sa, SetConst* out) 
   out->dx = dx;
   out->dy1 = (D0 * M[0] * M[1] + D1 * M[3] * M[4] + D2 * M[6] * M[7]) * idx;
   out->dy2 = sqrt(D0 * D1 * M[8] * M[8] + D0 * D2 * M[5] * M[5] + D1 * D2 * M[2] * M[2]) * idx;
-  out->W0 = out->dx * out->dy2;
-  out->fdx = (float)out->dx;
-  out->fdy1 = (float)out->dy1;
-  out->fdy2 = (float)out->dy2;
-  out->fW0 = (float)out->W0;
+  finish_shape(out);
 }
 
 // Limb darkening in the basis (1, mu, r^2): I = c0 + c1 mu + c2 r^2 with
@@ -807,15 +815,16 @@ struct Trig2 {
   T A, B, C, D, E;
 };
 // omr2 = 1 - x0^2 - y0^2.
+// (A0, D, E depend on the shape only: finish_shape.)
 template <typename T>
 GL_HD Trig2<T> limb_poly(const SetConst& c, T x0, T y0, T omr2) {
   T dx = pick<T>(c.dx, c.fdx), dy1 = pick<T>(c.dy1, c.fdy1), dy2 = pick<T>(c.dy2, c.fdy2);
   Trig2<T> t;
-  t.A = -omr2 + T(0.5) * (dx * dx + dy1 * dy1 + dy2 * dy2);
+  t.A = pick<T>(c.lpA0, c.flpA0) - omr2;
   t.B = T(2) * (x0 * dx + y0 * dy1);
   t.C = T(2) * y0 * dy2;
-  t.D = T(0.5) * (dx * dx + dy1 * dy1 - dy2 * dy2);
-  t.E = dy1 * dy2;
+  t.D = pick<T>(c.lpD, c.flpD);
+  t.E = pick<T>(c.lpE, c.flpE);
   return t;
 }
 template <typename T>
@@ -991,10 +1000,13 @@ GL_HD Frame<T> make_frame_k(const Trig2<T>& t, int kbest) {
   const T r2 = T(0.70710678118654752440);
   const T cs8[8] = {T(1), r2, T(0), -r2, T(-1), -r2, T(0), r2};
   const T sn8[8] = {T(0), r2, T(1), r2, T(0), -r2, T(-1), -r2};
+  // delta = k pi/4 + pi, so 2 delta is a multiple of pi/2: cos, sin of it exactly
+  const T c4[4] = {T(1), T(0), T(-1), T(0)};
+  const T s4[4] = {T(0), T(1), T(0), T(-1)};
   Frame<T> f;
   f.cd = -cs8[kbest];
   f.sd = -sn8[kbest];
-  T c2d = f.cd * f.cd - f.sd * f.sd, s2d = T(2) * f.sd * f.cd;
+  const T c2d = c4[kbest & 3], s2d = s4[kbest & 3];
   T Bp = t.B * f.cd + t.C * f.sd, Cp = t.C * f.cd - t.B * f.sd;
   T Dp = t.D * c2d + t.E * s2d, Ep = t.E * c2d - t.D * s2d;
   f.q[4] = t.A - Bp + Dp;
@@ -1069,13 +1081,16 @@ GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, 
     double t = (double)xs[i];
     double fp = ((4.0 * f.q[4] * t + 3.0 * f.q[3]) * t + 2.0 * f.q[2]) * t + f.q[1];
     double r = rcp64(fp);
+    // One step from an FP32 estimate within 1e-5 leaves an error of order
+    // (P''/P') s^2 / 2, below the FP32 rounding that the quadrature applies to
+    // t next; a larger first step iterates to 1e-9.
     bool conv = false;
     for (int it = 0; it < 4; ++it) {
       double fv = (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
       double step = fv * r;
       if (!isfinite(step)) break;
       t -= step;
-      if (fabs(step) <= 1e-9 * (1.0 + fabs(t))) {
+      if (fabs(step) <= (it == 0 ? 1e-5 : 1e-9) * (1.0 + fabs(t))) {
         conv = true;
         break;
       }
@@ -1281,8 +1296,7 @@ GL_HD void whole_arcs(const Geo<R>& g, const Trig2<R>& tg, int nmax, const R* cm
 // zeros (one maximum).  R1 > 5 R2 leaves margin; below that two maxima may exist.
 GL_HD bool maybe_two_maxima(const SetConst& c, float x0, float y0) {
   const float B = 2.0f * (x0 * c.fdx + y0 * c.fdy1), C = 2.0f * y0 * c.fdy2;
-  const float D = 0.5f * (c.fdx * c.fdx + c.fdy1 * c.fdy1 - c.fdy2 * c.fdy2), E = c.fdy1 * c.fdy2;
-  return B * B + C * C <= 25.0f * (D * D + E * E);
+  return B * B + C * C <= 25.0f * (c.flpD * c.flpD + c.flpE * c.flpE);
 }
 
 // ------------------------------------------------------------------ occulted moments
