@@ -668,8 +668,9 @@ def main():
     ap.add_argument("--cpu-sets", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="",
-                    help="pin the FP32C configuration instead of autotuning it, as "
-                         "'nodes=N,quad=C' (a previous run's autotune report)")
+                    help="pin the configuration instead of autotuning it, as "
+                         "'nodes=N,quad=C,exp=B,quad64=C,exp64=B' (a previous run's "
+                         "autotune reports)")
     ap.add_argument("--sur-train", type=int, default=10_000_000)
     ap.add_argument("--sur-held", type=int, default=1_000_000)
     ap.add_argument("--sur-epochs", type=int, default=6)
@@ -787,8 +788,9 @@ def main():
     if args.config:
         kv = dict(item.split("=") for item in args.config.split(","))
         ctx.configure(binding.GL_FP32C, nodes=int(kv.get("nodes", 0)),
-                      quad_ctas=int(kv.get("quad", 0)))
-        ctx.configure(binding.GL_FP64, quad_ctas=int(kv.get("quad64", 0)))
+                      quad_ctas=int(kv.get("quad", 0)), exposure_block=int(kv.get("exp", 0)))
+        ctx.configure(binding.GL_FP64, quad_ctas=int(kv.get("quad64", 0)),
+                      exposure_block=int(kv.get("exp64", 0)))
         tune = tune64 = {"pinned": args.config}
     else:
         tune = ctx.autotune(dp, d_t, out32, d_exp, nsuper=d_ns, offsets=d_off,

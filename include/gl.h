@@ -271,13 +271,16 @@ typedef struct {
   int admissible;      /* configurations within 0.9 x tolerance of the FP64 path */
   int quad_ctas_per_sm; /* item pipeline: resident CTAs per SM of the chosen quadrature
                            kernel (4: all registers, 8: 64 registers), else 0 */
+  int exposure_block;  /* item pipeline: threads per CTA of the chosen exposure kernel
+                          (256 or 64; 64 exposures per CTA either way), else 0 */
 } gl_tune_report;
 
 /* Autotuner of the light-curve kernel for the batch (p, t) at precision prec.
  * Candidates: 128 or 256 threads per CTA of the tile kernel (tile = threads,
  * 4 x threads items per round) -- or, with the item pipeline on, the two
  * quadrature kernels (all registers, 4 CTAs per SM; or 64 registers, 8 CTAs per
- * SM) -- and, for GL_FP32C, 16, 20, 24 or 28 Gauss-Legendre nodes per arc.  Each
+ * SM) times the two exposure kernels (256 or 64 threads per CTA) -- and, for
+ * GL_FP32C, 16, 20, 24 or 28 Gauss-Legendre nodes per arc.  Each
  * candidate runs on the batch; only those whose max |flux - FP64 path| stays
  * within 0.9 x the precision's tolerance (1e-7 FP32C, 1e-10 FP64) are timed (CUDA
  * events, best of 5, each from a cold L2; as CUDA-graph replays when graphs are on,
@@ -294,11 +297,13 @@ int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *
 /* Sets the light-curve configuration for precision prec directly (for example
  * one an earlier gl_autotune chose): threads per CTA of the tile kernel (128 or
  * 256), Gauss-Legendre nodes per arc of the FP32C quadrature (16, 20, 24, 28;
- * the FP64 order is fixed) and resident CTAs per SM of the item pipeline's
- * quadrature kernel (4 or 8).  0 selects the default of each (256 threads, the
- * shape-dependent default order, 4 CTAs).  Drops the cached graphs.  GL_EINVAL
- * for other values. */
-int gl_configure(gl_context *ctx, gl_precision prec, int threads, int nodes, int quad_ctas);
+ * the FP64 order is fixed), resident CTAs per SM of the item pipeline's
+ * quadrature kernel (4 or 8) and threads per CTA of its exposure kernel (256 or
+ * 64).  0 selects the default of each (256 threads, the shape-dependent default
+ * order, 4 CTAs, 256 threads).  Drops the cached graphs.  GL_EINVAL for other
+ * values. */
+int gl_configure(gl_context *ctx, gl_precision prec, int threads, int nodes, int quad_ctas,
+                 int exposure_block);
 
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */

@@ -78,7 +78,8 @@ class _TuneReport(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("tile", ctypes.c_int), ("nodes", ctypes.c_int),
                 ("ms", ctypes.c_double), ("default_ms", ctypes.c_double),
                 ("max_abs_err", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("admissible", ctypes.c_int), ("quad_ctas_per_sm", ctypes.c_int)]
+                ("admissible", ctypes.c_int), ("quad_ctas_per_sm", ctypes.c_int),
+                ("exposure_block", ctypes.c_int)]
 
 
 GL_FIT_DIM = 10
@@ -182,7 +183,7 @@ def load():
         lib.gl_autotune.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Times), vp, i32,
                                     vp, ctypes.POINTER(_TuneReport)]
         lib.gl_autotune.restype = i32
-        lib.gl_configure.argtypes = [vp, i32, i32, i32, i32]
+        lib.gl_configure.argtypes = [vp, i32, i32, i32, i32, i32]
         lib.gl_configure.restype = i32
         lib.gl_counts_enable.argtypes = [vp, i32]
         lib.gl_counts_enable.restype = i32
@@ -313,10 +314,10 @@ def gl_autotune(ctx, params: dict, t, out, precision: int = GL_FP32C, offsets=No
 
 
 def gl_configure(ctx, precision: int, threads: int = 0, nodes: int = 0,
-                 quad_ctas: int = 0) -> None:
+                 quad_ctas: int = 0, exposure_block: int = 0) -> None:
     """Set the light-curve configuration of a precision directly (0 = default)."""
     _check(ctx, load().gl_configure(ctx, int(precision), int(threads), int(nodes),
-                                    int(quad_ctas)))
+                                    int(quad_ctas), int(exposure_block)))
 
 
 def gl_flux_sky(ctx, x0, y0, z, k, f, eta, xi, u1, u2, out, precision: int = GL_FP32C,
@@ -589,8 +590,8 @@ class Context:
     def last_error(self) -> str:
         return gl_last_error(self.handle)
 
-    def configure(self, precision, threads=0, nodes=0, quad_ctas=0):
-        gl_configure(self.handle, precision, threads, nodes, quad_ctas)
+    def configure(self, precision, threads=0, nodes=0, quad_ctas=0, exposure_block=0):
+        gl_configure(self.handle, precision, threads, nodes, quad_ctas, exposure_block)
 
     def autotune(self, params, t, out, exptime, nsuper=None, nsuper_all=1, offsets=None,
                  precision=GL_FP32C, stream=None) -> dict:

@@ -42,7 +42,7 @@ constexpr int kNodes32 = 20;
 // count, set, flags, tau, midpoint state); plus three ints per exposure for
 // the kept-exposure list and the overflow list
 constexpr int64_t kItemMaxDefault = 1LL << 23;
-constexpr size_t kItemBytes = 5 * sizeof(double) + 9 * sizeof(int) + sizeof(gl::MidState);
+constexpr size_t kItemBytes = 4 * sizeof(double) + 6 * sizeof(int);
 
 __constant__ NodeRule<double> c_rule64;
 __constant__ NodeRule<double> c_rule64_wide;
@@ -234,10 +234,12 @@ __global__ void gl_maxdiff_kernel(const double* a, const double* b, int64_t n,
 //   gl_win_kernel    one thread per exposure: conservative FP32 window test and
 //                    the exact FP64 one; exposures outside get flux 1, the rest
 //                    are appended to a kept-exposure list
-//   gl_exp_kernel    one thread per kept exposure: midpoint state (FP64 Kepler),
-//                    the position and overlap class of each sub-exposure; items
-//                    that meet the disk go to a global queue (crossing items
-//                    from the back, whole-ellipse items from the front)
+//   gl_expgeo_kernel one thread per kept exposure: midpoint state (FP64 Kepler);
+//                    then the block's threads together: the position and overlap
+//                    class of each sub-exposure; items that meet the disk go to
+//                    global queues (crossing items from the back of one, whole
+//                    ellipses from its front, whole ellipses that may have two
+//                    maxima of g to a second)
 //   gl_items_quad_kernel   the quadrature of every queued item, warps spread over
 //                    the whole GPU, crossing (heavier) items first
 //   gl_items_sum_kernel    FP64 mean of each exposure, in sub-exposure order
@@ -259,9 +261,11 @@ __global__ void gl_maxdiff_kernel(const double* a, const double* b, int64_t n,
 //   phase 6  mean over the exposure's sub-exposures -> out
 //
 // Every exposure's midpoint state, every item's geometry and deficit come from
-// the same compiled functions (exposure_prep, item_geometry, item_deficit) and
-// every exposure is summed in sub-exposure order, so the two ways, and any
-// workspace size, give bit-identical results.
+// the same compiled functions (exposure_prep, item_geometry, item_deficit; the
+// FP32 Taylor geometry, taylor_item, is written with fixed-rounding operations
+// and gives the same bits inlined or not) and every exposure is summed in
+// sub-exposure order, so the two ways, and any workspace size, give
+// bit-identical results.
 struct LcArgs {
   const SetConst* sets;
   const double* t;
@@ -285,15 +289,11 @@ struct LcArgs {
   int n_smsp;                   // SM sub-partitions of the device (4 per SM)
   int64_t item_cap;
   int* ovlist;                  // kept-list indices of exposures left to the sum kernel
-  // per record: set, flags, tau, midpoint state; per item: record
-  int *rset, *rflag, *irec;
-  double* rtau;
-  gl::MidState* rmid;
 };
 
 enum : int {
   kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcOver = 6,
-  kIcValid = 7, kIcFetchP = 8, kIcHeavy = 9, kIcFetchH = 10, kIcSlots = 11,
+  kIcFetchP = 7, kIcHeavy = 8, kIcFetchH = 9, kIcSlots = 10,
   // per-sub-partition counters of crossing batches (32-bit, after the kIc slots)
   kSmspSlots = 1024,
   kIcWords = kIcSlots + kSmspSlots / 2   // 64-bit words zeroed by every step
@@ -398,12 +398,12 @@ template <typename R>
 __device__ __noinline__ int item_geometry(const SetConst& c, int flag, const gl::MidState& mid,
                                           double tau, int twice, R* x, R* y, R* o) {
   if (flag & kExpTaylor) {
-    float xf, yf, zf, of;
-    gl::taylor_position(mid, 0.5f * (float)twice * c.fsub_step, &xf, &yf, &zf, &of);
+    float xf, yf, of;
+    const int cls = gl::taylor_item(c, mid, twice, &xf, &yf, &of);
     *x = (R)xf;
     *y = (R)yf;
     *o = (R)of;
-    return gl::classify_t<float>(c.freq, xf, yf, zf, 1e-6f);
+    return cls;
   }
   double xd, yd, zd;
   gl::sky_position(c, tau + 0.5 * (double)twice * c.sub_step, &xd, &yd, &zd);
@@ -644,30 +644,40 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
   }
 }
 
-// Item pipeline, stage 2a: one thread per kept exposure: exact window and
-// midpoint state, stored in an exposure record with the exposure's range of
-// sub-exposure slots (one atomic add per block reserves the block's slots and
-// records).  If the workspace is full, the exposure goes to the overflow list,
-// finished by the sum kernel.
-// 64-thread blocks spread the FP64 work (the midpoint state) over every SM
-// even when few exposures are kept.
-constexpr int kExpThreads = 64;
-constexpr int kGeoThreads = 256;
+// Item pipeline, stage 2 (kept exposures and their sub-exposures in one kernel):
+// the first 64 threads of a 256-thread block take one kept exposure each: exact
+// window and FP64 midpoint state, kept in shared memory, with one atomic add each
+// reserving the block's item slots and records.  Then all 256 threads expand the
+// 64 exposures' sub-exposures, up to 1024 at a time (four per thread; item i
+// belongs to the exposure whose slot range holds i, found by binary search over
+// the block's offsets): FP32 Taylor position and overlap class (taylor_item, the
+// same fixed-rounding code as everywhere else, inlined so that a thread's four
+// items overlap), queued with one atomic add per pass and queue.  Exposures that
+// do not fit the workspace go to the overflow list.
+// NT = 64: every thread also takes an exposure (the most FP64 warps per SM, for
+// large batches); NT = 256: the expansion has four times the threads (shorter
+// per-thread chains, for small batches).  The autotuner chooses.
+constexpr int kFuseExp = 64;
 
-template <typename R>
-__global__ void __launch_bounds__(kExpThreads) gl_exp_kernel(LcArgs a) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) gl_expgeo_kernel(LcArgs a) {
+  constexpr int NE = kFuseExp, V = 4;
   __shared__ int warp_tot[32];
-  __shared__ long long s_base, s_rec;
-  __shared__ int s_fits;
+  __shared__ long long s_base, s_rec, s_q[3];
+  __shared__ int s_fits, s_total, s_n[3];
+  __shared__ int s_off[NE], s_st[NE], s_fl[NE], s_ns[NE];
+  __shared__ double s_tau[NE];
+  __shared__ gl::MidState s_mid[NE];
   const int tid = threadIdx.x;
   const long long nk = (long long)a.ictr[kIcKept];
-  for (long long k0 = (long long)blockIdx.x * kExpThreads; k0 < nk;
-       k0 += (long long)gridDim.x * kExpThreads) {
+  R* ipos = (R*)a.ipos;
+  R* idef = (R*)a.idef;
+  for (long long k0 = (long long)blockIdx.x * NE; k0 < nk; k0 += (long long)gridDim.x * NE) {
     const long long k = k0 + tid;
     int j = 0, st = 0, fl = kExpDead, ns = 0;
     double tau = 0.0;
     gl::MidState mid;
-    if (k < nk) {
+    if (tid < NE && k < nk) {
       j = a.klist[k];
       st = a.kset[k];
       const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)st * a.n_times;
@@ -676,94 +686,104 @@ __global__ void __launch_bounds__(kExpThreads) gl_exp_kernel(LcArgs a) {
       else ns = a.sets[st].nsuper;
     }
     int total, n_live;
-    const int off = block_scan<kExpThreads>(ns, warp_tot, &total);
-    const int roff = block_scan<kExpThreads>(ns > 0 ? 1 : 0, warp_tot, &n_live);
+    const int off = block_scan<NT>(ns, warp_tot, &total);
+    const int roff = block_scan<NT>(ns > 0 ? 1 : 0, warp_tot, &n_live);
     if (tid == 0) {
       long long b = 0, r = 0;
       int fits = 0;
       if (total > 0) {
         b = (long long)atomicAdd(&a.ictr[kIcItems], (unsigned long long)total);
         fits = b + total <= a.item_cap;
-        // records <= items <= item_cap; reservations are contiguous from slot 0,
-        // so the largest end of a fitting one bounds the filled slots
-        if (fits) {
-          r = (long long)atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_live);
-          atomicMax(&a.ictr[kIcValid], (unsigned long long)(b + total));
-        }
+        if (fits) r = (long long)atomicAdd(&a.ictr[kIcRecs], (unsigned long long)n_live);
       }
       s_base = b;
       s_rec = r;
       s_fits = fits;
+      s_total = total;
+      s_n[0] = s_n[1] = s_n[2] = 0;
+    }
+    if (tid < NE) {
+      s_off[tid] = off;
+      s_st[tid] = st;
+      s_fl[tid] = fl;
+      s_ns[tid] = ns;
+      s_tau[tid] = tau;
+      s_mid[tid] = mid;
     }
     __syncthreads();
     if (ns > 0) {
       if (s_fits) {
-        const long long r = s_rec + roff, first = s_base + off;
+        const long long r = s_rec + roff;
         a.rj[r] = j;
-        a.rfirst[r] = (int)first;
+        a.rfirst[r] = (int)(s_base + off);
         a.rns[r] = ns;
-        a.rset[r] = st;
-        a.rflag[r] = fl;
-        a.rtau[r] = tau;
-        a.rmid[r] = mid;
-        for (int q = 0; q < ns; ++q) a.irec[first + q] = (int)r;
       } else {
         a.ovlist[atomicAdd(&a.ictr[kIcOver], 1ull)] = (int)k;
       }
     }
-    __syncthreads();
-  }
-}
-
-// Item pipeline, stage 2b: one thread per sub-exposure slot: position and
-// overlap class; items that meet the disk are appended to the queue (one atomic
-// add per block and class), the others get a zero deficit.
-template <typename R>
-__global__ void __launch_bounds__(kGeoThreads) gl_geo_kernel(LcArgs a) {
-  __shared__ int s_nf, s_np, s_nh;
-  __shared__ long long s_qf, s_qp, s_qh;
-  const int tid = threadIdx.x;
-  const long long n = (long long)a.ictr[kIcValid];
-  R* ipos = (R*)a.ipos;
-  R* idef = (R*)a.idef;
-  for (long long g0 = (long long)blockIdx.x * kGeoThreads; g0 < n;
-       g0 += (long long)gridDim.x * kGeoThreads) {
-    const long long g = g0 + tid;
-    if (tid == 0) {
-      s_nf = 0;
-      s_np = 0;
-      s_nh = 0;
-    }
-    __syncthreads();
-    int cls = gl::kOut, slot = 0;
-    bool heavy = false;
-    if (g < n) {
-      const int r = a.irec[g];
-      const int st = a.rset[r], ns = a.rns[r], q = (int)(g - a.rfirst[r]);
-      R x, y, o;
-      cls = item_geometry<R>(a.sets[st], a.rflag[r], a.rmid[r], a.rtau[r], 2 * q + 1 - ns, &x, &y,
-                             &o);
-      if (cls == gl::kOut) {
-        idef[g] = R(0);
-      } else {
-        ipos[3 * g] = x;
-        ipos[3 * g + 1] = y;
-        ipos[3 * g + 2] = o;
-        a.iset[g] = st;
-        heavy = cls == gl::kFull && gl::maybe_two_maxima(a.sets[st], (float)x, (float)y);
-        slot = atomicAdd(heavy ? &s_nh : cls == gl::kFull ? &s_nf : &s_np, 1);
+    if (s_fits) {
+      const int tot = s_total;
+      for (int i0 = 0; i0 < tot; i0 += V * NT) {
+        int qk[V], slot[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int i = i0 + tid + v * NT;
+          qk[v] = -1;
+          slot[v] = 0;
+          if (i < tot) {
+            int lo = 0, hi = NE;   // largest e with s_off[e] <= i (it has items)
+            while (hi - lo > 1) {
+              const int md = (lo + hi) >> 1;
+              if (s_off[md] <= i) lo = md;
+              else hi = md;
+            }
+            const int e = lo, q = i - s_off[lo];
+            const SetConst& c = a.sets[s_st[e]];
+            const long long g = s_base + i;
+            R x, y, o;
+            int cls;
+            if (s_fl[e] & kExpTaylor) {
+              float xf, yf, of;
+              cls = gl::taylor_item(c, s_mid[e], 2 * q + 1 - s_ns[e], &xf, &yf, &of);
+              x = (R)xf;
+              y = (R)yf;
+              o = (R)of;
+            } else {
+              cls = item_geometry<R>(c, s_fl[e], s_mid[e], s_tau[e], 2 * q + 1 - s_ns[e], &x, &y,
+                                     &o);
+            }
+            if (cls == gl::kOut) {
+              idef[g] = R(0);
+            } else {
+              ipos[3 * g] = x;
+              ipos[3 * g + 1] = y;
+              ipos[3 * g + 2] = o;
+              a.iset[g] = s_st[e];
+              qk[v] = cls == gl::kPartial ? 1
+                                          : (gl::maybe_two_maxima(c, (float)x, (float)y) ? 2 : 0);
+              slot[v] = atomicAdd(&s_n[qk[v]], 1);
+            }
+          }
+        }
+        __syncthreads();
+        if (tid < 3) {
+          const int ic = tid == 0 ? kIcFull : (tid == 1 ? kIcPart : kIcHeavy);
+          s_q[tid] = s_n[tid] ? (long long)atomicAdd(&a.ictr[ic], (unsigned long long)s_n[tid]) : 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int g = (int)(s_base + i0 + tid + v * NT);
+          if (qk[v] == 0) a.iq[s_q[0] + slot[v]] = g;
+          else if (qk[v] == 1) a.iq[a.item_cap - 1 - (s_q[1] + slot[v])] = g;
+          else if (qk[v] == 2) a.ihq[s_q[2] + slot[v]] = g;
+        }
+        __syncthreads();
+        if (tid < 3) s_n[tid] = 0;
+        __syncthreads();
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      s_qf = s_nf ? (long long)atomicAdd(&a.ictr[kIcFull], (unsigned long long)s_nf) : 0;
-      s_qp = s_np ? (long long)atomicAdd(&a.ictr[kIcPart], (unsigned long long)s_np) : 0;
-      s_qh = s_nh ? (long long)atomicAdd(&a.ictr[kIcHeavy], (unsigned long long)s_nh) : 0;
-    }
-    __syncthreads();
-    if (heavy) a.ihq[s_qh + slot] = (int)g;
-    else if (cls == gl::kFull) a.iq[s_qf + slot] = (int)g;
-    else if (cls == gl::kPartial) a.iq[a.item_cap - 1 - (s_qp + slot)] = (int)g;
   }
 }
 
@@ -1605,7 +1625,8 @@ struct gl_context {
   struct LcCfg {
     int threads, tile, cap, rule_idx;
     int qvar;   // item pipeline: quadrature kernel variant (0: MINB = 4, 1: MINB = 8)
-  } cfg[2] = {{256, 256, 1024, -1, 0}, {256, 256, 1024, -1, 0}};   // FP64, FP32C
+    int gvar;   // item pipeline: exposure kernel block (0: 256 threads, 1: 64 threads)
+  } cfg[2] = {{256, 256, 1024, -1, 0, 0}, {256, 256, 1024, -1, 0, 0}};   // FP64, FP32C
   struct TuneInfo {
     int tuned = 0, candidates = 0, admissible = 0;
     double best_ms = 0, default_ms = 0, max_err = 0;
@@ -1634,7 +1655,7 @@ struct gl_context {
   double* d_ens = nullptr;
   size_t ens_cap = 0;
   int qocc[2][2] = {{0, 0}, {0, 0}};       // resident quadrature CTAs per SM (FP64, FP32C) x variant
-  int eocc[2] = {0, 0};                    // resident kept-exposure CTAs per SM
+  int eocc[2][2] = {{0, 0}, {0, 0}};       // resident exposure-kernel CTAs per SM x variant
   // graph cache: one captured step per distinct argument set
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
@@ -1808,11 +1829,6 @@ void item_arrays(void* base, int64_t cap, int64_t n_total, size_t rsize, LcArgs*
   a->rfirst = (int*)take(sizeof(int) * (size_t)cap);
   a->rns = (int*)take(sizeof(int) * (size_t)cap);
   a->item_cap = cap;
-  a->rset = (int*)take(sizeof(int) * (size_t)cap);
-  a->rflag = (int*)take(sizeof(int) * (size_t)cap);
-  a->irec = (int*)take(sizeof(int) * (size_t)cap);
-  a->rtau = (double*)take(sizeof(double) * (size_t)cap);
-  a->rmid = (gl::MidState*)take(sizeof(gl::MidState) * (size_t)cap);
   a->klist = (int*)take(sizeof(int) * (size_t)n_total);
   a->kset = (int*)take(sizeof(int) * (size_t)n_total);
   a->ovlist = (int*)take(sizeof(int) * (size_t)n_total);
@@ -1827,13 +1843,15 @@ template <typename R>
 int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   const int qvar = ctx->cfg[sizeof(R) == 4 ? 1 : 0].qvar;
   int& qocc = ctx->qocc[sizeof(R) == 4 ? 1 : 0][qvar];
-  int& eocc = ctx->eocc[sizeof(R) == 4 ? 1 : 0];
-  if (qocc == 0) {
+  const int gvar = ctx->cfg[sizeof(R) == 4 ? 1 : 0].gvar;
+  int& eocc = ctx->eocc[sizeof(R) == 4 ? 1 : 0][gvar];
+  if (qocc == 0 || eocc == 0) {
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                      &qocc, qvar ? gl_items_quad_kernel<R, 128, 8> : gl_items_quad_kernel<R, 128, 4>,
                      128, 0));
-    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&eocc, gl_exp_kernel<R>,
-                                                               kExpThreads, 0));
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &eocc, gvar ? gl_expgeo_kernel<R, 64> : gl_expgeo_kernel<R, 256>,
+                     gvar ? 64 : 256, 0));
     if (qocc < 1 || eocc < 1) return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
   }
   // (the counters were zeroed by the setup kernel of this step)
@@ -1842,10 +1860,12 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   if (wb < 1) wb = 1;
   long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
   gl_win_kernel<<<(int)wb, 256, 0, st>>>(args);
-  gl_exp_kernel<R><<<ctx->sms * eocc, kExpThreads, 0, st>>>(args);
-  gl_geo_kernel<R><<<ctx->sms * 8, kGeoThreads, 0, st>>>(args);
+  if (gvar)
+    gl_expgeo_kernel<R, 64><<<ctx->sms * eocc, 64, 0, st>>>(args);
+  else
+    gl_expgeo_kernel<R, 256><<<ctx->sms * eocc, 256, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_CURVE, pe, st);
-  ctx->launches += 3;
+  ctx->launches += 2;
   GL_CUDA(ctx, cudaGetLastError());
   pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
   if (qvar)
@@ -1886,7 +1906,7 @@ int launch_lc_nt(gl_context* ctx, LcArgs args, int occ_slot, cudaStream_t st) {
 bool lc_ready(const gl_context* ctx, int prec, bool items) {
   if (items) {
     const int pi = prec == GL_FP64 ? 0 : 1;
-    return ctx->qocc[pi][ctx->cfg[pi].qvar] != 0;
+    return ctx->qocc[pi][ctx->cfg[pi].qvar] != 0 && ctx->eocc[pi][ctx->cfg[pi].gvar] != 0;
   }
   const gl_context::LcCfg& cf = ctx->cfg[prec == GL_FP64 ? 0 : 1];
   int slot = (prec == GL_FP64 ? 0 : 1) + (ctx->counting ? 2 : 0) + (cf.threads == 128 ? 4 : 0);
@@ -2126,7 +2146,8 @@ int gl_item_pipeline(gl_context* ctx, int on, int64_t max_items) {
   return GL_OK;
 }
 
-int gl_configure(gl_context* ctx, gl_precision prec, int threads, int nodes, int quad_ctas) {
+int gl_configure(gl_context* ctx, gl_precision prec, int threads, int nodes, int quad_ctas,
+                 int exposure_block) {
   if (!ctx) return GL_EINVAL;
   ctx->err[0] = 0;
   if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision");
@@ -2134,6 +2155,8 @@ int gl_configure(gl_context* ctx, gl_precision prec, int threads, int nodes, int
     return fail(ctx, GL_EINVAL, "threads must be 0, 128 or 256");
   if (quad_ctas != 0 && quad_ctas != 4 && quad_ctas != 8)
     return fail(ctx, GL_EINVAL, "quad_ctas must be 0, 4 or 8");
+  if (exposure_block != 0 && exposure_block != 64 && exposure_block != 256)
+    return fail(ctx, GL_EINVAL, "exposure_block must be 0, 64 or 256");
   int ni = -1;
   if (nodes != 0) {
     if (prec == GL_FP64) return fail(ctx, GL_EINVAL, "the FP64 path has a fixed order");
@@ -2142,7 +2165,8 @@ int gl_configure(gl_context* ctx, gl_precision prec, int threads, int nodes, int
     if (ni < 0) return fail(ctx, GL_EINVAL, "nodes must be 0, 16, 20, 24 or 28");
   }
   const int th = threads ? threads : 256;
-  ctx->cfg[prec == GL_FP64 ? 0 : 1] = {th, th, 4 * th, ni, quad_ctas == 8 ? 1 : 0};
+  ctx->cfg[prec == GL_FP64 ? 0 : 1] = {th, th, 4 * th, ni, quad_ctas == 8 ? 1 : 0,
+                                       exposure_block == 64 ? 1 : 0};
   drop_graphs(ctx);
   return GL_OK;
 }
@@ -2168,23 +2192,25 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
   if (!ctx->d_err) GL_CUDA(ctx, cudaMalloc(&ctx->d_err, sizeof(unsigned long long)));
   // reference: the FP64 path with its default configuration
   gl_context::LcCfg saved[2] = {ctx->cfg[0], ctx->cfg[1]};
-  ctx->cfg[0] = {256, 256, 1024, -1, 0};
+  ctx->cfg[0] = {256, 256, 1024, -1, 0, 0};
   rc = gl_lightcurve_batch(ctx, p, tm, ctx->d_ref, GL_FP64, stream);
   if (rc) return rc;
   const int pi = prec == GL_FP64 ? 0 : 1;
   const double tol = prec == GL_FP64 ? 1e-10 : 1e-7;
   // The second axis is the tile kernel's CTA size, or with the item pipeline
   // (whose launch shapes are fixed) the quadrature kernel's variant.
-  struct Cand { int threads, nodes_idx, qvar; };
-  Cand cands[8];
+  struct Cand { int threads, nodes_idx, qvar, gvar; };
+  Cand cands[16];
   int nc = 0;
-  for (int ax = 0; ax < 2; ++ax) {
-    const int th = ctx->item_pipeline ? 256 : (ax ? 256 : 128);
-    const int qv = ctx->item_pipeline ? ax : 0;
-    if (prec == GL_FP64) {
-      cands[nc++] = {th, -1, qv};
-    } else {
-      for (int ni = 0; ni < 4; ++ni) cands[nc++] = {th, ni, qv};
+  for (int gv = 0; gv < (ctx->item_pipeline ? 2 : 1); ++gv) {
+    for (int ax = 0; ax < 2; ++ax) {
+      const int th = ctx->item_pipeline ? 256 : (ax ? 256 : 128);
+      const int qv = ctx->item_pipeline ? ax : 0;
+      if (prec == GL_FP64) {
+        cands[nc++] = {th, -1, qv, gv};
+      } else {
+        for (int ni = 0; ni < 4; ++ni) cands[nc++] = {th, ni, qv, gv};
+      }
     }
   }
   cudaEvent_t e0, e1;
@@ -2205,7 +2231,7 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
   int best = -1, admissible = 0;
   for (int ci = 0; ci < nc && rc == GL_OK; ++ci) {
     ctx->cfg[pi] = {cands[ci].threads, cands[ci].threads, 4 * cands[ci].threads,
-                    cands[ci].nodes_idx, cands[ci].qvar};
+                    cands[ci].nodes_idx, cands[ci].qvar, cands[ci].gvar};
     drop_graphs(ctx);
     ctx->graphs = was_graph;
     rc = gl_lightcurve_batch(ctx, p, tm, out, prec, stream);
@@ -2241,7 +2267,7 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
         best_err = err;
       }
     }
-    if (cands[ci].threads == 256 && cands[ci].qvar == 0 &&
+    if (cands[ci].threads == 256 && cands[ci].qvar == 0 && cands[ci].gvar == 0 &&
         (cands[ci].nodes_idx == 1 || cands[ci].nodes_idx == -1))
       default_ms = ok ? ms : 0.0;
     ctx->graphs = false;
@@ -2257,7 +2283,7 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
   ctx->cfg[1] = saved[1];
   if (best >= 0)
     ctx->cfg[pi] = {cands[best].threads, cands[best].threads, 4 * cands[best].threads,
-                    cands[best].nodes_idx, cands[best].qvar};
+                    cands[best].nodes_idx, cands[best].qvar, cands[best].gvar};
   ctx->profiling = was_prof;
   ctx->counting = was_count;
   ctx->graphs = was_graph;
@@ -2282,6 +2308,7 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
     rep->admissible = admissible;
     rep->quad_ctas_per_sm =
         ctx->item_pipeline ? ctx->qocc[pi][cands[best].qvar] : 0;
+    rep->exposure_block = ctx->item_pipeline ? (cands[best].gvar ? 64 : 256) : 0;
   }
   return GL_OK;
 }

@@ -1642,17 +1642,63 @@ GL_HD MidState mid_state_at(const SetConst& c, double tau, bool derivs) {
   return m;
 }
 
+// FP32 operations with fixed rounding (no contraction left to the compiler), so
+// that code built from them gives the same bits wherever it is inlined.
+GL_HD float f_fma(float a, float b, float c) {
+#if defined(__CUDA_ARCH__)
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
+}
+GL_HD float f_mul(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+GL_HD float f_add(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+GL_HD float f_sqrt(float a) {
+#if defined(__CUDA_ARCH__)
+  return __fsqrt_rn(a);
+#else
+  return sqrtf(a);
+#endif
+}
+
 // Position dt after the midpoint by the cubic Taylor step, in FP32.  The step
 // is small (|v dt| < 0.1 stellar radii), so its rounding error is far below
 // the FP32 quadrature's.
 GL_HD void taylor_position(const MidState& m, float dt, float* x, float* y, float* z,
                            float* omr2) {
   float dd[3];
-  for (int k = 0; k < 3; ++k) dd[k] = ((m.d3[k] * dt + m.d2[k]) * dt + m.d1[k]) * dt;
-  *x = m.x + dd[0];
-  *y = m.y + dd[1];
-  *z = m.z + dd[2];
-  *omr2 = m.omr2 - 2.0f * (m.x * dd[0] + m.y * dd[1]) - (dd[0] * dd[0] + dd[1] * dd[1]);
+  for (int k = 0; k < 3; ++k) dd[k] = f_mul(f_fma(f_fma(m.d3[k], dt, m.d2[k]), dt, m.d1[k]), dt);
+  *x = f_add(m.x, dd[0]);
+  *y = f_add(m.y, dd[1]);
+  *z = f_add(m.z, dd[2]);
+  const float lin = f_fma(m.x, dd[0], f_mul(m.y, dd[1]));
+  const float quad = f_fma(dd[0], dd[0], f_mul(dd[1], dd[1]));
+  *omr2 = f_add(f_fma(-2.0f, lin, m.omr2), -quad);
+}
+
+// Position and overlap class of the sub-exposure at offset (twice / 2) x the
+// sub-exposure step from the midpoint, by the Taylor step (fixed-rounding FP32).
+GL_HD int taylor_item(const SetConst& c, const MidState& m, int twice, float* x, float* y,
+                      float* omr2) {
+  float z;
+  taylor_position(m, f_mul(0.5f * (float)twice, c.fsub_step), x, y, &z, omr2);
+  if (z > 0.0f) return kOut;
+  const float rho = f_sqrt(f_fma(*x, *x, f_mul(*y, *y)));
+  if (rho >= f_add(f_add(1.0f, c.freq), 1e-6f)) return kOut;
+  if (f_add(rho, c.freq) <= f_add(1.0f, -1e-6f)) return kFull;
+  return kPartial;
 }
 
 // Deficit (1 - flux) of one sub-exposure at the given FP32 geometry.

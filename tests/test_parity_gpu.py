@@ -417,11 +417,11 @@ def test_autotuner_keeps_only_tolerance_passing_configurations(ctx, mcmc):
     t, exp = _dev(wl["t"]), _dev(wl["exptime"])
     out = torch.empty(256 * len(wl["t"]), dtype=torch.float64, device="cuda")
     rep = ctx.autotune(p, t, out, exp, nsuper_all=15, precision=binding.GL_FP32C)
-    assert rep["candidates"] == 8 and rep["admissible"] >= 1
+    assert rep["candidates"] == 16 and rep["admissible"] >= 1
     assert rep["max_abs_err"] <= 0.9e-7 and rep["threads"] in (128, 256)
     assert rep["nodes"] in (16, 20, 24, 28)
     # with the item pipeline (the default) the second axis is the quadrature kernel variant
-    assert rep["quad_ctas_per_sm"] >= 4
+    assert rep["quad_ctas_per_sm"] >= 4 and rep["exposure_block"] in (64, 256)
     # later calls use the chosen configuration and stay within tolerance of the oracle
     out2 = torch.empty_like(out)
     ctx.lightcurve(p, t, out2, exp, nsuper_all=15, precision=binding.GL_FP32C)
@@ -436,12 +436,12 @@ def test_configure_pins_a_configuration(ctx, mcmc):
     p = {k: _dev(v) for k, v in product_params(wl).items()}
     t, exp = _dev(wl["t"]), _dev(wl["exptime"])
     out = torch.empty(256 * len(wl["t"]), dtype=torch.float64, device="cuda")
-    for nodes, quad in ((16, 4), (16, 8), (28, 8)):
-        ctx.configure(binding.GL_FP32C, nodes=nodes, quad_ctas=quad)
+    for nodes, quad, eb in ((16, 4, 256), (16, 8, 64), (28, 8, 256), (20, 4, 64)):
+        ctx.configure(binding.GL_FP32C, nodes=nodes, quad_ctas=quad, exposure_block=eb)
         ctx.lightcurve(p, t, out, exp, nsuper_all=15, precision=binding.GL_FP32C)
         got = out.cpu().numpy().reshape(256, -1)
         _compare(got[idx].ravel(), ref.ravel(), binding.GL_FP32C)
-    for bad in (dict(nodes=17), dict(quad_ctas=5), dict(threads=64)):
+    for bad in (dict(nodes=17), dict(quad_ctas=5), dict(threads=64), dict(exposure_block=128)):
         with pytest.raises(binding.GLError):
             ctx.configure(binding.GL_FP32C, **bad)
     with pytest.raises(binding.GLError):
