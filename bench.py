@@ -51,7 +51,7 @@ def alu_peaks(sm_mhz: float):
 
 # Algorithmic work per unit of the FP32C light-curve step (flops, FMA = 2),
 # counted from the source, by kernel:
-#   exposures (gl_win_kernel + gl_exp_kernel + gl_geo_kernel): FP32 per exposure
+#   exposures (gl_win_kernel + gl_expgeo_kernel): FP32 per exposure
 #         window test 12, per sub-exposure position and class 40; FP64 per
 #         in-window exposure 10 (exact window), midpoint Kepler state 90 (one
 #         Halley step with its series, second-order update, sky position), per
@@ -93,7 +93,7 @@ def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak:
             "kernel_ms": ms}
 
 
-KERNEL_NAMES = {"tiles": "gl_win_kernel+gl_exp_kernel+gl_geo_kernel",
+KERNEL_NAMES = {"tiles": "gl_win_kernel+gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
 
 
