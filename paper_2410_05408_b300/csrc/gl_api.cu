@@ -45,6 +45,15 @@ constexpr int64_t kItemMaxDefault = 1LL << 23;
 constexpr size_t kItemBytes = 4 * sizeof(double) + 6 * sizeof(int);
 
 __constant__ NodeRule<double> c_rule64;
+__constant__ double c_inv_n[65];   // 1 / n for n = 1..64 (entry 0 unused)
+
+// Exposure flux from S, the FP64 sum of its n sub-exposure deficits: the mean of
+// 1 - deficit, 1 - S / n (one FMA with 1/n from a table; every path of the light
+// curve ends here, so they agree to the bit).
+__device__ __forceinline__ double exposure_mean(double S, int n) {
+  const double inv = n <= 64 ? c_inv_n[n] : 1.0 / (double)n;
+  return fma(-S, inv, 1.0);
+}
 __constant__ NodeRule<double> c_rule64_wide;
 __constant__ NodeRule<float> c_rule32;                 // default order (kNodes32)
 // orders the autotuner may choose for the FP32C light-curve kernel
@@ -432,9 +441,9 @@ __device__ double exposure_local(const SetConst& c, int flag, const gl::MidState
     R x, y, o;
     const int cls = item_geometry<R>(c, flag, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
     const R d = cls == gl::kOut ? R(0) : item_deficit<R>(c, x, y, o, cls, base);
-    acc += 1.0 - (double)d;
+    acc += (double)d;
   }
-  return acc / ns;
+  return exposure_mean(acc, ns);
 }
 
 template <typename R, int NT, bool COUNT>
@@ -583,14 +592,14 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
       for (int i = tid; i < m; i += NT) {
         int b0 = max(e_base[i], r0), b1 = min(e_base[i + 1], r0 + nr);
         double acc = e_acc[i];
-        for (int it = b0; it < b1; ++it) acc += 1.0 - (double)it_def[it - r0];
+        for (int it = b0; it < b1; ++it) acc += (double)it_def[it - r0];
         e_acc[i] = acc;
       }
       __syncthreads();
     }
     // ---- phase 6: exposure means (exposures that failed the exact test are done)
     for (int i = tid; i < m; i += NT)
-      if (e_ns[i] > 0) a.out[e_j[i]] = e_acc[i] / e_ns[i];
+      if (e_ns[i] > 0) a.out[e_j[i]] = exposure_mean(e_acc[i], e_ns[i]);
     __syncthreads();
   }
 }
@@ -883,8 +892,8 @@ __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
       const int ns = a.rns[r];
       const long long f = a.rfirst[r];
       double acc = 0.0;
-      for (int q = 0; q < ns; ++q) acc += 1.0 - (double)idef[f + q];
-      a.out[a.rj[r]] = acc / ns;
+      for (int q = 0; q < ns; ++q) acc += (double)idef[f + q];
+      a.out[a.rj[r]] = exposure_mean(acc, ns);
     } else {
       const int k = a.ovlist[r - nrec];
       const int j = a.klist[k], st = a.kset[k];
@@ -1599,6 +1608,12 @@ cudaError_t ensure_device_tables(int device) {
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule64_wide, &r64w, sizeof r64w);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32, &r32, sizeof r32);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rule32_tuned, rt, sizeof rt);
+  if (e == cudaSuccess) {
+    double inv[65];
+    inv[0] = 0.0;
+    for (int n = 1; n <= 64; ++n) inv[n] = 1.0 / (double)n;
+    e = cudaMemcpyToSymbol(c_inv_n, inv, sizeof inv);
+  }
   if (e == cudaSuccess) g_dev_ready[device] = 1;
   return e;
 }
