@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
                                                        SetConst* sets, int* status,
                                                        unsigned long long* zero, int n_zero) {
   __shared__ double sh_s[4][32], sh_c[4][32], sh_cb[32];
-  __shared__ int sh_win[32];
+  __shared__ int sh_win[32], sh_valid[32];
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
   if (zero)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_zero; i += gridDim.x * blockDim.x)
@@ -133,9 +133,11 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
   int orbit_ok = 0;
   if (live) {
     SetConst* c = sets + s;
+    // four FP64 chains of similar length, one per warp
     if (role == 0) {
       orbit_ok = gl::set_orbit(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s], sh_s[0][lane],
                                sh_c[0][lane], c);
+      gl::set_kepler(c);   // (meaningless for an invalid orbit; such sets are never used)
     } else if (role == 1) {
       const double g = p.g ? p.g[s] : 0.0, f = p.f[s];
       if (g != 0.0)
@@ -143,9 +145,6 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
                                sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
       else
         gl::set_shape(p.k[s], f, cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
-      const double cax = p.k[s] * gl::rcp64(cb);   // c = k ((1 - f)(1 - g))^(-1/3)
-      gl::set_body(cax * (1.0 - f), cax * (1.0 - g), cax, sh_s[3][lane], sh_c[3][lane],
-                   sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
     } else if (role == 2) {
       const double period = p.period[s], invP = gl::rcp64(period);
       sh_win[lane] = gl::set_window(p.t0[s], period, p.a_rs[s], p.ecc[s], p.omega[s],
@@ -153,18 +152,21 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
                                     p.exptime[s], p.nsuper ? p.nsuper[s] : p.nsuper_all, c);
     } else {
       gl::set_ld(p.u1[s], p.u2[s], c);
+      const double g = p.g ? p.g[s] : 0.0, f = p.f[s];
+      const double cax = p.k[s] * gl::rcp64(cb);   // c = k ((1 - f)(1 - g))^(-1/3)
+      gl::set_body(cax * (1.0 - f), cax * (1.0 - g), cax, sh_s[3][lane], sh_c[3][lane],
+                   sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
+      const int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
+      const double zeta = p.zeta ? p.zeta[s] : 0.0;
+      sh_valid[lane] = isfinite(g) && g >= 0.0 && g < 1.0 && isfinite(zeta) &&
+                       gl::set_valid(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s],
+                                     p.omega[s], p.k[s], p.f[s], p.eta[s], p.xi[s],
+                                     p.u1[s], p.u2[s], p.exptime[s], ns);
     }
   }
   __syncthreads();
-  if (!live) return;
-  if (role == 3) gl::set_kepler(sets + s);   // reads the orbit role 0 wrote
-  if (role != 0) return;
-  const int ns = p.nsuper ? p.nsuper[s] : p.nsuper_all;
-  const double g = p.g ? p.g[s] : 0.0, zeta = p.zeta ? p.zeta[s] : 0.0;
-  const bool ok = orbit_ok && isfinite(g) && g >= 0.0 && g < 1.0 && isfinite(zeta) &&
-                  gl::set_valid(p.t0[s], p.period[s], p.a_rs[s], p.b[s], p.ecc[s],
-                                p.omega[s], p.k[s], p.f[s], p.eta[s], p.xi[s],
-                                p.u1[s], p.u2[s], p.exptime[s], ns);
+  if (!live || role != 0) return;
+  const bool ok = orbit_ok && sh_valid[lane];
   sets[s].flags = ok ? sh_win[lane] : gl::kSetInvalid;
   if (!ok) atomicOr(status, kStatusInvalidSet);
   if (offsets) {
