@@ -89,6 +89,30 @@ def test_host_and_device_buffers_agree(ctx, prec):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_central_chords_of_strongly_flattened_planets(ctx, prec):
+    """Chords through the middle of the disk with f up to 0.9 and the spin axis near
+    the sky plane: whole-ellipse items near the centre, where g(th) may have two
+    maxima (the separate queue, two mapped arcs), and the single-maximum items
+    around them (Newton's maximum); both precisions against the oracle."""
+    import oracle
+    n = 6
+    params = dict(t0=np.zeros(n), period=np.full(n, 542.0), a_rs=np.full(n, 230.0),
+                  b=np.array([0.0, 0.02, 0.05, 0.0, 0.1, 0.03]), ecc=np.zeros(n),
+                  omega=np.full(n, 0.5 * math.pi),
+                  k=np.array([0.1, 0.15, 0.2, 0.12, 0.18, 0.2]),
+                  f=np.array([0.6, 0.8, 0.7, 0.85, 0.5, 0.9]),
+                  eta=np.array([0.0, 0.1, 0.2, 0.05, 0.0, 0.3]),
+                  xi=np.array([0.0, 0.5, 1.0, 1.5, 2.0, 2.5]),
+                  u1=np.full(n, 0.4), u2=np.full(n, 0.25))
+    t = np.linspace(-0.25, 0.25, 80)   # +- 6 h about mid-transit
+    wl = dict(params=params, t=t, offsets=None, exptime=np.full(n, 10.0 / 1440.0), nsuper=5)
+    ref = oracle.lightcurve(oracle_params(wl), t, wl["exptime"], 5)
+    got = _run(ctx, wl, prec).reshape(n, -1)
+    assert np.mean(ref < 1.0) > 0.5
+    _compare(got.ravel(), np.asarray(ref).ravel(), prec)
+
+
 # ---------------------------------------------------------------- MCMC batch
 @pytest.fixture(scope="module")
 def mcmc():
