@@ -1252,6 +1252,27 @@ GL_HD void snapped_integrands(T x0, T y0, T dx, T dy1, T dy2, T ct, T st, T* ff,
   }
 }
 
+// The two arcs into which two directions u0, u1 split the turn: the
+// counter-clockwise one from u0 to u1 (half-width h = Delta / 2, Delta in
+// (0, 2 pi], its middle u0 rotated by h) and the rest (half-width pi - h, middle
+// opposite).  Built from the angle alone, so no arc end can sit at a frame's
+// t = infinity (two maxima exactly opposite each other are a case of symmetric
+// geometry).
+template <typename R>
+GL_HD void split_turn(R c0, R s0, R c1, R s1, R* acm, R* asn, R* ah) {
+  R d = m_atan2(c0 * s1 - s0 * c1, c0 * c1 + s0 * s1);
+  if (!(d > R(0))) d += R(2 * kPi);
+  const R h = R(0.5) * d;
+  R sh, ch;
+  sincos_<R>(h, &sh, &ch);
+  acm[0] = c0 * ch - s0 * sh;
+  asn[0] = s0 * ch + c0 * sh;
+  ah[0] = h;
+  acm[1] = -acm[0];
+  asn[1] = -asn[0];
+  ah[1] = R(kPi) - h;
+}
+
 // The arcs (mid-direction cos/sin, half-width) into which the whole turn of a
 // boundary lying inside the disk is split for the f_lin quadrature: at the two
 // inner maxima when there are two, otherwise one arc whose two ends meet at the
@@ -1260,20 +1281,9 @@ template <typename R>
 GL_HD void whole_arcs(const Geo<R>& g, const Trig2<R>& tg, int nmax, const R* cmx, const R* smx,
                       R* acm, R* asn, R* ah, int* na) {
   if (nmax == 2) {
-    Frame<R> fr = make_frame<R>(tg);
-    R ta = frame_t<R>(fr, cmx[0], smx[0]), tb2 = frame_t<R>(fr, cmx[1], smx[1]);
-    if (m_finite(ta) && m_finite(tb2)) {
-      R ca = cmx[0], sa = smx[0], cb = cmx[1], sb = smx[1];
-      if (ta > tb2) {
-        R tmp = ta; ta = tb2; tb2 = tmp;
-        tmp = ca; ca = cb; cb = tmp;
-        tmp = sa; sa = sb; sb = tmp;
-      }
-      frame_arc<R>(tb2 - ta, R(1) + ta * tb2, false, ca, sa, &ah[0], &acm[0], &asn[0]);
-      frame_arc<R>(ta - tb2, R(1) + ta * tb2, true, cb, sb, &ah[1], &acm[1], &asn[1]);
-      *na = 2;
-      return;
-    }
+    split_turn<R>(cmx[0], smx[0], cmx[1], smx[1], acm, asn, ah);
+    *na = 2;
+    return;
   }
   R cs, ss;
   if (nmax >= 1) {
@@ -1465,22 +1475,9 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
     }
     I[1] = lin_full<R>(g, cs, ss, rule);
   } else {
-    Frame<R> fr = make_frame<R>(tg);
-    R ta = frame_t<R>(fr, cmx[0], smx[0]), tb2 = frame_t<R>(fr, cmx[1], smx[1]);
-    R ca = cmx[0], sa = smx[0], cb = cmx[1], sb = smx[1];
-    if (!m_finite(ta) || !m_finite(tb2)) {
-      I[1] = lin_full<R>(g, cmx[0], smx[0], rule);
-      return;
-    }
-    if (ta > tb2) {
-      R tmp = ta; ta = tb2; tb2 = tmp;
-      tmp = ca; ca = cb; cb = tmp;
-      tmp = sa; sa = sb; sb = tmp;
-    }
-    R h1, cm1, sm1, h2, cm2, sm2;
-    frame_arc<R>(tb2 - ta, R(1) + ta * tb2, false, ca, sa, &h1, &cm1, &sm1);
-    frame_arc<R>(ta - tb2, R(1) + ta * tb2, true, cb, sb, &h2, &cm2, &sm2);
-    I[1] = lin_arc<R>(g, cm1, sm1, h1, rule) + lin_arc<R>(g, cm2, sm2, h2, rule);
+    R acm[2], asn[2], ah[2];
+    split_turn<R>(cmx[0], smx[0], cmx[1], smx[1], acm, asn, ah);
+    I[1] = lin_arc<R>(g, acm[0], asn[0], ah[0], rule) + lin_arc<R>(g, acm[1], asn[1], ah[1], rule);
   }
 }
 
