@@ -93,11 +93,17 @@ def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak:
             "kernel_ms": ms}
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, summed over
+# the kernels of the group) from one ncu capture of the current kernels on the
+# workload named; other workloads report null.
+TRAFFIC = {("mcmc_batch", "quadrature"): 3.168e6 + 3.7e3 + 1.011e6,
+           ("mcmc_batch", "tiles"): 0.139e6 + 0.308e6 + 1.5e3}
+
 KERNEL_NAMES = {"tiles": "gl_win_kernel+gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
 
 
-def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float) -> dict:
+def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float, workload: str = "") -> dict:
     """ALU roofline of the dominant kernel of the FP32C step (the one with the
     largest measured time), with every kernel's own figures beside it."""
     flops = kernel_flops(c)
@@ -105,7 +111,7 @@ def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float) -> dict:
            for k in flops if kern.get(k)}
     top = max(per, key=lambda k: per[k]["kernel_ms"])
     line = dict(per[top])
-    line.update({"kernel": KERNEL_NAMES[top], "traffic": None,
+    line.update({"kernel": KERNEL_NAMES[top], "traffic": TRAFFIC.get((workload, top)),
                  "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x "
                                 "max SM clock",
                  "kernels": {KERNEL_NAMES[k]: {"ms": v["kernel_ms"], "pipe": v["pipe"],
@@ -871,7 +877,7 @@ def main():
         "workload_counts": counts,
         "autotune": tune,
         "autotune_fp64": tune64,
-        "roofline": roofline(counts, kern32, fp32_peak, fp64_peak),
+        "roofline": roofline(counts, kern32, fp32_peak, fp64_peak, args.workload),
         "gpu_launches": launches,
         "status": status,
         "clocks": clocks,
