@@ -22,6 +22,20 @@ import numpy as np
 from . import binding, inputs
 
 N_BINS = binding.SUR_BINS
+WIDTHS = (7, 256, 256, 256, 256, 1)
+
+
+def init_params(seed: int = 0, widths=WIDTHS) -> np.ndarray:
+    """He-style uniform initial parameters in the layout gl_mlp expects: per layer
+    the weights (fan_in x fan_out, row-major, U(-sqrt(6 / fan_in), +)) then the
+    biases (U(-0.1, 0.1)), layers in order, as one float32 vector."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fi, fo in zip(widths[:-1], widths[1:]):
+        lim = math.sqrt(6.0 / fi)
+        parts.append(rng.uniform(-lim, lim, (fi, fo)).ravel())
+        parts.append(rng.uniform(-0.1, 0.1, fo))
+    return np.concatenate(parts).astype(np.float32)
 
 
 def make_dataset(ctx: binding.Context, n: int, seed: int, chunk: int = 2_000_000) -> dict:
