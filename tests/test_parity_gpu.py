@@ -162,6 +162,27 @@ def test_uneven_batch_full_size_sampled(ctx, uneven, prec):
     assert np.all(np.isfinite(got))
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_uneven_batch_every_kernel_variant(ctx, uneven, prec):
+    """The full CSR batch under each exposure-kernel block and quadrature variant
+    (the autotuner's axes): the sampled curves stay within tolerance of the
+    oracle and every variant gives the same bits."""
+    wl, idx, ref = uneven
+    off = wl["offsets"]
+    first = None
+    try:
+        for eb, q in ((256, 4), (64, 8), (64, 4), (256, 8)):
+            ctx.configure(prec, quad_ctas=q, exposure_block=eb)
+            got = _run(ctx, wl, prec)
+            _compare(np.concatenate([got[off[s]:off[s + 1]] for s in idx]), ref, prec)
+            if first is None:
+                first = got
+            else:
+                assert np.array_equal(got, first)
+    finally:
+        ctx.configure(prec)
+
+
 # ---------------------------------------------------------------- extreme orbits
 @pytest.fixture(scope="module")
 def extreme():
