@@ -58,12 +58,13 @@ def alu_peaks(sm_mhz: float):
 #         sub-exposure FP64 Kepler (sets without the expansion) 90
 #   quadrature (gl_items_quad_kernel, then gl_items_sum_kernel): FP32 whole-ellipse
 #         item 840 (geometry and limb polynomial 35, Newton for the maximum 150,
-#         16 nodes x 40, closed forms 15), crossing item 1850 (inner maxima 310,
-#         frame 90, FP32 Ferrari 290, breakpoints 40, closed forms 160, arcs 110,
-#         one inside arc of 16 nodes x 56); FP64 crossing item 105 (limb
+#         16 nodes x 40, closed forms 15), crossing item 1540 (frame 90, FP32
+#         Ferrari 290, breakpoints 40, closed forms 160, arcs 110, one inside arc
+#         of 16 nodes x 56; the few items whose g may have two maxima add a 310-flop
+#         quartic); FP64 crossing item 105 (limb
 #         polynomial 15, frame 25, Newton polish of two roots 58, ordering 7),
 #         exposure sums 2 per sub-exposure
-F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 840, 1850
+F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 840, 1540
 F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 90, 105, 2
 
 
