@@ -98,7 +98,9 @@ def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak:
 # the kernels of the group) from one ncu capture of the current kernels on the
 # workload named; other workloads report null.
 TRAFFIC = {("mcmc_batch", "quadrature"): 3.168e6 + 3.7e3 + 1.011e6,
-           ("mcmc_batch", "tiles"): 0.139e6 + 0.308e6 + 1.5e3}
+           ("mcmc_batch", "tiles"): 0.139e6 + 0.308e6 + 1.5e3,
+           ("uneven_batch", "quadrature"): 195.8e6 + 41.0e6,
+           ("uneven_batch", "tiles"): 486.8e6 + 79.1e6}
 
 KERNEL_NAMES = {"tiles": "gl_win_kernel+gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
