@@ -368,18 +368,6 @@ __device__ __forceinline__ void count_add(unsigned long long* c, bool pred) {
   if (m && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicAdd(c, (unsigned long long)__popc(m));
 }
 
-// Warp-aggregated append: the lanes (of those active) with pred get consecutive
-// slots from one atomic add on *ctr; returns the slot, or -1 without pred.
-__device__ __forceinline__ long long warp_append(unsigned long long* ctr, bool pred) {
-  const unsigned mask = __activemask();
-  const unsigned bal = __ballot_sync(mask, pred);
-  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-  unsigned long long base = 0;
-  if (lane == leader && bal) base = atomicAdd(ctr, (unsigned long long)__popc(bal));
-  base = __shfl_sync(mask, base, leader);
-  return pred ? (long long)base + __popc(bal & ((1u << lane) - 1u)) : -1;
-}
-
 // Exposure at time t: tau (t - t0 wrapped about the conjunction), the exact FP64
 // window test (kExpDead outside) and, for the FP32C path of a set that allows
 // it, the FP64 Kepler state at the midpoint for the cubic Taylor steps.
@@ -606,51 +594,105 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
   }
 }
 
-// Item pipeline, stage 1: window tests over all exposures.  Each block takes a
-// contiguous range of exposures, 256 at a time, and follows the owning set of a
-// CSR batch forward from the range's start.
+// Item pipeline, stage 1: the window tests of every exposure.  Each block walks
+// a contiguous range in passes of 256 x U exposures; a thread first issues the
+// loads of its U times (coalesced, none behind a store), then tests them.  It
+// keeps the FP32 window constants of its current set in registers and the index
+// where the next set starts, so a set lookup is one integer compare, and no pass
+// needs a block barrier.  No FP64 instruction runs unless the FP32 test passes.
+constexpr int kWinU = 4;
+
+// start of set s + 1 relative to the range start lo (clamped to the int range)
+__device__ __forceinline__ int next_set_start(const int64_t* offs, int64_t n_times,
+                                              int64_t n_sets, int s, int64_t lo) {
+  if (s + 1 >= n_sets) return INT_MAX;
+  const int64_t b = (offs ? offs[s + 1] : (int64_t)(s + 1) * n_times) - lo;
+  return b > (int64_t)INT_MAX ? INT_MAX : (int)b;
+}
+
+template <int U>
 __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
-  __shared__ long long s_set;
-  const int64_t per = (a.n_total + gridDim.x - 1) / gridDim.x;
+  __shared__ int s_first;
+  const int64_t per = (((a.n_total + gridDim.x - 1) / gridDim.x) + 31) & ~(int64_t)31;
   const int64_t lo = (int64_t)blockIdx.x * per;
   const int64_t hi = min(a.n_total, lo + per);
-  if (lo >= hi) return;
-  if (a.offsets && threadIdx.x == 0) s_set = owner_of(a.offsets, a.n_sets, lo);
-  __syncthreads();
-  for (int64_t j0 = lo; j0 < hi; j0 += 256) {
-    const int64_t j = j0 + threadIdx.x;
-    int64_t first = a.offsets ? s_set : 0;
-    bool keep = false;
-    int s = 0;
-    if (j < hi) {
-      int64_t ti;
-      if (a.offsets) {
-        int64_t ss = first;
-        while (ss + 1 < a.n_sets && a.offsets[ss + 1] <= j) ++ss;
-        s = (int)ss;
-        ti = j;
-      } else {
-        s = (int)((unsigned)j / (unsigned)a.n_times);
-        ti = j - (int64_t)s * a.n_times;
+  if (lo >= hi) return;   // whole block
+  const int n = (int)(hi - lo);   // n_total < 2^31
+  const int tid = threadIdx.x, lane = tid & 31;
+  const double* __restrict__ tt = a.t;
+  double* __restrict__ out = a.out + lo;
+  const SetConst* __restrict__ sets = a.sets;
+  const int64_t* __restrict__ offs = a.offsets;
+  int s_run;   // owner of this thread's previous exposure
+  if (offs) {
+    if (tid == 0) s_first = (int)owner_of(offs, a.n_sets, lo);
+    __syncthreads();
+    s_run = s_first;
+  } else {
+    s_run = (int)((unsigned)(lo + tid) / (unsigned)a.n_times);
+  }
+  int nb = next_set_start(offs, a.n_times, a.n_sets, s_run, lo);
+  int sc = -1;   // set whose constants wc holds
+  gl::WinTest wc{};
+  for (int i0 = 0; i0 < n; i0 += 256 * U) {
+    double tv[U];
+    int sv[U];
+    if (offs) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * 256 + tid;
+        tv[u] = i < n ? __ldcs(tt + lo + i) : 0.0;   // read once: do not keep in L2
       }
-      const SetConst& c = a.sets[s];
-      const double tj = a.t[ti];
-      if (c.flags & gl::kSetInvalid)
-        a.out[j] = __longlong_as_double(0x7ff8000000000000LL);
-      else if (gl::window_maybe(c, tj) && gl::in_window(c, gl::wrap_tau(c, tj), 0.5 * c.exptime))
-        keep = true;
-      else
-        a.out[j] = 1.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * 256 + tid;
+        if (i < n)
+          while (i >= nb) nb = next_set_start(offs, a.n_times, a.n_sets, ++s_run, lo);
+        sv[u] = s_run;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * 256 + tid;
+        tv[u] = 0.0;
+        if (i < n) {
+          while (i >= nb) nb = next_set_start(offs, a.n_times, a.n_sets, ++s_run, lo);
+          tv[u] = __ldg(tt + (lo + i - (int64_t)s_run * a.n_times));
+        }
+        sv[u] = s_run;
+      }
     }
-    const long long slot = warp_append(&a.ictr[kIcKept], keep);
-    if (keep) {   // at most n_total entries
-      a.klist[slot] = (int)j;
-      a.kset[slot] = s;
-    }
-    if (a.offsets) {
-      __syncthreads();
-      if (j < hi && (threadIdx.x == 255 || j == hi - 1)) s_set = s;   // owner of the pass's last exposure
-      __syncthreads();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * 256 + tid;
+      const int s = sv[u];
+      bool keep = false;
+      if (i < n) {
+        if (s != sc) {
+          wc = gl::win_test(sets[s]);
+          sc = s;
+        }
+        if (wc.flags & gl::kSetInvalid) {
+          out[i] = __longlong_as_double(0x7ff8000000000000LL);
+        } else {
+          if (gl::window_maybe(wc, tv[u])) {
+            const SetConst& c = sets[s];
+            keep = gl::in_window(c, gl::wrap_tau(c, tv[u]), 0.5 * c.exptime);
+          }
+          if (!keep) __stcs(out + i, 1.0);
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);   // all lanes reach this
+      if (bal) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.ictr[kIcKept], (unsigned long long)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {   // at most n_total entries
+          const long long slot = (long long)base + __popc(bal & ((1u << lane) - 1u));
+          a.klist[slot] = (int)(lo + i);
+          a.kset[slot] = s;
+        }
+      }
     }
   }
 }
@@ -1673,6 +1715,7 @@ struct gl_context {
   size_t ens_cap = 0;
   int qocc[2][2] = {{0, 0}, {0, 0}};       // resident quadrature CTAs per SM (FP64, FP32C) x variant
   int eocc[2][2] = {{0, 0}, {0, 0}};       // resident exposure-kernel CTAs per SM x variant
+  int wocc = 0;                            // resident window-kernel CTAs per SM
   // graph cache: one captured step per distinct argument set
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
@@ -1862,21 +1905,25 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   int& qocc = ctx->qocc[sizeof(R) == 4 ? 1 : 0][qvar];
   const int gvar = ctx->cfg[sizeof(R) == 4 ? 1 : 0].gvar;
   int& eocc = ctx->eocc[sizeof(R) == 4 ? 1 : 0][gvar];
-  if (qocc == 0 || eocc == 0) {
+  if (qocc == 0 || eocc == 0 || ctx->wocc == 0) {
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                      &qocc, qvar ? gl_items_quad_kernel<R, 128, 8> : gl_items_quad_kernel<R, 128, 4>,
                      128, 0));
     GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                      &eocc, gvar ? gl_expgeo_kernel<R, 64> : gl_expgeo_kernel<R, 256>,
                      gvar ? 64 : 256, 0));
-    if (qocc < 1 || eocc < 1) return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
+    GL_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->wocc, gl_win_kernel<kWinU>,
+                                                               256, 0));
+    if (qocc < 1 || eocc < 1 || ctx->wocc < 1)
+      return fail(ctx, GL_ECUDA, "item kernels do not fit on an SM");
   }
   // (the counters were zeroed by the setup kernel of this step)
-  int64_t wb = (args.n_total + 1023) / 1024;   // at least 4 passes of 256 per block
-  if (wb > (int64_t)ctx->sms * 8) wb = (int64_t)ctx->sms * 8;
+  // window kernel: one pass of 256 x kWinU exposures per block, one wave at most
+  int64_t wb = (args.n_total + 256 * kWinU - 1) / (256 * kWinU);
+  if (wb > (int64_t)ctx->sms * ctx->wocc) wb = (int64_t)ctx->sms * ctx->wocc;
   if (wb < 1) wb = 1;
   long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
-  gl_win_kernel<<<(int)wb, 256, 0, st>>>(args);
+  gl_win_kernel<kWinU><<<(int)wb, 256, 0, st>>>(args);
   if (gvar)
     gl_expgeo_kernel<R, 64><<<ctx->sms * eocc, 64, 0, st>>>(args);
   else
@@ -1923,7 +1970,8 @@ int launch_lc_nt(gl_context* ctx, LcArgs args, int occ_slot, cudaStream_t st) {
 bool lc_ready(const gl_context* ctx, int prec, bool items) {
   if (items) {
     const int pi = prec == GL_FP64 ? 0 : 1;
-    return ctx->qocc[pi][ctx->cfg[pi].qvar] != 0 && ctx->eocc[pi][ctx->cfg[pi].gvar] != 0;
+    return ctx->qocc[pi][ctx->cfg[pi].qvar] != 0 && ctx->eocc[pi][ctx->cfg[pi].gvar] != 0 &&
+           ctx->wocc != 0;
   }
   const gl_context::LcCfg& cf = ctx->cfg[prec == GL_FP64 ? 0 : 1];
   int slot = (prec == GL_FP64 ? 0 : 1) + (ctx->counting ? 2 : 0) + (cf.threads == 128 ? 4 : 0);

@@ -19,6 +19,8 @@
 #pragma once
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
+#include <limits.h>
 
 #if defined(__CUDACC__)
 #define GL_HD __host__ __device__ __forceinline__
@@ -583,17 +585,65 @@ GL_HD double wrap_tau(const SetConst& c, double t) {
   return tau - c.period * rint(tau * c.invP);
 }
 
+// FP32 window constants of a set for the per-exposure test (window_maybe), in a
+// form a thread can keep in registers while its exposures stay in one set.
+struct WinTest {
+  float t0f, Pf, invPf, wlo_f, whi_f, slack_f;
+  int flags;
+};
+GL_HD WinTest win_test(const SetConst& c) {
+  return WinTest{c.t0f, c.Pf, c.invPf, c.wlo_f, c.whi_f, c.slack_f, c.flags};
+}
+
+// FP64 -> FP32 rounded to nearest-even with integer operations only (on B300 an
+// FP64 conversion instruction holds the FP64 unit like any FP64 operation).
+// Normal results equal the hardware conversion; magnitudes below 2^-126 give a
+// signed zero instead of a subnormal; infinities and NaN are kept.
+GL_HD float f64_to_f32_int(double x) {
+#if defined(__CUDA_ARCH__)
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+#endif
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int fe = e - 1023 + 127;
+  unsigned r;
+  if (e == 0x7ff) {
+    r = (b << 12) ? 0x7fc00000u : 0x7f800000u;
+  } else if (fe >= 255) {
+    r = 0x7f800000u;
+  } else if (fe <= 0) {
+    r = 0u;
+  } else {
+    r = ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;   // the 29 dropped bits
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  }
+  const unsigned bits = sign | r;
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(bits);
+#else
+  float f;
+  memcpy(&f, &bits, sizeof f);
+  return f;
+#endif
+}
+
 // Conservative FP32 window test of an exposure at time t (true whenever any
 // sub-exposure may overlap the star; false positives are resolved in FP64).
-GL_HD bool window_maybe(const SetConst& c, double t) {
-  if (c.flags & kSetWholeOrbit) return true;
-  float tf = (float)t;
-  float tau = tf - c.t0f;
-  float ep = rintf(tau * c.invPf);
-  float tw = fmaf(-ep, c.Pf, tau);
-  float m = (fabsf(tf) + fabsf(c.t0f)) * 4.76837158203125e-07f + c.slack_f;   // 2^-21
-  return tw >= c.wlo_f - m && tw <= c.whi_f + m;
+GL_HD bool window_maybe(const WinTest& w, double t) {
+  if (w.flags & kSetWholeOrbit) return true;
+  float tf = f64_to_f32_int(t);
+  float tau = tf - w.t0f;
+  float ep = rintf(tau * w.invPf);
+  float tw = fmaf(-ep, w.Pf, tau);
+  float m = (fabsf(tf) + fabsf(w.t0f)) * 4.76837158203125e-07f + w.slack_f;   // 2^-21
+  return tw >= w.wlo_f - m && tw <= w.whi_f + m;
 }
+GL_HD bool window_maybe(const SetConst& c, double t) { return window_maybe(win_test(c), t); }
 
 GL_HD bool in_window(const SetConst& c, double tau, double halfwidth) {
   if (c.flags & kSetWholeOrbit) return true;

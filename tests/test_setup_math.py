@@ -55,3 +55,64 @@ def test_own_sincos_and_cbrt_against_long_double():
     assert float(wb) <= 4 * eps
     assert float(wn) <= 4 * eps
     assert exact0 == "1"
+
+
+CONV_SRC = r'''
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <cfloat>
+#include <random>
+#include "gl_math.cuh"
+static unsigned fb(float f) { unsigned u; memcpy(&u, &f, 4); return u; }
+static double db(unsigned long long u) { double d; memcpy(&d, &u, 8); return d; }
+int main() {
+  std::mt19937_64 g(3);
+  long bad = 0, n = 0, zeroed = 0;
+  auto check = [&](double x) {
+    ++n;
+    const float got = gl::f64_to_f32_int(x), ref = (float)x;
+    if (std::isnan(ref)) { bad += !std::isnan(got); return; }
+    if (std::fabs(ref) < FLT_MIN) {   // subnormal range: a signed zero by design
+      zeroed += 1;
+      bad += !(got == 0.0f && std::signbit(got) == std::signbit(x));
+      return;
+    }
+    bad += fb(got) != fb(ref);
+  };
+  for (int i = 0; i < 2000000; ++i) check(db(g()));                  // every exponent
+  std::uniform_real_distribution<double> U(-1e6, 1e6);
+  for (int i = 0; i < 2000000; ++i) check(U(g));                      // times in days
+  for (int i = 0; i < 200000; ++i) {                                  // ties and neighbours
+    const float f = std::ldexp((float)(g() % 16777215u + 1u), -(int)(g() % 200) + 60);
+    const double ulp = std::ldexp(1.0, std::ilogb(f) - 23);
+    for (int k = -2; k <= 2; ++k) check((double)f + 0.5 * ulp + k * std::ldexp(ulp, -29));
+    check(-((double)f + 0.5 * ulp));
+  }
+  const double edge[] = {0.0, -0.0, INFINITY, -INFINITY, NAN, DBL_MAX, -DBL_MAX, FLT_MAX,
+                         (double)FLT_MAX * (1 + 1e-9), (double)FLT_MAX + std::ldexp(1.0, 103),
+                         FLT_MIN, -FLT_MIN, 0.5 * FLT_MIN, DBL_MIN, 1.0, -1.0};
+  for (double x : edge) check(x);
+  printf("%ld %ld %ld\n", bad, n, zeroed);
+}
+'''
+
+
+def test_integer_double_to_float_conversion_matches_the_c_conversion():
+    """f64_to_f32_int (the window test's conversion without an FP64 instruction)
+    must give the bits of C's round-to-nearest-even conversion for every normal
+    result, infinity on overflow, NaN for NaN and a signed zero below FLT_MIN."""
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "c.cpp")
+        exe = os.path.join(d, "c")
+        with open(src, "w") as fh:
+            fh.write(CONV_SRC)
+        inc = os.path.join(ROOT, "paper_2410_05408_b300", "csrc")
+        r = subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", inc, src,
+                            "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail(r.stderr)
+        bad, n, zeroed = map(int, subprocess.run([exe], capture_output=True, text=True,
+                                                 check=True).stdout.split())
+    assert n > 5_000_000 and zeroed > 0
+    assert bad == 0
