@@ -594,12 +594,15 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
   }
 }
 
-// Item pipeline, stage 1: the window tests of every exposure.  Each block walks
-// a contiguous range in passes of 256 x U exposures; a thread first issues the
-// loads of its U times (coalesced, none behind a store), then tests them.  It
-// keeps the FP32 window constants of its current set in registers and the index
-// where the next set starts, so a set lookup is one integer compare, and no pass
-// needs a block barrier.  No FP64 instruction runs unless the FP32 test passes.
+// Item pipeline, stage 1: the conservative FP32 window test of every exposure.
+// Each block walks a contiguous range in passes of 256 x U exposures; a thread
+// first issues the loads of its U times (coalesced, none behind a store), then
+// tests them.  It keeps the FP32 window constants of its current set in
+// registers and the index where the next set starts; a pass in which every
+// lane's exposures lie in the set it holds (almost all of them) takes a path
+// with no lookup at all.  Exposures that pass are appended to the kept list;
+// the exact FP64 test is the exposure kernel's (exposure_prep), so no FP64
+// instruction runs here.
 constexpr int kWinU = 4;
 
 // start of set s + 1 relative to the range start lo (clamped to the int range)
@@ -610,6 +613,29 @@ __device__ __forceinline__ int next_set_start(const int64_t* offs, int64_t n_tim
   return b > (int64_t)INT_MAX ? INT_MAX : (int)b;
 }
 
+// window test of exposure lo + i of set s at time t: flux 1 (NaN for an invalid
+// set) outside, else a kept-list entry (one atomic add per warp with keeps); all
+// 32 lanes call it, lanes without an exposure with valid = false
+__device__ __forceinline__ void win_one(const LcArgs& a, double* __restrict__ out,
+                                        const gl::WinTest& w, int64_t lo, int i, int s,
+                                        double t, bool valid) {
+  const bool dead = w.flags & gl::kSetInvalid;
+  const bool keep = valid && !dead && gl::window_maybe(w, t);
+  if (valid && !keep) __stcs(out + i, dead ? __longlong_as_double(0x7ff8000000000000LL) : 1.0);
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (bal) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.ictr[kIcKept], (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) {   // at most n_total entries
+      const long long slot = (long long)base + __popc(bal & ((1u << lane) - 1u));
+      a.klist[slot] = (int)(lo + i);
+      a.kset[slot] = s;
+    }
+  }
+}
+
 template <int U>
 __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
   __shared__ int s_first;
@@ -618,7 +644,7 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
   const int64_t hi = min(a.n_total, lo + per);
   if (lo >= hi) return;   // whole block
   const int n = (int)(hi - lo);   // n_total < 2^31
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   const double* __restrict__ tt = a.t;
   double* __restrict__ out = a.out + lo;
   const SetConst* __restrict__ sets = a.sets;
@@ -635,7 +661,18 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
   int sc = -1;   // set whose constants wc holds
   gl::WinTest wc{};
   for (int i0 = 0; i0 < n; i0 += 256 * U) {
+    const int il = i0 + (U - 1) * 256 + tid;   // this thread's last exposure of the pass
     double tv[U];
+    if (__all_sync(0xffffffffu, il < n && il < nb && s_run == sc)) {
+      // every exposure of the warp's pass exists and lies in the lane's cached set
+      const double* tb = offs ? tt + lo : tt + (lo - (int64_t)s_run * a.n_times);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        tv[u] = offs ? __ldcs(tb + i0 + u * 256 + tid) : __ldg(tb + i0 + u * 256 + tid);
+#pragma unroll
+      for (int u = 0; u < U; ++u) win_one(a, out, wc, lo, i0 + u * 256 + tid, s_run, tv[u], true);
+      continue;
+    }
     int sv[U];
     if (offs) {
 #pragma unroll
@@ -665,34 +702,11 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int i = i0 + u * 256 + tid;
-      const int s = sv[u];
-      bool keep = false;
-      if (i < n) {
-        if (s != sc) {
-          wc = gl::win_test(sets[s]);
-          sc = s;
-        }
-        if (wc.flags & gl::kSetInvalid) {
-          out[i] = __longlong_as_double(0x7ff8000000000000LL);
-        } else {
-          if (gl::window_maybe(wc, tv[u])) {
-            const SetConst& c = sets[s];
-            keep = gl::in_window(c, gl::wrap_tau(c, tv[u]), 0.5 * c.exptime);
-          }
-          if (!keep) __stcs(out + i, 1.0);
-        }
+      if (i < n && sv[u] != sc) {
+        sc = sv[u];
+        wc = gl::win_test(sets[sc]);
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);   // all lanes reach this
-      if (bal) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.ictr[kIcKept], (unsigned long long)__popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) {   // at most n_total entries
-          const long long slot = (long long)base + __popc(bal & ((1u << lane) - 1u));
-          a.klist[slot] = (int)(lo + i);
-          a.kset[slot] = s;
-        }
-      }
+      win_one(a, out, wc, lo, i, sv[u], tv[u], i < n);
     }
   }
 }
