@@ -51,11 +51,14 @@ def alu_peaks(sm_mhz: float):
 
 # Algorithmic work per unit of the FP32C light-curve step (flops, FMA = 2),
 # counted from the source, by kernel:
-#   exposures (gl_win_kernel + gl_expgeo_kernel): FP32 per exposure
-#         window test 12, per sub-exposure position and class 40; FP64 per
-#         in-window exposure 10 (exact window), midpoint Kepler state 90 (one
-#         Halley step with its series, second-order update, sky position), per
-#         sub-exposure FP64 Kepler (sets without the expansion) 90
+#   window (gl_win_kernel): HBM-bound; algorithmic bytes = the distinct times read
+#         (8 B each: the shared grid once, or every exposure of a CSR batch) + 8 B
+#         of flux written per exposure outside the window + 8 B of kept-list
+#         entry per kept exposure; FP32 window test 12 per exposure, no FP64
+#   exposures (gl_expgeo_kernel): FP64 per kept exposure 10 (exact window),
+#         midpoint Kepler state 90 (one Halley step with its series, second-order
+#         update, sky position); per sub-exposure FP32 position and class 40, and
+#         FP64 Kepler 90 for sets without the Taylor expansion
 #   quadrature (gl_items_quad_kernel, then gl_items_sum_kernel): FP32 whole-ellipse
 #         item 840 (geometry and limb polynomial 35, Newton for the maximum 150,
 #         16 nodes x 40, closed forms 15), crossing item 1540 (frame 90, FP32
@@ -69,13 +72,18 @@ F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 90, 105, 2
 
 
 def kernel_flops(c: dict) -> dict:
-    """(FP32, FP64) algorithmic flops of one step, per kernel of the step."""
+    """(FP32, FP64) algorithmic flops of one step, per ALU-bound kernel group."""
     return {
-        "tiles": (c["exposures"] * F32_EXPOSURE + c["items"] * F32_ITEM,
-                  c["in_window"] * F64_WINDOW + (c["kepler"] + c["item_kepler"]) * F64_KEPLER),
+        "exposures": (c["items"] * F32_ITEM,
+                      c["kept"] * F64_WINDOW + (c["kepler"] + c["item_kepler"]) * F64_KEPLER),
         "quadrature": (c["full"] * F32_FULL + c["partial"] * F32_PARTIAL,
                        c["partial"] * F64_PARTIAL + c["items"] * F64_SUM),
     }
+
+
+def window_bytes(c: dict, time_bytes: int) -> int:
+    """Algorithmic DRAM bytes of one window-kernel launch."""
+    return time_bytes + 8 * (c["exposures"] - c["kept"]) + 8 * c["kept"]
 
 
 def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak: float) -> dict:
@@ -91,34 +99,51 @@ def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak:
                      "flops_per_launch": f32},
             "fp64": {"achieved": a64, "peak": fp64_peak, "frac": a64 / fp64_peak,
                      "flops_per_launch": f64},
-            "kernel_ms": ms}
+            "kernel_ms": ms,
+            "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x "
+                           "max SM clock"}
+
+
+def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
+    """Algorithmic bytes over a CUDA-event duration against the copy bandwidth
+    (the measured one, else the fallback 6.4 TB/s)."""
+    src = "of measured (STREAM-style copy)" if hbm_peak else "of fallback (6.4 TB/s)"
+    hbm_peak = hbm_peak or 6400.0
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": ach / hbm_peak, "bytes_per_launch": nbytes, "kernel_ms": ms,
+            "peak_source": src}
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, summed over
 # the kernels of the group) from one ncu capture of the current kernels on the
 # workload named; other workloads report null.
-TRAFFIC = {("mcmc_batch", "quadrature"): 3.168e6 + 3.7e3 + 1.011e6,
-           ("mcmc_batch", "tiles"): 0.139e6 + 0.308e6 + 1.5e3,
-           ("uneven_batch", "quadrature"): 195.8e6 + 41.0e6,
-           ("uneven_batch", "tiles"): 486.8e6 + 79.1e6}
+TRAFFIC = {("mcmc_batch", "window"): 0.075e6,
+           ("mcmc_batch", "exposures"): 0.312e6,
+           ("mcmc_batch", "quadrature"): 3.176e6 + 1.011e6,
+           ("uneven_batch", "window"): 471.05e6,
+           ("uneven_batch", "exposures"): 78.66e6,
+           ("uneven_batch", "quadrature"): 195.92e6 + 41.00e6}
 
-KERNEL_NAMES = {"tiles": "gl_win_kernel+gl_expgeo_kernel",
+KERNEL_NAMES = {"window": "gl_win_kernel", "exposures": "gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
 
 
-def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float, workload: str = "") -> dict:
-    """ALU roofline of the dominant kernel of the FP32C step (the one with the
-    largest measured time), with every kernel's own figures beside it."""
-    flops = kernel_flops(c)
-    per = {k: alu_roofline(*flops[k], kern[k], fp32_peak, fp64_peak)
-           for k in flops if kern.get(k)}
+def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float, hbm_peak: float,
+             time_bytes: int, workload: str = "") -> dict:
+    """Roofline of the dominant kernel of the FP32C step (the one with the largest
+    measured time), with every kernel's own figures beside it."""
+    per = {k: alu_roofline(*f, kern[k], fp32_peak, fp64_peak)
+           for k, f in kernel_flops(c).items() if kern.get(k)}
+    if kern.get("window"):
+        per["window"] = hbm_roofline(window_bytes(c, time_bytes), kern["window"], hbm_peak)
     top = max(per, key=lambda k: per[k]["kernel_ms"])
     line = dict(per[top])
     line.update({"kernel": KERNEL_NAMES[top], "traffic": TRAFFIC.get((workload, top)),
-                 "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x "
-                                "max SM clock",
-                 "kernels": {KERNEL_NAMES[k]: {"ms": v["kernel_ms"], "pipe": v["pipe"],
-                                               "frac": v["frac"]} for k, v in per.items()}})
+                 "kernels": {KERNEL_NAMES[k]: {"ms": v["kernel_ms"], "bound": v["bound"],
+                                               "pipe": v.get("pipe"), "frac": v["frac"],
+                                               "traffic": TRAFFIC.get((workload, k))}
+                             for k, v in per.items()}})
     return line
 
 
@@ -790,7 +815,8 @@ def main():
         ms = sum(per_step)
         kern = {}
         if profile:
-            for name, kind in (("tiles", binding.GL_KERNEL_CURVE),
+            for name, kind in (("window", binding.GL_KERNEL_WINDOW),
+                               ("exposures", binding.GL_KERNEL_CURVE),
                                ("quadrature", binding.GL_KERNEL_QUAD),
                                ("setup", binding.GL_KERNEL_SETUP)):
                 t_ms, n = ctx.profile_read(kind)
@@ -821,10 +847,16 @@ def main():
     counts = ctx.counts_read()
     ctx.counts(False)
 
-    # The clock sampler starts (and settles) before the warm-up steps, so that the
-    # GPU runs the warm-up right before the timed steps instead of idling while
-    # the sampler starts (an idle GPU lowers its clocks).
+    # The clock sampler starts (and settles) before the warm-up steps.  Its second
+    # of start-up leaves the GPU idle, and a GPU that has idled that long ran this
+    # short, latency-bound step up to twice as slow for a while afterwards (with or
+    # without the sampler; the sampled SM clock stayed at its maximum), so 0.3 s
+    # of L2-flush writes bring it back to its working state before the warm-up.
     with ClockSampler(local) as clk:
+        t_busy = time.perf_counter()
+        while time.perf_counter() - t_busy < 0.3:
+            flush.zero_()
+            torch.cuda.synchronize(dev)
         for _ in range(args.warmup):
             step(out32, binding.GL_FP32C)
             step(out64, binding.GL_FP64)
@@ -885,7 +917,9 @@ def main():
         "workload_counts": counts,
         "autotune": tune,
         "autotune_fp64": tune64,
-        "roofline": roofline(counts, kern32, fp32_peak, fp64_peak, args.workload),
+        "roofline": roofline(counts, kern32, fp32_peak, fp64_peak,
+                             peaks.get("hbm_gbs"), 8 * len(t) if offsets is None
+                             else 8 * n_tot, args.workload),
         "gpu_launches": launches,
         "status": status,
         "clocks": clocks,

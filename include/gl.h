@@ -307,13 +307,14 @@ int gl_configure(gl_context *ctx, gl_precision prec, int threads, int nodes, int
 
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */
-#define GL_KERNEL_CURVE 1   /* light-curve tile kernel, or the item pipeline's window and
-                               kept-exposure kernels (FP64 or FP32C) */
+#define GL_KERNEL_CURVE 1   /* light-curve tile kernel, or the item pipeline's
+                               kept-exposure kernel (FP64 or FP32C) */
 #define GL_KERNEL_SKY 2     /* geometry-level kernel */
 #define GL_KERNEL_SPHERE 3  /* spherical-planet kernel */
 #define GL_KERNEL_SIMPSON 5 /* the paper's snapped Simpson scheme (gl_flux_sky_simpson) */
 #define GL_KERNEL_QUAD 4    /* item pipeline: quadrature of queued sub-exposures and the
                                exposure means (two kernels) */
+#define GL_KERNEL_WINDOW 6  /* item pipeline: the window test of every exposure */
 #define GL_KERNEL_KINDS 8
 
 /* Per-kernel device timing for benchmarks.  While enabled (on != 0), every

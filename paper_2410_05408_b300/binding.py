@@ -51,6 +51,7 @@ GL_KERNEL_SKY = 2
 GL_KERNEL_SPHERE = 3
 GL_KERNEL_QUAD = 4
 GL_KERNEL_SIMPSON = 5
+GL_KERNEL_WINDOW = 6
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
 // with no lookup at all.  Exposures that pass are appended to the kept list;
 // the exact FP64 test is the exposure kernel's (exposure_prep), so no FP64
 // instruction runs here.
-constexpr int kWinU = 4;
+constexpr int kWinU = 2;
 
 // start of set s + 1 relative to the range start lo (clamped to the int range)
 __device__ __forceinline__ int next_set_start(const int64_t* offs, int64_t n_times,
@@ -1933,11 +1933,15 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   }
   // (the counters were zeroed by the setup kernel of this step)
   // window kernel: one pass of 256 x kWinU exposures per block, one wave at most
+  // (two exposures per thread and pass measured fastest: a pass that spans a set
+  // boundary takes the slower path, and wider passes span more of them)
   int64_t wb = (args.n_total + 256 * kWinU - 1) / (256 * kWinU);
   if (wb > (int64_t)ctx->sms * ctx->wocc) wb = (int64_t)ctx->sms * ctx->wocc;
   if (wb < 1) wb = 1;
-  long pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
+  long pe = prof_begin(ctx, GL_KERNEL_WINDOW, st);
   gl_win_kernel<kWinU><<<(int)wb, 256, 0, st>>>(args);
+  prof_end(ctx, GL_KERNEL_WINDOW, pe, st);
+  pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
   if (gvar)
     gl_expgeo_kernel<R, 64><<<ctx->sms * eocc, 64, 0, st>>>(args);
   else

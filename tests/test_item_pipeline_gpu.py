@@ -104,7 +104,7 @@ def test_pipeline_kernels_are_profiled(ctx):
     d = _prepare(inputs.mcmc_batch(seed=14))
     ctx.profile(True)
     _run(ctx, d, binding.GL_FP32C)
-    got = {k: ctx.profile_read(k)[1] for k in (binding.GL_KERNEL_SETUP, binding.GL_KERNEL_CURVE,
-                                                binding.GL_KERNEL_QUAD)}
+    got = {k: ctx.profile_read(k)[1] for k in (binding.GL_KERNEL_SETUP, binding.GL_KERNEL_WINDOW,
+                                                binding.GL_KERNEL_CURVE, binding.GL_KERNEL_QUAD)}
     ctx.profile(False)
     assert all(n == 2 for n in got.values()), got
