@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) gl_curve_kernel(const SetConst* __restric
     }
     double tau = gl::wrap_tau(c, tj);
     int ns = c.nsuper;
-    if (!gl::in_window(c, tau, 0.5 * c.exptime)) {
+    if (!gl::exposure_in_window(c, tau)) {
       out[j] = 1.0;
       continue;
     }
@@ -379,7 +379,7 @@ __device__ __noinline__ int exposure_prep(const SetConst& c, double t, double* t
                                           gl::MidState* mid) {
   const double tau = gl::wrap_tau(c, t);
   *tau_out = tau;
-  if (!gl::in_window(c, tau, 0.5 * c.exptime)) return kExpDead;
+  if (!gl::exposure_in_window(c, tau)) return kExpDead;
   if (sizeof(R) == 4 && (c.flags & gl::kSetTaylor)) {
     // with one sub-exposure it sits at the midpoint: no derivatives needed (the
     // Taylor step with dt = 0 returns the midpoint values unchanged)
@@ -997,7 +997,7 @@ __global__ void __launch_bounds__(128) gl_locked_kernel(const SetConst* __restri
     }
     const double tau = gl::wrap_tau(c, tj);
     const int ns = c.nsuper;
-    if (!gl::in_window(c, tau, 0.5 * c.exptime)) {
+    if (!gl::exposure_in_window(c, tau)) {
       out[j] = 1.0;
       continue;
     }
@@ -1116,7 +1116,7 @@ __global__ void __launch_bounds__(NT) gl_collect_kernel(CollectArgs a) {
         a.out[j] = __longlong_as_double(0x7ff8000000000000LL);
       } else if (gl::window_maybe(c, my_t)) {
         double tau = gl::wrap_tau(c, my_t);
-        if (gl::in_window(c, tau, 0.5 * c.exptime)) {
+        if (gl::exposure_in_window(c, tau)) {
           keep = 1;
           my_ns = c.nsuper;
           my_t = tau;

@@ -44,6 +44,7 @@ struct SetConst {
   double cosEc, sinEc, rc;         // eccentric anomaly and radius at conjunction
   double tau_lo, tau_hi;           // window of (t - t0) wrapped to [-P/2, P/2) outside
                                    // of which the planet cannot overlap the star
+  double elo, ehi;                 // the window widened by half an exposure (exposure test)
   // projected ellipse x = x0 + dx cos th, y = y0 + dy1 cos th + dy2 sin th
   double dx, dy1, dy2, req;
   // limb darkening I = c0 + c1 mu + c2 r^2, F0 = pi (1 - u1/3 - u2/6)
@@ -67,8 +68,8 @@ struct SetConst {
   // R(zeta, eta, xi), for projections that change along the orbit (tidal locking)
   double ax[3], rot[9];
   // Kepler solve about the conjunction (set_kepler): e cos E_c, e sin E_c and the
-  // Halley error constant; FP32 copies of the orbit for the FP32 stages
-  double kep_ec, kep_es, kep_C;
+  // largest accepted Newton step; FP32 copies of the orbit for the FP32 stages
+  double kep_ec, kep_es, kep_smax;
   float kf_ec, kf_es, kf_ir1;          // e cos E_c, e sin E_c, 1 / (1 - e cos E_c)
   float kf_a, kf_bo, kf_e, kf_nm;      // a, a sqrt(1 - e^2), e, n
   float kf_cEc, kf_sEc, kf_cw, kf_sw, kf_ci, kf_si;
@@ -444,15 +445,24 @@ GL_HD bool set_orbit(double t0, double period, double a_rs, double b, double ecc
 }
 
 // Constants of the Kepler solve about the conjunction (from set_orbit's fields).
-// With F' >= 1 - e and the second and third derivatives of F at most e in size,
-// a Halley step s leaves an error below C |s|^3, C = q (1 + q), q = e / (1 - e).
+// kepler_offset takes Newton steps s = F r with r the reciprocal of F' to a
+// relative error below rho = 2^-44 (an FP32 reciprocal refined once in FP64).
+// With F' >= 1 - e and |F''| <= e, such a step leaves an error below
+// rho |s| + C_N s^2, C_N = e / (2 (1 - e)).  A step is accepted when that bound is
+// below 1e-15 and |s| <= 1e-5 (the sin/cos update drops terms of order |s|^3/6);
+// kep_smax is the largest such |s|, computed in FP32 and lowered by 10 %.
 // (An invalid orbit gives meaningless values here; such sets are never used.)
 GL_HD void set_kepler(SetConst* c) {
   const double e = c->ecc;
   c->kep_ec = e * c->cosEc;
   c->kep_es = e * c->sinEc;
-  const double q = e * rcp64(1.0 - e);
-  c->kep_C = q * (1.0 + q);
+  {
+    const float ef = (float)e, tol = 1e-15f, rho = 5.684342e-14f;   // 2^-44
+    const float cn = ef / (2.0f * (1.0f - ef));
+    // positive root of cn s^2 + rho s = tol, in the form without cancellation
+    const float sq = 2.0f * tol / (rho + sqrtf(rho * rho + 4.0f * cn * tol));
+    c->kep_smax = (double)fminf(0.9f * sq, 1e-5f);
+  }
   c->kf_ec = (float)c->kep_ec;
   c->kf_es = (float)c->kep_es;
   c->kf_ir1 = 1.0f / (1.0f - c->kf_ec);
@@ -514,6 +524,8 @@ GL_HD int set_window(double t0, double period, double a_rs, double ecc, double o
     c->tau_lo = fmin((double)taus[0], 0.0) - margin;
     c->tau_hi = fmax((double)taus[1], 0.0) + margin;
   }
+  c->elo = c->tau_lo - 0.5 * exptime;
+  c->ehi = c->tau_hi + 0.5 * exptime;
   c->sub_step = exptime / nsuper;
   c->fsub_step = (float)c->sub_step;
   // FP32 copy of the window for the per-exposure test, widened for rounding:
@@ -595,17 +607,37 @@ GL_HD WinTest win_test(const SetConst& c) {
   return WinTest{c.t0f, c.Pf, c.invPf, c.wlo_f, c.whi_f, c.slack_f, c.flags};
 }
 
+// Bit patterns of doubles (host and device).
+GL_HD unsigned long long dbits(double x) {
+#if defined(__CUDA_ARCH__)
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+GL_HD double dfrombits(unsigned long long b) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof x);
+  return x;
+#endif
+}
+// |x| <= m for a finite m >= 0, by the ordering of the bit patterns of
+// non-negative doubles (no FP64 instruction); false for NaN.
+GL_HD bool abs_le(double x, double m) { return (dbits(x) & 0x7fffffffffffffffull) <= dbits(m); }
+// isfinite from the exponent bits
+GL_HD bool finite_bits(double x) { return ((dbits(x) >> 52) & 0x7ffu) != 0x7ffu; }
+
 // FP64 -> FP32 rounded to nearest-even with integer operations only (on B300 an
 // FP64 conversion instruction holds the FP64 unit like any FP64 operation).
 // Normal results equal the hardware conversion; magnitudes below 2^-126 give a
 // signed zero instead of a subnormal; infinities and NaN are kept.
 GL_HD float f64_to_f32_int(double x) {
-#if defined(__CUDA_ARCH__)
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-#else
-  unsigned long long b;
-  memcpy(&b, &x, sizeof b);
-#endif
+  const unsigned long long b = dbits(x);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const unsigned sign = hi & 0x80000000u;
   const int e = (int)((hi >> 20) & 0x7ffu);
@@ -632,6 +664,24 @@ GL_HD float f64_to_f32_int(double x) {
 #endif
 }
 
+// FP32 -> FP64 with integer operations only: exact for normal numbers, zeros,
+// infinities and NaN; FP32 subnormals (below 2^-126) give a signed zero.
+GL_HD double f32_to_f64_int(float f) {
+#if defined(__CUDA_ARCH__)
+  const unsigned u = __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, sizeof u);
+#endif
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned long long r;
+  if (e == 0) r = 0;
+  else if (e == 0xff) r = (0x7ffull << 52) | ((unsigned long long)m << 29);
+  else r = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  return dfrombits(sign | r);
+}
+
 // Conservative FP32 window test of an exposure at time t (true whenever any
 // sub-exposure may overlap the star; false positives are resolved in FP64).
 GL_HD bool window_maybe(const WinTest& w, double t) {
@@ -644,6 +694,13 @@ GL_HD bool window_maybe(const WinTest& w, double t) {
   return tw >= w.wlo_f - m && tw <= w.whi_f + m;
 }
 GL_HD bool window_maybe(const SetConst& c, double t) { return window_maybe(win_test(c), t); }
+
+// Window test of a whole exposure centred at tau (any of its sub-exposures may
+// overlap the star).
+GL_HD bool exposure_in_window(const SetConst& c, double tau) {
+  if (c.flags & kSetWholeOrbit) return true;
+  return tau >= c.elo && tau <= c.ehi;
+}
 
 GL_HD bool in_window(const SetConst& c, double tau, double halfwidth) {
   if (c.flags & kSetWholeOrbit) return true;
@@ -668,18 +725,20 @@ GL_HD void sin_cosm1_f(float d, float* sd, float* cm1) {
 
 // Kepler's equation for the eccentric anomaly E = E_c + d about the
 // conjunction:  d - e [cos E_c sin d + sin E_c (cos d - 1)] = n tau.
-// Newton's method in FP32 first (cheap), then Halley's method in FP64 from the
-// FP32 iterate; the error after a step s is below C |s|^3 (set_kepler), so the
-// FP64 iteration stops once C |s|^3 <= 1e-17 -- one step from a converged FP32
-// iterate (|s| ~ 1e-7 |d|).  sin d and cos d - 1 of the final iterate follow
-// from those of the last evaluated one by the angle-difference formulas to
-// second order in s (the dropped terms are below |s|^3 / 6 < 1e-20).  A
+// Newton's method in FP32 first (cheap), then Newton's method in FP64 from the
+// FP32 iterate: the residual F in FP64, the reciprocal of F' from FP32 refined by
+// one FP64 step (set_kepler bounds the error after a step s and accepts the step
+// when |s| <= kep_smax -- one step from a converged FP32 iterate, |s| ~ 1e-7 |d|).
+// sin d and cos d - 1 of the final iterate follow from those of the last
+// evaluated one by the angle-difference formulas to second order in s.  A
 // bisection on the bracket |E - M| <= e backs up an iteration that does not
-// settle.  Returns sin d and cos d - 1.
+// settle.  The FP32 <-> FP64 conversions are integer operations (on B300 an FP64
+// conversion holds the FP64 unit like an FP64 operation).  Returns sin d and
+// cos d - 1.
 GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* cm1_out) {
   const double nt = c.nmean * tau;
   const double ec = c.kep_ec, es = c.kep_es;
-  const float ntf = (float)nt, ecf = c.kf_ec, esf = c.kf_es;
+  const float ntf = f64_to_f32_int(nt), ecf = c.kf_ec, esf = c.kf_es;
   const float ir1f = c.kf_ir1;
   float df = ntf * ir1f;
   df -= 0.5f * esf * df * df * ir1f;   // second-order start: F ~ d (1 - ec) + es d^2 / 2 - n tau
@@ -690,32 +749,26 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
     const float Fp = 1.0f - ecf * (1.0f + cmf) + esf * sdf;
     df -= F / Fp;
   }
-  const double C = c.kep_C;
-  double d = isfinite(df) ? (double)df : nt;
+  const double smax = c.kep_smax;
+  double d = isfinite(df) ? f32_to_f64_int(df) : nt;   // (FP32 test)
   double sd, cm1;
-  bool conv = false;
   for (int it = 0; it < 12; ++it) {
     sin_cosm1(d, &sd, &cm1);
+    const double cp = 1.0 + cm1;
     const double F = d - ec * sd - es * cm1 - nt;
-    const double Fp = 1.0 - ec * (1.0 + cm1) + es * sd;
-    const double Fpp = ec * sd + es * (1.0 + cm1);
-    // Halley step: 2 F F1 / (2 F1^2 - F F2) with F1, F2 the first two derivatives
-    const double step = 2.0 * F * Fp * rcp64(2.0 * Fp * Fp - F * Fpp);
+    const double Fp = 1.0 - ec * cp + es * sd;
+    const double r0 = f32_to_f64_int(rcp_<float>(f64_to_f32_int(Fp)));
+    const double er = fma(-Fp, r0, 1.0);       // 1 - F' r0
+    const double sr = F * r0;
+    const double step = fma(sr, er, sr);       // F / F' to a relative 2^-44
     d -= step;
-    const double as = fabs(step);
-    if (C * as * as * as <= 1e-17 || as <= 1e-16 * (1.0 + fabs(d))) {
-      conv = isfinite(d);
-      if (conv) {
-        // sin(d - s), cos(d - s) - 1 from sin d, cos d - 1 of the previous iterate
-        const double hs2 = 0.5 * step * step;
-        const double sd1 = sd - step * (1.0 + cm1) - hs2 * sd;
-        const double cm11 = cm1 + step * sd - hs2 * (1.0 + cm1);
-        *sd_out = sd1;
-        *cm1_out = cm11;
-        return;
-      }
-      break;
-    }
+    if (!abs_le(step, smax)) continue;         // (NaN continues to the bisection)
+    if (!finite_bits(d)) break;
+    // sin(d - s), cos(d - s) - 1 from sin d, cos d - 1 of the previous iterate
+    const double hs2 = 0.5 * step * step;
+    *sd_out = sd - step * cp - hs2 * sd;
+    *cm1_out = cm1 + step * sd - hs2 * cp;
+    return;
   }
   {
     double Ec = atan2(c.sinEc, c.cosEc);
@@ -1653,17 +1706,17 @@ GL_HD MidState mid_state_at(const SetConst& c, double tau, bool derivs) {
   const double p1 = dX * c.cosw - dY * c.sinw;
   const double p2 = c.rc + (dX * c.sinw + dY * c.cosw);
   const double x = p2 * c.cosi, y = -p1;
-  MidState m;
-  m.x = (float)x;
-  m.y = (float)y;
-  m.z = (float)(-p2 * c.sini);
-  m.omr2 = (float)((1.0 - x) * (1.0 + x) - y * y);
+  MidState m;   // (conversions by integer operations, see kepler_offset)
+  m.x = f64_to_f32_int(x);
+  m.y = f64_to_f32_int(y);
+  m.z = f64_to_f32_int(-p2 * c.sini);
+  m.omr2 = f64_to_f32_int((1.0 - x) * (1.0 + x) - y * y);
   if (!derivs) {
     for (int k = 0; k < 3; ++k) m.d1[k] = m.d2[k] = m.d3[k] = 0.0f;
     return m;
   }
   const float a = c.kf_a, bo = c.kf_bo, ef = c.kf_e, nm = c.kf_nm;
-  const float cosE = c.kf_cEc + (float)dcosE, sinE = c.kf_sEc + (float)dsinE;
+  const float cosE = c.kf_cEc + f64_to_f32_int(dcosE), sinE = c.kf_sEc + f64_to_f32_int(dsinE);
   const float X = a * (cosE - ef), Y = bo * sinE;
   const float r = a * (1.0f - ef * cosE);
   const float ir = 1.0f / r;

@@ -116,3 +116,102 @@ def test_integer_double_to_float_conversion_matches_the_c_conversion():
                                                  check=True).stdout.split())
     assert n > 5_000_000 and zeroed > 0
     assert bad == 0
+
+
+KEPLER_SRC = r'''
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <cfloat>
+#include <random>
+#include "gl_math.cuh"
+typedef long double L;
+// independent long-double sky position: E - e sin E = M by Newton from M
+static void ref_pos(L tau, L P, L a, L e, L w, L cosi, L* x, L* y) {
+  const L pi = 3.14159265358979323846264338327950288L;
+  const L sw = sinl(w), cw = cosl(w), se = sqrtl((1 - e) * (1 + e));
+  const L cEc = (e + sw) / (1 + e * sw), sEc = se * cw / (1 + e * sw);
+  const L Ec = atan2l(sEc, cEc);
+  const L M = Ec - e * sinl(Ec) + 2 * pi / P * tau;
+  L E = M;
+  for (int i = 0; i < 100; ++i) {
+    L dE = (E - e * sinl(E) - M) / (1 - e * cosl(E));
+    E -= dE;
+    if (fabsl(dE) < 1e-19L) break;
+  }
+  const L X = a * (cosl(E) - e), Y = a * se * sinl(E);
+  const L p1 = X * cw - Y * sw, p2 = X * sw + Y * cw;
+  *y = -p1;
+  *x = p2 * cosi;
+}
+int main() {
+  std::mt19937_64 g(11);
+  std::uniform_real_distribution<double> U(0, 1);
+  double worst = 0, worst_mid = 0, bad_conv = 0;
+  long n = 0;
+  for (int i = 0; i < 20000; ++i) {
+    const double e = (i % 4 == 0) ? 0.0 : 0.95 * U(g) * U(g);
+    const double P = 1 + 500 * U(g), a = 3 + 250 * U(g), w = 6.283185307179586 * U(g);
+    const double b = 0.9 * U(g);
+    gl::SetConst c;
+    if (!gl::set_setup(0.0, P, a, b, e, w, 0.1, 0.2, 0.3, 0.4, 0.4, 0.25, 0.02, 15, &c)) continue;
+    for (int k = 0; k < 8; ++k) {
+      // times in and around the transit window, and anywhere in the orbit
+      double tau = (k < 6) ? c.tau_lo + (c.tau_hi - c.tau_lo) * (1.5 * U(g) - 0.25)
+                           : P * (U(g) - 0.5);
+      double x, y, z;
+      gl::sky_position(c, tau, &x, &y, &z);
+      L xr, yr;
+      ref_pos(tau, P, a, e, w, c.cosi, &xr, &yr);
+      const double err = (double)fmaxl(fabsl(x - xr), fabsl(y - yr)) / a;
+      if (err > worst) worst = err;
+      if (fabs(xr) < 2 && fabs(yr) < 2) {   // the FP32 midpoint state near the star
+        const gl::MidState m = gl::mid_state_at(c, tau, false);
+        const double em = (double)fmaxl(fabsl(m.x - xr), fabsl(m.y - yr));
+        if (em > worst_mid) worst_mid = em;
+      }
+      ++n;
+    }
+  }
+  // integer FP32 -> FP64 conversion and the bit-pattern comparison
+  for (int i = 0; i < 3000000; ++i) {
+    unsigned u = (unsigned)g();
+    float f;
+    memcpy(&f, &u, 4);
+    const double r = gl::f32_to_f64_int(f);
+    if (std::isnan(f)) { bad_conv += !std::isnan(r); continue; }
+    if (std::fabs(f) < FLT_MIN) { bad_conv += !(r == 0.0 && std::signbit(r) == std::signbit(f)); continue; }
+    bad_conv += !(r == (double)f);
+    const double m = std::fabs((double)U(g) * 4.0);
+    const double x = (double)f;
+    bad_conv += gl::abs_le(x, m) != (std::fabs(x) <= m);
+  }
+  bad_conv += gl::abs_le(NAN, 1.0) || !gl::abs_le(-0.0, 0.0) || gl::abs_le(INFINITY, DBL_MAX);
+  printf("%.6e %.6e %ld %.0f\n", worst, worst_mid, n, bad_conv);
+}
+'''
+
+
+def test_kepler_newton_step_against_long_double():
+    """The FP64 Kepler solve (FP32 Newton, then FP64 Newton steps with a refined
+    FP32 reciprocal, accepted below a per-set step bound) against a long-double
+    Newton solve of E - e sin E = M on 20 000 random orbits (e up to 0.95):
+    sky positions within 2e-14 of a (relative), and the FP32 midpoint state within
+    FP32 rounding of the exact position.  Also the integer FP32 -> FP64 conversion
+    (exact) and abs_le (|x| <= m by bit patterns)."""
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "k.cpp")
+        exe = os.path.join(d, "k")
+        with open(src, "w") as fh:
+            fh.write(KEPLER_SRC)
+        inc = os.path.join(ROOT, "paper_2410_05408_b300", "csrc")
+        r = subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", inc, src,
+                            "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail(r.stderr)
+        worst, worst_mid, n, bad = subprocess.run([exe], capture_output=True, text=True,
+                                                  check=True).stdout.split()
+    assert int(n) > 100_000
+    assert float(worst) <= 2e-14, worst   # measured 2.0e-15
+    assert float(worst_mid) <= 1.2e-7, worst_mid   # FP32 rounding of |x| < 2
+    assert float(bad) == 0
