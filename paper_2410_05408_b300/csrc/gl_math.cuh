@@ -45,6 +45,11 @@ struct SetConst {
   double tau_lo, tau_hi;           // window of (t - t0) wrapped to [-P/2, P/2) outside
                                    // of which the planet cannot overlap the star
   double elo, ehi;                 // the window widened by half an exposure (exposure test)
+  long long elo_key, ehi_key;      // ... as dkey() keys
+  double half_p;                   // 0.49 P: |t - t0| below it needs no wrapping
+  // sky position from the Kepler offset d = E - E_c (sky_position):
+  // r cos(w + nu) = kc1 (cos d - 1) + ks1 sin d, r sin(w + nu) = rc + kc2 (cos d - 1) + ks2 sin d
+  double kc1, ks1, kc2, ks2;
   // projected ellipse x = x0 + dx cos th, y = y0 + dy1 cos th + dy2 sin th
   double dx, dy1, dy2, req;
   // limb darkening I = c0 + c1 mu + c2 r^2, F0 = pi (1 - u1/3 - u2/6)
@@ -161,6 +166,39 @@ template <> GL_HD float pick<float>(double, float f) { return f; }
 
 // Reciprocal: hardware approximation refined by Newton steps (full precision
 // after two; used where a divide would cost a long FP64 sequence).
+// Bit patterns of doubles (host and device).
+GL_HD unsigned long long dbits(double x) {
+#if defined(__CUDA_ARCH__)
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+GL_HD double dfrombits(unsigned long long b) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof x);
+  return x;
+#endif
+}
+// |x| <= m for a finite m >= 0, by the ordering of the bit patterns of
+// non-negative doubles (no FP64 instruction); false for NaN.
+GL_HD bool abs_le(double x, double m) { return (dbits(x) & 0x7fffffffffffffffull) <= dbits(m); }
+// |x| < m likewise
+GL_HD bool abs_lt(double x, double m) { return (dbits(x) & 0x7fffffffffffffffull) < dbits(m); }
+// isfinite from the exponent bits
+GL_HD bool finite_bits(double x) { return ((dbits(x) >> 52) & 0x7ffu) != 0x7ffu; }
+// A key that orders doubles like their values (signed integer compare; -0 sorts
+// just below +0, NaN above +infinity)
+GL_HD long long dkey(double x) {
+  const long long b = (long long)dbits(x);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+
 GL_HD double rcp64(double x) {
 #if defined(__CUDA_ARCH__)
   double r;
@@ -176,7 +214,7 @@ GL_HD double rcp64(double x) {
 // sin(d) and cos(d) - 1 for the Kepler update.  Small |d|: Taylor series in d^2
 // (coefficients 1/n!, truncation below 1e-21 for |d| < 1/4); otherwise sincos.
 GL_HD void sin_cosm1(double d, double* sd, double* cm1) {
-  if (fabs(d) < 0.02) {
+  if (abs_lt(d, 0.02)) {   // (integer compares: no FP64 instruction)
     // truncation below 1e-26 for |d| < 0.02
     double d2 = d * d;
     double s = -1.0 / 5040.0;
@@ -188,7 +226,7 @@ GL_HD void sin_cosm1(double d, double* sd, double* cm1) {
     c = c * d2 + 1.0 / 24.0;
     c = c * d2 - 0.5;
     *cm1 = d2 * c;
-  } else if (fabs(d) < 0.25) {
+  } else if (abs_lt(d, 0.25)) {
     double d2 = d * d;
     double s = 1.0 / 6227020800.0;
     s = s * d2 - 1.0 / 39916800.0;
@@ -441,6 +479,15 @@ GL_HD bool set_orbit(double t0, double period, double a_rs, double b, double ecc
   c->cosEc = (ecc + sinw) * iden;
   c->sinEc = se * cosw * iden;
   c->rc = a_rs * (1.0 - ecc) * (1.0 + ecc) * iden;
+  // X = a (cos E - e), Y = a sqrt(1 - e^2) sin E rotated by w, with
+  // cos E = cos E_c + cosEc (cos d - 1) - sinEc sin d and
+  // sin E = sin E_c + sinEc (cos d - 1) + cosEc sin d
+  const double a = a_rs, bo = c->b_orb, ce = c->cosEc, sE = c->sinEc;
+  c->kc1 = a * cosw * ce - bo * sinw * sE;
+  c->ks1 = -(a * cosw * sE + bo * sinw * ce);
+  c->kc2 = a * sinw * ce + bo * cosw * sE;
+  c->ks2 = bo * cosw * ce - a * sinw * sE;
+  c->half_p = 0.49 * period;
   return fabs(cosi) <= 1.0;
 }
 
@@ -526,6 +573,8 @@ GL_HD int set_window(double t0, double period, double a_rs, double ecc, double o
   }
   c->elo = c->tau_lo - 0.5 * exptime;
   c->ehi = c->tau_hi + 0.5 * exptime;
+  c->elo_key = dkey(c->elo);
+  c->ehi_key = dkey(c->ehi);
   c->sub_step = exptime / nsuper;
   c->fsub_step = (float)c->sub_step;
   // FP32 copy of the window for the per-exposure test, widened for rounding:
@@ -594,6 +643,7 @@ GL_HD bool set_setup(double t0, double period, double a_rs, double b, double ecc
 // (t - t0) wrapped to one period around the conjunction.
 GL_HD double wrap_tau(const SetConst& c, double t) {
   double tau = t - c.t0;
+  if (abs_le(tau, c.half_p)) return tau;   // rint(tau / P) = 0: the same value
   return tau - c.period * rint(tau * c.invP);
 }
 
@@ -606,31 +656,6 @@ struct WinTest {
 GL_HD WinTest win_test(const SetConst& c) {
   return WinTest{c.t0f, c.Pf, c.invPf, c.wlo_f, c.whi_f, c.slack_f, c.flags};
 }
-
-// Bit patterns of doubles (host and device).
-GL_HD unsigned long long dbits(double x) {
-#if defined(__CUDA_ARCH__)
-  return (unsigned long long)__double_as_longlong(x);
-#else
-  unsigned long long b;
-  memcpy(&b, &x, sizeof b);
-  return b;
-#endif
-}
-GL_HD double dfrombits(unsigned long long b) {
-#if defined(__CUDA_ARCH__)
-  return __longlong_as_double((long long)b);
-#else
-  double x;
-  memcpy(&x, &b, sizeof x);
-  return x;
-#endif
-}
-// |x| <= m for a finite m >= 0, by the ordering of the bit patterns of
-// non-negative doubles (no FP64 instruction); false for NaN.
-GL_HD bool abs_le(double x, double m) { return (dbits(x) & 0x7fffffffffffffffull) <= dbits(m); }
-// isfinite from the exponent bits
-GL_HD bool finite_bits(double x) { return ((dbits(x) >> 52) & 0x7ffu) != 0x7ffu; }
 
 // FP64 -> FP32 rounded to nearest-even with integer operations only (on B300 an
 // FP64 conversion instruction holds the FP64 unit like any FP64 operation).
@@ -699,7 +724,8 @@ GL_HD bool window_maybe(const SetConst& c, double t) { return window_maybe(win_t
 // overlap the star).
 GL_HD bool exposure_in_window(const SetConst& c, double tau) {
   if (c.flags & kSetWholeOrbit) return true;
-  return tau >= c.elo && tau <= c.ehi;
+  const long long k = dkey(tau);   // (integer compares: no FP64 instruction)
+  return k >= c.elo_key && k <= c.ehi_key;
 }
 
 GL_HD bool in_window(const SetConst& c, double tau, double halfwidth) {
@@ -791,11 +817,8 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
 GL_HD void sky_position(const SetConst& c, double tau, double* x0, double* y0, double* z) {
   double sd, cm1;
   kepler_offset(c, tau, &sd, &cm1);
-  double dcosE = c.cosEc * cm1 - c.sinEc * sd;    // cos E - cos E_c
-  double dsinE = c.sinEc * cm1 + c.cosEc * sd;    // sin E - sin E_c
-  double dX = c.a_rs * dcosE, dY = c.b_orb * dsinE;
-  double p1 = dX * c.cosw - dY * c.sinw;          // r cos(w + nu)     (0 at conjunction)
-  double p2 = c.rc + (dX * c.sinw + dY * c.cosw); // r sin(w + nu)     (r_c at conjunction)
+  const double p1 = fma(cm1, c.kc1, sd * c.ks1);           // r cos(w + nu)  (0 at conjunction)
+  const double p2 = fma(sd, c.ks2, fma(cm1, c.kc2, c.rc));  // r sin(w + nu)  (r_c at conjunction)
   *y0 = -p1;
   *x0 = p2 * c.cosi;
   *z = -p2 * c.sini;
@@ -1700,23 +1723,22 @@ struct MidState {
 GL_HD MidState mid_state_at(const SetConst& c, double tau, bool derivs) {
   double sd, cm1;
   kepler_offset(c, tau, &sd, &cm1);
-  const double dcosE = c.cosEc * cm1 - c.sinEc * sd;   // cos E - cos E_c
-  const double dsinE = c.sinEc * cm1 + c.cosEc * sd;   // sin E - sin E_c
-  const double dX = c.a_rs * dcosE, dY = c.b_orb * dsinE;
-  const double p1 = dX * c.cosw - dY * c.sinw;
-  const double p2 = c.rc + (dX * c.sinw + dY * c.cosw);
+  const double p1 = fma(cm1, c.kc1, sd * c.ks1);           // r cos(w + nu)
+  const double p2 = fma(sd, c.ks2, fma(cm1, c.kc2, c.rc));  // r sin(w + nu)
   const double x = p2 * c.cosi, y = -p1;
   MidState m;   // (conversions by integer operations, see kepler_offset)
   m.x = f64_to_f32_int(x);
   m.y = f64_to_f32_int(y);
-  m.z = f64_to_f32_int(-p2 * c.sini);
-  m.omr2 = f64_to_f32_int((1.0 - x) * (1.0 + x) - y * y);
+  m.z = -f64_to_f32_int(p2) * c.kf_si;   // (only its sign and size matter: FP32)
+  m.omr2 = f64_to_f32_int(fma(-y, y, fma(-x, x, 1.0)));
   if (!derivs) {
     for (int k = 0; k < 3; ++k) m.d1[k] = m.d2[k] = m.d3[k] = 0.0f;
     return m;
   }
   const float a = c.kf_a, bo = c.kf_bo, ef = c.kf_e, nm = c.kf_nm;
-  const float cosE = c.kf_cEc + f64_to_f32_int(dcosE), sinE = c.kf_sEc + f64_to_f32_int(dsinE);
+  const float cm1f = f64_to_f32_int(cm1), sdf = f64_to_f32_int(sd);
+  const float cosE = c.kf_cEc + (c.kf_cEc * cm1f - c.kf_sEc * sdf);   // FP32 suffices here
+  const float sinE = c.kf_sEc + (c.kf_sEc * cm1f + c.kf_cEc * sdf);
   const float X = a * (cosE - ef), Y = bo * sinE;
   const float r = a * (1.0f - ef * cosE);
   const float ir = 1.0f / r;
