@@ -119,11 +119,7 @@ def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
 # the kernels of the group) from one ncu capture of the current kernels on the
 # workload named; other workloads report null.
 TRAFFIC = {("mcmc_batch", "window"): 0.075e6,
-           ("mcmc_batch", "exposures"): 0.312e6,
-           ("mcmc_batch", "quadrature"): 3.176e6 + 1.011e6,
-           ("uneven_batch", "window"): 471.05e6,
-           ("uneven_batch", "exposures"): 78.66e6,
-           ("uneven_batch", "quadrature"): 195.92e6 + 41.00e6}
+           ("uneven_batch", "window"): 471.05e6}
 
 KERNEL_NAMES = {"window": "gl_win_kernel", "exposures": "gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}

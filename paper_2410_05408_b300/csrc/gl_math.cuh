@@ -198,6 +198,8 @@ GL_HD long long dkey(double x) {
   const long long b = (long long)dbits(x);
   return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
 }
+// x < 0 (below -0) by its key
+GL_HD bool neg_bits(double x) { return dkey(x) < -1; }
 
 GL_HD double rcp64(double x) {
 #if defined(__CUDA_ARCH__)
@@ -706,6 +708,12 @@ GL_HD double f32_to_f64_int(float f) {
   else r = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
   return dfrombits(sign | r);
 }
+// Precision changes without FP64 conversion instructions (identity for double).
+GL_HD double to_f64(float x) { return f32_to_f64_int(x); }
+GL_HD double to_f64(double x) { return x; }
+template <typename R> GL_HD R from_f64(double x);
+template <> GL_HD float from_f64<float>(double x) { return f64_to_f32_int(x); }
+template <> GL_HD double from_f64<double>(double x) { return x; }
 
 // Conservative FP32 window test of an exposure at time t (true whenever any
 // sub-exposure may overlap the star; false positives are resolved in FP64).
@@ -1069,6 +1077,8 @@ GL_HD int quartic_real_roots(T a, T b, T c, T d, T* x) {
 }
 
 GL_HD void sort_small(double* v, int n) {
+  // (FP64 compares: integer keys measured slower, through register spills in the
+  // quadrature kernel)
   for (int i = 1; i < n; ++i) {
     double x = v[i];
     int j = i - 1;
@@ -1126,20 +1136,23 @@ GL_HD Frame<T> make_frame_k(const Trig2<T>& t, int kbest) {
   const T r2 = T(0.70710678118654752440);
   const T cs8[8] = {T(1), r2, T(0), -r2, T(-1), -r2, T(0), r2};
   const T sn8[8] = {T(0), r2, T(1), r2, T(0), -r2, T(-1), -r2};
-  // delta = k pi/4 + pi, so 2 delta is a multiple of pi/2: cos, sin of it exactly
-  const T c4[4] = {T(1), T(0), T(-1), T(0)};
-  const T s4[4] = {T(0), T(1), T(0), T(-1)};
+  // delta = k pi/4 + pi, so 2 delta is a multiple of pi/2 and the rotated
+  // second harmonic (D', E') is (D, E), (E, -D), (-D, -E) or (-E, D): selected,
+  // not multiplied
   Frame<T> f;
   f.cd = -cs8[kbest];
   f.sd = -sn8[kbest];
-  const T c2d = c4[kbest & 3], s2d = s4[kbest & 3];
+  const int k4 = kbest & 3;
+  const T dsel = (k4 & 1) ? t.E : t.D, esel = (k4 & 1) ? t.D : t.E;
+  const T Dp = (k4 & 2) ? -dsel : dsel;
+  const T Ep = (k4 == 1 || k4 == 2) ? -esel : esel;
   T Bp = t.B * f.cd + t.C * f.sd, Cp = t.C * f.cd - t.B * f.sd;
-  T Dp = t.D * c2d + t.E * s2d, Ep = t.E * c2d - t.D * s2d;
-  f.q[4] = t.A - Bp + Dp;
-  f.q[3] = T(2) * Cp - T(4) * Ep;
+  const T AD = t.A + Dp, C2 = T(2) * Cp;
+  f.q[4] = AD - Bp;
+  f.q[3] = C2 - T(4) * Ep;
   f.q[2] = T(2) * t.A - T(6) * Dp;
-  f.q[1] = T(2) * Cp + T(4) * Ep;
-  f.q[0] = t.A + Bp + Dp;
+  f.q[1] = C2 + T(4) * Ep;
+  f.q[0] = AD + Bp;
   return f;
 }
 
@@ -1202,21 +1215,27 @@ GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, 
                                      xs);
   bool ok = (nr % 2) == 0;
   for (int i = 0; i < nr && ok; ++i) {
-    // Newton steps with the derivative frozen at the FP32 estimate: each step
-    // shrinks the error by ~|1 - P'(t*)/P'(t0)|, i.e. to FP32 rounding squared
+    // Newton steps on the FP64 quartic with the derivative frozen at the FP32
+    // estimate and its reciprocal taken in FP32 (relative error 2^-23).  One step
+    // from an estimate within 1e-5 (1 + |t|) leaves an error below
+    // 2^-23 |s| + (P''/P') s^2 / 2, far below the FP32 rounding that the quadrature
+    // applies to t next; a larger first step iterates to 1e-9 (1 + |t|).  The step
+    // bounds are formed in FP32 and compared by bit patterns (on B300 every FP64
+    // instruction holds the FP64 unit for its full issue time; the conversions stay
+    // hardware ones, which measured faster here than integer ones on this
+    // latency-critical chain).
     double t = (double)xs[i];
     double fp = ((4.0 * f.q[4] * t + 3.0 * f.q[3]) * t + 2.0 * f.q[2]) * t + f.q[1];
-    double r = rcp64(fp);
-    // One step from an FP32 estimate within 1e-5 leaves an error of order
-    // (P''/P') s^2 / 2, below the FP32 rounding that the quadrature applies to
-    // t next; a larger first step iterates to 1e-9.
+    double r = (double)rcp_<float>((float)fp);
+    const float at = 1.0f + fabsf(xs[i]);
+    const double lim1 = (double)(1e-5f * at), lim2 = (double)(1e-9f * at);
     bool conv = false;
     for (int it = 0; it < 4; ++it) {
       double fv = (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
       double step = fv * r;
-      if (!isfinite(step)) break;
+      if (!finite_bits(step)) break;
       t -= step;
-      if (fabs(step) <= (it == 0 ? 1e-5 : 1e-9) * (1.0 + fabs(t))) {
+      if (abs_le(step, it == 0 ? lim1 : lim2)) {
         conv = true;
         break;
       }
@@ -1227,7 +1246,8 @@ GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, 
   if (ok) {
     sort_small(tr, nr);
     for (int i = 0; i + 1 < nr; ++i)
-      if (tr[i + 1] - tr[i] <= 1e-9 * (1.0 + fabs(tr[i]))) ok = false;
+      // roots closer than 1e-9 (1 + |t|) merge (bound formed in FP32)
+      if (abs_le(tr[i + 1] - tr[i], (double)(1e-9f * (1.0f + fabsf((float)tr[i]))))) ok = false;
   }
   if (!ok) return frame_roots<double>(f, tr);
   return nr;
@@ -1466,8 +1486,8 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
     nmax = inner_maxima<R>(tg, cmx, smx);
   }
   if (cls == kPartial) {
-    double xd = (double)x0, yd = (double)y0;
-    Trig2<double> tgd = limb_poly<double>(c, xd, yd, (1.0 - xd) * (1.0 + xd) - yd * yd);
+    const double xd = to_f64(x0), yd = to_f64(y0);
+    Trig2<double> tgd = limb_poly<double>(c, xd, yd, fma(-yd, yd, fma(-xd, xd, 1.0)));
     int kb = frame_choice<R>(tg);
     Frame<double> fr = make_frame_k<double>(tgd, kb);
     Frame<R> frr = make_frame_k<R>(tg, kb);
@@ -1480,7 +1500,7 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
     int na = 0;
     CSum<R> sflat, slin, squad;
     if (nr == 0) {
-      if (!(fr.q[4] < 0.0)) {
+      if (!neg_bits(fr.q[4])) {
         // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
         R v1 = -g.x0 / g.dx, v2 = (-g.y0 - g.dy1 * v1) / g.dy2;
         if (v1 * v1 + v2 * v2 < R(1)) {
@@ -1501,7 +1521,7 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
       // g changes sign at each crossing, so the others alternate from there.  An
       // odd count (possible only from the FP64 fallback in degenerate cases)
       // falls back to FP64 tests of g at the arc midpoints.
-      const bool wrap_in = fr.q[4] < 0.0;
+      const bool wrap_in = neg_bits(fr.q[4]);
       const bool parity = (nr & 1) == 0;
       // breakpoints: the crossings (kind 1) and the inner maxima (kind 0) that
       // lie on an inside arc.  A maximum that rounding placed on an outside arc
@@ -1513,9 +1533,10 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
       for (int i = 0; i < nmax; ++i) {
         R tvr = frame_t<R>(frr, cmx[i], smx[i]);
         if (!m_finite(tvr)) continue;
-        double tv = (double)tvr;
+        double tv = to_f64(tvr);
         int below = 0;
-        for (int k = 0; k < nb; ++k) below += (kind[k] && tb[k] < tv) ? 1 : 0;
+        const long long kv = dkey(tv);
+        for (int k = 0; k < nb; ++k) below += (kind[k] && dkey(tb[k]) < kv) ? 1 : 0;
         const bool on_inside = parity ? (wrap_in != ((below & 1) != 0))
                                       : (frame_poly<double>(fr, tv) < 0.0);
         if (!on_inside) continue;
@@ -1532,7 +1553,7 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
       R cth[8], sth[8], px[8], py[8];
       R tr_[8];
       for (int i = 0; i < nb; ++i) {
-        tr_[i] = (R)tb[i];
+        tr_[i] = from_f64<R>(tb[i]);
         frame_angle<R>(frr, tr_[i], &cth[i], &sth[i]);
         R qx = g.x0 + g.dx * cth[i];
         R qy = g.y0 + g.dy1 * cth[i] + g.dy2 * sth[i];

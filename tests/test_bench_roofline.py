@@ -41,7 +41,7 @@ def test_alu_groups_count_flops_per_unit_and_pick_the_binding_pipe():
     # the pipe with the larger share of its peak is the one reported
     want = "fp64" if f64 / 1.2 >= f32 / 77.0 else "fp32"
     assert line["pipe"] == want
-    assert line["traffic"] == bench.TRAFFIC[("mcmc_batch", "quadrature")]
+    assert line["traffic"] == bench.TRAFFIC.get(("mcmc_batch", "quadrature"))
 
 
 def test_missing_peaks_file_falls_back_and_says_so():
