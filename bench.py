@@ -118,8 +118,12 @@ def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, summed over
 # the kernels of the group) from one ncu capture of the current kernels on the
 # workload named; other workloads report null.
-TRAFFIC = {("mcmc_batch", "window"): 0.075e6,
-           ("uneven_batch", "window"): 471.05e6}
+TRAFFIC = {("mcmc_batch", "window"): 0.082e6,
+           ("mcmc_batch", "exposures"): 0.331e6,
+           ("mcmc_batch", "quadrature"): 3.169e6 + 1.012e6,
+           ("uneven_batch", "window"): 470.97e6,
+           ("uneven_batch", "exposures"): 78.23e6,
+           ("uneven_batch", "quadrature"): 126.63e6 + 41.01e6}
 
 KERNEL_NAMES = {"window": "gl_win_kernel", "exposures": "gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
