@@ -108,3 +108,65 @@ def test_pipeline_kernels_are_profiled(ctx):
                                                 binding.GL_KERNEL_CURVE, binding.GL_KERNEL_QUAD)}
     ctx.profile(False)
     assert all(n == 2 for n in got.values()), got
+
+
+def _boundary_batch(csr):
+    """Curve lengths around the window kernel's pass and warp widths (0, 1, 31-33,
+    255-257, 511-513, 1023-1025 exposures) or a shared grid of 777 times; three
+    invalid sets (unbound orbits) and three whole-orbit sets (a/R* = 1.05) mixed in."""
+    wl = inputs.uneven_batch(n_curves=240, seed=21, min_len=100, max_len=2000)
+    p = {k: np.array(v, copy=True) for k, v in wl["params"].items()}
+    n = len(p["t0"])
+    for s in (5, 77, 200):
+        p["ecc"][s] = 1.5
+    for s in (9, 110, 233):   # an orbit inside 1 + R_eq: no window, every time kept
+        p["a_rs"][s], p["b"][s], p["ecc"][s] = 1.05, 0.1, 0.0
+    if csr:
+        pattern = [0, 1, 2, 31, 32, 33, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 0, 3]
+        lengths = np.array([pattern[s % len(pattern)] for s in range(n)], dtype=np.int64)
+        off = np.zeros(n + 1, dtype=np.int64)
+        off[1:] = np.cumsum(lengths)
+        t = np.concatenate([(np.arange(m) - 0.5 * (m - 1)) * wl["exptime"][s]
+                            for s, m in enumerate(lengths)])
+        return dict(wl, params=p, t=t, offsets=off), lengths
+    t = (np.arange(777) - 388.0) * 900.0 / 86400.0
+    out = dict(wl, params=p, t=t, exptime=np.full(n, 900.0 / 86400.0), nsuper=15)
+    out.pop("offsets")
+    return out, np.full(n, 777, dtype=np.int64)
+
+
+@pytest.mark.parametrize("csr", [True, False])
+@pytest.mark.parametrize("prec", PRECS)
+def test_window_kernel_set_boundaries(ctx, csr, prec):
+    """The window kernel's per-thread set cursor and its fast and general passes,
+    on ranges that start and end at every offset within a pass: the pipeline must
+    equal the tile path bit for bit, invalid sets must be NaN throughout and the
+    others finite."""
+    wl, lengths = _boundary_batch(csr)
+    d = _prepare(wl)
+
+    def run():
+        out = torch.empty(d["n_total"], dtype=torch.float64, device="cuda")
+        for _ in range(2):   # eager first call, then the captured graph
+            ctx.lightcurve(d["p"], d["t"], out, d["exptime"], nsuper=d["ns"],
+                           offsets=d["offsets"], precision=prec)
+        torch.cuda.synchronize()
+        assert ctx.sync() == binding.GL_ENUMERIC   # the invalid sets are reported
+        return out.cpu().numpy()
+
+    try:
+        ctx.item_pipeline(True)
+        on = run()
+        ctx.item_pipeline(False)
+        off = run()
+    finally:
+        ctx.item_pipeline(True)
+    same = (on == off) | (np.isnan(on) & np.isnan(off))
+    assert same.all(), (int((~same).sum()), float(np.nanmax(np.abs(on - off))))
+    starts = np.concatenate([[0], np.cumsum(lengths)])
+    bad = np.zeros(len(on), dtype=bool)
+    for s in (5, 77, 200):
+        bad[starts[s]:starts[s + 1]] = True
+    assert np.isnan(on[bad]).all()
+    assert np.isfinite(on[~bad]).all()
+    assert (on[~bad] < 1.0).sum() > 0
