@@ -208,21 +208,33 @@ def load():
         return lib
 
 
+_TORCH = None   # (torch.Tensor, {dtype name: torch dtype}) once torch is imported
+_NP_DTYPES = {n: np.dtype(n) for n in ("float64", "int64", "int32", "float32")}
+
+
+def _torch():
+    global _TORCH
+    if _TORCH is None:
+        import torch
+        _TORCH = (torch.Tensor, {"float64": torch.float64, "int64": torch.int64,
+                                 "int32": torch.int32, "float32": torch.float32})
+    return _TORCH
+
+
 def _ptr(a, dtype: str):
-    """Raw pointer of a contiguous tensor/array of the given dtype (None stays None)."""
+    """Raw pointer of a contiguous tensor/array of the given dtype (None stays None).
+    (Called ~20 times per light-curve call: the checks are kept cheap.)"""
     if a is None:
         return None
-    if isinstance(a, np.ndarray):
-        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
-            raise TypeError(f"expected contiguous {dtype} numpy array, got {a.dtype}")
-        return a.ctypes.data
-    import torch
-    if isinstance(a, torch.Tensor):
-        want = {"float64": torch.float64, "int64": torch.int64, "int32": torch.int32,
-                "float32": torch.float32}[dtype]
-        if a.dtype != want or not a.is_contiguous():
+    tensor, want = _TORCH if _TORCH is not None else _torch()
+    if isinstance(a, tensor):
+        if a.dtype is not want[dtype] or not a.is_contiguous():
             raise TypeError(f"expected contiguous {dtype} tensor, got {a.dtype}")
         return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if a.dtype != _NP_DTYPES[dtype] or not a.flags.c_contiguous:
+            raise TypeError(f"expected contiguous {dtype} numpy array, got {a.dtype}")
+        return a.ctypes.data
     raise TypeError(f"unsupported array type {type(a)}")
 
 
