@@ -242,10 +242,12 @@ __global__ void gl_maxdiff_kernel(const double* a, const double* b, int64_t n,
 // Two ways to the same numbers (chosen by gl_item_pipeline):
 //
 // Item pipeline (default), four flat kernels after the per-set constants:
-//   gl_win_kernel    one thread per exposure: conservative FP32 window test and
-//                    the exact FP64 one; exposures outside get flux 1, the rest
-//                    are appended to a kept-exposure list
-//   gl_expgeo_kernel one thread per kept exposure: midpoint state (FP64 Kepler);
+//   gl_win_kernel    two exposures per thread and pass: the conservative FP32
+//                    window test (no FP64 instruction); exposures outside get
+//                    flux 1, the rest are appended to a kept-exposure list
+//   gl_expgeo_kernel one thread per kept exposure: the exact FP64 window test
+//                    (exposures that fail it get flux 1) and the midpoint state
+//                    (FP64 Kepler);
 //                    then the block's threads together: the position and overlap
 //                    class of each sub-exposure; items that meet the disk go to
 //                    global queues (crossing items from the back of one, whole
