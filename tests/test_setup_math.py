@@ -215,3 +215,65 @@ def test_kepler_newton_step_against_long_double():
     assert float(worst) <= 2e-14, worst   # measured 2.0e-15
     assert float(worst_mid) <= 1.2e-7, worst_mid   # FP32 rounding of |x| < 2
     assert float(bad) == 0
+
+
+KEYS_SRC = r'''
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <cfloat>
+#include <random>
+#include "gl_math.cuh"
+static double db(unsigned long long u) { double d; memcpy(&d, &u, 8); return d; }
+int main() {
+  std::mt19937_64 g(9);
+  std::uniform_real_distribution<double> U(-3.0, 3.0);
+  long bad = 0, n = 0;
+  const double edge[] = {0.0, -0.0, 1.0, -1.0, DBL_MIN, -DBL_MIN, DBL_MAX, -DBL_MAX, INFINITY,
+                         -INFINITY, 5e-324, -5e-324, 0.25, 0.02, -0.02};
+  auto pick = [&](int i) -> double {
+    if (i % 4 == 0) return edge[g() % 15];
+    if (i % 4 == 1) return db(g());             // any bit pattern, every exponent
+    return U(g);
+  };
+  for (int i = 0; i < 4000000; ++i) {
+    const double a = pick(i), b = pick(i + 1);
+    if (std::isnan(a) || std::isnan(b)) continue;
+    ++n;
+    // order of values (pairs of zeros aside: -0 sorts just below +0, pinned below)
+    if (!(a == 0.0 && b == 0.0)) {
+      bad += (gl::dkey(a) < gl::dkey(b)) != (a < b);
+      bad += (gl::dkey(a) <= gl::dkey(b)) != (a <= b);
+    }
+    bad += gl::neg_bits(a) != (a < 0.0);
+    const double m = std::fabs(b);
+    bad += gl::abs_lt(a, m) != (std::fabs(a) < m);
+    bad += gl::abs_le(a, m) != (std::fabs(a) <= m);
+    bad += gl::finite_bits(a) != (bool)std::isfinite(a);
+  }
+  bad += gl::neg_bits(NAN) || gl::abs_lt(NAN, 1.0) || gl::finite_bits(NAN);
+  bad += gl::dkey(-0.0) != gl::dkey(0.0) - 1 || gl::neg_bits(-0.0) || !gl::abs_le(-0.0, 0.0);
+  printf("%ld %ld\n", bad, n);
+}
+'''
+
+
+def test_integer_keys_order_doubles_like_their_values():
+    """dkey, neg_bits, abs_lt, abs_le and finite_bits (the integer compares that
+    replace FP64 compares in the window test, sign tests and series branches)
+    against the FP64 comparisons on random bit patterns, ordinary values and
+    edge cases (zeros, subnormals, extremes, infinities; -0 sorts just below +0)."""
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "k.cpp")
+        exe = os.path.join(d, "k")
+        with open(src, "w") as fh:
+            fh.write(KEYS_SRC)
+        inc = os.path.join(ROOT, "paper_2410_05408_b300", "csrc")
+        r = subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", inc, src,
+                            "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail(r.stderr)
+        bad, n = map(int, subprocess.run([exe], capture_output=True, text=True,
+                                         check=True).stdout.split())
+    assert n > 3_000_000
+    assert bad == 0
