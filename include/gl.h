@@ -102,7 +102,9 @@ typedef struct {
  *             nsuper_all for every set.
  * Sub-exposure q of an exposure at t sits at t + ((q + 1/2)/n - 1/2) exptime and
  * the exposure's flux is the mean of its sub-exposure fluxes (the paper does not
- * describe supersampling; this is the midpoint rule).
+ * describe supersampling; this is the midpoint rule).  A time that is NaN or
+ * infinite lies outside the transit window, so its flux is 1; for an orbit so
+ * tight that its window spans the whole orbit, such a time gives NaN instead.
  */
 typedef struct {
   const double *t;
@@ -469,8 +471,9 @@ int gl_ensemble_sweep(gl_context *ctx, const gl_ensemble *e, const double *rnd,
  * hosted by a process that forbids allocation outside its own allocator.  This
  * entry point needs no context and calls no cudaMalloc, cudaFree or other
  * allocating routine.  Its per-set workspace is one fixed array compiled into
- * the library (GL_NOALLOC_MAX_SETS entries, about 0.8 MB), which every GPU that
- * runs it holds until the process exits.
+ * the library: GL_NOALLOC_MAX_SETS x 576 bytes of per-set constants plus 256
+ * bytes of status, 2 359 552 bytes (about 2.36 MB), which every GPU that loads
+ * the library holds until the process exits.
  *
  *   p, t, out, prec, stream  as for gl_lightcurve_batch, on the current CUDA
  *                            device, except that every array must be device
@@ -479,6 +482,10 @@ int gl_ensemble_sweep(gl_context *ctx, const gl_ensemble *e, const double *rnd,
  * Returns GL_OK; GL_EINVAL for a NULL or host pointer, n_sets > GL_NOALLOC_MAX_SETS
  * or any size check of gl_lightcurve_batch; GL_ECUDA on a runtime failure.
  * Physically invalid parameter sets give NaN outputs (no status is kept).
+ * CSR offsets are not validated by this entry point: offsets that do not rise
+ * from 0 to n_total give unspecified light curves (exposures attributed to other
+ * sets), still with every read inside offsets[0 .. n_sets], t[0 .. n_total) and
+ * the parameter arrays, every write inside out[0 .. n_total), and GL_OK.
  *
  * The first call on a device uploads the quadrature tables and looks up the
  * array's device address on that device; make that first call before any

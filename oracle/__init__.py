@@ -96,11 +96,46 @@ def _load():
         lib.orc_triaxial_ellipse.argtypes = [d, d, d, d, d, d, pd, pd, pd]
         lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_max_threads.argtypes = []
+        lib.orc_failures.restype = ctypes.c_int64
+        lib.orc_failures.argtypes = []
+        lib.orc_reset_failures.restype = None
+        lib.orc_reset_failures.argtypes = []
         _lib = lib
         return lib
 
 
 DEFAULT_TOL = 1e-15
+
+
+class OracleQuadratureError(RuntimeError):
+    """Some evaluation's adaptive quadrature ran out of panels before reaching
+    its tolerance: that value is not the Sec. 2 integral to the stated accuracy."""
+
+
+def failures() -> int:
+    """Evaluations whose quadrature missed its tolerance since the last reset
+    (each one's flux is NaN)."""
+    return int(_load().orc_failures())
+
+
+def reset_failures() -> None:
+    _load().orc_reset_failures()
+
+
+def _checked(run, strict: bool):
+    """Run one oracle call with the failure counter reset before it; raise if any
+    evaluation in it missed its tolerance (strict), else leave the NaNs."""
+    with _lock_calls:
+        reset_failures()
+        out = run()
+        nfail = failures()
+    if nfail and strict:
+        raise OracleQuadratureError(
+            f"{nfail} oracle evaluation(s) did not reach the quadrature tolerance")
+    return out
+
+
+_lock_calls = threading.Lock()
 
 
 def _p(a: np.ndarray):
@@ -178,9 +213,12 @@ def occulted_moments(x0, y0, dx, dy1, dy2, tol=DEFAULT_TOL):
     return out
 
 
-def flux_sky(x0, y0, z, dx, dy1, dy2, u1, u2, tol=DEFAULT_TOL):
-    return _load().orc_flux_sky(float(x0), float(y0), float(z), float(dx), float(dy1),
-                                float(dy2), float(u1), float(u2), float(tol))
+def flux_sky(x0, y0, z, dx, dy1, dy2, u1, u2, tol=DEFAULT_TOL, strict: bool = True):
+    """Relative flux of one sky configuration.  OracleQuadratureError if the
+    quadrature missed `tol` (strict), else NaN for that case."""
+    return _checked(lambda: _load().orc_flux_sky(float(x0), float(y0), float(z), float(dx),
+                                                 float(dy1), float(dy2), float(u1), float(u2),
+                                                 float(tol)), strict)
 
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi",
@@ -188,7 +226,8 @@ PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi
 
 
 def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
-               tol: float = DEFAULT_TOL, nthreads: int = 0, locked: bool = False) -> np.ndarray:
+               tol: float = DEFAULT_TOL, nthreads: int = 0, locked: bool = False,
+               strict: bool = True) -> np.ndarray:
     """Supersampled light curves for a batch of parameter sets.
 
     ``params`` maps each of PARAM_NAMES to an array of n_sets floats, and may add
@@ -223,9 +262,10 @@ def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
         ns_p, ns_all = ns_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0
     g_arr, g_p = _optional(params.get("g"), n_sets)
     z_arr, z_p = _optional(params.get("zeta"), n_sets)
-    st = lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], g_p, z_p, int(bool(locked)), _p(t),
-                            offp, n_times,
-                            _p(exptime), ns_p, ns_all, float(tol), int(nthreads), _p(out))
+    st = _checked(lambda: lib.orc_lightcurve(n_sets, *[_p(a) for a in arrs], g_p, z_p,
+                                             int(bool(locked)), _p(t), offp, n_times,
+                                             _p(exptime), ns_p, ns_all, float(tol),
+                                             int(nthreads), _p(out)), strict)
     if st != 0:
         raise ValueError("oracle rejected its inputs")
     if offsets is None:
@@ -234,17 +274,19 @@ def lightcurve(params: dict, t, exptime, nsuper, offsets=None,
 
 
 def flux_sky_batch(x0, y0, z, k, f, eta, xi, u1, u2, tol: float = DEFAULT_TOL,
-                   nthreads: int = 0, g=None, zeta=None) -> np.ndarray:
+                   nthreads: int = 0, g=None, zeta=None, strict: bool = True) -> np.ndarray:
     """Relative flux for arrays of sky positions and shapes (k, f, eta, xi; with
-    g and zeta, the triaxial shape of triaxial_ellipse)."""
+    g and zeta, the triaxial shape of triaxial_ellipse).  An evaluation whose
+    quadrature misses ``tol`` raises OracleQuadratureError (``strict``), else is
+    NaN."""
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
             for a in (x0, y0, z, k, f, eta, xi, u1, u2)]
     n = arrs[0].size
     g_arr, g_p = _optional(g, n)
     z_arr, z_p = _optional(zeta, n)
     out = np.empty(n)
-    _load().orc_flux_sky_batch(n, *[_p(a) for a in arrs], g_p, z_p, float(tol), int(nthreads),
-                               _p(out))
+    _checked(lambda: _load().orc_flux_sky_batch(n, *[_p(a) for a in arrs], g_p, z_p, float(tol),
+                                                int(nthreads), _p(out)), strict)
     return out
 
 
@@ -254,5 +296,5 @@ def max_threads() -> int:
 
 __all__ = ["build", "kepler_E", "cos_inclination", "sky_position", "projected_ellipse",
            "oblate_ellipse", "q_to_u", "occulted_moments", "flux_sky", "lightcurve",
-           "flux_sky_batch",
+           "flux_sky_batch", "failures", "reset_failures", "OracleQuadratureError",
            "max_threads", "PARAM_NAMES", "DEFAULT_TOL", "math"]

@@ -12,6 +12,12 @@ loss).
 
 Parameters are a list of (W, b) per layer, W of shape (fan_in, fan_out), so a
 layer computes z = x @ W + b.
+
+``round_act`` (optional) is a rounding applied, as the workload's BF16 network
+does, to every hidden activation SiLU(z) before the next layer uses it and to
+every gradient with respect to a hidden pre-activation z before it is used (the
+output layer's z and its gradient are not rounded).  With ``round_act`` None the
+computation is the plain FP64 network.
 """
 from __future__ import annotations
 
@@ -38,21 +44,27 @@ def init_params(rng: np.random.Generator, widths=WIDTHS):
     return params
 
 
-def forward(params, x):
+def _identity(a):
+    return a
+
+
+def forward(params, x, round_act=None):
     """Returns the output (n,) and the per-layer inputs and pre-activations."""
+    rnd = round_act or _identity
     a = np.asarray(x, dtype=np.float64)
     acts, pres = [a], []
     for li, (W, b) in enumerate(params):
         z = a @ W + b
         pres.append(z)
-        a = silu(z) if li + 1 < len(params) else z
+        a = rnd(silu(z)) if li + 1 < len(params) else z
         acts.append(a)
     return a[:, 0], (acts, pres)
 
 
-def loss_and_grads(params, x, target):
+def loss_and_grads(params, x, target, round_act=None):
     """Mean squared error over the batch and its gradient for every (W, b)."""
-    y, (acts, pres) = forward(params, x)
+    rnd = round_act or _identity
+    y, (acts, pres) = forward(params, x, round_act)
     n = y.shape[0]
     r = y - np.asarray(target, dtype=np.float64)
     loss = float(np.mean(r * r))
@@ -62,7 +74,7 @@ def loss_and_grads(params, x, target):
         W, _ = params[li]
         grads[li] = (acts[li].T @ dz, dz.sum(axis=0))
         if li > 0:
-            dz = (dz @ W.T) * silu_grad(pres[li - 1])
+            dz = rnd((dz @ W.T) * silu_grad(pres[li - 1]))
     return loss, grads
 
 

@@ -96,7 +96,8 @@ def prior_draw(u, w):
 def stretch_half(walkers, logpost, active, other, r_z, r_j, r_u, lnpost_fn, a=2.0):
     """One half-step: the walkers `active` propose along lines through members of
     `other` (partner = other[floor(r_j * len(other))]), z = ((a - 1) r_z + 1)^2 / a,
-    accept if log(r_u) < (D - 1) log z + lnpost(Y) - lnpost(X).  Returns the new
+    accept if log(r_u) < (D - 1) log z + lnpost(Y) - lnpost(X), never if
+    lnpost(Y) = -inf, always (for a finite lnpost(Y)) if lnpost(X) = -inf.  Returns the new
     walkers, log posteriors, accepted mask and the proposals' log posteriors."""
     walkers = np.array(walkers, dtype=np.float64, copy=True)
     logpost = np.array(logpost, dtype=np.float64, copy=True)
@@ -105,8 +106,16 @@ def stretch_half(walkers, logpost, active, other, r_z, r_j, r_u, lnpost_fn, a=2.
     partner = np.asarray(other)[np.minimum((r_j * len(other)).astype(np.int64), len(other) - 1)]
     prop = walkers[partner] + z[:, None] * (walkers[active] - walkers[partner])
     lp_new = lnpost_fn(prop)
-    log_r = (d - 1) * np.log(z) + lp_new - logpost[active]
-    ok = np.log(r_u) < log_r
+    lp_old = logpost[active]
+    # Acceptance probability min(1, z^(D-1) p(Y)/p(X)) (Goodman and Weare 2010)
+    # with the cases of zero density written out, so that no NaN decides a move:
+    # a proposal outside the prior (p(Y) = 0) is never taken; a walker outside
+    # the prior (p(X) = 0) takes any proposal inside it; otherwise the log test.
+    new_in = lp_new > -np.inf
+    old_in = lp_old > -np.inf
+    with np.errstate(invalid="ignore"):
+        log_r = (d - 1) * np.log(z) + np.where(new_in & old_in, lp_new - lp_old, 0.0)
+    ok = new_in & (~old_in | (np.log(r_u) < log_r))
     walkers[np.asarray(active)[ok]] = prop[ok]
     logpost[np.asarray(active)[ok]] = lp_new[ok]
     return walkers, logpost, ok, lp_new

@@ -436,16 +436,39 @@ int orc_occulted_moments(double x0, double y0, double dx, double dy1, double dy2
     return status < 0 ? -1 : niv;
 }
 
+/* Evaluations whose occulted moments ran out of panels before reaching the
+ * tolerance since the last orc_reset_failures().  Such an evaluation is not the
+ * Sec. 2 integral to the stated accuracy, so its flux is returned as NaN and
+ * counted here; the Python layer refuses results when this is non-zero. */
+static int64_t orc_nfail = 0;
+
+int64_t orc_failures(void) {
+    int64_t v;
+#pragma omp atomic read
+    v = orc_nfail;
+    return v;
+}
+
+void orc_reset_failures(void) {
+#pragma omp atomic write
+    orc_nfail = 0;
+}
+
 /* Relative flux of one sky configuration (Sec. 2, "Ellipsoid Transit Model").
  * I(r) = c0 + c1 mu + c2 r^2 with c0 = 1-u1-2u2, c1 = u1+2u2, c2 = u2 (the
  * quadratic law rewritten in the basis of the three integrands f_flat, f_lin,
  * f_quad), F0 = pi (1 - u1/3 - u2/6).  A planet behind the star (z > 0) does
- * not occult it (secondary eclipse is not modelled). */
+ * not occult it (secondary eclipse is not modelled).  NaN (and a count in
+ * orc_failures) if the quadrature did not reach `tol`. */
 double orc_flux_sky(double x0, double y0, double z, double dx, double dy1, double dy2,
                     double u1, double u2, double tol) {
     if (z > 0.0) return 1.0;
     double m[3];
-    orc_occulted_moments(x0, y0, dx, dy1, dy2, tol, m);
+    if (orc_occulted_moments(x0, y0, dx, dy1, dy2, tol, m) < 0) {
+#pragma omp atomic update
+        orc_nfail += 1;
+        return NAN;
+    }
     if (m[0] == 0.0 && m[1] == 0.0 && m[2] == 0.0) return 1.0;
     double c0 = 1.0 - u1 - 2.0 * u2, c1 = u1 + 2.0 * u2, c2 = u2;
     double F0 = M_PI * (1.0 - u1 / 3.0 - u2 / 6.0);

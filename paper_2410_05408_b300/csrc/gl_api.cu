@@ -1517,7 +1517,11 @@ __global__ void gl_ens_post_kernel(int64_t m, const double* __restrict__ logprio
     logpost[i] = isfinite(logprior[i]) ? logprior[i] + ll[i] : -INFINITY;
 }
 
-// Accept or reject the half's proposals: log(r_u) < (D - 1) log z + lp(Y) - lp(X).
+// Accept or reject the half's proposals with probability min(1, z^(D-1) p(Y)/p(X))
+// (Goodman and Weare 2010), the zero-density cases written out so that no NaN
+// decides a move: a proposal outside the prior (lp(Y) = -inf, or NaN) is never
+// taken; a walker outside the prior (lp(X) = -inf) takes any proposal inside it;
+// otherwise log(r_u) < (D - 1) log z + lp(Y) - lp(X).
 __global__ void gl_ens_accept_kernel(double* __restrict__ walkers, double* __restrict__ logpost,
                                      int64_t m, int h, const double* __restrict__ prop,
                                      const double* __restrict__ z,
@@ -1527,8 +1531,12 @@ __global__ void gl_ens_accept_kernel(double* __restrict__ walkers, double* __res
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = 2 * i + h;
-    const double log_r = (GL_FIT_DIM - 1) * log(z[i]) + lp_new[i] - logpost[k];
-    if (log(ru[i]) < log_r) {
+    const double ly = lp_new[i], lx = logpost[k];
+    bool take;
+    if (!(ly > -INFINITY)) take = false;
+    else if (!(lx > -INFINITY)) take = true;
+    else take = log(ru[i]) < (GL_FIT_DIM - 1) * log(z[i]) + ly - lx;
+    if (take) {
       for (int d = 0; d < GL_FIT_DIM; ++d) walkers[k * GL_FIT_DIM + d] = prop[i * GL_FIT_DIM + d];
       logpost[k] = lp_new[i];
       if (accepted) atomicAdd(accepted, 1ull);
@@ -3042,6 +3050,8 @@ int gl_flux_sky_simpson(gl_context* ctx, int64_t n, const double* x0, const doub
 // loaded, on every device that runs the entry point.
 namespace {
 
+// The header states the array's size from this layout: keep the two in step.
+static_assert(sizeof(SetConst) == 576, "gl.h documents 576-byte per-set constants");
 constexpr size_t kNoallocStatusOffset = (size_t)GL_NOALLOC_MAX_SETS * sizeof(SetConst);
 constexpr size_t kNoallocBytes = kNoallocStatusOffset + 256;
 

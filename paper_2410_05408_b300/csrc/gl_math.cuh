@@ -193,12 +193,13 @@ GL_HD bool abs_lt(double x, double m) { return (dbits(x) & 0x7fffffffffffffffull
 // isfinite from the exponent bits
 GL_HD bool finite_bits(double x) { return ((dbits(x) >> 52) & 0x7ffu) != 0x7ffu; }
 // A key that orders doubles like their values (signed integer compare; -0 sorts
-// just below +0, NaN above +infinity)
+// just below +0; a NaN sorts by its sign bit: above +infinity when the bit is
+// clear, below -infinity when it is set)
 GL_HD long long dkey(double x) {
   const long long b = (long long)dbits(x);
   return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
 }
-// x < 0 (below -0) by its key
+// x < 0 (below -0) by its key; for a NaN, whether its sign bit is set
 GL_HD bool neg_bits(double x) { return dkey(x) < -1; }
 
 GL_HD double rcp64(double x) {

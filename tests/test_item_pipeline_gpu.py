@@ -170,3 +170,26 @@ def test_window_kernel_set_boundaries(ctx, csr, prec):
     assert np.isnan(on[bad]).all()
     assert np.isfinite(on[~bad]).all()
     assert (on[~bad] < 1.0).sum() > 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_non_finite_times_give_flux_one(ctx, prec):
+    """A time that is NaN (either sign bit) or infinite lies outside every transit
+    window (documented in the header): flux exactly 1, on the pipeline, on the
+    tile path and with the graph replay, while the finite times around it keep
+    their values."""
+    wl = inputs.single_transit(n_times=200)
+    t = np.array(wl["t"], copy=True)
+    nan_neg = np.frombuffer(np.uint64(0xFFF8000000000000).tobytes(), dtype=np.float64)[0]
+    bad = [7, 100, 101, 150]
+    t[bad] = [np.nan, nan_neg, np.inf, -np.inf]
+    wl_bad = dict(wl, t=t)
+    ref = _run(ctx, _prepare(wl), prec)
+    assert np.any(ref[0, bad] < 1.0) if ref.ndim == 2 else np.any(ref[bad] < 1.0)
+    for on in (True, False):
+        ctx.item_pipeline(on)
+        got = _run(ctx, _prepare(wl_bad), prec).reshape(-1)
+        assert np.all(got[bad] == 1.0)
+        keep = np.setdiff1d(np.arange(got.size), bad)
+        assert np.array_equal(got[keep], ref.reshape(-1)[keep])
+    ctx.item_pipeline(True)

@@ -1,10 +1,16 @@
 """Surrogate network kernels (tcgen05) against the FP64 MLP oracle.
 
-The GPU network keeps BF16 copies of the three hidden weight matrices and BF16
-activations; the oracle gets the same BF16-rounded hidden weights and runs in
-FP64, so the comparison measures the kernels' arithmetic (BF16 activations,
-FP32 accumulation) and layout, not a weight mismatch.  Tolerances are relative:
-1.5e-2 on outputs and loss, 5e-2 on each layer's gradient (norm-wise)."""
+The GPU network keeps BF16 copies of the three hidden weight matrices, BF16
+hidden activations and BF16 gradients at the hidden pre-activations; the oracle
+gets the same BF16-rounded hidden weights and rounds the same quantities to BF16
+(its ``round_act`` hook), in FP64 otherwise.  What remains between the two is the
+FP32 accumulation and the rare BF16 rounding that lands on the other side of a
+tie point, so every output and every gradient element is held to
+4 x 2^-8 x sum |a_i b_i| of its own dot product (the BF16 half-ulp scale of each
+term; a single flipped rounding moves one term by at most 2^-7 of itself).  A
+wrong row, column or tile would miss this by orders of magnitude.  The former
+norm-wise checks (1.5e-2 on outputs and loss against the unrounded FP64
+network, 5e-2 per layer's gradient) are kept beside them."""
 import numpy as np
 import pytest
 
@@ -42,6 +48,35 @@ def as_gpu_sees(params):
     return [(bf16(W) if 0 < li < 4 else W, b) for li, (W, b) in enumerate(params)]
 
 
+ELEM = 4.0 * 2.0 ** -8
+
+
+def _out_scale(params, x):
+    """sum_k |h4_k w5_k| + |b5| per sample, on the BF16-aware oracle."""
+    _, (acts, _) = omlp.forward(params, x, round_act=bf16)
+    return np.abs(acts[4]) @ np.abs(params[4][0][:, 0]) + abs(params[4][1][0])
+
+
+def _grad_scales(params, x, t):
+    """Per gradient element, the sum over samples of |input activation x dz| (and
+    of |dz| for the biases), on the BF16-aware oracle."""
+    y, (acts, pres) = omlp.forward(params, x, round_act=bf16)
+    n = y.shape[0]
+    dz = (2.0 / n) * (y - t)[:, None]
+    out = [None] * len(params)
+    for li in range(len(params) - 1, -1, -1):
+        W, _ = params[li]
+        out[li] = (np.abs(acts[li]).T @ np.abs(dz), np.abs(dz).sum(axis=0))
+        if li > 0:
+            dz = bf16((dz @ W.T) * omlp.silu_grad(pres[li - 1]))
+    return out
+
+
+def _elementwise(got, ref, scale, what):
+    bad = np.abs(got - ref) > ELEM * scale + 1e-30
+    assert not bad.any(), (what, int(bad.sum()), float(np.max(np.abs(got - ref) / (scale + 1e-300))))
+
+
 @pytest.fixture(scope="module")
 def net():
     assert torch.cuda.is_available()
@@ -71,8 +106,11 @@ def test_forward_matches_oracle(net, n):
     y = torch.empty(n, dtype=torch.float32, device="cuda")
     net.forward(torch.tensor(x, device="cuda"), y)
     torch.cuda.synchronize()
-    ref, _ = omlp.forward(as_gpu_sees(params), x.astype(np.float64))
+    gp = as_gpu_sees(params)
+    ref, _ = omlp.forward(gp, x.astype(np.float64))
     assert _rel(y.cpu().numpy(), ref) < 1.5e-2
+    ref_b, _ = omlp.forward(gp, x.astype(np.float64), round_act=bf16)
+    _elementwise(y.cpu().numpy(), ref_b, _out_scale(gp, x.astype(np.float64)), "y")
     assert net.status() == binding.GL_OK
 
 
@@ -81,11 +119,22 @@ def test_gradients_match_oracle(net):
     params, x, t = _setup(net, 2, n)
     loss = net.loss_grad(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
     g = unflatten(net.get_grads())
-    ref_loss, ref_g = omlp.loss_and_grads(as_gpu_sees(params), x.astype(np.float64), t)
+    gp = as_gpu_sees(params)
+    xd, td = x.astype(np.float64), t.astype(np.float64)
+    ref_loss, ref_g = omlp.loss_and_grads(gp, xd, td)
     assert abs(loss - ref_loss) / ref_loss < 1.5e-2
     for li, ((gW, gb), (rW, rb)) in enumerate(zip(g, ref_g)):
         assert _rel(gW, rW) < 5e-2, (li, _rel(gW, rW))
         assert _rel(gb, rb) < 5e-2, (li, _rel(gb, rb))
+    # element by element against the BF16-aware oracle
+    lb, gb_ref = omlp.loss_and_grads(gp, xd, td, round_act=bf16)
+    yb, _ = omlp.forward(gp, xd, round_act=bf16)
+    ls = np.mean(2.0 * np.abs(yb - td) * _out_scale(gp, xd))   # d loss = mean 2 r dy
+    assert abs(loss - lb) <= ELEM * ls, (loss, lb, ls)
+    scales = _grad_scales(gp, xd, td)
+    for li, ((gW, gbias), (rW, rb), (sW, sb)) in enumerate(zip(g, gb_ref, scales)):
+        _elementwise(gW, rW, sW, f"dW{li + 1}")
+        _elementwise(gbias, rb, sb, f"db{li + 1}")
     assert net.status() == binding.GL_OK
 
 

@@ -82,3 +82,62 @@ def test_forward_and_adam_match_torch():
     for (W, b), lin in zip(newp, lins):
         np.testing.assert_allclose(W, lin.weight.detach().numpy().T, rtol=0, atol=1e-12)
         np.testing.assert_allclose(b, lin.bias.detach().numpy(), rtol=0, atol=1e-12)
+
+
+def test_rounded_network_matches_torch_autograd():
+    """The BF16 rounding hook, pinned against torch autograd of the same network
+    built independently: hidden activations rounded to BF16 in the forward pass
+    (identity gradient), and the gradient at each hidden pre-activation rounded to
+    BF16 in the backward pass (a function that is the identity forward).  Also:
+    every rounded quantity is a BF16 number, and the hook set to the identity
+    reproduces the plain network bit for bit."""
+    torch = pytest.importorskip("torch")
+
+    def rnd_np(a):
+        return torch.from_numpy(np.asarray(a, dtype=np.float64)).to(torch.bfloat16).double().numpy()
+
+    class RoundFwd(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            return a.to(torch.bfloat16).double()
+
+        @staticmethod
+        def backward(ctx, g):
+            return g
+
+    class RoundGrad(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, z):
+            return z.clone()
+
+        @staticmethod
+        def backward(ctx, g):
+            return g.to(torch.bfloat16).double()
+
+    rng = np.random.default_rng(5)
+    params = mlp.init_params(rng)
+    x = rng.uniform(-1, 1, (24, 7))
+    t = rng.normal(size=24) * 0.3
+    tw = [(torch.from_numpy(W.copy()).requires_grad_(), torch.from_numpy(b.copy()).requires_grad_())
+          for W, b in params]
+    a = torch.from_numpy(x)
+    for li, (W, b) in enumerate(tw):
+        z = a @ W + b
+        if li + 1 < len(tw):
+            a = RoundFwd.apply(torch.nn.functional.silu(RoundGrad.apply(z)))
+        else:
+            a = z
+    loss_t = ((a[:, 0] - torch.from_numpy(t)) ** 2).mean()
+    loss_t.backward()
+    y, (acts, _) = mlp.forward(params, x, round_act=rnd_np)
+    np.testing.assert_allclose(y, a.detach().numpy()[:, 0], rtol=1e-12, atol=1e-12)
+    for h in acts[1:-1]:
+        assert np.array_equal(h, rnd_np(h))
+    loss, grads = mlp.loss_and_grads(params, x, t, round_act=rnd_np)
+    assert abs(loss - float(loss_t)) < 1e-12
+    for (gW, gb), (W, b) in zip(grads, tw):
+        np.testing.assert_allclose(gW, W.grad.numpy(), rtol=1e-10, atol=1e-14)
+        np.testing.assert_allclose(gb, b.grad.numpy(), rtol=1e-10, atol=1e-14)
+    l0, g0 = mlp.loss_and_grads(params, x, t)
+    l1, g1 = mlp.loss_and_grads(params, x, t, round_act=lambda v: v)
+    assert l0 == l1 and all(np.array_equal(p, q) for u, v in zip(g0, g1) for p, q in zip(u, v))

@@ -105,3 +105,26 @@ def test_stretch_half_acceptance_rule():
         else:
             np.testing.assert_array_equal(nw[k], w[k])
     np.testing.assert_array_equal(nw[oth], w[oth])
+
+
+def test_stretch_half_zero_density_cases():
+    """min(1, z^(D-1) p(Y)/p(X)) with zero densities: a proposal outside the prior
+    is never taken, a walker outside the prior takes any proposal inside it, and
+    neither case goes through a NaN (warnings are errors here)."""
+    rng = np.random.default_rng(8)
+    w = rng.normal(size=(8, 3))
+    lp = np.array([-np.inf, 0.0, -np.inf, 0.0, 0.0, 0.0, -np.inf, 0.0])
+    act, oth = np.arange(0, 8, 2), np.arange(1, 8, 2)
+    rz = np.full(4, 0.5)
+    rj = np.array([0.1, 0.3, 0.6, 0.9])
+    ru = np.full(4, 0.999999)   # only a forced acceptance passes the log test
+    inside = np.array([1.0, -np.inf, -np.inf, 5.0])   # lp(Y) per active walker
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        nw, nlp, ok, lp_new = M.stretch_half(w, lp, act, oth, rz, rj, ru,
+                                             lambda y: inside.copy())
+    # walker 0: outside -> finite proposal: taken; walker 2: both outside: kept;
+    # walker 4: inside -> proposal outside: kept; walker 6: outside -> finite: taken
+    np.testing.assert_array_equal(ok, [True, False, False, True])
+    np.testing.assert_array_equal(nlp[act], [1.0, -np.inf, 0.0, 5.0])

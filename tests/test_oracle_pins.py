@@ -533,3 +533,32 @@ def test_kipping_inverse_and_validity():
             mu = np.linspace(0, 1, 101)
             inten = 1 - u1 * (1 - mu) - u2 * (1 - mu) ** 2
             assert inten.min() >= -1e-14 and np.all(np.diff(inten) >= -1e-14)
+
+
+# ---------------------------------------------------------------- failure reporting
+def test_quadrature_failure_is_loud():
+    """An evaluation whose adaptive quadrature cannot reach its tolerance (here an
+    impossible tolerance of 0) is not the Sec. 2 integral: the flux is NaN, it is
+    counted, and the default (strict) wrappers raise instead of returning it."""
+    dx, dy1, dy2 = oracle.oblate_ellipse(0.1, 0.3, 0.4, 0.7)
+    geo = (0.95, 0.2, -1.0, dx, dy1, dy2, 0.4, 0.25)
+    with pytest.raises(oracle.OracleQuadratureError):
+        oracle.flux_sky(*geo, tol=0.0)
+    v = oracle.flux_sky(*geo, tol=0.0, strict=False)
+    assert math.isnan(v) and oracle.failures() == 1
+    # the same geometry at the default tolerance is fine and resets the counter
+    assert 0.0 < oracle.flux_sky(*geo) < 1.0 and oracle.failures() == 0
+    arr = dict(x0=[0.95, 3.0], y0=[0.2, 0.0], z=[-1.0, -1.0], k=[0.1, 0.1], f=[0.3, 0.3],
+               eta=[0.4, 0.4], xi=[0.7, 0.7], u1=[0.4, 0.4], u2=[0.25, 0.25])
+    with pytest.raises(oracle.OracleQuadratureError):
+        oracle.flux_sky_batch(**arr, tol=0.0)
+    out = oracle.flux_sky_batch(**arr, tol=0.0, strict=False)
+    assert math.isnan(out[0]) and out[1] == 1.0 and oracle.failures() == 1
+    p = {n: np.array([v]) for n, v in dict(t0=0.0, period=10.0, a_rs=20.0, b=0.3, ecc=0.0,
+                                            omega=math.pi / 2, k=0.1, f=0.3, eta=0.4, xi=0.7,
+                                            u1=0.4, u2=0.25).items()}
+    t = np.array([-0.04, 0.0, 3.0])
+    with pytest.raises(oracle.OracleQuadratureError):
+        oracle.lightcurve(p, t, 0.01, 3, tol=0.0)
+    lc = oracle.lightcurve(p, t, 0.01, 3, tol=0.0, strict=False)[0]
+    assert np.isnan(lc[:2]).all() and lc[2] == 1.0

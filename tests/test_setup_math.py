@@ -251,7 +251,12 @@ int main() {
     bad += gl::abs_le(a, m) != (std::fabs(a) <= m);
     bad += gl::finite_bits(a) != (bool)std::isfinite(a);
   }
-  bad += gl::neg_bits(NAN) || gl::abs_lt(NAN, 1.0) || gl::finite_bits(NAN);
+  // NaN of either sign: ordered by its sign bit, never finite, never below a bound
+  const double pnan = db(0x7ff8000000000000ull), nnan = db(0xfff8000000000000ull);
+  bad += gl::neg_bits(pnan) || !gl::neg_bits(nnan);
+  bad += !(gl::dkey(pnan) > gl::dkey(INFINITY)) || !(gl::dkey(nnan) < gl::dkey(-INFINITY));
+  bad += gl::abs_lt(pnan, 1.0) || gl::abs_lt(nnan, 1.0) || gl::abs_le(nnan, DBL_MAX);
+  bad += gl::finite_bits(pnan) || gl::finite_bits(nnan);
   bad += gl::dkey(-0.0) != gl::dkey(0.0) - 1 || gl::neg_bits(-0.0) || !gl::abs_le(-0.0, 0.0);
   printf("%ld %ld\n", bad, n);
 }
@@ -262,7 +267,8 @@ def test_integer_keys_order_doubles_like_their_values():
     """dkey, neg_bits, abs_lt, abs_le and finite_bits (the integer compares that
     replace FP64 compares in the window test, sign tests and series branches)
     against the FP64 comparisons on random bit patterns, ordinary values and
-    edge cases (zeros, subnormals, extremes, infinities; -0 sorts just below +0)."""
+    edge cases (zeros, subnormals, extremes, infinities; -0 sorts just below +0;
+    a NaN sorts by its sign bit, beyond the infinity of that sign)."""
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "k.cpp")
         exe = os.path.join(d, "k")

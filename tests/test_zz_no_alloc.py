@@ -84,3 +84,24 @@ def test_noalloc_rejects_what_it_cannot_do(ctx):
     assert binding.gl_lightcurve_batch_noalloc(p, wl["t"], host_out, binding.GL_FP32C,
                                                exptime=np.array([0.02]),
                                                nsuper_all=3) == binding.GL_EINVAL
+
+
+def test_noalloc_bad_offsets_stay_in_bounds(ctx):
+    """Offsets are not validated by the allocation-free entry point (documented):
+    a decreasing CSR index returns GL_OK and writes only the n_total outputs
+    (a guard region behind them keeps its sentinel); every output is written."""
+    wl = inputs.uneven_batch(n_curves=8, max_len=400, seed=8)
+    dp, t, exptime, ns, off, n_total = _device_inputs(wl)
+    bad = off.clone()
+    bad[3], bad[4] = off[5], off[2]   # offsets[3] > offsets[4]: not a CSR index
+    guard = 64
+    buf = torch.full((n_total + guard,), -7.0, dtype=torch.float64, device="cuda")
+    rc = binding.gl_lightcurve_batch_noalloc(dp, t, buf[:n_total], binding.GL_FP32C,
+                                             offsets=bad, exptime=exptime, nsuper=ns)
+    assert rc == binding.GL_OK
+    torch.cuda.synchronize()
+    host = buf.cpu().numpy()
+    assert np.all(host[n_total:] == -7.0)
+    body = host[:n_total]
+    assert not np.any(body == -7.0)
+    assert np.all(np.isnan(body) | ((body >= 0.0) & (body <= 1.0)))
