@@ -8,7 +8,9 @@ path is the FP32-compensated one (FP64 Kepler, roots and exposure sums), whose
 max |delta flux| against the plain FP64 GPU path is reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload mcmc_batch|uneven_batch|single_transit]
+                    [--workload mcmc_batch|uneven_batch|single_transit|peaks|
+                                surrogate_train|surrogate_mcmc|simpson_variant|
+                                locked_batch|ensemble]
 
 Under torchrun (N > 1) every rank evaluates its own batch (different seeds):
 the work units are independent, so the ranks share no data-path collective
@@ -38,8 +40,10 @@ from paper_2410_05408_b300 import inputs  # noqa: E402
 METRIC = "oblate flux evals/sec at |dflux|<=1e-7 (FP32) vs FP64 GPU path"
 UNIT = "evals/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 / FP64 non-tensor peaks from unit counts x maximum SM clock (148 SMs,
-# 128 FP32 lanes and 2 FP64 lanes (measured: 1/62 of FP32) per SM, FMA = 2 flops)
+# FP32 / FP64 non-tensor peaks.  Measured in the same run by the pipe probes of
+# libglpeaks.so (include/gl_peaks.h: independent FMA chains over 8 CTAs per SM,
+# best of 5 launches); if the probe cannot run, derived from unit counts x
+# maximum SM clock (148 SMs, 128 FP32 lanes and 2 FP64 lanes per SM, FMA = 2).
 SM_COUNT = 148
 
 
@@ -47,6 +51,19 @@ def alu_peaks(sm_mhz: float):
     fp32 = SM_COUNT * 128 * 2 * sm_mhz * 1e6 / 1e12
     fp64 = SM_COUNT * 2 * 2 * sm_mhz * 1e6 / 1e12
     return fp32, fp64
+
+
+def measured_alu_peaks(device: int, sm_mhz_fallback: float):
+    """(FP32 TFLOP/s, FP64 TFLOP/s, MUFU Top/s, source) from the probes."""
+    from paper_2410_05408_b300 import binding
+    try:
+        f32 = binding.glp_measure(device, binding.GLP_FFMA)["flops_per_s"] / 1e12
+        f64 = binding.glp_measure(device, binding.GLP_DFMA)["flops_per_s"] / 1e12
+        mufu = binding.glp_measure(device, binding.GLP_MUFU)["flops_per_s"] / 1e12
+        return f32, f64, mufu, "of measured (FFMA/DFMA probe, libglpeaks, same run)"
+    except Exception as e:   # noqa: BLE001 - reported in the line
+        f32, f64 = alu_peaks(sm_mhz_fallback)
+        return f32, f64, None, f"of derived (probe failed: {e}): unit counts x max SM clock"
 
 
 # Algorithmic work per unit of the FP32C light-curve step (flops, FMA = 2),
@@ -86,7 +103,9 @@ def window_bytes(c: dict, time_bytes: int) -> int:
     return time_bytes + 8 * (c["exposures"] - c["kept"]) + 8 * c["kept"]
 
 
-def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak: float) -> dict:
+def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak: float,
+                 peak_source: str = "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x "
+                                    "max SM clock") -> dict:
     """Algorithmic FP32 and FP64 flops over a CUDA-event duration, against the
     pipe that bounds them (the larger of flops/peak)."""
     t = ms * 1e-3
@@ -100,8 +119,7 @@ def alu_roofline(f32: float, f64: float, ms: float, fp32_peak: float, fp64_peak:
             "fp64": {"achieved": a64, "peak": fp64_peak, "frac": a64 / fp64_peak,
                      "flops_per_launch": f64},
             "kernel_ms": ms,
-            "peak_source": "derived: 148 SMs x (128 FP32 | 2 FP64) lanes x 2 flops x "
-                           "max SM clock"}
+            "peak_source": peak_source}
 
 
 def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
@@ -130,10 +148,11 @@ KERNEL_NAMES = {"window": "gl_win_kernel", "exposures": "gl_expgeo_kernel",
 
 
 def roofline(c: dict, kern: dict, fp32_peak: float, fp64_peak: float, hbm_peak: float,
-             time_bytes: int, workload: str = "") -> dict:
+             time_bytes: int, workload: str = "", peak_source: str = None) -> dict:
     """Roofline of the dominant kernel of the FP32C step (the one with the largest
     measured time), with every kernel's own figures beside it."""
-    per = {k: alu_roofline(*f, kern[k], fp32_peak, fp64_peak)
+    extra = {"peak_source": peak_source} if peak_source else {}
+    per = {k: alu_roofline(*f, kern[k], fp32_peak, fp64_peak, **extra)
            for k, f in kernel_flops(c).items() if kern.get(k)}
     if kern.get("window"):
         per["window"] = hbm_roofline(window_bytes(c, time_bytes), kern["window"], hbm_peak)
@@ -291,24 +310,69 @@ def run_oracle(wl, idx, nthreads=0):
         t_sub = np.concatenate([wl["t"][off[s]:off[s + 1]] for s in idx])
         evals = int(np.sum(lengths * np.asarray(ns_sub)))
     t0 = time.perf_counter()
-    oracle.lightcurve(p, t_sub, exptime, ns_sub, offsets=off_sub, nthreads=nthreads)
+    ref = oracle.lightcurve(p, t_sub, exptime, ns_sub, offsets=off_sub, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return evals, dt, oracle.max_threads()
+    return evals, dt, oracle.max_threads(), np.asarray(ref).reshape(-1)
 
 
-def cpu_baseline(wl, sample_sets: int, min_seconds: float = 10.0):
+def sample_outputs(wl, idx, out: np.ndarray) -> np.ndarray:
+    """The GPU outputs of the sampled parameter sets, in the oracle's layout."""
+    if wl.get("offsets") is None:
+        return out.reshape(len(wl["params"]["t0"]), len(wl["t"]))[idx].reshape(-1)
+    off = wl["offsets"]
+    return np.concatenate([out[off[s]:off[s + 1]] for s in idx])
+
+
+def cpu_baseline(wl, sample_sets: int, min_seconds: float = 10.0, gpu_out=None):
     """The oracle on a seeded sample of the workload's parameter sets (all their
-    exposures and sub-exposures), repeated until at least min_seconds of CPU work."""
+    exposures and sub-exposures), repeated until at least min_seconds of CPU work.
+    With gpu_out (the timed path's output), also the max |dflux| of that path
+    against the oracle over the sample."""
     idx = oracle_sample(wl, sample_sets)
     evals, dt, reps = 0, 0.0, 0
+    ref = None
     while dt < min_seconds or reps == 0:
-        e, t, cores = run_oracle(wl, idx)
+        e, t, cores, ref = run_oracle(wl, idx)
         evals += e
         dt += t
         reps += 1
-    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(idx)} of {len(wl['params']['t0'])} parameter sets, all their "
-                      f"exposures and sub-exposures, {reps} passes ({evals} evals, {dt:.1f} s)"}
+    res = {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(idx)} of {len(wl['params']['t0'])} parameter sets, all their "
+                     f"exposures and sub-exposures, {reps} passes ({evals} evals, {dt:.1f} s)"}
+    if gpu_out is not None:
+        got = sample_outputs(wl, idx, gpu_out)
+        res["max_dflux_vs_oracle"] = float(np.max(np.abs(got - ref)))
+        res["sample_exposures"] = int(ref.size)
+        res["sample_in_transit"] = int(np.sum(ref < 1.0))
+    return res
+
+
+def peaks_arm(args):
+    """Measured non-tensor pipe throughput of this GPU (libglpeaks probes), with
+    the SM clock sampled while they run: the denominators of the ALU rooflines."""
+    from paper_2410_05408_b300 import binding, build
+    build.build()
+    world, rank, local = dist_setup()
+    res = {}
+    with ClockSampler(local) as clk:
+        for name, kind in (("ffma", binding.GLP_FFMA), ("dfma", binding.GLP_DFMA),
+                           ("mufu_rsqrt", binding.GLP_MUFU)):
+            res[name] = binding.glp_measure(local, kind, repeats=max(3, args.steps))
+    clocks = clk.summary()
+    if rank != 0:
+        return
+    line = {"metric": "non-tensor pipe throughput", "unit": "TFLOP/s (FMA = 2 flops; MUFU: Top/s)",
+            "value": res["ffma"]["flops_per_s"] / 1e12, "n_gpus": 1, "steps": max(3, args.steps),
+            "warmup": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "peaks", "grid": "8 x 256-thread CTAs per SM",
+                       "chains": "FFMA 8, DFMA 4, MUFU 8 independent chains per thread"},
+            "fp32_tflops": res["ffma"]["flops_per_s"] / 1e12,
+            "fp64_tflops": res["dfma"]["flops_per_s"] / 1e12,
+            "mufu_tops": res["mufu_rsqrt"]["flops_per_s"] / 1e12,
+            "fp32_to_fp64": res["ffma"]["flops_per_s"] / res["dfma"]["flops_per_s"],
+            "best_ms": {k: v["best_ms"] for k, v in res.items()},
+            "clocks": clocks}
+    print(json.dumps(line))
 
 
 def reference_arm(args):
@@ -322,7 +386,7 @@ def reference_arm(args):
         run_oracle(wl, idx[:1])
     tot_evals, tot_t, cores = 0, 0.0, 1
     for _ in range(args.steps):
-        e, dt, cores = run_oracle(wl, idx)
+        e, dt, cores, _ = run_oracle(wl, idx)
         tot_evals += e
         tot_t += dt
     value = tot_evals / tot_t
@@ -734,6 +798,8 @@ def main():
         return locked_arm(args)
     if args.workload == "ensemble":
         return ensemble_arm(args)
+    if args.workload == "peaks":
+        return peaks_arm(args)
 
     import torch
     from paper_2410_05408_b300 import binding, build
@@ -787,17 +853,16 @@ def main():
     def timed(prec, out, k, profile):
         """k steps, L2 flushed before each, CUDA events on the launch stream around
         each step (the flush is outside them).  With profile=True the library also
-        times each kernel with events (graph replay is off then)."""
+        times each kernel with CUDA events recorded inside the replayed step graph
+        (event-record nodes at the kernel boundaries, on the same stream)."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(k)]
         l0 = ctx.launches()
-        ctx.profile(profile)
+        ctx.profile(binding.PROFILE_GRAPH if profile else False)
         if profile:
-            # a queue head start: with per-kernel events the host issues more work
-            # per step, and it must stay ahead of the GPU for the events to time
-            # the kernels rather than the launches
-            for _ in range(4):
-                flush.zero_()
+            step(out, prec)   # capture of the profiled graph, untimed
+            torch.cuda.synchronize(dev)
+            ctx.profile(binding.PROFILE_GRAPH)   # reset the accumulated times
         gc_was = gc.isenabled()
         gc.disable()   # no collector pause between a step's events
         try:
@@ -818,9 +883,12 @@ def main():
             for name, kind in (("window", binding.GL_KERNEL_WINDOW),
                                ("exposures", binding.GL_KERNEL_CURVE),
                                ("quadrature", binding.GL_KERNEL_QUAD),
-                               ("setup", binding.GL_KERNEL_SETUP)):
+                               ("quadrature_kernel", binding.GL_KERNEL_ITEMS),
+                               ("setup", binding.GL_KERNEL_SETUP),
+                               ("step", binding.GL_KERNEL_STEP)):
                 t_ms, n = ctx.profile_read(kind)
                 kern[name] = t_ms / n if n else None
+            kern["timed_steps"] = k
             ctx.profile(False)
         return ms, ctx.launches() - l0, kern
 
@@ -897,10 +965,18 @@ def main():
         h_exp.numel() * 8 + h_ns.numel() * 4 + (0 if h_off is None else h_off.numel() * 8)
     d2h = h_out.numel() * 8
 
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    with ClockSampler(local) as clk_probe:
+        fp32_peak, fp64_peak, mufu_peak, peak_src = measured_alu_peaks(
+            local, peaks.get("sm_max_mhz", 2032.0))
+    probe_clocks = clk_probe.summary()
     if rank != 0:
         return
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    fp32_peak, fp64_peak = alu_peaks(peaks.get("sm_max_mhz", 2032.0))
+    step_s = ms32 / args.steps * 1e-3
+    on_disk = counts["full"] + counts["partial"]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_sets, gpu_out=out32.cpu().numpy())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
@@ -912,6 +988,14 @@ def main():
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
                    "graphs": "step replayed as a CUDA graph"},
         "max_dflux_vs_fp64_gpu": max_dflux, "in_transit_exposures": in_transit,
+        "max_dflux_vs_oracle": None if cpu is None else cpu["max_dflux_vs_oracle"],
+        "in_transit_evals_per_s": world * on_disk / step_s,
+        "in_window_evals_per_s": world * counts["items"] / step_s,
+        "rates_note": "in_transit = sub-exposures whose planet overlaps the star (the "
+                      "quadrature's items); in_window = sub-exposures of exposures inside "
+                      "the exact transit window; value counts every evaluation",
+        "alu_peaks": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak,
+                      "mufu_tops": mufu_peak, "source": peak_src, "clocks": probe_clocks},
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / k64},
         "kernel_ms": {"fp32c": kern32, "fp64": kern64},
         "workload_counts": counts,
@@ -919,15 +1003,15 @@ def main():
         "autotune_fp64": tune64,
         "roofline": roofline(counts, kern32, fp32_peak, fp64_peak,
                              peaks.get("hbm_gbs"), 8 * len(t) if offsets is None
-                             else 8 * n_tot, args.workload),
+                             else 8 * n_tot, args.workload, peak_src),
         "gpu_launches": launches,
         "status": status,
         "clocks": clocks,
         "e2e": {"value": world * evals * k_e2e / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sets)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line))
     ctx.close()
 

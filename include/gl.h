@@ -317,12 +317,24 @@ int gl_configure(gl_context *ctx, gl_precision prec, int threads, int nodes, int
 #define GL_KERNEL_QUAD 4    /* item pipeline: quadrature of queued sub-exposures and the
                                exposure means (two kernels) */
 #define GL_KERNEL_WINDOW 6  /* item pipeline: the window test of every exposure */
-#define GL_KERNEL_KINDS 8
+#define GL_KERNEL_ITEMS 7   /* item pipeline: the quadrature kernel alone */
+#define GL_KERNEL_STEP 8    /* mode 2 only: the whole captured light-curve step */
+#define GL_KERNEL_KINDS 9
 
-/* Per-kernel device timing for benchmarks.  While enabled (on != 0), every
- * kernel launch of the context is bracketed by CUDA events recorded on its
- * launch stream (at most 65536 launches per kind are kept; later ones are not
- * timed).  Enabling resets the accumulated times.  GL_EINVAL on a NULL context. */
+/* Per-kernel device timing for benchmarks.
+ *   on = 1: every kernel launch of the context is bracketed by CUDA events
+ *           recorded on its launch stream; light-curve steps run eagerly (no
+ *           graph replay), so host launch gaps fall inside the timed spans.
+ *   on = 2: light-curve steps keep their CUDA-graph replay; the step graph is
+ *           captured with event-record nodes before the constants kernel and
+ *           after each kernel (cudaEventRecordExternal), and every replay points
+ *           them at a fresh set of events, so each kernel is timed inside the
+ *           replayed graph, on the caller's stream.  Read with kinds SETUP,
+ *           WINDOW, CURVE, ITEMS, QUAD (quadrature + exposure sums) and STEP.
+ *   on = 0: off.
+ * At most 65536 launches (replays) are kept; later ones are not timed.
+ * Enabling resets the accumulated times.  GL_EINVAL on a NULL context or another
+ * value of on. */
 int gl_profile_enable(gl_context *ctx, int on);
 
 /* Total device time in milliseconds and number of timed launches of kernel kind

@@ -52,6 +52,9 @@ GL_KERNEL_SPHERE = 3
 GL_KERNEL_QUAD = 4
 GL_KERNEL_SIMPSON = 5
 GL_KERNEL_WINDOW = 6
+GL_KERNEL_ITEMS = 7
+GL_KERNEL_STEP = 8
+PROFILE_OFF, PROFILE_EAGER, PROFILE_GRAPH = 0, 1, 2
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 
@@ -487,8 +490,11 @@ def gl_item_pipeline(ctx, on: bool = True, max_items: int = 0) -> None:
     _check(ctx, load().gl_item_pipeline(ctx, int(bool(on)), int(max_items)))
 
 
-def gl_profile_enable(ctx, on: bool = True) -> int:
-    return load().gl_profile_enable(ctx, int(bool(on)))
+def gl_profile_enable(ctx, on=True) -> int:
+    """on: False/0 off, True/1 eager per-kernel events, 2 event nodes inside the
+    replayed step graph (PROFILE_GRAPH)."""
+    mode = int(on) if not isinstance(on, bool) else int(on)
+    return load().gl_profile_enable(ctx, mode)
 
 
 def gl_profile_read(ctx, kind: int):
@@ -626,8 +632,41 @@ class Context:
     def item_pipeline(self, on: bool = True, max_items: int = 0):
         gl_item_pipeline(self.handle, on, max_items)
 
-    def profile(self, on: bool = True):
-        gl_profile_enable(self.handle, on)
+    def profile(self, on=True):
+        _check(self.handle, gl_profile_enable(self.handle, on))
 
     def profile_read(self, kind: int):
         return gl_profile_read(self.handle, kind)
+
+
+# ------------------------------------------------------------------ pipe throughput
+GLP_FFMA, GLP_DFMA, GLP_MUFU = 0, 1, 2
+_peaks_lib = None
+
+
+def _load_peaks():
+    global _peaks_lib
+    if _peaks_lib is None:
+        from . import build as _build
+        path = _build.PEAKS_LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2410_05408_b300.build.build()")
+        lib = ctypes.CDLL(path)
+        lib.glp_measure.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+        lib.glp_measure.restype = ctypes.c_int
+        _peaks_lib = lib
+    return _peaks_lib
+
+
+def glp_measure(device: int, kind: int, repeats: int = 5) -> dict:
+    """Measured throughput of one pipe (include/gl_peaks.h): flops/s (FMA = 2),
+    the best launch's milliseconds and operations per launch."""
+    f, ms, ops = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = _load_peaks().glp_measure(int(device), int(kind), int(repeats), ctypes.byref(f),
+                                   ctypes.byref(ms), ctypes.byref(ops))
+    if rc != 0:
+        raise GLError(rc, f"glp_measure(kind={kind}) failed")
+    return {"flops_per_s": f.value, "best_ms": ms.value, "ops": ops.value}

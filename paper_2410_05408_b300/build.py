@@ -15,6 +15,10 @@ LIB = os.path.join(HERE, "libgl.so")
 SOURCES = [os.path.join(HERE, "csrc", "gl_api.cu"), os.path.join(HERE, "csrc", "gl_mlp.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
                   if f.endswith((".cuh", ".h"))] + [os.path.join(ROOT, "include", "gl.h")]
+# the pipe-throughput probes of the roofline denominators (include/gl_peaks.h)
+PEAKS_LIB = os.path.join(HERE, "libglpeaks.so")
+PEAKS_SOURCES = [os.path.join(HERE, "csrc", "gl_peaks.cu")]
+PEAKS_DEPS = PEAKS_SOURCES + [os.path.join(ROOT, "include", "gl_peaks.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -25,24 +29,30 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB, deps=None) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in DEPS if os.path.exists(d))
+    t = os.path.getmtime(lib)
+    return all(os.path.getmtime(d) <= t for d in (deps or DEPS) if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+def _compile(lib: str, sources, verbose: bool) -> None:
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), *SOURCES, "-o", tmp]
+           "-I", os.path.join(ROOT, "include"), *sources, "-o", tmp]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Build libgl.so and libglpeaks.so if a source changed; returns libgl.so's path."""
+    if force or not up_to_date(PEAKS_LIB, PEAKS_DEPS):
+        _compile(PEAKS_LIB, PEAKS_SOURCES, verbose)
+    if force or not up_to_date():
+        _compile(LIB, SOURCES, verbose)
     return LIB
 
 

@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <array>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -30,6 +31,10 @@ namespace {
 
 // status bits accumulated on the device
 enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4, kStatusOverflow = 8 };
+// Boundaries of a light-curve step at which profiling mode 2 records events
+// inside the step graph: before the constants, then after each kernel.
+enum : int { kMarkStart = 0, kMarkSetup, kMarkWindow, kMarkExposures, kMarkItems, kMarkSums,
+             kMarks };
 
 // quadrature orders: FP64 path and FP32C path
 constexpr int kNodes64 = 32;
@@ -1747,6 +1752,8 @@ struct gl_context {
     unsigned char key[256];
     size_t key_len;
     cudaGraphExec_t exec;
+    cudaGraph_t graph;                 // kept only for profiled steps (their mark nodes)
+    cudaGraphNode_t marks[kMarks];     // event-record nodes at the kernel boundaries
     uint64_t last_use;
     int64_t kernels;   // kernel launches in the captured step
   };
@@ -1755,9 +1762,14 @@ struct gl_context {
   int64_t graph_launches = 0;
   int64_t launches = 0;
   // per-kernel event timing (gl_profile_enable)
-  bool profiling = false;
+  bool profiling = false;      // mode 1: eager launches bracketed by events
+  bool gprof = false;          // mode 2: event-record nodes inside the step graph
+  bool capturing = false;      // a step is being captured
   std::vector<cudaEvent_t> ev[GL_KERNEL_KINDS];   // pairs: start, stop
   size_t ev_used[GL_KERNEL_KINDS] = {0};
+  cudaEvent_t gmark_cap[kMarks] = {};              // recorded at capture (names the nodes)
+  std::vector<std::array<cudaEvent_t, kMarks>> gpool;   // one set per profiled replay
+  size_t gpool_used = 0;
 };
 
 namespace {
@@ -1794,8 +1806,13 @@ bool is_device_ptr(const void* p, int device) {
   return false;
 }
 
+void drop_graph(gl_context::GraphEntry& g) {
+  cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+}
+
 void drop_graphs(gl_context* ctx) {
-  for (auto& g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+  for (auto& g : ctx->graph_cache) drop_graph(g);
   ctx->graph_cache.clear();
 }
 
@@ -1888,6 +1905,13 @@ void prof_end(gl_context* ctx, int kind, long i, cudaStream_t st) {
   if (i >= 0) cudaEventRecord(ctx->ev[kind][2 * i + 1], st);
 }
 
+// Mode 2: while a step is captured for profiling, record boundary mark k as an
+// event-record node of the graph (each replay then points it at its own event).
+void gmark(gl_context* ctx, int k, cudaStream_t st) {
+  if (ctx->gprof && ctx->capturing && ctx->gmark_cap[k])
+    cudaEventRecordWithFlags(ctx->gmark_cap[k], st, cudaEventRecordExternal);
+}
+
 int launch_grid(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   const int64_t cap = 148LL * 32;
@@ -1951,21 +1975,27 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   long pe = prof_begin(ctx, GL_KERNEL_WINDOW, st);
   gl_win_kernel<kWinU><<<(int)wb, 256, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_WINDOW, pe, st);
+  gmark(ctx, kMarkWindow, st);
   pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
   if (gvar)
     gl_expgeo_kernel<R, 64><<<ctx->sms * eocc, 64, 0, st>>>(args);
   else
     gl_expgeo_kernel<R, 256><<<ctx->sms * eocc, 256, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_CURVE, pe, st);
+  gmark(ctx, kMarkExposures, st);
   ctx->launches += 2;
   GL_CUDA(ctx, cudaGetLastError());
   pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
+  long pq = prof_begin(ctx, GL_KERNEL_ITEMS, st);
   if (qvar)
     gl_items_quad_kernel<R, 128, 8><<<ctx->sms * qocc, 128, 0, st>>>(args);
   else
     gl_items_quad_kernel<R, 128, 4><<<ctx->sms * qocc, 128, 0, st>>>(args);
+  prof_end(ctx, GL_KERNEL_ITEMS, pq, st);
+  gmark(ctx, kMarkItems, st);
   gl_items_sum_kernel<R><<<ctx->sms * 2, 256, 0, st>>>(args);
   prof_end(ctx, GL_KERNEL_QUAD, pe, st);
+  gmark(ctx, kMarkSums, st);
   ctx->launches += 2;
   GL_CUDA(ctx, cudaGetLastError());
   return GL_OK;
@@ -2036,9 +2066,11 @@ struct StepArgs {
   void* items;        // item workspace, or null: every tile integrates locally
   int64_t item_cap;
   int locked;         // tidally locked bodies: gl_locked_kernel
+  int gprof;          // captured with boundary marks (profiling mode 2)
 };
 
 int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
+  gmark(ctx, kMarkStart, st);
   long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
   // the item pipeline's counters are zeroed here (one graph node less than a
   // separate memset)
@@ -2047,6 +2079,7 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
       sa.pp, sa.n_sets, sa.offsets, sa.n_total, sa.sets, ctx->d_status,
       pipeline ? ctx->d_ictr : nullptr, pipeline ? (int)kIcWords : 0);
   prof_end(ctx, GL_KERNEL_SETUP, pe, st);
+  gmark(ctx, kMarkSetup, st);
   ctx->launches++;
   GL_CUDA(ctx, cudaGetLastError());
   LcArgs la;
@@ -2096,9 +2129,14 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     // the occupancy query and attribute setting must not happen inside a capture
     if (!sa.locked && !lc_ready(ctx, sa.prec, sa.items != nullptr))
       return enqueue_step(ctx, sa, st);   // first call: eager
+    if (sa.gprof)
+      for (int k = 0; k < kMarks; ++k)
+        if (!ctx->gmark_cap[k]) GL_CUDA(ctx, cudaEventCreate(&ctx->gmark_cap[k]));
     GL_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int64_t l0 = ctx->launches;
+    ctx->capturing = true;
     int rc = enqueue_step(ctx, sa, ctx->cap_stream);
+    ctx->capturing = false;
     const int64_t kernels = ctx->launches - l0;
     ctx->launches = l0;
     cudaGraph_t graph = nullptr;
@@ -2108,18 +2146,40 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
       return rc;
     }
     if (e != cudaSuccess) return fail(ctx, GL_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    gl_context::GraphEntry ge;
+    memset(&ge, 0, sizeof ge);
+    if (sa.gprof) {
+      // find the boundary marks among the graph's nodes by the event each records
+      size_t nn = 0;
+      cudaGraphGetNodes(graph, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord)
+          continue;
+        cudaEvent_t ev = nullptr;
+        if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
+        for (int k = 0; k < kMarks; ++k)
+          if (ev == ctx->gmark_cap[k]) ge.marks[k] = nodes[i];
+      }
+      cudaGetLastError();
+    }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(ctx, GL_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    if (sa.gprof) ge.graph = graph;
+    else cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      if (ge.graph) cudaGraphDestroy(ge.graph);
+      return fail(ctx, GL_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
     if (ctx->graph_cache.size() >= 16) {
       size_t lru = 0;
       for (size_t i = 1; i < ctx->graph_cache.size(); ++i)
         if (ctx->graph_cache[i].last_use < ctx->graph_cache[lru].last_use) lru = i;
-      cudaGraphExecDestroy(ctx->graph_cache[lru].exec);
+      drop_graph(ctx->graph_cache[lru]);
       ctx->graph_cache.erase(ctx->graph_cache.begin() + lru);
     }
-    gl_context::GraphEntry ge;
     memcpy(ge.key, key, sizeof key);
     ge.key_len = sizeof key;
     ge.exec = exec;
@@ -2129,6 +2189,19 @@ int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
     hit = &ctx->graph_cache.back();
   }
   hit->last_use = ++ctx->graph_clock;
+  if (sa.gprof && ctx->gpool_used < kMaxTimed) {
+    // this replay's marks record into a fresh set of events
+    if (ctx->gpool.size() <= ctx->gpool_used) {
+      std::array<cudaEvent_t, kMarks> evs{};
+      for (int k = 0; k < kMarks; ++k) GL_CUDA(ctx, cudaEventCreate(&evs[k]));
+      ctx->gpool.push_back(evs);
+    }
+    const auto& evs = ctx->gpool[ctx->gpool_used];
+    for (int k = 0; k < kMarks; ++k)
+      if (hit->marks[k])
+        GL_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(hit->exec, hit->marks[k], evs[k]));
+    ctx->gpool_used++;
+  }
   GL_CUDA(ctx, cudaGraphLaunch(hit->exec, st));
   ctx->launches += hit->kernels;
   ctx->graph_launches++;
@@ -2407,9 +2480,11 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
 }
 
 int gl_profile_enable(gl_context* ctx, int on) {
-  if (!ctx) return GL_EINVAL;
-  ctx->profiling = on != 0;
+  if (!ctx || on < 0 || on > 2) return GL_EINVAL;
+  ctx->profiling = on == 1;
+  ctx->gprof = on == 2;
   for (int k = 0; k < GL_KERNEL_KINDS; ++k) ctx->ev_used[k] = 0;
+  ctx->gpool_used = 0;
   return GL_OK;
 }
 
@@ -2417,6 +2492,31 @@ int gl_profile_read(gl_context* ctx, int kind, double* ms, int64_t* launches) {
   if (!ctx || !ms || !launches || kind < 0 || kind >= GL_KERNEL_KINDS) return GL_EINVAL;
   GL_CUDA(ctx, cudaSetDevice(ctx->device));
   double tot = 0.0;
+  if (ctx->gprof) {
+    // graph replays: the span between the kind's two boundary marks
+    int a = -1, b = -1;
+    switch (kind) {
+      case GL_KERNEL_SETUP: a = kMarkStart; b = kMarkSetup; break;
+      case GL_KERNEL_WINDOW: a = kMarkSetup; b = kMarkWindow; break;
+      case GL_KERNEL_CURVE: a = kMarkWindow; b = kMarkExposures; break;
+      case GL_KERNEL_QUAD: a = kMarkExposures; b = kMarkSums; break;
+      case GL_KERNEL_ITEMS: a = kMarkExposures; b = kMarkItems; break;
+      case GL_KERNEL_STEP: a = kMarkStart; b = kMarkSums; break;
+      default: break;
+    }
+    int64_t n = 0;
+    if (a >= 0)
+      for (size_t i = 0; i < ctx->gpool_used; ++i) {
+        GL_CUDA(ctx, cudaEventSynchronize(ctx->gpool[i][b]));
+        float m = 0.f;
+        GL_CUDA(ctx, cudaEventElapsedTime(&m, ctx->gpool[i][a], ctx->gpool[i][b]));
+        tot += m;
+        ++n;
+      }
+    *ms = tot;
+    *launches = n;
+    return GL_OK;
+  }
   for (size_t i = 0; i < ctx->ev_used[kind]; ++i) {
     GL_CUDA(ctx, cudaEventSynchronize(ctx->ev[kind][2 * i + 1]));
     float m = 0.f;
@@ -2562,6 +2662,7 @@ int lightcurve_impl(gl_context* ctx, const gl_params* p, const gl_times* tm, dou
   sa.sets = ctx->d_sets;
   // host buffers are staged at fixed device addresses, so their steps replay a
   // graph too (the copies are ordered around it on the stream)
+  sa.gprof = ctx->gprof ? 1 : 0;
   bool use_graph = ctx->graphs && !ctx->profiling && !ctx->counting;
   if (use_graph) {
     rc = launch_step_graph(ctx, sa, st);

@@ -13,25 +13,39 @@ from paper_2410_05408_b300 import binding, build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
+def _declared_functions(header=None, prefix="gl_"):
     names = []
     for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
+        if fn.endswith(".h") and (header is None or fn == header):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(gl_[a-z0-9_]+)\s*\(",
-                                src, flags=re.M)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(" + prefix +
+                                r"[a-z0-9_]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
 def test_library_builds_and_exports_every_declared_symbol():
     build.build()
     lib = ctypes.CDLL(binding.LIB_PATH)
-    declared = _declared_functions()
+    declared = _declared_functions("gl.h")
     assert "gl_lightcurve_batch" in declared and "gl_context_create" in declared
     for name in declared:
         assert hasattr(lib, name), name
     assert set(binding.EXPORTED) == set(declared)
+
+
+def test_peaks_library_exports_its_header():
+    build.build()
+    lib = ctypes.CDLL(build.PEAKS_LIB)
+    declared = _declared_functions("gl_peaks.h", prefix="glp_")
+    assert declared == ["glp_measure"]
+    for name in declared:
+        assert hasattr(lib, name), name
+    # bad arguments are refused before any CUDA call
+    d = ctypes.c_double()
+    assert lib.glp_measure(0, 7, 3, ctypes.byref(d), ctypes.byref(d), ctypes.byref(d)) == -1
+    assert lib.glp_measure(0, 0, 0, ctypes.byref(d), ctypes.byref(d), ctypes.byref(d)) == -1
+    assert lib.glp_measure(0, 0, 3, None, None, None) == -1
 
 
 def test_q_to_u_host_entry_point():

@@ -193,3 +193,37 @@ def test_non_finite_times_give_flux_one(ctx, prec):
         keep = np.setdiff1d(np.arange(got.size), bad)
         assert np.array_equal(got[keep], ref.reshape(-1)[keep])
     ctx.item_pipeline(True)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_graph_profiling_times_kernels_inside_the_replay(ctx, prec):
+    """Profiling mode 2 keeps the graph replay and times every kernel of the step
+    with event-record nodes inside the graph: each profiled replay yields one span
+    per kernel, the spans add up to the step's span, and the light curve is bit
+    for bit the unprofiled one."""
+    d = _prepare(inputs.mcmc_batch(n_sets=32, n_times=600, seed=3))
+    ref = _run(ctx, d, prec)
+    out = torch.empty(d["n_total"], dtype=torch.float64, device="cuda")
+    call = lambda: ctx.lightcurve(d["p"], d["t"], out, d["exptime"], nsuper=d["ns"],  # noqa: E731
+                                  offsets=d["offsets"], precision=prec)
+    ctx.profile(binding.PROFILE_GRAPH)
+    call()                               # capture of the profiled graph
+    torch.cuda.synchronize()
+    ctx.profile(binding.PROFILE_GRAPH)   # reset
+    g0 = ctx.graph_launches()
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    assert ctx.graph_launches() - g0 == 5
+    kinds = {"setup": binding.GL_KERNEL_SETUP, "window": binding.GL_KERNEL_WINDOW,
+             "exposures": binding.GL_KERNEL_CURVE, "quad_sum": binding.GL_KERNEL_QUAD,
+             "quad": binding.GL_KERNEL_ITEMS, "step": binding.GL_KERNEL_STEP}
+    got = {k: ctx.profile_read(v) for k, v in kinds.items()}
+    ctx.profile(False)
+    assert all(n == 5 for _, n in got.values()), got
+    assert all(ms > 0.0 for ms, _ in got.values()), got
+    parts = sum(got[k][0] for k in ("setup", "window", "exposures", "quad_sum"))
+    assert abs(parts - got["step"][0]) <= 1e-3 * 5 + 1e-3 * got["step"][0], got
+    assert got["quad"][0] <= got["quad_sum"][0] + 1e-3
+    assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref)
+    assert ctx.sync() == binding.GL_OK

@@ -317,7 +317,9 @@ def test_large_flattened_planets_parity(ctx, large_flat, prec):
 
 
 # ---------------------------------------------------------------- spherical planet
-SPHERE_TOL = {binding.GL_FP64: 1e-10, binding.GL_FP32C: 2e-7}
+# the FP32C spherical base meets the same 1e-7 as the oblate path (worst case on
+# this sample, large planets p ~ 0.4 near the limb: 6.3e-8)
+SPHERE_TOL = {binding.GL_FP64: 1e-10, binding.GL_FP32C: 1e-7}
 
 
 @pytest.fixture(scope="module")
