@@ -438,7 +438,7 @@ __device__ double exposure_local(const SetConst& c, int flag, const gl::MidState
     R x, y, o;
     const int cls = item_geometry<R>(c, flag, mid, tau, 2 * q + 1 - ns, &x, &y, &o);
     const R d = cls == gl::kOut ? R(0) : item_deficit<R>(c, x, y, o, cls, base);
-    acc += (double)d;
+    acc += gl::to_f64(d);
   }
   return exposure_mean(acc, ns);
 }
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(NT) gl_lc_kernel(LcArgs a) {
       for (int i = tid; i < m; i += NT) {
         int b0 = max(e_base[i], r0), b1 = min(e_base[i + 1], r0 + nr);
         double acc = e_acc[i];
-        for (int it = b0; it < b1; ++it) acc += (double)it_def[it - r0];
+        for (int it = b0; it < b1; ++it) acc += gl::to_f64(it_def[it - r0]);
         e_acc[i] = acc;
       }
       __syncthreads();
@@ -942,7 +942,9 @@ __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
 }
 
 // Item pipeline, stage 4: the FP64 mean of each exposure with items on the disk,
-// summed in sub-exposure order.
+// summed in sub-exposure order (the deficits loaded eight at a time ahead of the
+// adds, and widened to FP64 by integer operations: on B300 a conversion
+// instruction holds the FP64 unit like an FP64 add).
 // Exposures that did not fit the workspace are finished here, each by one
 // thread (exact window, midpoint state, every sub-exposure in order).
 template <typename R>
@@ -955,9 +957,16 @@ __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
        r += (long long)gridDim.x * blockDim.x) {
     if (r < nrec) {
       const int ns = a.rns[r];
-      const long long f = a.rfirst[r];
+      const R* d = idef + a.rfirst[r];
       double acc = 0.0;
-      for (int q = 0; q < ns; ++q) acc += (double)idef[f + q];
+      for (int q0 = 0; q0 < ns; q0 += 8) {
+        R v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = q0 + k < ns ? d[q0 + k] : R(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (q0 + k < ns) acc += gl::to_f64(v[k]);
+      }
       a.out[a.rj[r]] = exposure_mean(acc, ns);
     } else {
       const int k = a.ovlist[r - nrec];

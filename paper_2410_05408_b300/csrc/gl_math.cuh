@@ -993,28 +993,47 @@ GL_HD void nearest_limb_angle(const Geo<R>& g, const Trig2<R>& t, R* cs, R* ss) 
 }
 
 // ------------------------------------------------------------------ quartics
+// Division and cosine for the quartic solver.  FAST (FP32 on the GPU only): the
+// hardware's approximate divide and cosine, for estimates that an FP64 Newton
+// polish refines afterwards (crossing_roots); otherwise the correctly rounded
+// divide and the library cosine.
+template <typename T, bool FAST>
+GL_HD T q_div(T a, T b) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (FAST && sizeof(T) == 4) return __fdividef(a, b);
+#endif
+  return a / b;
+}
+template <typename T, bool FAST>
+GL_HD T q_cos(T x) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (FAST && sizeof(T) == 4) return __cosf(x);
+#endif
+  return m_cos(x);
+}
+
 // Largest real root of z^3 + a z^2 + b z + c, refined by Newton.
-template <typename T>
+template <typename T, bool FAST = false>
 GL_HD T cubic_largest_root(T a, T b, T c) {
-  T Q = (a * a - T(3) * b) / T(9);
-  T Rr = (T(2) * a * a * a - T(9) * a * b + T(27) * c) / T(54);
+  T Q = (a * a - T(3) * b) * T(1.0 / 9.0);
+  T Rr = (T(2) * a * a * a - T(9) * a * b + T(27) * c) * T(1.0 / 54.0);
   T z;
   if (Q > T(0) && Rr * Rr < Q * Q * Q) {
-    T arg = Rr / m_sqrt(Q * Q * Q);
+    T arg = q_div<T, FAST>(Rr, m_sqrt(Q * Q * Q));
     arg = arg < T(-1) ? T(-1) : (arg > T(1) ? T(1) : arg);
     T th = m_acos(arg);
-    z = -T(2) * m_sqrt(Q) * m_cos((th + T(2 * kPi)) / T(3)) - a / T(3);
+    z = -T(2) * m_sqrt(Q) * q_cos<T, FAST>((th + T(2 * kPi)) * T(1.0 / 3.0)) - a * T(1.0 / 3.0);
   } else {
     T disc = Rr * Rr - Q * Q * Q;
     T A = -m_copysign(m_cbrt(m_abs(Rr) + m_sqrt(disc > T(0) ? disc : T(0))), Rr);
-    T B = (A != T(0)) ? Q / A : T(0);
-    z = A + B - a / T(3);
+    T B = (A != T(0)) ? q_div<T, FAST>(Q, A) : T(0);
+    z = A + B - a * T(1.0 / 3.0);
   }
   for (int it = 0; it < 3; ++it) {
     T f = ((z + a) * z + b) * z + c;
     T fp = (T(3) * z + T(2) * a) * z + b;
     if (fp == T(0)) break;
-    T step = f / fp;
+    T step = q_div<T, FAST>(f, fp);
     z -= step;
     if (m_abs(step) <= m_eps<T>() * m_abs(z)) break;
   }
@@ -1022,20 +1041,20 @@ GL_HD T cubic_largest_root(T a, T b, T c) {
 }
 
 // Real roots of the monic quadratic y^2 + p y + q; returns how many (0 or 2).
-template <typename T>
+template <typename T, bool FAST = false>
 GL_HD int quad_roots(T p, T q, T* r) {
   T disc = p * p - T(4) * q;
   if (disc < T(0)) return 0;
   T s = m_sqrt(disc);
   T y1 = -T(0.5) * (p + m_copysign(s, p));
   r[0] = y1;
-  r[1] = (y1 != T(0)) ? q / y1 : T(0);
+  r[1] = (y1 != T(0)) ? q_div<T, FAST>(q, y1) : T(0);
   return 2;
 }
 
 // Real roots of x^4 + a x^3 + b x^2 + c x + d by Ferrari's resolvent, each
 // polished by Newton on the quartic.  Returns the count (0..4).
-template <typename T>
+template <typename T, bool FAST = false>
 GL_HD int quartic_real_roots(T a, T b, T c, T d, T* x) {
   T a2 = a * a;
   T p = b - T(0.375) * a2;
@@ -1044,16 +1063,17 @@ GL_HD int quartic_real_roots(T a, T b, T c, T d, T* x) {
   T y[4];
   int n = 0;
   // resolvent: z^3 + 2p z^2 + (p^2 - 4r) z - q^2 = 0, z = s^2 >= 0
-  T z = cubic_largest_root<T>(T(2) * p, p * p - T(4) * r, -q * q);
+  T z = cubic_largest_root<T, FAST>(T(2) * p, p * p - T(4) * r, -q * q);
   if (z > T(64) * m_eps<T>() * (m_abs(p) + m_sqrt(m_abs(r)) + T(1e-30))) {
     T s = m_sqrt(z);
-    T al = T(0.5) * (p + z - q / s), be = T(0.5) * (p + z + q / s);
-    n += quad_roots<T>(s, al, y + n);
-    n += quad_roots<T>(-s, be, y + n);
+    const T qs = q_div<T, FAST>(q, s);
+    T al = T(0.5) * (p + z - qs), be = T(0.5) * (p + z + qs);
+    n += quad_roots<T, FAST>(s, al, y + n);
+    n += quad_roots<T, FAST>(-s, be, y + n);
   } else {
     // biquadratic: y^2 = w, w^2 + p w + r = 0
     T w[2];
-    int nw = quad_roots<T>(p, r, w);
+    int nw = quad_roots<T, FAST>(p, r, w);
     for (int i = 0; i < nw; ++i) {
       if (w[i] >= T(0)) {
         T sw = m_sqrt(w[i]);
@@ -1068,7 +1088,7 @@ GL_HD int quartic_real_roots(T a, T b, T c, T d, T* x) {
       T f = (((t + a) * t + b) * t + c) * t + d;
       T fp = ((T(4) * t + T(3) * a) * t + T(2) * b) * t + c;
       if (fp == T(0)) break;
-      T step = f / fp;
+      T step = q_div<T, FAST>(f, fp);
       t -= step;
       if (m_abs(step) <= m_eps<T>() * (T(1) + m_abs(t))) break;
     }
@@ -1212,8 +1232,9 @@ GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, 
   if (!(fabsf(fr.q[4]) > 0.0f)) return frame_roots<double>(f, tr);
   float inv = 1.0f / fr.q[4];
   float xs[4];
-  int nr = quartic_real_roots<float>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv, fr.q[0] * inv,
-                                     xs);
+  // estimates only: every root is polished below in FP64 (fast divide and cosine)
+  int nr = quartic_real_roots<float, true>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv,
+                                           fr.q[0] * inv, xs);
   bool ok = (nr % 2) == 0;
   for (int i = 0; i < nr && ok; ++i) {
     // Newton steps on the FP64 quartic with the derivative frozen at the FP32
@@ -1324,7 +1345,9 @@ GL_HD int inner_maxima(const Trig2<T>& t, T* cm, T* sm) {
 
 // Closed-form antiderivative of f_quad along the ellipse boundary (a trig
 // polynomial of degree 4 plus a linear term; derived from Sec. 2's f_quad with
-// x = x0 + a cos th, y = y0 + b1 cos th + b2 sin th).
+// x = x0 + a cos th, y = y0 + b1 cos th + b2 sin th).  Divisions by constants
+// are written as products with their reciprocals (a divide is a long
+// instruction sequence; the product differs by at most one rounding).
 template <typename R>
 struct QuadPoly {
   R K, S[4], C[4];
@@ -1335,21 +1358,21 @@ GL_HD QuadPoly<R> quad_poly(R x0, R y0, R a, R b1, R b2) {
   R a2 = a * a, b12 = b1 * b1, b22 = b2 * b2, x02 = x0 * x0, y02 = y0 * y0;
   q.K = a * b2 * (a2 + b12 + b22 + R(4) * x02 + R(4) * y02) / R(8);
   q.S[0] = R(5) * a2 * b2 * x0 / R(8) + R(3) * a * b1 * b2 * y0 / R(4) + b12 * b2 * x0 / R(8) +
-           b22 * b2 * x0 / R(8) + b2 * x02 * x0 / R(6) + b2 * x0 * y02 / R(2);
+           b22 * b2 * x0 / R(8) + b2 * x02 * x0 * R(1.0 / 6.0) + b2 * x0 * y02 / R(2);
   q.C[0] = -a2 * a * y0 / R(8) - a2 * b1 * x0 / R(8) + a * b12 * y0 / R(8) -
-           R(5) * a * b22 * y0 / R(8) - a * x02 * y0 / R(2) - a * y02 * y0 / R(6) +
-           b12 * b1 * x0 / R(8) + b1 * b22 * x0 / R(8) + b1 * x02 * x0 / R(6) +
+           R(5) * a * b22 * y0 / R(8) - a * x02 * y0 / R(2) - a * y02 * y0 * R(1.0 / 6.0) +
+           b12 * b1 * x0 / R(8) + b1 * b22 * x0 / R(8) + b1 * x02 * x0 * R(1.0 / 6.0) +
            b1 * x0 * y02 / R(2);
-  q.C[1] = -a2 * a * b1 / R(24) - a2 * x0 * y0 / R(4) + a * b12 * b1 / R(24) -
+  q.C[1] = -a2 * a * b1 * R(1.0 / 24.0) - a2 * x0 * y0 / R(4) + a * b12 * b1 * R(1.0 / 24.0) -
            a * b1 * b22 / R(8) + b12 * x0 * y0 / R(4) - b22 * x0 * y0 / R(4);
-  q.S[1] = a2 * a * b2 / R(24) + a * b12 * b2 / R(8) - a * b22 * b2 / R(24) +
+  q.S[1] = a2 * a * b2 * R(1.0 / 24.0) + a * b12 * b2 / R(8) - a * b22 * b2 * R(1.0 / 24.0) +
            b1 * b2 * x0 * y0 / R(2);
-  q.C[2] = -a2 * a * y0 / R(24) - a2 * b1 * x0 / R(24) + a * b12 * y0 / R(24) -
-           a * b22 * y0 / R(24) + b12 * b1 * x0 / R(24) - b1 * b22 * x0 / R(8);
-  q.S[2] = -a2 * b2 * x0 / R(24) + a * b1 * b2 * y0 / R(12) + b12 * b2 * x0 / R(8) -
-           b22 * b2 * x0 / R(24);
-  q.C[3] = -a2 * a * b1 / R(96) + a * b12 * b1 / R(96) - a * b1 * b22 / R(32);
-  q.S[3] = -a2 * a * b2 / R(96) + a * b12 * b2 / R(32) - a * b22 * b2 / R(96);
+  q.C[2] = -a2 * a * y0 * R(1.0 / 24.0) - a2 * b1 * x0 * R(1.0 / 24.0) + a * b12 * y0 * R(1.0 / 24.0) -
+           a * b22 * y0 * R(1.0 / 24.0) + b12 * b1 * x0 * R(1.0 / 24.0) - b1 * b22 * x0 / R(8);
+  q.S[2] = -a2 * b2 * x0 * R(1.0 / 24.0) + a * b1 * b2 * y0 * R(1.0 / 12.0) + b12 * b2 * x0 / R(8) -
+           b22 * b2 * x0 * R(1.0 / 24.0);
+  q.C[3] = -a2 * a * b1 * R(1.0 / 96.0) + a * b12 * b1 * R(1.0 / 96.0) - a * b1 * b22 / R(32);
+  q.S[3] = -a2 * a * b2 * R(1.0 / 96.0) + a * b12 * b2 / R(32) - a * b22 * b2 * R(1.0 / 96.0);
   return q;
 }
 
@@ -1420,6 +1443,22 @@ GL_HD void split_turn(R c0, R s0, R c1, R s1, R* acm, R* asn, R* ah) {
   ah[1] = R(kPi) - h;
 }
 
+// The centre of a single-centre whole-turn rule: the point of the boundary nearest
+// the limb (the global maximum of g).  When the quartic of g' found fewer than
+// two inner maxima, its one maximum (if any) is compared with Newton's from the
+// outward normal along the centre direction and the one with the larger g is
+// kept: the FP32 quartic can miss or misplace a shallow second maximum, and a
+// turn clustered on a lesser maximum resolves the near-limb part poorly.
+template <typename R>
+GL_HD void nearest_limb_center(const Geo<R>& g, const Trig2<R>& tg, int nmax, R* cmx, R* smx) {
+  R cn, sn;
+  nearest_limb_angle<R>(g, tg, &cn, &sn);
+  if (nmax == 0 || trig2_eval<R>(tg, cn, sn) > trig2_eval<R>(tg, cmx[0], smx[0])) {
+    cmx[0] = cn;
+    smx[0] = sn;
+  }
+}
+
 // The arcs (mid-direction cos/sin, half-width) into which the whole turn of a
 // boundary lying inside the disk is split for the f_lin quadrature: at the two
 // inner maxima when there are two, otherwise one arc whose two ends meet at the
@@ -1432,15 +1471,10 @@ GL_HD void whole_arcs(const Geo<R>& g, const Trig2<R>& tg, int nmax, const R* cm
     *na = 2;
     return;
   }
-  R cs, ss;
-  if (nmax >= 1) {
-    cs = cmx[0];
-    ss = smx[0];
-  } else {
-    nearest_limb_angle<R>(g, tg, &cs, &ss);
-  }
-  acm[0] = -cs;
-  asn[0] = -ss;
+  R cs[1] = {nmax >= 1 ? cmx[0] : R(0)}, ss[1] = {nmax >= 1 ? smx[0] : R(0)};
+  nearest_limb_center<R>(g, tg, nmax, cs, ss);
+  acm[0] = -cs[0];
+  asn[0] = -ss[0];
   ah[0] = R(kPi);
   *na = 1;
 }
@@ -1599,8 +1633,8 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
           R s4a = R(4) * px[i] * py[i] * (px[i] * px[i] - py[i] * py[i]);
           R s4b = R(4) * px[ip] * py[ip] * (px[ip] * px[ip] - py[ip] * py[ip]);
           sflat.add(R(0.5) * dl);
-          slin.add(dl / R(3));
-          squad.add(R(0.25) * dl - (s4b - s4a) / R(48));
+          slin.add(dl * R(1.0 / 3.0));
+          squad.add(R(0.25) * dl - (s4b - s4a) * R(1.0 / 48.0));
         }
       }
     }
@@ -1614,14 +1648,9 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
   I[0] = area;
   I[2] = area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4));
   if (nmax <= 1) {
-    R cs, ss;
-    if (nmax == 1) {
-      cs = cmx[0];
-      ss = smx[0];
-    } else {
-      nearest_limb_angle<R>(g, tg, &cs, &ss);
-    }
-    I[1] = lin_full<R>(g, cs, ss, rule);
+    // (a single maximum from Newton's method is already the nearest point)
+    if (!(cls == kFull && one_max)) nearest_limb_center<R>(g, tg, nmax, cmx, smx);
+    I[1] = lin_full<R>(g, cmx[0], smx[0], rule);
   } else {
     R acm[2], asn[2], ah[2];
     split_turn<R>(cmx[0], smx[0], cmx[1], smx[1], acm, asn, ah);
