@@ -432,13 +432,20 @@ def stretch_move(logp, walkers: np.ndarray, rng, a: float = 2.0):
     return walkers, acc / n
 
 
+def flux_error_quantiles(err, data, qs=(0.5, 0.99, 0.999, 1.0)) -> dict:
+    """Quantiles of the held-out |error| in flux units (normalised error x R_eq^2)
+    over the samples that overlap the star (reporting only)."""
+    e = (err * data["scale"])[data["bins"] >= 0].double().cpu().numpy()
+    return {str(q): float(np.quantile(e, q)) for q in qs}
+
+
 def surrogate_train_arm(args):
     import torch
     from paper_2410_05408_b300 import binding, build, surrogate
     build.build()
     ctx = binding.Context(0)
     mlp = binding.Mlp(0)
-    mlp.set_params(surrogate.init_params(seed=0))
+    mlp.init(0)
     t0 = time.perf_counter()
     train = surrogate.make_dataset(ctx, args.sur_train, seed=3)
     held = surrogate.make_dataset(ctx, args.sur_held, seed=1003)
@@ -454,11 +461,14 @@ def surrogate_train_arm(args):
     torch.cuda.synchronize()
     train_s = ev0.elapsed_time(ev1) * 1e-3
     samples = args.sur_epochs * n
-    table = surrogate.error_table(mlp, held)
-    q = surrogate.flux_error_quantiles(mlp, held)
+    err = torch.empty_like(held["t"])
+    table = surrogate.error_table(mlp, held, err)
+    q = flux_error_quantiles(err, held)
     if args.sur_save:
-        surrogate.save(args.sur_save, mlp, table, dict(train=n, epochs=args.sur_epochs,
-                                                        batch=batch, history=hist))
+        cfg = surrogate.config(n, args.sur_epochs, batch, args.sur_lr)
+        surrogate.save(args.sur_save, mlp, table, cfg,
+                       args.sur_epochs * surrogate.steps_per_epoch(n, cfg),
+                       dict(train=n, epochs=args.sur_epochs, batch=batch, history=hist))
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     tc = samples * MLP_TC_TRAIN_FLOPS / train_s / 1e12
     line = {"metric": "surrogate training samples/sec (forward + backward + Adam)",
@@ -486,9 +496,9 @@ def surrogate_mcmc_arm(args):
     ctx = binding.Context(0)
     mlp = binding.Mlp(0)
     if args.sur_load:
-        table, _ = surrogate.load(args.sur_load, mlp)
+        table, _, _ = surrogate.load(args.sur_load, mlp)
     else:   # no saved surrogate: train one here (untimed), as the training arm does
-        mlp.set_params(surrogate.init_params(seed=0))
+        mlp.init(0)
         train = surrogate.make_dataset(ctx, args.sur_train, seed=3)
         held = surrogate.make_dataset(ctx, args.sur_held, seed=1003)
         surrogate.train(mlp, train, epochs=args.sur_epochs, batch=args.sur_batch, lr=args.sur_lr)

@@ -53,6 +53,7 @@ extern "C" {
 #define GL_ECUDA (-3)     /* a CUDA runtime call failed */
 #define GL_ETIMEOUT (-4)  /* a bounded device wait gave up */
 #define GL_ENUMERIC (-5)  /* a parameter set was physically invalid (output NaN) */
+#define GL_EIO (-6)       /* a file could not be written or read, or is not a checkpoint */
 
 typedef enum {
   GL_FP64 = 0,  /* plain FP64 path: everything in double */
@@ -375,6 +376,69 @@ int gl_mlp_adam(gl_mlp *m, float lr, float beta1, float beta2, float eps, void *
 /* GL_ETIMEOUT if a tensor-core wait gave up since the last call, else GL_OK. */
 int gl_mlp_status(gl_mlp *m);
 
+/* Initial parameters: weights U(-sqrt(6 / fan_in), +sqrt(6 / fan_in)), biases
+ * U(-0.1, 0.1), each entry i drawn from SplitMix64 (Steele, Lea and Flood 2014)
+ * at (seed, i); resets the Adam state.  GL_EINVAL on NULL. */
+int gl_mlp_init(gl_mlp *m, uint64_t seed);
+
+/* ------------------------------------------------------------------------
+ * Surrogate training, error table and checkpoint (not in the paper).
+ *
+ * Training minimises the mean squared error of the network on (feat, target)
+ * by Adam over mini-batches.  The n samples are visited once per epoch in the
+ * order of a permutation drawn afresh each epoch: a four-round Feistel network
+ * on the sample index keyed by SplitMix64 at (seed, epoch), walked until it
+ * lands below n.  The learning rate of step s of the whole run (epochs x
+ * ceil(n / batch) steps) follows a cosine from lr (s = 0) to lr_end (last step).
+ * Everything a step draws follows from (seed, s), so a run can be split into
+ * calls, or resumed from a checkpoint, and gives the same parameters bit for bit
+ * as one uninterrupted call. */
+typedef struct {
+  int64_t epochs;          /* passes over the training samples (>= 1) */
+  int64_t batch;           /* samples per Adam step (1 .. 2^24); the last of an epoch may be short */
+  float lr, lr_end;        /* cosine learning-rate schedule (lr > 0, lr_end >= 0) */
+  float beta1, beta2, eps; /* Adam (as gl_mlp_adam) */
+  uint64_t seed;           /* permutation of each epoch */
+} gl_train_config;
+
+/* Steps [first_step, first_step + n_steps) of the run that cfg describes, on n
+ * samples: feat (n x 7 FP32) and target (n FP32), device memory.  *mean_loss
+ * (host, may be NULL) receives the mean of the steps' mini-batch losses (this
+ * synchronises `stream`).  The network keeps a mini-batch workspace of 32 bytes
+ * per sample of cfg->batch.  GL_EINVAL for bad arguments or a step range beyond
+ * the run. */
+int gl_surrogate_train(gl_mlp *m, int64_t n, const float *feat, const float *target,
+                       const gl_train_config *cfg, int64_t first_step, int64_t n_steps,
+                       double *mean_loss, void *stream);
+
+#define GL_SURROGATE_BINS 16
+
+/* Held-out error table of the network: table[b] = the largest |network(feat_i) -
+ * target_i| over the samples with bin_i = b (bins as gl_surrogate_features
+ * writes them; -1 ignored), +infinity for a bin without samples (its items are
+ * always recomputed exactly).  feat (n x 7), target, bin (n int32) and err (n
+ * FP32, optional: the per-sample |error|) in device memory; table
+ * (GL_SURROGATE_BINS FP32) host or device.  Synchronises `stream`. */
+int gl_surrogate_error_table(gl_mlp *m, int64_t n, const float *feat, const float *target,
+                             const int32_t *bin, float *table, float *err, void *stream);
+
+/* Checkpoint of a surrogate: the FP32 parameters, both Adam moments, the Adam
+ * step, the next schedule step `train_step`, the training configuration (with
+ * its seed, the whole state of the shuffle) and the error table
+ * (GL_SURROGATE_BINS FP32, host or device).  A binary file: a fixed header
+ * (magic "GLSURR01", version 1, sizes, steps, configuration) followed by the
+ * arrays.  Waits for the network's outstanding work.  GL_EIO if the file cannot
+ * be written. */
+int gl_surrogate_save(gl_mlp *m, const char *path, const float *table,
+                      const gl_train_config *cfg, int64_t train_step);
+
+/* Restore a checkpoint written by gl_surrogate_save into m (parameters, Adam
+ * moments and step); table (host or device), cfg and train_step (host) receive
+ * the rest and may be NULL.  GL_EIO if the file cannot be read or is not a
+ * checkpoint of this network. */
+int gl_surrogate_load(gl_mlp *m, const char *path, float *table, gl_train_config *cfg,
+                      int64_t *train_step);
+
 /* ------------------------------------------------------------------------
  * Surrogate light curves (not in the paper).  For every sub-exposure whose
  * planet overlaps the star, the deficit is the spherical planet's of equal
@@ -384,7 +448,8 @@ int gl_mlp_status(gl_mlp *m);
  * projected spin axis and the radial direction folded into [0, pi/2], k, f,
  * cos(eta) and Kipping's q1 = (u1+u2)^2, q2 = u1/(2 (u1+u2)), each scaled to
  * about [-1, 1].  A sub-exposure whose error bound, bound_table[bin] x R_eq^2,
- * exceeds bound_limit is recomputed by the exact FP32C path.  Bins (16): 8
+ * exceeds bound_limit is recomputed by the exact FP32C path.  Bins
+ * (GL_SURROGATE_BINS = 16): 8
  * equal bins of k over [0.01, 0.2] (clamped), for sub-exposures with the whole
  * ellipse on the disk (bins 0-7) and with crossings (8-15).  bound_table is 16
  * floats, host or device.  Geometry and orbit as in gl_lightcurve_batch (FP64

@@ -36,9 +36,23 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_mlp_loss_grad", "gl_mlp_adam", "gl_mlp_status", "gl_lightcurve_surrogate",
             "gl_surrogate_features", "gl_surrogate_targets", "gl_loglike", "gl_item_pipeline",
             "gl_flux_sky_simpson", "gl_lightcurve_locked", "gl_munu_to_feta",
-            "gl_feta_to_munu", "gl_munu_prior", "gl_ensemble_init", "gl_ensemble_sweep")
+            "gl_feta_to_munu", "gl_munu_prior", "gl_ensemble_init", "gl_ensemble_sweep",
+            "gl_mlp_init", "gl_surrogate_train", "gl_surrogate_error_table",
+            "gl_surrogate_save", "gl_surrogate_load")
 
-SUR_BINS = 16
+SUR_BINS = 16   # GL_SURROGATE_BINS
+GL_EIO = -6
+
+
+class TrainConfig(ctypes.Structure):
+    """gl_train_config: the schedule, batch and shuffle seed of a training run."""
+    _fields_ = [("epochs", ctypes.c_int64), ("batch", ctypes.c_int64),
+                ("lr", ctypes.c_float), ("lr_end", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 COUNT_NAMES = ("exposures", "kept", "in_window", "kepler", "items", "item_kepler", "full",
                "partial")
@@ -176,6 +190,18 @@ def load():
         lib.gl_mlp_adam.restype = i32
         lib.gl_mlp_status.argtypes = [vp]
         lib.gl_mlp_status.restype = i32
+        lib.gl_mlp_init.argtypes = [vp, ctypes.c_uint64]
+        lib.gl_mlp_init.restype = i32
+        lib.gl_surrogate_train.argtypes = [vp, i64, vp, vp, ctypes.POINTER(TrainConfig), i64, i64,
+                                           ctypes.POINTER(ctypes.c_double), vp]
+        lib.gl_surrogate_train.restype = i32
+        lib.gl_surrogate_error_table.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+        lib.gl_surrogate_error_table.restype = i32
+        lib.gl_surrogate_save.argtypes = [vp, ctypes.c_char_p, vp, ctypes.POINTER(TrainConfig), i64]
+        lib.gl_surrogate_save.restype = i32
+        lib.gl_surrogate_load.argtypes = [vp, ctypes.c_char_p, vp, ctypes.POINTER(TrainConfig),
+                                          ctypes.POINTER(i64)]
+        lib.gl_surrogate_load.restype = i32
         lib.gl_flux_sphere.argtypes = [vp, i64] + [vp] * 7 + [i32, vp]
         lib.gl_flux_sphere.restype = i32
         lib.gl_q_to_u.argtypes = [i64, vp, vp, vp, vp]
@@ -564,6 +590,43 @@ class Mlp:
 
     def status(self) -> int:
         return load().gl_mlp_status(self.handle)
+
+    def init(self, seed: int = 0):
+        self._rc(load().gl_mlp_init(self.handle, int(seed)), "gl_mlp_init")
+
+    def train(self, feat, target, cfg: TrainConfig, first_step: int, n_steps: int,
+              stream=None) -> float:
+        """Steps [first_step, first_step + n_steps) of the run cfg describes; returns
+        their mean mini-batch loss."""
+        loss = ctypes.c_double()
+        self._rc(load().gl_surrogate_train(self.handle, int(len(target)), _ptr(feat, "float32"),
+                                           _ptr(target, "float32"), ctypes.byref(cfg),
+                                           int(first_step), int(n_steps), ctypes.byref(loss),
+                                           _stream_ptr(stream)), "gl_surrogate_train")
+        return loss.value
+
+    def error_table(self, feat, target, bins, err=None, stream=None) -> np.ndarray:
+        table = np.empty(SUR_BINS, dtype=np.float32)
+        self._rc(load().gl_surrogate_error_table(
+            self.handle, int(len(target)), _ptr(feat, "float32"), _ptr(target, "float32"),
+            _ptr(bins, "int32"), table.ctypes.data, _ptr(err, "float32"), _stream_ptr(stream)),
+            "gl_surrogate_error_table")
+        return table
+
+    def save(self, path: str, table, cfg: TrainConfig, train_step: int):
+        table = np.ascontiguousarray(table, dtype=np.float32)
+        self._rc(load().gl_surrogate_save(self.handle, os.fsencode(path), table.ctypes.data,
+                                          ctypes.byref(cfg), int(train_step)), "gl_surrogate_save")
+
+    def load(self, path: str):
+        """Restore a checkpoint; returns (table, TrainConfig, train_step)."""
+        table = np.empty(SUR_BINS, dtype=np.float32)
+        cfg = TrainConfig()
+        step = ctypes.c_int64()
+        self._rc(load().gl_surrogate_load(self.handle, os.fsencode(path), table.ctypes.data,
+                                          ctypes.byref(cfg), ctypes.byref(step)),
+                 "gl_surrogate_load")
+        return table, cfg, step.value
 
 
 class Context:

@@ -1248,7 +1248,7 @@ __device__ __forceinline__ SurFeat sur_features(double x0, double y0, double k, 
   return o;
 }
 
-constexpr int kSurBins = 16;
+constexpr int kSurBins = GL_SURROGATE_BINS;
 __device__ __forceinline__ int sur_bin(int cls, double k) {
   int kb = (int)floor((k - 0.01) / (0.19 / 8.0));
   kb = kb < 0 ? 0 : (kb > 7 ? 7 : kb);

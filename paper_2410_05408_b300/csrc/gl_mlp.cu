@@ -20,12 +20,15 @@
 //                        FP32 gradient
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <vector>
 
 #include "../../include/gl.h"
+#include "gl_shuffle.cuh"
 
 namespace {
 
@@ -227,7 +230,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_gemm_kernel(GemmArgs g) {
 struct WgradArgs {
   const __nv_bfloat16* a;    // layer input activations [n][256]
   const __nv_bfloat16* dz;   // layer output gradient [n][256]
-  float* dw;                 // FP32 gradient [256 (in)][256 (out)] (added to)
+  float* part;               // per-CTA partial gradients [gridDim.x][256 (in)][256 (out)],
+                             // summed in CTA order by gl_mlp_partsum_kernel
   int64_t n;
   int* status;
 };
@@ -314,7 +318,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
         uint32_t acc[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * W + c), acc);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) atomicAdd(&g.dw[(int64_t)f * W + c + j], __uint_as_float(acc[j]));
+        for (int j = 0; j < 32; ++j)
+          g.part[(int64_t)blockIdx.x * W * W + (int64_t)f * W + c + j] = __uint_as_float(acc[j]);
       }
     }
   }
@@ -371,11 +376,12 @@ __global__ void gl_mlp_outgrad_kernel(const float* __restrict__ z4, const float*
     dz4[s * W + k] = __float2bfloat16(d * p[OFF_W5 + k] * silu_grad(z4[s * W + k]));
 }
 
-// output-layer reductions: dw5[k] += sum_s h4[s][k] dy[s]; thread 0 also sums
-// dy (db5) and rr (loss).  Thread per k, samples strided over blocks.
+// output-layer reductions: per block, sum_s h4[s][k] dy[s] (dw5), and in thread 0
+// the sums of dy (db5) and rr (loss), over the samples s = block, block + grid, ...;
+// the partials are summed over the blocks in block order afterwards.
 __global__ void gl_mlp_outred_kernel(const __nv_bfloat16* __restrict__ h4,
                                      const float* __restrict__ dy, const float* __restrict__ rr,
-                                     float* __restrict__ grad, double* __restrict__ loss,
+                                     float* __restrict__ part, double* __restrict__ lpart,
                                      int64_t n) {
   int k = threadIdx.x;
   float acc = 0.f, sdy = 0.f;
@@ -388,26 +394,27 @@ __global__ void gl_mlp_outred_kernel(const __nv_bfloat16* __restrict__ h4,
       sl += (double)rr[s];
     }
   }
-  atomicAdd(&grad[OFF_W5 + k], acc);
+  part[(int64_t)blockIdx.x * (W + 1) + k] = acc;
   if (k == 0) {
-    atomicAdd(&grad[OFF_B5], sdy);
-    atomicAdd(loss, sl);
+    part[(int64_t)blockIdx.x * (W + 1) + W] = sdy;
+    lpart[blockIdx.x] = sl;
   }
 }
 
-// bias gradient: db[o] += sum_s dz[s][o]; one thread per output column, samples
-// strided over blocks
-__global__ void gl_mlp_bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* __restrict__ db,
+// bias gradient: per block, sum_s dz[s][o] over its samples; one thread per
+// output column (partials summed in block order afterwards)
+__global__ void gl_mlp_bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* __restrict__ part,
                                     int64_t n) {
   int o = threadIdx.x;
   float acc = 0.f;
   for (int64_t s = blockIdx.x; s < n; s += gridDim.x) acc += __bfloat162float(dz[s * W + o]);
-  atomicAdd(&db[o], acc);
+  part[(int64_t)blockIdx.x * W + o] = acc;
 }
 
-// input-layer weight gradient: dW1[k][o] += sum_s x[s][k] dz1[s][o]
+// input-layer weight gradient: per block, sum_s x[s][k] dz1[s][o] (partials
+// summed in block order afterwards)
 __global__ void gl_mlp_w1grad_kernel(const float* __restrict__ x, const __nv_bfloat16* __restrict__ dz1,
-                                     float* __restrict__ grad, int64_t n) {
+                                     float* __restrict__ part, int64_t n) {
   int o = threadIdx.x;
   float acc[NIN] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
@@ -416,7 +423,25 @@ __global__ void gl_mlp_w1grad_kernel(const float* __restrict__ x, const __nv_bfl
     for (int k = 0; k < NIN; ++k) acc[k] = fmaf(x[s * NIN + k], d, acc[k]);
   }
 #pragma unroll
-  for (int k = 0; k < NIN; ++k) atomicAdd(&grad[OFF_W1 + k * W + o], acc[k]);
+  for (int k = 0; k < NIN; ++k) part[(int64_t)blockIdx.x * NIN * W + k * W + o] = acc[k];
+}
+
+// out[i] = sum over b < nb, in order, of part[b * stride + i]: the gradient sums
+// over blocks in a fixed order, so that a training run is reproducible bit for bit
+__global__ void gl_mlp_partsum_kernel(const float* __restrict__ part, int nb, int64_t stride,
+                                      int64_t count, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float acc = 0.f;
+  for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * stride + i];
+  out[i] = acc;
+}
+
+__global__ void gl_mlp_losssum_kernel(const double* __restrict__ lpart, int nb,
+                                      double* __restrict__ loss) {
+  double acc = 0.0;
+  for (int b = 0; b < nb; ++b) acc += lpart[b];
+  *loss = acc;
 }
 
 // Adam on the FP32 master parameters (bias-corrected), then refresh the BF16
@@ -445,6 +470,14 @@ __global__ void gl_mlp_cast_kernel(const float* __restrict__ p, __nv_bfloat16* _
 }
 
 constexpr size_t GEMM_SMEM = 131072 + 65536;
+// blocks of the CUDA-core gradient reductions (samples strided over them)
+constexpr int kRedBlocks = 1024;
+// floats of the partial-gradient buffer: the larger of one 256 x 256 slab per
+// tensor-core CTA (at most one per SM) and the CUDA-core reductions' partials
+constexpr size_t part_floats(int sms) {
+  return (size_t)sms * W * W > (size_t)kRedBlocks * NIN * W ? (size_t)sms * W * W
+                                                             : (size_t)kRedBlocks * NIN * W;
+}
 constexpr size_t WGRAD_SMEM = 65536 + 65536;
 
 }  // namespace
@@ -470,6 +503,14 @@ struct gl_mlp {
   double* d_loss = nullptr;
   int* d_status = nullptr;
   bool attr_set = false;
+  float* part = nullptr;       // per-block partial gradients (largest: sms x 256 x 256)
+  double* lpart = nullptr;     // per-block partial losses
+  // training (gl_surrogate_train): the gathered mini-batch and the loss sum
+  int64_t bcap = 0;
+  float* xb = nullptr;         // [bcap][7]
+  float* tb = nullptr;         // [bcap]
+  double* d_lsum = nullptr;    // sum of the mini-batch losses of a call
+  unsigned* d_table = nullptr; // per-bin maximum error, as float bits
 };
 
 namespace {
@@ -560,6 +601,8 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
   return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
 }
 
+int mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, cudaStream_t st);
+
 }  // namespace
 
 extern "C" {
@@ -579,7 +622,9 @@ int gl_mlp_create(gl_mlp** out, int device) {
       cudaMalloc(&m->wt, (size_t)3 * W * W * 2) != cudaSuccess ||
       cudaMalloc(&m->wk, (size_t)3 * W * W * 2) != cudaSuccess ||
       cudaMalloc(&m->d_loss, sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&m->part, part_floats(m->sms) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->lpart, kRedBlocks * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     delete m;
     return GL_ENOMEM;
@@ -611,6 +656,12 @@ int gl_mlp_destroy(gl_mlp* m) {
   cudaFree(m->rr);
   cudaFree(m->d_loss);
   cudaFree(m->d_status);
+  cudaFree(m->part);
+  cudaFree(m->lpart);
+  cudaFree(m->xb);
+  cudaFree(m->tb);
+  cudaFree(m->d_lsum);
+  cudaFree(m->d_table);
   delete m;
   return GL_OK;
 }
@@ -656,29 +707,53 @@ int gl_mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, doubl
   if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
   if (!dev_ptr(x, m->device) || !dev_ptr(t, m->device)) return GL_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  int rc = mlp_loss_grad(m, n, x, t, st);
+  if (rc) return rc;
+  if (loss) {
+    if (cudaMemcpyAsync(loss, m->d_loss, sizeof(double), cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return GL_ECUDA;
+  }
+  return GL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Loss (left in m->d_loss) and gradients of the mean squared error on (x, t).
+int mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, cudaStream_t st) {
   int rc = mlp_grow(m, n);
   if (rc) return rc;
   rc = mlp_forward(m, n, x, m->y, true, st);
   if (rc) return rc;
   const int64_t cs = m->cap * W;
-  cudaMemsetAsync(m->g, 0, (size_t)NPARAM * sizeof(float), st);
-  cudaMemsetAsync(m->d_loss, 0, sizeof(double), st);
   __nv_bfloat16* dzA = m->dz;
   __nv_bfloat16* dzB = m->dz + cs;
-  int bgrid = (int)(n < 1024 ? n : 1024);
+  const int bgrid = (int)(n < kRedBlocks ? n : kRedBlocks);
+  // every gradient entry is the sum of per-block partials, taken in block order
+  auto partsum = [&](int nb, int64_t stride, int64_t count, float* out) {
+    gl_mlp_partsum_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(m->part, nb, stride,
+                                                                          count, out);
+  };
   gl_mlp_outgrad_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
       m->z + 3 * cs, m->y, t, m->p, m->dy, m->rr, dzA, n);
-  gl_mlp_outred_kernel<<<bgrid, W, 0, st>>>(m->h + 3 * cs, m->dy, m->rr, m->g, m->d_loss, n);
+  gl_mlp_outred_kernel<<<bgrid, W, 0, st>>>(m->h + 3 * cs, m->dy, m->rr, m->part, m->lpart, n);
+  partsum(bgrid, W + 1, W + 1, m->g + OFF_W5);   // w5 and b5 are contiguous
+  gl_mlp_losssum_kernel<<<1, 1, 0, st>>>(m->lpart, bgrid, m->d_loss);
   for (int l = 4; l >= 2; --l) {
     // bias and weight gradients of layer l from dz_l (in dzA)
-    gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->g + off_b(l), n);
+    gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->part, n);
+    partsum(bgrid, W, W, m->g + off_b(l));
     WgradArgs wg;
     wg.a = m->h + (l - 2) * cs;
     wg.dz = dzA;
-    wg.dw = m->g + off_w(l);
+    wg.part = m->part;
     wg.n = n;
     wg.status = m->d_status;
-    gl_mlp_wgrad_kernel<<<grid_for(m, n), NTHREADS, WGRAD_SMEM, st>>>(wg);
+    const int wgrid = grid_for(m, n);
+    gl_mlp_wgrad_kernel<<<wgrid, NTHREADS, WGRAD_SMEM, st>>>(wg);
+    partsum(wgrid, (int64_t)W * W, (int64_t)W * W, m->g + off_w(l));
     // dz_{l-1} = (dz_l W_l^T) * SiLU'(z_{l-1})
     GemmArgs g;
     memset(&g, 0, sizeof g);
@@ -694,23 +769,15 @@ int gl_mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, doubl
     dzB = tmp;
   }
   // layer 1 from dz_1 (in dzA)
-  gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->g + OFF_B1, n);
-  gl_mlp_w1grad_kernel<<<bgrid, W, 0, st>>>(x, dzA, m->g, n);
-  if (cudaGetLastError() != cudaSuccess) return GL_ECUDA;
-  if (loss) {
-    if (cudaMemcpyAsync(loss, m->d_loss, sizeof(double), cudaMemcpyDefault, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return GL_ECUDA;
-  }
-  return GL_OK;
+  gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->part, n);
+  partsum(bgrid, W, W, m->g + OFF_B1);
+  gl_mlp_w1grad_kernel<<<bgrid, W, 0, st>>>(x, dzA, m->part, n);
+  partsum(bgrid, (int64_t)NIN * W, (int64_t)NIN * W, m->g + OFF_W1);
+  return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
 }
 
-int gl_mlp_adam(gl_mlp* m, float lr, float beta1, float beta2, float eps, void* stream) {
-  if (!m || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
-      !(eps > 0.f))
-    return GL_EINVAL;
-  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
-  cudaStream_t st = (cudaStream_t)stream;
+// One bias-corrected Adam step with the last gradient, then the BF16 copies.
+int mlp_adam(gl_mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t st) {
   m->step++;
   float c1 = 1.0f - powf(beta1, (float)m->step), c2 = 1.0f - powf(beta2, (float)m->step);
   gl_mlp_adam_kernel<<<(unsigned)((NPARAM + 255) / 256), 256, 0, st>>>(m->p, m->g, m->m, m->v, lr,
@@ -719,12 +786,299 @@ int gl_mlp_adam(gl_mlp* m, float lr, float beta1, float beta2, float eps, void* 
   return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
 }
 
+bool adam_args_ok(float lr, float beta1, float beta2, float eps) {
+  return (lr > 0.f) && (beta1 >= 0.f && beta1 < 1.f) && (beta2 >= 0.f && beta2 < 1.f) &&
+         (eps > 0.f);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gl_mlp_adam(gl_mlp* m, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!m || !adam_args_ok(lr, beta1, beta2, eps)) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  return mlp_adam(m, lr, beta1, beta2, eps, (cudaStream_t)stream);
+}
+
 int gl_mlp_status(gl_mlp* m) {
   if (!m) return GL_EINVAL;
   int h = 0;
   if (cudaMemcpy(&h, m->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GL_ECUDA;
   cudaMemset(m->d_status, 0, sizeof(int));
   return h ? GL_ETIMEOUT : GL_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ training
+// Initialisation, the shuffled mini-batches and the held-out error table of the
+// surrogate, and its checkpoint.  Random numbers come from SplitMix64 keyed by a
+// seed and a counter (gl_shuffle.cuh), so every draw can be recomputed from
+// (seed, counter) alone: a run resumed from a checkpoint (which stores the seed
+// and the step) draws what the uninterrupted run would have.
+namespace {
+using gl::splitmix64;
+using gl::Shuffle;
+using gl::make_shuffle;
+using gl::shuffle_index;
+
+// uniform in [0, 1) from the top 24 bits of the generator at (seed, i)
+__device__ __forceinline__ float uniform01(uint64_t seed, uint64_t i) {
+  return (float)(splitmix64(seed ^ splitmix64(i)) >> 40) * (1.0f / 16777216.0f);
+}
+
+// He-style uniform initialisation: weights U(-sqrt(6 / fan_in), +), biases U(-0.1, 0.1)
+__global__ void gl_mlp_init_kernel(float* __restrict__ p, uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NPARAM) return;
+  int fan_in;
+  bool bias;
+  if (i < OFF_B1) {
+    fan_in = NIN;
+    bias = false;
+  } else if (i < OFF_W2) {
+    fan_in = NIN;
+    bias = true;
+  } else if (i < OFF_W5) {
+    const int64_t r = (i - OFF_W2) % LAYER_STRIDE;
+    fan_in = W;
+    bias = r >= (int64_t)W * W;
+  } else {
+    fan_in = W;
+    bias = i == OFF_B5;
+  }
+  const float lim = bias ? 0.1f : sqrtf(6.0f / (float)fan_in);
+  p[i] = (2.0f * uniform01(seed, (uint64_t)i) - 1.0f) * lim;
+}
+
+// mini-batch rows [b0, b0 + nb) of the epoch's permutation gathered contiguously
+__global__ void gl_mlp_gather_kernel(const float* __restrict__ feat, const float* __restrict__ target,
+                                     int64_t n, Shuffle s, int64_t b0, int64_t nb,
+                                     float* __restrict__ xb, float* __restrict__ tb) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const int64_t src = shuffle_index(s, b0 + j, n);
+  tb[j] = target[src];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) xb[j * NIN + k] = feat[src * NIN + k];
+}
+
+__global__ void gl_mlp_addloss_kernel(const double* __restrict__ loss, double* __restrict__ sum) {
+  *sum += *loss;
+}
+
+// per-bin maximum of |y - t| (non-negative floats order like their bit patterns;
+// bit pattern + 1 is stored so that 0 marks a bin without samples)
+__global__ void gl_mlp_binmax_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                                     const int32_t* __restrict__ bin, int64_t n,
+                                     unsigned* __restrict__ table, float* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float e = fabsf(y[i] - t[i]);
+  if (err) err[i] = e;
+  const int b = bin[i];
+  if (b >= 0 && b < GL_SURROGATE_BINS) atomicMax(&table[b], __float_as_uint(e) + 1u);
+}
+
+int train_grow(gl_mlp* m, int64_t batch) {
+  if (!m->d_lsum && (cudaMalloc(&m->d_lsum, sizeof(double)) != cudaSuccess ||
+                     cudaMalloc(&m->d_table, GL_SURROGATE_BINS * sizeof(unsigned)) != cudaSuccess)) {
+    cudaGetLastError();
+    return GL_ENOMEM;
+  }
+  if (batch <= m->bcap) return GL_OK;
+  cudaFree(m->xb);
+  cudaFree(m->tb);
+  m->xb = m->tb = nullptr;
+  m->bcap = 0;
+  if (cudaMalloc(&m->xb, (size_t)batch * NIN * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&m->tb, (size_t)batch * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return GL_ENOMEM;
+  }
+  m->bcap = batch;
+  return GL_OK;
+}
+
+// learning rate of step s of a cosine schedule over `total` steps
+float cosine_lr(const gl_train_config* c, int64_t s, int64_t total) {
+  const double frac = total > 1 ? (double)s / (double)(total - 1) : 0.0;
+  return (float)(c->lr_end + 0.5 * ((double)c->lr - c->lr_end) * (1.0 + cos(3.14159265358979323846 * frac)));
+}
+
+}  // namespace
+
+extern "C" {
+
+int gl_mlp_init(gl_mlp* m, uint64_t seed) {
+  if (!m) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  gl_mlp_init_kernel<<<(unsigned)((NPARAM + 255) / 256), 256>>>(m->p, seed);
+  gl_mlp_cast_kernel<<<3 * W, W>>>(m->p, m->wt, m->wk);
+  const size_t pb = (size_t)NPARAM * sizeof(float);
+  cudaMemset(m->m, 0, pb);
+  cudaMemset(m->v, 0, pb);
+  m->step = 0;
+  return cudaDeviceSynchronize() == cudaSuccess ? GL_OK : GL_ECUDA;
+}
+
+int gl_surrogate_train(gl_mlp* m, int64_t n, const float* feat, const float* target,
+                       const gl_train_config* cfg, int64_t first_step, int64_t n_steps,
+                       double* mean_loss, void* stream) {
+  if (!m || !cfg || n <= 0 || !feat || !target || first_step < 0 || n_steps < 0) return GL_EINVAL;
+  if (cfg->epochs < 1 || cfg->batch < 1 || cfg->batch > (1 << 24) || !(cfg->lr_end >= 0.f) ||
+      !adam_args_ok(cfg->lr, cfg->beta1, cfg->beta2, cfg->eps))
+    return GL_EINVAL;
+  const int64_t spe = (n + cfg->batch - 1) / cfg->batch;   // steps per epoch
+  const int64_t total = cfg->epochs * spe;
+  if (first_step + n_steps > total) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  if (!dev_ptr(feat, m->device) || !dev_ptr(target, m->device)) return GL_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = train_grow(m, cfg->batch);
+  if (rc) return rc;
+  if (cudaMemsetAsync(m->d_lsum, 0, sizeof(double), st) != cudaSuccess) return GL_ECUDA;
+  int64_t epoch = -1;
+  Shuffle sh{};
+  for (int64_t s = first_step; s < first_step + n_steps; ++s) {
+    const int64_t e = s / spe, b0 = (s % spe) * cfg->batch;
+    if (e != epoch) {
+      epoch = e;
+      sh = make_shuffle(cfg->seed, e, n);
+    }
+    const int64_t nb = b0 + cfg->batch <= n ? cfg->batch : n - b0;
+    gl_mlp_gather_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(feat, target, n, sh, b0, nb,
+                                                                      m->xb, m->tb);
+    if ((rc = mlp_loss_grad(m, nb, m->xb, m->tb, st))) return rc;
+    gl_mlp_addloss_kernel<<<1, 1, 0, st>>>(m->d_loss, m->d_lsum);
+    if ((rc = mlp_adam(m, cosine_lr(cfg, s, total), cfg->beta1, cfg->beta2, cfg->eps, st)))
+      return rc;
+  }
+  if (cudaGetLastError() != cudaSuccess) return GL_ECUDA;
+  if (mean_loss) {
+    double sum = 0.0;
+    if (cudaMemcpyAsync(&sum, m->d_lsum, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return GL_ECUDA;
+    *mean_loss = n_steps > 0 ? sum / (double)n_steps : 0.0;
+  }
+  return GL_OK;
+}
+
+int gl_surrogate_error_table(gl_mlp* m, int64_t n, const float* feat, const float* target,
+                             const int32_t* bin, float* table, float* err, void* stream) {
+  if (!m || n < 0 || !table || (n > 0 && (!feat || !target || !bin))) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  if (n > 0 && (!dev_ptr(feat, m->device) || !dev_ptr(target, m->device) ||
+                !dev_ptr(bin, m->device) || (err && !dev_ptr(err, m->device))))
+    return GL_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = train_grow(m, 1);
+  if (rc) return rc;
+  if (cudaMemsetAsync(m->d_table, 0, GL_SURROGATE_BINS * sizeof(unsigned), st) != cudaSuccess)
+    return GL_ECUDA;
+  const int64_t chunk = (int64_t)1 << 20;
+  for (int64_t a = 0; a < n; a += chunk) {
+    const int64_t nb = a + chunk <= n ? chunk : n - a;
+    if ((rc = mlp_grow(m, nb))) return rc;
+    if ((rc = mlp_forward(m, nb, feat + a * NIN, m->y, false, st))) return rc;
+    gl_mlp_binmax_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
+        m->y, target + a, bin + a, nb, m->d_table, err ? err + a : nullptr);
+  }
+  unsigned h[GL_SURROGATE_BINS];
+  if (cudaMemcpyAsync(h, m->d_table, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GL_ECUDA;
+  // bins with no sample get +inf: their items are always recomputed exactly
+  float out[GL_SURROGATE_BINS];
+  for (int b = 0; b < GL_SURROGATE_BINS; ++b) {
+    const unsigned bits = h[b] - 1u;
+    float v;
+    memcpy(&v, &bits, sizeof v);
+    out[b] = h[b] ? v : INFINITY;
+  }
+  return cudaMemcpy(table, out, sizeof out, cudaMemcpyDefault) == cudaSuccess ? GL_OK : GL_ECUDA;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checkpoint layout: this header, then NPARAM FP32 parameters, the Adam first
+// and second moments (NPARAM FP32 each) and GL_SURROGATE_BINS FP32 error-table
+// entries, little-endian as the host writes them.
+struct CkptHeader {
+  char magic[8];          // "GLSURR01"
+  uint32_t version;       // 1
+  uint32_t nbins;         // GL_SURROGATE_BINS
+  int64_t nparam;         // gl_mlp_param_count()
+  int64_t adam_step;      // Adam steps taken (bias correction)
+  int64_t train_step;     // schedule position of the next gl_surrogate_train step
+  gl_train_config cfg;    // the schedule, batch and shuffle seed
+};
+const char kCkptMagic[8] = {'G', 'L', 'S', 'U', 'R', 'R', '0', '1'};
+
+}  // namespace
+
+extern "C" {
+
+int gl_surrogate_save(gl_mlp* m, const char* path, const float* table, const gl_train_config* cfg,
+                      int64_t train_step) {
+  if (!m || !path || !table || !cfg || train_step < 0) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  const size_t pb = (size_t)NPARAM * sizeof(float);
+  std::vector<float> buf((size_t)3 * NPARAM + GL_SURROGATE_BINS);
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(buf.data(), m->p, pb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + NPARAM, m->m, pb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + 2 * NPARAM, m->v, pb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + 3 * NPARAM, table, GL_SURROGATE_BINS * sizeof(float),
+                 cudaMemcpyDefault) != cudaSuccess)
+    return GL_ECUDA;
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kCkptMagic, sizeof kCkptMagic);
+  hd.version = 1;
+  hd.nbins = GL_SURROGATE_BINS;
+  hd.nparam = NPARAM;
+  hd.adam_step = m->step;
+  hd.train_step = train_step;
+  hd.cfg = *cfg;
+  FILE* f = fopen(path, "wb");
+  if (!f) return GL_EIO;
+  const bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 &&
+                  fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  return (fclose(f) == 0 && ok) ? GL_OK : GL_EIO;
+}
+
+int gl_surrogate_load(gl_mlp* m, const char* path, float* table, gl_train_config* cfg,
+                      int64_t* train_step) {
+  if (!m || !path) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  FILE* f = fopen(path, "rb");
+  if (!f) return GL_EIO;
+  CkptHeader hd;
+  std::vector<float> buf((size_t)3 * NPARAM + GL_SURROGATE_BINS);
+  bool ok = fread(&hd, sizeof hd, 1, f) == 1 && memcmp(hd.magic, kCkptMagic, 8) == 0 &&
+            hd.version == 1 && hd.nbins == GL_SURROGATE_BINS && hd.nparam == NPARAM &&
+            fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) return GL_EIO;
+  const size_t pb = (size_t)NPARAM * sizeof(float);
+  if (cudaMemcpy(m->p, buf.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->m, buf.data() + NPARAM, pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->v, buf.data() + 2 * NPARAM, pb, cudaMemcpyHostToDevice) != cudaSuccess)
+    return GL_ECUDA;
+  gl_mlp_cast_kernel<<<3 * W, W>>>(m->p, m->wt, m->wk);
+  if (cudaDeviceSynchronize() != cudaSuccess) return GL_ECUDA;
+  m->step = hd.adam_step;
+  if (table && cudaMemcpy(table, buf.data() + 3 * NPARAM, GL_SURROGATE_BINS * sizeof(float),
+                          cudaMemcpyDefault) != cudaSuccess)
+    return GL_ECUDA;
+  if (cfg) *cfg = hd.cfg;
+  if (train_step) *train_step = hd.train_step;
+  return GL_OK;
 }
 
 }  // extern "C"

@@ -145,14 +145,17 @@ def uneven_batch(n_curves: int = 4096, seed: int = 2, min_len: int = 100,
 def surrogate_samples(n: int, seed: int = 3) -> dict:
     """Uniform samples of the surrogate's input box: sky x, y in [-1.2, 1.2],
     k in [0.01, 0.2], f in [0, 0.9], projected-ellipse angle psi in [0, pi),
-    cos(axis tilt) in [0, 1], q1, q2 in [0, 1]."""
+    cos(axis tilt) in [0, 1], q1, q2 in [0, 1]; eta = arccos(cos(axis tilt)) is
+    the tilt angle itself (the box is uniform in its cosine)."""
     rng = _rng(seed)
-    return dict(
+    d = dict(
         x=rng.uniform(-1.2, 1.2, n), y=rng.uniform(-1.2, 1.2, n),
         k=rng.uniform(0.01, 0.2, n), f=rng.uniform(0.0, 0.9, n),
         psi=rng.uniform(0.0, np.pi, n), cos_tilt=rng.uniform(0.0, 1.0, n),
         q1=rng.uniform(0.0, 1.0, n), q2=rng.uniform(0.0, 1.0, n),
     )
+    d["eta"] = np.arccos(d["cos_tilt"])
+    return d
 
 
 def injected_curve(n_times: int = 3000, n_walkers: int = 1024, noise_ppm: float = 100.0,

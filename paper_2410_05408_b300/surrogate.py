@@ -1,11 +1,13 @@
-"""Oblate-minus-spherical flux surrogate: data, training, error table, checkpoint.
+"""Oblate-minus-spherical flux surrogate: argument marshalling over the C-ABI.
 
-Every number here is computed by the library's kernels through the C-ABI:
-the training targets come from the exact FP64 GPU integrator (gl_flux_sky for
-the oblate planet, gl_flux_sphere for the sphere of equal projected area), the
-features from gl_surrogate_features, the network's forward, backward and Adam
-steps from the tcgen05 kernels of gl_mlp.  PyTorch only holds device memory and
-shuffles sample indices.
+Every number is computed by the library (include/gl.h): the training targets by
+the exact FP64 GPU integrator (gl_flux_sky for the oblate planet, gl_flux_sphere
+for the sphere of equal projected area) and gl_surrogate_targets, the features
+by gl_surrogate_features, the initial parameters by gl_mlp_init, the training
+(shuffle, learning-rate schedule, forward, backward, Adam) by gl_surrogate_train,
+the held-out error table by gl_surrogate_error_table, the checkpoint by
+gl_surrogate_save / gl_surrogate_load.  This module only moves arrays and loops
+over epochs.  PyTorch holds device memory.
 
 The surrogate is not part of the paper; it serves the light-curve path as a
 cheaper replacement of the quadrature wherever its held-out error bound allows
@@ -14,28 +16,12 @@ cheaper replacement of the quadrature wherever its held-out error bound allows
 from __future__ import annotations
 
 import json
-import math
-import os
 
 import numpy as np
 
 from . import binding, inputs
 
 N_BINS = binding.SUR_BINS
-WIDTHS = (7, 256, 256, 256, 256, 1)
-
-
-def init_params(seed: int = 0, widths=WIDTHS) -> np.ndarray:
-    """He-style uniform initial parameters in the layout gl_mlp expects: per layer
-    the weights (fan_in x fan_out, row-major, U(-sqrt(6 / fan_in), +)) then the
-    biases (U(-0.1, 0.1)), layers in order, as one float32 vector."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for fi, fo in zip(widths[:-1], widths[1:]):
-        lim = math.sqrt(6.0 / fi)
-        parts.append(rng.uniform(-lim, lim, (fi, fo)).ravel())
-        parts.append(rng.uniform(-0.1, 0.1, fo))
-    return np.concatenate(parts).astype(np.float32)
 
 
 def make_dataset(ctx: binding.Context, n: int, seed: int, chunk: int = 2_000_000) -> dict:
@@ -44,9 +30,8 @@ def make_dataset(ctx: binding.Context, n: int, seed: int, chunk: int = 2_000_000
     import torch
     s = inputs.surrogate_samples(n, seed)
     u1, u2 = binding.gl_q_to_u(s["q1"], s["q2"])
-    # the box is uniform in cos(eta) and in the position angle of the axis
-    cols = dict(x0=s["x"], y0=s["y"], k=s["k"], f=s["f"], eta=np.arccos(s["cos_tilt"]),
-                xi=s["psi"], u1=u1, u2=u2)
+    cols = dict(x0=s["x"], y0=s["y"], k=s["k"], f=s["f"], eta=s["eta"], xi=s["psi"], u1=u1,
+                u2=u2)
     feat = torch.empty((n, 7), dtype=torch.float32, device="cuda")
     t = torch.empty(n, dtype=torch.float32, device="cuda")
     scale = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -70,31 +55,27 @@ def make_dataset(ctx: binding.Context, n: int, seed: int, chunk: int = 2_000_000
     return dict(feat=feat, t=t, scale=scale, bins=bins)
 
 
+def config(n: int, epochs: int, batch: int = 16384, lr: float = 2e-3, lr_end: float = 5e-5,
+           seed: int = 0) -> binding.TrainConfig:
+    """The gl_train_config of a run (Adam's usual betas and epsilon)."""
+    return binding.TrainConfig(epochs=epochs, batch=batch, lr=lr, lr_end=lr_end, beta1=0.9,
+                               beta2=0.999, eps=1e-8, seed=seed)
+
+
+def steps_per_epoch(n: int, cfg: binding.TrainConfig) -> int:
+    return -(-n // cfg.batch)
+
+
 def train(mlp: binding.Mlp, data: dict, epochs: int, batch: int = 16384, lr: float = 2e-3,
           lr_end: float = 5e-5, seed: int = 0, log=None) -> list:
-    """Mini-batch Adam with a cosine learning-rate schedule; returns the mean
+    """A whole run of gl_surrogate_train, one call per epoch; returns the mean
     training loss of each epoch."""
-    import torch
     n = data["t"].numel()
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
-    steps_per_epoch = (n + batch - 1) // batch
-    total = epochs * steps_per_epoch
-    step, history = 0, []
+    cfg = config(n, epochs, batch, lr, lr_end, seed)
+    spe = steps_per_epoch(n, cfg)
+    history = []
     for ep in range(epochs):
-        perm = torch.randperm(n, device="cuda", generator=g)
-        acc, cnt = 0.0, 0
-        for a in range(0, n, batch):
-            idx = perm[a:a + batch]
-            x = data["feat"].index_select(0, idx).contiguous()
-            t = data["t"].index_select(0, idx).contiguous()
-            loss = mlp.loss_grad(x, t)
-            frac = step / max(1, total - 1)
-            mlp.adam(lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * frac)))
-            acc += loss
-            cnt += 1
-            step += 1
-        history.append(acc / max(cnt, 1))
+        history.append(mlp.train(data["feat"], data["t"], cfg, ep * spe, spe))
         if log:
             log(f"epoch {ep + 1}/{epochs}: loss {history[-1]:.3e}")
     return history
@@ -110,41 +91,23 @@ def predict(mlp: binding.Mlp, feat, chunk: int = 1 << 20):
     return out
 
 
-def error_table(mlp: binding.Mlp, data: dict) -> np.ndarray:
+def error_table(mlp: binding.Mlp, data: dict, err=None) -> np.ndarray:
     """Per bin, the largest |predicted - exact| normalised residual on the data
-    (held-out samples); bins without samples get +inf (always fall back)."""
-    import torch
-    err = (predict(mlp, data["feat"]) - data["t"]).abs()
-    b = data["bins"].long()
-    keep = b >= 0
-    table = torch.full((N_BINS,), -1.0, dtype=torch.float32, device="cuda")
-    table.scatter_reduce_(0, b[keep], err[keep], reduce="amax", include_self=True)
-    out = table.cpu().numpy()
-    out[out < 0] = np.inf
-    return out.astype(np.float32)
+    (held-out samples), +inf for bins without samples (gl_surrogate_error_table);
+    `err` (n float32 on the GPU, optional) receives the per-sample error."""
+    return mlp.error_table(data["feat"], data["t"], data["bins"], err)
 
 
-def flux_error_quantiles(mlp: binding.Mlp, data: dict, qs=(0.5, 0.99, 0.999, 1.0)) -> dict:
-    """Quantiles of |error| in flux units (normalised error x R_eq^2) over the
-    samples that overlap the star."""
-    import torch
-    err = ((predict(mlp, data["feat"]) - data["t"]).abs() * data["scale"])[data["bins"] >= 0]
-    v = torch.quantile(err.double()[: 1 << 24], torch.tensor(qs, dtype=torch.float64,
-                                                              device="cuda"))
-    return {str(q): float(x) for q, x in zip(qs, v.cpu())}
-
-
-def save(path: str, mlp: binding.Mlp, table: np.ndarray, meta: dict) -> None:
-    """Checkpoint: FP32 parameters (.npy), error table and metadata (.json)."""
-    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
-    np.save(path + ".params.npy", mlp.get_params())
-    with open(path + ".json", "w") as fh:
-        json.dump(dict(meta, table=[float(x) for x in table]), fh, indent=1)
+def save(path: str, mlp: binding.Mlp, table, cfg: binding.TrainConfig, train_step: int,
+         meta: dict | None = None) -> None:
+    """Checkpoint (gl_surrogate_save); `meta` (run notes, optional) goes to a JSON
+    file beside it."""
+    mlp.save(path, table, cfg, train_step)
+    if meta is not None:
+        with open(path + ".json", "w") as fh:
+            json.dump(meta, fh, indent=1)
 
 
 def load(path: str, mlp: binding.Mlp):
-    """Restore parameters into `mlp` (Adam state restarts); returns (table, meta)."""
-    mlp.set_params(np.load(path + ".params.npy"))
-    with open(path + ".json") as fh:
-        meta = json.load(fh)
-    return np.asarray(meta.pop("table"), dtype=np.float32), meta
+    """Restore a checkpoint into `mlp`; returns (table, TrainConfig, train_step)."""
+    return mlp.load(path)
