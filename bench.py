@@ -875,6 +875,7 @@ def main():
             ctx.profile(binding.PROFILE_GRAPH)   # reset the accumulated times
         gc_was = gc.isenabled()
         gc.disable()   # no collector pause between a step's events
+        torch.cuda.nvtx.range_push(f"timed steps (precision {prec}, profile {profile})")
         try:
             for i in range(k):
                 flush.zero_()
@@ -883,6 +884,7 @@ def main():
                 evs[i][1].record(stream)
             torch.cuda.synchronize(dev)
         finally:
+            torch.cuda.nvtx.range_pop()
             if gc_was:
                 gc.enable()
         per_step = [a.elapsed_time(b) for a, b in evs]

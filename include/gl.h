@@ -308,6 +308,14 @@ int gl_autotune(gl_context *ctx, const gl_params *p, const gl_times *t, double *
 int gl_configure(gl_context *ctx, gl_precision prec, int threads, int nodes, int quad_ctas,
                  int exposure_block);
 
+/* Allocation-failure hook (for tests; not in the paper).  With bytes > 0 the
+ * context refuses to grow any workspace to more than `bytes`, exactly as if
+ * cudaMalloc had failed: the call returns GL_ENOMEM with a message and the
+ * context stays usable (the refused buffer is released, so a later call with the
+ * limit lifted allocates it again).  bytes = 0 lifts the limit.  GL_EINVAL on
+ * NULL or bytes < 0. */
+int gl_debug_alloc_limit(gl_context *ctx, int64_t bytes);
+
 /* Kernel kinds for gl_profile_read. */
 #define GL_KERNEL_SETUP 0   /* per-set constants */
 #define GL_KERNEL_CURVE 1   /* light-curve tile kernel, or the item pipeline's
@@ -375,6 +383,16 @@ int gl_mlp_loss_grad(gl_mlp *m, int64_t n, const float *x, const float *t, doubl
 int gl_mlp_adam(gl_mlp *m, float lr, float beta1, float beta2, float eps, void *stream);
 /* GL_ETIMEOUT if a tensor-core wait gave up since the last call, else GL_OK. */
 int gl_mlp_status(gl_mlp *m);
+
+/* Failure-detection probe (for tests; not in the paper).  With polls > 0, every
+ * tensor-core kernel of the following gl_mlp_forward / gl_mlp_loss_grad calls,
+ * after allocating its tensor memory and before issuing any MMA, waits `polls`
+ * times on an mbarrier phase that nothing completes.  The wait runs out as any
+ * bounded device wait that gives up would: the kernel records it (gl_mlp_status
+ * then returns GL_ETIMEOUT), frees its tensor memory and returns, leaving that
+ * call's outputs undefined.  No tensor-core work is in flight when it gives up.
+ * polls = 0 turns the probe off.  GL_EINVAL on NULL or polls < 0. */
+int gl_mlp_wait_probe(gl_mlp *m, int polls);
 
 /* Initial parameters: weights U(-sqrt(6 / fan_in), +sqrt(6 / fan_in)), biases
  * U(-0.1, 0.1), each entry i drawn from SplitMix64 (Steele, Lea and Flood 2014)

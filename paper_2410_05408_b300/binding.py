@@ -38,7 +38,8 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_flux_sky_simpson", "gl_lightcurve_locked", "gl_munu_to_feta",
             "gl_feta_to_munu", "gl_munu_prior", "gl_ensemble_init", "gl_ensemble_sweep",
             "gl_mlp_init", "gl_surrogate_train", "gl_surrogate_error_table",
-            "gl_surrogate_save", "gl_surrogate_load")
+            "gl_surrogate_save", "gl_surrogate_load", "gl_mlp_wait_probe",
+            "gl_debug_alloc_limit")
 
 SUR_BINS = 16   # GL_SURROGATE_BINS
 GL_EIO = -6
@@ -192,6 +193,10 @@ def load():
         lib.gl_mlp_status.restype = i32
         lib.gl_mlp_init.argtypes = [vp, ctypes.c_uint64]
         lib.gl_mlp_init.restype = i32
+        lib.gl_mlp_wait_probe.argtypes = [vp, i32]
+        lib.gl_mlp_wait_probe.restype = i32
+        lib.gl_debug_alloc_limit.argtypes = [vp, i64]
+        lib.gl_debug_alloc_limit.restype = i32
         lib.gl_surrogate_train.argtypes = [vp, i64, vp, vp, ctypes.POINTER(TrainConfig), i64, i64,
                                            ctypes.POINTER(ctypes.c_double), vp]
         lib.gl_surrogate_train.restype = i32
@@ -591,6 +596,9 @@ class Mlp:
     def status(self) -> int:
         return load().gl_mlp_status(self.handle)
 
+    def wait_probe(self, polls: int):
+        self._rc(load().gl_mlp_wait_probe(self.handle, int(polls)), "gl_mlp_wait_probe")
+
     def init(self, seed: int = 0):
         self._rc(load().gl_mlp_init(self.handle, int(seed)), "gl_mlp_init")
 
@@ -694,6 +702,9 @@ class Context:
 
     def item_pipeline(self, on: bool = True, max_items: int = 0):
         gl_item_pipeline(self.handle, on, max_items)
+
+    def alloc_limit(self, nbytes: int):
+        _check(self.handle, load().gl_debug_alloc_limit(self.handle, int(nbytes)))
 
     def profile(self, on=True):
         _check(self.handle, gl_profile_enable(self.handle, on))

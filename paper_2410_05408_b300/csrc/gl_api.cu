@@ -10,6 +10,7 @@
 //                      exposure mean
 //   gl_sky_kernel      geometry-level flux for given sky positions
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -31,6 +32,15 @@ namespace {
 
 // status bits accumulated on the device
 enum : int { kStatusInvalidSet = 1, kStatusBadOffsets = 2, kStatusTimeout = 4, kStatusOverflow = 8 };
+// NVTX range over a scope (shown by profilers on the host timeline; a no-op
+// when none is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Boundaries of a light-curve step at which profiling mode 2 records events
 // inside the step graph: before the constants, then after each kernel.
 enum : int { kMarkStart = 0, kMarkSetup, kMarkWindow, kMarkExposures, kMarkItems, kMarkSums,
@@ -1770,6 +1780,7 @@ struct gl_context {
   uint64_t graph_clock = 0;
   int64_t graph_launches = 0;
   int64_t launches = 0;
+  size_t alloc_limit = 0;       // gl_debug_alloc_limit (0: none)
   // per-kernel event timing (gl_profile_enable)
   bool profiling = false;      // mode 1: eager launches bracketed by events
   bool gprof = false;          // mode 2: event-record nodes inside the step graph
@@ -1832,6 +1843,9 @@ int grow(gl_context* ctx, void** buf, size_t* cap, size_t need) {
   *buf = nullptr;
   *cap = 0;
   size_t sz = need + need / 4 + 4096;
+  if (ctx->alloc_limit && sz > ctx->alloc_limit)
+    return fail(ctx, GL_ENOMEM, "allocation of %zu bytes refused (test limit %zu bytes)", sz,
+                ctx->alloc_limit);
   if (cudaMalloc(buf, sz) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, GL_ENOMEM, "cudaMalloc of %zu bytes failed", sz);
@@ -2079,6 +2093,7 @@ struct StepArgs {
 };
 
 int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
+  NvtxRange nv("light-curve step: enqueue kernels");
   gmark(ctx, kMarkStart, st);
   long pe = prof_begin(ctx, GL_KERNEL_SETUP, st);
   // the item pipeline's counters are zeroed here (one graph node less than a
@@ -2129,6 +2144,7 @@ int enqueue_step(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
 // Replay a captured step for these exact arguments, capturing it on first use.
 // Capture happens on the context's private stream; the graph is launched on `st`.
 int launch_step_graph(gl_context* ctx, const StepArgs& sa, cudaStream_t st) {
+  NvtxRange nv("light-curve step: graph");
   unsigned char key[sizeof(StepArgs)];
   memcpy(key, &sa, sizeof sa);
   gl_context::GraphEntry* hit = nullptr;
@@ -2348,6 +2364,7 @@ int gl_configure(gl_context* ctx, gl_precision prec, int threads, int nodes, int
 
 int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
                 gl_precision prec, void* stream, gl_tune_report* rep) {
+  NvtxRange nv("gl_autotune");
   if (!ctx || !p || !tm || !out) return GL_EINVAL;
   if (prec != GL_FP64 && prec != GL_FP32C) return fail(ctx, GL_EINVAL, "bad precision");
   if (!is_device_ptr(out, ctx->device) || !is_device_ptr(tm->t, ctx->device))
@@ -2488,6 +2505,12 @@ int gl_autotune(gl_context* ctx, const gl_params* p, const gl_times* tm, double*
   return GL_OK;
 }
 
+int gl_debug_alloc_limit(gl_context* ctx, int64_t bytes) {
+  if (!ctx || bytes < 0) return GL_EINVAL;
+  ctx->alloc_limit = (size_t)bytes;
+  return GL_OK;
+}
+
 int gl_profile_enable(gl_context* ctx, int on) {
   if (!ctx || on < 0 || on > 2) return GL_EINVAL;
   ctx->profiling = on == 1;
@@ -2567,6 +2590,7 @@ namespace {
 
 int lightcurve_impl(gl_context* ctx, const gl_params* p, const gl_times* tm, double* out,
                     gl_precision prec, void* stream, bool locked) {
+  NvtxRange nv(locked ? "gl_lightcurve_locked" : "gl_lightcurve_batch");
   if (!ctx) return GL_EINVAL;
   ctx->err[0] = 0;
   if (!p || !tm) return fail(ctx, GL_EINVAL, "NULL params or times");
@@ -2926,6 +2950,7 @@ int gl_ensemble_sweep(gl_context* ctx, const gl_ensemble* e, const double* rnd,
 int gl_lightcurve_surrogate(gl_context* ctx, gl_mlp* mlp, const gl_params* p, const gl_times* tm,
                             double* out, const float* bound_table, double bound_limit,
                             void* stream, gl_surrogate_stats* stats) {
+  NvtxRange nv("gl_lightcurve_surrogate");
   if (!ctx) return GL_EINVAL;
   ctx->err[0] = 0;
   if (!mlp || !p || !tm || !out || !bound_table) return fail(ctx, GL_EINVAL, "NULL argument");

@@ -20,6 +20,7 @@
 //                        FP32 gradient
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -84,10 +85,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
       smem_u32(mbar)));
 }
-// bounded wait on an mbarrier phase; returns 1 if the phase completed
-__device__ __forceinline__ uint32_t mbar_wait(uint64_t* mbar, uint32_t parity) {
+// bounded wait on an mbarrier phase (at most `limit` polls); returns 1 if the
+// phase completed
+__device__ __forceinline__ uint32_t mbar_wait(uint64_t* mbar, uint32_t parity,
+                                              long limit = 1L << 22) {
   uint32_t done = 0;
-  for (long it = 0; it < (1L << 22) && !done; ++it) {
+  for (long it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
@@ -126,6 +129,7 @@ struct GemmArgs {
   __nv_bfloat16* hout;        // forward: SiLU(z); backward: dz_prev  [n][256]
   int64_t n;
   int* status;
+  int probe_polls;             // > 0: failure-detection probe (gl_mlp_wait_probe)
 };
 
 // Persistent tensor-core layer: B resident in shared memory, one 128-row tile
@@ -162,7 +166,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_gemm_kernel(GemmArgs g) {
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_bf16(TILE_M, W);
   uint32_t phase = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  if (g.probe_polls > 0) {
+    // Failure-detection probe: before any MMA is issued, wait on the current
+    // phase of the mbarrier, which nothing arrives on, for probe_polls polls.
+    // The wait gives up; the CTA records the timeout like any bounded wait that
+    // ran out and leaves through the normal exit (TMEM freed below).
+    const uint32_t done = mbar_wait(&mbar, 0, g.probe_polls);
+    if (tid == 0) {
+      if (!done) atomicOr(g.status, 1);
+      s_abort = 1;
+    }
+    __syncthreads();
+  }
+  for (int64_t tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
     const int64_t row0 = tile * TILE_M;
     for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
       int r = v >> 5, kg = v & 31;
@@ -503,6 +519,7 @@ struct gl_mlp {
   double* d_loss = nullptr;
   int* d_status = nullptr;
   bool attr_set = false;
+  int probe_polls = 0;         // gl_mlp_wait_probe
   float* part = nullptr;       // per-block partial gradients (largest: sms x 256 x 256)
   double* lpart = nullptr;     // per-block partial losses
   // training (gl_surrogate_train): the gathered mini-batch and the loss sum
@@ -592,6 +609,7 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
     g.hout = m->h + (l - 1) * cs;
     g.n = n;
     g.status = m->d_status;
+    g.probe_polls = m->probe_polls;
     if (train)
       gl_mlp_gemm_kernel<EPI_FWD_TRAIN><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
     else
@@ -602,6 +620,9 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
 }
 
 int mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, cudaStream_t st);
+int surrogate_train(gl_mlp* m, int64_t n, const float* feat, const float* target,
+                    const gl_train_config* cfg, int64_t first_step, int64_t n_steps,
+                    double* mean_loss, void* stream);
 
 }  // namespace
 
@@ -911,6 +932,12 @@ float cosine_lr(const gl_train_config* c, int64_t s, int64_t total) {
 
 extern "C" {
 
+int gl_mlp_wait_probe(gl_mlp* m, int polls) {
+  if (!m || polls < 0) return GL_EINVAL;
+  m->probe_polls = polls;
+  return GL_OK;
+}
+
 int gl_mlp_init(gl_mlp* m, uint64_t seed) {
   if (!m) return GL_EINVAL;
   if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
@@ -926,6 +953,19 @@ int gl_mlp_init(gl_mlp* m, uint64_t seed) {
 int gl_surrogate_train(gl_mlp* m, int64_t n, const float* feat, const float* target,
                        const gl_train_config* cfg, int64_t first_step, int64_t n_steps,
                        double* mean_loss, void* stream) {
+  nvtxRangePushA("gl_surrogate_train");
+  const int rc = surrogate_train(m, n, feat, target, cfg, first_step, n_steps, mean_loss, stream);
+  nvtxRangePop();
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+int surrogate_train(gl_mlp* m, int64_t n, const float* feat, const float* target,
+                    const gl_train_config* cfg, int64_t first_step, int64_t n_steps,
+                    double* mean_loss, void* stream) {
   if (!m || !cfg || n <= 0 || !feat || !target || first_step < 0 || n_steps < 0) return GL_EINVAL;
   if (cfg->epochs < 1 || cfg->batch < 1 || cfg->batch > (1 << 24) || !(cfg->lr_end >= 0.f) ||
       !adam_args_ok(cfg->lr, cfg->beta1, cfg->beta2, cfg->eps))
@@ -965,6 +1005,10 @@ int gl_surrogate_train(gl_mlp* m, int64_t n, const float* feat, const float* tar
   }
   return GL_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int gl_surrogate_error_table(gl_mlp* m, int64_t n, const float* feat, const float* target,
                              const int32_t* bin, float* table, float* err, void* stream) {
