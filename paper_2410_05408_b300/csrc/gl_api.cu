@@ -429,9 +429,23 @@ __device__ __noinline__ int item_geometry(const SetConst& c, int flag, const gl:
   return gl::classify(c, xd, yd, zd);
 }
 
-// Deficit of one item: limb-darkened occulted flux over F0, in precision R.
+// Deficit of a whole ellipse on the disk whose g has a single maximum (the common
+// item; a small function of its own), in precision R.
+template <typename R>
+__device__ __noinline__ R whole_deficit(const SetConst& c, R x, R y, R o, int base) {
+  R I[3];
+  gl::whole_single_moments<R>(c, x, y, o, set_rule<R>(c, base), I);
+  return (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
+          gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
+}
+
+// Deficit of one item: limb-darkened occulted flux over F0, in precision R.  A
+// whole ellipse with a single maximum of g goes to whole_deficit (every path, so
+// that they agree to the bit).
 template <typename R>
 __device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls, int base) {
+  if (cls == gl::kFull && !gl::maybe_two_maxima(c, (float)x, (float)y))
+    return whole_deficit<R>(c, x, y, o, base);
   R I[3];
   gl::occulted_r<R>(c, x, y, o, cls, set_rule<R>(c, base), I);
   return (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
@@ -905,7 +919,13 @@ __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
     idef[g] = item_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2], cls, rb);
   };
   auto run = [&](long long u, bool part) {
-    run_item(part ? a.iq[a.item_cap - 1 - u] : a.iq[u], part ? gl::kPartial : gl::kFull);
+    if (part) {
+      run_item(a.iq[a.item_cap - 1 - u], gl::kPartial);
+    } else {   // the front of the queue: whole ellipses with a single maximum of g
+      const long long g = a.iq[u];
+      const SetConst& c = a.sets[a.iset[g]];
+      idef[g] = whole_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2], rb);
+    }
   };
   // Pass 1, crossing items: a warp of them issues ~200 FP64 instructions and each
   // holds its sub-partition's FP64 unit ~64 cycles whatever the active lanes, so

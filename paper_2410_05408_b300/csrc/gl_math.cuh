@@ -898,10 +898,22 @@ GL_HD Geo<R> make_geo(const SetConst& c, R x0, R y0, R omr2) {
 }
 
 // (1 - mu^3) / (3 r^2) written without the r -> 0 cancellation:
-// (1 + mu + mu^2) / (3 (1 + mu)), mu = sqrt(1 - r^2).
+// (1 + mu + mu^2) / (3 (1 + mu)), mu = sqrt(1 - r^2).  In FP32 on the GPU the
+// square root and the reciprocal are the hardware approximations (about one ulp;
+// every node of the f_lin quadrature evaluates this, and the correctly rounded
+// forms cost a multi-instruction sequence each).
 template <typename R>
 GL_HD R lin_kernel(R omr2) {
-  R mu = m_sqrt(omr2 > R(0) ? omr2 : R(0));
+  const R o = omr2 > R(0) ? omr2 : R(0);
+#if defined(__CUDA_ARCH__)
+  if constexpr (sizeof(R) == 4) {
+    float mu, r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(mu) : "f"(o));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(3.0f + 3.0f * mu));
+    return (1.0f + mu + mu * mu) * r;
+  }
+#endif
+  R mu = m_sqrt(o);
   return (R(1) + mu + mu * mu) * rcp_<R>(R(3) + R(3) * mu);
 }
 
@@ -983,14 +995,37 @@ GL_HD void nearest_limb_angle(const Geo<R>& g, const Trig2<R>& t, R* cs, R* ss) 
     if (step > R(0.5)) step = R(0.5);
     if (step < R(-0.5)) step = R(-0.5);
     R sa, ca;
-    sincos_<R>(-step, &sa, &ca);
+    if constexpr (sizeof(R) == 4) {
+      // |step| <= 1/2: Taylor polynomials of sin (to x^7) and cos (to x^8),
+      // truncation below 5e-9, under the FP32 rounding
+      const R x = -step, x2 = x * x;
+      sa = x * (R(1) - x2 * (R(1.0 / 6.0) - x2 * (R(1.0 / 120.0) - x2 * R(1.0 / 5040.0))));
+      ca = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24.0) - x2 * (R(1.0 / 720.0) - x2 * R(1.0 / 40320.0))));
+    } else {
+      sincos_<R>(-step, &sa, &ca);
+    }
     R nc = ct * ca - st * sa, ns = st * ca + ct * sa;
     ct = nc;
     st = ns;
   }
+  if constexpr (sizeof(R) == 4) {   // back onto the unit circle after the rotations
+    const R r = rsqrt_<R>(ct * ct + st * st);
+    ct *= r;
+    st *= r;
+  }
   *cs = ct;
   *ss = st;
 }
+
+// Moments of a whole ellipse on the disk whose g has a single maximum (the
+// classification and maybe_two_maxima decide that): area, the full-turn f_lin
+// rule clustered at the maximum (Newton's method), second moment in closed form.
+// The same as occulted_r's whole-ellipse branch for such an ellipse, written on
+// its own so that the light-curve kernels can call a small function for the
+// common case.
+template <typename R>
+GL_HD void whole_single_moments(const SetConst& c, R x0, R y0, R omr2, const NodeRule<R>& rule,
+                                R I[3]);
 
 // ------------------------------------------------------------------ quartics
 // Division and cosine for the quartic solver.  FAST (FP32 on the GPU only): the
@@ -1236,35 +1271,61 @@ GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, 
   int nr = quartic_real_roots<float, true>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv,
                                            fr.q[0] * inv, xs);
   bool ok = (nr % 2) == 0;
-  for (int i = 0; i < nr && ok; ++i) {
-    // Newton steps on the FP64 quartic with the derivative frozen at the FP32
-    // estimate and its reciprocal taken in FP32 (relative error 2^-23).  One step
-    // from an estimate within 1e-5 (1 + |t|) leaves an error below
-    // 2^-23 |s| + (P''/P') s^2 / 2, far below the FP32 rounding that the quadrature
-    // applies to t next; a larger first step iterates to 1e-9 (1 + |t|).  The step
-    // bounds are formed in FP32 and compared by bit patterns (on B300 every FP64
-    // instruction holds the FP64 unit for its full issue time; the conversions stay
-    // hardware ones, which measured faster here than integer ones on this
-    // latency-critical chain).
-    double t = (double)xs[i];
-    double fp = ((4.0 * f.q[4] * t + 3.0 * f.q[3]) * t + 2.0 * f.q[2]) * t + f.q[1];
-    double r = (double)rcp_<float>((float)fp);
-    const float at = 1.0f + fabsf(xs[i]);
-    const double lim1 = (double)(1e-5f * at), lim2 = (double)(1e-9f * at);
-    bool conv = false;
-    for (int it = 0; it < 4; ++it) {
-      double fv = (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
-      double step = fv * r;
-      if (!finite_bits(step)) break;
-      t -= step;
-      if (abs_le(step, it == 0 ? lim1 : lim2)) {
-        conv = true;
-        break;
-      }
+  // Newton steps on the FP64 quartic with the derivative frozen at the FP32
+  // estimate and its reciprocal taken in FP32.  One step from an estimate within
+  // 1e-5 (1 + |t|) leaves an error below eps_r |s| + (P''/P') s^2 / 2 (eps_r the
+  // relative error of the FP32 derivative), far below the FP32 rounding that the
+  // quadrature applies to t next; a larger first step iterates to 1e-9 (1 + |t|).
+  // The step bounds are formed in FP32 and compared by bit patterns (on B300 every
+  // FP64 instruction, conversions included, holds the FP64 unit for its full issue
+  // time).  The roots take their steps side by side (unrolled over the at most
+  // four roots, each its own dependency chain).
+  double tt[4], rr[4], l1[4], l2[4];
+  bool conv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    tt[i] = rr[i] = l1[i] = l2[i] = 0.0;
+    conv[i] = i >= nr;
+    if (i < nr) {   // (skipped by a warp none of whose items has this many roots)
+      // The frozen derivative only scales the step (the fixed point t - P(t) r is
+      // P(t) = 0 for any r != 0), so it comes from the FP32 frame; the estimate,
+      // the scale and the bounds reach FP64 by integer conversion.  The FP64 unit
+      // sees only the residual of the FP64 quartic and the update.
+      const float xi = xs[i];
+      const float fpf = ((4.0f * fr.q[4] * xi + 3.0f * fr.q[3]) * xi + 2.0f * fr.q[2]) * xi +
+                        fr.q[1];
+      rr[i] = f32_to_f64_int(rcp_<float>(fpf));
+      const float at = 1.0f + fabsf(xi);
+      l1[i] = f32_to_f64_int(1e-5f * at);
+      l2[i] = f32_to_f64_int(1e-9f * at);
+      tt[i] = f32_to_f64_int(xi);
     }
-    ok = conv;
-    tr[i] = t;
   }
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    bool all = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) all = all && conv[i];
+    if (all) break;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (conv[i]) continue;
+      const double t = tt[i];
+      const double fv = (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
+      const double step = fv * rr[i];
+      if (!finite_bits(step)) {
+        conv[i] = true;   // gives up: this root cannot be polished (fallback below)
+        ok = false;
+        continue;
+      }
+      tt[i] = t - step;
+      if (abs_le(step, it == 0 ? l1[i] : l2[i])) conv[i] = true;
+      else if (it == 3) ok = false;   // not converged in four steps
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < nr) tr[i] = tt[i];
   if (ok) {
     sort_small(tr, nr);
     for (int i = 0; i + 1 < nr; ++i)
@@ -1488,6 +1549,19 @@ GL_HD void whole_arcs(const Geo<R>& g, const Trig2<R>& tg, int nmax, const R* cm
 GL_HD bool maybe_two_maxima(const SetConst& c, float x0, float y0) {
   const float B = 2.0f * (x0 * c.fdx + y0 * c.fdy1), C = 2.0f * y0 * c.fdy2;
   return B * B + C * C <= 25.0f * (c.flpD * c.flpD + c.flpE * c.flpE);
+}
+
+template <typename R>
+GL_HD void whole_single_moments(const SetConst& c, R x0, R y0, R omr2, const NodeRule<R>& rule,
+                                R I[3]) {
+  Geo<R> g = make_geo<R>(c, x0, y0, omr2);
+  Trig2<R> tg = limb_poly<R>(c, x0, y0, omr2);
+  const R area = R(kPi) * g.dx * g.dy2;
+  R cs, ss;
+  nearest_limb_angle<R>(g, tg, &cs, &ss);
+  I[0] = area;
+  I[1] = lin_full<R>(g, cs, ss, rule);
+  I[2] = area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) * R(0.25));
 }
 
 // ------------------------------------------------------------------ occulted moments
