@@ -439,17 +439,25 @@ __device__ __noinline__ R whole_deficit(const SetConst& c, R x, R y, R o, int ba
           gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
 }
 
-// Deficit of one item: limb-darkened occulted flux over F0, in precision R.  A
-// whole ellipse with a single maximum of g goes to whole_deficit (every path, so
-// that they agree to the bit).
-template <typename R>
-__device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls, int base) {
-  if (cls == gl::kFull && !gl::maybe_two_maxima(c, (float)x, (float)y))
-    return whole_deficit<R>(c, x, y, o, base);
+// Deficit of an item of class CLS (kPartial: the boundary may cross the limb;
+// kFull: a whole ellipse whose g may have two maxima), each class compiled on its
+// own so that each routine carries only its own branch of occulted_r.
+template <typename R, int CLS>
+__device__ __noinline__ R class_deficit(const SetConst& c, R x, R y, R o, int base) {
   R I[3];
-  gl::occulted_r<R>(c, x, y, o, cls, set_rule<R>(c, base), I);
+  gl::occulted_r<R>(c, x, y, o, CLS, set_rule<R>(c, base), I);
   return (gl::pick<R>(c.c0, c.fc0) * I[0] + gl::pick<R>(c.c1, c.fc1) * I[1] +
           gl::pick<R>(c.c2, c.fc2) * I[2]) * gl::pick<R>(c.invF0, c.finvF0);
+}
+
+// Deficit of one item: limb-darkened occulted flux over F0, in precision R, by
+// the routine of its kind (every path calls these same routines, so that they
+// agree to the bit).
+template <typename R>
+__device__ __noinline__ R item_deficit(const SetConst& c, R x, R y, R o, int cls, int base) {
+  if (cls == gl::kPartial) return class_deficit<R, gl::kPartial>(c, x, y, o, base);
+  if (!gl::maybe_two_maxima(c, (float)x, (float)y)) return whole_deficit<R>(c, x, y, o, base);
+  return class_deficit<R, gl::kFull>(c, x, y, o, base);
 }
 
 // Flux of one live exposure computed by the calling thread alone (the item
@@ -919,8 +927,11 @@ __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
     idef[g] = item_deficit<R>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2], cls, rb);
   };
   auto run = [&](long long u, bool part) {
-    if (part) {
-      run_item(a.iq[a.item_cap - 1 - u], gl::kPartial);
+    if (part) {   // the back of the queue: items whose boundary may cross the limb
+      const long long g = a.iq[a.item_cap - 1 - u];
+      const SetConst& c = a.sets[a.iset[g]];
+      idef[g] = class_deficit<R, gl::kPartial>(c, ipos[3 * g], ipos[3 * g + 1], ipos[3 * g + 2],
+                                               rb);
     } else {   // the front of the queue: whole ellipses with a single maximum of g
       const long long g = a.iq[u];
       const SetConst& c = a.sets[a.iset[g]];
