@@ -988,6 +988,19 @@ __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
 // instruction holds the FP64 unit like an FP64 add).
 // Exposures that did not fit the workspace are finished here, each by one
 // thread (exact window, midpoint state, every sub-exposure in order).
+// An exposure the workspace could not hold, finished by the calling thread
+// (compiled apart from the sum kernel's loop, which it would otherwise swell).
+template <typename R>
+__device__ __noinline__ void finish_overflow(const LcArgs& a, int k, int rb) {
+  const int j = a.klist[k], st = a.kset[k];
+  const SetConst& c = a.sets[st];
+  const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)st * a.n_times;
+  double tau;
+  gl::MidState mid;
+  const int fl = exposure_prep<R>(c, a.t[ti], &tau, &mid);
+  a.out[j] = (fl & kExpDead) ? 1.0 : exposure_local<R>(c, fl, mid, tau, c.nsuper, rb);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
   const long long nrec = (long long)a.ictr[kIcRecs];
@@ -1010,14 +1023,7 @@ __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
       }
       a.out[a.rj[r]] = exposure_mean(acc, ns);
     } else {
-      const int k = a.ovlist[r - nrec];
-      const int j = a.klist[k], st = a.kset[k];
-      const SetConst& c = a.sets[st];
-      const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)st * a.n_times;
-      double tau;
-      gl::MidState mid;
-      const int fl = exposure_prep<R>(c, a.t[ti], &tau, &mid);
-      a.out[j] = (fl & kExpDead) ? 1.0 : exposure_local<R>(c, fl, mid, tau, c.nsuper, rb);
+      finish_overflow<R>(a, a.ovlist[r - nrec], rb);
     }
   }
 }
