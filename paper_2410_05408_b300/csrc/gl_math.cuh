@@ -1036,8 +1036,8 @@ GL_HD void whole_single_moments(const SetConst& c, R x0, R y0, R omr2, const Nod
 
 // ------------------------------------------------------------------ quartics
 // Division and cosine for the quartic solver.  FAST (FP32 on the GPU only): the
-// hardware's approximate divide and cosine, for estimates that an FP64 Newton
-// polish refines afterwards (crossing_roots); otherwise the correctly rounded
+// hardware's approximate divide and cosine, for estimates that Newton steps
+// refine afterwards (crossing_roots_f32); otherwise the correctly rounded
 // divide and the library cosine.
 template <typename T, bool FAST>
 GL_HD T q_div(T a, T b) {
@@ -1256,90 +1256,55 @@ GL_HD int frame_roots(const Frame<T>& f, T* tr) {
   return drop_pairs<T>(tr, nr, T(1024) * m_eps<T>());
 }
 
-// Crossings of the boundary with the limb, in FP64 (frame f; fr is the same
-// frame in precision R).  R = double: FP64 Ferrari.  R = float: FP32 Ferrari
-// estimates, each polished by FP64 Newton steps on the FP64 quartic; if a
-// polish does not converge, two roots merge or the count is odd, the FP64
-// Ferrari result is used instead.
-template <typename R>
-GL_HD int crossing_roots(const Frame<double>& f, const Frame<R>& fr, double* tr);
-
-template <>
-GL_HD int crossing_roots<double>(const Frame<double>& f, const Frame<double>&, double* tr) {
-  return frame_roots<double>(f, tr);
-}
-
-template <>
-GL_HD int crossing_roots<float>(const Frame<double>& f, const Frame<float>& fr, double* tr) {
-  if (!(fabsf(fr.q[4]) > 0.0f)) return frame_roots<double>(f, tr);
-  float inv = 1.0f / fr.q[4];
+// Crossings of the boundary with the limb for the FP32 quadrature, from the FP32
+// frame alone: Ferrari estimates (fast divide and cosine), then Newton steps on
+// the same FP32 quartic, all on the FP32 pipe.  FP32 is enough here: the
+// quadrature rounds every crossing to FP32 anyway, and each limb arc starts at
+// the radial projection of the ellipse point at the crossing, where the
+// Green's-theorem integrands of all three moments vanish (they are multiples of
+// x dy - y dx), so an error d in a crossing leaves only the sliver between the
+// two curves, O(d^2), in the moments.  Returns the number of roots (sorted, as
+// doubles), or -1 when the estimates cannot be trusted: an odd count, a root
+// whose Newton step has not fallen below 1e-4 (1 + |t|) within three steps (it
+// then sits on rounding noise: an ill-conditioned, near-tangent root), or two
+// roots within 1e-3 (1 + |t|) of each other (near tangency).  The caller then
+// solves the FP64 quartic.
+GL_HD int crossing_roots_f32(const Frame<float>& fr, double* tr) {
+  if (!(fabsf(fr.q[4]) > 0.0f)) return -1;
+  const float inv = 1.0f / fr.q[4];
   float xs[4];
-  // estimates only: every root is polished below in FP64 (fast divide and cosine)
-  int nr = quartic_real_roots<float, true>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv,
-                                           fr.q[0] * inv, xs);
-  bool ok = (nr % 2) == 0;
-  // Newton steps on the FP64 quartic with the derivative frozen at the FP32
-  // estimate and its reciprocal taken in FP32.  One step from an estimate within
-  // 1e-5 (1 + |t|) leaves an error below eps_r |s| + (P''/P') s^2 / 2 (eps_r the
-  // relative error of the FP32 derivative), far below the FP32 rounding that the
-  // quadrature applies to t next; a larger first step iterates to 1e-9 (1 + |t|).
-  // The step bounds are formed in FP32 and compared by bit patterns (on B300 every
-  // FP64 instruction, conversions included, holds the FP64 unit for its full issue
-  // time).  The roots take their steps side by side (unrolled over the at most
-  // four roots, each its own dependency chain).
-  double tt[4], rr[4], l1[4], l2[4];
-  bool conv[4];
+  const int nr = quartic_real_roots<float, true>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv,
+                                                 fr.q[0] * inv, xs);
+  if (nr & 1) return -1;
+  const float q0 = fr.q[0], q1 = fr.q[1], q2 = fr.q[2], q3 = fr.q[3], q4 = fr.q[4];
+  const float d3 = 4.0f * q4, d2 = 3.0f * q3, d1 = 2.0f * q2;
+  bool ok = true;
+  // the roots take their steps side by side (each its own dependency chain)
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    tt[i] = rr[i] = l1[i] = l2[i] = 0.0;
-    conv[i] = i >= nr;
-    if (i < nr) {   // (skipped by a warp none of whose items has this many roots)
-      // The frozen derivative only scales the step (the fixed point t - P(t) r is
-      // P(t) = 0 for any r != 0), so it comes from the FP32 frame; the estimate,
-      // the scale and the bounds reach FP64 by integer conversion.  The FP64 unit
-      // sees only the residual of the FP64 quartic and the update.
-      const float xi = xs[i];
-      const float fpf = ((4.0f * fr.q[4] * xi + 3.0f * fr.q[3]) * xi + 2.0f * fr.q[2]) * xi +
-                        fr.q[1];
-      rr[i] = f32_to_f64_int(rcp_<float>(fpf));
-      const float at = 1.0f + fabsf(xi);
-      l1[i] = f32_to_f64_int(1e-5f * at);
-      l2[i] = f32_to_f64_int(1e-9f * at);
-      tt[i] = f32_to_f64_int(xi);
-    }
-  }
+    if (i < nr) {
+      float t = xs[i];
+      bool settled = false;
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    bool all = true;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) all = all && conv[i];
-    if (all) break;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (conv[i]) continue;
-      const double t = tt[i];
-      const double fv = (((f.q[4] * t + f.q[3]) * t + f.q[2]) * t + f.q[1]) * t + f.q[0];
-      const double step = fv * rr[i];
-      if (!finite_bits(step)) {
-        conv[i] = true;   // gives up: this root cannot be polished (fallback below)
-        ok = false;
-        continue;
+      for (int it = 0; it < 3; ++it) {
+        if (!settled) {
+          const float p = (((q4 * t + q3) * t + q2) * t + q1) * t + q0;
+          const float dp = ((d3 * t + d2) * t + d1) * t + q1;
+          const float step = q_div<float, true>(p, dp);
+          if (!(fabsf(step) <= 1e-2f * (1.0f + fabsf(t)))) break;   // (NaN too)
+          t -= step;
+          settled = fabsf(step) <= 1e-4f * (1.0f + fabsf(t));
+        }
       }
-      tt[i] = t - step;
-      if (abs_le(step, it == 0 ? l1[i] : l2[i])) conv[i] = true;
-      else if (it == 3) ok = false;   // not converged in four steps
+      ok = ok && settled;
+      xs[i] = t;
     }
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (i < nr) tr[i] = tt[i];
-  if (ok) {
-    sort_small(tr, nr);
-    for (int i = 0; i + 1 < nr; ++i)
-      // roots closer than 1e-9 (1 + |t|) merge (bound formed in FP32)
-      if (abs_le(tr[i + 1] - tr[i], (double)(1e-9f * (1.0f + fabsf((float)tr[i]))))) ok = false;
-  }
-  if (!ok) return frame_roots<double>(f, tr);
+  if (!ok) return -1;
+  sort_small(xs, nr);
+  for (int i = 0; i + 1 < nr; ++i)
+    if (!(xs[i + 1] - xs[i] > 1e-3f * (1.0f + fabsf(xs[i])))) return -1;
+  for (int i = 0; i < nr; ++i) tr[i] = f32_to_f64_int(xs[i]);
   return nr;
 }
 
@@ -1602,13 +1567,26 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
     nmax = inner_maxima<R>(tg, cmx, smx);
   }
   if (cls == kPartial) {
-    const double xd = to_f64(x0), yd = to_f64(y0);
-    Trig2<double> tgd = limb_poly<double>(c, xd, yd, fma(-yd, yd, fma(-xd, xd, 1.0)));
-    int kb = frame_choice<R>(tg);
-    Frame<double> fr = make_frame_k<double>(tgd, kb);
-    Frame<R> frr = make_frame_k<R>(tg, kb);
+    const int kb = frame_choice<R>(tg);
+    const Frame<R> frr = make_frame_k<R>(tg, kb);
     double tb[8];
-    int nr = crossing_roots<R>(fr, frr, tb);
+    // FP32 quadrature: the crossings from the FP32 frame (crossing_roots_f32);
+    // the FP64 frame and its roots only where those cannot be trusted, and
+    // always for the FP64 quadrature
+    Frame<double> fr;
+    bool have64 = false;
+    int nr = -1;
+    if constexpr (sizeof(R) == 4) nr = crossing_roots_f32(frr, tb);
+    if (nr < 0) {
+      const double xd = to_f64(x0), yd = to_f64(y0);
+      const Trig2<double> tgd = limb_poly<double>(c, xd, yd, fma(-yd, yd, fma(-xd, xd, 1.0)));
+      fr = make_frame_k<double>(tgd, kb);
+      have64 = true;
+      nr = frame_roots<double>(fr, tb);
+    }
+    // sign of g at the frame's t = infinity (q4: the largest |g| of eight
+    // samples, so its sign is the same in either precision)
+    const bool q4_neg = have64 ? neg_bits(fr.q[4]) : neg_bits(to_f64(frr.q[4]));
     // The arcs of the boundary inside the disk are gathered first and integrated
     // by one loop afterwards, so that a warp runs the quadrature once per arc
     // count rather than once per breakpoint index.
@@ -1616,7 +1594,7 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
     int na = 0;
     CSum<R> sflat, slin, squad;
     if (nr == 0) {
-      if (!neg_bits(fr.q[4])) {
+      if (!q4_neg) {
         // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
         R v1 = -g.x0 / g.dx, v2 = (-g.y0 - g.dy1 * v1) / g.dy2;
         if (v1 * v1 + v2 * v2 < R(1)) {
@@ -1637,8 +1615,8 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
       // g changes sign at each crossing, so the others alternate from there.  An
       // odd count (possible only from the FP64 fallback in degenerate cases)
       // falls back to FP64 tests of g at the arc midpoints.
-      const bool wrap_in = neg_bits(fr.q[4]);
-      const bool parity = (nr & 1) == 0;
+      const bool wrap_in = q4_neg;
+      const bool parity = (nr & 1) == 0 || !have64;   // (FP32 roots come in pairs)
       // breakpoints: the crossings (kind 1) and the inner maxima (kind 0) that
       // lie on an inside arc.  A maximum that rounding placed on an outside arc
       // (between two close crossings) would split that arc and lose the limb arc
@@ -1657,7 +1635,7 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
                                       : (frame_poly<double>(fr, tv) < 0.0);
         if (!on_inside) continue;
         int j = nb - 1;
-        while (j >= 0 && tb[j] > tv) {
+        while (j >= 0 && dkey(tb[j]) > kv) {
           tb[j + 1] = tb[j];
           kind[j + 1] = kind[j];
           --j;

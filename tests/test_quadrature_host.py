@@ -6,7 +6,10 @@
 * crossing-arc classification by parity: the inside/outside flags agree with the
   sign of g at each arc's midpoint, evaluated directly from the ellipse;
 * the crossing moments with gathered arcs equal the whole-ellipse moments when the
-  ellipse lies inside the disk and approach them as it reaches the limb.
+  ellipse lies inside the disk and approach them as it reaches the limb;
+* the FP32 crossings (crossing_roots_f32) against the roots of the FP64 quartic of
+  the same centre: the same count, roots within 1e-4 (1 + |t|), the FP64 fallback
+  rare on random limb geometries and taken at near-tangency.
 """
 import os
 import subprocess
@@ -74,7 +77,7 @@ int main() {
     int kb = frame_choice<double>(t);
     Frame<double> fr = make_frame_k<double>(t, kb);
     double tr[8];
-    int nr = crossing_roots<double>(fr, fr, tr);
+    int nr = frame_roots<double>(fr, tr);
     if (nr < 2 || (nr & 1)) continue;
     bool wrap_in = fr.q[4] < 0.0;
     for (int i = 0; i + 1 < nr; ++i) {
@@ -90,6 +93,87 @@ int main() {
   printf("%ld %ld %ld %.3e %ld %ld\n", n_one, bad_count, n_two_flag, worst_angle, arcs, mismatch);
 }
 '''
+
+
+SRC_F32 = r'''
+#include <cstdio>
+#include <cmath>
+#include <random>
+#include "gl_math.cuh"
+using namespace gl;
+// FP32 and FP64 frames of the same (FP32) centre, as the FP32 quadrature forms them
+static void frames(const SetConst& c, float x0, float y0, Frame<float>* ff, Frame<double>* fd) {
+  const double xd = x0, yd = y0, omr2 = fma(-yd, yd, fma(-xd, xd, 1.0));
+  const Trig2<float> tf = limb_poly<float>(c, x0, y0, (float)omr2);
+  const int kb = frame_choice<float>(tf);
+  *ff = make_frame_k<float>(tf, kb);
+  *fd = make_frame_k<double>(limb_poly<double>(c, xd, yd, omr2), kb);
+}
+int main() {
+  std::mt19937_64 gen(21);
+  std::uniform_real_distribution<double> U(0, 1);
+  long n = 0, fallback = 0, count_mismatch = 0, with_roots = 0;
+  double worst = 0;
+  for (int it = 0; it < 200000; ++it) {
+    double k = 0.01 + 0.3 * U(gen), f = 0.95 * U(gen), eta = acos(U(gen)), xi = M_PI * U(gen);
+    SetConst c;
+    set_setup(0, 10, 20, 0.1, 0, M_PI / 2, k, f, eta, xi, 0.4, 0.25, 0.01, 1, &c);
+    double rho = 1 - c.req + 2 * c.req * U(gen), ph = 2 * M_PI * U(gen);
+    Frame<float> ff;
+    Frame<double> fd;
+    frames(c, (float)(rho * cos(ph)), (float)(rho * sin(ph)), &ff, &fd);
+    double t32[8], t64[8];
+    const int n64 = frame_roots<double>(fd, t64), n32 = crossing_roots_f32(ff, t32);
+    ++n;
+    if (n32 < 0) { ++fallback; continue; }
+    if (n32 != n64) { ++count_mismatch; continue; }
+    with_roots += n32 > 0;
+    for (int i = 0; i < n32; ++i)
+      worst = fmax(worst, fabs(t32[i] - t64[i]) / (1 + fabs(t64[i])));
+  }
+  // near-tangency: a circle (f = 0) whose edge passes about 1e-9 beyond the limb
+  // (the FP32 centre moves it by up to ~1e-7) crosses it twice, very close
+  // together: mostly the FP64 fallback or no crossing; a pair that does stand
+  // must be the FP64 quartic's pair for the same centre
+  long tangent_total = 0, tangent_fb = 0, tangent_zero = 0, tangent_bad = 0;
+  for (int it = 0; it < 2000; ++it) {
+    double k = 0.05 + 0.2 * U(gen), ph = 2 * M_PI * U(gen);
+    SetConst c;
+    set_setup(0, 10, 20, 0.1, 0, M_PI / 2, k, 0.0, 0.3, 0.2, 0.4, 0.25, 0.01, 1, &c);
+    const double rho = 1 - c.req + 1e-9;
+    Frame<float> ff;
+    Frame<double> fd;
+    frames(c, (float)(rho * cos(ph)), (float)(rho * sin(ph)), &ff, &fd);
+    double t32[8], t64[8];
+    const int n32 = crossing_roots_f32(ff, t32), n64 = frame_roots<double>(fd, t64);
+    ++tangent_total;
+    tangent_fb += n32 < 0;
+    tangent_zero += n32 == 0;
+    if (n32 > 0) {
+      bool same = n32 == n64;
+      for (int i = 0; same && i < n32; ++i)
+        same = fabs(t32[i] - t64[i]) <= 1e-4 * (1 + fabs(t64[i]));
+      tangent_bad += !same;
+    }
+  }
+  printf("%ld %ld %ld %ld %.3e %ld %ld %ld %ld\n", n, fallback, count_mismatch, with_roots, worst,
+         tangent_total, tangent_fb, tangent_zero, tangent_bad);
+}
+'''
+
+
+def _build_run(code):
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.cpp")
+        exe = os.path.join(d, "t")
+        with open(src, "w") as fh:
+            fh.write(code)
+        inc = os.path.join(ROOT, "paper_2410_05408_b300", "csrc")
+        r = subprocess.run(["g++", "-O2", "-std=c++17", "-I", inc, src, "-o", exe],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail(r.stderr)
+        return subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
 
 
 def _run():
@@ -115,3 +199,17 @@ def test_single_maximum_hint_and_parity_classification():
     assert float(worst_angle) < 2e-3
     # crossing parity reproduces the direct sign of g on every arc
     assert arcs > 10000 and mismatch == 0
+
+
+def test_fp32_crossings_against_the_fp64_quartic():
+    n, fb, mis, with_roots, worst, t_total, t_fb, t_zero, t_bad = _build_run(SRC_F32)
+    n, fb, mis, with_roots = int(n), int(fb), int(mis), int(with_roots)
+    t_total, t_fb, t_zero = int(t_total), int(t_fb), int(t_zero)
+    # random limb geometries: the FP32 roots stand (fallback rare), with the FP64
+    # count, within 1e-4 (1 + |t|) of the FP64 roots (the Newton acceptance bound)
+    assert n == 200000 and fb < n // 1000 and mis == 0 and with_roots > n // 2
+    assert float(worst) < 1e-4
+    # at near-tangency: mostly the FP64 fallback or no crossing (the sliver beyond
+    # the limb is then below 1e-10 of the disk); any pair that stands is exact
+    assert t_total == 2000 and t_fb + t_zero > 0.99 * t_total and t_fb > 0
+    assert int(t_bad) == 0
