@@ -97,6 +97,16 @@ __device__ __forceinline__ const NodeRule<float>& set_rule<float>(const SetConst
 }
 
 // ------------------------------------------------------------------ kernels
+// Programmatic dependent launch: the item pipeline's kernels after the setup
+// kernel are launched with programmatic stream serialisation, so a kernel's CTAs
+// are dispatched as its predecessor's CTAs exit rather than after the
+// predecessor's completion has been signalled, and each waits in pdl_wait, before
+// it touches memory, until the predecessor has completed and its writes are
+// visible (a no-op for a kernel launched without the attribute).  No kernel
+// triggers its successor early: successors resident beside a running kernel
+// measured slower than the saved launch latency.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 struct ParamPtrs {
   const double *t0, *period, *a_rs, *b, *ecc, *omega, *k, *f, *eta, *xi, *u1, *u2;
   const double *g, *zeta;   // optional triaxial shape (NULL: oblate)
@@ -678,6 +688,7 @@ __device__ __forceinline__ void win_one(const LcArgs& a, double* __restrict__ ou
 template <int U>
 __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
   __shared__ int s_first;
+  pdl_wait();
   const int64_t per = (((a.n_total + gridDim.x - 1) / gridDim.x) + 31) & ~(int64_t)31;
   const int64_t lo = (int64_t)blockIdx.x * per;
   const int64_t hi = min(a.n_total, lo + per);
@@ -774,6 +785,7 @@ __global__ void __launch_bounds__(NT) gl_expgeo_kernel(LcArgs a) {
   __shared__ int s_off[NE], s_st[NE], s_fl[NE], s_ns[NE];
   __shared__ double s_tau[NE];
   __shared__ gl::MidState s_mid[NE];
+  pdl_wait();
   const int tid = threadIdx.x;
   const long long nk = (long long)a.ictr[kIcKept];
   R* ipos = (R*)a.ipos;
@@ -916,6 +928,7 @@ __device__ __forceinline__ unsigned warpid_() {
 // autotuner chooses between the two.
 template <typename R, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
+  pdl_wait();
   const int rb = rule_base(a.rule_idx);
   const long long np = (long long)a.ictr[kIcPart], nf = (long long)a.ictr[kIcFull];
   const long long nh = (long long)a.ictr[kIcHeavy];
@@ -1003,6 +1016,7 @@ __device__ __noinline__ void finish_overflow(const LcArgs& a, int k, int rb) {
 
 template <typename R>
 __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
+  pdl_wait();
   const long long nrec = (long long)a.ictr[kIcRecs];
   const long long nover = (long long)a.ictr[kIcOver];
   const R* idef = (const R*)a.idef;
@@ -2006,6 +2020,27 @@ size_t item_workspace_bytes(int64_t cap, int64_t n_total) {
   return (size_t)cap * kItemBytes + (size_t)n_total * 3 * sizeof(int) + 20 * 256;
 }
 
+// Launch of an item-pipeline kernel that depends on the kernel before it in the
+// stream: with programmatic stream serialisation (its CTAs are dispatched as that
+// kernel's CTAs exit, and wait in pdl_wait), unless profiling puts event records
+// between the kernels.
+void launch_dependent(gl_context* ctx, void (*k)(LcArgs), int grid, int block, cudaStream_t st,
+                      const LcArgs& args) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  if (!ctx->profiling && !ctx->gprof) {
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, k, args);
+}
+
 // The item pipeline: window tests, kept exposures, quadrature, exposure sums.
 template <typename R>
 int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
@@ -2033,27 +2068,25 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
   if (wb > (int64_t)ctx->sms * ctx->wocc) wb = (int64_t)ctx->sms * ctx->wocc;
   if (wb < 1) wb = 1;
   long pe = prof_begin(ctx, GL_KERNEL_WINDOW, st);
-  gl_win_kernel<kWinU><<<(int)wb, 256, 0, st>>>(args);
+  launch_dependent(ctx, gl_win_kernel<kWinU>, (int)wb, 256, st, args);
   prof_end(ctx, GL_KERNEL_WINDOW, pe, st);
   gmark(ctx, kMarkWindow, st);
   pe = prof_begin(ctx, GL_KERNEL_CURVE, st);
   if (gvar)
-    gl_expgeo_kernel<R, 64><<<ctx->sms * eocc, 64, 0, st>>>(args);
+    launch_dependent(ctx, gl_expgeo_kernel<R, 64>, ctx->sms * eocc, 64, st, args);
   else
-    gl_expgeo_kernel<R, 256><<<ctx->sms * eocc, 256, 0, st>>>(args);
+    launch_dependent(ctx, gl_expgeo_kernel<R, 256>, ctx->sms * eocc, 256, st, args);
   prof_end(ctx, GL_KERNEL_CURVE, pe, st);
   gmark(ctx, kMarkExposures, st);
   ctx->launches += 2;
   GL_CUDA(ctx, cudaGetLastError());
   pe = prof_begin(ctx, GL_KERNEL_QUAD, st);
   long pq = prof_begin(ctx, GL_KERNEL_ITEMS, st);
-  if (qvar)
-    gl_items_quad_kernel<R, 128, 8><<<ctx->sms * qocc, 128, 0, st>>>(args);
-  else
-    gl_items_quad_kernel<R, 128, 4><<<ctx->sms * qocc, 128, 0, st>>>(args);
+  launch_dependent(ctx, qvar ? gl_items_quad_kernel<R, 128, 8> : gl_items_quad_kernel<R, 128, 4>,
+                   ctx->sms * qocc, 128, st, args);
   prof_end(ctx, GL_KERNEL_ITEMS, pq, st);
   gmark(ctx, kMarkItems, st);
-  gl_items_sum_kernel<R><<<ctx->sms * 2, 256, 0, st>>>(args);
+  launch_dependent(ctx, gl_items_sum_kernel<R>, ctx->sms * 2, 256, st, args);
   prof_end(ctx, GL_KERNEL_QUAD, pe, st);
   gmark(ctx, kMarkSums, st);
   ctx->launches += 2;
