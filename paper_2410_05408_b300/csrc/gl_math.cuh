@@ -24,8 +24,10 @@
 
 #if defined(__CUDACC__)
 #define GL_HD __host__ __device__ __forceinline__
+#define GL_HD_NOINLINE __host__ __device__ __noinline__
 #else
 #define GL_HD inline
+#define GL_HD_NOINLINE inline
 #endif
 
 namespace gl {
@@ -1257,54 +1259,114 @@ GL_HD int frame_roots(const Frame<T>& f, T* tr) {
 }
 
 // Crossings of the boundary with the limb for the FP32 quadrature, from the FP32
-// frame alone: Ferrari estimates (fast divide and cosine), then Newton steps on
-// the same FP32 quartic, all on the FP32 pipe.  FP32 is enough here: the
-// quadrature rounds every crossing to FP32 anyway, and each limb arc starts at
-// the radial projection of the ellipse point at the crossing, where the
+// frame alone: Ferrari estimates (the steps of quartic_real_roots, fast divide and
+// cosine), then Newton steps on the same FP32 quartic, all on the FP32 pipe and
+// in registers (four candidate slots, sorted by a fixed network).  FP32 is enough
+// here: the quadrature rounds every crossing to FP32 anyway, and each limb arc
+// starts at the radial projection of the ellipse point at the crossing, where the
 // Green's-theorem integrands of all three moments vanish (they are multiples of
 // x dy - y dx), so an error d in a crossing leaves only the sliver between the
-// two curves, O(d^2), in the moments.  Returns the number of roots (sorted, as
-// doubles), or -1 when the estimates cannot be trusted: an odd count, a root
-// whose Newton step has not fallen below 1e-4 (1 + |t|) within three steps (it
-// then sits on rounding noise: an ill-conditioned, near-tangent root), or two
-// roots within 1e-3 (1 + |t|) of each other (near tangency).  The caller then
-// solves the FP64 quartic.
-GL_HD int crossing_roots_f32(const Frame<float>& fr, double* tr) {
+// two curves, O(d^2), in the moments.  Returns the number of roots (r[0..n),
+// ascending), or -1 when the estimates cannot be trusted: a root whose Newton
+// step has not fallen below 1e-4 (1 + |t|) within three steps (it then sits on
+// rounding noise: an ill-conditioned, near-tangent root), or two roots within
+// 1e-3 (1 + |t|) of each other (near tangency).  The caller then solves the FP64
+// quartic.
+GL_HD void quad_roots_slot(float p, float q, float* r0, float* r1, bool* ok) {
+  // quad_roots<float, true> into two fixed slots
+  const float disc = p * p - 4.0f * q;
+  *ok = !(disc < 0.0f);
+  const float sq = sqrtf(disc);
+  const float y1 = -0.5f * (p + copysignf(sq, p));
+  *r0 = y1;
+  *r1 = (y1 != 0.0f) ? q_div<float, true>(q, y1) : 0.0f;
+}
+
+GL_HD int crossing_roots_f32(const Frame<float>& fr, float r[4]) {
   if (!(fabsf(fr.q[4]) > 0.0f)) return -1;
   const float inv = 1.0f / fr.q[4];
-  float xs[4];
-  const int nr = quartic_real_roots<float, true>(fr.q[3] * inv, fr.q[2] * inv, fr.q[1] * inv,
-                                                 fr.q[0] * inv, xs);
-  if (nr & 1) return -1;
+  const float a = fr.q[3] * inv, b = fr.q[2] * inv, c = fr.q[1] * inv, d = fr.q[0] * inv;
+  const float a2 = a * a;
+  const float p = b - 0.375f * a2;
+  const float q = c - 0.5f * a * b + 0.125f * a2 * a;
+  const float rq = d - 0.25f * a * c + 0.0625f * a2 * b - 0.01171875f * a2 * a2;
+  float y[4];
+  bool v[4];
+  // resolvent: z^3 + 2p z^2 + (p^2 - 4r) z - q^2 = 0, z = s^2 >= 0
+  const float z = cubic_largest_root<float, true>(2.0f * p, p * p - 4.0f * rq, -q * q);
+  if (z > 64.0f * m_eps<float>() * (fabsf(p) + sqrtf(fabsf(rq)) + 1e-30f)) {
+    const float sz = sqrtf(z);
+    const float qs = q_div<float, true>(q, sz);
+    quad_roots_slot(sz, 0.5f * (p + z - qs), &y[0], &y[1], &v[0]);
+    quad_roots_slot(-sz, 0.5f * (p + z + qs), &y[2], &y[3], &v[2]);
+  } else {
+    // biquadratic: y^2 = w, w^2 + p w + r = 0
+    float w0, w1;
+    bool vw;
+    quad_roots_slot(p, rq, &w0, &w1, &vw);
+    v[0] = vw && w0 >= 0.0f;
+    v[2] = vw && w1 >= 0.0f;
+    y[0] = v[0] ? sqrtf(w0) : 0.0f;
+    y[2] = v[2] ? sqrtf(w1) : 0.0f;
+    y[1] = -y[0];
+    y[3] = -y[2];
+  }
+  v[1] = v[0];
+  v[3] = v[2];
   const float q0 = fr.q[0], q1 = fr.q[1], q2 = fr.q[2], q3 = fr.q[3], q4 = fr.q[4];
   const float d3 = 4.0f * q4, d2 = 3.0f * q3, d1 = 2.0f * q2;
   bool ok = true;
-  // the roots take their steps side by side (each its own dependency chain)
+  int nr = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (i < nr) {
-      float t = xs[i];
+    if (v[i]) {
+      ++nr;
+      // Newton on the monic quartic (quartic_real_roots' polish)
+      float t = y[i] - 0.25f * a;
+      for (int it = 0; it < 3; ++it) {
+        const float f = (((t + a) * t + b) * t + c) * t + d;
+        const float fp = ((4.0f * t + 3.0f * a) * t + 2.0f * b) * t + c;
+        if (fp == 0.0f) break;
+        const float step = q_div<float, true>(f, fp);
+        t -= step;
+        if (fabsf(step) <= m_eps<float>() * (1.0f + fabsf(t))) break;
+      }
+      // settle on the frame's quartic
       bool settled = false;
 #pragma unroll
       for (int it = 0; it < 3; ++it) {
         if (!settled) {
-          const float p = (((q4 * t + q3) * t + q2) * t + q1) * t + q0;
+          const float pv = (((q4 * t + q3) * t + q2) * t + q1) * t + q0;
           const float dp = ((d3 * t + d2) * t + d1) * t + q1;
-          const float step = q_div<float, true>(p, dp);
+          const float step = q_div<float, true>(pv, dp);
           if (!(fabsf(step) <= 1e-2f * (1.0f + fabsf(t)))) break;   // (NaN too)
           t -= step;
           settled = fabsf(step) <= 1e-4f * (1.0f + fabsf(t));
         }
       }
       ok = ok && settled;
-      xs[i] = t;
+      y[i] = t;
+    } else {
+      y[i] = INFINITY;   // empty slots sort last
     }
   }
   if (!ok) return -1;
-  sort_small(xs, nr);
-  for (int i = 0; i + 1 < nr; ++i)
-    if (!(xs[i + 1] - xs[i] > 1e-3f * (1.0f + fabsf(xs[i])))) return -1;
-  for (int i = 0; i < nr; ++i) tr[i] = f32_to_f64_int(xs[i]);
+  // sorting network on four slots
+  auto cx = [&](int i, int j) {
+    const float lo = fminf(y[i], y[j]), hi = fmaxf(y[i], y[j]);
+    y[i] = lo;
+    y[j] = hi;
+  };
+  cx(0, 1);
+  cx(2, 3);
+  cx(0, 2);
+  cx(1, 3);
+  cx(1, 2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (i + 1 < nr && !(y[i + 1] - y[i] > 1e-3f * (1.0f + fabsf(y[i])))) return -1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r[i] = y[i];
   return nr;
 }
 
@@ -1536,6 +1598,228 @@ GL_HD void whole_single_moments(const SetConst& c, R x0, R y0, R omr2, const Nod
   I[2] = area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) * R(0.25));
 }
 
+// Moments of a crossing-class item, every case (Sec. 2): the crossings of the
+// boundary with the limb (the FP32 ones, r0.. sorted, the first nr32, when nr32 >= 0;
+// else the roots of the FP64 quartic), the inner maxima of g that lie on an
+// inside arc as extra breakpoints, the arcs classified by crossing parity (FP64
+// tests of g at the arc midpoints for an odd count), the boundary arcs inside
+// the disk and the limb arcs inside the ellipse.  Compiled apart (not inlined):
+// the FP32 quadrature's common cases take the short path of occulted_r.
+template <typename R>
+GL_HD_NOINLINE void partial_general(const SetConst& c, R x0, R y0, const Geo<R>& g,
+                                    const Trig2<R>& tg, const Frame<R>& frr, int kb, int nmax,
+                                    const R* cmx, const R* smx, R area, const NodeRule<R>& rule,
+                                    int nr32, float r0, float r1, float r2, float r3, R I[3]) {
+  I[0] = I[1] = I[2] = R(0);
+  const float r32[4] = {r0, r1, r2, r3};
+  double tb[8];
+  // the FP32 crossings when they stand (nr32 >= 0), else the FP64 frame and
+  // its roots (always for the FP64 quadrature)
+  Frame<double> fr;
+  bool have64 = false;
+  int nr = nr32;
+  for (int i = 0; i < 4; ++i)
+    if (i < nr) tb[i] = f32_to_f64_int(r32[i]);
+  if (nr < 0) {
+    const double xd = to_f64(x0), yd = to_f64(y0);
+    const Trig2<double> tgd = limb_poly<double>(c, xd, yd, fma(-yd, yd, fma(-xd, xd, 1.0)));
+    fr = make_frame_k<double>(tgd, kb);
+    have64 = true;
+    nr = frame_roots<double>(fr, tb);
+  }
+  // sign of g at the frame's t = infinity (q4: the largest |g| of eight
+  // samples, so its sign is the same in either precision)
+  const bool q4_neg = have64 ? neg_bits(fr.q[4]) : neg_bits(to_f64(frr.q[4]));
+  // The arcs of the boundary inside the disk are gathered first and integrated
+  // by one loop afterwards, so that a warp runs the quadrature once per arc
+  // count rather than once per breakpoint index.
+  R acm[4], asn[4], ah[4];
+  int na = 0;
+  CSum<R> sflat, slin, squad;
+  if (nr == 0) {
+    if (!q4_neg) {
+      // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
+      R v1 = -g.x0 / g.dx, v2 = (-g.y0 - g.dy1 * v1) / g.dy2;
+      if (v1 * v1 + v2 * v2 < R(1)) {
+        I[0] = R(kPi);
+        I[1] = R(2.0 * kPi / 3.0);
+        I[2] = R(0.5 * kPi);
+      }
+      return;
+    }
+    // boundary entirely inside the disk: the whole turn, split at the inner
+    // maxima as in the whole-ellipse case below
+    sflat.add(area);
+    squad.add(area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4)));
+    whole_arcs<R>(g, tg, nmax, cmx, smx, acm, asn, ah, &na);
+  } else {
+    // g at the frame's t = infinity (q4, the largest |g| of eight samples, so
+    // its sign is safe) says whether the arc through it lies inside the disk;
+    // g changes sign at each crossing, so the others alternate from there.  An
+    // odd count (possible only from the FP64 fallback in degenerate cases)
+    // falls back to FP64 tests of g at the arc midpoints.
+    const bool wrap_in = q4_neg;
+    const bool parity = (nr & 1) == 0 || !have64;   // (FP32 roots come in pairs)
+    // breakpoints: the crossings (kind 1) and the inner maxima (kind 0) that
+    // lie on an inside arc.  A maximum that rounding placed on an outside arc
+    // (between two close crossings) would split that arc and lose the limb arc
+    // joining the two crossings, so it is dropped.
+    int kind[8];
+    for (int i = 0; i < nr; ++i) kind[i] = 1;
+    int nb = nr;
+    for (int i = 0; i < nmax; ++i) {
+      R tvr = frame_t<R>(frr, cmx[i], smx[i]);
+      if (!m_finite(tvr)) continue;
+      double tv = to_f64(tvr);
+      int below = 0;
+      const long long kv = dkey(tv);
+      for (int k = 0; k < nb; ++k) below += (kind[k] && dkey(tb[k]) < kv) ? 1 : 0;
+      const bool on_inside = parity ? (wrap_in != ((below & 1) != 0))
+                                    : (frame_poly<double>(fr, tv) < 0.0);
+      if (!on_inside) continue;
+      int j = nb - 1;
+      while (j >= 0 && dkey(tb[j]) > kv) {
+        tb[j + 1] = tb[j];
+        kind[j + 1] = kind[j];
+        --j;
+      }
+      tb[j + 1] = tv;
+      kind[j + 1] = 0;
+      ++nb;
+    }
+    R cth[8], sth[8], px[8], py[8];
+    R tr_[8];
+    for (int i = 0; i < nb; ++i) {
+      tr_[i] = from_f64<R>(tb[i]);
+      frame_angle<R>(frr, tr_[i], &cth[i], &sth[i]);
+      R qx = g.x0 + g.dx * cth[i];
+      R qy = g.y0 + g.dy1 * cth[i] + g.dy2 * sth[i];
+      R nrm = rsqrt_<R>(qx * qx + qy * qy);
+      px[i] = qx * nrm;
+      py[i] = qy * nrm;
+    }
+    QuadPoly<R> qp = quad_poly<R>(g.x0, g.y0, g.dx, g.dy1, g.dy2);
+    int ncross = 0;
+    for (int i = 0; i < nb; ++i) {
+      int ip = (i + 1 == nb) ? 0 : i + 1;
+      bool wrap = (i + 1 == nb);
+      ncross += kind[i];
+      R h, cm, sm;
+      frame_arc<R>(tr_[ip] - tr_[i], R(1) + tr_[i] * tr_[ip], wrap, cth[i], sth[i], &h, &cm,
+                   &sm);
+      if (nb == 1) {   // a lone breakpoint: the arc is the full turn
+        h = R(kPi);
+        cm = -cth[i];
+        sm = -sth[i];
+      }
+      bool inside;
+      if (wrap) inside = wrap_in;
+      else if (parity) inside = wrap_in != ((ncross & 1) != 0);
+      else inside = frame_poly<double>(fr, 0.5 * (tb[i] + tb[ip])) < 0.0;
+      if (inside) {
+        if (na < 4) {
+          acm[na] = cm;
+          asn[na] = sm;
+          ah[na] = h;
+          ++na;
+        }
+        R ca = cth[i], sa = sth[i], cb = cth[ip], sb = sth[ip];
+        R dth = R(2) * h;
+        sflat.add(R(0.5) * (g.W0 * dth + g.Wc * (sb - sa) - g.Ws * (cb - ca)));
+        squad.add(qp.K * dth + (quad_poly_trig<R>(qp, cb, sb) - quad_poly_trig<R>(qp, ca, sa)));
+      } else if (kind[i] && kind[ip]) {
+        // the limb arc between the same two crossings lies inside the ellipse
+        R cr = px[i] * py[ip] - py[i] * px[ip], dt = px[i] * px[ip] + py[i] * py[ip];
+        R dl = m_atan2(cr, dt);
+        if (dl < R(0)) dl += R(2 * kPi);
+        R s4a = R(4) * px[i] * py[i] * (px[i] * px[i] - py[i] * py[i]);
+        R s4b = R(4) * px[ip] * py[ip] * (px[ip] * px[ip] - py[ip] * py[ip]);
+        sflat.add(R(0.5) * dl);
+        slin.add(dl * R(1.0 / 3.0));
+        squad.add(R(0.25) * dl - (s4b - s4a) * R(1.0 / 48.0));
+      }
+    }
+  }
+  for (int k = 0; k < na; ++k) slin.add(lin_arc<R>(g, acm[k], asn[k], ah[k], rule));
+  I[0] = sflat.value();
+  I[1] = slin.value();
+  I[2] = squad.value();
+}
+
+// The common cases of a crossing-class item in the FP32 quadrature, where g has a
+// single maximum: no crossing (the boundary wholly outside the disk, or wholly
+// inside it: the whole turn centred opposite the maximum of g nearest the limb),
+// or two crossings t0 < t1 (one boundary arc inside the disk, the limb arc
+// between the crossings inside the ellipse).  The operations and their order are
+// partial_general's for these cases, so both give the same bits.
+template <typename R>
+GL_HD void partial_short(const Geo<R>& g, const Trig2<R>& tg, const Frame<R>& frr, R x0, R y0,
+                         R area, const NodeRule<R>& rule, int nr, R t0, R t1, bool q4_neg,
+                         R I[3]) {
+  CSum<R> sflat, slin, squad;
+  R h, cm, sm;
+  if (nr == 0) {
+    if (!q4_neg) {
+      // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
+      R v1 = -g.x0 / g.dx, v2 = (-g.y0 - g.dy1 * v1) / g.dy2;
+      const bool cover = v1 * v1 + v2 * v2 < R(1);
+      I[0] = cover ? R(kPi) : R(0);
+      I[1] = cover ? R(2.0 * kPi / 3.0) : R(0);
+      I[2] = cover ? R(0.5 * kPi) : R(0);
+      return;
+    }
+    sflat.add(area);
+    squad.add(area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4)));
+    R cs[1] = {R(0)}, ss[1] = {R(0)};
+    nearest_limb_center<R>(g, tg, 0, cs, ss);
+    cm = -cs[0];
+    sm = -ss[0];
+    h = R(kPi);
+  } else {
+    R c0, s0, c1, s1;
+    frame_angle<R>(frr, t0, &c0, &s0);
+    frame_angle<R>(frr, t1, &c1, &s1);
+    // the crossings projected radially onto the limb
+    const R qx0 = g.x0 + g.dx * c0, qy0 = g.y0 + g.dy1 * c0 + g.dy2 * s0;
+    const R n0 = rsqrt_<R>(qx0 * qx0 + qy0 * qy0);
+    const R px0 = qx0 * n0, py0 = qy0 * n0;
+    const R qx1 = g.x0 + g.dx * c1, qy1 = g.y0 + g.dy1 * c1 + g.dy2 * s1;
+    const R n1 = rsqrt_<R>(qx1 * qx1 + qy1 * qy1);
+    const R px1 = qx1 * n1, py1 = qy1 * n1;
+    const QuadPoly<R> qp = quad_poly<R>(g.x0, g.y0, g.dx, g.dy1, g.dy2);
+    // boundary arc ta -> tb inside the disk
+    auto ellipse = [&](R ta, R tb, bool wrap, R ca, R sa, R cb, R sb) {
+      frame_arc<R>(tb - ta, R(1) + ta * tb, wrap, ca, sa, &h, &cm, &sm);
+      const R dth = R(2) * h;
+      sflat.add(R(0.5) * (g.W0 * dth + g.Wc * (sb - sa) - g.Ws * (cb - ca)));
+      squad.add(qp.K * dth + (quad_poly_trig<R>(qp, cb, sb) - quad_poly_trig<R>(qp, ca, sa)));
+    };
+    // limb arc a -> b inside the ellipse
+    auto limb = [&](R pxa, R pya, R pxb, R pyb) {
+      const R cr = pxa * pyb - pya * pxb, dt = pxa * pxb + pya * pyb;
+      R dl = m_atan2(cr, dt);
+      if (dl < R(0)) dl += R(2 * kPi);
+      const R s4a = R(4) * pxa * pya * (pxa * pxa - pya * pya);
+      const R s4b = R(4) * pxb * pyb * (pxb * pxb - pyb * pyb);
+      sflat.add(R(0.5) * dl);
+      slin.add(dl * R(1.0 / 3.0));
+      squad.add(R(0.25) * dl - (s4b - s4a) * R(1.0 / 48.0));
+    };
+    // g < 0 at t = infinity: the arc through it (t1 -> t0) lies inside the disk
+    if (q4_neg) {
+      limb(px0, py0, px1, py1);
+      ellipse(t1, t0, true, c1, s1, c0, s0);
+    } else {
+      ellipse(t0, t1, false, c0, s0, c1, s1);
+      limb(px1, py1, px0, py0);
+    }
+  }
+  slin.add(lin_arc<R>(g, cm, sm, h, rule));
+  I[0] = sflat.value();
+  I[1] = slin.value();
+  I[2] = squad.value();
+}
+
 // ------------------------------------------------------------------ occulted moments
 // Moments of the region where the projected ellipse covers the stellar disk:
 // I[0] = area, I[1] = Integral mu dA, I[2] = Integral r^2 dA.
@@ -1569,138 +1853,20 @@ GL_HD void occulted_r(const SetConst& c, R x0, R y0, R omr2, int cls, const Node
   if (cls == kPartial) {
     const int kb = frame_choice<R>(tg);
     const Frame<R> frr = make_frame_k<R>(tg, kb);
-    double tb[8];
-    // FP32 quadrature: the crossings from the FP32 frame (crossing_roots_f32);
-    // the FP64 frame and its roots only where those cannot be trusted, and
-    // always for the FP64 quadrature
-    Frame<double> fr;
-    bool have64 = false;
-    int nr = -1;
-    if constexpr (sizeof(R) == 4) nr = crossing_roots_f32(frr, tb);
-    if (nr < 0) {
-      const double xd = to_f64(x0), yd = to_f64(y0);
-      const Trig2<double> tgd = limb_poly<double>(c, xd, yd, fma(-yd, yd, fma(-xd, xd, 1.0)));
-      fr = make_frame_k<double>(tgd, kb);
-      have64 = true;
-      nr = frame_roots<double>(fr, tb);
-    }
-    // sign of g at the frame's t = infinity (q4: the largest |g| of eight
-    // samples, so its sign is the same in either precision)
-    const bool q4_neg = have64 ? neg_bits(fr.q[4]) : neg_bits(to_f64(frr.q[4]));
-    // The arcs of the boundary inside the disk are gathered first and integrated
-    // by one loop afterwards, so that a warp runs the quadrature once per arc
-    // count rather than once per breakpoint index.
-    R acm[4], asn[4], ah[4];
-    int na = 0;
-    CSum<R> sflat, slin, squad;
-    if (nr == 0) {
-      if (!q4_neg) {
-        // boundary entirely outside the disk: disjoint, or the disk inside the ellipse
-        R v1 = -g.x0 / g.dx, v2 = (-g.y0 - g.dy1 * v1) / g.dy2;
-        if (v1 * v1 + v2 * v2 < R(1)) {
-          I[0] = R(kPi);
-          I[1] = R(2.0 * kPi / 3.0);
-          I[2] = R(0.5 * kPi);
-        }
+    float r32[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int nr32 = -1;
+    if constexpr (sizeof(R) == 4) {
+      // FP32 quadrature: the crossings from the FP32 frame, in registers; the
+      // common cases (g with a single maximum, no crossing or two) stay here
+      nr32 = crossing_roots_f32(frr, r32);
+      if (nmax == 0 && (nr32 == 0 || nr32 == 2)) {
+        const bool q4_neg = neg_bits(to_f64(frr.q[4]));
+        partial_short<R>(g, tg, frr, x0, y0, area, rule, nr32, r32[0], r32[1], q4_neg, I);
         return;
       }
-      // boundary entirely inside the disk: the whole turn, split at the inner
-      // maxima as in the whole-ellipse case below
-      sflat.add(area);
-      squad.add(area * ((x0 * x0 + y0 * y0) + (g.dx * g.dx + g.dy1 * g.dy1 + g.dy2 * g.dy2) / R(4)));
-      whole_arcs<R>(g, tg, nmax, cmx, smx, acm, asn, ah, &na);
-    } else {
-      // g at the frame's t = infinity (q4, the largest |g| of eight samples, so
-      // its sign is safe) says whether the arc through it lies inside the disk;
-      // g changes sign at each crossing, so the others alternate from there.  An
-      // odd count (possible only from the FP64 fallback in degenerate cases)
-      // falls back to FP64 tests of g at the arc midpoints.
-      const bool wrap_in = q4_neg;
-      const bool parity = (nr & 1) == 0 || !have64;   // (FP32 roots come in pairs)
-      // breakpoints: the crossings (kind 1) and the inner maxima (kind 0) that
-      // lie on an inside arc.  A maximum that rounding placed on an outside arc
-      // (between two close crossings) would split that arc and lose the limb arc
-      // joining the two crossings, so it is dropped.
-      int kind[8];
-      for (int i = 0; i < nr; ++i) kind[i] = 1;
-      int nb = nr;
-      for (int i = 0; i < nmax; ++i) {
-        R tvr = frame_t<R>(frr, cmx[i], smx[i]);
-        if (!m_finite(tvr)) continue;
-        double tv = to_f64(tvr);
-        int below = 0;
-        const long long kv = dkey(tv);
-        for (int k = 0; k < nb; ++k) below += (kind[k] && dkey(tb[k]) < kv) ? 1 : 0;
-        const bool on_inside = parity ? (wrap_in != ((below & 1) != 0))
-                                      : (frame_poly<double>(fr, tv) < 0.0);
-        if (!on_inside) continue;
-        int j = nb - 1;
-        while (j >= 0 && dkey(tb[j]) > kv) {
-          tb[j + 1] = tb[j];
-          kind[j + 1] = kind[j];
-          --j;
-        }
-        tb[j + 1] = tv;
-        kind[j + 1] = 0;
-        ++nb;
-      }
-      R cth[8], sth[8], px[8], py[8];
-      R tr_[8];
-      for (int i = 0; i < nb; ++i) {
-        tr_[i] = from_f64<R>(tb[i]);
-        frame_angle<R>(frr, tr_[i], &cth[i], &sth[i]);
-        R qx = g.x0 + g.dx * cth[i];
-        R qy = g.y0 + g.dy1 * cth[i] + g.dy2 * sth[i];
-        R nrm = rsqrt_<R>(qx * qx + qy * qy);
-        px[i] = qx * nrm;
-        py[i] = qy * nrm;
-      }
-      QuadPoly<R> qp = quad_poly<R>(g.x0, g.y0, g.dx, g.dy1, g.dy2);
-      int ncross = 0;
-      for (int i = 0; i < nb; ++i) {
-        int ip = (i + 1 == nb) ? 0 : i + 1;
-        bool wrap = (i + 1 == nb);
-        ncross += kind[i];
-        R h, cm, sm;
-        frame_arc<R>(tr_[ip] - tr_[i], R(1) + tr_[i] * tr_[ip], wrap, cth[i], sth[i], &h, &cm,
-                     &sm);
-        if (nb == 1) {   // a lone breakpoint: the arc is the full turn
-          h = R(kPi);
-          cm = -cth[i];
-          sm = -sth[i];
-        }
-        bool inside;
-        if (wrap) inside = wrap_in;
-        else if (parity) inside = wrap_in != ((ncross & 1) != 0);
-        else inside = frame_poly<double>(fr, 0.5 * (tb[i] + tb[ip])) < 0.0;
-        if (inside) {
-          if (na < 4) {
-            acm[na] = cm;
-            asn[na] = sm;
-            ah[na] = h;
-            ++na;
-          }
-          R ca = cth[i], sa = sth[i], cb = cth[ip], sb = sth[ip];
-          R dth = R(2) * h;
-          sflat.add(R(0.5) * (g.W0 * dth + g.Wc * (sb - sa) - g.Ws * (cb - ca)));
-          squad.add(qp.K * dth + (quad_poly_trig<R>(qp, cb, sb) - quad_poly_trig<R>(qp, ca, sa)));
-        } else if (kind[i] && kind[ip]) {
-          // the limb arc between the same two crossings lies inside the ellipse
-          R cr = px[i] * py[ip] - py[i] * px[ip], dt = px[i] * px[ip] + py[i] * py[ip];
-          R dl = m_atan2(cr, dt);
-          if (dl < R(0)) dl += R(2 * kPi);
-          R s4a = R(4) * px[i] * py[i] * (px[i] * px[i] - py[i] * py[i]);
-          R s4b = R(4) * px[ip] * py[ip] * (px[ip] * px[ip] - py[ip] * py[ip]);
-          sflat.add(R(0.5) * dl);
-          slin.add(dl * R(1.0 / 3.0));
-          squad.add(R(0.25) * dl - (s4b - s4a) * R(1.0 / 48.0));
-        }
-      }
     }
-    for (int k = 0; k < na; ++k) slin.add(lin_arc<R>(g, acm[k], asn[k], ah[k], rule));
-    I[0] = sflat.value();
-    I[1] = slin.value();
-    I[2] = squad.value();
+    partial_general<R>(c, x0, y0, g, tg, frr, kb, nmax, cmx, smx, area, rule, nr32, r32[0], r32[1],
+                       r32[2], r32[3], I);
     return;
   }
   // whole ellipse inside the disk: split the turn at the inner maxima

@@ -9,7 +9,9 @@
   ellipse lies inside the disk and approach them as it reaches the limb;
 * the FP32 crossings (crossing_roots_f32) against the roots of the FP64 quartic of
   the same centre: the same count, roots within 1e-4 (1 + |t|), the FP64 fallback
-  rare on random limb geometries and taken at near-tangency.
+  rare on random limb geometries and taken at near-tangency;
+* the short path of the FP32 crossing items (partial_short: no crossing or two)
+  gives the bits of the general routine (partial_general) on the same items.
 """
 import os
 import subprocess
@@ -122,7 +124,8 @@ int main() {
     Frame<float> ff;
     Frame<double> fd;
     frames(c, (float)(rho * cos(ph)), (float)(rho * sin(ph)), &ff, &fd);
-    double t32[8], t64[8];
+    float t32[4];
+    double t64[8];
     const int n64 = frame_roots<double>(fd, t64), n32 = crossing_roots_f32(ff, t32);
     ++n;
     if (n32 < 0) { ++fallback; continue; }
@@ -144,7 +147,8 @@ int main() {
     Frame<float> ff;
     Frame<double> fd;
     frames(c, (float)(rho * cos(ph)), (float)(rho * sin(ph)), &ff, &fd);
-    double t32[8], t64[8];
+    float t32[4];
+    double t64[8];
     const int n32 = crossing_roots_f32(ff, t32), n64 = frame_roots<double>(fd, t64);
     ++tangent_total;
     tangent_fb += n32 < 0;
@@ -158,6 +162,56 @@ int main() {
   }
   printf("%ld %ld %ld %ld %.3e %ld %ld %ld %ld\n", n, fallback, count_mismatch, with_roots, worst,
          tangent_total, tangent_fb, tangent_zero, tangent_bad);
+}
+'''
+
+
+SRC_SHORT = r'''
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include "gl_math.cuh"
+using namespace gl;
+int main() {
+  std::mt19937_64 gen(5);
+  std::uniform_real_distribution<double> U(0, 1);
+  NodeRule<float> rule;
+  rule.n = 16;
+  for (int j = 0; j < 16; ++j) {   // any rule serves for an equality test
+    const double s = -1 + (2 * j + 1) / 16.0;
+    rule.sig[j] = (float)sin(M_PI * s / 2);
+    rule.wt[j] = (float)(M_PI / 16 * cos(M_PI * s / 2));
+    rule.cph[j] = (float)cos(M_PI * rule.sig[j]);
+    rule.sph[j] = (float)sin(M_PI * rule.sig[j]);
+  }
+  long n[3] = {0, 0, 0}, differ = 0, general = 0;
+  for (int it = 0; it < 100000; ++it) {
+    double k = 0.01 + 0.3 * U(gen), f = 0.9 * U(gen), eta = acos(U(gen)), xi = M_PI * U(gen);
+    SetConst c;
+    set_setup(0, 10, 20, 0.1, 0, M_PI / 2, k, f, eta, xi, 0.4, 0.25, 0.01, 1, &c);
+    double rho = 1 - c.req + 2 * c.req * U(gen), ph = 2 * M_PI * U(gen);
+    const float x0 = (float)(rho * cos(ph)), y0 = (float)(rho * sin(ph));
+    const double xd = x0, yd = y0;
+    const float omr2 = (float)fma(-yd, yd, fma(-xd, xd, 1.0));
+    if (maybe_two_maxima(c, x0, y0)) continue;
+    float a[3], b[3];
+    occulted_r<float>(c, x0, y0, omr2, kPartial, rule, a);   // short path where it applies
+    const Geo<float> g = make_geo<float>(c, x0, y0, omr2);
+    const Trig2<float> tg = limb_poly<float>(c, x0, y0, omr2);
+    const int kb = frame_choice<float>(tg);
+    const Frame<float> frr = make_frame_k<float>(tg, kb);
+    float r32[4];
+    const int nr = crossing_roots_f32(frr, r32);
+    const float cmx[2] = {0, 0}, smx[2] = {0, 0};
+    partial_general<float>(c, x0, y0, g, tg, frr, kb, 0, cmx, smx, (float)M_PI * g.dx * g.dy2, rule,
+                           nr, r32[0], r32[1], r32[2], r32[3], b);
+    if (nr == 2) ++n[2];
+    else if (nr == 0) ++n[neg_bits((double)frr.q[4]) ? 1 : 0];
+    else ++general;
+    if (memcmp(a, b, sizeof a) != 0) ++differ;
+  }
+  printf("%ld %ld %ld %ld %ld\n", n[0], n[1], n[2], general, differ);
 }
 '''
 
@@ -213,3 +267,10 @@ def test_fp32_crossings_against_the_fp64_quartic():
     # the limb is then below 1e-10 of the disk); any pair that stands is exact
     assert t_total == 2000 and t_fb + t_zero > 0.99 * t_total and t_fb > 0
     assert int(t_bad) == 0
+
+
+def test_short_crossing_path_matches_the_general_routine():
+    outside, inside, two, general, differ = (int(v) for v in _build_run(SRC_SHORT))
+    # every case of the short path is exercised, and it gives the general bits
+    assert outside > 100 and inside > 100 and two > 10000
+    assert differ == 0
