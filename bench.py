@@ -78,14 +78,15 @@ def measured_alu_peaks(device: int, sm_mhz_fallback: float):
 #         FP64 Kepler 90 for sets without the Taylor expansion
 #   quadrature (gl_items_quad_kernel, then gl_items_sum_kernel): FP32 whole-ellipse
 #         item 840 (geometry and limb polynomial 35, Newton for the maximum 150,
-#         16 nodes x 40, closed forms 15), crossing item 1540 (frame 90, FP32
-#         Ferrari 290, breakpoints 40, closed forms 160, arcs 110, one inside arc
-#         of 16 nodes x 56; the few items whose g may have two maxima add a 310-flop
-#         quartic); FP64 crossing item 105 (limb
-#         polynomial 15, frame 25, Newton polish of two roots 58, ordering 7),
-#         exposure sums 2 per sub-exposure
-F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 840, 1540
-F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 90, 105, 2
+#         16 nodes x 40, closed forms 15), crossing item 1590 (frame 90, FP32
+#         Ferrari 290, Newton steps settling two roots on the frame's quartic 50,
+#         breakpoints 40, closed forms 160, arcs 110, one inside arc of 16 nodes
+#         x 56; the few items whose g may have two maxima add a 310-flop quartic);
+#         no FP64 in a crossing item (the FP64 quartic runs only where the FP32
+#         roots cannot be trusted: none on the MCMC batch); FP64 exposure sums 2
+#         per sub-exposure
+F32_EXPOSURE, F32_ITEM, F32_FULL, F32_PARTIAL = 12, 40, 840, 1590
+F64_WINDOW, F64_KEPLER, F64_PARTIAL, F64_SUM = 10, 90, 0, 2
 
 
 def kernel_flops(c: dict) -> dict:
@@ -135,13 +136,14 @@ def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, summed over
 # the kernels of the group) from one ncu capture of the current kernels on the
-# workload named; other workloads report null.
-TRAFFIC = {("mcmc_batch", "window"): 0.082e6,
+# workload named (the launch lists under profiles/); None where no capture of the
+# current kernel exists, and for other workloads.
+TRAFFIC = {("mcmc_batch", "window"): 0.083e6,
            ("mcmc_batch", "exposures"): 0.331e6,
-           ("mcmc_batch", "quadrature"): 3.169e6 + 1.012e6,
-           ("uneven_batch", "window"): 470.97e6,
-           ("uneven_batch", "exposures"): 78.23e6,
-           ("uneven_batch", "quadrature"): 126.63e6 + 41.01e6}
+           ("mcmc_batch", "quadrature"): 3.150e6 + 1.012e6,
+           ("uneven_batch", "window"): 472.6e6,
+           ("uneven_batch", "exposures"): None,
+           ("uneven_batch", "quadrature"): None}
 
 KERNEL_NAMES = {"window": "gl_win_kernel", "exposures": "gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
