@@ -18,8 +18,10 @@
 //   gl_mlp_wgrad_kernel  dW[256 x 256] += A^T dZ over row tiles (two M = 128
 //                        accumulators, 512 TMEM columns), then added to the
 //                        FP32 gradient
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdint.h>
@@ -85,6 +87,42 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
       smem_u32(mbar)));
 }
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle (the layout
+// a TMA box of 64 bf16 x rows with CU_TENSOR_MAP_SWIZZLE_128B writes): rows of
+// 128 B, 8-row atoms of 1024 B (SBO), 1024-byte-aligned atoms; the leading byte
+// offset is not used by this layout.  A K = 16 slice inside the 64-element row
+// starts 32 B further (the hardware applies the swizzle to the final address).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version
+  d |= (uint64_t)2 << 61;   // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+// TMA: a 2-D box of the tensor map at (x, y) into shared memory, completion
+// counted in bytes on the mbarrier (x * 2 B is a multiple of 16 by construction)
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 // bounded wait on an mbarrier phase (at most `limit` polls); returns 1 if the
 // phase completed
 __device__ __forceinline__ uint32_t mbar_wait(uint64_t* mbar, uint32_t parity,
@@ -96,6 +134,20 @@ __device__ __forceinline__ uint32_t mbar_wait(uint64_t* mbar, uint32_t parity,
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(smem_u32(mbar)), "r"(parity));
+  }
+  return done;
+}
+// the same, giving up early once another role of the CTA has set *abort
+__device__ __forceinline__ uint32_t mbar_wait_ab(uint64_t* mbar, uint32_t parity,
+                                                 volatile int* abort, long limit = 1L << 22) {
+  uint32_t done = 0;
+  for (long it = 0; it < limit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity));
+    if (!done && (it & 255) == 255 && *abort) break;
   }
   return done;
 }
@@ -112,9 +164,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// sigmoid as the correctly rounded reciprocal of 1 + e^-z (a reciprocal is a
+// few instructions; a divide is a longer sequence, and the epilogues apply this
+// to every element)
+__device__ __forceinline__ float sigmoid_(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigmoid_(z); }
 __device__ __forceinline__ float silu_grad(float z) {
-  float s = 1.0f / (1.0f + __expf(-z));
+  const float s = sigmoid_(z);
   return s * (1.0f + z * (1.0f - s));
 }
 
@@ -132,31 +188,56 @@ struct GemmArgs {
   int probe_polls;             // > 0: failure-detection probe (gl_mlp_wait_probe)
 };
 
-// Persistent tensor-core layer: B resident in shared memory, one 128-row tile
-// of A at a time, D in TMEM (256 columns).
+// Persistent, warp-specialised tensor-core layer D[128 x 256] = A[128 x 256] B^T
+// per 128-row tile of A (B = [256 (N)][256 (K)], both K-major):
+//   warp 0   TMA producer: B once (4 boxes of 64 x 256, 128 KB), then per tile
+//            the two K-halves of A (2 boxes of 64 x 128 each) into a two-stage
+//            ring, 128-byte swizzle
+//   warp 1   MMA issuer (one thread): 16 tcgen05.mma (K = 16 each) per tile into
+//            one of two TMEM accumulators (2 x 256 columns), committing each
+//            K-half's stage back to the producer and the finished accumulator to
+//            the epilogue
+//   warps 2-9 epilogue: warp w reads the 32-lane quarter w mod 4 of TMEM (its 32
+//            rows) and one half of the 256 columns, applies bias + SiLU (or the
+//            SiLU derivative) and stores; the accumulator is then released
+// so that the loads of tile t + 1, its MMAs and the epilogue of tile t overlap.
+// Every wait is bounded; a role that gives up sets the CTA's abort flag (the
+// others then give up too), and before TMEM is freed the CTA waits, again with a
+// bound, for the copies and MMAs it issued.
+constexpr int GEMM_THREADS = 320;
+constexpr uint32_t kAChunk = 16384;   // 128 rows x 64 bf16
+constexpr uint32_t kBChunk = 32768;   // 256 rows x 64 bf16
+constexpr size_t GEMM_SMEM = 4 * (size_t)kBChunk + 4 * (size_t)kAChunk + 1024;
+
 template <int EPI>
-__global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_gemm_kernel(GemmArgs g) {
-  extern __shared__ __align__(1024) uint8_t sm[];
-  uint8_t* sB = sm;                    // 256 x 256 bf16 = 128 KB
-  uint8_t* sA = sm + 131072;           // 128 x 256 bf16 = 64 KB
-  __shared__ __align__(8) uint64_t mbar;
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    gl_mlp_gemm_kernel(GemmArgs g, const __grid_constant__ CUtensorMap tmA,
+                       const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ uint8_t sm_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sB = sm;                  // 4 x 32 KB
+  uint8_t* sA = sm + 4 * kBChunk;    // stage h: 2 x 16 KB at sA + h * 2 * kAChunk
+  __shared__ __align__(8) uint64_t bar_b, full[2], empty[2], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_abort;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (g.n + TILE_M - 1) / TILE_M;
   if ((int64_t)blockIdx.x >= ntiles) return;
-  for (int v = tid; v < W * 32; v += NTHREADS) {
-    int r = v >> 5, kg = v & 31;
-    uint4 val = *(const uint4*)(g.b + (int64_t)r * W + kg * 8);
-    *(uint4*)(sB + kmaj_off(r, kg * 8, 32)) = val;
-  }
-  if (tid == 0) {
+  const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  if (threadIdx.x == 0) {
     s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    mbar_init(&bar_b, 1);
+    mbar_init(&drain, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 8);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
         smem_u32(&tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -164,83 +245,144 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_gemm_kernel(GemmArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16(TILE_M, W);
-  uint32_t phase = 0;
+  int issued[2] = {0, 0};   // producer: A loads issued per stage
+  bool b_issued = false;
+  int committed = 0;        // MMA thread: tiles committed
+  bool mma_open = false;    // MMA thread: MMAs issued since the last commit
   if (g.probe_polls > 0) {
-    // Failure-detection probe: before any MMA is issued, wait on the current
-    // phase of the mbarrier, which nothing arrives on, for probe_polls polls.
-    // The wait gives up; the CTA records the timeout like any bounded wait that
-    // ran out and leaves through the normal exit (TMEM freed below).
-    const uint32_t done = mbar_wait(&mbar, 0, g.probe_polls);
-    if (tid == 0) {
+    // Failure-detection probe: before any copy or MMA is issued, wait on the
+    // first phase of an accumulator-release barrier, which nothing arrives on,
+    // for probe_polls polls; the wait gives up and the CTA records the timeout
+    // like any bounded wait that ran out, then leaves through the normal exit.
+    const uint32_t done = mbar_wait(&tempty[0], 0, g.probe_polls);
+    if (threadIdx.x == 0) {
       if (!done) atomicOr(g.status, 1);
       s_abort = 1;
     }
-    __syncthreads();
-  }
-  for (int64_t tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
-    const int64_t row0 = tile * TILE_M;
-    for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
-      int r = v >> 5, kg = v & 31;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (row0 + r < g.n) val = *(const uint4*)(g.a + (row0 + r) * W + kg * 8);
-      *(uint4*)(sA + kmaj_off(r, kg * 8, 32)) = val;
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      for (int ks = 0; ks < W / 16; ++ks) {
-        uint64_t ad = umma_desc(smem_u32(sA) + ks * 256, 128, 32 * 128);
-        uint64_t bd = umma_desc(smem_u32(sB) + ks * 256, 128, 32 * 128);
-        mma_bf16(tmem, ad, bd, idesc, ks > 0);
-      }
-      mma_commit(&mbar);
-    }
-    uint32_t done = mbar_wait(&mbar, phase);
-    done = __shfl_sync(0xffffffffu, done, 0);
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!done) {
-      if (lane == 0) {
-        atomicOr(g.status, 1);
-        s_abort = 1;
-      }
-    } else {
-      const int r = warp * 32 + lane;
-      const int64_t row = row0 + r;
-      for (int c = 0; c < W; c += 32) {
-        uint32_t acc[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, acc);
-        if (row < g.n) {
-          if (EPI == EPI_BWD) {
-            const float* zp = g.zprev + row * W + c;
-            __align__(16) __nv_bfloat16 hv[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) hv[j] = __float2bfloat16(__uint_as_float(acc[j]) * silu_grad(zp[j]));
-#pragma unroll
-            for (int q = 0; q < 4; ++q) *(uint4*)(g.hout + row * W + c + 8 * q) = *(uint4*)(hv + 8 * q);
-          } else {
-            __align__(16) __nv_bfloat16 hv[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              float z = __uint_as_float(acc[j]) + g.bias[c + j];
-              if (EPI == EPI_FWD_TRAIN) g.zout[row * W + c + j] = z;
-              hv[j] = __float2bfloat16(silu(z));
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) *(uint4*)(g.hout + row * W + c + 8 * q) = *(uint4*)(hv + 8 * q);
+  } else if (warp == 0) {
+    if (lane == 0) {
+      mbar_expect_tx(&bar_b, 4 * kBChunk);
+      for (int c = 0; c < 4; ++c) tma_load_2d(sB + c * kBChunk, &tmB, c * 64, 0, &bar_b);
+      b_issued = true;
+      for (int t = 0; t < my_tiles && !s_abort; ++t) {
+        const int row0 = (int)((blockIdx.x + (int64_t)t * gridDim.x) * TILE_M);
+        for (int h = 0; h < 2; ++h) {
+          if (t > 0 && !mbar_wait_ab(&empty[h], (t - 1) & 1, &s_abort)) {
+            s_abort = 1;
+            break;
           }
+          uint8_t* st = sA + h * 2 * kAChunk;
+          mbar_expect_tx(&full[h], 2 * kAChunk);
+          tma_load_2d(st, &tmA, (2 * h) * 64, row0, &full[h]);
+          tma_load_2d(st + kAChunk, &tmA, (2 * h + 1) * 64, row0, &full[h]);
+          issued[h] = t + 1;
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (s_abort) break;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(TILE_M, W);
+      bool ok = mbar_wait_ab(&bar_b, 0, &s_abort) != 0;
+      for (int t = 0; ok && t < my_tiles && !s_abort; ++t) {
+        const int buf = t & 1;
+        if (t >= 2 && !mbar_wait_ab(&tempty[buf], ((t >> 1) - 1) & 1, &s_abort)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int h = 0; h < 2 && ok; ++h) {
+          if (!mbar_wait_ab(&full[h], t & 1, &s_abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int j = 0; j < 8; ++j) {
+            const int ks = h * 8 + j, kc = ks >> 2;
+            const uint32_t within = (uint32_t)(ks & 3) * 32u;
+            const uint32_t a_addr = smem_u32(sA) + h * 2 * kAChunk + (kc - 2 * h) * kAChunk + within;
+            const uint32_t b_addr = smem_u32(sB) + kc * kBChunk + within;
+            mma_bf16(tmem + (uint32_t)buf * 256u, umma_desc_sw128(a_addr), umma_desc_sw128(b_addr),
+                     idesc, (h | j) != 0);
+            mma_open = true;
+          }
+          mma_commit(&empty[h]);   // the stage is free once these MMAs have read it
+        }
+        if (!ok) break;
+        mma_commit(&tfull[buf]);
+        mma_open = false;
+        committed = t + 1;
+      }
+      if (!ok) s_abort = 1;
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31, i.e. those rows,
+    // columns 128 ((w - 2) / 4) .. + 127
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * 128;
+    for (int t = 0; t < my_tiles; ++t) {
+      const int buf = t & 1;
+      uint32_t done = 0;
+      if (lane == 0) done = mbar_wait_ab(&tfull[buf], (t >> 1) & 1, &s_abort);
+      done = __shfl_sync(0xffffffffu, done, 0);
+      if (!done) {
+        if (lane == 0) s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t row = (blockIdx.x + (int64_t)t * gridDim.x) * TILE_M + q * 32 + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u;
+      for (int c = c0; c < c0 + 128; c += 32) {
+        uint32_t acc[32];
+        tmem_ld32(taddr + (uint32_t)c, acc);
+        if (row < g.n) {
+          __align__(16) __nv_bfloat16 hv[32];
+          if (EPI == EPI_BWD) {
+            const float4* zp = (const float4*)(g.zprev + row * W + c);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const float4 z4 = zp[v];
+              hv[4 * v] = __float2bfloat16(__uint_as_float(acc[4 * v]) * silu_grad(z4.x));
+              hv[4 * v + 1] = __float2bfloat16(__uint_as_float(acc[4 * v + 1]) * silu_grad(z4.y));
+              hv[4 * v + 2] = __float2bfloat16(__uint_as_float(acc[4 * v + 2]) * silu_grad(z4.z));
+              hv[4 * v + 3] = __float2bfloat16(__uint_as_float(acc[4 * v + 3]) * silu_grad(z4.w));
+            }
+          } else {
+            __align__(16) float zv[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              zv[j] = __uint_as_float(acc[j]) + g.bias[c + j];
+              hv[j] = __float2bfloat16(silu(zv[j]));
+            }
+            if (EPI == EPI_FWD_TRAIN) {
+#pragma unroll
+              for (int v = 0; v < 8; ++v) *(float4*)(g.zout + row * W + c + 4 * v) = *(float4*)(zv + 4 * v);
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) *(uint4*)(g.hout + row * W + c + 8 * v) = *(uint4*)(hv + 8 * v);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+    }
   }
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  __syncthreads();
+  // drain: nothing the CTA issued may still be in flight when TMEM is freed
+  if (warp == 0 && lane == 0) {
+    if (b_issued) mbar_wait(&bar_b, 0);
+    for (int h = 0; h < 2; ++h)
+      if (issued[h] > 0) mbar_wait(&full[h], (issued[h] - 1) & 1);
+  }
+  if (warp == 1 && lane == 0 && mma_open) {
+    mma_commit(&drain);
+    mbar_wait(&drain, 0);
+  }
+  if (warp == 1 && lane == 0 && committed > 0 && s_abort)
+    mbar_wait(&tfull[(committed - 1) & 1], ((committed - 1) >> 1) & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 struct WgradArgs {
@@ -444,20 +586,42 @@ __global__ void gl_mlp_w1grad_kernel(const float* __restrict__ x, const __nv_bfl
 
 // out[i] = sum over b < nb, in order, of part[b * stride + i]: the gradient sums
 // over blocks in a fixed order, so that a training run is reproducible bit for bit
-__global__ void gl_mlp_partsum_kernel(const float* __restrict__ part, int nb, int64_t stride,
-                                      int64_t count, float* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+// (1024 threads per block, 32 consecutive outputs i per block: warp w sums the
+// partials of the blocks b = w, w + 32, ... in that order for the 32 outputs,
+// lane by lane, with coalesced loads; warp 0 then adds the 32 warp sums in warp
+// order.  The order depends only on nb, so every run sums alike.)
+__global__ void __launch_bounds__(1024) gl_mlp_partsum_kernel(const float* __restrict__ part,
+                                                              int nb, int64_t stride,
+                                                              int64_t count,
+                                                              float* __restrict__ out) {
+  __shared__ float s_w[32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
   float acc = 0.f;
-  for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * stride + i];
-  out[i] = acc;
+  if (i < count)
+    for (int b = warp; b < nb; b += 32) acc += part[(int64_t)b * stride + i];
+  s_w[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && i < count) {
+    float t = 0.f;
+    for (int w = 0; w < 32; ++w) t += s_w[w][lane];
+    out[i] = t;
+  }
 }
 
-__global__ void gl_mlp_losssum_kernel(const double* __restrict__ lpart, int nb,
-                                      double* __restrict__ loss) {
-  double acc = 0.0;
-  for (int b = 0; b < nb; ++b) acc += lpart[b];
-  *loss = acc;
+// sum of nb <= 1024 per-block losses: a fixed pairwise tree over one block
+__global__ void __launch_bounds__(1024) gl_mlp_losssum_kernel(const double* __restrict__ lpart,
+                                                              int nb,
+                                                              double* __restrict__ loss) {
+  __shared__ double s_l[1024];
+  const int t = threadIdx.x;
+  s_l[t] = t < nb ? lpart[t] : 0.0;
+  __syncthreads();
+  for (int h = 512; h > 0; h >>= 1) {
+    if (t < h) s_l[t] += s_l[t + h];
+    __syncthreads();
+  }
+  if (t == 0) *loss = s_l[0];
 }
 
 // Adam on the FP32 master parameters (bias-corrected), then refresh the BF16
@@ -485,7 +649,6 @@ __global__ void gl_mlp_cast_kernel(const float* __restrict__ p, __nv_bfloat16* _
   wk[(int64_t)l * W * W + (int64_t)i * W + o] = b;
 }
 
-constexpr size_t GEMM_SMEM = 131072 + 65536;
 // blocks of the CUDA-core gradient reductions (samples strided over them)
 constexpr int kRedBlocks = 1024;
 // floats of the partial-gradient buffer: the larger of one 256 x 256 slab per
@@ -576,9 +739,52 @@ int mlp_attrs(gl_mlp* m) {
   return GL_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query,
+// so that the library needs no link against the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of a [rows][256] row-major BF16 matrix in boxes of 64 columns x
+// box_rows rows with the 128-byte swizzle (the layout umma_desc_sw128 reads);
+// rows beyond the matrix read as zeros.
+int make_tmap(CUtensorMap* tm, const void* base, int64_t rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc) return GL_ECUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)W * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? GL_OK : GL_ECUDA;
+}
+
 int grid_for(const gl_mlp* m, int64_t n) {
   int64_t tiles = (n + TILE_M - 1) / TILE_M;
   return (int)(tiles < m->sms ? tiles : m->sms);
+}
+
+// One tensor-core layer over n rows (g.a: [n][256] BF16, g.b: [256][256] BF16).
+template <int EPI>
+int launch_gemm(const gl_mlp* m, const GemmArgs& g, int64_t n, cudaStream_t st) {
+  alignas(64) CUtensorMap ta, tb;
+  if (make_tmap(&ta, g.a, n, TILE_M) || make_tmap(&tb, g.b, W, W)) return GL_ECUDA;
+  gl_mlp_gemm_kernel<EPI><<<grid_for(m, n), GEMM_THREADS, GEMM_SMEM, st>>>(g, ta, tb);
+  return GL_OK;
 }
 
 bool dev_ptr(const void* p, int device) {
@@ -610,10 +816,8 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
     g.n = n;
     g.status = m->d_status;
     g.probe_polls = m->probe_polls;
-    if (train)
-      gl_mlp_gemm_kernel<EPI_FWD_TRAIN><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
-    else
-      gl_mlp_gemm_kernel<EPI_FWD_INFER><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
+    rc = train ? launch_gemm<EPI_FWD_TRAIN>(m, g, n, st) : launch_gemm<EPI_FWD_INFER>(m, g, n, st);
+    if (rc) return rc;
   }
   gl_mlp_out_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(m->h + 3 * cs, m->p, y, n);
   return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
@@ -754,14 +958,14 @@ int mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, cudaStre
   const int bgrid = (int)(n < kRedBlocks ? n : kRedBlocks);
   // every gradient entry is the sum of per-block partials, taken in block order
   auto partsum = [&](int nb, int64_t stride, int64_t count, float* out) {
-    gl_mlp_partsum_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(m->part, nb, stride,
-                                                                          count, out);
+    gl_mlp_partsum_kernel<<<(unsigned)((count + 31) / 32), 1024, 0, st>>>(m->part, nb, stride,
+                                                                         count, out);
   };
   gl_mlp_outgrad_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
       m->z + 3 * cs, m->y, t, m->p, m->dy, m->rr, dzA, n);
   gl_mlp_outred_kernel<<<bgrid, W, 0, st>>>(m->h + 3 * cs, m->dy, m->rr, m->part, m->lpart, n);
   partsum(bgrid, W + 1, W + 1, m->g + OFF_W5);   // w5 and b5 are contiguous
-  gl_mlp_losssum_kernel<<<1, 1, 0, st>>>(m->lpart, bgrid, m->d_loss);
+  gl_mlp_losssum_kernel<<<1, 1024, 0, st>>>(m->lpart, bgrid, m->d_loss);
   for (int l = 4; l >= 2; --l) {
     // bias and weight gradients of layer l from dz_l (in dzA)
     gl_mlp_bgrad_kernel<<<bgrid, W, 0, st>>>(dzA, m->part, n);
@@ -784,7 +988,7 @@ int mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, cudaStre
     g.hout = dzB;
     g.n = n;
     g.status = m->d_status;
-    gl_mlp_gemm_kernel<EPI_BWD><<<grid_for(m, n), NTHREADS, GEMM_SMEM, st>>>(g);
+    if ((rc = launch_gemm<EPI_BWD>(m, g, n, st))) return rc;
     __nv_bfloat16* tmp = dzA;
     dzA = dzB;
     dzB = tmp;
