@@ -473,6 +473,22 @@ def surrogate_train_arm(args):
                        dict(train=n, epochs=args.sur_epochs, batch=batch, history=hist))
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     tc = samples * MLP_TC_TRAIN_FLOPS / train_s / 1e12
+    # inference forward of one training batch (its three 256 x 256 layers run on
+    # the tensor cores; the 7-wide input and 1-wide output layers on CUDA cores),
+    # CUDA events around 50 calls after 5 untimed ones
+    fb = min(batch, held["t"].numel())
+    fx, fy = held["feat"][:fb], torch.empty(fb, dtype=torch.float32, device="cuda")
+    for _ in range(5):
+        mlp.forward(fx, fy)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(50):
+        mlp.forward(fx, fy)
+    f1.record()
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / 50
+    fwd_tf = fb * 3 * 2 * 256 * 256 / (fwd_ms * 1e-3) / 1e12
+    burst = peaks.get("bf16_tflops", 1718.5)
     line = {"metric": "surrogate training samples/sec (forward + backward + Adam)",
             "value": samples / train_s, "unit": "samples/s", "n_gpus": 1,
             "steps": args.sur_epochs * ((n + batch - 1) // batch), "warmup": 0,
@@ -486,6 +502,10 @@ def surrogate_train_arm(args):
                             "frac": tc / peaks.get("bf16_tflops_sustained", 1407.5),
                             "note": "3 hidden 256x256 layers, forward + 2 backward GEMMs, "
                                     "whole training step time (incl. CUDA-core layers, Adam)"},
+            "forward_batch": {"rows": fb, "ms": fwd_ms, "tensor_tflops": fwd_tf,
+                              "peak": burst, "frac": fwd_tf / burst,
+                              "note": "three gl_mlp_gemm_kernel launches plus the CUDA-core "
+                                      "input and output layers, against the burst BF16 peak"},
             "heldout_flux_error_quantiles": q,
             "error_table_normalised": [float(x) for x in table]}
     print(json.dumps(line))
@@ -583,6 +603,7 @@ def surrogate_mcmc_arm(args):
                                             "bound_limit": args.sur_limit},
             "exact_fp32c": {"value": evals / te, "ms_per_step": te * 1e3},
             "gain_vs_exact": te / ts, "fallback": stats,
+            "fallback_fraction": stats["fallback"] / max(stats["items"], 1),
             "max_dflux_vs_fp64_gpu": max_err,
             "sampler": {"sweeps": args.sweeps, "acceptance": accs, "s_per_sweep": sweep_s}}
     print(json.dumps(line))

@@ -190,7 +190,8 @@ struct GemmArgs {
 
 // Persistent, warp-specialised tensor-core layer D[128 x 256] = A[128 x 256] B^T
 // per 128-row tile of A (B = [256 (N)][256 (K)], both K-major):
-//   warp 0   TMA producer: B once (4 boxes of 64 x 256, 128 KB), then per tile
+//   warp 0   TMA producer: B once (4 boxes of 64 x 256, 128 KB, one barrier
+//            each, so that the first MMAs need only the first box), then per tile
 //            the two K-halves of A (2 boxes of 64 x 128 each) into a two-stage
 //            ring, 128-byte swizzle
 //   warp 1   MMA issuer (one thread): 16 tcgen05.mma (K = 16 each) per tile into
@@ -217,7 +218,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint8_t* sm = (uint8_t*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sB = sm;                  // 4 x 32 KB
   uint8_t* sA = sm + 4 * kBChunk;    // stage h: 2 x 16 KB at sA + h * 2 * kAChunk
-  __shared__ __align__(8) uint64_t bar_b, full[2], empty[2], tfull[2], tempty[2], drain;
+  __shared__ __align__(8) uint64_t bar_b[4], full[2], empty[2], tfull[2], tempty[2], drain;
+  __shared__ float s_bias[8][128];   // each epilogue warp's copy of its half of the bias
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   if (threadIdx.x == 0) {
     s_abort = 0;
-    mbar_init(&bar_b, 1);
+    for (int c = 0; c < 4; ++c) mbar_init(&bar_b[c], 1);
     mbar_init(&drain, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&full[i], 1);
@@ -261,8 +263,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
   } else if (warp == 0) {
     if (lane == 0) {
-      mbar_expect_tx(&bar_b, 4 * kBChunk);
-      for (int c = 0; c < 4; ++c) tma_load_2d(sB + c * kBChunk, &tmB, c * 64, 0, &bar_b);
+      for (int c = 0; c < 4; ++c) {
+        mbar_expect_tx(&bar_b[c], kBChunk);
+        tma_load_2d(sB + c * kBChunk, &tmB, c * 64, 0, &bar_b[c]);
+      }
       b_issued = true;
       for (int t = 0; t < my_tiles && !s_abort; ++t) {
         const int row0 = (int)((blockIdx.x + (int64_t)t * gridDim.x) * TILE_M);
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(TILE_M, W);
-      bool ok = mbar_wait_ab(&bar_b, 0, &s_abort) != 0;
+      bool ok = true;
       for (int t = 0; ok && t < my_tiles && !s_abort; ++t) {
         const int buf = t & 1;
         if (t >= 2 && !mbar_wait_ab(&tempty[buf], ((t >> 1) - 1) & 1, &s_abort)) {
@@ -298,6 +302,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;");
           for (int j = 0; j < 8; ++j) {
             const int ks = h * 8 + j, kc = ks >> 2;
+            if (t == 0 && (ks & 3) == 0 && !mbar_wait_ab(&bar_b[kc], 0, &s_abort)) {
+              ok = false;
+              break;
+            }
             const uint32_t within = (uint32_t)(ks & 3) * 32u;
             const uint32_t a_addr = smem_u32(sA) + h * 2 * kAChunk + (kc - 2 * h) * kAChunk + within;
             const uint32_t b_addr = smem_u32(sB) + kc * kBChunk + within;
@@ -305,6 +313,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                      idesc, (h | j) != 0);
             mma_open = true;
           }
+          if (!ok) break;
           mma_commit(&empty[h]);   // the stage is free once these MMAs have read it
         }
         if (!ok) break;
@@ -318,6 +327,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31, i.e. those rows,
     // columns 128 ((w - 2) / 4) .. + 127
     const int q = warp & 3, c0 = ((warp - 2) >> 2) * 128;
+    float* bias = s_bias[warp - 2];
+    if (EPI != EPI_BWD) {
+      for (int j = lane; j < 128; j += 32) bias[j] = g.bias[c0 + j];
+      __syncwarp();
+    }
     for (int t = 0; t < my_tiles; ++t) {
       const int buf = t & 1;
       uint32_t done = 0;
@@ -349,7 +363,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             __align__(16) float zv[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              zv[j] = __uint_as_float(acc[j]) + g.bias[c + j];
+              zv[j] = __uint_as_float(acc[j]) + bias[c - c0 + j];
               hv[j] = __float2bfloat16(silu(zv[j]));
             }
             if (EPI == EPI_FWD_TRAIN) {
@@ -369,7 +383,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   __syncthreads();
   // drain: nothing the CTA issued may still be in flight when TMEM is freed
   if (warp == 0 && lane == 0) {
-    if (b_issued) mbar_wait(&bar_b, 0);
+    if (b_issued)
+      for (int c = 0; c < 4; ++c) mbar_wait(&bar_b[c], 0);
     for (int h = 0; h < 2; ++h)
       if (issued[h] > 0) mbar_wait(&full[h], (issued[h] - 1) & 1);
   }
