@@ -762,23 +762,25 @@ __global__ void __launch_bounds__(256) gl_win_kernel(LcArgs a) {
 }
 
 // Item pipeline, stage 2 (kept exposures and their sub-exposures in one kernel):
-// the first 64 threads of a 256-thread block take one kept exposure each: exact
+// the first NE threads of a block take one kept exposure each: exact
 // window and FP64 midpoint state, kept in shared memory, with one atomic add each
-// reserving the block's item slots and records.  Then all 256 threads expand the
-// 64 exposures' sub-exposures, up to 1024 at a time (four per thread; item i
+// reserving the block's item slots and records.  Then all threads expand the
+// NE exposures' sub-exposures, four per thread and pass (item i
 // belongs to the exposure whose slot range holds i, found by binary search over
 // the block's offsets): FP32 Taylor position and overlap class (taylor_item, the
 // same fixed-rounding code as everywhere else, inlined so that a thread's four
 // items overlap), queued with one atomic add per pass and queue.  Exposures that
 // do not fit the workspace go to the overflow list.
 // NT = 64: every thread also takes an exposure (the most FP64 warps per SM, for
-// large batches); NT = 256: the expansion has four times the threads (shorter
-// per-thread chains, for small batches).  The autotuner chooses.
+// large batches); NT = 256: 32 exposures per block iteration, expanded by eight
+// times the threads (shorter per-thread chains and twice the blocks with work,
+// for small batches; 64 or 16 per block measured slower there).  The autotuner
+// chooses.
 constexpr int kFuseExp = 64;
 
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) gl_expgeo_kernel(LcArgs a) {
-  constexpr int NE = kFuseExp, V = 4;
+  constexpr int NE = NT == 256 ? kFuseExp / 2 : kFuseExp, V = 4;
   __shared__ int warp_tot[32];
   __shared__ long long s_base, s_rec, s_q[3];
   __shared__ int s_fits, s_total, s_n[3];
