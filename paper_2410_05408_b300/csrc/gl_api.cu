@@ -120,15 +120,16 @@ struct ParamPtrs {
 // instruction costs the same whether one lane or 32 are active).
 //   stage 1: warps 0-2 compute sin and cos of omega, xi and eta, warp 3 the cube
 //            root of 1 - f, one set per lane
-//   stage 2: warp 0 the orbit and validity, warp 1 the projected ellipse, warp 2
-//            the transit window, warp 3 the limb darkening, each writing its own
-//            fields of the set's constants; warp 0 then sets the flags
+//   stage 2: warp 0 the orbit and validity, warp 1 the projected ellipse and the
+//            exposure fields, warp 2 the transit window, warp 3 the limb
+//            darkening, each writing its own fields of the set's constants; warp
+//            0 then sets the flags
 __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_sets,
                                                        const int64_t* offsets, int64_t n_total,
                                                        SetConst* sets, int* status,
                                                        unsigned long long* zero, int n_zero) {
   __shared__ double sh_s[4][32], sh_c[4][32], sh_cb[32];
-  __shared__ int sh_win[32], sh_valid[32];
+  __shared__ int sh_win[32], sh_tay[32], sh_valid[32];
   const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
   if (zero)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_zero; i += gridDim.x * blockDim.x)
@@ -170,6 +171,11 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
                                sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
       else
         gl::set_shape(p.k[s], f, cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
+      // the exposure fields and the Taylor-expansion flag (independent of the
+      // window, which is the longest role)
+      const double period = p.period[s], invP = gl::rcp64(period);
+      sh_tay[lane] = gl::set_exposure(p.t0[s], period, p.a_rs[s], p.ecc[s], 2.0 * gl::kPi * invP, invP,
+                                      p.exptime[s], p.nsuper ? p.nsuper[s] : p.nsuper_all, c);
     } else if (role == 2) {
       const double period = p.period[s], invP = gl::rcp64(period);
       sh_win[lane] = gl::set_window(p.t0[s], period, p.a_rs[s], p.ecc[s], p.omega[s],
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
   __syncthreads();
   if (!live || role != 0) return;
   const bool ok = orbit_ok && sh_valid[lane];
-  sets[s].flags = ok ? sh_win[lane] : gl::kSetInvalid;
+  sets[s].flags = ok ? (sh_win[lane] | sh_tay[lane]) : gl::kSetInvalid;
   if (!ok) atomicOr(status, kStatusInvalidSet);
   if (offsets) {
     bool bad = offsets[s] > offsets[s + 1] || (s == 0 && offsets[0] != 0) ||

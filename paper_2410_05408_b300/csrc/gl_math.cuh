@@ -268,9 +268,13 @@ GL_HD double ecc_anomaly_from_true(double nu, double e) {
 // series of sin r and cos r on |r| <= pi/4 (terms through r^19 and r^18: the
 // first omitted term is below 1e-19) and the quadrant of k.  Beyond |x| = 1e5
 // the library sincos is used.
+// (the library sincos for the rare large argument, compiled once rather than
+// inlined at every call site: the constants kernel runs with cold caches)
+GL_HD_NOINLINE void sincos_large(double x, double* s, double* c) { sincos_<double>(x, s, c); }
+
 GL_HD void sincos_setup(double x, double* s, double* c) {
   if (!(fabs(x) <= 1e5)) {
-    sincos_<double>(x, s, c);
+    sincos_large(x, s, c);
     return;
   }
   const double two_over_pi = 0.63661977236758134308;
@@ -307,8 +311,10 @@ GL_HD void sincos_setup(double x, double* s, double* c) {
 
 // Cube root of a > 0 in FP64: FP32 estimate and one Halley step
 // y <- y (y^3 + 2a) / (2 y^3 + a), which triples the number of correct digits.
+GL_HD_NOINLINE double cbrt_large(double a) { return cbrt(a); }
+
 GL_HD double cbrt_setup(double a) {
-  if (!(a > 1e-30 && a < 1e30)) return cbrt(a);
+  if (!(a > 1e-30 && a < 1e30)) return cbrt_large(a);
   const double y = (double)cbrtf((float)a);
   const double y3 = y * y * y;
   return y * (y3 + 2.0 * a) * rcp64(2.0 * y3 + a);
@@ -530,8 +536,8 @@ GL_HD void set_kepler(SetConst* c) {
   c->kf_si = (float)c->sini;
 }
 
-// Transit window, exposure fields and the sub-exposure expansion flag; returns
-// the flags kSetWholeOrbit and kSetTaylor.
+// Transit window (and its exposure-widened forms); returns the flag
+// kSetWholeOrbit.
 //  The sky separation is at least r |sin phi| >= a (1-e) |sin phi|, phi = angle
 //  from conjunction along the orbit; behind the star (|phi| > pi/2) nothing is
 //  occulted.  Outside |phi| <= phi_w the flux is exactly 1.  The window only has
@@ -542,8 +548,6 @@ GL_HD int set_window(double t0, double period, double a_rs, double ecc, double o
                      double req, double nmean, double invP, double exptime, int nsuper,
                      SetConst* c) {
   int flags = 0;
-  c->exptime = exptime;
-  c->nsuper = nsuper;
   double smax = 1.0 + req * (1.0 + 1e-9) + 1e-9;
   double rmin = a_rs * (1.0 - ecc);
   if (smax >= rmin * (1.0 - 1e-4)) {
@@ -566,10 +570,21 @@ GL_HD int set_window(double t0, double period, double a_rs, double ecc, double o
                 6.283185307179586f * turns;
       return E - ef * sinf(E);
     };
-    float Mcf = mean_anomaly(nucf);
+    // the mean anomaly at the conjunction and at both ends, in one loop (the
+    // function's code is fetched once, not three inlined copies)
+    float Mk[3];
+#pragma unroll 1
+    for (int q = 0; q < 3; ++q) {
+      const float nu = q == 0 ? nucf : nucf + (q == 2 ? phw : -phw);
+      const float m = mean_anomaly(nu);
+      Mk[0] = q == 0 ? m : Mk[0];
+      Mk[1] = q == 1 ? m : Mk[1];
+      Mk[2] = q == 2 ? m : Mk[2];
+    }
+    const float Mcf = Mk[0];
     float taus[2];
     for (int sgn = 0; sgn < 2; ++sgn) {
-      float dM = mean_anomaly(nucf + (sgn ? phw : -phw)) - Mcf;
+      float dM = (sgn ? Mk[2] : Mk[1]) - Mcf;
       taus[sgn] = dM / (float)nmean;
     }
     double margin = 1e-4 * (fabs((double)taus[0]) + fabs((double)taus[1])) + 1e-4;
@@ -580,6 +595,21 @@ GL_HD int set_window(double t0, double period, double a_rs, double ecc, double o
   c->ehi = c->tau_hi + 0.5 * exptime;
   c->elo_key = dkey(c->elo);
   c->ehi_key = dkey(c->ehi);
+  // FP32 copy of the window for the per-exposure test (set_exposure holds the
+  // rest of it)
+  c->wlo_f = (float)(c->tau_lo - 0.5 * exptime);
+  c->whi_f = (float)(c->tau_hi + 0.5 * exptime);
+  return flags;
+}
+
+// Exposure fields, the rest of the FP32 window test's constants and the
+// sub-exposure expansion flag (independent of the window, so that another part
+// of the constants kernel can form them); returns the flag kSetTaylor.
+GL_HD int set_exposure(double t0, double period, double a_rs, double ecc, double nmean,
+                       double invP, double exptime, int nsuper, SetConst* c) {
+  int flags = 0;
+  c->exptime = exptime;
+  c->nsuper = nsuper;
   c->sub_step = exptime / nsuper;
   c->fsub_step = (float)c->sub_step;
   // FP32 copy of the window for the per-exposure test, widened for rounding:
@@ -588,8 +618,6 @@ GL_HD int set_window(double t0, double period, double a_rs, double ecc, double o
   c->Pf = (float)period;
   c->invPf = (float)invP;
   c->slack_f = (float)(ldexp(fabs(t0) + period, -20) + 1e-6);
-  c->wlo_f = (float)(c->tau_lo - 0.5 * exptime);
-  c->whi_f = (float)(c->tau_hi + 0.5 * exptime);
   // Sub-exposure positions may come from a cubic Taylor expansion about the
   // exposure midpoint.  For a Kepler orbit |d^4 r/dt^4| <= C n^4 a (2+e)/(1-e)^5
   // (from r'' = -mu r/|r|^3, mu = n^2 a^3, r >= a(1-e)); with C = 60 the
@@ -627,7 +655,8 @@ GL_HD bool set_setup_trig(double t0, double period, double a_rs, double b, doubl
   set_shape(k, f, cbrt1mf, ce, sx, cx, c);
   set_ld(u1, u2, c);
   c->flags = set_window(t0, period, a_rs, ecc, omega, c->req, c->nmean, c->invP, exptime, nsuper,
-                        c);
+                        c) |
+             set_exposure(t0, period, a_rs, ecc, c->nmean, c->invP, exptime, nsuper, c);
   return true;
 }
 
