@@ -801,6 +801,23 @@ GL_HD void sin_cosm1_f(float d, float* sd, float* cm1) {
 // settle.  The FP32 <-> FP64 conversions are integer operations (on B300 an FP64
 // conversion holds the FP64 unit like an FP64 operation).  Returns sin d and
 // cos d - 1.
+// Bisection on the bracket |E - M| <= e for Kepler's equation about the
+// conjunction (the backup of kepler_offset's Newton steps; compiled once).
+GL_HD_NOINLINE void kepler_bisect(const SetConst& c, double nt, double* sd_out, double* cm1_out) {
+  const double ec = c.kep_ec, es = c.kep_es;
+  double sd, cm1;
+  double Ec = atan2(c.sinEc, c.cosEc);
+  double M = Ec - c.ecc * c.sinEc + nt;
+  double lo = M - c.ecc - Ec, hi = M + c.ecc - Ec;
+  for (int it = 0; it < 200 && hi - lo > 1e-16 * (1.0 + fabs(lo)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    sin_cosm1(mid, &sd, &cm1);
+    double F = mid - ec * sd - es * cm1 - nt;
+    if (F > 0.0) hi = mid; else lo = mid;
+  }
+  sin_cosm1(0.5 * (lo + hi), sd_out, cm1_out);
+}
+
 GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* cm1_out) {
   const double nt = c.nmean * tau;
   const double ec = c.kep_ec, es = c.kep_es;
@@ -808,6 +825,7 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
   const float ir1f = c.kf_ir1;
   float df = ntf * ir1f;
   df -= 0.5f * esf * df * df * ir1f;   // second-order start: F ~ d (1 - ec) + es d^2 / 2 - n tau
+#pragma unroll 1
   for (int it = 0; it < 4; ++it) {
     float sdf, cmf;
     sin_cosm1_f(df, &sdf, &cmf);
@@ -836,19 +854,7 @@ GL_HD void kepler_offset(const SetConst& c, double tau, double* sd_out, double* 
     *cm1_out = cm1 + step * sd - hs2 * cp;
     return;
   }
-  {
-    double Ec = atan2(c.sinEc, c.cosEc);
-    double M = Ec - c.ecc * c.sinEc + nt;
-    double lo = M - c.ecc - Ec, hi = M + c.ecc - Ec;
-    for (int it = 0; it < 200 && hi - lo > 1e-16 * (1.0 + fabs(lo)); ++it) {
-      double mid = 0.5 * (lo + hi);
-      sin_cosm1(mid, &sd, &cm1);
-      double F = mid - ec * sd - es * cm1 - nt;
-      if (F > 0.0) hi = mid; else lo = mid;
-    }
-    d = 0.5 * (lo + hi);
-  }
-  sin_cosm1(d, sd_out, cm1_out);
+  kepler_bisect(c, nt, sd_out, cm1_out);
 }
 
 // Sky position at time offset tau from conjunction.  The sky coordinates are
@@ -1024,6 +1030,7 @@ GL_HD void nearest_limb_angle(const Geo<R>& g, const Trig2<R>& t, R* cs, R* ss) 
   R bx = g.dx * g.x0 + g.dy1 * g.y0, by = g.dy2 * g.y0;
   R nrm = m_sqrt(bx * bx + by * by);
   R ct = nrm > R(0) ? bx / nrm : R(1), st = nrm > R(0) ? by / nrm : R(0);
+#pragma unroll 1
   for (int it = 0; it < 3; ++it) {
     R c2 = ct * ct - st * st, s2 = R(2) * st * ct;
     R g1 = -t.B * st + t.C * ct - R(2) * t.D * s2 + R(2) * t.E * c2;
@@ -1102,6 +1109,7 @@ GL_HD T cubic_largest_root(T a, T b, T c) {
     T B = (A != T(0)) ? q_div<T, FAST>(Q, A) : T(0);
     z = A + B - a * T(1.0 / 3.0);
   }
+#pragma unroll 1
   for (int it = 0; it < 3; ++it) {
     T f = ((z + a) * z + b) * z + c;
     T fp = (T(3) * z + T(2) * a) * z + b;
@@ -1352,6 +1360,7 @@ GL_HD int crossing_roots_f32(const Frame<float>& fr, float r[4]) {
       ++nr;
       // Newton on the monic quartic (quartic_real_roots' polish)
       float t = y[i] - 0.25f * a;
+#pragma unroll 1
       for (int it = 0; it < 3; ++it) {
         const float f = (((t + a) * t + b) * t + c) * t + d;
         const float fp = ((4.0f * t + 3.0f * a) * t + 2.0f * b) * t + c;
@@ -1362,7 +1371,7 @@ GL_HD int crossing_roots_f32(const Frame<float>& fr, float r[4]) {
       }
       // settle on the frame's quartic
       bool settled = false;
-#pragma unroll
+#pragma unroll 1
       for (int it = 0; it < 3; ++it) {
         if (!settled) {
           const float pv = (((q4 * t + q3) * t + q2) * t + q1) * t + q0;
