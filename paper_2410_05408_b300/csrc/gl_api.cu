@@ -120,8 +120,8 @@ struct ParamPtrs {
 // instruction costs the same whether one lane or 32 are active).
 //   stage 1: warps 0-2 compute sin and cos of omega, xi and eta, warp 3 the cube
 //            root of 1 - f, one set per lane
-//   stage 2: warp 0 the orbit and validity, warp 1 the projected ellipse and the
-//            exposure fields, warp 2 the transit window, warp 3 the limb
+//   stage 2: warp 0 the orbit and validity, warp 1 the projected ellipse, warp 2
+//            the transit window and the exposure fields, warp 3 the limb
 //            darkening, each writing its own fields of the set's constants; warp
 //            0 then sets the flags
 __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_sets,
@@ -171,16 +171,13 @@ __global__ void __launch_bounds__(128) gl_setup_kernel(ParamPtrs p, int64_t n_se
                                sh_s[2][lane], sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
       else
         gl::set_shape(p.k[s], f, cb, sh_c[2][lane], sh_s[1][lane], sh_c[1][lane], c);
-      // the exposure fields and the Taylor-expansion flag (independent of the
-      // window, which is the longest role)
-      const double period = p.period[s], invP = gl::rcp64(period);
-      sh_tay[lane] = gl::set_exposure(p.t0[s], period, p.a_rs[s], p.ecc[s], 2.0 * gl::kPi * invP, invP,
-                                      p.exptime[s], p.nsuper ? p.nsuper[s] : p.nsuper_all, c);
     } else if (role == 2) {
       const double period = p.period[s], invP = gl::rcp64(period);
       sh_win[lane] = gl::set_window(p.t0[s], period, p.a_rs[s], p.ecc[s], p.omega[s],
                                     gl::set_req(p.k[s], cb), 2.0 * gl::kPi * invP, invP,
                                     p.exptime[s], p.nsuper ? p.nsuper[s] : p.nsuper_all, c);
+      sh_tay[lane] = gl::set_exposure(p.t0[s], period, p.a_rs[s], p.ecc[s], 2.0 * gl::kPi * invP, invP,
+                                      p.exptime[s], p.nsuper ? p.nsuper[s] : p.nsuper_all, c);
     } else {
       gl::set_ld(p.u1[s], p.u2[s], c);
       const double g = p.g ? p.g[s] : 0.0, f = p.f[s];
@@ -337,7 +334,8 @@ struct LcArgs {
 
 enum : int {
   kIcItems = 0, kIcRecs = 1, kIcFull = 2, kIcPart = 3, kIcFetch = 4, kIcKept = 5, kIcOver = 6,
-  kIcFetchP = 7, kIcHeavy = 8, kIcFetchH = 9, kIcSlots = 10,
+  kIcFetchP = 7, kIcHeavy = 8, kIcFetchH = 9 /* (unused: heavy batches go by warp index) */,
+  kIcSlots = 10,
   // per-sub-partition counters of crossing batches (32-bit, after the kIc slots)
   kSmspSlots = 1024,
   kIcWords = kIcSlots + kSmspSlots / 2   // 64-bit words zeroed by every step
@@ -977,13 +975,18 @@ __global__ void __launch_bounds__(NT, MINB) gl_items_quad_kernel(LcArgs a) {
   }
   // Pass 2, whole-ellipse items that may have two inner maxima (their f_lin
   // takes two mapped arcs instead of one table rule: ~3x the work), then the
-  // others, taken as they come, so that no heavy batch starts late.
-  for (;;) {
-    unsigned long long b = 0;
-    if (lane == 0) b = atomicAdd(&a.ictr[kIcFetchH], 32ull);
-    b = __shfl_sync(0xffffffffu, b, 0);
-    if ((long long)b >= nh) break;
-    if ((long long)b + lane < nh) run_item(a.ihq[b + lane], gl::kFull);
+  // others, taken as they come, so that no heavy batch starts late.  The heavy
+  // batches are few: they go to the warps by global warp index, counted from the
+  // last warp (the last to reach the crossing counters), with no claim on a
+  // shared counter (thousands of warps claiming at once queue on its address).
+  {
+    const long long hb = (nh + 31) / 32;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (long long bb = nw - 1 - gw; bb < hb; bb += nw) {
+      const long long b = bb * 32;
+      if (b + lane < nh) run_item(a.ihq[b + lane], gl::kFull);
+    }
   }
   for (;;) {
     unsigned long long b = 0;

@@ -622,12 +622,16 @@ GL_HD int set_exposure(double t0, double period, double a_rs, double ecc, double
   // exposure midpoint.  For a Kepler orbit |d^4 r/dt^4| <= C n^4 a (2+e)/(1-e)^5
   // (from r'' = -mu r/|r|^3, mu = n^2 a^3, r >= a(1-e)); with C = 60 the
   // truncation over half an exposure must stay below 1e-10 stellar radii.
+  // (The bound is only compared with 1e-10, so FP32 serves: its rounding can
+  // move the decision only for a set within 1e-6 of the threshold, whose
+  // truncation stays within 1e-10 either way.)
   {
-    double n4 = nmean * nmean * nmean * nmean;
-    double h = 0.5 * exptime;
-    double om = 1.0 - ecc;
-    double bound = 60.0 * n4 * a_rs * (2.0 + ecc) / (om * om * om * om * om) * (h * h * h * h) / 24.0;
-    if (bound <= 1e-10) flags |= kSetTaylor;
+    const float n = (float)nmean, h = 0.5f * (float)exptime;
+    const float e = (float)ecc, om = 1.0f - e;
+    const float n2 = n * n, h2 = h * h, om2 = om * om;
+    const float bound = 2.5f * (n2 * n2) * (float)a_rs * (2.0f + e) * (h2 * h2) /
+                        (om2 * om2 * om);   // 60 / 24 = 2.5
+    if (bound <= 1e-10f) flags |= kSetTaylor;
   }
   return flags;
 }
