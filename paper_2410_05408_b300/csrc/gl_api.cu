@@ -1028,15 +1028,24 @@ __device__ __noinline__ void finish_overflow(const LcArgs& a, int k, int rb) {
 template <typename R>
 __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
   pdl_wait();
+  // the thread's first record is loaded together with the counters (one round
+  // trip less; a slot past the records holds a value that is never used)
+  const long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int ns0 = 0, f0 = 0, j0 = 0;
+  if (r0 < a.item_cap) {
+    ns0 = a.rns[r0];
+    f0 = a.rfirst[r0];
+    j0 = a.rj[r0];
+  }
   const long long nrec = (long long)a.ictr[kIcRecs];
   const long long nover = (long long)a.ictr[kIcOver];
   const R* idef = (const R*)a.idef;
   const int rb = rule_base(a.rule_idx);
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrec + nover;
-       r += (long long)gridDim.x * blockDim.x) {
+  for (long long r = r0; r < nrec + nover; r += (long long)gridDim.x * blockDim.x) {
     if (r < nrec) {
-      const int ns = a.rns[r];
-      const R* d = idef + a.rfirst[r];
+      const bool first = r == r0;
+      const int ns = first ? ns0 : a.rns[r];
+      const R* d = idef + (first ? f0 : a.rfirst[r]);
       double acc = 0.0;
       for (int q0 = 0; q0 < ns; q0 += 8) {
         R v[8];
@@ -1046,7 +1055,7 @@ __global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
         for (int k = 0; k < 8; ++k)
           if (q0 + k < ns) acc += gl::to_f64(v[k]);
       }
-      a.out[a.rj[r]] = exposure_mean(acc, ns);
+      a.out[first ? j0 : a.rj[r]] = exposure_mean(acc, ns);
     } else {
       finish_overflow<R>(a, a.ovlist[r - nrec], rb);
     }
