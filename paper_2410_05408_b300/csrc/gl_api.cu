@@ -793,6 +793,14 @@ __global__ void __launch_bounds__(NT) gl_expgeo_kernel(LcArgs a) {
   __shared__ gl::MidState s_mid[NE];
   pdl_wait();
   const int tid = threadIdx.x;
+  // the block's first kept-list entries are loaded together with the kept count
+  // (one dependent round trip less; an entry past the count is never used)
+  const long long kf = (long long)blockIdx.x * NE + tid;
+  int jf = 0, sf = 0;
+  if (tid < NE && kf < a.n_total) {
+    jf = a.klist[kf];
+    sf = a.kset[kf];
+  }
   const long long nk = (long long)a.ictr[kIcKept];
   R* ipos = (R*)a.ipos;
   R* idef = (R*)a.idef;
@@ -802,8 +810,8 @@ __global__ void __launch_bounds__(NT) gl_expgeo_kernel(LcArgs a) {
     double tau = 0.0;
     gl::MidState mid;
     if (tid < NE && k < nk) {
-      j = a.klist[k];
-      st = a.kset[k];
+      j = k == kf ? jf : a.klist[k];
+      st = k == kf ? sf : a.kset[k];
       const int64_t ti = a.offsets ? (int64_t)j : (int64_t)j - (int64_t)st * a.n_times;
       fl = exposure_prep<R>(a.sets[st], a.t[ti], &tau, &mid);
       if (fl & kExpDead) a.out[j] = 1.0;
