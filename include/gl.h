@@ -251,7 +251,7 @@ int64_t gl_graph_launches(const gl_context *ctx);
  * warps spread over the whole GPU, and each exposure's FP64 mean in
  * sub-exposure order.  With it off, a tile kernel takes consecutive exposures and does all of
  * this per tile.  The pipeline balances batches whose transits fall in few
- * places; its workspace (56 bytes per sub-exposure and 8 per exposure,
+ * places; its workspace (56 bytes per sub-exposure and 12 per exposure,
  * context-owned, grown on demand and kept) holds n_total x nsuper_all sub-exposures (16 per exposure
  * with per-set nsuper), at most `max_items` (0 = default 2^23); an exposure that
  * does not fit is finished by the thread holding it.  Every sub-exposure is
