@@ -415,6 +415,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* sA = sm;             // 256 (features) x 128 (samples) bf16 = 64 KB
   uint8_t* sB = sm + 65536;     // 256 (outputs)  x 128 (samples) bf16 = 64 KB
+  uint8_t* sT = sm + 131072;    // staging: 128 (samples) x 256 bf16, row-major = 64 KB
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
@@ -441,21 +442,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t row0 = tile * TILE_M;
     // transpose on the way in: element (sample s, feature f) -> (f, s) of a K-major
-    // tile with K = samples (16 core matrices along K)
-    for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
-      int s = v >> 5, fg = v & 31;
-      uint4 av = make_uint4(0, 0, 0, 0), dv = make_uint4(0, 0, 0, 0);
-      if (row0 + s < g.n) {
-        av = *(const uint4*)(g.a + (row0 + s) * W + fg * 8);
-        dv = *(const uint4*)(g.dz + (row0 + s) * W + fg * 8);
+    // tile with K = samples (16 core matrices along K).  Each operand is first
+    // copied row-major into the staging buffer (16-byte stores); then each thread
+    // gathers eight consecutive samples of one feature (2-byte loads, consecutive
+    // features on consecutive lanes) and writes them as one 16-byte row of a core
+    // matrix.
+    for (int op = 0; op < 2; ++op) {
+      const __nv_bfloat16* src = op ? g.dz : g.a;
+      uint8_t* dst = op ? sB : sA;
+      for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
+        const int s = v >> 5, fg = v & 31;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (row0 + s < g.n) val = *(const uint4*)(src + (row0 + s) * W + fg * 8);
+        *(uint4*)(sT + s * (W * 2) + fg * 16) = val;
       }
-      const __nv_bfloat16* ae = (const __nv_bfloat16*)&av;
-      const __nv_bfloat16* de = (const __nv_bfloat16*)&dv;
+      __syncthreads();
+      for (int v = tid; v < W * (TILE_M / 8); v += NTHREADS) {
+        const int f = v & (W - 1), sg = v >> 8;   // feature, group of 8 samples
+        __align__(16) __nv_bfloat16 e[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        *(__nv_bfloat16*)(sA + kmaj_off(fg * 8 + j, s, 16)) = ae[j];
-        *(__nv_bfloat16*)(sB + kmaj_off(fg * 8 + j, s, 16)) = de[j];
+        for (int j = 0; j < 8; ++j)
+          e[j] = *(const __nv_bfloat16*)(sT + (sg * 8 + j) * (W * 2) + f * 2);
+        *(uint4*)(dst + kmaj_off(f, sg * 8, 16)) = *(const uint4*)e;
       }
+      __syncthreads();
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -490,9 +500,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
       for (int c = 0; c < W; c += 32) {
         uint32_t acc[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * W + c), acc);
+        float* dstp = g.part + (int64_t)blockIdx.x * W * W + (int64_t)f * W + c;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          g.part[(int64_t)blockIdx.x * W * W + (int64_t)f * W + c + j] = __uint_as_float(acc[j]);
+        for (int j = 0; j < 32; j += 4)
+          *(float4*)(dstp + j) = make_float4(__uint_as_float(acc[j]), __uint_as_float(acc[j + 1]),
+                                             __uint_as_float(acc[j + 2]), __uint_as_float(acc[j + 3]));
       }
     }
   }
@@ -672,7 +684,7 @@ constexpr size_t part_floats(int sms) {
   return (size_t)sms * W * W > (size_t)kRedBlocks * NIN * W ? (size_t)sms * W * W
                                                              : (size_t)kRedBlocks * NIN * W;
 }
-constexpr size_t WGRAD_SMEM = 65536 + 65536;
+constexpr size_t WGRAD_SMEM = 65536 + 65536 + 65536;
 
 }  // namespace
 
