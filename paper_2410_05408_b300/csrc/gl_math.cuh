@@ -1357,41 +1357,52 @@ GL_HD int crossing_roots_f32(const Frame<float>& fr, float r[4]) {
   const float q0 = fr.q[0], q1 = fr.q[1], q2 = fr.q[2], q3 = fr.q[3], q4 = fr.q[4];
   const float d3 = 4.0f * q4, d2 = 3.0f * q3, d1 = 2.0f * q2;
   bool ok = true;
-  int nr = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (v[i]) {
-      ++nr;
-      // Newton on the monic quartic (quartic_real_roots' polish)
-      float t = y[i] - 0.25f * a;
+  // Newton on the monic quartic (quartic_real_roots' polish), then on the frame's
+  // quartic until the step settles
+  auto refine = [&](float y0) -> float {
+    float t = y0 - 0.25f * a;   // (a root of the depressed quartic, shifted back)
 #pragma unroll 1
-      for (int it = 0; it < 3; ++it) {
-        const float f = (((t + a) * t + b) * t + c) * t + d;
-        const float fp = ((4.0f * t + 3.0f * a) * t + 2.0f * b) * t + c;
-        if (fp == 0.0f) break;
-        const float step = q_div<float, true>(f, fp);
+    for (int it = 0; it < 3; ++it) {
+      const float f = (((t + a) * t + b) * t + c) * t + d;
+      const float fp = ((4.0f * t + 3.0f * a) * t + 2.0f * b) * t + c;
+      if (fp == 0.0f) break;
+      const float step = q_div<float, true>(f, fp);
+      t -= step;
+      if (fabsf(step) <= m_eps<float>() * (1.0f + fabsf(t))) break;
+    }
+    bool settled = false;
+#pragma unroll 1
+    for (int it = 0; it < 3; ++it) {
+      if (!settled) {
+        const float pv = (((q4 * t + q3) * t + q2) * t + q1) * t + q0;
+        const float dp = ((d3 * t + d2) * t + d1) * t + q1;
+        const float step = q_div<float, true>(pv, dp);
+        if (!(fabsf(step) <= 1e-2f * (1.0f + fabsf(t)))) break;   // (NaN too)
         t -= step;
-        if (fabsf(step) <= m_eps<float>() * (1.0f + fabsf(t))) break;
+        settled = fabsf(step) <= 1e-4f * (1.0f + fabsf(t));
       }
-      // settle on the frame's quartic
-      bool settled = false;
+    }
+    ok = ok && settled;
+    return t;
+  };
+  // roots come in pairs (one quadratic each: v[0] == v[1], v[2] == v[3]); the
+  // pairs are refined in a loop (the code of one pair, not four unrolled slots),
+  // the slots kept in registers by selects
+  const int nr = (v[0] ? 2 : 0) + (v[2] ? 2 : 0);
 #pragma unroll 1
-      for (int it = 0; it < 3; ++it) {
-        if (!settled) {
-          const float pv = (((q4 * t + q3) * t + q2) * t + q1) * t + q0;
-          const float dp = ((d3 * t + d2) * t + d1) * t + q1;
-          const float step = q_div<float, true>(pv, dp);
-          if (!(fabsf(step) <= 1e-2f * (1.0f + fabsf(t)))) break;   // (NaN too)
-          t -= step;
-          settled = fabsf(step) <= 1e-4f * (1.0f + fabsf(t));
-        }
-      }
-      ok = ok && settled;
-      y[i] = t;
-    } else {
-      y[i] = INFINITY;   // empty slots sort last
+  for (int pq = 0; pq < 2; ++pq) {
+    if (v[2 * pq]) {
+      const float ta = refine(pq == 0 ? y[0] : y[2]);
+      const float tb = refine(pq == 0 ? y[1] : y[3]);
+      y[0] = pq == 0 ? ta : y[0];
+      y[1] = pq == 0 ? tb : y[1];
+      y[2] = pq == 1 ? ta : y[2];
+      y[3] = pq == 1 ? tb : y[3];
     }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (!v[i]) y[i] = INFINITY;   // empty slots sort last
   if (!ok) return -1;
   // sorting network on four slots
   auto cx = [&](int i, int j) {
