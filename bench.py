@@ -139,8 +139,8 @@ def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
 # workload named (the launch lists under profiles/); None where no capture of the
 # current kernel exists, and for other workloads.
 TRAFFIC = {("mcmc_batch", "window"): 0.083e6,
-           ("mcmc_batch", "exposures"): 0.326e6,
-           ("mcmc_batch", "quadrature"): 3.153e6 + 1.012e6,
+           ("mcmc_batch", "exposures"): 0.337e6,
+           ("mcmc_batch", "quadrature"): 3.148e6 + 1.763e6,
            ("uneven_batch", "window"): 472.6e6,
            ("uneven_batch", "exposures"): 79.4e6,
            ("uneven_batch", "quadrature"): 75.6e6 + 41.0e6}
