@@ -520,28 +520,64 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
 
 // ---- CUDA-core kernels
 // layer 1: z1 = x W1 + b1, h1 = SiLU(z1); one thread per (sample, output)
+// Input layer: one thread per 8 consecutive outputs of a sample (a warp takes a
+// whole sample, so its 7 inputs are one broadcast load each), 16-byte loads of
+// the weights and 16-byte stores of z and h.
 __global__ void gl_mlp_in_kernel(const float* __restrict__ x, const float* __restrict__ p,
                                  float* __restrict__ z1, __nv_bfloat16* __restrict__ h1,
                                  int64_t n) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * W) return;
-  int64_t s = i / W;
-  int o = (int)(i % W);
-  float z = p[OFF_B1 + o];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // 8-output group
+  if (i >= n * (W / 8)) return;
+  const int64_t s = i / (W / 8);
+  const int o = (int)(i % (W / 8)) * 8;
+  float z[8];
+  {
+    const float4 b0 = *(const float4*)(p + OFF_B1 + o), b1 = *(const float4*)(p + OFF_B1 + o + 4);
+    z[0] = b0.x; z[1] = b0.y; z[2] = b0.z; z[3] = b0.w;
+    z[4] = b1.x; z[5] = b1.y; z[6] = b1.z; z[7] = b1.w;
+  }
 #pragma unroll
-  for (int k = 0; k < NIN; ++k) z = fmaf(x[s * NIN + k], p[OFF_W1 + k * W + o], z);
-  if (z1) z1[i] = z;
-  h1[i] = __float2bfloat16(silu(z));
+  for (int k = 0; k < NIN; ++k) {
+    const float xk = x[s * NIN + k];
+    const float4 w0 = *(const float4*)(p + OFF_W1 + k * W + o);
+    const float4 w1 = *(const float4*)(p + OFF_W1 + k * W + o + 4);
+    z[0] = fmaf(xk, w0.x, z[0]); z[1] = fmaf(xk, w0.y, z[1]);
+    z[2] = fmaf(xk, w0.z, z[2]); z[3] = fmaf(xk, w0.w, z[3]);
+    z[4] = fmaf(xk, w1.x, z[4]); z[5] = fmaf(xk, w1.y, z[5]);
+    z[6] = fmaf(xk, w1.z, z[6]); z[7] = fmaf(xk, w1.w, z[7]);
+  }
+  if (z1) {
+    *(float4*)(z1 + s * W + o) = make_float4(z[0], z[1], z[2], z[3]);
+    *(float4*)(z1 + s * W + o + 4) = make_float4(z[4], z[5], z[6], z[7]);
+  }
+  __align__(16) __nv_bfloat162 hv[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) hv[j] = __floats2bfloat162_rn(silu(z[2 * j]), silu(z[2 * j + 1]));
+  *(uint4*)(h1 + s * W + o) = *(const uint4*)hv;
 }
 
 // output layer y = h4 . w5 + b5; one warp per sample
 __global__ void gl_mlp_out_kernel(const __nv_bfloat16* __restrict__ h4, const float* __restrict__ p,
                                   float* __restrict__ y, int64_t n) {
+  // one warp per sample: each lane reads 8 consecutive activations (one 16-byte
+  // load), then the lanes' partial sums are added by a fixed shuffle tree
   int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (s >= n) return;
-  float acc = 0.f;
-  for (int k = lane; k < W; k += 32) acc = fmaf(__bfloat162float(h4[s * W + k]), p[OFF_W5 + k], acc);
+  const uint4 hq = *(const uint4*)(h4 + s * W + 8 * lane);
+  const __nv_bfloat162* hp = (const __nv_bfloat162*)&hq;
+  const float4 w0 = *(const float4*)(p + OFF_W5 + 8 * lane);
+  const float4 w1 = *(const float4*)(p + OFF_W5 + 8 * lane + 4);
+  const float2 h01 = __bfloat1622float2(hp[0]), h23 = __bfloat1622float2(hp[1]);
+  const float2 h45 = __bfloat1622float2(hp[2]), h67 = __bfloat1622float2(hp[3]);
+  float acc = h01.x * w0.x;
+  acc = fmaf(h01.y, w0.y, acc);
+  acc = fmaf(h23.x, w0.z, acc);
+  acc = fmaf(h23.y, w0.w, acc);
+  acc = fmaf(h45.x, w1.x, acc);
+  acc = fmaf(h45.y, w1.y, acc);
+  acc = fmaf(h67.x, w1.z, acc);
+  acc = fmaf(h67.y, w1.w, acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) y[s] = acc + p[OFF_B5];
 }
@@ -833,7 +869,7 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
   if (rc) return rc;
   if ((rc = mlp_attrs(m))) return rc;
   const int64_t cs = m->cap * W;
-  int64_t nth = n * W;
+  int64_t nth = n * (W / 8);
   gl_mlp_in_kernel<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(x, m->p, train ? m->z : nullptr,
                                                                   m->h, n);
   for (int l = 2; l <= 4; ++l) {
