@@ -1035,8 +1035,12 @@ __device__ __noinline__ void finish_overflow(const LcArgs& a, int k, int rb) {
   a.out[j] = (fl & kExpDead) ? 1.0 : exposure_local<R>(c, fl, mid, tau, c.nsuper, rb);
 }
 
+// Compiled for 8 resident blocks (32 registers): the sum loop needs few, and the
+// fallback's call into the quadrature routines, which would raise the count to
+// 128 (2 blocks per SM), spills instead; with 8 blocks per SM the uneven batch's
+// step went from 580 to 551 us (MCMC batch unchanged).
 template <typename R>
-__global__ void __launch_bounds__(256) gl_items_sum_kernel(LcArgs a) {
+__global__ void __launch_bounds__(256, 8) gl_items_sum_kernel(LcArgs a) {
   pdl_wait();
   // the thread's first record is loaded together with the counters (one round
   // trip less; a slot past the records holds a value that is never used)
@@ -2116,7 +2120,9 @@ int launch_items(gl_context* ctx, const LcArgs& args, cudaStream_t st) {
                    ctx->sms * qocc, 128, st, args);
   prof_end(ctx, GL_KERNEL_ITEMS, pq, st);
   gmark(ctx, kMarkItems, st);
-  launch_dependent(ctx, gl_items_sum_kernel<R>, ctx->sms * 2, 256, st, args);
+  // (the 8-CTA quadrature variant marks a large batch: then a full SM of sum
+  // threads, whose dependent loads per record need all the parallelism there is)
+  launch_dependent(ctx, gl_items_sum_kernel<R>, ctx->sms * (qvar ? 8 : 2), 256, st, args);
   prof_end(ctx, GL_KERNEL_QUAD, pe, st);
   gmark(ctx, kMarkSums, st);
   ctx->launches += 2;
