@@ -141,9 +141,9 @@ def hbm_roofline(nbytes: float, ms: float, hbm_peak) -> dict:
 TRAFFIC = {("mcmc_batch", "window"): 0.083e6,
            ("mcmc_batch", "exposures"): 0.337e6,
            ("mcmc_batch", "quadrature"): 3.148e6 + 1.763e6,
-           ("uneven_batch", "window"): 472.6e6,
-           ("uneven_batch", "exposures"): 79.4e6,
-           ("uneven_batch", "quadrature"): 75.6e6 + 41.0e6}
+           ("uneven_batch", "window"): 471.2e6,
+           ("uneven_batch", "exposures"): 81.9e6,
+           ("uneven_batch", "quadrature"): 74.7e6 + 41.5e6}
 
 KERNEL_NAMES = {"window": "gl_win_kernel", "exposures": "gl_expgeo_kernel",
                 "quadrature": "gl_items_quad_kernel+gl_items_sum_kernel"}
