@@ -384,6 +384,28 @@ int gl_mlp_adam(gl_mlp *m, float lr, float beta1, float beta2, float eps, void *
 /* GL_ETIMEOUT if a tensor-core wait gave up since the last call, else GL_OK. */
 int gl_mlp_status(gl_mlp *m);
 
+/* Kernel kinds for gl_mlp_profile_read. */
+#define GL_MLP_KERNEL_GEMM_FWD 0 /* a tensor-core layer of the forward pass (D = A B^T, bias,
+                                    SiLU; 2 x rows x 256 x 256 flops) */
+#define GL_MLP_KERNEL_GEMM_BWD 1 /* a tensor-core layer of the backward pass (dZ W, SiLU') */
+#define GL_MLP_KERNEL_WGRAD 2    /* a weight-gradient GEMM (A^T dZ, partial per CTA) */
+#define GL_MLP_KERNEL_IN 3       /* the CUDA-core input layer (7 -> 256, SiLU) */
+#define GL_MLP_KERNEL_OUT 4      /* the CUDA-core output layer (256 -> 1) */
+#define GL_MLP_KERNEL_KINDS 5
+
+/* Kernel timing (instrumentation, not in the paper).  With on = 1 every launch
+ * of the kinds above made by gl_mlp_forward, gl_mlp_loss_grad and
+ * gl_surrogate_train is bracketed by CUDA events on its stream; on = 0 stops.
+ * Enabling resets the accumulated times; at most 65536 launches per kind are
+ * timed.  The events are freed by gl_mlp_destroy.  GL_EINVAL on NULL or another
+ * value of on. */
+int gl_mlp_profile(gl_mlp *m, int on);
+
+/* Total device time in milliseconds and number of timed launches of kernel kind
+ * `kind` since timing was enabled (waits for the recorded events).  GL_EINVAL on
+ * NULL pointers or an unknown kind, GL_ECUDA on a runtime failure. */
+int gl_mlp_profile_read(gl_mlp *m, int kind, double *ms, int64_t *launches);
+
 /* Failure-detection probe (for tests; not in the paper).  With polls > 0, every
  * tensor-core kernel of the following gl_mlp_forward / gl_mlp_loss_grad calls,
  * after allocating its tensor memory and before issuing any MMA, waits `polls`

@@ -39,7 +39,7 @@ EXPORTED = ("gl_context_create", "gl_context_destroy", "gl_last_error", "gl_ligh
             "gl_feta_to_munu", "gl_munu_prior", "gl_ensemble_init", "gl_ensemble_sweep",
             "gl_mlp_init", "gl_surrogate_train", "gl_surrogate_error_table",
             "gl_surrogate_save", "gl_surrogate_load", "gl_mlp_wait_probe",
-            "gl_debug_alloc_limit")
+            "gl_debug_alloc_limit", "gl_mlp_profile", "gl_mlp_profile_read")
 
 SUR_BINS = 16   # GL_SURROGATE_BINS
 GL_EIO = -6
@@ -70,6 +70,8 @@ GL_KERNEL_WINDOW = 6
 GL_KERNEL_ITEMS = 7
 GL_KERNEL_STEP = 8
 PROFILE_OFF, PROFILE_EAGER, PROFILE_GRAPH = 0, 1, 2
+GL_MLP_KERNEL_GEMM_FWD, GL_MLP_KERNEL_GEMM_BWD, GL_MLP_KERNEL_WGRAD = 0, 1, 2
+GL_MLP_KERNEL_IN, GL_MLP_KERNEL_OUT = 3, 4
 
 PARAM_NAMES = ("t0", "period", "a_rs", "b", "ecc", "omega", "k", "f", "eta", "xi", "u1", "u2")
 
@@ -195,6 +197,11 @@ def load():
         lib.gl_mlp_init.restype = i32
         lib.gl_mlp_wait_probe.argtypes = [vp, i32]
         lib.gl_mlp_wait_probe.restype = i32
+        lib.gl_mlp_profile.argtypes = [vp, i32]
+        lib.gl_mlp_profile.restype = i32
+        lib.gl_mlp_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(i64)]
+        lib.gl_mlp_profile_read.restype = i32
         lib.gl_debug_alloc_limit.argtypes = [vp, i64]
         lib.gl_debug_alloc_limit.restype = i32
         lib.gl_surrogate_train.argtypes = [vp, i64, vp, vp, ctypes.POINTER(TrainConfig), i64, i64,
@@ -598,6 +605,17 @@ class Mlp:
 
     def wait_probe(self, polls: int):
         self._rc(load().gl_mlp_wait_probe(self.handle, int(polls)), "gl_mlp_wait_probe")
+
+    def profile(self, on: bool = True):
+        """Time every launch of the network's kernels with CUDA events (resets)."""
+        self._rc(load().gl_mlp_profile(self.handle, 1 if on else 0), "gl_mlp_profile")
+
+    def profile_read(self, kind: int):
+        """(total device ms, timed launches) of kernel kind GL_MLP_KERNEL_*."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._rc(load().gl_mlp_profile_read(self.handle, int(kind), ctypes.byref(ms),
+                                            ctypes.byref(n)), "gl_mlp_profile_read")
+        return ms.value, n.value
 
     def init(self, seed: int = 0):
         self._rc(load().gl_mlp_init(self.handle, int(seed)), "gl_mlp_init")

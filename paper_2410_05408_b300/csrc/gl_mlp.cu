@@ -30,6 +30,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/gl.h"
@@ -520,66 +521,78 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
 
 // ---- CUDA-core kernels
 // layer 1: z1 = x W1 + b1, h1 = SiLU(z1); one thread per (sample, output)
-// Input layer: one thread per 8 consecutive outputs of a sample (a warp takes a
-// whole sample, so its 7 inputs are one broadcast load each), 16-byte loads of
-// the weights and 16-byte stores of z and h.
-__global__ void gl_mlp_in_kernel(const float* __restrict__ x, const float* __restrict__ p,
-                                 float* __restrict__ z1, __nv_bfloat16* __restrict__ h1,
-                                 int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // 8-output group
-  if (i >= n * (W / 8)) return;
-  const int64_t s = i / (W / 8);
-  const int o = (int)(i % (W / 8)) * 8;
-  float z[8];
+// Input layer: lane l of a warp owns outputs 8 l .. 8 l + 7 and keeps their
+// weights and biases in registers; the warp walks over samples (its 7 inputs one
+// broadcast load each), with 16-byte stores of z and h.  Launched with a grid of
+// a few blocks per SM, so that each warp's weight loads serve several samples.
+__global__ void __launch_bounds__(128) gl_mlp_in_kernel(const float* __restrict__ x,
+                                                        const float* __restrict__ p,
+                                                        float* __restrict__ z1,
+                                                        __nv_bfloat16* __restrict__ h1,
+                                                        int64_t n) {
+  const int o = (threadIdx.x & 31) * 8;
+  float w[NIN][8], b[8];
   {
     const float4 b0 = *(const float4*)(p + OFF_B1 + o), b1 = *(const float4*)(p + OFF_B1 + o + 4);
-    z[0] = b0.x; z[1] = b0.y; z[2] = b0.z; z[3] = b0.w;
-    z[4] = b1.x; z[5] = b1.y; z[6] = b1.z; z[7] = b1.w;
+    b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+    b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
   }
 #pragma unroll
   for (int k = 0; k < NIN; ++k) {
-    const float xk = x[s * NIN + k];
     const float4 w0 = *(const float4*)(p + OFF_W1 + k * W + o);
     const float4 w1 = *(const float4*)(p + OFF_W1 + k * W + o + 4);
-    z[0] = fmaf(xk, w0.x, z[0]); z[1] = fmaf(xk, w0.y, z[1]);
-    z[2] = fmaf(xk, w0.z, z[2]); z[3] = fmaf(xk, w0.w, z[3]);
-    z[4] = fmaf(xk, w1.x, z[4]); z[5] = fmaf(xk, w1.y, z[5]);
-    z[6] = fmaf(xk, w1.z, z[6]); z[7] = fmaf(xk, w1.w, z[7]);
+    w[k][0] = w0.x; w[k][1] = w0.y; w[k][2] = w0.z; w[k][3] = w0.w;
+    w[k][4] = w1.x; w[k][5] = w1.y; w[k][6] = w1.z; w[k][7] = w1.w;
   }
-  if (z1) {
-    *(float4*)(z1 + s * W + o) = make_float4(z[0], z[1], z[2], z[3]);
-    *(float4*)(z1 + s * W + o + 4) = make_float4(z[4], z[5], z[6], z[7]);
-  }
-  __align__(16) __nv_bfloat162 hv[4];
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
+    float xs[NIN];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) hv[j] = __floats2bfloat162_rn(silu(z[2 * j]), silu(z[2 * j + 1]));
-  *(uint4*)(h1 + s * W + o) = *(const uint4*)hv;
+    for (int k = 0; k < NIN; ++k) xs[k] = x[s * NIN + k];
+    float z[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) z[j] = b[j];
+#pragma unroll
+    for (int k = 0; k < NIN; ++k)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) z[j] = fmaf(xs[k], w[k][j], z[j]);
+    if (z1) {
+      *(float4*)(z1 + s * W + o) = make_float4(z[0], z[1], z[2], z[3]);
+      *(float4*)(z1 + s * W + o + 4) = make_float4(z[4], z[5], z[6], z[7]);
+    }
+    __align__(16) __nv_bfloat162 hv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hv[j] = __floats2bfloat162_rn(silu(z[2 * j]), silu(z[2 * j + 1]));
+    *(uint4*)(h1 + s * W + o) = *(const uint4*)hv;
+  }
 }
-
-// output layer y = h4 . w5 + b5; one warp per sample
-__global__ void gl_mlp_out_kernel(const __nv_bfloat16* __restrict__ h4, const float* __restrict__ p,
-                                  float* __restrict__ y, int64_t n) {
-  // one warp per sample: each lane reads 8 consecutive activations (one 16-byte
-  // load), then the lanes' partial sums are added by a fixed shuffle tree
-  int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (s >= n) return;
-  const uint4 hq = *(const uint4*)(h4 + s * W + 8 * lane);
-  const __nv_bfloat162* hp = (const __nv_bfloat162*)&hq;
+// Output layer: lane l keeps w5[8 l .. 8 l + 7] in registers and the warp walks
+// over samples: one 16-byte load of 8 activations per lane, then the lanes'
+// partial sums added by a fixed shuffle tree.
+__global__ void __launch_bounds__(128) gl_mlp_out_kernel(const __nv_bfloat16* __restrict__ h4,
+                                                         const float* __restrict__ p,
+                                                         float* __restrict__ y, int64_t n) {
+  const int lane = threadIdx.x & 31;
   const float4 w0 = *(const float4*)(p + OFF_W5 + 8 * lane);
   const float4 w1 = *(const float4*)(p + OFF_W5 + 8 * lane + 4);
-  const float2 h01 = __bfloat1622float2(hp[0]), h23 = __bfloat1622float2(hp[1]);
-  const float2 h45 = __bfloat1622float2(hp[2]), h67 = __bfloat1622float2(hp[3]);
-  float acc = h01.x * w0.x;
-  acc = fmaf(h01.y, w0.y, acc);
-  acc = fmaf(h23.x, w0.z, acc);
-  acc = fmaf(h23.y, w0.w, acc);
-  acc = fmaf(h45.x, w1.x, acc);
-  acc = fmaf(h45.y, w1.y, acc);
-  acc = fmaf(h67.x, w1.z, acc);
-  acc = fmaf(h67.y, w1.w, acc);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[s] = acc + p[OFF_B5];
+  const float b5 = p[OFF_B5];
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
+    const uint4 hq = *(const uint4*)(h4 + s * W + 8 * lane);
+    const __nv_bfloat162* hp = (const __nv_bfloat162*)&hq;
+    const float2 h01 = __bfloat1622float2(hp[0]), h23 = __bfloat1622float2(hp[1]);
+    const float2 h45 = __bfloat1622float2(hp[2]), h67 = __bfloat1622float2(hp[3]);
+    float acc = h01.x * w0.x;
+    acc = fmaf(h01.y, w0.y, acc);
+    acc = fmaf(h23.x, w0.z, acc);
+    acc = fmaf(h23.y, w0.w, acc);
+    acc = fmaf(h45.x, w1.x, acc);
+    acc = fmaf(h45.y, w1.y, acc);
+    acc = fmaf(h67.x, w1.z, acc);
+    acc = fmaf(h67.y, w1.w, acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) y[s] = acc + b5;
+  }
 }
 
 // output-layer backward, per sample: r = y - t, dy = 2 r / n, rr = r^2 / n,
@@ -758,6 +771,10 @@ struct gl_mlp {
   float* tb = nullptr;         // [bcap]
   double* d_lsum = nullptr;    // sum of the mini-batch losses of a call
   unsigned* d_table = nullptr; // per-bin maximum error, as float bits
+  // kernel timing (gl_mlp_profile): event pairs per kernel kind
+  bool prof = false;
+  std::vector<cudaEvent_t> pev[GL_MLP_KERNEL_KINDS];
+  size_t pused[GL_MLP_KERNEL_KINDS] = {};
 };
 
 namespace {
@@ -840,6 +857,33 @@ int make_tmap(CUtensorMap* tm, const void* base, int64_t rows, int box_rows) {
   return r == CUDA_SUCCESS ? GL_OK : GL_ECUDA;
 }
 
+// Kernel timing: the start event of a launch of `kind` (returns the pair index,
+// or -1 when timing is off, the kind's pairs are used up or an event cannot be
+// made), and its end event.
+constexpr size_t kMlpMaxTimed = 65536;
+long prof_begin(gl_mlp* m, int kind, cudaStream_t st) {
+  if (!m->prof) return -1;
+  const size_t i = m->pused[kind];
+  if (i >= kMlpMaxTimed) return -1;
+  auto& v = m->pev[kind];
+  if (v.size() < 2 * (i + 1)) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return -1;
+    }
+    v.push_back(a);
+    v.push_back(b);
+  }
+  cudaEventRecord(v[2 * i], st);
+  m->pused[kind] = i + 1;
+  return (long)i;
+}
+void prof_end(gl_mlp* m, int kind, long i, cudaStream_t st) {
+  if (i >= 0) cudaEventRecord(m->pev[kind][2 * i + 1], st);
+}
+
 int grid_for(const gl_mlp* m, int64_t n) {
   int64_t tiles = (n + TILE_M - 1) / TILE_M;
   return (int)(tiles < m->sms ? tiles : m->sms);
@@ -847,10 +891,13 @@ int grid_for(const gl_mlp* m, int64_t n) {
 
 // One tensor-core layer over n rows (g.a: [n][256] BF16, g.b: [256][256] BF16).
 template <int EPI>
-int launch_gemm(const gl_mlp* m, const GemmArgs& g, int64_t n, cudaStream_t st) {
+int launch_gemm(gl_mlp* m, const GemmArgs& g, int64_t n, cudaStream_t st) {
   alignas(64) CUtensorMap ta, tb;
   if (make_tmap(&ta, g.a, n, TILE_M) || make_tmap(&tb, g.b, W, W)) return GL_ECUDA;
+  const int kind = EPI == EPI_BWD ? GL_MLP_KERNEL_GEMM_BWD : GL_MLP_KERNEL_GEMM_FWD;
+  const long pe = prof_begin(m, kind, st);
   gl_mlp_gemm_kernel<EPI><<<grid_for(m, n), GEMM_THREADS, GEMM_SMEM, st>>>(g, ta, tb);
+  prof_end(m, kind, pe, st);
   return GL_OK;
 }
 
@@ -869,9 +916,11 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
   if (rc) return rc;
   if ((rc = mlp_attrs(m))) return rc;
   const int64_t cs = m->cap * W;
-  int64_t nth = n * (W / 8);
-  gl_mlp_in_kernel<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(x, m->p, train ? m->z : nullptr,
-                                                                  m->h, n);
+  // (a few resident blocks per SM: each warp's weight loads serve several samples)
+  const unsigned lgrid = (unsigned)std::min<int64_t>((n + 3) / 4, (int64_t)m->sms * 6);
+  long pe = prof_begin(m, GL_MLP_KERNEL_IN, st);
+  gl_mlp_in_kernel<<<lgrid, 128, 0, st>>>(x, m->p, train ? m->z : nullptr, m->h, n);
+  prof_end(m, GL_MLP_KERNEL_IN, pe, st);
   for (int l = 2; l <= 4; ++l) {
     GemmArgs g;
     memset(&g, 0, sizeof g);
@@ -886,7 +935,9 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
     rc = train ? launch_gemm<EPI_FWD_TRAIN>(m, g, n, st) : launch_gemm<EPI_FWD_INFER>(m, g, n, st);
     if (rc) return rc;
   }
-  gl_mlp_out_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(m->h + 3 * cs, m->p, y, n);
+  pe = prof_begin(m, GL_MLP_KERNEL_OUT, st);
+  gl_mlp_out_kernel<<<lgrid, 128, 0, st>>>(m->h + 3 * cs, m->p, y, n);
+  prof_end(m, GL_MLP_KERNEL_OUT, pe, st);
   return cudaGetLastError() == cudaSuccess ? GL_OK : GL_ECUDA;
 }
 
@@ -954,6 +1005,8 @@ int gl_mlp_destroy(gl_mlp* m) {
   cudaFree(m->tb);
   cudaFree(m->d_lsum);
   cudaFree(m->d_table);
+  for (auto& v : m->pev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   delete m;
   return GL_OK;
 }
@@ -1044,7 +1097,9 @@ int mlp_loss_grad(gl_mlp* m, int64_t n, const float* x, const float* t, cudaStre
     wg.n = n;
     wg.status = m->d_status;
     const int wgrid = grid_for(m, n);
+    const long pw = prof_begin(m, GL_MLP_KERNEL_WGRAD, st);
     gl_mlp_wgrad_kernel<<<wgrid, NTHREADS, WGRAD_SMEM, st>>>(wg);
+    prof_end(m, GL_MLP_KERNEL_WGRAD, pw, st);
     partsum(wgrid, (int64_t)W * W, (int64_t)W * W, m->g + off_w(l));
     // dz_{l-1} = (dz_l W_l^T) * SiLU'(z_{l-1})
     GemmArgs g;
@@ -1091,6 +1146,29 @@ int gl_mlp_adam(gl_mlp* m, float lr, float beta1, float beta2, float eps, void* 
   if (!m || !adam_args_ok(lr, beta1, beta2, eps)) return GL_EINVAL;
   if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
   return mlp_adam(m, lr, beta1, beta2, eps, (cudaStream_t)stream);
+}
+
+int gl_mlp_profile(gl_mlp* m, int on) {
+  if (!m || on < 0 || on > 1) return GL_EINVAL;
+  m->prof = on == 1;
+  for (size_t& u : m->pused) u = 0;
+  return GL_OK;
+}
+
+int gl_mlp_profile_read(gl_mlp* m, int kind, double* ms, int64_t* launches) {
+  if (!m || !ms || !launches || kind < 0 || kind >= GL_MLP_KERNEL_KINDS) return GL_EINVAL;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GL_ECUDA;
+  double tot = 0.0;
+  for (size_t i = 0; i < m->pused[kind]; ++i) {
+    float t = 0.f;
+    if (cudaEventSynchronize(m->pev[kind][2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, m->pev[kind][2 * i], m->pev[kind][2 * i + 1]) != cudaSuccess)
+      return GL_ECUDA;
+    tot += t;
+  }
+  *ms = tot;
+  *launches = (int64_t)m->pused[kind];
+  return GL_OK;
 }
 
 int gl_mlp_status(gl_mlp* m) {

@@ -63,6 +63,9 @@ def test_null_context_is_rejected():
     assert lib.gl_sync(None, None) == binding.GL_EINVAL
     assert lib.gl_context_destroy(None) == binding.GL_OK
     assert lib.gl_context_create(None, 0) == binding.GL_EINVAL
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    assert lib.gl_mlp_profile(None, 1) == binding.GL_EINVAL
+    assert lib.gl_mlp_profile_read(None, 0, ctypes.byref(ms), ctypes.byref(n)) == binding.GL_EINVAL
 
 
 def test_context_without_gpu_fails_cleanly():

@@ -160,3 +160,26 @@ def test_training_reduces_loss(net):
         net.adam(2e-3)
         last = net.loss_grad(xd, td)
     assert last < 0.1 * first, (first, last)
+
+
+def test_kernel_timing_counts_every_launch(net):
+    """gl_mlp_profile brackets every launch of each kernel kind with events: one
+    forward (3 layer GEMMs, input and output layers) and one loss-and-gradient
+    call (another forward, 3 backward layer GEMMs, 3 weight-gradient GEMMs)."""
+    n = 700
+    _, x, t = _setup(net, 3, n)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    net.profile(True)
+    net.forward(xd, y)
+    net.loss_grad(xd, td)
+    got = [net.profile_read(k) for k in range(5)]
+    net.profile(False)
+    assert [c for _, c in got] == [6, 3, 3, 2, 2], got
+    assert all(ms > 0.0 for ms, _ in got), got
+    net.profile(True)   # enabling resets the accumulated times
+    assert net.profile_read(binding.GL_MLP_KERNEL_GEMM_FWD) == (0.0, 0)
+    net.profile(False)
+    with pytest.raises(binding.GLError):
+        net.profile_read(5)
+    assert net.status() == binding.GL_OK
