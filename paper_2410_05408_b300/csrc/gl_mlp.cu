@@ -771,6 +771,16 @@ struct gl_mlp {
   float* tb = nullptr;         // [bcap]
   double* d_lsum = nullptr;    // sum of the mini-batch losses of a call
   unsigned* d_table = nullptr; // per-bin maximum error, as float bits
+  // encoded tensor maps of the layer GEMMs' operands, by (base, rows, box rows):
+  // the buffers are reused from call to call, and an encode is host work in
+  // front of every launch
+  struct TmapEntry {
+    alignas(64) CUtensorMap tm;
+    const void* base;
+    int64_t rows;
+    int box;
+  };
+  std::vector<TmapEntry> tmaps;
   // kernel timing (gl_mlp_profile): event pairs per kernel kind
   bool prof = false;
   std::vector<cudaEvent_t> pev[GL_MLP_KERNEL_KINDS];
@@ -890,10 +900,34 @@ int grid_for(const gl_mlp* m, int64_t n) {
 }
 
 // One tensor-core layer over n rows (g.a: [n][256] BF16, g.b: [256][256] BF16).
+// The tensor map of (base, rows, box_rows) from the network's cache, encoded on
+// first use (NULL on an encode failure).  A map depends on nothing but its key
+// (the row stride, type and swizzle are fixed), so an entry stays valid when a
+// buffer is freed and another one later takes its address.  The pointer is
+// valid until the next call.
+const CUtensorMap* cached_tmap(gl_mlp* m, const void* base, int64_t rows, int box_rows) {
+  for (const auto& e : m->tmaps)
+    if (e.base == base && e.rows == rows && e.box == box_rows) return &e.tm;
+  gl_mlp::TmapEntry e;
+  if (make_tmap(&e.tm, base, rows, box_rows)) return nullptr;
+  e.base = base;
+  e.rows = rows;
+  e.box = box_rows;
+  if (m->tmaps.size() >= 64) m->tmaps.clear();   // (shapes change rarely)
+  m->tmaps.push_back(e);
+  return &m->tmaps.back().tm;
+}
+
 template <int EPI>
 int launch_gemm(gl_mlp* m, const GemmArgs& g, int64_t n, cudaStream_t st) {
+  // (each map copied before the next lookup, which may grow the cache)
   alignas(64) CUtensorMap ta, tb;
-  if (make_tmap(&ta, g.a, n, TILE_M) || make_tmap(&tb, g.b, W, W)) return GL_ECUDA;
+  const CUtensorMap* pa = cached_tmap(m, g.a, n, TILE_M);
+  if (!pa) return GL_ECUDA;
+  ta = *pa;
+  const CUtensorMap* pb = cached_tmap(m, g.b, W, W);
+  if (!pb) return GL_ECUDA;
+  tb = *pb;
   const int kind = EPI == EPI_BWD ? GL_MLP_KERNEL_GEMM_BWD : GL_MLP_KERNEL_GEMM_FWD;
   const long pe = prof_begin(m, kind, st);
   gl_mlp_gemm_kernel<EPI><<<grid_for(m, n), GEMM_THREADS, GEMM_SMEM, st>>>(g, ta, tb);
