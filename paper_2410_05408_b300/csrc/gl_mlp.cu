@@ -405,6 +405,222 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
+// The three tensor-core layers of the forward pass in one kernel, one 128-row tile
+// at a time:
+//   warp 0   TMA producer: the tile's input activations (4 boxes of 64 x 128),
+//            then each layer's weights (4 boxes of 64 x 256, 128 KB), the next
+//            layer's as soon as the previous layer's MMAs have completed (the
+//            weights buffer is then free), i.e. while its epilogue runs
+//   warp 1   MMA issuer (one thread): 16 tcgen05.mma per layer into one TMEM
+//            accumulator (256 columns), once the layer's input is in shared
+//            memory and the previous epilogue has read the accumulator
+//   warps 2-9 epilogue: bias + SiLU of the accumulator, written as BF16 into the
+//            activation buffer in the same 128-byte-swizzled K-major layout the
+//            TMA writes (row r, 16-byte unit u of a 64-column chunk at
+//            r * 128 + ((u ^ (r mod 8)) * 16)), so that the next layer reads it
+//            where it is; to global memory only what the caller keeps (training:
+//            z and h of every layer; inference: h of the last layer)
+// Layer L of the CTA (L = 3 t + l, tile t, layer l) completes each barrier once,
+// so every wait is on the parity of a completion count; a barrier cannot run two
+// completions ahead of its waiter, because each completion needs the waiter's
+// own next step.  Every wait is bounded; a role that gives up sets the abort
+// flag, and before TMEM is freed the CTA waits, again with a bound, for the
+// copies and MMAs it issued.
+struct Fwd3Args {
+  const float* bias[3];       // b2, b3, b4
+  float* zout[3];             // training: pre-activations of layers 2-4 [n][256]
+  __nv_bfloat16* hout[3];     // SiLU of layers 2-4 [n][256] (inference: the last only)
+  int64_t n;
+  int* status;
+  int probe_polls;            // > 0: failure-detection probe (gl_mlp_wait_probe)
+};
+
+template <bool TRAIN>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    gl_mlp_fwd3_kernel(Fwd3Args g, const __grid_constant__ CUtensorMap tmA,
+                       const __grid_constant__ CUtensorMap tmB0,
+                       const __grid_constant__ CUtensorMap tmB1,
+                       const __grid_constant__ CUtensorMap tmB2) {
+  extern __shared__ uint8_t sm_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sB = sm;                  // one layer's weights: 4 x 32 KB
+  uint8_t* sA = sm + 4 * kBChunk;    // the tile's activations: 4 K-chunks of 16 KB
+  __shared__ __align__(8) uint64_t bar_b[4], a_full, acc_full, epi_done, drain;
+  __shared__ float s_bias[3][W];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (g.n + TILE_M - 1) / TILE_M;
+  if ((int64_t)blockIdx.x >= ntiles) return;
+  const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int nlay = 3 * my_tiles;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int c = 0; c < 4; ++c) mbar_init(&bar_b[c], 1);
+    mbar_init(&a_full, 1);
+    mbar_init(&acc_full, 1);
+    mbar_init(&epi_done, 8);
+    mbar_init(&drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) s_bias[i / W][i % W] = g.bias[i / W][i % W];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  int a_loads = 0, b_loads = 0;   // producer: copies issued
+  int committed = 0;              // MMA thread: layers committed
+  bool mma_open = false;          // MMA thread: MMAs issued since the last commit
+  if (g.probe_polls > 0) {
+    // Failure-detection probe: before any copy or MMA is issued, wait on the
+    // first phase of the epilogue barrier, which nothing completes, for
+    // probe_polls polls; the CTA records the timeout like any bounded wait that
+    // ran out and leaves through the normal exit.
+    const uint32_t done = mbar_wait(&epi_done, 0, g.probe_polls);
+    if (threadIdx.x == 0) {
+      if (!done) atomicOr(g.status, 1);
+      s_abort = 1;
+    }
+  } else if (warp == 0) {
+    if (lane == 0) {
+      const CUtensorMap* tmB[3] = {&tmB0, &tmB1, &tmB2};
+      for (int L = 0; L < nlay && !s_abort; ++L) {
+        const int t = L / 3, l = L % 3;
+        // the weights buffer, and for a new tile the activations, are free once
+        // the previous layer's MMAs have completed
+        if (L > 0 && !mbar_wait_ab(&acc_full, (uint32_t)(L - 1) & 1u, &s_abort)) {
+          s_abort = 1;
+          break;
+        }
+        if (l == 0) {
+          const int row0 = (int)((blockIdx.x + (int64_t)t * gridDim.x) * TILE_M);
+          mbar_expect_tx(&a_full, 4 * kAChunk);
+          for (int c = 0; c < 4; ++c) tma_load_2d(sA + c * kAChunk, &tmA, c * 64, row0, &a_full);
+          ++a_loads;
+        }
+        for (int c = 0; c < 4; ++c) {
+          mbar_expect_tx(&bar_b[c], kBChunk);
+          tma_load_2d(sB + c * kBChunk, tmB[l], c * 64, 0, &bar_b[c]);
+        }
+        ++b_loads;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(TILE_M, W);
+      bool ok = true;
+      for (int L = 0; ok && L < nlay && !s_abort; ++L) {
+        const int t = L / 3, l = L % 3;
+        // input: by TMA for a tile's first layer, else by the previous epilogue,
+        // which has also read the accumulator by the time it signals
+        if (l == 0 && !mbar_wait_ab(&a_full, (uint32_t)t & 1u, &s_abort)) {
+          ok = false;
+          break;
+        }
+        if (L > 0 && !mbar_wait_ab(&epi_done, (uint32_t)(L - 1) & 1u, &s_abort)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int ks = 0; ks < 16; ++ks) {
+          const int kc = ks >> 2;
+          if ((ks & 3) == 0 && !mbar_wait_ab(&bar_b[kc], (uint32_t)L & 1u, &s_abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t within = (uint32_t)(ks & 3) * 32u;
+          mma_bf16(tmem, umma_desc_sw128(smem_u32(sA) + kc * kAChunk + within),
+                   umma_desc_sw128(smem_u32(sB) + kc * kBChunk + within), idesc, ks != 0);
+          mma_open = true;
+        }
+        if (!ok) break;
+        mma_commit(&acc_full);
+        mma_open = false;
+        committed = L + 1;
+      }
+      if (!ok) s_abort = 1;
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (those rows of the
+    // tile) and columns 128 ((w - 2) / 4) .. + 127
+    const int q = warp & 3, c0 = ((warp - 2) >> 2) * 128;
+    const int r = q * 32 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+    for (int L = 0; L < nlay; ++L) {
+      const int t = L / 3, l = L % 3;
+      uint32_t done = 0;
+      if (lane == 0) done = mbar_wait_ab(&acc_full, (uint32_t)L & 1u, &s_abort);
+      done = __shfl_sync(0xffffffffu, done, 0);
+      if (!done) {
+        if (lane == 0) s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int64_t row = (blockIdx.x + (int64_t)t * gridDim.x) * TILE_M + r;
+      const float* bias = s_bias[l];
+      for (int c = c0; c < c0 + 128; c += 32) {
+        uint32_t acc[32];
+        tmem_ld32(taddr + (uint32_t)c, acc);
+        __align__(16) float zv[32];
+        __align__(16) __nv_bfloat162 hv[16];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) zv[j] = __uint_as_float(acc[j]) + bias[c + j];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hv[j] = __floats2bfloat162_rn(silu(zv[2 * j]), silu(zv[2 * j + 1]));
+        if (row < g.n) {
+          if (TRAIN) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+              *(float4*)(g.zout[l] + row * W + c + 4 * v) = *(const float4*)(zv + 4 * v);
+          }
+          if (TRAIN || l == 2) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              *(uint4*)(g.hout[l] + row * W + c + 8 * v) = *(const uint4*)(hv + 4 * v);
+          }
+        }
+        if (l < 2) {
+          // the next layer's input, in place (rows past n are never stored)
+          uint8_t* rb = sA + (c >> 6) * kAChunk + r * 128;
+          const int u0 = (c & 63) >> 3;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            *(uint4*)(rb + (((u0 + j) ^ (r & 7)) << 4)) = *(const uint4*)(hv + 4 * j);
+        }
+      }
+      // the generic-proxy stores become visible to the tensor cores' reads
+      if (l < 2) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&epi_done);
+    }
+  }
+  __syncthreads();
+  // drain: nothing the CTA issued may still be in flight when TMEM is freed
+  // (each barrier has at most its last copy outstanding: a copy is issued only
+  // after the previous one on that barrier was consumed)
+  if (warp == 0 && lane == 0) {
+    if (b_loads > 0)
+      for (int c = 0; c < 4; ++c) mbar_wait(&bar_b[c], (uint32_t)(b_loads - 1) & 1u);
+    if (a_loads > 0) mbar_wait(&a_full, (uint32_t)(a_loads - 1) & 1u);
+  }
+  if (warp == 1 && lane == 0 && mma_open) {
+    mma_commit(&drain);
+    mbar_wait(&drain, 0);
+  }
+  if (warp == 1 && lane == 0 && committed > 0 && s_abort)
+    mbar_wait(&acc_full, (uint32_t)(committed - 1) & 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
 struct WgradArgs {
   const __nv_bfloat16* a;    // layer input activations [n][256]
   const __nv_bfloat16* dz;   // layer output gradient [n][256]
@@ -826,6 +1042,10 @@ int mlp_attrs(gl_mlp* m) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(gl_mlp_gemm_kernel<EPI_BWD>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(gl_mlp_fwd3_kernel<true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(gl_mlp_fwd3_kernel<false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(gl_mlp_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)WGRAD_SMEM) != cudaSuccess)
     return GL_ECUDA;
@@ -935,6 +1155,28 @@ int launch_gemm(gl_mlp* m, const GemmArgs& g, int64_t n, cudaStream_t st) {
   return GL_OK;
 }
 
+// The three tensor-core layers of the forward pass (f: biases and outputs; the
+// input is the first layer's activations m->h, the weights m->wt).
+int launch_fwd3(gl_mlp* m, const Fwd3Args& f, bool train, int64_t n, cudaStream_t st) {
+  alignas(64) CUtensorMap ta, tb[3];
+  const CUtensorMap* pm = cached_tmap(m, m->h, n, TILE_M);
+  if (!pm) return GL_ECUDA;
+  ta = *pm;
+  for (int l = 0; l < 3; ++l) {
+    if (!(pm = cached_tmap(m, m->wt + (int64_t)l * W * W, W, W))) return GL_ECUDA;
+    tb[l] = *pm;
+  }
+  const long pe = prof_begin(m, GL_MLP_KERNEL_GEMM_FWD, st);
+  if (train)
+    gl_mlp_fwd3_kernel<true><<<grid_for(m, n), GEMM_THREADS, GEMM_SMEM, st>>>(f, ta, tb[0], tb[1],
+                                                                             tb[2]);
+  else
+    gl_mlp_fwd3_kernel<false><<<grid_for(m, n), GEMM_THREADS, GEMM_SMEM, st>>>(f, ta, tb[0], tb[1],
+                                                                              tb[2]);
+  prof_end(m, GL_MLP_KERNEL_GEMM_FWD, pe, st);
+  return GL_OK;
+}
+
 bool dev_ptr(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -955,20 +1197,17 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
   long pe = prof_begin(m, GL_MLP_KERNEL_IN, st);
   gl_mlp_in_kernel<<<lgrid, 128, 0, st>>>(x, m->p, train ? m->z : nullptr, m->h, n);
   prof_end(m, GL_MLP_KERNEL_IN, pe, st);
-  for (int l = 2; l <= 4; ++l) {
-    GemmArgs g;
-    memset(&g, 0, sizeof g);
-    g.a = m->h + (l - 2) * cs;
-    g.b = m->wt + (int64_t)(l - 2) * W * W;
-    g.bias = m->p + off_b(l);
-    g.zout = m->z + (l - 1) * cs;
-    g.hout = m->h + (l - 1) * cs;
-    g.n = n;
-    g.status = m->d_status;
-    g.probe_polls = m->probe_polls;
-    rc = train ? launch_gemm<EPI_FWD_TRAIN>(m, g, n, st) : launch_gemm<EPI_FWD_INFER>(m, g, n, st);
-    if (rc) return rc;
+  Fwd3Args f;
+  memset(&f, 0, sizeof f);
+  for (int l = 0; l < 3; ++l) {
+    f.bias[l] = m->p + off_b(l + 2);
+    f.zout[l] = train ? m->z + (l + 1) * cs : nullptr;
+    f.hout[l] = m->h + (l + 1) * cs;
   }
+  f.n = n;
+  f.status = m->d_status;
+  f.probe_polls = m->probe_polls;
+  if ((rc = launch_fwd3(m, f, train, n, st))) return rc;
   pe = prof_begin(m, GL_MLP_KERNEL_OUT, st);
   gl_mlp_out_kernel<<<lgrid, 128, 0, st>>>(m->h + 3 * cs, m->p, y, n);
   prof_end(m, GL_MLP_KERNEL_OUT, pe, st);
