@@ -497,7 +497,7 @@ def surrogate_train_arm(args):
     i_ms, i_n = mlp.profile_read(binding.GL_MLP_KERNEL_IN)
     o_ms, o_n = mlp.profile_read(binding.GL_MLP_KERNEL_OUT)
     mlp.profile(False)
-    gemm_ms = g_ms / max(g_n, 1)   # one launch: the three hidden layers
+    gemm_ms = g_ms / 20            # per forward (one launch at this batch)
     gemm_tf = fb * 3 * 2 * 256 * 256 / (gemm_ms * 1e-3) / 1e12
     burst = peaks.get("bf16_tflops", 1718.5)
     line = {"metric": "surrogate training samples/sec (forward + backward + Adam)",

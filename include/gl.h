@@ -385,9 +385,10 @@ int gl_mlp_adam(gl_mlp *m, float lr, float beta1, float beta2, float eps, void *
 int gl_mlp_status(gl_mlp *m);
 
 /* Kernel kinds for gl_mlp_profile_read. */
-#define GL_MLP_KERNEL_GEMM_FWD 0 /* the forward pass's tensor-core kernel: its three hidden
-                                    layers (D = A B^T, bias, SiLU; 3 x 2 x rows x 256 x 256
-                                    flops per launch) */
+#define GL_MLP_KERNEL_GEMM_FWD 0 /* the forward pass's tensor-core work (D = A B^T, bias,
+                                    SiLU; 3 x 2 x rows x 256 x 256 flops per forward): one
+                                    launch for the three hidden layers when the batch has
+                                    at most one 128-row tile per SM, else one per layer */
 #define GL_MLP_KERNEL_GEMM_BWD 1 /* a tensor-core layer of the backward pass (dZ W, SiLU') */
 #define GL_MLP_KERNEL_WGRAD 2    /* a weight-gradient GEMM (A^T dZ, partial per CTA) */
 #define GL_MLP_KERNEL_IN 3       /* the CUDA-core input layer (7 -> 256, SiLU) */

@@ -9,13 +9,16 @@
 // in tensor memory.  The 7-wide input layer, the 1-wide output layer, the
 // biases, the loss and Adam run on CUDA cores in FP32.
 //
-// Tensor-core kernels (one CTA per SM, accumulators in TMEM):
+// Tensor-core kernels (one CTA per SM, accumulators in TMEM, operands moved by
+// TMA in the 128-byte-swizzled K-major layout, warp specialised: loads, MMA
+// issue, eight epilogue warps):
+//   gl_mlp_fwd3_kernel   the three hidden layers of the forward pass per 128-row
+//                        tile, each layer's activations kept in shared memory
+//                        for the next (batches of at most one tile per SM)
 //   gl_mlp_gemm_kernel   D[128 x 256] = A[128 x 256] B[256 x 256] per row tile,
-//                        operands moved by TMA in the 128-byte-swizzled K-major
-//                        layout, weights resident in shared memory, warp
-//                        specialised (loads, MMA issue, eight epilogue warps);
-//                        epilogue: forward (z = D + b, h = SiLU(z)) or backward
-//                        (dz_prev = D * SiLU'(z_prev))
+//                        one layer, weights resident in shared memory while the
+//                        tiles overlap; epilogue: forward (z = D + b, h = SiLU(z);
+//                        larger batches) or backward (dz_prev = D * SiLU'(z_prev))
 //   gl_mlp_wgrad_kernel  dW[256 x 256] += A^T dZ over row tiles (two M = 128
 //                        accumulators, 512 TMEM columns; operands staged in the
 //                        K-major no-swizzle core-matrix layout), then added to
@@ -991,7 +994,7 @@ struct gl_mlp {
   // the buffers are reused from call to call, and an encode is host work in
   // front of every launch
   struct TmapEntry {
-    alignas(64) CUtensorMap tm;
+    CUtensorMap tm;   // (the type carries its own alignment)
     const void* base;
     int64_t rows;
     int box;
@@ -1197,17 +1200,39 @@ int mlp_forward(gl_mlp* m, int64_t n, const float* x, float* y, bool train, cuda
   long pe = prof_begin(m, GL_MLP_KERNEL_IN, st);
   gl_mlp_in_kernel<<<lgrid, 128, 0, st>>>(x, m->p, train ? m->z : nullptr, m->h, n);
   prof_end(m, GL_MLP_KERNEL_IN, pe, st);
-  Fwd3Args f;
-  memset(&f, 0, sizeof f);
-  for (int l = 0; l < 3; ++l) {
-    f.bias[l] = m->p + off_b(l + 2);
-    f.zout[l] = train ? m->z + (l + 1) * cs : nullptr;
-    f.hout[l] = m->h + (l + 1) * cs;
+  if ((n + TILE_M - 1) / TILE_M <= m->sms) {
+    // at most one tile per SM: the three layers in one kernel, each layer's
+    // activations kept on chip for the next
+    Fwd3Args f;
+    memset(&f, 0, sizeof f);
+    for (int l = 0; l < 3; ++l) {
+      f.bias[l] = m->p + off_b(l + 2);
+      f.zout[l] = train ? m->z + (l + 1) * cs : nullptr;
+      f.hout[l] = m->h + (l + 1) * cs;
+    }
+    f.n = n;
+    f.status = m->d_status;
+    f.probe_polls = m->probe_polls;
+    if ((rc = launch_fwd3(m, f, train, n, st))) return rc;
+  } else {
+    // several tiles per SM: one kernel per layer, whose weights stay resident
+    // while the tiles' loads, MMAs and epilogues overlap (the fused kernel would
+    // load every layer's weights again for each tile)
+    for (int l = 2; l <= 4; ++l) {
+      GemmArgs g;
+      memset(&g, 0, sizeof g);
+      g.a = m->h + (l - 2) * cs;
+      g.b = m->wt + (int64_t)(l - 2) * W * W;
+      g.bias = m->p + off_b(l);
+      g.zout = m->z + (l - 1) * cs;
+      g.hout = m->h + (l - 1) * cs;
+      g.n = n;
+      g.status = m->d_status;
+      g.probe_polls = m->probe_polls;
+      rc = train ? launch_gemm<EPI_FWD_TRAIN>(m, g, n, st) : launch_gemm<EPI_FWD_INFER>(m, g, n, st);
+      if (rc) return rc;
+    }
   }
-  f.n = n;
-  f.status = m->d_status;
-  f.probe_polls = m->probe_polls;
-  if ((rc = launch_fwd3(m, f, train, n, st))) return rc;
   pe = prof_begin(m, GL_MLP_KERNEL_OUT, st);
   gl_mlp_out_kernel<<<lgrid, 128, 0, st>>>(m->h + 3 * cs, m->p, y, n);
   prof_end(m, GL_MLP_KERNEL_OUT, pe, st);

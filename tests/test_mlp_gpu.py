@@ -184,3 +184,24 @@ def test_kernel_timing_counts_every_launch(net):
     with pytest.raises(binding.GLError):
         net.profile_read(5)
     assert net.status() == binding.GL_OK
+
+
+def test_large_batch_rows_match_the_fused_kernel(net):
+    """Batches of more than one 128-row tile per SM run one tensor-core kernel per
+    layer; at most one, a single kernel for the three layers.  Both do the same
+    arithmetic on each row, so a row's output is the same bits either way."""
+    props = torch.cuda.get_device_properties(0)
+    n_big = props.multi_processor_count * 128 + 1000
+    _, x, _ = _setup(net, 4, n_big)
+    xd = torch.tensor(x, device="cuda")
+    y_big = torch.empty(n_big, dtype=torch.float32, device="cuda")
+    y_small = torch.empty(1000, dtype=torch.float32, device="cuda")
+    net.profile(True)
+    net.forward(xd, y_big)
+    _, launches = net.profile_read(binding.GL_MLP_KERNEL_GEMM_FWD)
+    net.profile(False)
+    assert launches == 3                      # one per layer
+    net.forward(xd[:1000], y_small)
+    assert np.array_equal(y_big[:1000].cpu().numpy(), y_small.cpu().numpy())
+    assert np.isfinite(y_big.cpu().numpy()).all()
+    assert net.status() == binding.GL_OK
