@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint8_t* sB = sm;                  // 4 x 32 KB
   uint8_t* sA = sm + 4 * kBChunk;    // stage h: 2 x 16 KB at sA + h * 2 * kAChunk
   __shared__ __align__(8) uint64_t bar_b[4], full[2], empty[2], tfull[2], tempty[2], drain;
-  __shared__ float s_bias[8][128];   // each epilogue warp's copy of its half of the bias
+  __shared__ __align__(16) float s_bias[8][128];   // each epilogue warp's copy of its half of the bias
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -371,7 +371,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           } else {
             __align__(16) float zv[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) zv[j] = __uint_as_float(acc[j]) + bias[c - c0 + j];
+            for (int v = 0; v < 8; ++v) {
+              const float4 b4 = *(const float4*)(bias + c - c0 + 4 * v);
+              zv[4 * v] = __uint_as_float(acc[4 * v]) + b4.x;
+              zv[4 * v + 1] = __uint_as_float(acc[4 * v + 1]) + b4.y;
+              zv[4 * v + 2] = __uint_as_float(acc[4 * v + 2]) + b4.z;
+              zv[4 * v + 3] = __uint_as_float(acc[4 * v + 3]) + b4.w;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) hv[j] = __floats2bfloat162_rn(silu(zv[2 * j]), silu(zv[2 * j + 1]));
             if (EPI == EPI_FWD_TRAIN) {
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint8_t* sB = sm;                  // one layer's weights: 4 x 32 KB
   uint8_t* sA = sm + 4 * kBChunk;    // the tile's activations: 4 K-chunks of 16 KB
   __shared__ __align__(8) uint64_t bar_b[4], a_full, acc_full, epi_done, drain;
-  __shared__ float s_bias[3][W];
+  __shared__ __align__(16) float s_bias[3][W];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -571,8 +577,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         tmem_ld32(taddr + (uint32_t)c, acc);
         __align__(16) float zv[32];
         __align__(16) __nv_bfloat162 hv[16];
+        // (the bias four at a time: fewer shared-memory loads beside the copies
+        // landing there)
 #pragma unroll
-        for (int j = 0; j < 32; ++j) zv[j] = __uint_as_float(acc[j]) + bias[c + j];
+        for (int v = 0; v < 8; ++v) {
+          const float4 b4 = *(const float4*)(bias + c + 4 * v);
+          zv[4 * v] = __uint_as_float(acc[4 * v]) + b4.x;
+          zv[4 * v + 1] = __uint_as_float(acc[4 * v + 1]) + b4.y;
+          zv[4 * v + 2] = __uint_as_float(acc[4 * v + 2]) + b4.z;
+          zv[4 * v + 3] = __uint_as_float(acc[4 * v + 3]) + b4.w;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) hv[j] = __floats2bfloat162_rn(silu(zv[2 * j]), silu(zv[2 * j + 1]));
         if (row < g.n) {
