@@ -778,10 +778,18 @@ __global__ void __launch_bounds__(128) gl_mlp_in_kernel(const float* __restrict_
     w[k][4] = w1.x; w[k][5] = w1.y; w[k][6] = w1.z; w[k][7] = w1.w;
   }
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
+  int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  // the next sample's inputs are loaded while this one is computed
+  float xn[NIN];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) xn[k] = s < n ? x[s * NIN + k] : 0.f;
+  for (; s < n; s += nw) {
     float xs[NIN];
 #pragma unroll
-    for (int k = 0; k < NIN; ++k) xs[k] = x[s * NIN + k];
+    for (int k = 0; k < NIN; ++k) {
+      xs[k] = xn[k];
+      xn[k] = s + nw < n ? x[(s + nw) * NIN + k] : 0.f;
+    }
     float z[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) z[j] = b[j];
@@ -810,8 +818,12 @@ __global__ void __launch_bounds__(128) gl_mlp_out_kernel(const __nv_bfloat16* __
   const float4 w1 = *(const float4*)(p + OFF_W5 + 8 * lane + 4);
   const float b5 = p[OFF_B5];
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n; s += nw) {
-    const uint4 hq = *(const uint4*)(h4 + s * W + 8 * lane);
+  int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  // the next sample's activations are loaded while this one is reduced
+  uint4 hn = s < n ? *(const uint4*)(h4 + s * W + 8 * lane) : make_uint4(0u, 0u, 0u, 0u);
+  for (; s < n; s += nw) {
+    const uint4 hq = hn;
+    if (s + nw < n) hn = *(const uint4*)(h4 + (s + nw) * W + 8 * lane);
     const __nv_bfloat162* hp = (const __nv_bfloat162*)&hq;
     const float2 h01 = __bfloat1622float2(hp[0]), h23 = __bfloat1622float2(hp[1]);
     const float2 h45 = __bfloat1622float2(hp[2]), h67 = __bfloat1622float2(hp[3]);
