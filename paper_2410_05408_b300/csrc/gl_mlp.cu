@@ -472,7 +472,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) s_bias[i / W][i % W] = g.bias[i / W][i % W];
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
         smem_u32(&tmem_base)));
@@ -560,6 +559,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int q = warp & 3, c0 = ((warp - 2) >> 2) * 128;
     const int r = q * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+    // the biases, staged by the epilogue warps alone (the copies and the MMAs
+    // start meanwhile), then a barrier among these eight warps
+    for (int i = threadIdx.x - 64; i < 3 * W; i += 256) s_bias[i / W][i % W] = g.bias[i / W][i % W];
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     for (int L = 0; L < nlay; ++L) {
       const int t = L / 3, l = L % 3;
       uint32_t done = 0;
