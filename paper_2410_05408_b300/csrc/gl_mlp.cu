@@ -456,6 +456,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint8_t* sA = sm + 4 * kBChunk;    // the tile's activations: 4 K-chunks of 16 KB
   __shared__ __align__(8) uint64_t bar_b[4], a_full, acc_full, epi_done, drain;
   __shared__ __align__(16) float s_bias[3][W];
+  // per epilogue warp: 32 rows x 16 words (+1 against bank conflicts), through
+  // which its global stores go out as contiguous row segments
+  __shared__ __align__(16) uint32_t s_stage[8][32 * 17];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -592,18 +595,33 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) hv[j] = __floats2bfloat162_rn(silu(zv[2 * j]), silu(zv[2 * j + 1]));
-        if (row < g.n) {
-          if (TRAIN) {
+        // global stores through the warp's staging rows: each lane writes its
+        // row's 16 words, then the warp stores 8 rows x 64 bytes per instruction
+        // (lane: row 8 k + lane / 4, bytes 16 (lane mod 4) .. + 15)
+        auto store16 = [&](const uint32_t* w16, char* dst_row0, int64_t row_bytes) {
+          uint32_t* stg = s_stage[warp - 2];
 #pragma unroll
-            for (int v = 0; v < 8; ++v)
-              *(float4*)(g.zout[l] + row * W + c + 4 * v) = *(const float4*)(zv + 4 * v);
-          }
-          if (TRAIN || l == 2) {
+          for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = w16[j];
+          __syncwarp();
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-              *(uint4*)(g.hout[l] + row * W + c + 8 * v) = *(const uint4*)(hv + 4 * v);
+          for (int k = 0; k < 4; ++k) {
+            const int rr = 8 * k + (lane >> 2), cc = (lane & 3) * 4;
+            if (row - r + q * 32 + rr < g.n) {
+              const uint4 v = make_uint4(stg[rr * 17 + cc], stg[rr * 17 + cc + 1],
+                                         stg[rr * 17 + cc + 2], stg[rr * 17 + cc + 3]);
+              *(uint4*)(dst_row0 + (int64_t)rr * row_bytes + cc * 4) = v;
+            }
           }
+          __syncwarp();
+        };
+        // (row - r + q * 32 is the warp's first row)
+        if (TRAIN) {
+          char* z0 = (char*)(g.zout[l] + (row - r + q * 32) * W + c);
+          store16((const uint32_t*)zv, z0, (int64_t)W * 4);
+          store16((const uint32_t*)zv + 16, z0 + 64, (int64_t)W * 4);
         }
+        if (TRAIN || l == 2)
+          store16((const uint32_t*)hv, (char*)(g.hout[l] + (row - r + q * 32) * W + c), (int64_t)W * 2);
         if (l < 2) {
           // the next layer's input, in place (rows past n are never stored)
           uint8_t* rb = sA + (c >> 6) * kAChunk + r * 128;
