@@ -228,6 +228,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint8_t* sA = sm + 4 * kBChunk;    // stage h: 2 x 16 KB at sA + h * 2 * kAChunk
   __shared__ __align__(8) uint64_t bar_b[4], full[2], empty[2], tfull[2], tempty[2], drain;
   __shared__ __align__(16) float s_bias[8][128];   // each epilogue warp's copy of its half of the bias
+  // per epilogue warp: 32 rows x 16 words (+1 against bank conflicts), through
+  // which its global loads and stores go as contiguous row segments
+  __shared__ __align__(16) uint32_t s_stage[8][32 * 17];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -350,44 +353,77 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int64_t row = (blockIdx.x + (int64_t)t * gridDim.x) * TILE_M + q * 32 + lane;
+      // the warp's rows: row0w .. row0w + 31, this lane's row0w + lane
+      const int64_t row0w = (blockIdx.x + (int64_t)t * gridDim.x) * TILE_M + q * 32;
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u;
+      uint32_t* stg = s_stage[warp - 2];
+      // 16 words of the lane's row out to global memory, 8 rows x 64 bytes per
+      // instruction (lane: row 8 k + lane / 4, bytes 16 (lane mod 4) .. + 15)
+      auto store16 = [&](const uint32_t* w16, char* dst_row0, int64_t row_bytes) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = w16[j];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int rr = 8 * k + (lane >> 2), cc = (lane & 3) * 4;
+          if (row0w + rr < g.n)
+            *(uint4*)(dst_row0 + (int64_t)rr * row_bytes + cc * 4) =
+                make_uint4(stg[rr * 17 + cc], stg[rr * 17 + cc + 1], stg[rr * 17 + cc + 2],
+                           stg[rr * 17 + cc + 3]);
+        }
+        __syncwarp();
+      };
+      // the converse: 16 words of each row in, the lane taking its own row's
+      auto load16 = [&](uint32_t* w16, const char* src_row0, int64_t row_bytes) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int rr = 8 * k + (lane >> 2), cc = (lane & 3) * 4;
+          const uint4 v = row0w + rr < g.n
+                              ? *(const uint4*)(src_row0 + (int64_t)rr * row_bytes + cc * 4)
+                              : make_uint4(0u, 0u, 0u, 0u);
+          stg[rr * 17 + cc] = v.x;
+          stg[rr * 17 + cc + 1] = v.y;
+          stg[rr * 17 + cc + 2] = v.z;
+          stg[rr * 17 + cc + 3] = v.w;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) w16[j] = stg[lane * 17 + j];
+        __syncwarp();
+      };
       for (int c = c0; c < c0 + 128; c += 32) {
         uint32_t acc[32];
         tmem_ld32(taddr + (uint32_t)c, acc);
-        if (row < g.n) {
-          // (pairs converted by one instruction, each half rounded to nearest)
-          __align__(16) __nv_bfloat162 hv[16];
-          if (EPI == EPI_BWD) {
-            const float4* zp = (const float4*)(g.zprev + row * W + c);
+        // (pairs converted by one instruction, each half rounded to nearest)
+        __align__(16) __nv_bfloat162 hv[16];
+        if (EPI == EPI_BWD) {
+          __align__(16) float zp[32];
+          const char* z0 = (const char*)(g.zprev + row0w * W + c);
+          load16((uint32_t*)zp, z0, (int64_t)W * 4);
+          load16((uint32_t*)zp + 16, z0 + 64, (int64_t)W * 4);
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              const float4 z4 = zp[v];
-              hv[2 * v] = __floats2bfloat162_rn(__uint_as_float(acc[4 * v]) * silu_grad(z4.x),
-                                                __uint_as_float(acc[4 * v + 1]) * silu_grad(z4.y));
-              hv[2 * v + 1] = __floats2bfloat162_rn(__uint_as_float(acc[4 * v + 2]) * silu_grad(z4.z),
-                                                    __uint_as_float(acc[4 * v + 3]) * silu_grad(z4.w));
-            }
-          } else {
-            __align__(16) float zv[32];
+          for (int v = 0; v < 16; ++v)
+            hv[v] = __floats2bfloat162_rn(__uint_as_float(acc[2 * v]) * silu_grad(zp[2 * v]),
+                                          __uint_as_float(acc[2 * v + 1]) * silu_grad(zp[2 * v + 1]));
+        } else {
+          __align__(16) float zv[32];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              const float4 b4 = *(const float4*)(bias + c - c0 + 4 * v);
-              zv[4 * v] = __uint_as_float(acc[4 * v]) + b4.x;
-              zv[4 * v + 1] = __uint_as_float(acc[4 * v + 1]) + b4.y;
-              zv[4 * v + 2] = __uint_as_float(acc[4 * v + 2]) + b4.z;
-              zv[4 * v + 3] = __uint_as_float(acc[4 * v + 3]) + b4.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) hv[j] = __floats2bfloat162_rn(silu(zv[2 * j]), silu(zv[2 * j + 1]));
-            if (EPI == EPI_FWD_TRAIN) {
-#pragma unroll
-              for (int v = 0; v < 8; ++v) *(float4*)(g.zout + row * W + c + 4 * v) = *(float4*)(zv + 4 * v);
-            }
+          for (int v = 0; v < 8; ++v) {
+            const float4 b4 = *(const float4*)(bias + c - c0 + 4 * v);
+            zv[4 * v] = __uint_as_float(acc[4 * v]) + b4.x;
+            zv[4 * v + 1] = __uint_as_float(acc[4 * v + 1]) + b4.y;
+            zv[4 * v + 2] = __uint_as_float(acc[4 * v + 2]) + b4.z;
+            zv[4 * v + 3] = __uint_as_float(acc[4 * v + 3]) + b4.w;
           }
 #pragma unroll
-          for (int v = 0; v < 4; ++v) *(uint4*)(g.hout + row * W + c + 8 * v) = *(uint4*)(hv + 4 * v);
+          for (int j = 0; j < 16; ++j) hv[j] = __floats2bfloat162_rn(silu(zv[2 * j]), silu(zv[2 * j + 1]));
+          if (EPI == EPI_FWD_TRAIN) {
+            char* z0 = (char*)(g.zout + row0w * W + c);
+            store16((const uint32_t*)zv, z0, (int64_t)W * 4);
+            store16((const uint32_t*)zv + 16, z0 + 64, (int64_t)W * 4);
+          }
         }
+        store16((const uint32_t*)hv, (char*)(g.hout + row0w * W + c), (int64_t)W * 2);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
