@@ -118,6 +118,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
+// Bulk copy of `bytes` contiguous bytes (both addresses 16-byte aligned, a
+// multiple of 16 bytes) into shared memory, completion counted on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
 // TMA: a 2-D box of the tensor map at (x, y) into shared memory, completion
 // counted in bytes on the mbarrier (x * 2 B is a multiple of 16 by construction)
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
@@ -711,7 +721,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
   uint8_t* sA = sm;             // 256 (features) x 128 (samples) bf16 = 64 KB
   uint8_t* sB = sm + 65536;     // 256 (outputs)  x 128 (samples) bf16 = 64 KB
   uint8_t* sT = sm + 131072;    // staging: 128 (samples) x 256 bf16, row-major = 64 KB
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar, lbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -720,6 +730,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&lbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -732,26 +743,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = idesc_bf16(128, W);
-  uint32_t phase = 0;
+  uint32_t phase = 0, lphase = 0;
+  bool lpending = false;   // a bulk copy issued and not seen complete
   bool first = true;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t row0 = tile * TILE_M;
     // transpose on the way in: element (sample s, feature f) -> (f, s) of a K-major
-    // tile with K = samples (16 core matrices along K).  Each operand is first
-    // copied row-major into the staging buffer (16-byte stores); then each thread
-    // gathers eight consecutive samples of one feature (2-byte loads, consecutive
-    // features on consecutive lanes) and writes them as one 16-byte row of a core
-    // matrix.
+    // tile with K = samples (16 core matrices along K).  Each operand's rows (one
+    // contiguous block of global memory) arrive row-major in the staging buffer
+    // by one bulk copy, the rows past n as zeros; then each thread gathers eight
+    // consecutive samples of one feature (2-byte loads, consecutive features on
+    // consecutive lanes) and writes them as one 16-byte row of a core matrix.
+    const int valid = (int)(g.n - row0 < TILE_M ? g.n - row0 : TILE_M);
     for (int op = 0; op < 2; ++op) {
       const __nv_bfloat16* src = op ? g.dz : g.a;
       uint8_t* dst = op ? sB : sA;
-      for (int v = tid; v < TILE_M * 32; v += NTHREADS) {
-        const int s = v >> 5, fg = v & 31;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (row0 + s < g.n) val = *(const uint4*)(src + (row0 + s) * W + fg * 8);
-        *(uint4*)(sT + s * (W * 2) + fg * 16) = val;
+      for (int v = valid * 32 + tid; v < TILE_M * 32; v += NTHREADS)
+        *(uint4*)(sT + v * 16) = make_uint4(0, 0, 0, 0);
+      if (tid == 0) {
+        // (the previous gather's reads of the buffer are ordered before the copy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t bytes = (uint32_t)valid * (W * 2);
+        mbar_expect_tx(&lbar, bytes);
+        bulk_load(sT, src + row0 * W, bytes, &lbar);
+      }
+      lpending = true;
+      const uint32_t got = mbar_wait(&lbar, lphase);
+      if (got) {
+        lpending = false;
+        lphase ^= 1;
+      } else {   // (any thread whose wait gave up stops the CTA)
+        atomicOr(g.status, 1);
+        s_abort = 1;
       }
       __syncthreads();
+      if (s_abort) break;
       for (int v = tid; v < W * (TILE_M / 8); v += NTHREADS) {
         const int f = v & (W - 1), sg = v >> 8;   // feature, group of 8 samples
         __align__(16) __nv_bfloat16 e[8];
@@ -762,6 +788,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
       }
       __syncthreads();
     }
+    if (s_abort) break;
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -790,19 +817,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) gl_mlp_wgrad_kernel(WgradArgs g) 
     if (s_abort) break;
   }
   if (!s_abort) {
+    // the partial out through the (now free) staging buffer: the warp's 32 rows
+    // x 32 columns at a time, then 4 rows x 128 bytes per store instruction
+    float* stg = (float*)sT + warp * (32 * 33);
     for (int h = 0; h < 2; ++h) {
-      const int f = h * 128 + warp * 32 + lane;
+      const int f0 = h * 128 + warp * 32;
       for (int c = 0; c < W; c += 32) {
         uint32_t acc[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * W + c), acc);
-        float* dstp = g.part + (int64_t)blockIdx.x * W * W + (int64_t)f * W + c;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          *(float4*)(dstp + j) = make_float4(__uint_as_float(acc[j]), __uint_as_float(acc[j + 1]),
-                                             __uint_as_float(acc[j + 2]), __uint_as_float(acc[j + 3]));
+        for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(acc[j]);
+        __syncwarp();
+        float* dst0 = g.part + (int64_t)blockIdx.x * W * W + (int64_t)f0 * W + c;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int rr = 4 * k + (lane >> 3), cc = (lane & 7) * 4;
+          *(float4*)(dst0 + (int64_t)rr * W + cc) =
+              make_float4(stg[rr * 33 + cc], stg[rr * 33 + cc + 1], stg[rr * 33 + cc + 2],
+                          stg[rr * 33 + cc + 3]);
+        }
+        __syncwarp();
       }
     }
   }
+  if (tid == 0 && lpending) mbar_wait(&lbar, lphase);   // no copy in flight at exit
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
