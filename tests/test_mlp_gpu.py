@@ -114,9 +114,8 @@ def test_forward_matches_oracle(net, n):
     assert net.status() == binding.GL_OK
 
 
-def test_gradients_match_oracle(net):
-    n = 700                            # several 128-row tiles and a ragged tail
-    params, x, t = _setup(net, 2, n)
+def _grads_match_oracle(net, seed, n):
+    params, x, t = _setup(net, seed, n)
     loss = net.loss_grad(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
     g = unflatten(net.get_grads())
     gp = as_gpu_sees(params)
@@ -136,6 +135,22 @@ def test_gradients_match_oracle(net):
         _elementwise(gW, rW, sW, f"dW{li + 1}")
         _elementwise(gbias, rb, sb, f"db{li + 1}")
     assert net.status() == binding.GL_OK
+
+
+def test_gradients_match_oracle(net):
+    _grads_match_oracle(net, 2, 700)   # several 128-row tiles and a ragged tail
+
+
+def test_large_batch_gradients_match_oracle(net):
+    """More than one 128-row tile per SM: the forward runs one tensor-core kernel
+    per layer (training epilogue), the weight gradients take several tiles per
+    CTA; a ragged tail as well."""
+    n = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 + 300
+    net.profile(True)
+    _grads_match_oracle(net, 5, n)
+    _, launches = net.profile_read(binding.GL_MLP_KERNEL_GEMM_FWD)
+    net.profile(False)
+    assert launches == 3                      # one per layer
 
 
 def test_adam_step_matches_oracle(net):
